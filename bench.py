@@ -1,0 +1,336 @@
+"""Benchmark of the GB300 plane rasterizer: one fwd+bwd+Adam training step of
+the 1,000,000-Gaussian extreme-anisotropy workload (64 planes per launch,
+square sizes drawn from {128, 192, 256, 384, 512}, triangular front-end, box
+cut-off), captured in one CUDA graph and replayed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. `value` is useful Gaussian-pixel pairs per second: the
+pairs the box cut-off includes (each evaluated in the forward and again in the
+backward pass of a step) divided by the step time; `steps_per_s` is the train
+step rate. `--impl reference` times the FP64 CPU oracle (the only other
+implementation of this method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gaussian·pixel evals/s and fwd+bwd train steps/s, 1M Gaussians, 1×GB300"
+WORKLOAD = "aniso_1m: 1,000,000 Gaussians, axis ratios log-uniform to 1e4, 64 planes/launch " \
+           "sized from {128,192,256,384,512}^2, fwd+bwd+Adam step"
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _clock_sampler(gpu_index: int, path: str):
+    fields = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={fields}",
+                              "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def _clock_summary(path: str) -> dict:
+    sm, smax, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active") or val == "0x0000000000000001" or val == "1":
+                    reasons.add(name)
+    except OSError:
+        pass
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax or None,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload(n_override=None):
+    from paper_2505_05643_gb300 import synth
+    g, pl = synth.workload_aniso_1m()
+    if n_override:
+        g = {k: v[..., :n_override] for k, v in g.items()}
+    g = synth.scale_rot_to_tri(g, 1e-4)
+    target = synth.target_images(np.random.default_rng(7), pl["total_pixels"])
+    return g, pl, target
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(g, pl, sample_planes=(0,), threads=0):
+    """FP64 oracle (scatter forward + analytic backward) on a bounded sample
+    of planes of the same workload. Returns (pairs/s, seconds, cores, pairs)."""
+    import oracle
+    from paper_2505_05643_gb300 import synth
+    cfg = oracle.Config(cov_param=0)
+    idx = np.asarray(sample_planes)
+    sub = synth.select_planes(pl, idx)
+    tgt = synth.target_images(np.random.default_rng(7), sub["total_pixels"])
+    t0 = time.perf_counter()
+    out = oracle.render(g, sub, cfg, mode="scatter", threads=threads)
+    _, gimg = oracle.mse_loss_grad(out["image"], tgt)
+    oracle.render_grad(g, sub, cfg, out["image"], out["alpha"], gimg, threads=threads)
+    dt = time.perf_counter() - t0
+    cores = threads or oracle.max_threads()
+    return out["pairs"] / dt, dt, cores, out["pairs"]
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    g, pl, _ = _workload()
+    sizes = pl["size"][:, 0]
+    smallest = [int(np.argmin(sizes))]
+    # each step: the oracle's forward + backward over the smallest plane (all 1M Gaussians)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps are not needed for a CPU program
+    rates, secs = [], []
+    cores = 1
+    pairs = 0
+    for _ in range(args.steps):
+        rate, dt, cores, pairs = cpu_oracle_rate(g, pl, smallest)
+        rates.append(rate)
+        secs.append(dt)
+    value = float(np.mean(rates))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"plane {smallest[0]} ({sizes[smallest[0]]}^2) of 64"},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                         "sample": f"FP64 oracle scatter forward + analytic backward, 1 of 64 planes "
+                                   f"({sizes[smallest[0]]}^2, {pairs} pairs), all 1,000,000 Gaussians"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU
+def run_ours(args):
+    import torch
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2505_05643_gb300 import binding as B
+    from paper_2505_05643_gb300 import render as R
+    from paper_2505_05643_gb300 import train as T
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+
+    # every rank trains its own replica of the workload (weak scaling, no collective)
+    g, pl, target = _workload(args.n)
+    cfg = R.make_config(cov_param=B.UG_COV_TRI, cutoff=B.UG_CUTOFF_BOX, tile=args.tile,
+                        variant=args.variant)
+    n = len(g["logit"])
+    renderer = R.Renderer(n, pl, cfg)
+    params = torch.from_numpy(R.pack_params(g, B.UG_COV_TRI)).to(dev)
+    targets = torch.from_numpy(target).to(dev)
+    step = T.TrainStep(renderer, params, targets)
+    # size the workspace with margin for the drift of a few hundred steps
+    st0 = renderer.preprocess(params, check=True)
+    rec = int(st0["records"] * 1.3) + 4096
+    inst = min(int(st0["instances"] * 1.3) + 65536, (1 << 31) - 1)
+    renderer._alloc(rec, inst)
+    step.g_struct = R.gaussians_struct(params, B.UG_COV_TRI)
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            step.enqueue(s)
+    s.synchronize()
+    graph = step.capture(s)
+    status_log = torch.zeros((args.warmup + args.steps, 64), dtype=torch.uint8, device=dev)
+
+    def one(k):
+        graph.replay()
+        B.ug_read_status(renderer.plan, renderer.ws, status_log[k], s)
+
+    with torch.cuda.stream(s):
+        for k in range(args.warmup):
+            one(k)
+    s.synchronize()
+    # phase timing of the dominant kernel: events around ug_render_backward in an
+    # eager copy of the step on the same stream (the graph replays the same launches)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                            f".bench_clocks_{rank}.csv")
+    sampler, fh = _clock_sampler(dev.index or 0, clk_path)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(s)
+    with torch.cuda.stream(s):
+        for k in range(args.steps):
+            one(args.warmup + k)
+    stop.record(s)
+    torch.cuda.synchronize()
+    total_ms = start.elapsed_time(stop)
+    # the dominant kernel's duration, on the launching stream, over K eager steps
+    bwd_ms, fwd_ms = [], []
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    r = renderer
+    with torch.cuda.stream(s):
+        for k in range(args.steps):
+            B.ug_preprocess(r.plan, step.g_struct, r.d_planes, r.ws, s)
+            B.ug_bin_sort(r.plan, r.ws, s)
+            e[0].record(s)
+            B.ug_render(r.plan, r.ws, step.image, step.alpha, s)
+            e[1].record(s)
+            B.ug_mse_loss_grad(step.image, step.targets, step.image.numel(), step.grad_image,
+                               step.loss, s)
+            e[2].record(s)
+            B.ug_render_backward(r.plan, step.g_struct, r.d_planes, r.ws, step.image, step.alpha,
+                                 step.grad_image, step.grad_struct, s)
+            e[3].record(s)
+            B.ug_adam_step(step.params, step.grads, step.m, step.v, r.rows, r.n, step.lr_rows,
+                           step.step, T.BETA1, T.BETA2, T.EPS, s)
+            s.synchronize()
+            fwd_ms.append(e[0].elapsed_time(e[1]))
+            bwd_ms.append(e[2].elapsed_time(e[3]))
+    if sampler is not None:
+        sampler.terminate()
+        sampler.wait()
+        fh.close()
+    clocks = _clock_summary(clk_path)
+    ms_step = total_ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    logs = status_log.cpu().numpy()
+    sts = [B.ug_ws_status.from_buffer_copy(row.tobytes()) for row in logs]
+    bad = [x.status for x in sts if x.status != 0]
+    if bad:
+        raise RuntimeError(f"device status {bad[0]} during the timed steps")
+    pairs = float(np.mean([x.box_pixels for x in sts[args.warmup:]]))
+    value = pairs * world / (ms_step * 1e-3)
+
+    # ---- e2e: the public API with host buffers; the step's inputs (targets and
+    # plane poses) copied from pinned host memory and the loss read back each step
+    h_targets = torch.from_numpy(target).pin_memory()
+    h_planes = torch.from_numpy(r.host_planes.view(np.uint8).copy()).pin_memory()
+    h_loss = torch.zeros(1, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, min(args.steps, 10))
+    with torch.cuda.stream(s):
+        for k in range(e2e_steps):
+            step.targets.copy_(h_targets, non_blocking=True)
+            r.d_planes.copy_(h_planes, non_blocking=True)
+            step.enqueue(s)
+            h_loss.copy_(step.loss[:1], non_blocking=True)
+            s.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": pairs * world / e2e_s, "unit": "pairs/s",
+           "h2d_bytes_per_step": int(h_targets.numel() * 4 + h_planes.numel()),
+           "d2h_bytes_per_step": 4}
+
+    # ---- roofline of the dominant kernel (backward rasterizer, ALU bound)
+    # algorithmic FP32 flops per included pair: forward 13 + 1 ex2,
+    # backward 30 + 1 ex2; peak from unit counts and clocks: 152 SMs x 128 FP32
+    # lanes x 2 flops (FMA) x 2070 MHz.
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    fp32_peak = sms * 128 * 2 * fmax
+    bwd_s = float(np.median(bwd_ms)) * 1e-3
+    fwd_s = float(np.median(fwd_ms)) * 1e-3
+    bwd_flops = 30.0 * pairs
+    roof = {"bound": "alu", "kernel": "k_render_bwd (ug_render_backward)",
+            "achieved": bwd_flops / bwd_s / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+            "frac": (bwd_flops / bwd_s) / fp32_peak, "traffic": None,
+            "peak_note": "derived: SMs x 128 FP32 lanes x 2 x max SM clock (FP32 FMA pipe)",
+            "fwd": {"achieved": 13.0 * pairs / fwd_s / 1e12, "ms": fwd_s * 1e3},
+            "bwd_ms": bwd_s * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sizes = pl["size"][:, 0]
+        smallest = int(np.argmin(sizes))
+        rate, dt, cores, cp = cpu_oracle_rate(g, pl, [smallest])
+        cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle scatter forward + analytic backward on plane {smallest} "
+                         f"({sizes[smallest]}^2, {cp} pairs) with all {n} Gaussians, {dt:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": n, "planes": len(pl["size"]),
+                       "pixels": int(pl["total_pixels"]), "pairs_per_step": pairs,
+                       "tile": args.tile, "variant": args.variant, "graph": True,
+                       "l2": "working set > L2 (129 MB); no flush",
+                       "parallelism": f"replicas x{world}"},
+            "steps_per_s": 1e3 / ms_step,
+            "gpu_launches": step.kernels_per_step() * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "fp64_records": int(sts[-1].fp64_records), "records": int(sts[-1].records),
+            "instances": int(sts[-1].instances),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--n", type=int, default=None, help="use the first n Gaussians (testing)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

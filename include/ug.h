@@ -1,0 +1,246 @@
+/*
+ * ug.h — C ABI of the GB300 UltraGauss plane rasterizer.
+ *
+ * UltraGauss (arXiv 2505.05643) renders an ultrasound image as the
+ * intersection of anisotropic 3D Gaussians with a probe plane (Sec. 3.1):
+ * each pixel x of the plane is lifted to x_|0 = [x1, x2, 0] in the probe frame
+ * and takes
+ *
+ *     C(x) = (sum_i w_i(x) c_i + a_bg c_bg) / (sum_i w_i(x) + a_bg),
+ *     w_i(x) = alpha_i exp(-1/2 (x_|0 - mu3D_i)^T (Sigma3D_i)^-1 (x_|0 - mu3D_i))
+ *
+ * (Eq. alpha-combine, Eq. colour-combine, Eq. us-render, Eq. mahalanobis-3d),
+ * summed only over pixels inside each Gaussian's chi^2 bounding box
+ * (Sec. 3.3, Eq. ellipsoid and Eq. boundary) and only for Gaussians whose
+ * box meets the plane (Sec. 3.4). Covariances use the paper's triangular
+ * precision factor Sigma^-1 = L L^T with diagonal l_kk^2 + beta (Sec. 3.2,
+ * Eq. tri-param) or, as a second front-end, Sigma = R diag(s^2) R^T.
+ *
+ * Conventions shared by every call:
+ *  - All array pointers are DEVICE pointers unless a parameter says "host".
+ *    The caller owns all memory; the library never allocates or frees and
+ *    never synchronises the stream.
+ *  - Gaussian parameters are structure-of-arrays, "row" layout: a parameter
+ *    with k components is a row-major [k][n] float32 array (component r of
+ *    Gaussian g at index r * n + g), n = ug_plan.n.
+ *  - Argument errors are returned synchronously. Data-dependent errors
+ *    (capacity overflow, an invalid plane pose in device memory, an internal
+ *    inconsistency) are written to the workspace status word by the kernels;
+ *    every later kernel of the same workspace then does nothing, the outputs
+ *    are invalid, and ug_read_status reports the error and the sizes needed.
+ *  - Every call only enqueues work on `stream` and can be captured in a CUDA
+ *    graph.
+ *  - Outputs are overwritten, not accumulated.
+ */
+#ifndef UG_H
+#define UG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (0 = the legacy default stream). */
+typedef struct CUstream_st* ug_stream;
+
+typedef enum {
+  UG_OK = 0,
+  UG_ERR_INVALID_ARGUMENT = 1,    /* bad pointer, size, config or host plane */
+  UG_ERR_WORKSPACE_TOO_SMALL = 2, /* ws_bytes < ug_plan.workspace_bytes */
+  UG_ERR_CAPACITY = 3,            /* device: more records/instances than the plan holds */
+  UG_ERR_CUDA = 4,                /* a CUDA launch or copy failed */
+  UG_ERR_TIMEOUT = 5,             /* device: a bounded wait gave up */
+  UG_ERR_NOT_SUPPORTED = 6,       /* config value not compiled in (e.g. tile shape) */
+  UG_ERR_INVALID_PLANE = 7,       /* device: a plane in device memory is not a valid pose */
+  UG_ERR_INTERNAL = 8             /* device: two passes disagreed (a bug) */
+} ug_status;
+
+enum { UG_COV_TRI = 0, UG_COV_SCALE_ROT = 1 };
+enum { UG_CUTOFF_BOX = 0, UG_CUTOFF_BOX_AND_ELLIPSOID = 1 };
+
+/* Gaussian parameters (device, row layout, float32). For UG_COV_TRI `tri` is
+ * [6][n] = l11, l21, l31, l22, l32, l33 and log_scale/quat are unused; for
+ * UG_COV_SCALE_ROT `log_scale` is [3][n] (s = exp(log_scale)) and `quat` is
+ * [4][n] = w, x, y, z (normalised inside; need not be unit). mean is [3][n];
+ * opacity_logit and intensity are [n] (alpha = sigmoid(logit), Sec. 3.4). */
+typedef struct {
+  const float* mean;
+  const float* tri;
+  const float* log_scale;
+  const float* quat;
+  const float* opacity_logit;
+  const float* intensity;
+} ug_gaussians;
+
+/* Gradient outputs, same layout as ug_gaussians (written, not accumulated).
+ * Rows of the unused front-end may be NULL. */
+typedef struct {
+  float* mean;
+  float* tri;
+  float* log_scale;
+  float* quat;
+  float* opacity_logit;
+  float* intensity;
+} ug_gaussian_grads;
+
+/* One probe plane (64 bytes). The probe frame has rows u, v, n = u x v and
+ * origin `origin` at the plane centre; u, v must be orthonormal to 1e-4.
+ * Pixel (i, j), 0 <= i < height, 0 <= j < width, has its centre at
+ *   x1 = (j + 1/2 - width/2) * pitch_u,  x2 = (i + 1/2 - height/2) * pitch_v
+ * and is stored at image[pixel_offset + i * width + j]. */
+typedef struct {
+  float origin[3];
+  float u[3];
+  float v[3];
+  float pitch_u, pitch_v;
+  int32_t width, height; /* 1 .. 16384 */
+  int32_t reserved;      /* must be 0 */
+  int64_t pixel_offset;
+} ug_plane;
+
+/* Cut-off and image-formation constants, tile shape and kernel variant. */
+typedef struct {
+  float chi2;        /* chi^2_3 bound of the cut-off ellipsoid; 7.815 (p = 95 %, Sec. 3.3) */
+  float beta;        /* diagonal offset of Eq. tri-param, > 0; default 1e-4 */
+  float alpha_bg;    /* background coefficient a_bg > 0 (Eq. alpha-combine); default 1e-3 */
+  float c_bg;        /* background intensity; default 0 */
+  int32_t cutoff;    /* UG_CUTOFF_BOX (paper) or UG_CUTOFF_BOX_AND_ELLIPSOID */
+  int32_t cov_param; /* UG_COV_TRI (paper) or UG_COV_SCALE_ROT */
+  int32_t tile;      /* square tile edge in pixels: 8 or 16 (default 16) */
+  int32_t variant;   /* rasterizer variant (ug_num_variants); 0 = default */
+  float fp64_ratio;  /* axis-ratio proxy above which the covariance inverse runs in FP64; 1e3 */
+  int32_t reserved[3];
+} ug_config;
+
+/* Sizes, capacities and the workspace layout of one rendering problem.
+ * Filled by ug_plan_init; treat as read-only afterwards. */
+typedef struct {
+  ug_config cfg;
+  int64_t n;                 /* Gaussians */
+  int32_t num_planes;
+  int32_t total_tiles;
+  int64_t total_pixels;      /* length of the image buffers */
+  int64_t record_capacity;   /* visible (plane, Gaussian) pairs the workspace holds */
+  int64_t instance_capacity; /* (tile, record) pairs the workspace holds, < 2^31 */
+  int32_t key_bits;          /* bits of the tile key */
+  int32_t sort_passes;       /* 8-bit LSD passes */
+  int64_t chunks;            /* ceil(n / 32) */
+  size_t workspace_bytes;
+  size_t off[24];            /* internal section offsets */
+} ug_plan;
+
+/* Workspace status (64 bytes), copied out by ug_read_status. */
+typedef struct {
+  int32_t status;       /* ug_status of the first data-dependent failure, 0 if none */
+  int32_t detail;       /* e.g. the index of an invalid plane */
+  int64_t records;      /* visible (plane, Gaussian) records found by the last preprocess */
+  int64_t instances;    /* (tile, record) instances found by the last preprocess */
+  int64_t fp64_records; /* records whose covariance inverse ran in FP64 */
+  int64_t box_pixels;   /* sum over records of their clipped pixel-box area: the number
+                           of (pixel, Gaussian) pairs the box cut-off includes */
+  int64_t reserved[3];
+} ug_ws_status;
+
+/* Adam learning-rate schedule of one parameter row (device array entry):
+ * lr(t) = lr_init * (lr_final / lr_init)^min(t / decay_steps, 1); decay_steps
+ * <= 0 keeps lr_init (Sec. 3.4: 0.05 for all rows, the means' rows decay from
+ * 1.6e-4). */
+typedef struct {
+  float lr_init, lr_final;
+  int32_t decay_steps;
+  int32_t reserved;
+} ug_adam_row;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int32_t ug_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char* ug_status_string(ug_status status);
+
+/* Number of rasterizer variants compiled in for `tile` (0 if unsupported). */
+int32_t ug_num_variants(int32_t tile);
+
+/* Fill *cfg with the defaults listed above. */
+ug_status ug_config_default(ug_config* cfg);
+
+/* Validate a configuration and the HOST copy of the planes (sizes, pixel
+ * offsets, finite orthonormal poses) and fill *plan: tile counts, key bits,
+ * and the workspace size for the given capacities. record_capacity and
+ * instance_capacity must be >= 1; instance_capacity < 2^31. The plane poses
+ * may change later in device memory; their sizes may not. */
+ug_status ug_plan_init(const ug_config* cfg, int64_t n, const ug_plane* host_planes,
+                       int32_t num_planes, int64_t record_capacity,
+                       int64_t instance_capacity, ug_plan* plan);
+
+/* Rows a1-a3 (Sec. 3.2-3.4): per (plane, Gaussian) activation, probe-frame
+ * mean, Sigma3D by forward substitution, chi^2 box, phase-1 rejection, pixel
+ * box, in-plane conic and peak weight; then the records of the visible pairs
+ * in (Gaussian chunk, plane, Gaussian) order and their (tile, record)
+ * instances. d_planes: device array of plan->num_planes ug_plane with the
+ * sizes given to ug_plan_init. Resets the status word first. */
+ug_status ug_preprocess(const ug_plan* plan, const ug_gaussians* gaussians,
+                        const ug_plane* d_planes, void* ws, size_t ws_bytes, ug_stream stream);
+
+/* Row a4: stable LSD radix sort of the instances on their tile key (so each
+ * tile lists its records in ascending (plane, Gaussian) order) and the
+ * [start, end) range of every tile. */
+ug_status ug_bin_sort(const ug_plan* plan, void* ws, size_t ws_bytes, ug_stream stream);
+
+/* Row a5 (Eq. us-render with Eq. alpha-combine / colour-combine): writes
+ * image[total_pixels] = C and alpha[total_pixels] = sum_i w_i + a_bg (the
+ * rendered opacity, kept for the backward pass). Pixels not covered by any
+ * plane are left untouched. */
+ug_status ug_render(const ug_plan* plan, void* ws, size_t ws_bytes, float* image,
+                    float* alpha, ug_stream stream);
+
+/* Floats of device memory the `loss` argument of ug_mse_loss_grad points to. */
+#define UG_MSE_LOSS_FLOATS 1025
+
+/* Row a6: mean squared error over n pixels. Writes grad_image[n] =
+ * 2 (image - target) / n (if grad_image != NULL) and loss[0] = mean((image -
+ * target)^2). `loss` points to UG_MSE_LOSS_FLOATS device floats: loss[0] gets
+ * the value, the rest holds per-block partial sums, so the result does not
+ * depend on scheduling (deterministic). */
+ug_status ug_mse_loss_grad(const float* image, const float* target, int64_t n,
+                           float* grad_image, float* loss, ug_stream stream);
+
+/* Rows a7-a8: gradient of a scalar loss with respect to the Gaussian
+ * parameters, given dL/dC per pixel (grad_image) and the image and alpha that
+ * ug_render wrote for the same workspace. The box cut-off is a constant of the
+ * derivative. Gradients are summed over planes and written to *grads. */
+ug_status ug_render_backward(const ug_plan* plan, const ug_gaussians* gaussians,
+                             const ug_plane* d_planes, void* ws, size_t ws_bytes,
+                             const float* image, const float* alpha, const float* grad_image,
+                             const ug_gaussian_grads* grads, ug_stream stream);
+
+/* Row a9: one Adam step on `rows` parameter rows of n floats each, all in one
+ * contiguous [rows][n] buffer (param, grad, exp_avg, exp_avg_sq alike):
+ *   m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2;
+ *   p <- p - lr_r(t) / (1 - b1^t) * m / (sqrt(v) / sqrt(1 - b2^t) + eps)
+ * where t = *d_step + 1 is read from device memory and *d_step is then
+ * incremented on the device (so a captured graph advances by itself), and
+ * lr_r(t) follows d_rows[r] (device array of `rows` ug_adam_row). */
+ug_status ug_adam_step(float* param, const float* grad, float* exp_avg, float* exp_avg_sq,
+                       int32_t rows, int64_t n, const ug_adam_row* d_rows, int32_t* d_step,
+                       float beta1, float beta2, float eps, ug_stream stream);
+
+/* Copy the workspace status to `out` (host pinned or device memory) on
+ * `stream`; the caller synchronises before reading it. */
+ug_status ug_read_status(const ug_plan* plan, const void* ws, size_t ws_bytes, ug_ws_status* out,
+                         ug_stream stream);
+
+/* Device pointers into the workspace, for inspection and tests: the sorted
+ * tile keys and record ids (instance order), the tile ranges (uint32 pairs
+ * [start, end) per tile), and the records' pixel boxes (uint32 pairs:
+ * j0 | j1 << 16, i0 | i1 << 16). Valid after ug_bin_sort. */
+ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_t** sorted_keys,
+                         uint32_t** sorted_records, uint32_t** tile_ranges,
+                         uint32_t** record_boxes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UG_H */

@@ -1,0 +1,332 @@
+// Per-Gaussian and per-(plane, Gaussian) geometry of the plane rasterizer.
+//
+// Everything that decides which pairs exist (the covariance factor, the
+// FP64 switch, the phase-1 test and the pixel box) is written with explicit
+// round-to-nearest intrinsics, so the compiler cannot contract or reorder it:
+// the counting pass and the emitting pass, compiled into different kernels,
+// take bit-identical decisions.
+#pragma once
+
+#include "ug_internal.cuh"
+
+namespace ug {
+
+// ------------------------------------------------------------ exact-rounding ops
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float r_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float r_sqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double r_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double r_sqrt(double a) { return __dsqrt_rn(a); }
+
+template <typename T>
+__device__ __forceinline__ T r_dot3(const T a[3], const T b[3]) {
+  return r_fma(a[2], b[2], r_fma(a[1], b[1], r_mul(a[0], b[0])));
+}
+
+// Parameters of one Gaussian as loaded from the structure-of-arrays rows.
+struct GaussParams {
+  float mu[3];
+  float cp[7];  // tri[6] or log_scale[3] + quat[4]
+  float logit, c;
+};
+
+__device__ __forceinline__ void load_params(const ug_gaussians& g, int64_t n, int64_t i, int cov,
+                                            GaussParams& p) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) p.mu[k] = __ldg(g.mean + k * n + i);
+  if (cov == UG_COV_TRI) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p.cp[k] = __ldg(g.tri + k * n + i);
+    p.cp[6] = 0.f;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p.cp[k] = __ldg(g.log_scale + k * n + i);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p.cp[3 + k] = __ldg(g.quat + k * n + i);
+  }
+  p.logit = __ldg(g.opacity_logit + i);
+  p.c = __ldg(g.intensity + i);
+}
+
+// Covariance factor of one Gaussian: Sigma^-1 = F F^T, Fi = F^-1.
+// Triangular (Sec. 3.2, Eq. tri-param): F = L lower triangular with diagonal
+// l_kk^2 + beta; Fi by forward substitution. Scale/rotation: F = R diag(1/s),
+// Fi = diag(s) R^T with R from the normalised quaternion.
+template <typename T>
+struct Factor {
+  T mu[3];
+  T F[3][3];
+  T Fi[3][3];
+  T s[3];      // scales (scale/rotation only)
+  T qn[4];     // normalised quaternion (scale/rotation only)
+  T qnorm;
+};
+
+template <typename T, int COV>
+__device__ __forceinline__ void make_factor(const GaussParams& p, float beta, Factor<T>& f) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) f.mu[k] = (T)p.mu[k];
+  if (COV == UG_COV_TRI) {
+    const T b = (T)beta;
+    const T t0 = (T)p.cp[0], t1 = (T)p.cp[1], t2 = (T)p.cp[2];
+    const T t3 = (T)p.cp[3], t4 = (T)p.cp[4], t5 = (T)p.cp[5];
+    f.F[0][0] = r_fma(t0, t0, b);
+    f.F[0][1] = (T)0;
+    f.F[0][2] = (T)0;
+    f.F[1][0] = t1;
+    f.F[1][1] = r_fma(t3, t3, b);
+    f.F[1][2] = (T)0;
+    f.F[2][0] = t2;
+    f.F[2][1] = t4;
+    f.F[2][2] = r_fma(t5, t5, b);
+    const T i00 = r_div((T)1, f.F[0][0]);
+    const T i11 = r_div((T)1, f.F[1][1]);
+    const T i22 = r_div((T)1, f.F[2][2]);
+    // L Fi = I column by column (forward substitution)
+    const T i10 = -r_mul(r_mul(f.F[1][0], i00), i11);
+    const T i21 = -r_mul(r_mul(f.F[2][1], i11), i22);
+    const T i20 = -r_mul(r_fma(f.F[2][1], i10, r_mul(f.F[2][0], i00)), i22);
+    f.Fi[0][0] = i00;
+    f.Fi[0][1] = (T)0;
+    f.Fi[0][2] = (T)0;
+    f.Fi[1][0] = i10;
+    f.Fi[1][1] = i11;
+    f.Fi[1][2] = (T)0;
+    f.Fi[2][0] = i20;
+    f.Fi[2][1] = i21;
+    f.Fi[2][2] = i22;
+    f.s[0] = f.s[1] = f.s[2] = (T)0;
+    f.qn[0] = f.qn[1] = f.qn[2] = f.qn[3] = (T)0;
+    f.qnorm = (T)1;
+  } else {
+    const T q0 = (T)p.cp[3], q1 = (T)p.cp[4], q2 = (T)p.cp[5], q3 = (T)p.cp[6];
+    const T nq = r_sqrt(r_fma(q3, q3, r_fma(q2, q2, r_fma(q1, q1, r_mul(q0, q0)))));
+    const T w = r_div(q0, nq), x = r_div(q1, nq), y = r_div(q2, nq), z = r_div(q3, nq);
+    f.qn[0] = w;
+    f.qn[1] = x;
+    f.qn[2] = y;
+    f.qn[3] = z;
+    f.qnorm = nq;
+    T R[3][3];
+    R[0][0] = (T)1 - (T)2 * r_fma(y, y, r_mul(z, z));
+    R[0][1] = (T)2 * r_fma(x, y, -r_mul(w, z));
+    R[0][2] = (T)2 * r_fma(x, z, r_mul(w, y));
+    R[1][0] = (T)2 * r_fma(x, y, r_mul(w, z));
+    R[1][1] = (T)1 - (T)2 * r_fma(x, x, r_mul(z, z));
+    R[1][2] = (T)2 * r_fma(y, z, -r_mul(w, x));
+    R[2][0] = (T)2 * r_fma(x, z, -r_mul(w, y));
+    R[2][1] = (T)2 * r_fma(y, z, r_mul(w, x));
+    R[2][2] = (T)1 - (T)2 * r_fma(x, x, r_mul(y, y));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      f.s[a] = (T)expf(p.cp[a]);
+      if (sizeof(T) == 8) f.s[a] = (T)exp((double)p.cp[a]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        f.F[k][a] = r_div(R[k][a], f.s[a]);
+        f.Fi[a][k] = r_mul(f.s[a], R[k][a]);
+      }
+  }
+}
+
+// Axis-ratio proxy: ||L||_F ||L^-1||_F (between the axis ratio and 3x it) for
+// the triangular factor, max(s)/min(s) for scale/rotation.
+template <int COV>
+__device__ __forceinline__ float axis_ratio_proxy(const Factor<float>& f) {
+  if (COV == UG_COV_TRI) {
+    float a = 0.f, b = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        a = r_fma(f.F[i][j], f.F[i][j], a);
+        b = r_fma(f.Fi[i][j], f.Fi[i][j], b);
+      }
+    return r_sqrt(r_mul(a, b));
+  } else {
+    const float smax = fmaxf(f.s[0], fmaxf(f.s[1], f.s[2]));
+    const float smin = fminf(f.s[0], fminf(f.s[1], f.s[2]));
+    return r_div(smax, smin);
+  }
+}
+
+// z = Fi r (Sigma3D_jk = z_j . z_k).
+template <typename T, int COV>
+__device__ __forceinline__ void apply_fi(const Factor<T>& f, const T r[3], T z[3]) {
+  if (COV == UG_COV_TRI) {
+    z[0] = r_mul(f.Fi[0][0], r[0]);
+    z[1] = r_fma(f.Fi[1][1], r[1], r_mul(f.Fi[1][0], r[0]));
+    z[2] = r_fma(f.Fi[2][2], r[2], r_fma(f.Fi[2][1], r[1], r_mul(f.Fi[2][0], r[0])));
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      z[a] = r_fma(f.Fi[a][2], r[2], r_fma(f.Fi[a][1], r[1], r_mul(f.Fi[a][0], r[0])));
+  }
+}
+
+// b = F^T r (probe-frame precision P3D_jk = b_j . b_k).
+template <typename T, int COV>
+__device__ __forceinline__ void apply_ft(const Factor<T>& f, const T r[3], T b[3]) {
+  if (COV == UG_COV_TRI) {
+    b[0] = r_fma(f.F[2][0], r[2], r_fma(f.F[1][0], r[1], r_mul(f.F[0][0], r[0])));
+    b[1] = r_fma(f.F[2][1], r[2], r_mul(f.F[1][1], r[1]));
+    b[2] = r_mul(f.F[2][2], r[2]);
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      b[a] = r_fma(f.F[2][a], r[2], r_fma(f.F[1][a], r[1], r_mul(f.F[0][a], r[0])));
+  }
+}
+
+// Plane axes in precision T.
+template <typename T>
+struct Frame {
+  T o[3], r[3][3];  // rows u, v, n
+};
+
+template <typename T>
+__device__ __forceinline__ void load_frame(const PlaneDev& pl, Frame<T>& fr) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    fr.o[k] = (T)pl.o[k];
+    fr.r[0][k] = (T)pl.u[k];
+    fr.r[1][k] = (T)pl.v[k];
+    fr.r[2][k] = (T)pl.n[k];
+  }
+}
+
+// Phase 1 and the pixel box of one (plane, Gaussian) pair.
+struct PairBox {
+  bool visible;
+  int j0, j1, i0, i1;
+};
+
+template <typename T>
+struct PairGeo {
+  T m[3];     // probe-frame mean
+  T z[3][3];  // Fi u, Fi v, Fi n
+  T S11, S22, S33;
+};
+
+// Pixel range [ceil(lo), floor(hi)] of the closed interval in pixel units,
+// clipped to [0, size - 1]; lo > hi or non-finite gives an empty range.
+template <typename T>
+__device__ __forceinline__ void pixel_range(T c, T h, T inv_pitch, T shift, int size, int& a,
+                                            int& b) {
+  const T lo = r_fma(r_sub(c, h), inv_pitch, shift);
+  const T hi = r_fma(r_add(c, h), inv_pitch, shift);
+  if (!(lo <= hi) || !(hi >= (T)0) || !(lo <= (T)(size - 1))) {
+    a = 1;
+    b = 0;
+    return;
+  }
+  const T lo_c = lo < (T)0 ? (T)0 : lo;
+  const T hi_c = hi > (T)(size - 1) ? (T)(size - 1) : hi;
+  a = (int)ceil(lo_c);
+  b = (int)floor(hi_c);
+}
+
+// Sec. 3.3-3.4: h_k = sqrt(chi2 Sigma3D_kk); reject unless m3 - h3 <= 0 <=
+// m3 + h3; pixel j is inside iff m1 - h1 <= (j + 1/2 - W/2) pitch_u <= m1 + h1.
+template <typename T, int COV>
+__device__ __forceinline__ PairBox pair_box(const Factor<T>& f, const PlaneDev& pl, float chi2,
+                                            PairGeo<T>& g) {
+  PairBox pb;
+  pb.visible = false;
+  pb.j0 = 1;
+  pb.j1 = 0;
+  pb.i0 = 1;
+  pb.i1 = 0;
+  Frame<T> fr;
+  load_frame(pl, fr);
+  T d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = r_sub(f.mu[k], fr.o[k]);
+  g.m[2] = r_dot3(fr.r[2], d);
+  apply_fi<T, COV>(f, fr.r[2], g.z[2]);
+  g.S33 = r_dot3(g.z[2], g.z[2]);
+  const T c2 = (T)chi2;
+  const T h3 = r_sqrt(r_mul(c2, g.S33));
+  if (!(r_sub(g.m[2], h3) <= (T)0 && r_add(g.m[2], h3) >= (T)0)) return pb;
+  g.m[0] = r_dot3(fr.r[0], d);
+  g.m[1] = r_dot3(fr.r[1], d);
+  apply_fi<T, COV>(f, fr.r[0], g.z[0]);
+  apply_fi<T, COV>(f, fr.r[1], g.z[1]);
+  g.S11 = r_dot3(g.z[0], g.z[0]);
+  g.S22 = r_dot3(g.z[1], g.z[1]);
+  const T h1 = r_sqrt(r_mul(c2, g.S11));
+  const T h2 = r_sqrt(r_mul(c2, g.S22));
+  pixel_range<T>(g.m[0], h1, (T)pl.inv_pu, (T)pl.jshift, pl.w, pb.j0, pb.j1);
+  pixel_range<T>(g.m[1], h2, (T)pl.inv_pv, (T)pl.ishift, pl.h, pb.i0, pb.i1);
+  pb.visible = (pb.j0 <= pb.j1) && (pb.i0 <= pb.i1);
+  return pb;
+}
+
+// Full record of a visible pair (render-side form, see ug_internal.cuh).
+template <typename T>
+struct PairRec {
+  T xs1, xs2;      // in-plane peak x* (world units)
+  T kappa[2];      // x* = m12 + m3 kappa, kappa = -(S13, S23) / S33
+  T k;             // m3 / S33
+  T q0;            // m3^2 / S33
+  T b[3][3];       // F^T u, F^T v, F^T n
+  T nb1, cr;       // |b1|, |b1 x b2|
+  T r11, r12, r22; // Cholesky of (log2 e / 2) D A D
+};
+
+template <typename T, int COV>
+__device__ __forceinline__ void pair_record(const Factor<T>& f, const PlaneDev& pl,
+                                            const PairGeo<T>& g, PairRec<T>& rc) {
+  Frame<T> fr;
+  load_frame(pl, fr);
+  const T S13 = r_dot3(g.z[0], g.z[2]);
+  const T S23 = r_dot3(g.z[1], g.z[2]);
+  rc.k = r_div(g.m[2], g.S33);
+  rc.kappa[0] = -r_div(S13, g.S33);
+  rc.kappa[1] = -r_div(S23, g.S33);
+  rc.xs1 = r_fma(g.m[2], rc.kappa[0], g.m[0]);
+  rc.xs2 = r_fma(g.m[2], rc.kappa[1], g.m[1]);
+  rc.q0 = r_mul(g.m[2], rc.k);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) apply_ft<T, COV>(f, fr.r[j], rc.b[j]);
+  // A = [b1 b2]^T [b1 b2]; R of (c D A D) with c = log2(e)/2 from b1, b2:
+  //   r11 = sqrt(c) pu |b1|, r12 = sqrt(c) pv (b1.b2)/|b1|, r22 = sqrt(c) pv |b1 x b2|/|b1|
+  const T* b1 = rc.b[0];
+  const T* b2 = rc.b[1];
+  T cx[3];
+  cx[0] = r_fma(b1[1], b2[2], -r_mul(b1[2], b2[1]));
+  cx[1] = r_fma(b1[2], b2[0], -r_mul(b1[0], b2[2]));
+  cx[2] = r_fma(b1[0], b2[1], -r_mul(b1[1], b2[0]));
+  rc.nb1 = r_sqrt(r_dot3(b1, b1));
+  rc.cr = r_sqrt(r_dot3(cx, cx));
+  const T sc = (T)0.84932180028801904272;  // sqrt(log2(e) / 2)
+  const T pu = (T)pl.pu, pv = (T)pl.pv;
+  rc.r11 = sc * pu * rc.nb1;
+  rc.r12 = sc * pv * r_div(r_dot3(b1, b2), rc.nb1);
+  rc.r22 = sc * pv * r_div(rc.cr, rc.nb1);
+}
+
+constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2
+constexpr float kLn2 = 0.69314718055994530942f;
+constexpr float kLog2e = 1.44269504088896340736f;
+
+// log2(sigmoid(x)) = -log2(1 + e^-x), computed without overflow.
+__device__ __forceinline__ float log2_sigmoid(float x) {
+  return x >= 0.f ? -log1pf(expf(-x)) * kLog2e : (x - log1pf(expf(x))) * kLog2e;
+}
+
+__device__ __forceinline__ float sigmoidf(float x) {
+  return x >= 0.f ? 1.f / (1.f + expf(-x)) : expf(x) / (1.f + expf(x));
+}
+
+}  // namespace ug

@@ -1,0 +1,189 @@
+// Internal definitions shared by the CUDA translation units of libug:
+// workspace layout, the device-side plane table, status handling and small
+// warp/block primitives.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ug.h"
+
+namespace ug {
+
+constexpr int kChunk = 32;        // Gaussians per warp chunk in the preprocess passes
+constexpr int kScanItems = 2048;  // entries per block of the count scan
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;    // keys per thread per sort block
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kMseBlocks = 1024;  // partial sums of the MSE loss
+
+// Workspace sections (indices into ug_plan::off).
+enum WsSection {
+  kOffHeader = 0,
+  kOffPlanes,
+  kOffTileOff,
+  kOffMask,
+  kOffInstCnt,
+  kOffRecBase,
+  kOffInstBase,
+  kOffScanPart,
+  kOffRecA,
+  kOffRecB,
+  kOffRecBox,
+  kOffKeys0,
+  kOffKeys1,
+  kOffVals0,
+  kOffVals1,
+  kOffSortHist,
+  kOffSortPart,
+  kOffRanges,
+  kOffRecGrad,
+  kOffEnd
+};
+
+// Header at the start of the workspace (256 bytes).
+struct WsHeader {
+  ug_ws_status st;            // 64 B, copied out by ug_read_status
+  uint32_t tile_counter[2];   // persistent-kernel work queues (forward, backward)
+  uint32_t pad0[2];
+  unsigned long long fp64_count;
+  unsigned long long box_pixels;
+  uint32_t pad1[40];
+};
+static_assert(sizeof(WsHeader) == 256, "header size");
+
+// Derived per-plane data (128 bytes), written by the plane set-up kernel.
+struct PlaneDev {
+  float o[3], u[3], v[3], n[3];
+  float pu, pv, inv_pu, inv_pv;
+  float half_w, half_h;       // width/2, height/2
+  float jshift, ishift;       // width/2 - 1/2, height/2 - 1/2
+  int32_t w, h, tiles_x, tiles_y;
+  int32_t tile_off, pad;
+  int64_t px_off;
+  int32_t pad2[4];
+};
+static_assert(sizeof(PlaneDev) == 128, "plane size");
+
+// Render-side record of one visible (plane, Gaussian) pair.
+//  a = (xs_j, xs_i, r11, r12): peak position x* in pixel units (pixel j has
+//      its centre at j + 1/2) and the upper Cholesky factor R of
+//      (log2 e / 2) D A D, D = diag(pitch_u, pitch_v), A the in-plane precision;
+//  b = (r22, lw2, c, e_thr): lw2 = log2(alpha) - (log2 e / 2) q0, intensity,
+//      ellipsoid threshold (log2 e / 2)(chi2 - q0);
+//  box = (j0 | j1 << 16, i0 | i1 << 16).
+// Weight at pixel (i, j): w = exp2(lw2 - t1^2 - t2^2), t1 = r11 dx + r12 dy,
+// t2 = r22 dy, dx = j + 1/2 - xs_j, dy = i + 1/2 - xs_i.
+
+struct WsView {
+  WsHeader* hdr;
+  PlaneDev* planes;
+  int32_t* tile_off;
+  uint32_t* mask;
+  uint32_t* inst_cnt;
+  uint32_t* rec_base;
+  uint32_t* inst_base;
+  unsigned long long* scan_part;
+  float4* rec_a;
+  float4* rec_b;
+  uint2* rec_box;
+  uint32_t* keys[2];
+  uint32_t* vals[2];
+  uint32_t* sort_hist;
+  unsigned long long* sort_part;
+  uint2* ranges;
+  float* rec_grad;  // 8 floats per record
+};
+
+inline WsView make_view(const ug_plan* plan, void* ws) {
+  char* b = static_cast<char*>(ws);
+  WsView v;
+  v.hdr = reinterpret_cast<WsHeader*>(b + plan->off[kOffHeader]);
+  v.planes = reinterpret_cast<PlaneDev*>(b + plan->off[kOffPlanes]);
+  v.tile_off = reinterpret_cast<int32_t*>(b + plan->off[kOffTileOff]);
+  v.mask = reinterpret_cast<uint32_t*>(b + plan->off[kOffMask]);
+  v.inst_cnt = reinterpret_cast<uint32_t*>(b + plan->off[kOffInstCnt]);
+  v.rec_base = reinterpret_cast<uint32_t*>(b + plan->off[kOffRecBase]);
+  v.inst_base = reinterpret_cast<uint32_t*>(b + plan->off[kOffInstBase]);
+  v.scan_part = reinterpret_cast<unsigned long long*>(b + plan->off[kOffScanPart]);
+  v.rec_a = reinterpret_cast<float4*>(b + plan->off[kOffRecA]);
+  v.rec_b = reinterpret_cast<float4*>(b + plan->off[kOffRecB]);
+  v.rec_box = reinterpret_cast<uint2*>(b + plan->off[kOffRecBox]);
+  v.keys[0] = reinterpret_cast<uint32_t*>(b + plan->off[kOffKeys0]);
+  v.keys[1] = reinterpret_cast<uint32_t*>(b + plan->off[kOffKeys1]);
+  v.vals[0] = reinterpret_cast<uint32_t*>(b + plan->off[kOffVals0]);
+  v.vals[1] = reinterpret_cast<uint32_t*>(b + plan->off[kOffVals1]);
+  v.sort_hist = reinterpret_cast<uint32_t*>(b + plan->off[kOffSortHist]);
+  v.sort_part = reinterpret_cast<unsigned long long*>(b + plan->off[kOffSortPart]);
+  v.ranges = reinterpret_cast<uint2*>(b + plan->off[kOffRanges]);
+  v.rec_grad = reinterpret_cast<float*>(b + plan->off[kOffRecGrad]);
+  return v;
+}
+
+// Number of blocks of the count scan and of a sort pass.
+inline int64_t scan_blocks(int64_t entries) { return (entries + kScanItems - 1) / kScanItems; }
+inline int64_t sort_blocks(int64_t capacity) { return (capacity + kSortTile - 1) / kSortTile; }
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ void dev_fail(WsHeader* h, int code, int detail) {
+  if (atomicCAS(&h->st.status, 0, code) == 0) h->st.detail = detail;
+}
+
+__device__ __forceinline__ bool dev_failed(const WsHeader* h) {
+  return *(volatile const int32_t*)&h->st.status != 0;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Inclusive warp prefix sum.
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// exp2 on the special-function unit (PTX ex2.approx.ftz.f32: relative error
+// about 2^-22 over the range used here; exp2 of very negative numbers flushes
+// to +0).
+__device__ __forceinline__ float fast_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ------------------------------------------------------------------ launchers
+// Each translation unit exposes host launchers; all return cudaGetLastError().
+cudaError_t launch_setup_planes(const ug_plan* plan, const ug_plane* d_planes, WsView v,
+                                cudaStream_t s);
+cudaError_t launch_preprocess(const ug_plan* plan, const ug_gaussians* g, WsView v,
+                              cudaStream_t s);
+cudaError_t launch_bin_sort(const ug_plan* plan, WsView v, cudaStream_t s);
+cudaError_t launch_render(const ug_plan* plan, WsView v, float* image, float* alpha,
+                          cudaStream_t s);
+cudaError_t launch_render_backward(const ug_plan* plan, const ug_gaussians* g, WsView v,
+                                   const float* image, const float* alpha,
+                                   const float* grad_image, const ug_gaussian_grads* grads,
+                                   cudaStream_t s);
+cudaError_t launch_mse(const float* image, const float* target, int64_t n, float* grad,
+                       float* loss, cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int32_t rows, int64_t n,
+                        const ug_adam_row* d_rows, int32_t* d_step, float b1, float b2,
+                        float eps, cudaStream_t s);
+int num_render_variants(int tile);
+
+}  // namespace ug

@@ -1,0 +1,385 @@
+// Rows a5 and a7: the forward tile rasterizer and its gradient.
+//
+// One CTA owns one TILE x TILE pixel tile at a time and takes tiles from a
+// device work counter (persistent launch over all tiles of all planes, so
+// planes of different sizes share one launch). The tile's records are
+// staged in shared memory in batches of one record per thread. Each warp
+// owns a WW x WH sub-rectangle of the tile (PPT vertically adjacent pixels
+// per lane) and skips, as a whole warp, every record whose pixel box misses
+// that sub-rectangle. Per pixel and record:
+//   dx = j + 1/2 - xs_j, dy = i + 1/2 - xs_i, t1 = r11 dx + r12 dy, t2 = r22 dy,
+//   w = 2^(lw2 - t1^2 - t2^2)      (= alpha exp(-q/2), Eq. mahalanobis-3d)
+// accumulated as S_a += w, S_c += w c in tile-list order (ascending Gaussian
+// id), then C = (S_c + a_bg c_bg)/(S_a + a_bg) (Eq. alpha-combine,
+// Eq. colour-combine). There are no atomics in the forward pass.
+#include "ug_internal.cuh"
+
+namespace ug {
+
+__device__ __forceinline__ int find_plane(const int32_t* tile_off, int P, int t) {
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_off[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct TileCtx {
+  int tile, plane, tx, ty, w, h;
+  int64_t px_off;
+};
+
+template <int NT>
+__device__ __forceinline__ bool next_tile(WsView& v, int which, int P, int total_tiles,
+                                          TileCtx& tc) {
+  __shared__ int s_tile, s_plane;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int t = (int)atomicAdd(&v.hdr->tile_counter[which], 1u);
+    s_tile = t;
+    s_plane = t < total_tiles ? find_plane(v.tile_off, P, t) : 0;
+  }
+  __syncthreads();
+  const int t = s_tile;
+  if (t >= total_tiles) return false;
+  const PlaneDev& pl = v.planes[s_plane];
+  const int local = t - pl.tile_off;
+  tc.plane = s_plane;
+  tc.tx = local % pl.tiles_x;
+  tc.ty = local / pl.tiles_x;
+  tc.w = pl.w;
+  tc.h = pl.h;
+  tc.px_off = pl.px_off;
+  tc.tile = t;
+  return true;
+}
+
+template <int TILE, int WW, int PPT>
+struct Layout {
+  static constexpr int NT = TILE * TILE / PPT;
+  static constexpr int NW = NT / 32;
+  static constexpr int LH = 32 / WW;       // lane rows per warp
+  static constexpr int WH = LH * PPT;      // warp footprint height
+  static constexpr int WPR = TILE / WW;    // warps per tile row
+  static_assert(NT % 32 == 0, "whole warps");
+  static_assert(WPR * (TILE / WH) == NW, "warps tile the tile");
+};
+
+template <int TILE, int WW, int PPT, int CUT>
+__global__ void __launch_bounds__(Layout<TILE, WW, PPT>::NT)
+    k_render_fwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles, float abg,
+                 float cbg, float* __restrict__ image, float* __restrict__ alpha) {
+  using Lay = Layout<TILE, WW, PPT>;
+  constexpr int NT = Lay::NT;
+  __shared__ float4 sA[NT];
+  __shared__ float4 sB[NT];
+  __shared__ uint2 sBox[NT];
+  if (dev_failed(v.hdr)) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wx = warp % Lay::WPR, wy = warp / Lay::WPR;
+  const int lx = lane % WW, ly = lane / WW;
+  TileCtx tc;
+  while (next_tile<NT>(v, 0, P, total_tiles, tc)) {
+    const int t = tc.tile;
+    const int fj0 = tc.tx * TILE + wx * WW, fi0 = tc.ty * TILE + wy * Lay::WH;
+    const int fj1 = fj0 + WW - 1, fi1 = fi0 + Lay::WH - 1;
+    const int j = fj0 + lx;
+    const int ib = fi0 + ly * PPT;
+    const float pxj = (float)j + 0.5f, pyi = (float)ib + 0.5f;
+    const uint2 rg = v.ranges[t];
+    float sa[PPT], sc[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) sa[k] = sc[k] = 0.f;
+    for (uint32_t b = rg.x; b < rg.y; b += NT) {
+      const int cnt = (int)min((uint32_t)NT, rg.y - b);
+      __syncthreads();
+      if (tid < cnt) {
+        const uint32_t rid = __ldg(vals + b + tid);
+        sA[tid] = __ldg(v.rec_a + rid);
+        sB[tid] = __ldg(v.rec_b + rid);
+        sBox[tid] = __ldg(v.rec_box + rid);
+      }
+      __syncthreads();
+      for (int r = 0; r < cnt; ++r) {
+        const uint2 bx = sBox[r];
+        const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
+        if (j1 < fj0 || j0 > fj1 || i1 < fi0 || i0 > fi1) continue;  // warp-uniform cull
+        const float4 a = sA[r];
+        const float4 c = sB[r];
+        const float dx = pxj - a.x, dy = pyi - a.y;
+        const float t1 = fmaf(a.z, dx, a.w * dy);
+        const float t2 = c.x * dy;
+        const bool jin = (unsigned)(j - j0) <= (unsigned)(j1 - j0);
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          const float t1k = fmaf((float)k, a.w, t1);
+          const float t2k = fmaf((float)k, c.x, t2);
+          const float qq = fmaf(t1k, t1k, t2k * t2k);
+          float w = fast_exp2(c.y - qq);
+          bool in = jin && (unsigned)(ib + k - i0) <= (unsigned)(i1 - i0);
+          if (CUT) in = in && qq <= c.w;
+          w = in ? w : 0.f;
+          sa[k] += w;
+          sc[k] = fmaf(w, c.z, sc[k]);
+        }
+      }
+    }
+    if (j < tc.w) {
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const int i = ib + k;
+        if (i < tc.h) {
+          const int64_t px = tc.px_off + (int64_t)i * tc.w + j;
+          const float al = sa[k] + abg;
+          image[px] = (sc[k] + abg * cbg) / al;
+          alpha[px] = al;
+        }
+      }
+    }
+  }
+}
+
+// Sum of 8 per-lane values over the warp; lane f (0 <= f < 7) returns the
+// total of value f. Recursive halving: each exchange sends half of the
+// remaining values, so the warp issues 4 + 2 + 1 + 1 + 1 shuffles.
+__device__ __forceinline__ float warp_reduce8(float v[8], int lane) {
+  // level 1 (xor 16): keep 4 values
+  float r4[4];
+  const bool up16 = lane & 16;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float send = up16 ? v[k] : v[k + 4];
+    const float keep = up16 ? v[k + 4] : v[k];
+    r4[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  // lanes < 16 hold values 0..3, lanes >= 16 hold 4..7
+  float r2[2];
+  const bool up8 = lane & 8;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = up8 ? r4[k] : r4[k + 2];
+    const float keep = up8 ? r4[k + 2] : r4[k];
+    r2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const bool up4 = lane & 4;
+  const float send = up4 ? r2[0] : r2[1];
+  const float keep = up4 ? r2[1] : r2[0];
+  float r1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  r1 += __shfl_xor_sync(0xffffffffu, r1, 2);
+  r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
+  // value index held: 4*(lane>>4 & 1) + 2*(lane>>3 & 1) + (lane>>2 & 1)
+  return r1;
+}
+
+template <int TILE, int WW, int PPT, int CUT>
+__global__ void __launch_bounds__(Layout<TILE, WW, PPT>::NT)
+    k_render_bwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles,
+                 const float* __restrict__ image, const float* __restrict__ alpha,
+                 const float* __restrict__ grad_image) {
+  using Lay = Layout<TILE, WW, PPT>;
+  constexpr int NT = Lay::NT;
+  __shared__ float4 sA[NT];
+  __shared__ float4 sB[NT];
+  __shared__ uint2 sBox[NT];
+  __shared__ uint32_t sRid[NT];
+  if (dev_failed(v.hdr)) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wx = warp % Lay::WPR, wy = warp / Lay::WPR;
+  const int lx = lane % WW, ly = lane / WW;
+  // lane -> reduced value index (see warp_reduce8); lanes with (lane & 3) == 0 write
+  const int fidx = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
+  TileCtx tc;
+  while (next_tile<NT>(v, 1, P, total_tiles, tc)) {
+    const int t = tc.tile;
+    const int fj0 = tc.tx * TILE + wx * WW, fi0 = tc.ty * TILE + wy * Lay::WH;
+    const int fj1 = fj0 + WW - 1, fi1 = fi0 + Lay::WH - 1;
+    const int j = fj0 + lx;
+    const int ib = fi0 + ly * PPT;
+    const float pxj = (float)j + 0.5f, pyi = (float)ib + 0.5f;
+    float rr[PPT], rc[PPT];  // r = G / alpha, r C
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int i = ib + k;
+      rr[k] = 0.f;
+      rc[k] = 0.f;
+      if (j < tc.w && i < tc.h) {
+        const int64_t px = tc.px_off + (int64_t)i * tc.w + j;
+        const float r = __ldg(grad_image + px) / __ldg(alpha + px);
+        rr[k] = r;
+        rc[k] = r * __ldg(image + px);
+      }
+    }
+    const uint2 rg = v.ranges[t];
+    for (uint32_t b = rg.x; b < rg.y; b += NT) {
+      const int cnt = (int)min((uint32_t)NT, rg.y - b);
+      __syncthreads();
+      if (tid < cnt) {
+        const uint32_t rid = __ldg(vals + b + tid);
+        sRid[tid] = rid;
+        sA[tid] = __ldg(v.rec_a + rid);
+        sB[tid] = __ldg(v.rec_b + rid);
+        sBox[tid] = __ldg(v.rec_box + rid);
+      }
+      __syncthreads();
+      for (int r = 0; r < cnt; ++r) {
+        const uint2 bx = sBox[r];
+        const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
+        if (j1 < fj0 || j0 > fj1 || i1 < fi0 || i0 > fi1) continue;
+        const float4 a = sA[r];
+        const float4 c = sB[r];
+        const float dx = pxj - a.x, dy = pyi - a.y;
+        const float t1 = fmaf(a.z, dx, a.w * dy);
+        const float t2 = c.x * dy;
+        const bool jin = (unsigned)(j - j0) <= (unsigned)(j1 - j0);
+        float acc[8];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) acc[f] = 0.f;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          const float t1k = fmaf((float)k, a.w, t1);
+          const float t2k = fmaf((float)k, c.x, t2);
+          const float dyk = dy + (float)k;
+          const float qq = fmaf(t1k, t1k, t2k * t2k);
+          float w = fast_exp2(c.y - qq);
+          bool in = jin && (unsigned)(ib + k - i0) <= (unsigned)(i1 - i0);
+          if (CUT) in = in && qq <= c.w;
+          w = in ? w : 0.f;
+          const float gww = fmaf(rr[k], c.z, -rc[k]) * w;  // dL/dw * w
+          acc[0] = fmaf(rr[k], w, acc[0]);
+          acc[1] += gww;
+          const float u1 = gww * t1k, u2 = gww * t2k;
+          acc[2] += u1;
+          acc[3] += u2;
+          acc[4] = fmaf(u1, dx, acc[4]);
+          acc[5] = fmaf(u1, dyk, acc[5]);
+          acc[6] = fmaf(u2, dyk, acc[6]);
+        }
+        const float tot = warp_reduce8(acc, lane);
+        if ((lane & 3) == 0 && fidx < 7) atomicAdd(v.rec_grad + (size_t)sRid[r] * 8 + fidx, tot);
+      }
+    }
+  }
+}
+
+__global__ void k_zero_rec_grad(WsView v, int64_t cap) {
+  if (dev_failed(v.hdr)) return;
+  const int64_t nrec = min((int64_t)v.hdr->st.records, cap);
+  float4* g = reinterpret_cast<float4*>(v.rec_grad);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrec * 2;
+       i += (int64_t)gridDim.x * blockDim.x)
+    g[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// ------------------------------------------------------------------ variants
+template <int TILE, int WW, int PPT>
+struct Variant {
+  static constexpr int NT = Layout<TILE, WW, PPT>::NT;
+  template <int CUT>
+  static cudaError_t fwd(const ug_plan* plan, WsView v, const uint32_t* vals, float* image,
+                         float* alpha, cudaStream_t s) {
+    static int grid = 0;
+    if (grid == 0) {
+      int dev = 0, sms = 0, occ = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_render_fwd<TILE, WW, PPT, CUT>, NT, 0);
+      grid = sms * (occ > 0 ? occ : 1);
+    }
+    const int g = min(grid, max(plan->total_tiles, 1));
+    k_render_fwd<TILE, WW, PPT, CUT><<<g, NT, 0, s>>>(v, vals, plan->num_planes, plan->total_tiles,
+                                                      plan->cfg.alpha_bg, plan->cfg.c_bg, image,
+                                                      alpha);
+    return cudaGetLastError();
+  }
+  template <int CUT>
+  static cudaError_t bwd(const ug_plan* plan, WsView v, const uint32_t* vals, const float* image,
+                         const float* alpha, const float* grad, cudaStream_t s) {
+    static int grid = 0;
+    if (grid == 0) {
+      int dev = 0, sms = 0, occ = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_render_bwd<TILE, WW, PPT, CUT>, NT, 0);
+      grid = sms * (occ > 0 ? occ : 1);
+    }
+    const int g = min(grid, max(plan->total_tiles, 1));
+    k_render_bwd<TILE, WW, PPT, CUT><<<g, NT, 0, s>>>(v, vals, plan->num_planes,
+                                                      plan->total_tiles, image, alpha, grad);
+    return cudaGetLastError();
+  }
+};
+
+// Variant tables: tile 16 and tile 8.
+template <int CUT>
+static cudaError_t dispatch_fwd(const ug_plan* plan, WsView v, const uint32_t* vals, float* image,
+                                float* alpha, cudaStream_t s) {
+  const int var = plan->cfg.variant;
+  if (plan->cfg.tile == 16) {
+    switch (var) {
+      case 0: return Variant<16, 8, 2>::fwd<CUT>(plan, v, vals, image, alpha, s);
+      case 1: return Variant<16, 16, 2>::fwd<CUT>(plan, v, vals, image, alpha, s);
+      case 2: return Variant<16, 8, 4>::fwd<CUT>(plan, v, vals, image, alpha, s);
+      default: return Variant<16, 16, 1>::fwd<CUT>(plan, v, vals, image, alpha, s);
+    }
+  }
+  switch (var) {
+    case 0: return Variant<8, 8, 2>::fwd<CUT>(plan, v, vals, image, alpha, s);
+    default: return Variant<8, 8, 1>::fwd<CUT>(plan, v, vals, image, alpha, s);
+  }
+}
+
+template <int CUT>
+static cudaError_t dispatch_bwd(const ug_plan* plan, WsView v, const uint32_t* vals,
+                                const float* image, const float* alpha, const float* grad,
+                                cudaStream_t s) {
+  const int var = plan->cfg.variant;
+  if (plan->cfg.tile == 16) {
+    switch (var) {
+      case 0: return Variant<16, 8, 2>::bwd<CUT>(plan, v, vals, image, alpha, grad, s);
+      case 1: return Variant<16, 16, 2>::bwd<CUT>(plan, v, vals, image, alpha, grad, s);
+      case 2: return Variant<16, 8, 4>::bwd<CUT>(plan, v, vals, image, alpha, grad, s);
+      default: return Variant<16, 16, 1>::bwd<CUT>(plan, v, vals, image, alpha, grad, s);
+    }
+  }
+  switch (var) {
+    case 0: return Variant<8, 8, 2>::bwd<CUT>(plan, v, vals, image, alpha, grad, s);
+    default: return Variant<8, 8, 1>::bwd<CUT>(plan, v, vals, image, alpha, grad, s);
+  }
+}
+
+int num_render_variants(int tile) { return tile == 16 ? 4 : (tile == 8 ? 2 : 0); }
+
+cudaError_t launch_render(const ug_plan* plan, WsView v, float* image, float* alpha,
+                          cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&v.hdr->tile_counter[0], 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  const uint32_t* vals = v.vals[plan->sort_passes & 1];
+  return plan->cfg.cutoff ? dispatch_fwd<1>(plan, v, vals, image, alpha, s)
+                          : dispatch_fwd<0>(plan, v, vals, image, alpha, s);
+}
+
+cudaError_t launch_pre_backward(const ug_plan* plan, const ug_gaussians* g, WsView v,
+                                const ug_gaussian_grads* grads, cudaStream_t s);
+
+cudaError_t launch_render_backward(const ug_plan* plan, const ug_gaussians* g, WsView v,
+                                   const float* image, const float* alpha,
+                                   const float* grad_image, const ug_gaussian_grads* grads,
+                                   cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&v.hdr->tile_counter[1], 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_zero_rec_grad<<<sms * 4, 256, 0, s>>>(v, plan->record_capacity);
+  }
+  const uint32_t* vals = v.vals[plan->sort_passes & 1];
+  e = plan->cfg.cutoff ? dispatch_bwd<1>(plan, v, vals, image, alpha, grad_image, s)
+                       : dispatch_bwd<0>(plan, v, vals, image, alpha, grad_image, s);
+  if (e != cudaSuccess) return e;
+  return launch_pre_backward(plan, g, v, grads, s);
+}
+
+}  // namespace ug

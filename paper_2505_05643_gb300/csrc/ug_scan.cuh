@@ -1,0 +1,167 @@
+// Exclusive prefix sums over large arrays: reduce -> scan of block partials
+// -> down-sweep. Three launches, no inter-block waiting, deterministic.
+#pragma once
+
+#include "ug_internal.cuh"
+
+namespace ug {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = kScanItems / kScanThreads;  // 8
+static_assert(kScanPerThread * kScanThreads == kScanItems, "scan tiling");
+
+// Block-wide exclusive scan of one value per thread (256 threads); returns the
+// exclusive prefix and writes the block total to *total.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T x, T* total) {
+  __shared__ T warp_tot[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  T base = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kScanThreads / 32; ++w) {
+    if (w < warp) base += warp_tot[w];
+    tot += warp_tot[w];
+  }
+  __syncthreads();
+  *total = tot;
+  return base + incl - x;
+}
+
+// Partial sums of NV values per block of kScanItems entries.
+template <int NV, class Load>
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_partial(Load ld, int64_t entries, unsigned long long* part, const WsHeader* hdr) {
+  if (hdr && dev_failed(hdr)) return;
+  const int64_t base = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kScanPerThread;
+  unsigned long long s[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) s[k] = 0;
+#pragma unroll
+  for (int it = 0; it < kScanPerThread; ++it) {
+    const int64_t e = base + it;
+    if (e < entries) {
+      uint32_t val[NV];
+      ld(e, val);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] += val[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    unsigned long long tot;
+    block_excl_scan<unsigned long long>(s[k], &tot);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * NV + k] = tot;
+  }
+}
+
+// Exclusive scan of the block partials in place (one block of 1024 threads).
+// mode 1 (count scan): writes the totals to the header and flags capacity
+// overflow.
+template <int NV>
+__global__ void __launch_bounds__(1024)
+    k_scan_top(unsigned long long* part, int64_t nblk, WsHeader* hdr, int mode, int64_t cap0,
+               int64_t cap1) {
+  if (hdr && dev_failed(hdr)) return;
+  __shared__ unsigned long long sh[32][NV];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t per = (nblk + 1023) / 1024;
+  const int64_t b0 = (int64_t)tid * per;
+  unsigned long long loc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) loc[k] = 0;
+  for (int64_t b = b0; b < b0 + per && b < nblk; ++b)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) loc[k] += part[b * NV + k];
+  unsigned long long excl[NV], tot[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    unsigned long long incl = loc[k];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) sh[warp][k] = incl;
+    excl[k] = incl - loc[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    unsigned long long base = 0, t = 0;
+    for (int w = 0; w < 32; ++w) {
+      if (w < warp) base += sh[w][k];
+      t += sh[w][k];
+    }
+    excl[k] += base;
+    tot[k] = t;
+  }
+  __syncthreads();
+  unsigned long long run[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) run[k] = excl[k];
+  for (int64_t b = b0; b < b0 + per && b < nblk; ++b)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      unsigned long long v = part[b * NV + k];
+      part[b * NV + k] = run[k];
+      run[k] += v;
+    }
+  if (mode == 1 && tid == 0) {
+    hdr->st.records = (int64_t)tot[0];
+    hdr->st.instances = NV > 1 ? (int64_t)tot[NV - 1] : 0;
+    if ((int64_t)tot[0] > cap0 || (NV > 1 && (int64_t)tot[NV - 1] > cap1))
+      dev_fail(hdr, UG_ERR_CAPACITY, 0);
+  }
+}
+
+// Down-sweep: exclusive prefix of every entry, passed to st(e, excl[NV]).
+template <int NV, class Load, class Store>
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_down(Load ld, Store st, int64_t entries, const unsigned long long* part,
+                const WsHeader* hdr) {
+  if (hdr && dev_failed(hdr)) return;
+  const int64_t base = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kScanPerThread;
+  uint32_t val[kScanPerThread][NV];
+  unsigned long long s[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) s[k] = 0;
+#pragma unroll
+  for (int it = 0; it < kScanPerThread; ++it) {
+    const int64_t e = base + it;
+    if (e < entries) {
+      ld(e, val[it]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) val[it][k] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s[k] += val[it][k];
+  }
+  unsigned long long run[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    unsigned long long tot;
+    run[k] = block_excl_scan<unsigned long long>(s[k], &tot) + part[(int64_t)blockIdx.x * NV + k];
+  }
+#pragma unroll
+  for (int it = 0; it < kScanPerThread; ++it) {
+    const int64_t e = base + it;
+    uint32_t ex[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      ex[k] = (uint32_t)run[k];
+      run[k] += val[it][k];
+    }
+    if (e < entries) st(e, ex);
+  }
+}
+
+}  // namespace ug

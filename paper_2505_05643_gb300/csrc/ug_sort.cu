@@ -1,0 +1,125 @@
+// Row a4: stable LSD radix sort of the (tile key, record id) instances and
+// the [start, end) range of every tile.
+//
+// Each 8-bit pass: (1) every block of kSortTile keys counts its digits in
+// shared memory and writes them digit-major, (2) one exclusive scan over
+// (digit, block) gives every block the output base of each digit, (3) every
+// block ranks its keys stably - rounds in order, warps in order, lanes in
+// order, equal digits found with __match_any_sync - and scatters keys and
+// values. Instances arrive in (Gaussian chunk, plane, Gaussian) order, so the
+// stable sort leaves each tile's records in ascending Gaussian order.
+#include "ug_scan.cuh"
+
+namespace ug {
+
+__global__ void __launch_bounds__(kSortThreads)
+    k_sort_hist(const uint32_t* __restrict__ keys, int shift, int64_t nblk, WsView v) {
+  __shared__ uint32_t hist[256];
+  if (dev_failed(v.hdr)) return;
+  const int64_t n = v.hdr->st.instances;
+  hist[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int k = 0; k < kSortItems; ++k) {
+    const int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&hist[(__ldg(keys + i) >> shift) & 0xffu], 1u);
+  }
+  __syncthreads();
+  v.sort_hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = hist[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+    k_sort_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                   uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int shift,
+                   int64_t nblk, WsView v) {
+  constexpr int NW = kSortThreads / 32;
+  __shared__ uint32_t cnt[NW][256];
+  __shared__ uint32_t gb[256];  // running output position of each digit
+  if (dev_failed(v.hdr)) return;
+  const int64_t n = v.hdr->st.instances;
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (base >= n) return;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  gb[tid] = v.sort_hist[(int64_t)tid * nblk + blockIdx.x];
+  for (int round = 0; round < kSortItems; ++round) {
+    const int64_t i = base + (int64_t)round * kSortThreads + tid;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) cnt[w][tid] = 0;
+    __syncthreads();
+    const bool valid = i < n;
+    uint32_t key = 0, val = 0, d = 256;
+    if (valid) {
+      key = __ldg(keys_in + i);
+      val = __ldg(vals_in + i);
+      d = (key >> shift) & 0xffu;
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & lanemask_lt());
+    if (valid && rank == 0) cnt[warp][d] = __popc(peers);
+    __syncthreads();
+    {  // thread tid owns digit tid: exclusive prefix over the warps, then advance
+      uint32_t acc = gb[tid];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t c = cnt[w][tid];
+        cnt[w][tid] = acc;
+        acc += c;
+      }
+      gb[tid] = acc;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = cnt[warp][d] + rank;
+      keys_out[pos] = key;
+      vals_out[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_tile_ranges(const uint32_t* __restrict__ keys, WsView v) {
+  if (dev_failed(v.hdr)) return;
+  const int64_t n = v.hdr->st.instances;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = keys[i];
+    if (i == 0 || keys[i - 1] != k) v.ranges[k].x = (uint32_t)i;
+    if (i == n - 1 || keys[i + 1] != k) v.ranges[k].y = (uint32_t)(i + 1);
+  }
+}
+
+struct HistLoad {
+  const uint32_t* h;
+  __device__ void operator()(int64_t e, uint32_t out[1]) const { out[0] = h[e]; }
+};
+struct HistStore {
+  uint32_t* h;
+  __device__ void operator()(int64_t e, const uint32_t ex[1]) const { h[e] = ex[0]; }
+};
+
+cudaError_t launch_bin_sort(const ug_plan* plan, WsView v, cudaStream_t s) {
+  const int64_t nblk = sort_blocks(plan->instance_capacity);
+  const int64_t entries = 256 * nblk;
+  const int64_t sblk = scan_blocks(entries);
+  HistLoad ld{v.sort_hist};
+  HistStore st{v.sort_hist};
+  for (int pass = 0; pass < plan->sort_passes; ++pass) {
+    const int shift = 8 * pass;
+    const int src = pass & 1, dst = src ^ 1;
+    k_sort_hist<<<(unsigned)nblk, kSortThreads, 0, s>>>(v.keys[src], shift, nblk, v);
+    k_scan_partial<1, HistLoad><<<(unsigned)sblk, kScanThreads, 0, s>>>(ld, entries, v.sort_part, v.hdr);
+    k_scan_top<1><<<1, 1024, 0, s>>>(v.sort_part, sblk, v.hdr, 0, 0, 0);
+    k_scan_down<1, HistLoad, HistStore><<<(unsigned)sblk, kScanThreads, 0, s>>>(ld, st, entries, v.sort_part, v.hdr);
+    k_sort_scatter<<<(unsigned)nblk, kSortThreads, 0, s>>>(v.keys[src], v.vals[src], v.keys[dst],
+                                                           v.vals[dst], shift, nblk, v);
+  }
+  cudaError_t e = cudaMemsetAsync(v.ranges, 0, sizeof(uint2) * (size_t)plan->total_tiles, s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_tile_ranges<<<sms * 8, 256, 0, s>>>(v.keys[plan->sort_passes & 1], v);
+  return cudaGetLastError();
+}
+
+}  // namespace ug

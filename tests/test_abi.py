@@ -1,0 +1,104 @@
+"""The C-ABI library builds, loads and exports every symbol include/ug.h
+declares; host-side argument checks (no GPU work). No GPU needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2505_05643_gb300 import binding as B
+from paper_2505_05643_gb300 import build_lib, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ug.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(ug_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return B.load()
+
+
+def test_header_declares_the_hot_path(lib):
+    names = declared_functions()
+    for f in ("ug_preprocess", "ug_bin_sort", "ug_render", "ug_render_backward", "ug_adam_step"):
+        assert f in names
+    assert set(names) == set(B.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_versions_and_strings(lib):
+    assert B.ug_version() >= 100
+    assert B.status_string(B.UG_ERR_CAPACITY).startswith("record or instance")
+    assert B.ug_num_variants(16) >= 1 and B.ug_num_variants(8) >= 1 and B.ug_num_variants(12) == 0
+
+
+def _planes(sizes=((64, 64), (70, 45))):
+    return synth.planes_to_struct(synth.planes_random(np.random.default_rng(0), list(sizes)))
+
+
+def test_plan_layout(lib):
+    cfg = B.ug_config_default()
+    pl = _planes()
+    plan = B.ug_plan_init(cfg, 1000, pl, 5000, 20000)
+    assert plan.total_tiles == 16 + 5 * 3
+    assert plan.total_pixels == 64 * 64 + 70 * 45
+    assert plan.key_bits == 5 and plan.sort_passes == 1
+    assert plan.chunks == 32
+    offs = list(plan.off)[:19]
+    assert all(o % 256 == 0 for o in offs) and offs == sorted(offs)
+    assert plan.workspace_bytes >= offs[-1]
+    cfg.tile = 8
+    plan8 = B.ug_plan_init(cfg, 1000, pl, 5000, 20000)
+    assert plan8.total_tiles == 64 + 9 * 6
+
+
+def test_plan_rejects_bad_arguments(lib):
+    cfg = B.ug_config_default()
+    pl = _planes()
+    bad = pl.copy()
+    bad["u"][0] = [1.0, 0.1, 0.0]  # not unit
+    with pytest.raises(B.UgError) as e:
+        B.ug_plan_init(cfg, 10, bad, 10, 10)
+    assert e.value.status == B.UG_ERR_INVALID_ARGUMENT
+    overlap = pl.copy()
+    overlap["pixel_offset"][1] = 100  # overlaps plane 0
+    with pytest.raises(B.UgError):
+        B.ug_plan_init(cfg, 10, overlap, 10, 10)
+    with pytest.raises(B.UgError):
+        B.ug_plan_init(cfg, 10, pl, 10, 1 << 31)
+    c2 = B.ug_config_default()
+    c2.tile = 12
+    with pytest.raises(B.UgError) as e:
+        B.ug_plan_init(c2, 10, pl, 10, 10)
+    assert e.value.status == B.UG_ERR_NOT_SUPPORTED
+    c3 = B.ug_config_default()
+    c3.beta = 0.0
+    with pytest.raises(B.UgError):
+        B.ug_plan_init(c3, 10, pl, 10, 10)
+
+
+def test_calls_reject_null_and_small_workspace(lib):
+    cfg = B.ug_config_default()
+    plan = B.ug_plan_init(cfg, 10, _planes(), 10, 10)
+    g = B.ug_gaussians()
+    # NULL workspace -> synchronous error, nothing launched
+    st = lib.ug_preprocess(ctypes.byref(plan), ctypes.byref(g), None, None, 0, None)
+    assert st == B.UG_ERR_INVALID_ARGUMENT
+    st = lib.ug_bin_sort(ctypes.byref(plan), ctypes.c_void_p(256), 16, None)
+    assert st == B.UG_ERR_WORKSPACE_TOO_SMALL
+    st = lib.ug_mse_loss_grad(None, None, 10, None, None, None)
+    assert st == B.UG_ERR_INVALID_ARGUMENT
+    st = lib.ug_adam_step(None, None, None, None, 1, 10, None, None, 0.9, 0.999, 1e-15, None)
+    assert st == B.UG_ERR_INVALID_ARGUMENT

@@ -1,0 +1,173 @@
+"""Backward parity: the CUDA gradient (backward rasterizer + chain rule)
+against the oracle's FP64 analytic gradient and FP64 central differences;
+the autograd.Function; the MSE loss kernel."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2505_05643_gb300 import binding as B
+from paper_2505_05643_gb300 import render as R
+from paper_2505_05643_gb300 import synth
+
+from gpu_helpers import gpu_render, oracle_config
+
+pytestmark = pytest.mark.gpu
+
+# Gradient tolerance: |gpu - ref| <= GRAD_RTOL |ref| + GRAD_FLOOR * S, where S is
+# the oracle's sum of |per-pair term| (the scale of FP32 rounding in a sum that
+# cancels): relative 1e-3 as stated for the gradient, and a floor of 1e-4 of
+# the absolute sum (FP32 sums of 1e3-1e5 terms carry a relative error of the
+# absolute sum of about sqrt(n) * 6e-8 <= 2e-5).
+GRAD_RTOL = 1e-3
+GRAD_FLOOR = 1e-4
+
+
+def _grad_rows(grads_t, cov_param, subset=None):
+    g = grads_t.cpu().numpy().astype(np.float64)  # (rows, n)
+    rows = g.T
+    return rows if subset is None else rows[subset]
+
+
+def _check_grads(gpu, ref, gabs, names, what):
+    tol = GRAD_RTOL * np.abs(ref) + GRAD_FLOOR * gabs + 1e-30
+    err = np.abs(gpu - ref)
+    bad = np.argwhere(err > tol)
+    if len(bad):
+        k, p = bad[0]
+        raise AssertionError(
+            f"{what}: {len(bad)} of {err.size} gradient entries out of tolerance; first: "
+            f"gaussian row {k} param {names[p]}: gpu {gpu[k, p]:.6e} ref {ref[k, p]:.6e} "
+            f"abs-sum {gabs[k, p]:.3e}; worst rel {(err / (np.abs(ref) + 1e-30)).max():.3e}")
+    return float((err / tol).max())
+
+
+def _backward_case(g, pl, cfg, target, subset=None):
+    ocfg = oracle_config(cfg)
+    ref = oracle.render(g, pl, ocfg)
+    _, gimg = oracle.mse_loss_grad(ref["image"], target)
+    r, params, image, alpha = gpu_render(g, pl, cfg)
+    gi = torch.from_numpy(gimg.astype(np.float32)).cuda()
+    im_t = torch.from_numpy(image.astype(np.float32)).cuda()
+    al_t = torch.from_numpy(alpha.astype(np.float32)).cuda()
+    grads = r.backward(params, im_t, al_t, gi)
+    torch.cuda.synchronize()
+    gref, gabs = oracle.render_grad(g, pl, ocfg, ref["image"], ref["alpha"], gimg, subset=subset)
+    gpu = _grad_rows(grads, cfg.cov_param, subset)
+    return gpu, gref, gabs, grads
+
+
+@pytest.mark.parametrize("cov_param", [B.UG_COV_SCALE_ROT, B.UG_COV_TRI])
+@pytest.mark.parametrize("cutoff", [B.UG_CUTOFF_BOX, B.UG_CUTOFF_BOX_AND_ELLIPSOID])
+def test_grad_small_scene(cov_param, cutoff):
+    rng = np.random.default_rng(31)
+    g = synth.gaussians_scale_rot(rng, 1500, 0.03, 0.15)
+    g["logit"] = rng.uniform(-1, 2, 1500).astype(np.float32)
+    if cov_param == B.UG_COV_TRI:
+        g = synth.scale_rot_to_tri(g, 1e-4)
+    pl = synth.planes_random(rng, [(64, 64), (50, 70)])
+    target = rng.uniform(0, 1, pl["total_pixels"])
+    cfg = R.make_config(cov_param=cov_param, cutoff=cutoff)
+    gpu, gref, gabs, _ = _backward_case(g, pl, cfg, target)
+    _check_grads(gpu, gref, gabs, oracle.param_names(cov_param), f"small cov{cov_param} cut{cutoff}")
+
+
+@pytest.mark.parametrize("tile,variant", [(16, 1), (16, 2), (16, 3), (8, 0), (8, 1)])
+def test_grad_variants(tile, variant):
+    rng = np.random.default_rng(32)
+    g = synth.gaussians_scale_rot(rng, 1000, 0.03, 0.15)
+    pl = synth.planes_random(rng, [(40, 33), (64, 64)])
+    target = rng.uniform(0, 1, pl["total_pixels"])
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, tile=tile, variant=variant)
+    gpu, gref, gabs, _ = _backward_case(g, pl, cfg, target)
+    _check_grads(gpu, gref, gabs, oracle.param_names(1), f"variant t{tile} v{variant}")
+
+
+def test_grad_50k_16_planes_subset_and_fd():
+    """50,000 scale/rotation Gaussians, 16 planes of 256x256, MSE against
+    targets rendered by the oracle from a separate seed-1 set of 50,000;
+    gradients of a random subset of 500 Gaussians against the FP64 oracle
+    gradient, and a sample against FP64 central differences with h = 1e-3."""
+    g, pl = synth.workload_grad_50k(seed=0)
+    g_t, _ = synth.workload_grad_50k(seed=1)
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    ocfg = oracle_config(cfg)
+    target = oracle.render(g_t, pl, ocfg)["image"]
+    subset = np.random.default_rng(0).choice(50_000, 500, replace=False)
+    gpu, gref, gabs, _ = _backward_case(g, pl, cfg, target, subset=subset)
+    names = oracle.param_names(1)
+    _check_grads(gpu, gref, gabs, names, "grad_50k")
+    # central differences of the FP64 oracle loss, h = 1e-3, on parameters whose
+    # pixel sets do not change at theta +- h; truncation error is O(h^2 / sigma^2)
+    base = oracle.render(g, pl, ocfg)
+    covp = oracle.covp_rows(g, 1)
+    keys = [("mean", r) for r in range(3)] + [("log_scale", r) for r in range(3)] + \
+        [("quat", r) for r in range(4)] + [("logit", None), ("intensity", None)]
+    h = 1e-3
+    checked = 0
+    for si in range(6):
+        k = int(subset[si])
+        pix0, w0 = oracle.contrib(g["mean"][:, k], covp[k], g["logit"][k], g["intensity"][k], pl, ocfg)
+        if len(pix0) < 20:
+            continue
+        for pi, (key, row) in enumerate(keys):
+            losses = []
+            same = True
+            for sgn in (1, -1):
+                gg = {kk: vv[..., k:k + 1].astype(np.float64).copy() for kk, vv in g.items()}
+                if row is None:
+                    gg[key][0] += sgn * h
+                else:
+                    gg[key][row, 0] += sgn * h
+                pix, w = oracle.contrib(gg["mean"][:, 0], oracle.covp_rows(gg, 1)[0],
+                                        gg["logit"][0], gg["intensity"][0], pl, ocfg)
+                same &= np.array_equal(pix, pix0)
+                sa = base["sa"].copy()
+                sc = base["sc"].copy()
+                np.subtract.at(sa, pix0, w0)
+                np.subtract.at(sc, pix0, w0 * float(g["intensity"][k]))
+                np.add.at(sa, pix, w)
+                np.add.at(sc, pix, w * float(gg["intensity"][0]))
+                C = (sc + ocfg.alpha_bg * ocfg.c_bg) / (sa + ocfg.alpha_bg)
+                losses.append(np.mean((C - target) ** 2))
+            if not same:
+                continue
+            fd = (losses[0] - losses[1]) / (2 * h)
+            assert abs(fd - gpu[si, pi]) <= 5e-2 * abs(fd) + 1e-3 * gabs[si, pi] + 1e-14, \
+                (k, key, row, fd, gpu[si, pi])
+            checked += 1
+    assert checked >= 20
+
+
+def test_autograd_function_matches_direct_call():
+    rng = np.random.default_rng(33)
+    g = synth.gaussians_scale_rot(rng, 800, 0.03, 0.15)
+    pl = synth.planes_random(rng, [(48, 48)] * 2)
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    r = R.Renderer(800, pl, cfg)
+    params = torch.from_numpy(R.pack_params(g, 1)).cuda().requires_grad_(True)
+    target = torch.rand(pl["total_pixels"], device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    image = R.UGRender.apply(params, r)
+    loss = torch.mean((image - target) ** 2)
+    loss.backward()
+    image2, alpha2 = r.forward(params.detach())
+    gi = 2 * (image2 - target) / image2.numel()
+    direct = r.backward(params.detach(), image2, alpha2, gi)
+    torch.testing.assert_close(params.grad, direct, rtol=1e-5, atol=1e-9)
+
+
+def test_mse_loss_kernel():
+    rng = np.random.default_rng(34)
+    for n in (1, 1000, 3 * 65536 + 7):
+        img = rng.uniform(0, 1, n).astype(np.float32)
+        tgt = rng.uniform(0, 1, n).astype(np.float32)
+        it, tt = torch.from_numpy(img).cuda(), torch.from_numpy(tgt).cuda()
+        grad = torch.empty_like(it)
+        loss = torch.empty(B.UG_MSE_LOSS_FLOATS, device="cuda")
+        B.ug_mse_loss_grad(it, tt, n, grad, loss)
+        L, G = oracle.mse_loss_grad(img, tgt)
+        np.testing.assert_allclose(loss[0].item(), L, rtol=1e-6)
+        np.testing.assert_allclose(grad.cpu().numpy(), G, rtol=1e-6, atol=1e-12)
+        loss2 = torch.empty_like(loss)
+        B.ug_mse_loss_grad(it, tt, n, grad, loss2)
+        assert loss2[0].item() == loss[0].item()  # deterministic

@@ -1,0 +1,157 @@
+"""Forward parity: the CUDA rasterizer against the FP64 oracle, element by
+element, on seeded workloads that span several tiles with ragged tails, and
+on the edge cases of the method."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2505_05643_gb300 import binding as B
+from paper_2505_05643_gb300 import render as R
+from paper_2505_05643_gb300 import synth
+
+from gpu_helpers import assert_forward_parity, gpu_render, oracle_config
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("cov_param", [B.UG_COV_SCALE_ROT, B.UG_COV_TRI])
+@pytest.mark.parametrize("cutoff", [B.UG_CUTOFF_BOX, B.UG_CUTOFF_BOX_AND_ELLIPSOID])
+def test_fwd_2k_parity(cov_param, cutoff):
+    """2,000 Gaussians, 4 random planes of 64x64 (seed 0), both front-ends and cut-offs."""
+    g, pl = synth.workload_fwd_2k()
+    if cov_param == B.UG_COV_TRI:
+        g = synth.scale_rot_to_tri(g, 1e-4)
+    cfg = R.make_config(cov_param=cov_param, cutoff=cutoff)
+    r, _, image, alpha = gpu_render(g, pl, cfg)
+    ref = oracle.render(g, pl, oracle_config(cfg))
+    assert ref["pairs"] > 40000
+    assert_forward_parity(image, alpha, ref, "fwd_2k")
+    st = r.status()
+    assert st["status"] == 0 and st["records"] > 500
+
+
+@pytest.mark.parametrize("tile,variant", [(16, v) for v in range(4)] + [(8, v) for v in range(2)])
+def test_ragged_planes_all_variants(tile, variant):
+    """Planes whose sizes are not multiples of the tile (ragged tails), several
+    sizes in one launch, every compiled rasterizer variant."""
+    rng = np.random.default_rng(5)
+    g = synth.gaussians_scale_rot(rng, 3000, 0.02, 0.15)
+    pl = synth.planes_random(rng, [(70, 45), (33, 97), (128, 16), (1, 1), (17, 3)])
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, tile=tile, variant=variant)
+    _, _, image, alpha = gpu_render(g, pl, cfg)
+    ref = oracle.render(g, pl, oracle_config(cfg))
+    assert_forward_parity(image, alpha, ref, f"ragged t{tile} v{variant}")
+
+
+def test_fwd_paper_init_triangular():
+    """The paper's initialisation (Sec. 3.4): l_ij in [4, 5), c = 0.5, alpha = 0.731."""
+    rng = np.random.default_rng(11)
+    g = synth.gaussians_paper_init(rng, 4000)
+    pl = synth.planes_random(rng, [(96, 96), (64, 80)])
+    cfg = R.make_config(cov_param=B.UG_COV_TRI)
+    _, _, image, alpha = gpu_render(g, pl, cfg)
+    ref = oracle.render(g, pl, oracle_config(cfg))
+    assert ref["pairs"] / len(ref["image"]) > 50
+    assert_forward_parity(image, alpha, ref, "paper init")
+
+
+def test_empty_and_degenerate_inputs():
+    """No Gaussian at all, a Gaussian set that misses every plane, a 1x1 plane."""
+    rng = np.random.default_rng(2)
+    pl = synth.planes_random(rng, [(20, 20), (1, 1)])
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, c_bg=0.25)
+    # n = 0: background only
+    g0 = {k: v[..., :0] for k, v in synth.gaussians_scale_rot(rng, 1).items()}
+    r = R.Renderer(0, pl, cfg)
+    image, alpha = r.forward(torch.zeros((12, 0), dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(image.cpu().numpy(), 0.25, rtol=1e-6)
+    np.testing.assert_allclose(alpha.cpu().numpy(), 1e-3, rtol=1e-6)
+    # Gaussians far outside every plane's box
+    g = synth.gaussians_scale_rot(rng, 64)
+    g["mean"][:] = 50.0
+    _, _, image, alpha = gpu_render(g, pl, cfg)
+    np.testing.assert_allclose(image, 0.25, rtol=1e-6)
+    assert oracle.render(g, pl, oracle_config(cfg))["pairs"] == 0
+
+
+def test_single_gaussian_closed_form():
+    """One isotropic Gaussian at plane distance d: C = w c / (w + a_bg),
+    w = alpha exp(-(d^2 + r^2) / 2 sigma^2) inside the box (pin K2 on the GPU)."""
+    sigma, dist = 0.1, 0.05
+    pl = synth.planes_random(np.random.default_rng(4), [(64, 64)], origin_range=0.0)
+    u, v = pl["u"][0].astype(np.float64), pl["v"][0].astype(np.float64)
+    nrm = np.cross(u, v)
+    mu = 0.1 * u - 0.05 * v + dist * nrm
+    g = dict(mean=mu.reshape(3, 1).astype(np.float32),
+             log_scale=np.full((3, 1), np.log(sigma), np.float32),
+             quat=np.array([[1.0], [0.0], [0.0], [0.0]], np.float32),
+             logit=np.array([1.0], np.float32), intensity=np.array([0.7], np.float32))
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    _, _, image, alpha = gpu_render(g, pl, cfg)
+    p = 2.0 / 64
+    x1 = (np.arange(64) + 0.5 - 32) * p
+    X1, X2 = np.meshgrid(x1, x1)
+    r2 = (X1 - 0.1) ** 2 + (X2 + 0.05) ** 2
+    w = (1 / (1 + np.e ** -1)) * np.exp(-(dist ** 2 + r2) / (2 * sigma ** 2))
+    h = np.sqrt(7.815) * sigma
+    inside = ((np.abs(X1 - 0.1) <= h) & (np.abs(X2 + 0.05) <= h)).ravel()
+    expect = np.where(inside, w.ravel() * 0.7 / (w.ravel() + 1e-3), 0.0)
+    np.testing.assert_allclose(image, expect, rtol=2e-4, atol=1e-6)
+
+
+def test_plane_change_between_calls():
+    """Poses updated in device memory (same sizes) are picked up."""
+    rng = np.random.default_rng(8)
+    g = synth.gaussians_scale_rot(rng, 2000)
+    pl_a = synth.planes_random(rng, [(48, 48)] * 3)
+    pl_b = synth.planes_random(rng, [(48, 48)] * 3)
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    r = R.Renderer(2000, pl_a, cfg)
+    params = torch.from_numpy(R.pack_params(g, cfg.cov_param)).cuda()
+    r.forward(params)
+    r.set_planes(pl_b)
+    image, alpha = r.forward(params)
+    ref = oracle.render(g, pl_b, oracle_config(cfg))
+    assert_forward_parity(image.cpu().numpy().astype(np.float64),
+                          alpha.cpu().numpy().astype(np.float64), ref, "replanned")
+
+
+def test_invalid_plane_in_device_memory_sets_status():
+    rng = np.random.default_rng(9)
+    g = synth.gaussians_scale_rot(rng, 100)
+    pl = synth.planes_random(rng, [(16, 16)])
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    r = R.Renderer(100, pl, cfg)
+    bad = synth.planes_to_struct(pl)
+    bad["u"][0] = [2.0, 0.0, 0.0]
+    r.d_planes.copy_(torch.from_numpy(bad.view(np.uint8).copy()))
+    params = torch.from_numpy(R.pack_params(g, cfg.cov_param)).cuda()
+    with pytest.raises(B.UgError) as e:
+        r.forward(params)
+    assert e.value.status == B.UG_ERR_INVALID_PLANE
+
+
+def test_capacity_overflow_is_reported_and_recovered():
+    g, pl = synth.workload_fwd_2k()
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    r = R.Renderer(2000, pl, cfg, record_capacity=16, instance_capacity=32)
+    params = torch.from_numpy(R.pack_params(g, cfg.cov_param)).cuda()
+    B.ug_preprocess(r.plan, R.gaussians_struct(params, cfg.cov_param), r.d_planes, r.ws)
+    st = r.status()
+    assert st["status"] == B.UG_ERR_CAPACITY and st["records"] > 16
+    image, alpha = r.forward(params)  # grows and retries
+    ref = oracle.render(g, pl, oracle_config(cfg))
+    assert_forward_parity(image.cpu().numpy().astype(np.float64),
+                          alpha.cpu().numpy().astype(np.float64), ref, "regrown")
+
+
+def test_forward_is_deterministic():
+    g, pl = synth.workload_fwd_2k()
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    r = R.Renderer(2000, pl, cfg)
+    params = torch.from_numpy(R.pack_params(g, cfg.cov_param)).cuda()
+    a, _ = r.forward(params)
+    b, _ = r.forward(params)
+    assert torch.equal(a, b)
