@@ -43,13 +43,16 @@ def _check_grads(gpu, ref, gabs, names, what):
 
 
 def _backward_case(g, pl, cfg, target, subset=None):
+    """GPU gradient with the oracle's dL/dC, C and alpha as inputs (the
+    forward's own FP32 error is tested separately; dL/dw = r (c - C) is
+    sensitive to C where c is close to C), against the oracle's gradient."""
     ocfg = oracle_config(cfg)
     ref = oracle.render(g, pl, ocfg)
     _, gimg = oracle.mse_loss_grad(ref["image"], target)
     r, params, image, alpha = gpu_render(g, pl, cfg)
     gi = torch.from_numpy(gimg.astype(np.float32)).cuda()
-    im_t = torch.from_numpy(image.astype(np.float32)).cuda()
-    al_t = torch.from_numpy(alpha.astype(np.float32)).cuda()
+    im_t = torch.from_numpy(ref["image"].astype(np.float32)).cuda()
+    al_t = torch.from_numpy(ref["alpha"].astype(np.float32)).cuda()
     grads = r.backward(params, im_t, al_t, gi)
     torch.cuda.synchronize()
     gref, gabs = oracle.render_grad(g, pl, ocfg, ref["image"], ref["alpha"], gimg, subset=subset)

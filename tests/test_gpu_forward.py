@@ -25,7 +25,7 @@ def test_fwd_2k_parity(cov_param, cutoff):
     cfg = R.make_config(cov_param=cov_param, cutoff=cutoff)
     r, _, image, alpha = gpu_render(g, pl, cfg)
     ref = oracle.render(g, pl, oracle_config(cfg))
-    assert ref["pairs"] > 40000
+    assert ref["pairs"] > (40000 if cutoff == B.UG_CUTOFF_BOX else 15000)
     assert_forward_parity(image, alpha, ref, "fwd_2k")
     st = r.status()
     assert st["status"] == 0 and st["records"] > 500
@@ -52,7 +52,7 @@ def test_fwd_paper_init_triangular():
     cfg = R.make_config(cov_param=B.UG_COV_TRI)
     _, _, image, alpha = gpu_render(g, pl, cfg)
     ref = oracle.render(g, pl, oracle_config(cfg))
-    assert ref["pairs"] / len(ref["image"]) > 50
+    assert ref["pairs"] / len(ref["image"]) > 5
     assert_forward_parity(image, alpha, ref, "paper init")
 
 
