@@ -47,14 +47,15 @@ class Config:
     c_bg: float = 0.0
     cutoff: int = 0      # 0: box (paper), 1: box and ellipsoid
     cov_param: int = 0   # 0: triangular, 1: scale + quaternion
-    amb: float = 1e-5    # ambiguity margin for FP32 decisions
+    amb: float = 1e-5      # relative ambiguity margin for FP32 decisions
+    amb_abs: float = 2e-6  # absolute margin (world units): FP32 rounding of m and h
 
 
 class _CConfig(ctypes.Structure):
     _fields_ = [
         ("chi2", ctypes.c_double), ("beta", ctypes.c_double),
         ("alpha_bg", ctypes.c_double), ("c_bg", ctypes.c_double),
-        ("amb", ctypes.c_double), ("cutoff", ctypes.c_int32),
+        ("amb", ctypes.c_double), ("amb_abs", ctypes.c_double), ("cutoff", ctypes.c_int32),
         ("cov_param", ctypes.c_int32),
     ]
 
@@ -85,7 +86,7 @@ def _lib():
         lib.or_geometry.restype = None
         lib.or_geometry.argtypes = [i64, P, P, P, P, i32, P, P, P, P, P, P, P, P]
         lib.or_render_grad.restype = None
-        lib.or_render_grad.argtypes = [i64, P, P, P, P, i32, P, P, P, P, P, P, P, i64, P, P, i32]
+        lib.or_render_grad.argtypes = [i64, P, P, P, P, i32, P, P, P, P, P, P, P, i64, P, P, P, i32]
         lib.or_contrib.restype = i64
         lib.or_contrib.argtypes = [P, P, ctypes.c_double, ctypes.c_double, i32, P, P, P, P, P, i64]
         lib.or_covariance.restype = None
@@ -100,7 +101,8 @@ def _ptr(a: np.ndarray):
 
 
 def _cfg(cfg: Config) -> _CConfig:
-    return _CConfig(cfg.chi2, cfg.beta, cfg.alpha_bg, cfg.c_bg, cfg.amb, cfg.cutoff, cfg.cov_param)
+    return _CConfig(cfg.chi2, cfg.beta, cfg.alpha_bg, cfg.c_bg, cfg.amb, cfg.amb_abs, cfg.cutoff,
+                    cfg.cov_param)
 
 
 def max_threads() -> int:
@@ -170,9 +172,11 @@ def geometry(g: dict, planes: dict, cfg: Config) -> dict:
 
 
 def render_grad(g: dict, planes: dict, cfg: Config, image, alpha, grad_image, subset=None,
-                threads: int = 0):
+                threads: int = 0, with_ambiguity: bool = False):
     """Analytic FP64 gradient. Returns (grads, grads_abs), each (k, nparam)
-    with nparam = 3 + (6|7) + 2 in the order mean, covp, logit, intensity."""
+    with nparam = 3 + (6|7) + 2 in the order mean, covp, logit, intensity;
+    with_ambiguity=True also returns a (k,) bool array: the Gaussian has an
+    inclusion decision within the ambiguity margin."""
     mean, covp, logit, inten = _gauss(g, cfg.cov_param)
     P, pl, sz, _ = _planes(planes)
     nc = 6 if cfg.cov_param == 0 else 7
@@ -189,9 +193,13 @@ def render_grad(g: dict, planes: dict, cfg: Config, image, alpha, grad_image, su
         sub_ptr, nsub = _ptr(subset), k
     grads = np.zeros((k, npar), np.float64)
     gabs = np.zeros((k, npar), np.float64)
+    amb = np.zeros(k, np.int32)
     _lib().or_render_grad(len(logit), _ptr(mean), _ptr(covp), _ptr(logit), _ptr(inten), P,
                           _ptr(pl), _ptr(sz), ctypes.byref(_cfg(cfg)), _ptr(image), _ptr(alpha),
-                          _ptr(grad_image), sub_ptr, nsub, _ptr(grads), _ptr(gabs), threads)
+                          _ptr(grad_image), sub_ptr, nsub, _ptr(grads), _ptr(gabs), _ptr(amb),
+                          threads)
+    if with_ambiguity:
+        return grads, gabs, amb.astype(bool)
     return grads, gabs
 
 

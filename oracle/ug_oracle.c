@@ -35,9 +35,11 @@
  * The gradient is the analytic FP64 chain rule of the same formulas, with the
  * cut-off treated as a constant mask (as in all splatting rasterizers).
  *
- * Every inclusion decision whose margin is within amb * pitch (in-plane) or
- * amb * h3 (plane test) or amb * chi2 (ellipsoid test) is reported as
- * ambiguous: an FP32 implementation may take either side of it.
+ * Every inclusion decision whose margin is within amb * pitch + amb_abs
+ * (in-plane), amb * h3 + amb_abs (plane test) or amb * chi2 (ellipsoid test)
+ * is reported as ambiguous: an FP32 implementation may take either side of
+ * it. amb_abs (world units) covers the FP32 rounding of the probe-frame mean
+ * and half-extents, a few ulps of the scene's coordinates.
  */
 #include <math.h>
 #include <stdint.h>
@@ -48,7 +50,7 @@
 #endif
 
 typedef struct {
-  double chi2, beta, alpha_bg, c_bg, amb;
+  double chi2, beta, alpha_bg, c_bg, amb, amb_abs;
   int32_t cutoff;    /* 0: box (paper), 1: box and ellipsoid */
   int32_t cov_param; /* 0: triangular, 1: scale + quaternion */
 } or_config;
@@ -190,7 +192,7 @@ static void pg_compute(const or_plane* pl, const double* mean, const double* cov
   double bmin = g->m[2] - g->h[2], bmax = g->m[2] + g->h[2];
   g->visible = !(bmin > 0.0 || bmax < 0.0);
   double margin = g->h[2] - fabs(g->m[2]);
-  g->amb_plane = fabs(margin) <= cfg->amb * g->h[2];
+  g->amb_plane = fabs(margin) <= cfg->amb * g->h[2] + cfg->amb_abs;
 }
 
 static inline double px_x1(const or_plane* p, int64_t j) { return ((double)j + 0.5 - 0.5 * (double)p->w) * p->pu; }
@@ -210,16 +212,17 @@ static double pair_q(const or_plane* p, const or_pg* g, double x1, double x2, do
 static int pair_included(const or_plane* p, const or_pg* g, const or_config* cfg, double x1,
                          double x2, double q, int* amb) {
   *amb = 0;
+  const double t1 = cfg->amb * p->pu + cfg->amb_abs, t2 = cfg->amb * p->pv + cfg->amb_abs;
   if (!g->visible) {
-    *amb = g->amb_plane && (fabs(x1 - g->m[0]) <= g->h[0] * (1 + cfg->amb) + cfg->amb * p->pu) &&
-           (fabs(x2 - g->m[1]) <= g->h[1] * (1 + cfg->amb) + cfg->amb * p->pv);
+    *amb = g->amb_plane && (fabs(x1 - g->m[0]) <= g->h[0] * (1 + cfg->amb) + t1) &&
+           (fabs(x2 - g->m[1]) <= g->h[1] * (1 + cfg->amb) + t2);
     return 0;
   }
   double e1 = g->h[0] - fabs(x1 - g->m[0]);
   double e2 = g->h[1] - fabs(x2 - g->m[1]);
   int in = (g->m[0] - g->h[0] <= x1) && (x1 <= g->m[0] + g->h[0]) && (g->m[1] - g->h[1] <= x2) &&
            (x2 <= g->m[1] + g->h[1]);
-  int near1 = fabs(e1) <= cfg->amb * p->pu, near2 = fabs(e2) <= cfg->amb * p->pv;
+  int near1 = fabs(e1) <= t1, near2 = fabs(e2) <= t2;
   /* a decision can only flip if the other axis is inside or also near */
   if ((near1 && (e2 >= 0 || near2)) || (near2 && (e1 >= 0 || near1))) *amb = 1;
   if (in && g->amb_plane) *amb = 1;
@@ -299,7 +302,8 @@ int64_t or_render(int64_t n, const double* mean, const double* covp, const doubl
         for (int64_t g = 0; g < n; ++g) {
           const or_pg* G = &gs[g];
           if (!G->visible && !G->amb_plane) continue;
-          double hx = G->h[0] * (1 + 2 * cfg->amb), hy = G->h[1] * (1 + 2 * cfg->amb);
+          double hx = G->h[0] * (1 + 2 * cfg->amb) + 2 * cfg->amb_abs;
+          double hy = G->h[1] * (1 + 2 * cfg->amb) + 2 * cfg->amb_abs;
           double jlo = (G->m[0] - hx) / pl.pu + 0.5 * W - 0.5;
           double jhi = (G->m[0] + hx) / pl.pu + 0.5 * W - 0.5;
           double ilo = (G->m[1] - hy) / pl.pv + 0.5 * H - 0.5;
@@ -498,7 +502,7 @@ void or_render_grad(int64_t n, const double* mean, const double* covp, const dou
                     const double* intensity, int32_t P, const double* planes, const int64_t* sizes,
                     const or_config* cfg, const double* image, const double* alpha,
                     const double* grad_image, const int64_t* subset, int64_t nsub, double* grads,
-                    double* grads_abs, int32_t nthreads) {
+                    double* grads_abs, int32_t* amb_gauss, int32_t nthreads) {
   const int nc = ncovp(cfg->cov_param);
   const int np = 3 + nc + 2;
   const int64_t count = subset ? nsub : n;
@@ -511,17 +515,21 @@ void or_render_grad(int64_t n, const double* mean, const double* covp, const dou
     double gmu[3] = {0, 0, 0}, amu[3] = {0, 0, 0};
     double gPi[3][3] = {{0}}, aPi[3][3] = {{0}};
     double glogit = 0, alogit = 0, gc = 0, ac = 0;
+    int any_amb = 0;
     for (int32_t pi = 0; pi < P; ++pi) {
       or_plane pl;
       load_plane(planes + 11 * pi, sizes + 3 * pi, &pl);
       or_pg G;
       pg_compute(&pl, gauss_mean(mean, g), covp + nc * g, logit[g], intensity[g], cfg, &G);
+      if (G.amb_plane) any_amb = 1;
       if (!G.visible) continue;
       const int64_t W = pl.w, H = pl.h;
-      double jlo = (G.m[0] - G.h[0]) / pl.pu + 0.5 * W - 0.5;
-      double jhi = (G.m[0] + G.h[0]) / pl.pu + 0.5 * W - 0.5;
-      double ilo = (G.m[1] - G.h[1]) / pl.pv + 0.5 * H - 0.5;
-      double ihi = (G.m[1] + G.h[1]) / pl.pv + 0.5 * H - 0.5;
+      double hx = G.h[0] * (1 + 2 * cfg->amb) + 2 * cfg->amb_abs;
+      double hy = G.h[1] * (1 + 2 * cfg->amb) + 2 * cfg->amb_abs;
+      double jlo = (G.m[0] - hx) / pl.pu + 0.5 * W - 0.5;
+      double jhi = (G.m[0] + hx) / pl.pu + 0.5 * W - 0.5;
+      double ilo = (G.m[1] - hy) / pl.pv + 0.5 * H - 0.5;
+      double ihi = (G.m[1] + hy) / pl.pv + 0.5 * H - 0.5;
       if (!(jhi >= -1.0) || !(jlo <= (double)W) || !(ihi >= -1.0) || !(ilo <= (double)H)) continue;
       int64_t j0 = (int64_t)floor(jlo) - 1, j1 = (int64_t)ceil(jhi) + 1;
       int64_t i0 = (int64_t)floor(ilo) - 1, i1 = (int64_t)ceil(ihi) + 1;
@@ -536,7 +544,9 @@ void or_render_grad(int64_t n, const double* mean, const double* covp, const dou
           double dl[3];
           double q = pair_q(&pl, &G, x1, x2, dl);
           int am;
-          if (!pair_included(&pl, &G, cfg, x1, x2, q, &am)) continue;
+          int inc = pair_included(&pl, &G, cfg, x1, x2, q, &am);
+          if (am) any_amb = 1;
+          if (!inc) continue;
           int64_t o = pl.off + i * W + j;
           double w = G.alpha * exp(-0.5 * q);
           double Gp = grad_image[o], A = alpha[o], C = image[o];
@@ -571,6 +581,7 @@ void or_render_grad(int64_t n, const double* mean, const double* covp, const dou
     aout[3 + nc] = alogit;
     out[4 + nc] = gc;
     aout[4 + nc] = ac;
+    if (amb_gauss) amb_gauss[s] = any_amb;
   }
 }
 

@@ -55,9 +55,14 @@ def _backward_case(g, pl, cfg, target, subset=None):
     al_t = torch.from_numpy(ref["alpha"].astype(np.float32)).cuda()
     grads = r.backward(params, im_t, al_t, gi)
     torch.cuda.synchronize()
-    gref, gabs = oracle.render_grad(g, pl, ocfg, ref["image"], ref["alpha"], gimg, subset=subset)
+    gref, gabs, amb = oracle.render_grad(g, pl, ocfg, ref["image"], ref["alpha"], gimg,
+                                         subset=subset, with_ambiguity=True)
     gpu = _grad_rows(grads, cfg.cov_param, subset)
-    return gpu, gref, gabs, grads
+    # a Gaussian with an inclusion decision within rounding of an edge may
+    # include or drop that pixel (either is correct): compare the others
+    keep = ~amb
+    assert keep.mean() > 0.9, keep.mean()
+    return gpu[keep], gref[keep], gabs[keep], grads
 
 
 @pytest.mark.parametrize("cov_param", [B.UG_COV_SCALE_ROT, B.UG_COV_TRI])
@@ -97,6 +102,10 @@ def test_grad_50k_16_planes_subset_and_fd():
     ocfg = oracle_config(cfg)
     target = oracle.render(g_t, pl, ocfg)["image"]
     subset = np.random.default_rng(0).choice(50_000, 500, replace=False)
+    _, _, amb = oracle.render_grad(g, pl, ocfg, np.zeros(pl["total_pixels"]),
+                                   np.ones(pl["total_pixels"]), np.zeros(pl["total_pixels"]),
+                                   subset=subset, with_ambiguity=True)
+    subset = subset[~amb]
     gpu, gref, gabs, _ = _backward_case(g, pl, cfg, target, subset=subset)
     names = oracle.param_names(1)
     _check_grads(gpu, gref, gabs, names, "grad_50k")
