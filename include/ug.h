@@ -135,9 +135,10 @@ typedef struct {
 typedef struct {
   int32_t status;       /* ug_status of the first data-dependent failure, 0 if none */
   int32_t detail;       /* e.g. the index of an invalid plane */
-  int64_t records;      /* visible (plane, Gaussian) records found by the last preprocess */
+  int64_t records;      /* record slots of the last preprocess: the visible (plane, Gaussian)
+                           pairs plus the FP64 candidates that the exact test rejected */
   int64_t instances;    /* (tile, record) instances found by the last preprocess */
-  int64_t fp64_records; /* records whose covariance inverse ran in FP64 */
+  int64_t fp64_records; /* visible records whose covariance inverse ran in FP64 */
   int64_t box_pixels;   /* sum over records of their clipped pixel-box area: the number
                            of (pixel, Gaussian) pairs the box cut-off includes */
   int64_t reserved[3];

@@ -156,25 +156,32 @@ ug_status ug_plan_init(const ug_config* cfg, int64_t n, const ug_plane* host_pla
   const int64_t nblk_sort = sort_blocks(instance_capacity);
   const int64_t hist_entries = 256 * nblk_sort;
   size_t sz[kOffEnd];
+  const int64_t rc = record_capacity, ic = instance_capacity;
   sz[kOffHeader] = sizeof(WsHeader);
   sz[kOffPlanes] = sizeof(PlaneDev) * (size_t)P;
   sz[kOffTileOff] = sizeof(int32_t) * (size_t)(P + 1);
+  sz[kOffGFlag] = sizeof(uint32_t) * (size_t)plan->chunks;
   sz[kOffMask] = sizeof(uint32_t) * (size_t)entries;
-  sz[kOffInstCnt] = sz[kOffMask];
-  sz[kOffRecBase] = sz[kOffMask];
-  sz[kOffInstBase] = sz[kOffMask];
+  sz[kOffSlotBase] = sz[kOffMask];
+  sz[kOffF64Base] = sz[kOffMask];
   sz[kOffScanPart] = 2 * sizeof(unsigned long long) * (size_t)(scan_blocks(entries) + 1);
-  sz[kOffRecA] = sizeof(float4) * (size_t)record_capacity;
-  sz[kOffRecB] = sizeof(float4) * (size_t)record_capacity;
-  sz[kOffRecBox] = sizeof(uint2) * (size_t)record_capacity;
-  sz[kOffKeys0] = sizeof(uint32_t) * (size_t)instance_capacity;
+  sz[kOffList] = sizeof(uint4) * (size_t)rc;
+  sz[kOffRecA] = sizeof(float4) * (size_t)rc;
+  sz[kOffRecB] = sizeof(float4) * (size_t)rc;
+  sz[kOffRecBox] = sizeof(uint2) * (size_t)rc;
+  sz[kOffRecPlane] = sizeof(uint32_t) * (size_t)rc;
+  sz[kOffInstOff] = sizeof(uint32_t) * (size_t)rc;
+  sz[kOffSlotPart] = sizeof(unsigned long long) * (size_t)(scan_blocks(rc) + 1);
+  sz[kOffKeys0] = sizeof(uint32_t) * (size_t)ic;
   sz[kOffKeys1] = sz[kOffKeys0];
   sz[kOffVals0] = sz[kOffKeys0];
   sz[kOffVals1] = sz[kOffKeys0];
   sz[kOffSortHist] = sizeof(uint32_t) * (size_t)hist_entries;
   sz[kOffSortPart] = sizeof(unsigned long long) * (size_t)(scan_blocks(hist_entries) + 1);
   sz[kOffRanges] = sizeof(uint2) * (size_t)total_tiles;
-  sz[kOffRecGrad] = 8 * sizeof(float) * (size_t)record_capacity;
+  sz[kOffRecGrad] = 8 * sizeof(float) * (size_t)rc;
+  sz[kOffRecPGrad] = 12 * sizeof(float) * (size_t)rc;
+  static_assert(kOffEnd <= 24, "ug_plan::off holds 24 sections");
   size_t off = 0;
   for (int k = 0; k < kOffEnd; ++k) {
     plan->off[k] = off;

@@ -22,14 +22,18 @@ enum WsSection {
   kOffHeader = 0,
   kOffPlanes,
   kOffTileOff,
-  kOffMask,
-  kOffInstCnt,
-  kOffRecBase,
-  kOffInstBase,
-  kOffScanPart,
+  kOffGFlag,     // per chunk: ballot of Gaussians whose covariance inverse runs in FP64
+  kOffMask,      // per (chunk, plane): candidate record bits
+  kOffSlotBase,  // per (chunk, plane): first record slot
+  kOffF64Base,   // per (chunk, plane): first FP64 list entry
+  kOffScanPart,  // partials of the (chunk, plane) scan
+  kOffList,      // record work list: uint4 (gaussian, plane, slot, 0); FP32 part then FP64 part
   kOffRecA,
   kOffRecB,
   kOffRecBox,
+  kOffRecPlane,
+  kOffInstOff,   // per record: tile count, scanned in place to the first instance
+  kOffSlotPart,  // partials of the record scan
   kOffKeys0,
   kOffKeys1,
   kOffVals0,
@@ -37,7 +41,8 @@ enum WsSection {
   kOffSortHist,
   kOffSortPart,
   kOffRanges,
-  kOffRecGrad,
+  kOffRecGrad,   // per record: 8 accumulators of the backward rasterizer
+  kOffRecPGrad,  // per record: gradient of the Gaussian's parameters (12 floats)
   kOffEnd
 };
 
@@ -45,10 +50,10 @@ enum WsSection {
 struct WsHeader {
   ug_ws_status st;            // 64 B, copied out by ug_read_status
   uint32_t tile_counter[2];   // persistent-kernel work queues (forward, backward)
-  uint32_t pad0[2];
-  unsigned long long fp64_count;
+  uint32_t slots, slots64;    // record slots and FP64 list entries of the last preprocess
   unsigned long long box_pixels;
-  uint32_t pad1[40];
+  uint32_t holes;             // FP64 candidates rejected by the exact test
+  uint32_t pad1[41];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
@@ -79,20 +84,25 @@ struct WsView {
   WsHeader* hdr;
   PlaneDev* planes;
   int32_t* tile_off;
+  uint32_t* gflag;
   uint32_t* mask;
-  uint32_t* inst_cnt;
-  uint32_t* rec_base;
-  uint32_t* inst_base;
+  uint32_t* slot_base;
+  uint32_t* f64_base;
   unsigned long long* scan_part;
+  uint4* list;
   float4* rec_a;
   float4* rec_b;
   uint2* rec_box;
+  uint32_t* rec_plane;
+  uint32_t* inst_off;
+  unsigned long long* slot_part;
   uint32_t* keys[2];
   uint32_t* vals[2];
   uint32_t* sort_hist;
   unsigned long long* sort_part;
   uint2* ranges;
-  float* rec_grad;  // 8 floats per record
+  float* rec_grad;   // 8 floats per record
+  float* rec_pgrad;  // 12 floats per record
 };
 
 inline WsView make_view(const ug_plan* plan, void* ws) {
@@ -101,14 +111,18 @@ inline WsView make_view(const ug_plan* plan, void* ws) {
   v.hdr = reinterpret_cast<WsHeader*>(b + plan->off[kOffHeader]);
   v.planes = reinterpret_cast<PlaneDev*>(b + plan->off[kOffPlanes]);
   v.tile_off = reinterpret_cast<int32_t*>(b + plan->off[kOffTileOff]);
+  v.gflag = reinterpret_cast<uint32_t*>(b + plan->off[kOffGFlag]);
   v.mask = reinterpret_cast<uint32_t*>(b + plan->off[kOffMask]);
-  v.inst_cnt = reinterpret_cast<uint32_t*>(b + plan->off[kOffInstCnt]);
-  v.rec_base = reinterpret_cast<uint32_t*>(b + plan->off[kOffRecBase]);
-  v.inst_base = reinterpret_cast<uint32_t*>(b + plan->off[kOffInstBase]);
+  v.slot_base = reinterpret_cast<uint32_t*>(b + plan->off[kOffSlotBase]);
+  v.f64_base = reinterpret_cast<uint32_t*>(b + plan->off[kOffF64Base]);
   v.scan_part = reinterpret_cast<unsigned long long*>(b + plan->off[kOffScanPart]);
+  v.list = reinterpret_cast<uint4*>(b + plan->off[kOffList]);
   v.rec_a = reinterpret_cast<float4*>(b + plan->off[kOffRecA]);
   v.rec_b = reinterpret_cast<float4*>(b + plan->off[kOffRecB]);
   v.rec_box = reinterpret_cast<uint2*>(b + plan->off[kOffRecBox]);
+  v.rec_plane = reinterpret_cast<uint32_t*>(b + plan->off[kOffRecPlane]);
+  v.inst_off = reinterpret_cast<uint32_t*>(b + plan->off[kOffInstOff]);
+  v.slot_part = reinterpret_cast<unsigned long long*>(b + plan->off[kOffSlotPart]);
   v.keys[0] = reinterpret_cast<uint32_t*>(b + plan->off[kOffKeys0]);
   v.keys[1] = reinterpret_cast<uint32_t*>(b + plan->off[kOffKeys1]);
   v.vals[0] = reinterpret_cast<uint32_t*>(b + plan->off[kOffVals0]);
@@ -117,6 +131,7 @@ inline WsView make_view(const ug_plan* plan, void* ws) {
   v.sort_part = reinterpret_cast<unsigned long long*>(b + plan->off[kOffSortPart]);
   v.ranges = reinterpret_cast<uint2*>(b + plan->off[kOffRanges]);
   v.rec_grad = reinterpret_cast<float*>(b + plan->off[kOffRecGrad]);
+  v.rec_pgrad = reinterpret_cast<float*>(b + plan->off[kOffRecPGrad]);
   return v;
 }
 
@@ -179,6 +194,9 @@ cudaError_t launch_render_backward(const ug_plan* plan, const ug_gaussians* g, W
                                    const float* image, const float* alpha,
                                    const float* grad_image, const ug_gaussian_grads* grads,
                                    cudaStream_t s);
+cudaError_t launch_pre_backward(const ug_plan* plan, const ug_gaussians* g, WsView v,
+                                const ug_gaussian_grads* grads, cudaStream_t s);
+int device_sms();
 cudaError_t launch_mse(const float* image, const float* target, int64_t n, float* grad,
                        float* loss, cudaStream_t s);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int32_t rows, int64_t n,

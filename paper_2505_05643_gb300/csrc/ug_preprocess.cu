@@ -1,17 +1,46 @@
-// Rows a1-a3 and a8: plane set-up, per-(plane, Gaussian) preprocess in two
-// passes (count, then emit records and tile instances), and the chain rule
-// from per-record gradients back to the Gaussian parameters.
+// Rows a1-a3 and a8: plane set-up, the per-(plane, Gaussian) preprocess, the
+// tile instances, and the chain rule from per-record gradients back to the
+// Gaussian parameters.
 //
-// Work decomposition: one warp owns a chunk of 32 consecutive Gaussians
-// (one per lane, structure-of-arrays loads are coalesced) and walks all
-// planes, so the per-Gaussian factor (a1) is built once per step. Counts are
-// kept per (chunk, plane); their exclusive scan in (chunk, plane) order gives
-// every record its slot, so for any plane the records - and after the stable
-// sort the tile lists - are in ascending Gaussian order.
+// Record-parallel pipeline (every heavy kernel runs with full warps):
+//  1. cull     one warp per chunk of 32 consecutive Gaussians (coalesced
+//              structure-of-arrays loads) walks all planes and sets one
+//              candidate bit per (plane, Gaussian): the phase-1 test and a
+//              non-empty pixel box in FP32 for ordinary Gaussians; for
+//              Gaussians whose axis-ratio proxy exceeds fp64_ratio an FP32
+//              test with a rigorous rounding bound that only drops pairs the
+//              FP64 test would drop too.
+//  2. scan     of the candidate counts in (chunk, plane) order: every
+//              candidate gets its record slot, so for any plane the records,
+//              and after the stable sort the tile lists, are in ascending
+//              Gaussian order.
+//  3. list     writes the candidates into a work list, FP32 part first, then
+//              the FP64 part.
+//  4. records  one thread per list entry: FP32 or FP64 geometry (phase 1, box,
+//              in-plane conic, peak weight) and the record; FP64 candidates
+//              that the exact test rejects become empty slots.
+//  5. scan     of the records' tile counts, then emit the (tile, record)
+//              instances, one thread per record.
+// The backward chain is one thread per record (per-record parameter
+// gradients), then a per-Gaussian gather in the same slot order: no atomics,
+// deterministic.
+#include <algorithm>
+
 #include "ug_geometry.cuh"
 #include "ug_scan.cuh"
 
 namespace ug {
+
+int device_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
 
 // ------------------------------------------------------------------ planes
 __global__ void __launch_bounds__(256)
@@ -26,11 +55,13 @@ __global__ void __launch_bounds__(256)
     h->st.records = 0;
     h->st.instances = 0;
     h->st.fp64_records = 0;
+    h->st.box_pixels = 0;
     h->tile_counter[0] = 0;
     h->tile_counter[1] = 0;
-    h->fp64_count = 0;
+    h->slots = 0;
+    h->slots64 = 0;
     h->box_pixels = 0;
-    h->st.box_pixels = 0;
+    h->holes = 0;
     s_run = 0;
   }
   __syncthreads();
@@ -59,13 +90,13 @@ __global__ void __launch_bounds__(256)
         d.u[k] = q.u[k];
         d.v[k] = q.v[k];
       }
-      d.n[0] = q.u[1] * q.v[2] - q.u[2] * q.v[1];
-      d.n[1] = q.u[2] * q.v[0] - q.u[0] * q.v[2];
-      d.n[2] = q.u[0] * q.v[1] - q.u[1] * q.v[0];
+      d.n[0] = __fmaf_rn(q.u[1], q.v[2], -__fmul_rn(q.u[2], q.v[1]));
+      d.n[1] = __fmaf_rn(q.u[2], q.v[0], -__fmul_rn(q.u[0], q.v[2]));
+      d.n[2] = __fmaf_rn(q.u[0], q.v[1], -__fmul_rn(q.u[1], q.v[0]));
       d.pu = q.pitch_u;
       d.pv = q.pitch_v;
-      d.inv_pu = 1.f / q.pitch_u;
-      d.inv_pv = 1.f / q.pitch_v;
+      d.inv_pu = __fdiv_rn(1.f, q.pitch_u);
+      d.inv_pv = __fdiv_rn(1.f, q.pitch_v);
       d.half_w = 0.5f * (float)q.width;
       d.half_h = 0.5f * (float)q.height;
       d.jshift = d.half_w - 0.5f;
@@ -97,11 +128,64 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// ------------------------------------------------------------------ passes
+// ------------------------------------------------------------------ 1. cull
+// Certified FP32 phase-1 and image-overlap test for an ill-conditioned
+// Gaussian. Fi is the FP64 inverse factor rounded to FP32; rs[i] = sum_k
+// |Fi_ik| and R2 = sum_i rs[i]^2. For z = Fi r with |r_k| <= 1 computed in
+// FP32 (rounded Fi, rounded r from u x v, three-term FMA dot):
+//   |z_i - z_i*| <= 5 eps rs[i],  |S - S*| <= 10 eps sqrt(S R2) + 25 eps^2 R2 + 3 eps S
+// (eps = 2^-24); the probe-frame mean has |m - m*| <= 8 eps sum_k |mu_k - o_k|.
+// Returns false only when the pair is outside the chi^2 box on the plane or
+// its box misses the image for every value inside these bounds.
+struct CertGauss {
+  float mu[3];
+  float Fi[3][3];
+  float R2;
+};
+
+__device__ __forceinline__ float cert_S(const CertGauss& c, const float r[3], float& bound) {
+  const float eps = 5.9604645e-8f;
+  float S = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float z = fmaf(c.Fi[i][2], r[2], fmaf(c.Fi[i][1], r[1], c.Fi[i][0] * r[0]));
+    S = fmaf(z, z, S);
+  }
+  bound = 10.f * eps * sqrtf(S * c.R2) + 25.f * eps * eps * c.R2 + 3.f * eps * S;
+  bound = bound * 1.001f + 1e-37f;
+  return S;
+}
+
+__device__ bool cert_candidate(const CertGauss& c, const PlaneDev& pl, float chi2) {
+  const float eps = 5.9604645e-8f;
+  float d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = c.mu[k] - pl.o[k];
+  const float Bm = 8.f * eps * (fabsf(d[0]) + fabsf(d[1]) + fabsf(d[2])) * 1.001f + 1e-30f;
+  const float m3 = fmaf(pl.n[2], d[2], fmaf(pl.n[1], d[1], pl.n[0] * d[0]));
+  float B33;
+  const float S33 = cert_S(c, pl.n, B33);
+  const float lo = fmaxf(fabsf(m3) - Bm, 0.f);
+  if (lo * lo > chi2 * (S33 + B33) * 1.0001f) return false;  // certainly rejected by phase 1
+  // the box must reach the image in both directions (one pixel of slack)
+  const float m1 = fmaf(pl.u[2], d[2], fmaf(pl.u[1], d[1], pl.u[0] * d[0]));
+  const float m2 = fmaf(pl.v[2], d[2], fmaf(pl.v[1], d[1], pl.v[0] * d[0]));
+  float B11, B22;
+  const float S11 = cert_S(c, pl.u, B11);
+  const float S22 = cert_S(c, pl.v, B22);
+  const float h1 = sqrtf(chi2 * (S11 + B11)) * 1.0001f + Bm;
+  const float h2 = sqrtf(chi2 * (S22 + B22)) * 1.0001f + Bm;
+  const float jlo = (m1 - h1) * pl.inv_pu + pl.jshift - 1.f;
+  const float jhi = (m1 + h1) * pl.inv_pu + pl.jshift + 1.f;
+  const float ilo = (m2 - h2) * pl.inv_pv + pl.ishift - 1.f;
+  const float ihi = (m2 + h2) * pl.inv_pv + pl.ishift + 1.f;
+  if (jhi < 0.f || jlo > (float)(pl.w - 1) || ihi < 0.f || ilo > (float)(pl.h - 1)) return false;
+  return true;
+}
+
 struct LaneGauss {
   GaussParams prm;
   Factor<float> ff;
-  Factor<double> fd;
   bool active, use64;
 };
 
@@ -114,157 +198,209 @@ __device__ __forceinline__ void lane_setup(const ug_gaussians& g, int64_t n, int
   load_params(g, n, i, COV, L.prm);
   make_factor<float, COV>(L.prm, beta, L.ff);
   L.use64 = !(axis_ratio_proxy<COV>(L.ff) <= ratio);
-  if (L.use64) make_factor<double, COV>(L.prm, beta, L.fd);
 }
 
+template <int COV>
+__global__ void __launch_bounds__(256)
+    k_cull(ug_gaussians g, int64_t n, int P, float chi2, float beta, float ratio, int64_t chunks,
+           WsView v) {
+  if (dev_failed(v.hdr)) return;
+  const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (chunk >= chunks) return;
+  const int lane = threadIdx.x & 31;
+  LaneGauss L;
+  lane_setup<COV>(g, n, chunk * kChunk + lane, beta, ratio, L);
+  CertGauss cg;
+  if (L.use64) {
+    Factor<double> fd;
+    make_factor<double, COV>(L.prm, beta, fd);
+    float R2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      cg.mu[i] = L.prm.mu[i];
+      float rs = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        cg.Fi[i][k] = (float)fd.Fi[i][k];
+        rs += fabsf(cg.Fi[i][k]);
+      }
+      R2 = fmaf(rs, rs, R2);
+    }
+    cg.R2 = R2 * 1.001f;
+  }
+  const uint32_t fl = __ballot_sync(0xffffffffu, L.use64);
+  if (lane == 0) v.gflag[chunk] = fl;
+  for (int p = 0; p < P; ++p) {
+    const PlaneDev pl = v.planes[p];
+    bool cand = false;
+    if (L.active) {
+      if (L.use64) {
+        cand = cert_candidate(cg, pl, chi2);
+      } else {
+        PairGeo<float> gg;
+        cand = pair_box<float, COV>(L.ff, pl, chi2, gg).visible;
+      }
+    }
+    const uint32_t mask = __ballot_sync(0xffffffffu, cand);
+    if (lane == 0) v.mask[chunk * P + p] = mask;
+  }
+}
+
+// ------------------------------------------------------------------ 2. scan
+struct CandLoad {
+  const uint32_t* mask;
+  const uint32_t* gflag;
+  int P;
+  __device__ void operator()(int64_t e, uint32_t out[2]) const {
+    const uint32_t m = mask[e];
+    out[0] = __popc(m);
+    out[1] = __popc(m & gflag[e / P]);
+  }
+};
+struct CandStore {
+  uint32_t* slot_base;
+  uint32_t* f64_base;
+  __device__ void operator()(int64_t e, const uint32_t ex[2]) const {
+    slot_base[e] = ex[0];
+    f64_base[e] = ex[1];
+  }
+};
+
+// ------------------------------------------------------------------ 3. list
+__global__ void __launch_bounds__(256) k_list(int P, int64_t chunks, WsView v) {
+  if (dev_failed(v.hdr)) return;
+  const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (chunk >= chunks) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t fl = v.gflag[chunk];
+  const uint32_t n32 = v.hdr->slots - v.hdr->slots64;
+  const uint32_t lt = lanemask_lt();
+  const uint32_t g = (uint32_t)(chunk * kChunk + lane);
+  for (int p = 0; p < P; ++p) {
+    const int64_t e = chunk * P + p;
+    const uint32_t mask = v.mask[e];
+    if (!((mask >> lane) & 1u)) continue;
+    const uint32_t slot = v.slot_base[e] + __popc(mask & lt);
+    uint32_t idx;
+    if ((fl >> lane) & 1u) idx = n32 + v.f64_base[e] + __popc(mask & fl & lt);
+    else idx = (v.slot_base[e] - v.f64_base[e]) + __popc(mask & ~fl & lt);
+    v.list[idx] = make_uint4(g, (uint32_t)p, slot, 0u);
+  }
+}
+
+// ------------------------------------------------------------------ 4. records
 __device__ __forceinline__ uint32_t tile_count(const PairBox& pb, int ts) {
   if (!pb.visible) return 0u;
   return (uint32_t)(((pb.j1 >> ts) - (pb.j0 >> ts) + 1) * ((pb.i1 >> ts) - (pb.i0 >> ts) + 1));
 }
 
-template <int COV>
-__global__ void __launch_bounds__(256)
-    k_pre_count(ug_gaussians g, int64_t n, int P, int ts, float chi2, float beta, float ratio,
-                int64_t chunks, WsView v) {
-  if (dev_failed(v.hdr)) return;
-  const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (chunk >= chunks) return;
-  const int lane = threadIdx.x & 31;
-  LaneGauss L;
-  lane_setup<COV>(g, n, chunk * kChunk + lane, beta, ratio, L);
-  for (int p = 0; p < P; ++p) {
-    const PlaneDev pl = v.planes[p];
-    PairBox pb;
-    pb.visible = false;
-    if (L.active) {
-      if (L.use64) {
-        PairGeo<double> gg;
-        pb = pair_box<double, COV>(L.fd, pl, chi2, gg);
-      } else {
-        PairGeo<float> gg;
-        pb = pair_box<float, COV>(L.ff, pl, chi2, gg);
-      }
-    }
-    const uint32_t mask = __ballot_sync(0xffffffffu, pb.visible);
-    const uint32_t tot = warp_sum(tile_count(pb, ts));
-    if (lane == 0) {
-      v.mask[chunk * P + p] = mask;
-      v.inst_cnt[chunk * P + p] = tot;
-    }
-  }
-}
-
 template <typename T>
-__device__ __forceinline__ void write_record(const PairRec<T>& rc, const PairGeo<T>& gg,
-                                             const PlaneDev& pl, const PairBox& pb,
-                                             const LaneGauss& L, float chi2, WsView& v,
-                                             uint32_t rid) {
+__device__ __forceinline__ void write_record(const PairRec<T>& rc, const PlaneDev& pl,
+                                             const PairBox& pb, const GaussParams& prm,
+                                             float chi2, WsView& v, uint32_t slot) {
   const float xs_j = (float)(rc.xs1 * (T)pl.inv_pu + (T)pl.half_w);
   const float xs_i = (float)(rc.xs2 * (T)pl.inv_pv + (T)pl.half_h);
   const float q0 = (float)rc.q0;
-  const float lw2 = log2_sigmoid(L.prm.logit) - kHalfLog2e * q0;
+  const float lw2 = log2_sigmoid(prm.logit) - kHalfLog2e * q0;
   const float ethr = kHalfLog2e * (chi2 - q0);
-  v.rec_a[rid] = make_float4(xs_j, xs_i, (float)rc.r11, (float)rc.r12);
-  v.rec_b[rid] = make_float4((float)rc.r22, lw2, L.prm.c, ethr);
-  v.rec_box[rid] = make_uint2((uint32_t)pb.j0 | ((uint32_t)pb.j1 << 16),
-                              (uint32_t)pb.i0 | ((uint32_t)pb.i1 << 16));
+  v.rec_a[slot] = make_float4(xs_j, xs_i, (float)rc.r11, (float)rc.r12);
+  v.rec_b[slot] = make_float4((float)rc.r22, lw2, prm.c, ethr);
+  v.rec_box[slot] = make_uint2((uint32_t)pb.j0 | ((uint32_t)pb.j1 << 16),
+                               (uint32_t)pb.i0 | ((uint32_t)pb.i1 << 16));
 }
 
-template <int COV>
+__device__ __forceinline__ bool box_empty(uint2 b) {
+  return (b.x & 0xffffu) > (b.x >> 16) || (b.y & 0xffffu) > (b.y >> 16);
+}
+
+template <typename T, int COV>
 __global__ void __launch_bounds__(256)
-    k_pre_emit(ug_gaussians g, int64_t n, int P, int ts, float chi2, float beta, float ratio,
-               int64_t chunks, WsView v, uint32_t rec_cap, uint32_t inst_cap) {
+    k_records(ug_gaussians g, int64_t n, int ts, float chi2, float beta, WsView v, int part) {
   if (dev_failed(v.hdr)) return;
-  const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (chunk >= chunks) return;
-  const int lane = threadIdx.x & 31;
-  LaneGauss L;
-  lane_setup<COV>(g, n, chunk * kChunk + lane, beta, ratio, L);
-  uint32_t n64 = 0;
+  const uint32_t slots = v.hdr->slots, n64 = v.hdr->slots64;
+  const uint32_t begin = part == 0 ? 0u : slots - n64;
+  const uint32_t end = part == 0 ? slots - n64 : slots;
   unsigned long long npx = 0;
-  for (int p = 0; p < P; ++p) {
-    const int64_t e = chunk * P + p;
-    const uint32_t mask = v.mask[e];
-    if (mask == 0u) continue;
-    const bool mine = (mask >> lane) & 1u;
-    const PlaneDev pl = v.planes[p];
-    PairBox pb;
-    pb.visible = false;
-    const uint32_t rid = v.rec_base[e] + __popc(mask & lanemask_lt());
-    const bool rid_ok = rid < rec_cap;  // always true after a successful count scan
-    if (mine && !rid_ok) dev_fail(v.hdr, UG_ERR_INTERNAL, 3);
-    if (mine && rid_ok) {
-      if (L.use64) {
-        PairGeo<double> gg;
-        pb = pair_box<double, COV>(L.fd, pl, chi2, gg);
-        if (pb.visible) {
-          PairRec<double> rc;
-          pair_record<double, COV>(L.fd, pl, gg, rc);
-          write_record<double>(rc, gg, pl, pb, L, chi2, v, rid);
-        }
-        n64++;
-      } else {
-        PairGeo<float> gg;
-        pb = pair_box<float, COV>(L.ff, pl, chi2, gg);
-        if (pb.visible) {
-          PairRec<float> rc;
-          pair_record<float, COV>(L.ff, pl, gg, rc);
-          write_record<float>(rc, gg, pl, pb, L, chi2, v, rid);
-        }
-      }
-      if (!pb.visible) dev_fail(v.hdr, UG_ERR_INTERNAL, 1);
-    }
-    const uint32_t cnt = tile_count(pb, ts);
-    const uint32_t incl = warp_incl_scan(cnt);
-    const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-    if (lane == 0 && tot != v.inst_cnt[e]) dev_fail(v.hdr, UG_ERR_INTERNAL, 2);
-    if (mine && pb.visible) {
+  uint32_t holes = 0;
+  for (uint32_t k = begin + blockIdx.x * blockDim.x + threadIdx.x; k < end;
+       k += gridDim.x * blockDim.x) {
+    const uint4 e = v.list[k];
+    const uint32_t slot = e.z;
+    const PlaneDev pl = v.planes[e.y];
+    GaussParams prm;
+    load_params(g, n, e.x, COV, prm);
+    Factor<T> f;
+    make_factor<T, COV>(prm, beta, f);
+    PairGeo<T> gg;
+    const PairBox pb = pair_box<T, COV>(f, pl, chi2, gg);
+    v.rec_plane[slot] = e.y;
+    if (pb.visible) {
+      PairRec<T> rc;
+      pair_record<T, COV>(f, pl, gg, rc);
+      write_record<T>(rc, pl, pb, prm, chi2, v, slot);
+      v.inst_off[slot] = tile_count(pb, ts);
       npx += (unsigned long long)(pb.j1 - pb.j0 + 1) * (unsigned long long)(pb.i1 - pb.i0 + 1);
-      uint32_t o = v.inst_base[e] + incl - cnt;
-      const int tx0 = pb.j0 >> ts, tx1 = pb.j1 >> ts, ty0 = pb.i0 >> ts, ty1 = pb.i1 >> ts;
-      uint32_t* keys = v.keys[0];
-      uint32_t* vals = v.vals[0];
-      for (int ty = ty0; ty <= ty1; ++ty) {
-        const uint32_t row = (uint32_t)(pl.tile_off + ty * pl.tiles_x);
-        for (int tx = tx0; tx <= tx1; ++tx) {
-          if (o < inst_cap) {  // guards a count/emit disagreement (flagged above)
-            keys[o] = row + (uint32_t)tx;
-            vals[o] = rid;
-          }
-          ++o;
+    } else {
+      v.rec_box[slot] = make_uint2(1u, 1u);  // empty: j0 = 1 > j1 = 0
+      v.inst_off[slot] = 0u;
+      holes++;
+      if (part == 0) dev_fail(v.hdr, UG_ERR_INTERNAL, 1);  // FP32 decisions are repeated exactly
+    }
+  }
+  npx = warp_sum(npx);
+  holes = warp_sum(holes);
+  if ((threadIdx.x & 31) == 0) {
+    if (npx) atomicAdd(&v.hdr->box_pixels, npx);
+    if (holes) atomicAdd(&v.hdr->holes, holes);
+  }
+}
+
+struct SlotLoad {
+  const uint32_t* cnt;
+  const WsHeader* hdr;
+  __device__ void operator()(int64_t e, uint32_t out[1]) const {
+    out[0] = e < (int64_t)hdr->slots ? cnt[e] : 0u;
+  }
+};
+struct SlotStore {
+  uint32_t* off;
+  const WsHeader* hdr;
+  __device__ void operator()(int64_t e, const uint32_t ex[1]) const {
+    if (e < (int64_t)hdr->slots) off[e] = ex[0];
+  }
+};
+
+// ------------------------------------------------------------------ 5. emit
+__global__ void __launch_bounds__(256) k_emit(int ts, uint32_t inst_cap, WsView v) {
+  if (dev_failed(v.hdr)) return;
+  const uint32_t slots = v.hdr->slots;
+  for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < slots;
+       slot += gridDim.x * blockDim.x) {
+    const uint2 bx = v.rec_box[slot];
+    if (box_empty(bx)) continue;
+    const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
+    const PlaneDev& pl = v.planes[v.rec_plane[slot]];
+    const int tiles_x = pl.tiles_x, toff = pl.tile_off;
+    uint32_t o = v.inst_off[slot];
+    for (int ty = i0 >> ts; ty <= (i1 >> ts); ++ty) {
+      const uint32_t row = (uint32_t)(toff + ty * tiles_x);
+      for (int tx = j0 >> ts; tx <= (j1 >> ts); ++tx) {
+        if (o < inst_cap) {
+          v.keys[0][o] = row + (uint32_t)tx;
+          v.vals[0][o] = slot;
         }
+        ++o;
       }
     }
   }
-  const uint32_t w64 = warp_sum(n64);
-  if (lane == 0 && w64) atomicAdd(&v.hdr->fp64_count, (unsigned long long)w64);
-  const unsigned long long wpx = warp_sum(npx);
-  if (lane == 0 && wpx) atomicAdd(&v.hdr->box_pixels, wpx);
 }
 
 __global__ void k_finish_pre(WsView v) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    v.hdr->st.fp64_records = (int64_t)v.hdr->fp64_count;
+    v.hdr->st.fp64_records = (int64_t)v.hdr->slots64 - (int64_t)v.hdr->holes;
     v.hdr->st.box_pixels = (int64_t)v.hdr->box_pixels;
   }
 }
-
-struct CountLoad {
-  const uint32_t* mask;
-  const uint32_t* cnt;
-  __device__ void operator()(int64_t e, uint32_t out[2]) const {
-    out[0] = __popc(mask[e]);
-    out[1] = cnt[e];
-  }
-};
-struct CountStore {
-  uint32_t* rec_base;
-  uint32_t* inst_base;
-  __device__ void operator()(int64_t e, const uint32_t ex[2]) const {
-    rec_base[e] = ex[0];
-    inst_base[e] = ex[1];
-  }
-};
 
 static int tile_shift(int tile) { return tile == 8 ? 3 : 4; }
 
@@ -275,42 +411,53 @@ cudaError_t launch_setup_planes(const ug_plan* plan, const ug_plane* d_planes, W
   return cudaGetLastError();
 }
 
-cudaError_t launch_preprocess(const ug_plan* plan, const ug_gaussians* g, WsView v,
-                              cudaStream_t s) {
+static unsigned list_grid(int64_t cap) {
+  const int64_t want = (cap + 255) / 256;
+  const int64_t most = (int64_t)device_sms() * 8;
+  return (unsigned)std::max<int64_t>(1, std::min(want, most));
+}
+
+template <int COV>
+static void launch_pre_cov(const ug_plan* plan, const ug_gaussians* g, WsView v, cudaStream_t s) {
   const int P = plan->num_planes;
   const int64_t chunks = plan->chunks;
   const int ts = tile_shift(plan->cfg.tile);
   const ug_config& c = plan->cfg;
-  if (chunks > 0) {
-    const int64_t blocks = (chunks * 32 + 255) / 256;
-    if (c.cov_param == UG_COV_TRI)
-      k_pre_count<UG_COV_TRI><<<(unsigned)blocks, 256, 0, s>>>(*g, plan->n, P, ts, c.chi2, c.beta,
-                                                               c.fp64_ratio, chunks, v);
-    else
-      k_pre_count<UG_COV_SCALE_ROT><<<(unsigned)blocks, 256, 0, s>>>(
-          *g, plan->n, P, ts, c.chi2, c.beta, c.fp64_ratio, chunks, v);
-  }
+  const int64_t wblocks = (chunks * 32 + 255) / 256;
+  if (chunks > 0)
+    k_cull<COV><<<(unsigned)wblocks, 256, 0, s>>>(*g, plan->n, P, c.chi2, c.beta, c.fp64_ratio,
+                                                  chunks, v);
   const int64_t entries = chunks * P;
   const int64_t nblk = scan_blocks(entries);
-  CountLoad ld{v.mask, v.inst_cnt};
-  CountStore st{v.rec_base, v.inst_base};
-  if (nblk > 0) k_scan_partial<2, CountLoad><<<(unsigned)nblk, kScanThreads, 0, s>>>(ld, entries, v.scan_part, v.hdr);
-  k_scan_top<2><<<1, 1024, 0, s>>>(v.scan_part, nblk, v.hdr, 1, plan->record_capacity,
-                                   plan->instance_capacity);
+  CandLoad ld{v.mask, v.gflag, P};
+  CandStore st{v.slot_base, v.f64_base};
   if (nblk > 0)
-    k_scan_down<2, CountLoad, CountStore><<<(unsigned)nblk, kScanThreads, 0, s>>>(ld, st, entries, v.scan_part, v.hdr);
-  if (chunks > 0) {
-    const int64_t blocks = (chunks * 32 + 255) / 256;
-    if (c.cov_param == UG_COV_TRI)
-      k_pre_emit<UG_COV_TRI><<<(unsigned)blocks, 256, 0, s>>>(
-          *g, plan->n, P, ts, c.chi2, c.beta, c.fp64_ratio, chunks, v,
-          (uint32_t)plan->record_capacity, (uint32_t)plan->instance_capacity);
-    else
-      k_pre_emit<UG_COV_SCALE_ROT><<<(unsigned)blocks, 256, 0, s>>>(
-          *g, plan->n, P, ts, c.chi2, c.beta, c.fp64_ratio, chunks, v,
-          (uint32_t)plan->record_capacity, (uint32_t)plan->instance_capacity);
-  }
+    k_scan_partial<2, CandLoad><<<(unsigned)nblk, kScanThreads, 0, s>>>(ld, entries, v.scan_part,
+                                                                        v.hdr);
+  k_scan_top<2><<<1, 1024, 0, s>>>(v.scan_part, nblk, v.hdr, 1, plan->record_capacity, 0);
+  if (nblk > 0)
+    k_scan_down<2, CandLoad, CandStore><<<(unsigned)nblk, kScanThreads, 0, s>>>(
+        ld, st, entries, v.scan_part, v.hdr);
+  if (chunks > 0) k_list<<<(unsigned)wblocks, 256, 0, s>>>(P, chunks, v);
+  const unsigned lg = list_grid(plan->record_capacity);
+  k_records<float, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.chi2, c.beta, v, 0);
+  k_records<double, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.chi2, c.beta, v, 1);
+  const int64_t rblk = scan_blocks(plan->record_capacity);
+  SlotLoad sl{v.inst_off, v.hdr};
+  SlotStore ss{v.inst_off, v.hdr};
+  k_scan_partial<1, SlotLoad><<<(unsigned)rblk, kScanThreads, 0, s>>>(
+      sl, plan->record_capacity, v.slot_part, v.hdr);
+  k_scan_top<1><<<1, 1024, 0, s>>>(v.slot_part, rblk, v.hdr, 2, plan->instance_capacity, 0);
+  k_scan_down<1, SlotLoad, SlotStore><<<(unsigned)rblk, kScanThreads, 0, s>>>(
+      sl, ss, plan->record_capacity, v.slot_part, v.hdr);
+  k_emit<<<lg, 256, 0, s>>>(ts, (uint32_t)plan->instance_capacity, v);
   k_finish_pre<<<1, 32, 0, s>>>(v);
+}
+
+cudaError_t launch_preprocess(const ug_plan* plan, const ug_gaussians* g, WsView v,
+                              cudaStream_t s) {
+  if (plan->cfg.cov_param == UG_COV_TRI) launch_pre_cov<UG_COV_TRI>(plan, g, v, s);
+  else launch_pre_cov<UG_COV_SCALE_ROT>(plan, g, v, s);
   return cudaGetLastError();
 }
 
@@ -328,7 +475,7 @@ template <typename T>
 struct ChainOut {
   T gmu[3];
   T gF[3][3];
-  T glw2;  // for the logit
+  T glw2;
 };
 
 template <typename T>
@@ -384,129 +531,163 @@ __device__ __forceinline__ void chain_record(const PairRec<T>& rc, const PairGeo
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const T u = (T)pl.u[k], vv = (T)pl.v[k], nn = (T)pl.n[k];
-    o.gmu[k] += gm1 * u + gm2 * vv + gm3 * nn;
+    o.gmu[k] = gm1 * u + gm2 * vv + gm3 * nn;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) o.gF[k][a] += u * gb1[a] + vv * gb2[a] + nn * gb3[a];
+    for (int a = 0; a < 3; ++a) o.gF[k][a] = u * gb1[a] + vv * gb2[a] + nn * gb3[a];
   }
-  o.glw2 += g_lw2;
+  o.glw2 = g_lw2;
 }
 
+// Parameter gradient of one record (12 floats: mean[3], tri[6] or
+// log_scale[3] + quat[4], logit, intensity; unused entries zero).
+template <typename T, int COV>
+__device__ __forceinline__ void record_param_grad(const ChainOut<T>& o, const Factor<T>& f,
+                                                  const GaussParams& prm, float gc, float* out) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) out[k] = (float)o.gmu[k];
+  const float alpha = sigmoidf(prm.logit);
+  if (COV == UG_COV_TRI) {
+    const float* t = prm.cp;
+    out[3] = (float)(2 * (T)t[0] * o.gF[0][0]);
+    out[4] = (float)o.gF[1][0];
+    out[5] = (float)o.gF[2][0];
+    out[6] = (float)(2 * (T)t[3] * o.gF[1][1]);
+    out[7] = (float)o.gF[2][1];
+    out[8] = (float)(2 * (T)t[5] * o.gF[2][2]);
+    out[9] = (float)o.glw2 * (1.f - alpha) * kLog2e;
+    out[10] = gc;
+    out[11] = 0.f;
+  } else {
+    // F = R diag(1/s): dL/dR_ka = gF_ka / s_a, dL/dlog s_a = -sum_k gF_ka F_ka
+    T gR[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T sacc = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        gR[k][a] = o.gF[k][a] / f.s[a];
+        sacc += o.gF[k][a] * f.F[k][a];
+      }
+      out[3 + a] = (float)(-sacc);
+    }
+    const T w = f.qn[0], x = f.qn[1], y = f.qn[2], z = f.qn[3];
+    const T gw = 2 * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] +
+                      x * gR[2][1]);
+    const T gx = 2 * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2 * x * gR[1][1] -
+                      w * gR[1][2] + z * gR[2][0] + w * gR[2][1] - 2 * x * gR[2][2]);
+    const T gy = 2 * (-2 * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] +
+                      z * gR[1][2] - w * gR[2][0] + z * gR[2][1] - 2 * y * gR[2][2]);
+    const T gz = 2 * (-2 * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] -
+                      2 * z * gR[1][1] + y * gR[1][2] + x * gR[2][0] + y * gR[2][1]);
+    const T dot = gw * w + gx * x + gy * y + gz * z;
+    const T inv = 1 / f.qnorm;
+    out[6] = (float)((gw - w * dot) * inv);
+    out[7] = (float)((gx - x * dot) * inv);
+    out[8] = (float)((gy - y * dot) * inv);
+    out[9] = (float)((gz - z * dot) * inv);
+    out[10] = (float)o.glw2 * (1.f - alpha) * kLog2e;
+    out[11] = gc;
+  }
+}
+
+template <typename T, int COV>
+__global__ void __launch_bounds__(256)
+    k_chain(ug_gaussians g, int64_t n, float chi2, float beta, WsView v, int part) {
+  if (dev_failed(v.hdr)) return;
+  const uint32_t slots = v.hdr->slots, n64 = v.hdr->slots64;
+  const uint32_t begin = part == 0 ? 0u : slots - n64;
+  const uint32_t end = part == 0 ? slots - n64 : slots;
+  for (uint32_t k = begin + blockIdx.x * blockDim.x + threadIdx.x; k < end;
+       k += gridDim.x * blockDim.x) {
+    const uint4 e = v.list[k];
+    const uint32_t slot = e.z;
+    float out[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) out[q] = 0.f;
+    if (!box_empty(v.rec_box[slot])) {
+      const float4 a0 = *reinterpret_cast<const float4*>(v.rec_grad + (size_t)slot * 8);
+      const float4 a1 = *reinterpret_cast<const float4*>(v.rec_grad + (size_t)slot * 8 + 4);
+      const float acc[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const PlaneDev pl = v.planes[e.y];
+      GaussParams prm;
+      load_params(g, n, e.x, COV, prm);
+      Factor<T> f;
+      make_factor<T, COV>(prm, beta, f);
+      PairGeo<T> gg;
+      pair_box<T, COV>(f, pl, chi2, gg);
+      PairRec<T> rc;
+      pair_record<T, COV>(f, pl, gg, rc);
+      ChainOut<T> o;
+      chain_record<T>(rc, gg, pl, acc, o);
+      record_param_grad<T, COV>(o, f, prm, acc[0], out);
+    }
+    float4* dst = reinterpret_cast<float4*>(v.rec_pgrad + (size_t)slot * 12);
+    dst[0] = make_float4(out[0], out[1], out[2], out[3]);
+    dst[1] = make_float4(out[4], out[5], out[6], out[7]);
+    dst[2] = make_float4(out[8], out[9], out[10], out[11]);
+  }
+}
+
+// Sum of the per-record parameter gradients of every Gaussian, in plane
+// order (deterministic), written to the gradient rows.
 template <int COV>
 __global__ void __launch_bounds__(256)
-    k_pre_bwd(ug_gaussians g, int64_t n, int P, float chi2, float beta, float ratio,
-              int64_t chunks, WsView v, ug_gaussian_grads out) {
+    k_gather(int64_t n, int P, int64_t chunks, WsView v, ug_gaussian_grads out) {
   if (dev_failed(v.hdr)) return;
   const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (chunk >= chunks) return;
   const int lane = threadIdx.x & 31;
   const int64_t i = chunk * kChunk + lane;
-  LaneGauss L;
-  lane_setup<COV>(g, n, i, beta, ratio, L);
-  ChainOut<float> of;
-  ChainOut<double> od;
+  const uint32_t lt = lanemask_lt();
+  float acc[12];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    of.gmu[k] = 0.f;
-    od.gmu[k] = 0.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      of.gF[k][a] = 0.f;
-      od.gF[k][a] = 0.0;
-    }
-  }
-  of.glw2 = 0.f;
-  od.glw2 = 0.0;
-  float gc = 0.f;
+  for (int q = 0; q < 12; ++q) acc[q] = 0.f;
   for (int p = 0; p < P; ++p) {
     const int64_t e = chunk * P + p;
     const uint32_t mask = v.mask[e];
     if (!((mask >> lane) & 1u)) continue;
-    const uint32_t rid = v.rec_base[e] + __popc(mask & lanemask_lt());
-    const float4 a0 = *reinterpret_cast<const float4*>(v.rec_grad + (size_t)rid * 8);
-    const float4 a1 = *reinterpret_cast<const float4*>(v.rec_grad + (size_t)rid * 8 + 4);
-    const float acc[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    gc += acc[0];
-    const PlaneDev pl = v.planes[p];
-    if (L.use64) {
-      PairGeo<double> gg;
-      pair_box<double, COV>(L.fd, pl, chi2, gg);
-      PairRec<double> rc;
-      pair_record<double, COV>(L.fd, pl, gg, rc);
-      chain_record<double>(rc, gg, pl, acc, od);
-    } else {
-      PairGeo<float> gg;
-      pair_box<float, COV>(L.ff, pl, chi2, gg);
-      PairRec<float> rc;
-      pair_record<float, COV>(L.ff, pl, gg, rc);
-      chain_record<float>(rc, gg, pl, acc, of);
-    }
+    const uint32_t slot = v.slot_base[e] + __popc(mask & lt);
+    const float4* src = reinterpret_cast<const float4*>(v.rec_pgrad + (size_t)slot * 12);
+    const float4 x0 = src[0], x1 = src[1], x2 = src[2];
+    acc[0] += x0.x; acc[1] += x0.y; acc[2] += x0.z; acc[3] += x0.w;
+    acc[4] += x1.x; acc[5] += x1.y; acc[6] += x1.z; acc[7] += x1.w;
+    acc[8] += x2.x; acc[9] += x2.y; acc[10] += x2.z; acc[11] += x2.w;
   }
-  if (!L.active) return;
-  float gmu[3], gF[3][3];
+  if (i >= n) return;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    gmu[k] = of.gmu[k] + (float)od.gmu[k];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) gF[k][a] = of.gF[k][a] + (float)od.gF[k][a];
-  }
-  const float glw2 = of.glw2 + (float)od.glw2;
-  const float alpha = sigmoidf(L.prm.logit);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) out.mean[k * n + i] = gmu[k];
-  out.opacity_logit[i] = glw2 * (1.f - alpha) * kLog2e;
-  out.intensity[i] = gc;
+  for (int k = 0; k < 3; ++k) out.mean[k * n + i] = acc[k];
   if (COV == UG_COV_TRI) {
-    const float* t = L.prm.cp;
-    out.tri[0 * n + i] = 2.f * t[0] * gF[0][0];
-    out.tri[1 * n + i] = gF[1][0];
-    out.tri[2 * n + i] = gF[2][0];
-    out.tri[3 * n + i] = 2.f * t[3] * gF[1][1];
-    out.tri[4 * n + i] = gF[2][1];
-    out.tri[5 * n + i] = 2.f * t[5] * gF[2][2];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out.tri[k * n + i] = acc[3 + k];
+    out.opacity_logit[i] = acc[9];
+    out.intensity[i] = acc[10];
   } else {
-    // F = R diag(1/s): dL/dR_ka = gF_ka / s_a, dL/dlog s_a = -sum_k gF_ka F_ka
-    const Factor<float>& f = L.ff;
-    float gR[3][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      float sacc = 0.f;
+    for (int k = 0; k < 3; ++k) out.log_scale[k * n + i] = acc[3 + k];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        gR[k][a] = gF[k][a] / f.s[a];
-        sacc += gF[k][a] * f.F[k][a];
-      }
-      out.log_scale[a * n + i] = -sacc;
-    }
-    const float w = f.qn[0], x = f.qn[1], y = f.qn[2], z = f.qn[3];
-    const float gw = 2.f * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] -
-                            y * gR[2][0] + x * gR[2][1]);
-    const float gx = 2.f * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2.f * x * gR[1][1] -
-                            w * gR[1][2] + z * gR[2][0] + w * gR[2][1] - 2.f * x * gR[2][2]);
-    const float gy = 2.f * (-2.f * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] +
-                            z * gR[1][2] - w * gR[2][0] + z * gR[2][1] - 2.f * y * gR[2][2]);
-    const float gz = 2.f * (-2.f * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] -
-                            2.f * z * gR[1][1] + y * gR[1][2] + x * gR[2][0] + y * gR[2][1]);
-    const float dot = gw * w + gx * x + gy * y + gz * z;
-    const float inv = 1.f / f.qnorm;
-    out.quat[0 * n + i] = (gw - w * dot) * inv;
-    out.quat[1 * n + i] = (gx - x * dot) * inv;
-    out.quat[2 * n + i] = (gy - y * dot) * inv;
-    out.quat[3 * n + i] = (gz - z * dot) * inv;
+    for (int k = 0; k < 4; ++k) out.quat[k * n + i] = acc[6 + k];
+    out.opacity_logit[i] = acc[10];
+    out.intensity[i] = acc[11];
   }
+}
+
+template <int COV>
+static void launch_chain_cov(const ug_plan* plan, const ug_gaussians* g, WsView v,
+                             const ug_gaussian_grads* grads, cudaStream_t s) {
+  const ug_config& c = plan->cfg;
+  const unsigned lg = list_grid(plan->record_capacity);
+  k_chain<float, COV><<<lg, 256, 0, s>>>(*g, plan->n, c.chi2, c.beta, v, 0);
+  k_chain<double, COV><<<lg, 256, 0, s>>>(*g, plan->n, c.chi2, c.beta, v, 1);
+  const int64_t chunks = plan->chunks;
+  if (chunks > 0)
+    k_gather<COV><<<(unsigned)((chunks * 32 + 255) / 256), 256, 0, s>>>(plan->n, plan->num_planes,
+                                                                         chunks, v, *grads);
 }
 
 cudaError_t launch_pre_backward(const ug_plan* plan, const ug_gaussians* g, WsView v,
                                 const ug_gaussian_grads* grads, cudaStream_t s) {
-  const int64_t chunks = plan->chunks;
-  if (chunks == 0) return cudaGetLastError();
-  const ug_config& c = plan->cfg;
-  const int64_t blocks = (chunks * 32 + 255) / 256;
-  if (c.cov_param == UG_COV_TRI)
-    k_pre_bwd<UG_COV_TRI><<<(unsigned)blocks, 256, 0, s>>>(*g, plan->n, plan->num_planes, c.chi2,
-                                                           c.beta, c.fp64_ratio, chunks, v, *grads);
-  else
-    k_pre_bwd<UG_COV_SCALE_ROT><<<(unsigned)blocks, 256, 0, s>>>(
-        *g, plan->n, plan->num_planes, c.chi2, c.beta, c.fp64_ratio, chunks, v, *grads);
+  if (plan->cfg.cov_param == UG_COV_TRI) launch_chain_cov<UG_COV_TRI>(plan, g, v, grads, s);
+  else launch_chain_cov<UG_COV_SCALE_ROT>(plan, g, v, grads, s);
   return cudaGetLastError();
 }
 

@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(Layout<TILE, WW, PPT>::NT)
 
 __global__ void k_zero_rec_grad(WsView v, int64_t cap) {
   if (dev_failed(v.hdr)) return;
-  const int64_t nrec = min((int64_t)v.hdr->st.records, cap);
+  const int64_t nrec = min((int64_t)v.hdr->slots, cap);
   float4* g = reinterpret_cast<float4*>(v.rec_grad);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrec * 2;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -359,9 +359,6 @@ cudaError_t launch_render(const ug_plan* plan, WsView v, float* image, float* al
   return plan->cfg.cutoff ? dispatch_fwd<1>(plan, v, vals, image, alpha, s)
                           : dispatch_fwd<0>(plan, v, vals, image, alpha, s);
 }
-
-cudaError_t launch_pre_backward(const ug_plan* plan, const ug_gaussians* g, WsView v,
-                                const ug_gaussian_grads* grads, cudaStream_t s);
 
 cudaError_t launch_render_backward(const ug_plan* plan, const ug_gaussians* g, WsView v,
                                    const float* image, const float* alpha,

@@ -63,8 +63,10 @@ __global__ void __launch_bounds__(kScanThreads)
 }
 
 // Exclusive scan of the block partials in place (one block of 1024 threads).
-// mode 1 (count scan): writes the totals to the header and flags capacity
-// overflow.
+// mode 1 (candidate scan, NV = 2): totals are the record slots and the FP64
+// entries; mode 2 (record scan, NV = 1): the total is the instance count.
+// Modes 1 and 2 write the totals to the header and flag capacity overflow
+// (cap0).
 template <int NV>
 __global__ void __launch_bounds__(1024)
     k_scan_top(unsigned long long* part, int64_t nblk, WsHeader* hdr, int mode, int64_t cap0,
@@ -116,9 +118,13 @@ __global__ void __launch_bounds__(1024)
     }
   if (mode == 1 && tid == 0) {
     hdr->st.records = (int64_t)tot[0];
-    hdr->st.instances = NV > 1 ? (int64_t)tot[NV - 1] : 0;
-    if ((int64_t)tot[0] > cap0 || (NV > 1 && (int64_t)tot[NV - 1] > cap1))
-      dev_fail(hdr, UG_ERR_CAPACITY, 0);
+    hdr->slots = (uint32_t)min(tot[0], (unsigned long long)cap0);
+    hdr->slots64 = NV > 1 ? (uint32_t)min(tot[NV - 1], (unsigned long long)cap0) : 0u;
+    if ((int64_t)tot[0] > cap0) dev_fail(hdr, UG_ERR_CAPACITY, 0);
+  }
+  if (mode == 2 && tid == 0) {
+    hdr->st.instances = (int64_t)tot[0];
+    if ((int64_t)tot[0] > cap0) dev_fail(hdr, UG_ERR_CAPACITY, 1);
   }
 }
 
