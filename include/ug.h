@@ -207,6 +207,25 @@ ug_status ug_render(const ug_plan* plan, void* ws, size_t ws_bytes, float* image
 ug_status ug_mse_loss_grad(const float* image, const float* target, int64_t n,
                            float* grad_image, float* loss, ug_stream stream);
 
+/* Largest n accepted by ug_mse_loss_grad_static (2^30 pixels). */
+#define UG_MSE_STATIC_MAX_N (1LL << 30)
+
+/* The same loss and gradient as ug_mse_loss_grad for callers that cannot
+ * allocate device memory. The paper has no counterpart; this exists for code
+ * that may not call cudaMalloc where it runs (inside a stream capture, in a
+ * plugin that is handed only the buffers it works on, under a memory budget
+ * owned by someone else). The caller passes only the inputs, grad_image (or
+ * NULL) and `loss`, which here is ONE device float. The per-block partial sums
+ * live in a 64 KiB array inside this library that stays allocated on every
+ * GPU that loads it until the process exits. Returns UG_ERR_INVALID_ARGUMENT
+ * for n < 1 or n > UG_MSE_STATIC_MAX_N. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture. All calls share
+ * the array: calls whose kernels may overlap on the GPU (unordered streams)
+ * race on it and must be serialised by the caller. Allocates nothing. */
+ug_status ug_mse_loss_grad_static(const float* image, const float* target, int64_t n,
+                                  float* grad_image, float* loss, ug_stream stream);
+
 /* Rows a7-a8: gradient of a scalar loss with respect to the Gaussian
  * parameters, given dL/dC per pixel (grad_image) and the image and alpha that
  * ug_render wrote for the same workspace. The box cut-off is a constant of the

@@ -34,8 +34,9 @@ UG_MSE_LOSS_FLOATS = 1025
 EXPORTS = (
     "ug_version", "ug_status_string", "ug_num_variants", "ug_config_default", "ug_plan_init",
     "ug_preprocess", "ug_bin_sort", "ug_render", "ug_mse_loss_grad", "ug_render_backward",
-    "ug_adam_step", "ug_read_status", "ug_debug_views",
+    "ug_adam_step", "ug_read_status", "ug_debug_views", "ug_mse_loss_grad_static",
 )
+UG_MSE_STATIC_MAX_N = 1 << 30
 
 
 class UgError(RuntimeError):
@@ -118,6 +119,7 @@ def load(build_if_missing: bool = True):
     lib.ug_bin_sort.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp]
     lib.ug_render.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp, vp, vp]
     lib.ug_mse_loss_grad.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.ug_mse_loss_grad_static.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.ug_render_backward.argtypes = [P(ug_plan), P(ug_gaussians), vp, vp, ctypes.c_size_t, vp,
                                        vp, vp, P(ug_gaussian_grads), vp]
     lib.ug_adam_step.argtypes = [vp, vp, vp, vp, i32, i64, vp, vp, f32, f32, f32, vp]
@@ -206,6 +208,13 @@ def ug_render(plan: ug_plan, ws, image, alpha, stream=None):
 def ug_mse_loss_grad(image, target, n: int, grad_image, loss, stream=None):
     _check(load().ug_mse_loss_grad(_ptr(image), _ptr(target), int(n), _ptr(grad_image),
                                    _ptr(loss), _stream(stream)), "ug_mse_loss_grad")
+
+
+def ug_mse_loss_grad_static(image, target, n: int, grad_image, loss, stream=None):
+    """MSE loss and gradient with the partial sums in the library's own static
+    device array: `loss` is one device float; nothing is allocated."""
+    _check(load().ug_mse_loss_grad_static(_ptr(image), _ptr(target), int(n), _ptr(grad_image),
+                                          _ptr(loss), _stream(stream)), "ug_mse_loss_grad_static")
 
 
 def ug_render_backward(plan: ug_plan, gaussians: ug_gaussians, d_planes, ws, image, alpha,
