@@ -159,7 +159,7 @@ def run_ours(args):
     # every rank trains its own replica of the workload (weak scaling, no collective)
     g, pl, target = _workload(args.n)
     cfg = R.make_config(cov_param=B.UG_COV_TRI, cutoff=B.UG_CUTOFF_BOX, tile=args.tile,
-                        variant=args.variant)
+                        variant=args.variant, variant_bwd=args.variant_bwd)
     n = len(g["logit"])
     renderer = R.Renderer(n, pl, cfg)
     params = torch.from_numpy(R.pack_params(g, B.UG_COV_TRI)).to(dev)
@@ -266,31 +266,38 @@ def run_ours(args):
            "h2d_bytes_per_step": int(h_targets.numel() * 4 + h_planes.numel()),
            "d2h_bytes_per_step": 4}
 
-    # ---- roofline of the dominant kernel (backward rasterizer, ALU bound)
-    # algorithmic FP32 flops per included pair: forward 13 + 1 ex2,
-    # backward 30 + 1 ex2; peak from unit counts and clocks: 152 SMs x 128 FP32
-    # lanes x 2 flops (FMA) x 2070 MHz.
+    # ---- roofline of the dominant kernel (backward rasterizer, FP32-pipe bound)
+    # Unit: one evaluated (pixel, record) pair. Algorithmic FP32-pipe operations
+    # per evaluated pair (an FMA counts once): forward 6 (+1 MUFU.EX2), backward
+    # 16 (+1 MUFU.EX2). Peak from unit counts and clocks: SMs x 128 FP32 lanes x
+    # max SM clock (2070 MHz); EX2 runs at 32/clk/SM and is not binding.
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    fp32_peak = sms * 128 * 2 * fmax
+    fp32_peak = sms * 128 * fmax
     bwd_s = float(np.median(bwd_ms)) * 1e-3
     fwd_s = float(np.median(fwd_ms)) * 1e-3
-    bwd_flops = 30.0 * pairs
-    roof = {"bound": "alu", "kernel": "k_render_bwd (ug_render_backward)",
-            "achieved": bwd_flops / bwd_s / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-            "frac": (bwd_flops / bwd_s) / fp32_peak, "traffic": None,
-            "peak_note": "derived: SMs x 128 FP32 lanes x 2 x max SM clock (FP32 FMA pipe)",
-            "fwd": {"achieved": 13.0 * pairs / fwd_s / 1e12, "ms": fwd_s * 1e3},
-            "bwd_ms": bwd_s * 1e3}
+    evaluated = float(np.mean([x.evaluated_pairs for x in sts[args.warmup:]]))
+    roof = {"bound": "alu", "kernel": "ug_render_backward (k_render_bwd + chain + gather)",
+            "achieved": 16.0 * evaluated / bwd_s / 1e12, "peak": fp32_peak / 1e12,
+            "unit": "Tops/s (FP32 pipe)", "frac": 16.0 * evaluated / bwd_s / fp32_peak,
+            "traffic": None,
+            "units_per_launch": evaluated, "ops_per_unit": 16,
+            "peak_note": "derived: SMs x 128 FP32 lanes x max SM clock",
+            "fwd": {"kernel": "ug_render (k_render_fwd)", "ms": fwd_s * 1e3,
+                    "achieved": 6.0 * evaluated / fwd_s / 1e12,
+                    "frac": 6.0 * evaluated / fwd_s / fp32_peak},
+            "bwd_ms": bwd_s * 1e3, "box_pairs_per_launch": pairs,
+            "evaluated_over_box_pairs": evaluated / pairs}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         sizes = pl["size"][:, 0]
-        smallest = int(np.argmin(sizes))
-        rate, dt, cores, cp = cpu_oracle_rate(g, pl, [smallest])
+        sample = list(range(args.cpu_planes))
+        rate, dt, cores, cp = cpu_oracle_rate(g, pl, sample)
         cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-               "sample": f"FP64 oracle scatter forward + analytic backward on plane {smallest} "
-                         f"({sizes[smallest]}^2, {cp} pairs) with all {n} Gaussians, {dt:.1f} s"}
+               "sample": f"FP64 oracle scatter forward + analytic backward on planes "
+                         f"0..{len(sample) - 1} (sizes {[int(x) for x in sizes[sample]]}; "
+                         f"{cp} pairs) with all {n} Gaussians, {dt:.1f} s"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
@@ -299,7 +306,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "gaussians": n, "planes": len(pl["size"]),
                        "pixels": int(pl["total_pixels"]), "pairs_per_step": pairs,
-                       "tile": args.tile, "variant": args.variant, "graph": True,
+                       "tile": args.tile, "variant": args.variant,
+                       "variant_bwd": args.variant_bwd, "graph": True,
                        "l2": "working set > L2 (129 MB); no flush",
                        "parallelism": f"replicas x{world}"},
             "steps_per_s": 1e3 / ms_step,
@@ -321,7 +329,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=16)
-    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=0, help="forward rasterizer variant")
+    ap.add_argument("--variant-bwd", type=int, default=3, help="backward rasterizer variant")
+    ap.add_argument("--cpu-planes", type=int, default=6, help="planes in the CPU oracle sample")
     ap.add_argument("--n", type=int, default=None, help="use the first n Gaussians (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()

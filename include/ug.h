@@ -109,9 +109,10 @@ typedef struct {
   int32_t cutoff;    /* UG_CUTOFF_BOX (paper) or UG_CUTOFF_BOX_AND_ELLIPSOID */
   int32_t cov_param; /* UG_COV_TRI (paper) or UG_COV_SCALE_ROT */
   int32_t tile;      /* square tile edge in pixels: 8 or 16 (default 16) */
-  int32_t variant;   /* rasterizer variant (ug_num_variants); 0 = default */
+  int32_t variant;   /* forward rasterizer variant (ug_num_variants); 0 = default */
   float fp64_ratio;  /* axis-ratio proxy above which the covariance inverse runs in FP64; 1e3 */
-  int32_t reserved[3];
+  int32_t variant_bwd; /* backward rasterizer variant (ug_num_variants); 0 = default */
+  int32_t reserved[2];
 } ug_config;
 
 /* Sizes, capacities and the workspace layout of one rendering problem.
@@ -141,7 +142,10 @@ typedef struct {
   int64_t fp64_records; /* visible records whose covariance inverse ran in FP64 */
   int64_t box_pixels;   /* sum over records of their clipped pixel-box area: the number
                            of (pixel, Gaussian) pairs the box cut-off includes */
-  int64_t reserved[3];
+  int64_t evaluated_pairs; /* (pixel, record) pairs the last ug_render evaluated: warp
+                              footprints x records that reach them; pairs whose weight is
+                              provably an FP32 zero are not evaluated */
+  int64_t reserved[2];
 } ug_ws_status;
 
 /* Adam learning-rate schedule of one parameter row (device array entry):

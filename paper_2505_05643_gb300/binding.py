@@ -50,7 +50,8 @@ class ug_config(ctypes.Structure):
                 ("alpha_bg", ctypes.c_float), ("c_bg", ctypes.c_float),
                 ("cutoff", ctypes.c_int32), ("cov_param", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("fp64_ratio", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
+                ("fp64_ratio", ctypes.c_float), ("variant_bwd", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class ug_plan(ctypes.Structure):
@@ -76,7 +77,7 @@ class ug_ws_status(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("detail", ctypes.c_int32),
                 ("records", ctypes.c_int64), ("instances", ctypes.c_int64),
                 ("fp64_records", ctypes.c_int64), ("box_pixels", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 3)]
+                ("evaluated_pairs", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2)]
 
 
 class ug_adam_row(ctypes.Structure):

@@ -25,6 +25,18 @@ __device__ __forceinline__ double r_fma(double a, double b, double c) { return _
 __device__ __forceinline__ double r_div(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ double r_sqrt(double a) { return __dsqrt_rn(a); }
 
+// Division and square root of values that are already accurate: in the FP64
+// branch the cancellation-prone sums (the covariance inverse and determinant
+// terms) run in FP64, and these well-conditioned operations on their results
+// run on the FP32 units (relative error 2^-24, far below the decision
+// margins), because FP64 division and square root are slow on GB300.
+__device__ __forceinline__ float m_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float m_sqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double m_div(double a, double b) {
+  return (double)__fdiv_rn((float)a, (float)b);
+}
+__device__ __forceinline__ double m_sqrt(double a) { return (double)__fsqrt_rn((float)a); }
+
 template <typename T>
 __device__ __forceinline__ T r_dot3(const T a[3], const T b[3]) {
   return r_fma(a[2], b[2], r_fma(a[1], b[1], r_mul(a[0], b[0])));
@@ -256,7 +268,7 @@ __device__ __forceinline__ PairBox pair_box(const Factor<T>& f, const PlaneDev& 
   apply_fi<T, COV>(f, fr.r[2], g.z[2]);
   g.S33 = r_dot3(g.z[2], g.z[2]);
   const T c2 = (T)chi2;
-  const T h3 = r_sqrt(r_mul(c2, g.S33));
+  const T h3 = m_sqrt(r_mul(c2, g.S33));
   if (!(r_sub(g.m[2], h3) <= (T)0 && r_add(g.m[2], h3) >= (T)0)) return pb;
   g.m[0] = r_dot3(fr.r[0], d);
   g.m[1] = r_dot3(fr.r[1], d);
@@ -264,8 +276,8 @@ __device__ __forceinline__ PairBox pair_box(const Factor<T>& f, const PlaneDev& 
   apply_fi<T, COV>(f, fr.r[1], g.z[1]);
   g.S11 = r_dot3(g.z[0], g.z[0]);
   g.S22 = r_dot3(g.z[1], g.z[1]);
-  const T h1 = r_sqrt(r_mul(c2, g.S11));
-  const T h2 = r_sqrt(r_mul(c2, g.S22));
+  const T h1 = m_sqrt(r_mul(c2, g.S11));
+  const T h2 = m_sqrt(r_mul(c2, g.S22));
   pixel_range<T>(g.m[0], h1, (T)pl.inv_pu, (T)pl.jshift, pl.w, pb.j0, pb.j1);
   pixel_range<T>(g.m[1], h2, (T)pl.inv_pv, (T)pl.ishift, pl.h, pb.i0, pb.i1);
   pb.visible = (pb.j0 <= pb.j1) && (pb.i0 <= pb.i1);
@@ -291,9 +303,9 @@ __device__ __forceinline__ void pair_record(const Factor<T>& f, const PlaneDev& 
   load_frame(pl, fr);
   const T S13 = r_dot3(g.z[0], g.z[2]);
   const T S23 = r_dot3(g.z[1], g.z[2]);
-  rc.k = r_div(g.m[2], g.S33);
-  rc.kappa[0] = -r_div(S13, g.S33);
-  rc.kappa[1] = -r_div(S23, g.S33);
+  rc.k = m_div(g.m[2], g.S33);
+  rc.kappa[0] = -m_div(S13, g.S33);
+  rc.kappa[1] = -m_div(S23, g.S33);
   rc.xs1 = r_fma(g.m[2], rc.kappa[0], g.m[0]);
   rc.xs2 = r_fma(g.m[2], rc.kappa[1], g.m[1]);
   rc.q0 = r_mul(g.m[2], rc.k);
@@ -307,13 +319,13 @@ __device__ __forceinline__ void pair_record(const Factor<T>& f, const PlaneDev& 
   cx[0] = r_fma(b1[1], b2[2], -r_mul(b1[2], b2[1]));
   cx[1] = r_fma(b1[2], b2[0], -r_mul(b1[0], b2[2]));
   cx[2] = r_fma(b1[0], b2[1], -r_mul(b1[1], b2[0]));
-  rc.nb1 = r_sqrt(r_dot3(b1, b1));
-  rc.cr = r_sqrt(r_dot3(cx, cx));
+  rc.nb1 = m_sqrt(r_dot3(b1, b1));
+  rc.cr = m_sqrt(r_dot3(cx, cx));
   const T sc = (T)0.84932180028801904272;  // sqrt(log2(e) / 2)
   const T pu = (T)pl.pu, pv = (T)pl.pv;
   rc.r11 = sc * pu * rc.nb1;
-  rc.r12 = sc * pv * r_div(r_dot3(b1, b2), rc.nb1);
-  rc.r22 = sc * pv * r_div(rc.cr, rc.nb1);
+  rc.r12 = sc * pv * m_div(r_dot3(b1, b2), rc.nb1);
+  rc.r22 = sc * pv * m_div(rc.cr, rc.nb1);
 }
 
 constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2

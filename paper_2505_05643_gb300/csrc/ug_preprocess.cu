@@ -495,11 +495,12 @@ __device__ __forceinline__ void chain_record(const PairRec<T>& rc, const PairGeo
   const T c = (T)kHalfLog2e;
   const T g_q0 = -c * g_lw2;
   // Cholesky backward of M = c D A D (M11 = r11^2, M12 = r11 r12, M22 = r12^2 + r22^2)
-  const T gM22 = g_r22 / (2 * rc.r22);
-  const T gr12 = g_r12 - g_r22 * rc.r12 / rc.r22;
-  const T gM12 = gr12 / rc.r11;
-  const T gr11 = g_r11 - gr12 * rc.r12 / rc.r11;
-  const T gM11 = gr11 / (2 * rc.r11);
+  const T i22 = m_div((T)1, rc.r22), i11 = m_div((T)1, rc.r11);
+  const T gM22 = g_r22 * i22 * (T)0.5;
+  const T gr12 = g_r12 - g_r22 * rc.r12 * i22;
+  const T gM12 = gr12 * i11;
+  const T gr11 = g_r11 - gr12 * rc.r12 * i11;
+  const T gM11 = gr11 * i11 * (T)0.5;
   T gA11 = c * pu * pu * gM11, gA12 = c * pu * pv * gM12, gA22 = c * pv * pv * gM22;
   // x* = m12 + m3 kappa, kappa = A^-1 s;  q0 = m3^2 (P33 - s^T A^-1 s)
   const T* b1 = rc.b[0];
@@ -507,9 +508,9 @@ __device__ __forceinline__ void chain_record(const PairRec<T>& rc, const PairGeo
   const T* b3 = rc.b[2];
   const T A11 = rc.nb1 * rc.nb1, A12 = b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2];
   const T A22 = b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2];
-  const T det = rc.cr * rc.cr;
-  const T gam0 = (A22 * gx1 - A12 * gx2) / det;
-  const T gam1 = (A11 * gx2 - A12 * gx1) / det;
+  const T idet = m_div((T)1, rc.cr * rc.cr);
+  const T gam0 = (A22 * gx1 - A12 * gx2) * idet;
+  const T gam1 = (A11 * gx2 - A12 * gx1) * idet;
   const T m3 = gg.m[2];
   const T kp0 = rc.kappa[0], kp1 = rc.kappa[1];
   const T gm1 = gx1, gm2 = gx2;
@@ -565,7 +566,7 @@ __device__ __forceinline__ void record_param_grad(const ChainOut<T>& o, const Fa
       T sacc = 0;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        gR[k][a] = o.gF[k][a] / f.s[a];
+        gR[k][a] = m_div(o.gF[k][a], f.s[a]);
         sacc += o.gF[k][a] * f.F[k][a];
       }
       out[3 + a] = (float)(-sacc);
@@ -580,7 +581,7 @@ __device__ __forceinline__ void record_param_grad(const ChainOut<T>& o, const Fa
     const T gz = 2 * (-2 * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] -
                       2 * z * gR[1][1] + y * gR[1][2] + x * gR[2][0] + y * gR[2][1]);
     const T dot = gw * w + gx * x + gy * y + gz * z;
-    const T inv = 1 / f.qnorm;
+    const T inv = m_div((T)1, f.qnorm);
     out[6] = (float)((gw - w * dot) * inv);
     out[7] = (float)((gx - x * dot) * inv);
     out[8] = (float)((gy - y * dot) * inv);

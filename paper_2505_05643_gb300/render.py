@@ -21,12 +21,13 @@ ROWS = {B.UG_COV_TRI: 11, B.UG_COV_SCALE_ROT: 12}
 
 
 def make_config(cov_param: int = B.UG_COV_TRI, cutoff: int = B.UG_CUTOFF_BOX, tile: int = 16,
-                variant: int = 0, **kw) -> B.ug_config:
+                variant: int = 0, variant_bwd: int | None = None, **kw) -> B.ug_config:
     cfg = B.ug_config_default()
     cfg.cov_param = cov_param
     cfg.cutoff = cutoff
     cfg.tile = tile
     cfg.variant = variant
+    cfg.variant_bwd = variant if variant_bwd is None else variant_bwd
     for k, v in kw.items():
         setattr(cfg, k, v)
     return cfg
@@ -140,7 +141,7 @@ class Renderer:
         st = B.ug_ws_status.from_buffer_copy(self._status.numpy().tobytes())
         return dict(status=st.status, detail=st.detail, records=st.records,
                     instances=st.instances, fp64_records=st.fp64_records,
-                    box_pixels=st.box_pixels)
+                    box_pixels=st.box_pixels, evaluated_pairs=st.evaluated_pairs)
 
     def preprocess(self, params: torch.Tensor, check: bool = True, stream=None):
         assert params.shape == (self.rows, self.n) and params.dtype == torch.float32

@@ -65,9 +65,11 @@ class TrainStep:
 
     def kernels_per_step(self) -> int:
         """Kernels of this library launched by one step (memsets excluded)."""
-        pre = 7                                  # planes, count, 3 scan, emit, finish
+        # preprocess: planes, cull, 3 scan, list, 2 records, 3 scan, emit, finish
+        pre = 13
         sort = 5 * int(self.r.plan.sort_passes) + 1  # per pass: hist, 3 scan, scatter; ranges
-        return pre + sort + 1 + 2 + 3 + 2        # render, mse (2), backward (3), adam (2)
+        # render 1, mse 2, backward: zero, raster, 2 chain, gather = 5, adam 2
+        return pre + sort + 1 + 2 + 5 + 2
 
     def ensure_capacity(self):
         """Run one checked forward so the workspace holds this step's records."""
