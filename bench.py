@@ -75,13 +75,15 @@ def _clock_summary(path: str) -> dict:
 
 
 def _workload(n_override=None):
+    """The model (seed 0) and a hidden volume of the same distribution (seed 1)
+    whose rendering on the same planes is the training target."""
     from paper_2505_05643_gb300 import synth
-    g, pl = synth.workload_aniso_1m()
+    g, pl = synth.workload_aniso_1m(seed=0)
+    hidden, _ = synth.workload_aniso_1m(seed=1)
     if n_override:
         g = {k: v[..., :n_override] for k, v in g.items()}
-    g = synth.scale_rot_to_tri(g, 1e-4)
-    target = synth.target_images(np.random.default_rng(7), pl["total_pixels"])
-    return g, pl, target
+        hidden = {k: v[..., :n_override] for k, v in hidden.items()}
+    return synth.scale_rot_to_tri(g, 1e-4), pl, synth.scale_rot_to_tri(hidden, 1e-4)
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -109,27 +111,26 @@ def run_reference(args):
         return 0
     g, pl, _ = _workload()
     sizes = pl["size"][:, 0]
-    smallest = [int(np.argmin(sizes))]
-    # each step: the oracle's forward + backward over the smallest plane (all 1M Gaussians)
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm state; warm-up steps are not needed for a CPU program
-    rates, secs = [], []
-    cores = 1
-    pairs = 0
-    for _ in range(args.steps):
-        rate, dt, cores, pairs = cpu_oracle_rate(g, pl, smallest)
+    # each step: the oracle's forward + backward over 4 of the 64 planes (all 1M
+    # Gaussians), a different 4 each step; the oracle has no warm state
+    rates, secs, cores, total_pairs = [], [], 1, 0
+    for k in range(args.steps):
+        sample = [(4 * k + j) % len(sizes) for j in range(4)]
+        rate, dt, cores, pairs = cpu_oracle_rate(g, pl, sample)
         rates.append(rate)
         secs.append(dt)
-    value = float(np.mean(rates))
+        total_pairs += pairs
+    value = float(total_pairs / np.sum(secs))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"plane {smallest[0]} ({sizes[smallest[0]]}^2) of 64"},
+        "config": {"workload": WORKLOAD, "sample": "4 of the 64 planes per step"},
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-                         "sample": f"FP64 oracle scatter forward + analytic backward, 1 of 64 planes "
-                                   f"({sizes[smallest[0]]}^2, {pairs} pairs), all 1,000,000 Gaussians"},
+                         "sample": "FP64 oracle scatter forward + analytic backward on 4 of 64 planes "
+                                   "per step (planes rotate), all 1,000,000 Gaussians, "
+                                   f"{total_pairs} pairs in {np.sum(secs):.1f} s"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -157,26 +158,60 @@ def run_ours(args):
         pass
 
     # every rank trains its own replica of the workload (weak scaling, no collective)
-    g, pl, target = _workload(args.n)
+    g, pl, hidden = _workload(args.n)
     cfg = R.make_config(cov_param=B.UG_COV_TRI, cutoff=B.UG_CUTOFF_BOX, tile=args.tile,
                         variant=args.variant, variant_bwd=args.variant_bwd)
     n = len(g["logit"])
+    # training data: the hidden volume rendered on the same planes (untimed)
+    hid = R.Renderer(len(hidden["logit"]), pl, cfg)
+    targets, _ = hid.forward(torch.from_numpy(R.pack_params(hidden, B.UG_COV_TRI)).to(dev))
+    targets = targets.clone()
+    target = targets.cpu().numpy()
+    del hid
     renderer = R.Renderer(n, pl, cfg)
+    r = renderer
     params = torch.from_numpy(R.pack_params(g, B.UG_COV_TRI)).to(dev)
-    targets = torch.from_numpy(target).to(dev)
     step = T.TrainStep(renderer, params, targets)
-    # size the workspace with margin for the drift of a few hundred steps
-    st0 = renderer.preprocess(params, check=True)
-    rec = int(st0["records"] * 1.3) + 4096
-    inst = min(int(st0["instances"] * 1.3) + 65536, (1 << 31) - 1)
-    renderer._alloc(rec, inst)
-    step.g_struct = R.gaussians_struct(params, B.UG_COV_TRI)
     s = torch.cuda.Stream(device=dev)
+    st_dev = torch.zeros(64, dtype=torch.uint8, device=dev)
+
+    # Every measured phase starts from the same state and runs W + K steps, so
+    # the parameters (and with them the record counts) follow the same path.
+    state0 = [t.clone() for t in (step.params, step.m, step.v, step.step)]
+
+    def restore():
+        for dst, src in zip((step.params, step.m, step.v, step.step), state0):
+            dst.copy_(src)
+        torch.cuda.synchronize()
+
+    def read_status():
+        B.ug_read_status(r.plan, r.ws, st_dev, s)
+        s.synchronize()
+        return B.ug_ws_status.from_buffer_copy(st_dev.cpu().numpy().tobytes())
+
+    # sizing run: W + K checked eager steps; grow the workspace until none overflows
+    st0 = renderer.preprocess(params, check=True)
+    need_rec, need_inst = st0["records"], st0["instances"]
+    for attempt in range(6):
+        rec = int(need_rec * 1.15) + 4096
+        inst = min(int(need_inst * 1.15) + 65536, (1 << 31) - 1)
+        renderer._alloc(rec, inst)
+        step.g_struct = R.gaussians_struct(params, B.UG_COV_TRI)
+        restore()
+        ok = True
+        with torch.cuda.stream(s):
+            for k in range(args.warmup + args.steps):
+                step.enqueue(s)
+                x = read_status()
+                need_rec = max(need_rec, x.records)
+                need_inst = max(need_inst, x.instances)
+                if x.status != 0:
+                    ok = False
+                    break
+        if ok:
+            break
+    restore()
     s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):
-        for _ in range(2):
-            step.enqueue(s)
-    s.synchronize()
     graph = step.capture(s)
     status_log = torch.zeros((args.warmup + args.steps, 64), dtype=torch.uint8, device=dev)
 
@@ -184,14 +219,11 @@ def run_ours(args):
         graph.replay()
         B.ug_read_status(renderer.plan, renderer.ws, status_log[k], s)
 
+    # ---- timed region: K replays of the captured step after W warm-up replays
     with torch.cuda.stream(s):
         for k in range(args.warmup):
             one(k)
     s.synchronize()
-    # phase timing of the dominant kernel: events around ug_render_backward in an
-    # eager copy of the step on the same stream (the graph replays the same launches)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-
     clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
                             f".bench_clocks_{rank}.csv")
     sampler, fh = _clock_sampler(dev.index or 0, clk_path)
@@ -206,12 +238,30 @@ def run_ours(args):
     stop.record(s)
     torch.cuda.synchronize()
     total_ms = start.elapsed_time(stop)
-    # the dominant kernel's duration, on the launching stream, over K eager steps
-    bwd_ms, fwd_ms = [], []
+    if sampler is not None:
+        sampler.terminate()
+        sampler.wait()
+        fh.close()
+    clocks = _clock_summary(clk_path)
+    ms_step = total_ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    sts = [B.ug_ws_status.from_buffer_copy(row.tobytes()) for row in status_log.cpu().numpy()]
+    bad = [x.status for x in sts if x.status != 0]
+    if bad:
+        raise RuntimeError(f"device status {bad[0]} during the timed steps")
+    pairs = float(np.mean([x.box_pixels for x in sts[args.warmup:]]))
+    value = pairs * world / (ms_step * 1e-3)
+
+    # ---- phase timing: the same W + K steps eagerly, CUDA events on the
+    # launching stream around ug_render and ug_render_backward
+    restore()
+    bwd_ms, fwd_ms, eager_st = [], [], []
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    r = renderer
     with torch.cuda.stream(s):
-        for k in range(args.steps):
+        for k in range(args.warmup + args.steps):
             B.ug_preprocess(r.plan, step.g_struct, r.d_planes, r.ws, s)
             B.ug_bin_sort(r.plan, r.ws, s)
             e[0].record(s)
@@ -225,46 +275,42 @@ def run_ours(args):
             e[3].record(s)
             B.ug_adam_step(step.params, step.grads, step.m, step.v, r.rows, r.n, step.lr_rows,
                            step.step, T.BETA1, T.BETA2, T.EPS, s)
-            s.synchronize()
-            fwd_ms.append(e[0].elapsed_time(e[1]))
-            bwd_ms.append(e[2].elapsed_time(e[3]))
-    if sampler is not None:
-        sampler.terminate()
-        sampler.wait()
-        fh.close()
-    clocks = _clock_summary(clk_path)
-    ms_step = total_ms / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
-    logs = status_log.cpu().numpy()
-    sts = [B.ug_ws_status.from_buffer_copy(row.tobytes()) for row in logs]
-    bad = [x.status for x in sts if x.status != 0]
-    if bad:
-        raise RuntimeError(f"device status {bad[0]} during the timed steps")
-    pairs = float(np.mean([x.box_pixels for x in sts[args.warmup:]]))
-    value = pairs * world / (ms_step * 1e-3)
+            x = read_status()
+            if k >= args.warmup:
+                eager_st.append(x)
+                fwd_ms.append(e[0].elapsed_time(e[1]))
+                bwd_ms.append(e[2].elapsed_time(e[3]))
+    if any(x.status != 0 for x in eager_st):
+        raise RuntimeError("device status error in the phase-timing steps")
 
     # ---- e2e: the public API with host buffers; the step's inputs (targets and
     # plane poses) copied from pinned host memory and the loss read back each step
+    restore()
     h_targets = torch.from_numpy(target).pin_memory()
     h_planes = torch.from_numpy(r.host_planes.view(np.uint8).copy()).pin_memory()
     h_loss = torch.zeros(1, dtype=torch.float32).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_steps = max(3, min(args.steps, 10))
     with torch.cuda.stream(s):
-        for k in range(e2e_steps):
+        for k in range(args.warmup):
+            step.enqueue(s)
+    s.synchronize()
+    e2e_st = []
+    t0 = time.perf_counter()
+    with torch.cuda.stream(s):
+        for k in range(args.steps):
             step.targets.copy_(h_targets, non_blocking=True)
             r.d_planes.copy_(h_planes, non_blocking=True)
             step.enqueue(s)
             h_loss.copy_(step.loss[:1], non_blocking=True)
+            B.ug_read_status(r.plan, r.ws, st_dev, s)
             s.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": pairs * world / e2e_s, "unit": "pairs/s",
+            e2e_st.append(B.ug_ws_status.from_buffer_copy(st_dev.cpu().numpy().tobytes()))
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if any(x.status != 0 for x in e2e_st):
+        raise RuntimeError("device status error in the end-to-end steps")
+    e2e_pairs = float(np.mean([x.box_pixels for x in e2e_st]))
+    e2e = {"value": e2e_pairs * world / e2e_s, "unit": "pairs/s",
            "h2d_bytes_per_step": int(h_targets.numel() * 4 + h_planes.numel()),
-           "d2h_bytes_per_step": 4}
+           "d2h_bytes_per_step": 4 + 64}
 
     # ---- roofline of the dominant kernel (backward rasterizer, FP32-pipe bound)
     # Unit: one evaluated (pixel, record) pair. Algorithmic FP32-pipe operations
@@ -274,9 +320,10 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     fp32_peak = sms * 128 * fmax
-    bwd_s = float(np.median(bwd_ms)) * 1e-3
-    fwd_s = float(np.median(fwd_ms)) * 1e-3
-    evaluated = float(np.mean([x.evaluated_pairs for x in sts[args.warmup:]]))
+    bwd_s = float(np.mean(bwd_ms)) * 1e-3
+    fwd_s = float(np.mean(fwd_ms)) * 1e-3
+    evaluated = float(np.mean([x.evaluated_pairs for x in eager_st]))
+    pairs_eager = float(np.mean([x.box_pixels for x in eager_st]))
     roof = {"bound": "alu", "kernel": "ug_render_backward (k_render_bwd + chain + gather)",
             "achieved": 16.0 * evaluated / bwd_s / 1e12, "peak": fp32_peak / 1e12,
             "unit": "Tops/s (FP32 pipe)", "frac": 16.0 * evaluated / bwd_s / fp32_peak,
@@ -286,18 +333,18 @@ def run_ours(args):
             "fwd": {"kernel": "ug_render (k_render_fwd)", "ms": fwd_s * 1e3,
                     "achieved": 6.0 * evaluated / fwd_s / 1e12,
                     "frac": 6.0 * evaluated / fwd_s / fp32_peak},
-            "bwd_ms": bwd_s * 1e3, "box_pairs_per_launch": pairs,
-            "evaluated_over_box_pairs": evaluated / pairs}
+            "bwd_ms": bwd_s * 1e3, "box_pairs_per_launch": pairs_eager,
+            "evaluated_over_box_pairs": evaluated / pairs_eager}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         sizes = pl["size"][:, 0]
-        sample = list(range(args.cpu_planes))
+        sample = list(range(min(args.cpu_planes, len(sizes))))
         rate, dt, cores, cp = cpu_oracle_rate(g, pl, sample)
         cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                "sample": f"FP64 oracle scatter forward + analytic backward on planes "
-                         f"0..{len(sample) - 1} (sizes {[int(x) for x in sizes[sample]]}; "
-                         f"{cp} pairs) with all {n} Gaussians, {dt:.1f} s"}
+                         f"0..{len(sample) - 1} of 64 ({cp} pairs) with all {n} Gaussians "
+                         f"(initial parameters), {dt:.1f} s"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
@@ -308,6 +355,7 @@ def run_ours(args):
                        "pixels": int(pl["total_pixels"]), "pairs_per_step": pairs,
                        "tile": args.tile, "variant": args.variant,
                        "variant_bwd": args.variant_bwd, "graph": True,
+                       "targets": "hidden 1M-Gaussian volume (seed 1) rendered on the same planes",
                        "l2": "working set > L2 (129 MB); no flush",
                        "parallelism": f"replicas x{world}"},
             "steps_per_s": 1e3 / ms_step,
@@ -331,7 +379,7 @@ def main():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--variant", type=int, default=0, help="forward rasterizer variant")
     ap.add_argument("--variant-bwd", type=int, default=3, help="backward rasterizer variant")
-    ap.add_argument("--cpu-planes", type=int, default=6, help="planes in the CPU oracle sample")
+    ap.add_argument("--cpu-planes", type=int, default=24, help="planes in the CPU oracle sample")
     ap.add_argument("--n", type=int, default=None, help="use the first n Gaussians (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()
