@@ -52,8 +52,9 @@ struct WsHeader {
   uint32_t tile_counter[2];   // persistent-kernel work queues (forward, backward)
   uint32_t slots, slots64;    // record slots and FP64 list entries of the last preprocess
   unsigned long long box_pixels;
-  uint32_t holes;             // FP64 candidates rejected by the exact test
-  uint32_t pad1[41];
+  uint32_t holes;             // candidates rejected by the exact test (empty slots)
+  uint32_t kept64;            // visible records of the FP64 list
+  uint32_t pad1[40];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 

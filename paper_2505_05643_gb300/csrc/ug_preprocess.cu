@@ -4,21 +4,19 @@
 //
 // Record-parallel pipeline (every heavy kernel runs with full warps):
 //  1. cull     one warp per chunk of 32 consecutive Gaussians (coalesced
-//              structure-of-arrays loads) walks all planes and sets one
-//              candidate bit per (plane, Gaussian): the phase-1 test and a
-//              non-empty pixel box in FP32 for ordinary Gaussians; for
-//              Gaussians whose axis-ratio proxy exceeds fp64_ratio an FP32
-//              test with a rigorous rounding bound that only drops pairs the
-//              FP64 test would drop too.
+//              structure-of-arrays loads) walks all planes (staged in shared
+//              memory) and sets one candidate bit per (plane, Gaussian) with a
+//              conservative FP32 test that carries a rigorous rounding bound:
+//              it only drops pairs that the exact test would drop too.
 //  2. scan     of the candidate counts in (chunk, plane) order: every
 //              candidate gets its record slot, so for any plane the records,
 //              and after the stable sort the tile lists, are in ascending
 //              Gaussian order.
 //  3. list     writes the candidates into a work list, FP32 part first, then
 //              the FP64 part.
-//  4. records  one thread per list entry: FP32 or FP64 geometry (phase 1, box,
-//              in-plane conic, peak weight) and the record; FP64 candidates
-//              that the exact test rejects become empty slots.
+//  4. records  one thread per list entry: the exact FP32 or FP64 geometry
+//              (phase 1, box, in-plane conic, peak weight) and the record;
+//              candidates that the exact test rejects become empty slots.
 //  5. scan     of the records' tile counts, then emit the (tile, record)
 //              instances, one thread per record.
 // The backward chain is one thread per record (per-record parameter
@@ -62,6 +60,7 @@ __global__ void __launch_bounds__(256)
     h->slots64 = 0;
     h->box_pixels = 0;
     h->holes = 0;
+    h->kept64 = 0;
     s_run = 0;
   }
   __syncthreads();
@@ -129,58 +128,51 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------------------ 1. cull
-// Certified FP32 phase-1 and image-overlap test for an ill-conditioned
-// Gaussian. Fi is the FP64 inverse factor rounded to FP32; rs[i] = sum_k
-// |Fi_ik| and R2 = sum_i rs[i]^2. For z = Fi r with |r_k| <= 1 computed in
-// FP32 (rounded Fi, rounded r from u x v, three-term FMA dot):
-//   |z_i - z_i*| <= 5 eps rs[i],  |S - S*| <= 10 eps sqrt(S R2) + 25 eps^2 R2 + 3 eps S
-// (eps = 2^-24); the probe-frame mean has |m - m*| <= 8 eps sum_k |mu_k - o_k|.
-// Returns false only when the pair is outside the chi^2 box on the plane or
-// its box misses the image for every value inside these bounds.
-struct CertGauss {
+// A conservative FP32 test per (plane, Gaussian), the same arithmetic for every
+// lane (no sqrt, no divergent branch): it keeps every pair that the exact
+// test in the record kernels can accept, and drops the rest.
+//   phase 1:  (|m3| - Bm)^2 <= chi2 (S33 + B33) (1 + 2e-3)
+//   image:    the pixel box with half-extent sqrt(chi2) ||Fi||_F >= sqrt(chi2
+//             Sigma3D_kk) (plus one pixel) overlaps the image.
+// Fi is the inverse factor (FP64-computed and rounded for ill-conditioned
+// Gaussians). With z = Fi r computed in FP32 (|r_k| <= 1), rs[i] = sum_k
+// |Fi_ik| and R2 = sum_i rs[i]^2:
+//   |z_i - z_i*| <= 5 eps rs[i],  |S - S*| <= 10 eps sqrt(S R2) + 25 eps^2 R2 + 3 eps S,
+//   |m - m*| <= 8 eps sum_k |mu_k - o_k|   (eps = 2^-24);
+// the factor 1 + 2e-3 also covers the FP32 forward substitution of ordinary
+// Gaussians (axis-ratio proxy <= fp64_ratio).
+struct CullGauss {
   float mu[3];
   float Fi[3][3];
   float R2;
+  float hb;  // sqrt(chi2) ||Fi||_F: bound of every half-extent
 };
 
-__device__ __forceinline__ float cert_S(const CertGauss& c, const float r[3], float& bound) {
-  const float eps = 5.9604645e-8f;
-  float S = 0.f;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const float z = fmaf(c.Fi[i][2], r[2], fmaf(c.Fi[i][1], r[1], c.Fi[i][0] * r[0]));
-    S = fmaf(z, z, S);
-  }
-  bound = 10.f * eps * sqrtf(S * c.R2) + 25.f * eps * eps * c.R2 + 3.f * eps * S;
-  bound = bound * 1.001f + 1e-37f;
-  return S;
-}
-
-__device__ bool cert_candidate(const CertGauss& c, const PlaneDev& pl, float chi2) {
+__device__ __forceinline__ bool cull_pair(const CullGauss& c, const PlaneDev& pl, float chi2) {
   const float eps = 5.9604645e-8f;
   float d[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) d[k] = c.mu[k] - pl.o[k];
   const float Bm = 8.f * eps * (fabsf(d[0]) + fabsf(d[1]) + fabsf(d[2])) * 1.001f + 1e-30f;
   const float m3 = fmaf(pl.n[2], d[2], fmaf(pl.n[1], d[1], pl.n[0] * d[0]));
-  float B33;
-  const float S33 = cert_S(c, pl.n, B33);
+  float S = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float z = fmaf(c.Fi[i][2], pl.n[2], fmaf(c.Fi[i][1], pl.n[1], c.Fi[i][0] * pl.n[0]));
+    S = fmaf(z, z, S);
+  }
+  // sqrt(S R2) <= (S + R2) / 2 keeps the bound free of a square root
+  const float B = 5.f * eps * (S + c.R2) + 25.f * eps * eps * c.R2 + 3.f * eps * S;
   const float lo = fmaxf(fabsf(m3) - Bm, 0.f);
-  if (lo * lo > chi2 * (S33 + B33) * 1.0001f) return false;  // certainly rejected by phase 1
-  // the box must reach the image in both directions (one pixel of slack)
+  const bool ph1 = lo * lo <= chi2 * (S + B) * 1.002f;
   const float m1 = fmaf(pl.u[2], d[2], fmaf(pl.u[1], d[1], pl.u[0] * d[0]));
   const float m2 = fmaf(pl.v[2], d[2], fmaf(pl.v[1], d[1], pl.v[0] * d[0]));
-  float B11, B22;
-  const float S11 = cert_S(c, pl.u, B11);
-  const float S22 = cert_S(c, pl.v, B22);
-  const float h1 = sqrtf(chi2 * (S11 + B11)) * 1.0001f + Bm;
-  const float h2 = sqrtf(chi2 * (S22 + B22)) * 1.0001f + Bm;
-  const float jlo = (m1 - h1) * pl.inv_pu + pl.jshift - 1.f;
-  const float jhi = (m1 + h1) * pl.inv_pu + pl.jshift + 1.f;
-  const float ilo = (m2 - h2) * pl.inv_pv + pl.ishift - 1.f;
-  const float ihi = (m2 + h2) * pl.inv_pv + pl.ishift + 1.f;
-  if (jhi < 0.f || jlo > (float)(pl.w - 1) || ihi < 0.f || ilo > (float)(pl.h - 1)) return false;
-  return true;
+  const float h = c.hb + Bm;
+  const float cj = fmaf(m1, pl.inv_pu, pl.jshift), hj = fmaf(h, pl.inv_pu, 1.f);
+  const float ci = fmaf(m2, pl.inv_pv, pl.ishift), hi = fmaf(h, pl.inv_pv, 1.f);
+  const bool img = cj + hj >= 0.f && cj - hj <= (float)(pl.w - 1) && ci + hi >= 0.f &&
+                   ci - hi <= (float)(pl.h - 1);
+  return ph1 && img;
 }
 
 struct LaneGauss {
@@ -200,49 +192,68 @@ __device__ __forceinline__ void lane_setup(const ug_gaussians& g, int64_t n, int
   L.use64 = !(axis_ratio_proxy<COV>(L.ff) <= ratio);
 }
 
+constexpr int kCullPlanesSmem = 64;  // planes staged in shared memory per pass
+
 template <int COV>
 __global__ void __launch_bounds__(256)
     k_cull(ug_gaussians g, int64_t n, int P, float chi2, float beta, float ratio, int64_t chunks,
            WsView v) {
+  __shared__ PlaneDev s_pl[kCullPlanesSmem];
   if (dev_failed(v.hdr)) return;
   const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (chunk >= chunks) return;
   const int lane = threadIdx.x & 31;
+  const bool live_warp = chunk < chunks;
   LaneGauss L;
-  lane_setup<COV>(g, n, chunk * kChunk + lane, beta, ratio, L);
-  CertGauss cg;
-  if (L.use64) {
-    Factor<double> fd;
-    make_factor<double, COV>(L.prm, beta, fd);
-    float R2 = 0.f;
+  L.active = false;
+  L.use64 = false;
+  if (live_warp) lane_setup<COV>(g, n, chunk * kChunk + lane, beta, ratio, L);
+  CullGauss cg;
+  {
+    float Fi[3][3];
+    if (L.use64) {
+      Factor<double> fd;
+      make_factor<double, COV>(L.prm, beta, fd);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Fi[i][k] = (float)fd.Fi[i][k];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Fi[i][k] = L.active ? L.ff.Fi[i][k] : 0.f;
+    }
+    float R2 = 0.f, fro = 0.f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      cg.mu[i] = L.prm.mu[i];
+      cg.mu[i] = L.active ? L.prm.mu[i] : 0.f;
       float rs = 0.f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        cg.Fi[i][k] = (float)fd.Fi[i][k];
-        rs += fabsf(cg.Fi[i][k]);
+        cg.Fi[i][k] = Fi[i][k];
+        rs += fabsf(Fi[i][k]);
+        fro = fmaf(Fi[i][k], Fi[i][k], fro);
       }
       R2 = fmaf(rs, rs, R2);
     }
     cg.R2 = R2 * 1.001f;
+    cg.hb = sqrtf(chi2 * fro) * 1.001f;
   }
-  const uint32_t fl = __ballot_sync(0xffffffffu, L.use64);
-  if (lane == 0) v.gflag[chunk] = fl;
-  for (int p = 0; p < P; ++p) {
-    const PlaneDev pl = v.planes[p];
-    bool cand = false;
-    if (L.active) {
-      if (L.use64) {
-        cand = cert_candidate(cg, pl, chi2);
-      } else {
-        PairGeo<float> gg;
-        cand = pair_box<float, COV>(L.ff, pl, chi2, gg).visible;
-      }
+  if (live_warp) {
+    const uint32_t fl = __ballot_sync(0xffffffffu, L.use64);
+    if (lane == 0) v.gflag[chunk] = fl;
+  }
+  for (int p0 = 0; p0 < P; p0 += kCullPlanesSmem) {
+    const int np = min(kCullPlanesSmem, P - p0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < np; q += blockDim.x) s_pl[q] = v.planes[p0 + q];
+    __syncthreads();
+    if (!live_warp) continue;
+    for (int q = 0; q < np; ++q) {
+      const bool cand = L.active && cull_pair(cg, s_pl[q], chi2);
+      const uint32_t mask = __ballot_sync(0xffffffffu, cand);
+      if (lane == 0) v.mask[chunk * P + p0 + q] = mask;
     }
-    const uint32_t mask = __ballot_sync(0xffffffffu, cand);
-    if (lane == 0) v.mask[chunk * P + p] = mask;
   }
 }
 
@@ -321,7 +332,7 @@ __global__ void __launch_bounds__(256)
   const uint32_t begin = part == 0 ? 0u : slots - n64;
   const uint32_t end = part == 0 ? slots - n64 : slots;
   unsigned long long npx = 0;
-  uint32_t holes = 0;
+  uint32_t holes = 0, kept = 0;
   for (uint32_t k = begin + blockIdx.x * blockDim.x + threadIdx.x; k < end;
        k += gridDim.x * blockDim.x) {
     const uint4 e = v.list[k];
@@ -340,18 +351,20 @@ __global__ void __launch_bounds__(256)
       write_record<T>(rc, pl, pb, prm, chi2, v, slot);
       v.inst_off[slot] = tile_count(pb, ts);
       npx += (unsigned long long)(pb.j1 - pb.j0 + 1) * (unsigned long long)(pb.i1 - pb.i0 + 1);
+      kept++;
     } else {
       v.rec_box[slot] = make_uint2(1u, 1u);  // empty: j0 = 1 > j1 = 0
       v.inst_off[slot] = 0u;
       holes++;
-      if (part == 0) dev_fail(v.hdr, UG_ERR_INTERNAL, 1);  // FP32 decisions are repeated exactly
     }
   }
   npx = warp_sum(npx);
   holes = warp_sum(holes);
+  kept = warp_sum(kept);
   if ((threadIdx.x & 31) == 0) {
     if (npx) atomicAdd(&v.hdr->box_pixels, npx);
     if (holes) atomicAdd(&v.hdr->holes, holes);
+    if (part == 1 && kept) atomicAdd(&v.hdr->kept64, kept);
   }
 }
 
@@ -397,7 +410,7 @@ __global__ void __launch_bounds__(256) k_emit(int ts, uint32_t inst_cap, WsView 
 
 __global__ void k_finish_pre(WsView v) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    v.hdr->st.fp64_records = (int64_t)v.hdr->slots64 - (int64_t)v.hdr->holes;
+    v.hdr->st.fp64_records = (int64_t)v.hdr->kept64;
     v.hdr->st.box_pixels = (int64_t)v.hdr->box_pixels;
   }
 }

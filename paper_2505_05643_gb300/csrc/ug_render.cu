@@ -394,8 +394,8 @@ struct Variant {
 };
 
 // Variant tables. Tile 16: 0 = 8x8 footprints (2 px/lane), 1 = 16x4 (2 px/lane),
-// 2 = 8x16 (4 px/lane), 3 = 16x8 (4 px/lane). Tile 8: 0 = 8x8 (2 px/lane),
-// 1 = 8x4 (1 px/lane).
+// 2 = 8x16 (4 px/lane), 3 = 16x8 (4 px/lane), 4 = one warp per tile (8 px/lane).
+// Tile 8: 0 = 8x8 (2 px/lane), 1 = 8x4 (1 px/lane).
 template <int CUT>
 static cudaError_t dispatch_fwd(const ug_plan* plan, WsView v, const uint32_t* vals, float* image,
                                 float* alpha, cudaStream_t s) {
@@ -405,7 +405,8 @@ static cudaError_t dispatch_fwd(const ug_plan* plan, WsView v, const uint32_t* v
       case 0: return Variant<16, 8, 2>::fwd<CUT>(plan, v, vals, image, alpha, s);
       case 1: return Variant<16, 16, 2>::fwd<CUT>(plan, v, vals, image, alpha, s);
       case 2: return Variant<16, 8, 4>::fwd<CUT>(plan, v, vals, image, alpha, s);
-      default: return Variant<16, 16, 4>::fwd<CUT>(plan, v, vals, image, alpha, s);
+      case 3: return Variant<16, 16, 4>::fwd<CUT>(plan, v, vals, image, alpha, s);
+      default: return Variant<16, 16, 8>::fwd<CUT>(plan, v, vals, image, alpha, s);
     }
   }
   switch (var) {
@@ -424,7 +425,8 @@ static cudaError_t dispatch_bwd(const ug_plan* plan, WsView v, const uint32_t* v
       case 0: return Variant<16, 8, 2>::bwd<CUT>(plan, v, vals, image, alpha, grad, s);
       case 1: return Variant<16, 16, 2>::bwd<CUT>(plan, v, vals, image, alpha, grad, s);
       case 2: return Variant<16, 8, 4>::bwd<CUT>(plan, v, vals, image, alpha, grad, s);
-      default: return Variant<16, 16, 4>::bwd<CUT>(plan, v, vals, image, alpha, grad, s);
+      case 3: return Variant<16, 16, 4>::bwd<CUT>(plan, v, vals, image, alpha, grad, s);
+      default: return Variant<16, 16, 8>::bwd<CUT>(plan, v, vals, image, alpha, grad, s);
     }
   }
   switch (var) {
@@ -433,7 +435,7 @@ static cudaError_t dispatch_bwd(const ug_plan* plan, WsView v, const uint32_t* v
   }
 }
 
-int num_render_variants(int tile) { return tile == 16 ? 4 : (tile == 8 ? 2 : 0); }
+int num_render_variants(int tile) { return tile == 16 ? 5 : (tile == 8 ? 2 : 0); }
 
 cudaError_t launch_render(const ug_plan* plan, WsView v, float* image, float* alpha,
                           cudaStream_t s) {

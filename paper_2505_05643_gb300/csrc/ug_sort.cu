@@ -41,18 +41,24 @@ __global__ void __launch_bounds__(kSortThreads)
   if (base >= n) return;
   const int tid = threadIdx.x, warp = tid >> 5;
   gb[tid] = v.sort_hist[(int64_t)tid * nblk + blockIdx.x];
+  // all of the block's keys and values are loaded up front, so the ranking
+  // rounds below do not wait on memory
+  uint32_t kreg[kSortItems], vreg[kSortItems];
+#pragma unroll
+  for (int round = 0; round < kSortItems; ++round) {
+    const int64_t i = base + (int64_t)round * kSortThreads + tid;
+    kreg[round] = i < n ? __ldg(keys_in + i) : 0u;
+    vreg[round] = i < n ? __ldg(vals_in + i) : 0u;
+  }
+#pragma unroll
   for (int round = 0; round < kSortItems; ++round) {
     const int64_t i = base + (int64_t)round * kSortThreads + tid;
 #pragma unroll
     for (int w = 0; w < NW; ++w) cnt[w][tid] = 0;
     __syncthreads();
     const bool valid = i < n;
-    uint32_t key = 0, val = 0, d = 256;
-    if (valid) {
-      key = __ldg(keys_in + i);
-      val = __ldg(vals_in + i);
-      d = (key >> shift) & 0xffu;
-    }
+    const uint32_t key = kreg[round], val = vreg[round];
+    const uint32_t d = valid ? (key >> shift) & 0xffu : 256u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t rank = __popc(peers & lanemask_lt());
     if (valid && rank == 0) cnt[warp][d] = __popc(peers);

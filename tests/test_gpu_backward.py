@@ -80,7 +80,18 @@ def test_grad_small_scene(cov_param, cutoff):
     _check_grads(gpu, gref, gabs, oracle.param_names(cov_param), f"small cov{cov_param} cut{cutoff}")
 
 
-@pytest.mark.parametrize("tile,variant", [(16, 1), (16, 2), (16, 3), (8, 0), (8, 1)])
+def test_grad_fp64_branch():
+    """Triangular front-end with every Gaussian on the FP64 branch."""
+    rng = np.random.default_rng(35)
+    g = synth.scale_rot_to_tri(synth.gaussians_scale_rot(rng, 1200, 0.03, 0.15), 1e-4)
+    pl = synth.planes_random(rng, [(64, 64), (48, 40)])
+    target = rng.uniform(0, 1, pl["total_pixels"])
+    cfg = R.make_config(cov_param=B.UG_COV_TRI, fp64_ratio=1.0)
+    gpu, gref, gabs, _ = _backward_case(g, pl, cfg, target)
+    _check_grads(gpu, gref, gabs, oracle.param_names(0), "fp64 branch")
+
+
+@pytest.mark.parametrize("tile,variant", [(16, 1), (16, 2), (16, 3), (16, 4), (8, 0), (8, 1)])
 def test_grad_variants(tile, variant):
     rng = np.random.default_rng(32)
     g = synth.gaussians_scale_rot(rng, 1000, 0.03, 0.15)
