@@ -37,6 +37,22 @@ __device__ __forceinline__ double m_div(double a, double b) {
 }
 __device__ __forceinline__ double m_sqrt(double a) { return (double)__fsqrt_rn((float)a); }
 
+// FP64-accurate reciprocal and reciprocal square root from an FP32 seed and
+// two Newton steps in FP64 (relative error ~1e-16; FP64 division and square
+// root take far longer on GB300). Only for arguments in the FP32 normal range.
+__device__ __forceinline__ double rcp64(double x) {
+  double r = (double)__frcp_rn((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+__device__ __forceinline__ double rsqrt64(double x) {
+  double r = (double)rsqrtf((float)x);
+  r = r * fma(-0.5 * x, r * r, 1.5);
+  r = r * fma(-0.5 * x, r * r, 1.5);
+  return r;
+}
+
 template <typename T>
 __device__ __forceinline__ T r_dot3(const T a[3], const T b[3]) {
   return r_fma(a[2], b[2], r_fma(a[1], b[1], r_mul(a[0], b[0])));
@@ -98,9 +114,16 @@ __device__ __forceinline__ void make_factor(const GaussParams& p, float beta, Fa
     f.F[2][0] = t2;
     f.F[2][1] = t4;
     f.F[2][2] = r_fma(t5, t5, b);
-    const T i00 = r_div((T)1, f.F[0][0]);
-    const T i11 = r_div((T)1, f.F[1][1]);
-    const T i22 = r_div((T)1, f.F[2][2]);
+    T i00, i11, i22;
+    if (sizeof(T) == 8) {
+      i00 = (T)rcp64((double)f.F[0][0]);
+      i11 = (T)rcp64((double)f.F[1][1]);
+      i22 = (T)rcp64((double)f.F[2][2]);
+    } else {
+      i00 = r_div((T)1, f.F[0][0]);
+      i11 = r_div((T)1, f.F[1][1]);
+      i22 = r_div((T)1, f.F[2][2]);
+    }
     // L Fi = I column by column (forward substitution)
     const T i10 = -r_mul(r_mul(f.F[1][0], i00), i11);
     const T i21 = -r_mul(r_mul(f.F[2][1], i11), i22);
@@ -119,8 +142,22 @@ __device__ __forceinline__ void make_factor(const GaussParams& p, float beta, Fa
     f.qnorm = (T)1;
   } else {
     const T q0 = (T)p.cp[3], q1 = (T)p.cp[4], q2 = (T)p.cp[5], q3 = (T)p.cp[6];
-    const T nq = r_sqrt(r_fma(q3, q3, r_fma(q2, q2, r_fma(q1, q1, r_mul(q0, q0)))));
-    const T w = r_div(q0, nq), x = r_div(q1, nq), y = r_div(q2, nq), z = r_div(q3, nq);
+    const T nq2 = r_fma(q3, q3, r_fma(q2, q2, r_fma(q1, q1, r_mul(q0, q0))));
+    T nq, w, x, y, z;
+    if (sizeof(T) == 8) {
+      const T rq = (T)rsqrt64((double)nq2);
+      nq = nq2 * rq;
+      w = q0 * rq;
+      x = q1 * rq;
+      y = q2 * rq;
+      z = q3 * rq;
+    } else {
+      nq = r_sqrt(nq2);
+      w = r_div(q0, nq);
+      x = r_div(q1, nq);
+      y = r_div(q2, nq);
+      z = r_div(q3, nq);
+    }
     f.qn[0] = w;
     f.qn[1] = x;
     f.qn[2] = y;
@@ -136,16 +173,19 @@ __device__ __forceinline__ void make_factor(const GaussParams& p, float beta, Fa
     R[2][0] = (T)2 * r_fma(x, z, -r_mul(w, y));
     R[2][1] = (T)2 * r_fma(y, z, r_mul(w, x));
     R[2][2] = (T)1 - (T)2 * r_fma(x, x, r_mul(y, y));
+    // the scales only rescale the rows of R (no cancellation follows), so FP32
+    // exp and reciprocal are accurate enough for both branches
+    T sinv[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       f.s[a] = (T)expf(p.cp[a]);
-      if (sizeof(T) == 8) f.s[a] = (T)exp((double)p.cp[a]);
+      sinv[a] = (T)expf(-p.cp[a]);
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        f.F[k][a] = r_div(R[k][a], f.s[a]);
+        f.F[k][a] = r_mul(R[k][a], sinv[a]);
         f.Fi[a][k] = r_mul(f.s[a], R[k][a]);
       }
   }

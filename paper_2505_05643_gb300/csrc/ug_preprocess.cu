@@ -484,67 +484,77 @@ cudaError_t launch_preprocess(const ug_plan* plan, const ug_gaussians* g, WsView
 //   dL/dlw2 = ln2 [1];  dL/dr11 = -2 ln2 [4];  dL/dr12 = -2 ln2 [5];
 //   dL/dr22 = -2 ln2 [6];  dL/dxs_j = 2 ln2 r11 [2];
 //   dL/dxs_i = 2 ln2 (r12 [2] + r22 [3]).
-template <typename T>
 struct ChainOut {
-  T gmu[3];
-  T gF[3][3];
-  T glw2;
+  float gmu[3];
+  float gF[3][3];
+  float glw2;
 };
 
+// Chain of one record's accumulators to (m, b1, b2, b3) and on to the
+// Gaussian's mean and factor F. The geometry comes in precision T; the chain
+// runs in FP32, except the 2x2 solve gamma = A^-1 dL/dx*, whose matrix is
+// ill-conditioned for thin Gaussians and is solved in T.
 template <typename T>
 __device__ __forceinline__ void chain_record(const PairRec<T>& rc, const PairGeo<T>& gg,
-                                             const PlaneDev& pl, const float* acc, ChainOut<T>& o) {
-  const T ln2 = (T)kLn2;
-  const T a_p = (T)acc[1], a_t1 = (T)acc[2], a_t2 = (T)acc[3];
-  const T a_t1dx = (T)acc[4], a_t1dy = (T)acc[5], a_t2dy = (T)acc[6];
-  const T g_r11 = -2 * ln2 * a_t1dx;
-  const T g_r12 = -2 * ln2 * a_t1dy;
-  const T g_r22 = -2 * ln2 * a_t2dy;
-  const T g_xsj = 2 * ln2 * rc.r11 * a_t1;
-  const T g_xsi = 2 * ln2 * (rc.r12 * a_t1 + rc.r22 * a_t2);
-  const T g_lw2 = ln2 * a_p;
-  const T pu = (T)pl.pu, pv = (T)pl.pv;
-  const T gx1 = g_xsj * (T)pl.inv_pu, gx2 = g_xsi * (T)pl.inv_pv;
-  const T c = (T)kHalfLog2e;
-  const T g_q0 = -c * g_lw2;
+                                             const PlaneDev& pl, const float* acc, ChainOut& o) {
+  const float ln2 = kLn2;
+  const float r11 = (float)rc.r11, r12 = (float)rc.r12, r22 = (float)rc.r22;
+  const float a_p = acc[1], a_t1 = acc[2], a_t2 = acc[3];
+  const float a_t1dx = acc[4], a_t1dy = acc[5], a_t2dy = acc[6];
+  const float g_r11 = -2.f * ln2 * a_t1dx;
+  const float g_r12 = -2.f * ln2 * a_t1dy;
+  const float g_r22 = -2.f * ln2 * a_t2dy;
+  const float g_xsj = 2.f * ln2 * r11 * a_t1;
+  const float g_xsi = 2.f * ln2 * (r12 * a_t1 + r22 * a_t2);
+  const float g_lw2 = ln2 * a_p;
+  const float pu = pl.pu, pv = pl.pv;
+  const float gx1 = g_xsj * pl.inv_pu, gx2 = g_xsi * pl.inv_pv;
+  const float c = kHalfLog2e;
+  const float g_q0 = -c * g_lw2;
   // Cholesky backward of M = c D A D (M11 = r11^2, M12 = r11 r12, M22 = r12^2 + r22^2)
-  const T i22 = m_div((T)1, rc.r22), i11 = m_div((T)1, rc.r11);
-  const T gM22 = g_r22 * i22 * (T)0.5;
-  const T gr12 = g_r12 - g_r22 * rc.r12 * i22;
-  const T gM12 = gr12 * i11;
-  const T gr11 = g_r11 - gr12 * rc.r12 * i11;
-  const T gM11 = gr11 * i11 * (T)0.5;
-  T gA11 = c * pu * pu * gM11, gA12 = c * pu * pv * gM12, gA22 = c * pv * pv * gM22;
+  const float i22 = 1.f / r22, i11 = 1.f / r11;
+  const float gM22 = g_r22 * i22 * 0.5f;
+  const float gr12 = g_r12 - g_r22 * r12 * i22;
+  const float gM12 = gr12 * i11;
+  const float gr11 = g_r11 - gr12 * r12 * i11;
+  const float gM11 = gr11 * i11 * 0.5f;
+  float gA11 = c * pu * pu * gM11, gA12 = c * pu * pv * gM12, gA22 = c * pv * pv * gM22;
   // x* = m12 + m3 kappa, kappa = A^-1 s;  q0 = m3^2 (P33 - s^T A^-1 s)
-  const T* b1 = rc.b[0];
-  const T* b2 = rc.b[1];
-  const T* b3 = rc.b[2];
-  const T A11 = rc.nb1 * rc.nb1, A12 = b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2];
-  const T A22 = b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2];
-  const T idet = m_div((T)1, rc.cr * rc.cr);
-  const T gam0 = (A22 * gx1 - A12 * gx2) * idet;
-  const T gam1 = (A11 * gx2 - A12 * gx1) * idet;
-  const T m3 = gg.m[2];
-  const T kp0 = rc.kappa[0], kp1 = rc.kappa[1];
-  const T gm1 = gx1, gm2 = gx2;
-  const T gm3 = gx1 * kp0 + gx2 * kp1 + 2 * rc.k * g_q0;
-  const T m3sq_gq0 = m3 * m3 * g_q0;
-  const T gs0 = m3 * gam0 - 2 * m3sq_gq0 * kp0;
-  const T gs1 = m3 * gam1 - 2 * m3sq_gq0 * kp1;
-  const T gP33 = m3sq_gq0;
-  gA11 += -m3 * gam0 * kp0 + m3sq_gq0 * kp0 * kp0;
-  gA12 += -m3 * (gam0 * kp1 + gam1 * kp0) + 2 * m3sq_gq0 * kp0 * kp1;
-  gA22 += -m3 * gam1 * kp1 + m3sq_gq0 * kp1 * kp1;
-  T gb1[3], gb2[3], gb3[3];
+  const T* B1 = rc.b[0];
+  const T* B2 = rc.b[1];
+  const T A11 = rc.nb1 * rc.nb1, A12 = B1[0] * B2[0] + B1[1] * B2[1] + B1[2] * B2[2];
+  const T A22 = B2[0] * B2[0] + B2[1] * B2[1] + B2[2] * B2[2];
+  const T det = rc.cr * rc.cr;
+  const float gam0 = (float)m_div(A22 * (T)gx1 - A12 * (T)gx2, det);
+  const float gam1 = (float)m_div(A11 * (T)gx2 - A12 * (T)gx1, det);
+  float b1[3], b2[3], b3[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    gb1[a] = 2 * gA11 * b1[a] + gA12 * b2[a] + gs0 * b3[a];
-    gb2[a] = gA12 * b1[a] + 2 * gA22 * b2[a] + gs1 * b3[a];
-    gb3[a] = gs0 * b1[a] + gs1 * b2[a] + 2 * gP33 * b3[a];
+    b1[a] = (float)rc.b[0][a];
+    b2[a] = (float)rc.b[1][a];
+    b3[a] = (float)rc.b[2][a];
+  }
+  const float m3 = (float)gg.m[2];
+  const float kp0 = (float)rc.kappa[0], kp1 = (float)rc.kappa[1];
+  const float gm1 = gx1, gm2 = gx2;
+  const float gm3 = gx1 * kp0 + gx2 * kp1 + 2.f * (float)rc.k * g_q0;
+  const float m3sq_gq0 = m3 * m3 * g_q0;
+  const float gs0 = m3 * gam0 - 2.f * m3sq_gq0 * kp0;
+  const float gs1 = m3 * gam1 - 2.f * m3sq_gq0 * kp1;
+  const float gP33 = m3sq_gq0;
+  gA11 += -m3 * gam0 * kp0 + m3sq_gq0 * kp0 * kp0;
+  gA12 += -m3 * (gam0 * kp1 + gam1 * kp0) + 2.f * m3sq_gq0 * kp0 * kp1;
+  gA22 += -m3 * gam1 * kp1 + m3sq_gq0 * kp1 * kp1;
+  float gb1[3], gb2[3], gb3[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gb1[a] = 2.f * gA11 * b1[a] + gA12 * b2[a] + gs0 * b3[a];
+    gb2[a] = gA12 * b1[a] + 2.f * gA22 * b2[a] + gs1 * b3[a];
+    gb3[a] = gs0 * b1[a] + gs1 * b2[a] + 2.f * gP33 * b3[a];
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const T u = (T)pl.u[k], vv = (T)pl.v[k], nn = (T)pl.n[k];
+    const float u = pl.u[k], vv = pl.v[k], nn = pl.n[k];
     o.gmu[k] = gm1 * u + gm2 * vv + gm3 * nn;
 #pragma unroll
     for (int a = 0; a < 3; ++a) o.gF[k][a] = u * gb1[a] + vv * gb2[a] + nn * gb3[a];
@@ -555,51 +565,52 @@ __device__ __forceinline__ void chain_record(const PairRec<T>& rc, const PairGeo
 // Parameter gradient of one record (12 floats: mean[3], tri[6] or
 // log_scale[3] + quat[4], logit, intensity; unused entries zero).
 template <typename T, int COV>
-__device__ __forceinline__ void record_param_grad(const ChainOut<T>& o, const Factor<T>& f,
+__device__ __forceinline__ void record_param_grad(const ChainOut& o, const Factor<T>& f,
                                                   const GaussParams& prm, float gc, float* out) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) out[k] = (float)o.gmu[k];
+  for (int k = 0; k < 3; ++k) out[k] = o.gmu[k];
   const float alpha = sigmoidf(prm.logit);
   if (COV == UG_COV_TRI) {
     const float* t = prm.cp;
-    out[3] = (float)(2 * (T)t[0] * o.gF[0][0]);
-    out[4] = (float)o.gF[1][0];
-    out[5] = (float)o.gF[2][0];
-    out[6] = (float)(2 * (T)t[3] * o.gF[1][1]);
-    out[7] = (float)o.gF[2][1];
-    out[8] = (float)(2 * (T)t[5] * o.gF[2][2]);
-    out[9] = (float)o.glw2 * (1.f - alpha) * kLog2e;
+    out[3] = 2.f * t[0] * o.gF[0][0];
+    out[4] = o.gF[1][0];
+    out[5] = o.gF[2][0];
+    out[6] = 2.f * t[3] * o.gF[1][1];
+    out[7] = o.gF[2][1];
+    out[8] = 2.f * t[5] * o.gF[2][2];
+    out[9] = o.glw2 * (1.f - alpha) * kLog2e;
     out[10] = gc;
     out[11] = 0.f;
   } else {
     // F = R diag(1/s): dL/dR_ka = gF_ka / s_a, dL/dlog s_a = -sum_k gF_ka F_ka
-    T gR[3][3];
+    float gR[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      T sacc = 0;
+      const float sinv = expf(-prm.cp[a]);
+      float sacc = 0.f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        gR[k][a] = m_div(o.gF[k][a], f.s[a]);
-        sacc += o.gF[k][a] * f.F[k][a];
+        gR[k][a] = o.gF[k][a] * sinv;
+        sacc += o.gF[k][a] * (float)f.F[k][a];
       }
-      out[3 + a] = (float)(-sacc);
+      out[3 + a] = -sacc;
     }
-    const T w = f.qn[0], x = f.qn[1], y = f.qn[2], z = f.qn[3];
-    const T gw = 2 * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] +
-                      x * gR[2][1]);
-    const T gx = 2 * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2 * x * gR[1][1] -
-                      w * gR[1][2] + z * gR[2][0] + w * gR[2][1] - 2 * x * gR[2][2]);
-    const T gy = 2 * (-2 * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] +
-                      z * gR[1][2] - w * gR[2][0] + z * gR[2][1] - 2 * y * gR[2][2]);
-    const T gz = 2 * (-2 * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] -
-                      2 * z * gR[1][1] + y * gR[1][2] + x * gR[2][0] + y * gR[2][1]);
-    const T dot = gw * w + gx * x + gy * y + gz * z;
-    const T inv = m_div((T)1, f.qnorm);
-    out[6] = (float)((gw - w * dot) * inv);
-    out[7] = (float)((gx - x * dot) * inv);
-    out[8] = (float)((gy - y * dot) * inv);
-    out[9] = (float)((gz - z * dot) * inv);
-    out[10] = (float)o.glw2 * (1.f - alpha) * kLog2e;
+    const float w = (float)f.qn[0], x = (float)f.qn[1], y = (float)f.qn[2], z = (float)f.qn[3];
+    const float gw = 2.f * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] -
+                            y * gR[2][0] + x * gR[2][1]);
+    const float gx = 2.f * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2.f * x * gR[1][1] -
+                            w * gR[1][2] + z * gR[2][0] + w * gR[2][1] - 2.f * x * gR[2][2]);
+    const float gy = 2.f * (-2.f * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] +
+                            z * gR[1][2] - w * gR[2][0] + z * gR[2][1] - 2.f * y * gR[2][2]);
+    const float gz = 2.f * (-2.f * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] -
+                            2.f * z * gR[1][1] + y * gR[1][2] + x * gR[2][0] + y * gR[2][1]);
+    const float dot = gw * w + gx * x + gy * y + gz * z;
+    const float inv = 1.f / (float)f.qnorm;
+    out[6] = (gw - w * dot) * inv;
+    out[7] = (gx - x * dot) * inv;
+    out[8] = (gy - y * dot) * inv;
+    out[9] = (gz - z * dot) * inv;
+    out[10] = o.glw2 * (1.f - alpha) * kLog2e;
     out[11] = gc;
   }
 }
@@ -631,7 +642,7 @@ __global__ void __launch_bounds__(256)
       pair_box<T, COV>(f, pl, chi2, gg);
       PairRec<T> rc;
       pair_record<T, COV>(f, pl, gg, rc);
-      ChainOut<T> o;
+      ChainOut o;
       chain_record<T>(rc, gg, pl, acc, o);
       record_param_grad<T, COV>(o, f, prm, acc[0], out);
     }

@@ -4,8 +4,8 @@
 // Each 8-bit pass: (1) every block of kSortTile keys counts its digits in
 // shared memory and writes them digit-major, (2) one exclusive scan over
 // (digit, block) gives every block the output base of each digit, (3) every
-// block ranks its keys stably - rounds in order, warps in order, lanes in
-// order, equal digits found with __match_any_sync - and scatters keys and
+// block ranks its keys stably (warps in order, each warp's items in element
+// order, equal digits found with __match_any_sync) and scatters keys and
 // values. Instances arrive in (Gaussian chunk, plane, Gaussian) order, so the
 // stable sort leaves each tile's records in ascending Gaussian order.
 #include "ug_scan.cuh"
@@ -28,58 +28,66 @@ __global__ void __launch_bounds__(kSortThreads)
   v.sort_hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = hist[threadIdx.x];
 }
 
+// Warp w of block b holds elements b*kSortTile + w*32*kSortItems + k*32 + lane
+// (item k of lane `lane`): each warp ranks its 32*kSortItems keys in element
+// order with per-warp digit counters in shared memory (items in order, lanes in
+// order, equal digits found with __match_any_sync), then one block-wide pass
+// turns the per-warp counts into output positions. Three block barriers per
+// block instead of one set per round.
 __global__ void __launch_bounds__(kSortThreads)
     k_sort_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int shift,
                    int64_t nblk, WsView v) {
   constexpr int NW = kSortThreads / 32;
   __shared__ uint32_t cnt[NW][256];
-  __shared__ uint32_t gb[256];  // running output position of each digit
   if (dev_failed(v.hdr)) return;
   const int64_t n = v.hdr->st.instances;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   if (base >= n) return;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  gb[tid] = v.sort_hist[(int64_t)tid * nblk + blockIdx.x];
-  // all of the block's keys and values are loaded up front, so the ranking
-  // rounds below do not wait on memory
-  uint32_t kreg[kSortItems], vreg[kSortItems];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 #pragma unroll
-  for (int round = 0; round < kSortItems; ++round) {
-    const int64_t i = base + (int64_t)round * kSortThreads + tid;
-    kreg[round] = i < n ? __ldg(keys_in + i) : 0u;
-    vreg[round] = i < n ? __ldg(vals_in + i) : 0u;
+  for (int w = 0; w < NW; ++w) cnt[w][tid] = 0;
+  const uint32_t gbase = v.sort_hist[(int64_t)tid * nblk + blockIdx.x];
+  const int64_t wbase = base + (int64_t)warp * 32 * kSortItems + lane;
+  uint32_t kreg[kSortItems], vreg[kSortItems], rank[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int64_t i = wbase + (int64_t)k * 32;
+    kreg[k] = i < n ? __ldg(keys_in + i) : 0u;
+    vreg[k] = i < n ? __ldg(vals_in + i) : 0u;
   }
+  __syncthreads();
+  const uint32_t lt = lanemask_lt();
 #pragma unroll
-  for (int round = 0; round < kSortItems; ++round) {
-    const int64_t i = base + (int64_t)round * kSortThreads + tid;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) cnt[w][tid] = 0;
-    __syncthreads();
-    const bool valid = i < n;
-    const uint32_t key = kreg[round], val = vreg[round];
-    const uint32_t d = valid ? (key >> shift) & 0xffu : 256u;
+  for (int k = 0; k < kSortItems; ++k) {
+    const bool valid = wbase + (int64_t)k * 32 < n;
+    const uint32_t d = valid ? (kreg[k] >> shift) & 0xffu : 256u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t rank = __popc(peers & lanemask_lt());
-    if (valid && rank == 0) cnt[warp][d] = __popc(peers);
-    __syncthreads();
-    {  // thread tid owns digit tid: exclusive prefix over the warps, then advance
-      uint32_t acc = gb[tid];
+    const uint32_t before = valid ? cnt[warp][d] : 0u;
+    __syncwarp();
+    if (valid && (peers & lt) == 0) cnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+    rank[k] = before + __popc(peers & lt);
+  }
+  __syncthreads();
+  {  // thread tid owns digit tid: exclusive prefix over the warps plus the block's base
+    uint32_t acc = gbase;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        const uint32_t c = cnt[w][tid];
-        cnt[w][tid] = acc;
-        acc += c;
-      }
-      gb[tid] = acc;
+    for (int w = 0; w < NW; ++w) {
+      const uint32_t c = cnt[w][tid];
+      cnt[w][tid] = acc;
+      acc += c;
     }
-    __syncthreads();
-    if (valid) {
-      const uint32_t pos = cnt[warp][d] + rank;
-      keys_out[pos] = key;
-      vals_out[pos] = val;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    if (wbase + (int64_t)k * 32 < n) {
+      const uint32_t d = (kreg[k] >> shift) & 0xffu;
+      const uint32_t pos = cnt[warp][d] + rank[k];
+      keys_out[pos] = kreg[k];
+      vals_out[pos] = vreg[k];
     }
-    __syncthreads();
   }
 }
 
