@@ -311,37 +311,67 @@ __global__ void __launch_bounds__(Layout<TILE, WW, PPT>::NT)
         const float dx = pxj - a.x, dy = pyi - a.y;
         const float t1 = fmaf(a.z, dx, a.w * dy);
         const float t2 = c.x * dy;
-        float lw = c.y;
-        int klo = 0, khi = PPT - 1;
-        if (!(ent & 0x8000u)) {
+        // Per lane: S0 = sum r w, S1 = sum gww, U1 = sum gww t1, U2 = sum gww t2,
+        // K1 = sum k gww t1, K2 = sum k gww t2 over its PPT pixels (row ib + k);
+        // then sum u1 dx = dx U1, sum u1 dy = dy U1 + K1, sum u2 dy = dy U2 + K2.
+        float s0 = 0.f, s1 = 0.f, U1 = 0.f, U2 = 0.f, K1 = 0.f, K2 = 0.f;
+        if (ent & 0x8000u) {  // the box covers the footprint: no per-pixel tests
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            const float t1k = k ? fmaf((float)k, a.w, t1) : t1;
+            const float t2k = k ? fmaf((float)k, c.x, t2) : t2;
+            float w;
+            if (CUT) {
+              const float qq = fmaf(t1k, t1k, t2k * t2k);
+              w = qq <= c.w ? fast_exp2(c.y - qq) : 0.f;
+            } else {
+              w = fast_exp2(fmaf(-t1k, t1k, fmaf(-t2k, t2k, c.y)));
+            }
+            const float gww = fmaf(rr[k], c.z, -rc[k]) * w;  // dL/dw * w
+            s0 = fmaf(rr[k], w, s0);
+            s1 += gww;
+            const float u1 = gww * t1k, u2 = gww * t2k;
+            U1 += u1;
+            U2 += u2;
+            if (k) {
+              K1 = fmaf((float)k, u1, K1);
+              K2 = fmaf((float)k, u2, K2);
+            }
+          }
+        } else {
           const uint2 bx = S.box[r];
           const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
-          if ((unsigned)(j - j0) > (unsigned)(j1 - j0)) lw = -INFINITY;
-          klo = i0 - ib;
-          khi = i1 - ib;
+          const float lw = (unsigned)(j - j0) <= (unsigned)(j1 - j0) ? c.y : -INFINITY;
+          const int klo = i0 - ib, khi = i1 - ib;
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            const float t1k = k ? fmaf((float)k, a.w, t1) : t1;
+            const float t2k = k ? fmaf((float)k, c.x, t2) : t2;
+            const float qq = fmaf(t1k, t1k, t2k * t2k);
+            bool in = k >= klo && k <= khi;
+            if (CUT) in = in && qq <= c.w;
+            const float w = in ? fast_exp2(lw - qq) : 0.f;
+            const float gww = fmaf(rr[k], c.z, -rc[k]) * w;
+            s0 = fmaf(rr[k], w, s0);
+            s1 += gww;
+            const float u1 = gww * t1k, u2 = gww * t2k;
+            U1 += u1;
+            U2 += u2;
+            if (k) {
+              K1 = fmaf((float)k, u1, K1);
+              K2 = fmaf((float)k, u2, K2);
+            }
+          }
         }
         float acc[8];
-#pragma unroll
-        for (int f = 0; f < 8; ++f) acc[f] = 0.f;
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-          const float t1k = k ? fmaf((float)k, a.w, t1) : t1;
-          const float t2k = k ? fmaf((float)k, c.x, t2) : t2;
-          const float dyk = dy + (float)k;
-          const float qq = fmaf(t1k, t1k, t2k * t2k);
-          bool in = k >= klo && k <= khi;
-          if (CUT) in = in && qq <= c.w;
-          const float w = in ? fast_exp2(lw - qq) : 0.f;
-          const float gww = fmaf(rr[k], c.z, -rc[k]) * w;  // dL/dw * w
-          acc[0] = fmaf(rr[k], w, acc[0]);
-          acc[1] += gww;
-          const float u1 = gww * t1k, u2 = gww * t2k;
-          acc[2] += u1;
-          acc[3] += u2;
-          acc[4] = fmaf(u1, dx, acc[4]);
-          acc[5] = fmaf(u1, dyk, acc[5]);
-          acc[6] = fmaf(u2, dyk, acc[6]);
-        }
+        acc[0] = s0;
+        acc[1] = s1;
+        acc[2] = U1;
+        acc[3] = U2;
+        acc[4] = dx * U1;
+        acc[5] = fmaf(dy, U1, K1);
+        acc[6] = fmaf(dy, U2, K2);
+        acc[7] = 0.f;
         const float tot = warp_reduce8(acc, lane);
         if ((lane & 3) == 0 && fidx < 7) atomicAdd(v.rec_grad + (size_t)S.rid[r] * 8 + fidx, tot);
       }

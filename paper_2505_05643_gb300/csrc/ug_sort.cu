@@ -31,36 +31,41 @@ __global__ void __launch_bounds__(kSortThreads)
 // Warp w of block b holds elements b*kSortTile + w*32*kSortItems + k*32 + lane
 // (item k of lane `lane`): each warp ranks its 32*kSortItems keys in element
 // order with per-warp digit counters in shared memory (items in order, lanes in
-// order, equal digits found with __match_any_sync), then one block-wide pass
-// turns the per-warp counts into output positions. Three block barriers per
-// block instead of one set per round.
+// order, equal digits found with __match_any_sync). The block then places its
+// keys in shared memory in digit order and writes them out so that consecutive
+// threads write consecutive addresses of each digit's output run.
 __global__ void __launch_bounds__(kSortThreads)
     k_sort_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int shift,
                    int64_t nblk, WsView v) {
   constexpr int NW = kSortThreads / 32;
   __shared__ uint32_t cnt[NW][256];
+  __shared__ uint32_t dstart[256];
+  __shared__ uint32_t gb[256];
+  __shared__ uint32_t sk[kSortTile];
+  __shared__ uint32_t sv[kSortTile];
   if (dev_failed(v.hdr)) return;
   const int64_t n = v.hdr->st.instances;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   if (base >= n) return;
+  const int count = (int)min((int64_t)kSortTile, n - base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 #pragma unroll
   for (int w = 0; w < NW; ++w) cnt[w][tid] = 0;
-  const uint32_t gbase = v.sort_hist[(int64_t)tid * nblk + blockIdx.x];
-  const int64_t wbase = base + (int64_t)warp * 32 * kSortItems + lane;
+  gb[tid] = v.sort_hist[(int64_t)tid * nblk + blockIdx.x];
+  const int wbase = warp * 32 * kSortItems + lane;
   uint32_t kreg[kSortItems], vreg[kSortItems], rank[kSortItems];
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
-    const int64_t i = wbase + (int64_t)k * 32;
-    kreg[k] = i < n ? __ldg(keys_in + i) : 0u;
-    vreg[k] = i < n ? __ldg(vals_in + i) : 0u;
+    const int i = wbase + k * 32;
+    kreg[k] = i < count ? __ldg(keys_in + base + i) : 0u;
+    vreg[k] = i < count ? __ldg(vals_in + base + i) : 0u;
   }
   __syncthreads();
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
-    const bool valid = wbase + (int64_t)k * 32 < n;
+    const bool valid = wbase + k * 32 < count;
     const uint32_t d = valid ? (kreg[k] >> shift) & 0xffu : 256u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t before = valid ? cnt[warp][d] : 0u;
@@ -70,24 +75,32 @@ __global__ void __launch_bounds__(kSortThreads)
     rank[k] = before + __popc(peers & lt);
   }
   __syncthreads();
-  {  // thread tid owns digit tid: exclusive prefix over the warps plus the block's base
-    uint32_t acc = gbase;
+  uint32_t total = 0;  // thread tid owns digit tid: exclusive prefix over the warps
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      const uint32_t c = cnt[w][tid];
-      cnt[w][tid] = acc;
-      acc += c;
-    }
+  for (int w = 0; w < NW; ++w) {
+    const uint32_t c = cnt[w][tid];
+    cnt[w][tid] = total;
+    total += c;
   }
+  uint32_t all;
+  dstart[tid] = block_excl_scan<uint32_t>(total, &all);
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
-    if (wbase + (int64_t)k * 32 < n) {
+    if (wbase + k * 32 < count) {
       const uint32_t d = (kreg[k] >> shift) & 0xffu;
-      const uint32_t pos = cnt[warp][d] + rank[k];
-      keys_out[pos] = kreg[k];
-      vals_out[pos] = vreg[k];
+      const uint32_t lpos = dstart[d] + cnt[warp][d] + rank[k];
+      sk[lpos] = kreg[k];
+      sv[lpos] = vreg[k];
     }
+  }
+  __syncthreads();
+  for (int i = tid; i < count; i += kSortThreads) {
+    const uint32_t key = sk[i];
+    const uint32_t d = (key >> shift) & 0xffu;
+    const uint32_t pos = gb[d] + (uint32_t)i - dstart[d];
+    keys_out[pos] = key;
+    vals_out[pos] = sv[i];
   }
 }
 
