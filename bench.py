@@ -8,12 +8,15 @@ cut-off), captured in one CUDA graph and replayed.
 Prints one JSON line. `value` is useful Gaussian-pixel pairs per second: the
 pairs the box cut-off includes (each evaluated in the forward and again in the
 backward pass of a step) divided by the step time; `steps_per_s` is the train
-step rate. `--impl reference` times the FP64 CPU oracle (the only other
+step rate. Every step starts from the same state (initial parameters, zero Adam
+moments), restored by a device copy inside the step, so the workload does not
+drift with the number of steps. `--impl reference` times the FP64 CPU oracle (the only other
 implementation of this method) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -25,6 +28,14 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+
+# FP32-pipe operations per evaluated (pixel, record) pair in the formulation the
+# rasterizers implement (derivation in the kernels' header comments).
+FWD_OPS = 6
+BWD_OPS = 16
+# DRAM bytes (read + write) of one k_render_bwd launch on this workload, from a
+# one-pass ncu capture of the kernel as it stands; None when not measured.
+BWD_TRAFFIC = None
 
 METRIC = "Gaussian·pixel evals/s and fwd+bwd train steps/s, 1M Gaussians, 1×GB300"
 WORKLOAD = "aniso_1m: 1,000,000 Gaussians, axis ratios log-uniform to 1e4, 64 planes/launch " \
@@ -39,33 +50,51 @@ def _dist_env():
 
 
 def _clock_sampler(gpu_index: int, path: str):
-    fields = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    fields = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     try:
         f = open(path, "w")
         p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={fields}",
-                              "--format=csv,noheader,nounits", "-lms", "200"],
+                              "--format=csv,noheader,nounits", "-lms", "100"],
                              stdout=f, stderr=subprocess.DEVNULL)
         return p, f
     except Exception:
         return None, None
 
 
-def _clock_summary(path: str) -> dict:
+def _wait_for_samples(path: str, timeout_s: float = 5.0):
+    """Block until the sampler has written its first line (nvidia-smi start-up)."""
+    t0 = time.time()
+    while time.time() - t0 < timeout_s:
+        try:
+            if os.path.getsize(path) > 0:
+                return
+        except OSError:
+            pass
+        time.sleep(0.05)
+
+
+def _clock_summary(path: str, t_start: datetime.datetime, t_stop: datetime.datetime) -> dict:
+    """Median SM clock and active throttle reasons of the samples taken between
+    t_start and t_stop (host wall clock, the same clock nvidia-smi stamps)."""
     sm, smax, reasons = [], 0.0, set()
     names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
     try:
         for line in open(path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax = max(smax, float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                clk, cmax = float(parts[2]), float(parts[3])
             except ValueError:
                 continue
-            for name, val in zip(names, parts[5:9]):
+            if ts < t_start or ts > t_stop:
+                continue
+            sm.append(clk)
+            smax = max(smax, cmax)
+            for name, val in zip(names, parts[6:10]):
                 if val.lower().startswith("active") or val == "0x0000000000000001" or val == "1":
                     reasons.add(name)
     except OSError:
@@ -111,11 +140,13 @@ def run_reference(args):
         return 0
     g, pl, _ = _workload()
     sizes = pl["size"][:, 0]
-    # each step: the oracle's forward + backward over 4 of the 64 planes (all 1M
-    # Gaussians), a different 4 each step; the oracle has no warm state
+    # each step: the oracle's forward + backward over a few of the 64 planes (all
+    # 1M Gaussians), different planes each step, so that K steps take about a
+    # minute or two on 16 host cores; the oracle has no warm state
+    per_step = 4 if args.steps <= 50 else 1
     rates, secs, cores, total_pairs = [], [], 1, 0
     for k in range(args.steps):
-        sample = [(4 * k + j) % len(sizes) for j in range(4)]
+        sample = [(per_step * k + j) % len(sizes) for j in range(per_step)]
         rate, dt, cores, pairs = cpu_oracle_rate(g, pl, sample)
         rates.append(rate)
         secs.append(dt)
@@ -126,10 +157,11 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "4 of the 64 planes per step"},
+        "config": {"workload": WORKLOAD, "sample": f"{per_step} of the 64 planes per step"},
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-                         "sample": "FP64 oracle scatter forward + analytic backward on 4 of 64 planes "
-                                   "per step (planes rotate), all 1,000,000 Gaussians, "
+                         "sample": "FP64 oracle scatter forward + analytic backward on "
+                                   f"{per_step} of 64 planes per step (planes rotate), "
+                                   "all 1,000,000 Gaussians, "
                                    f"{total_pairs} pairs in {np.sum(secs):.1f} s"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -175,13 +207,20 @@ def run_ours(args):
     s = torch.cuda.Stream(device=dev)
     st_dev = torch.zeros(64, dtype=torch.uint8, device=dev)
 
-    # Every measured phase starts from the same state and runs W + K steps, so
-    # the parameters (and with them the record counts) follow the same path.
+    # Every step starts from the same state: the initial parameters, zero Adam
+    # moments and step counter 0, copied on the device at the start of the step
+    # (inside the timed region). Without it the workload would drift with K:
+    # at the paper's learning rate the boxes of this scene grow several-fold
+    # within a few hundred steps.
     state0 = [t.clone() for t in (step.params, step.m, step.v, step.step)]
 
+    def reset_on(stream):
+        with torch.cuda.stream(stream):
+            for dst, src in zip((step.params, step.m, step.v, step.step), state0):
+                dst.copy_(src, non_blocking=True)
+
     def restore():
-        for dst, src in zip((step.params, step.m, step.v, step.step), state0):
-            dst.copy_(src)
+        reset_on(torch.cuda.current_stream())
         torch.cuda.synchronize()
 
     def read_status():
@@ -189,152 +228,214 @@ def run_ours(args):
         s.synchronize()
         return B.ug_ws_status.from_buffer_copy(st_dev.cpu().numpy().tobytes())
 
-    # sizing run: W + K checked eager steps; grow the workspace until none overflows
+    # sizing run: W + K checked eager steps; grow the workspace until none
+    # overflows (a capacity overflow reports the counts it needed)
     st0 = renderer.preprocess(params, check=True)
-    need_rec, need_inst = st0["records"], st0["instances"]
-    for attempt in range(6):
-        rec = int(need_rec * 1.15) + 4096
-        inst = min(int(need_inst * 1.15) + 65536, (1 << 31) - 1)
+    need = {"rec": st0["records"], "inst": st0["instances"]}
+
+    def grow():
+        rec = int(need["rec"] * 1.25) + 4096
+        inst = min(int(need["inst"] * 1.25) + 65536, (1 << 31) - 1)
         renderer._alloc(rec, inst)
         step.g_struct = R.gaussians_struct(params, B.UG_COV_TRI)
+
+    def note(x):
+        need["rec"] = max(need["rec"], int(x.records))
+        need["inst"] = max(need["inst"], int(x.instances))
+        if x.status not in (B.UG_OK, B.UG_ERR_CAPACITY):
+            raise RuntimeError(f"device status {x.status}")
+        return x.status == B.UG_OK
+
+    for attempt in range(12):
+        grow()
         restore()
         ok = True
         with torch.cuda.stream(s):
-            for k in range(args.warmup + args.steps):
+            for k in range(args.warmup):
+                reset_on(s)
                 step.enqueue(s)
-                x = read_status()
-                need_rec = max(need_rec, x.records)
-                need_inst = max(need_inst, x.instances)
-                if x.status != 0:
+                if not note(read_status()):
                     ok = False
                     break
         if ok:
             break
-    restore()
-    s.wait_stream(torch.cuda.current_stream())
-    graph = step.capture(s)
-    status_log = torch.zeros((args.warmup + args.steps, 64), dtype=torch.uint8, device=dev)
+    else:
+        raise RuntimeError("workspace sizing did not converge")
+    print(f"[bench] workspace: {renderer.plan.record_capacity} records, "
+          f"{renderer.plan.instance_capacity} instances", file=sys.stderr)
 
-    def one(k):
-        graph.replay()
-        B.ug_read_status(renderer.plan, renderer.ws, status_log[k], s)
-
-    # ---- timed region: K replays of the captured step after W warm-up replays
-    with torch.cuda.stream(s):
-        for k in range(args.warmup):
-            one(k)
-    s.synchronize()
+    # ---- timed region: K replays of the captured step after W warm-up replays.
+    # The backward's atomics make the trajectory differ slightly from the sizing
+    # run's; a capacity overflow in the timed steps resizes and measures again.
     clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
                             f".bench_clocks_{rank}.csv")
-    sampler, fh = _clock_sampler(dev.index or 0, clk_path)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    start.record(s)
-    with torch.cuda.stream(s):
-        for k in range(args.steps):
-            one(args.warmup + k)
-    stop.record(s)
-    torch.cuda.synchronize()
-    total_ms = start.elapsed_time(stop)
-    if sampler is not None:
-        sampler.terminate()
-        sampler.wait()
-        fh.close()
-    clocks = _clock_summary(clk_path)
+    status_log = torch.zeros((args.warmup + args.steps, 64), dtype=torch.uint8, device=dev)
+    for attempt in range(3):
+        restore()
+        s.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            reset_on(s)
+            step.enqueue(s)
+
+        def one(k):
+            graph.replay()
+            B.ug_read_status(renderer.plan, renderer.ws, status_log[k], s)
+
+        with torch.cuda.stream(s):
+            for k in range(args.warmup):
+                one(k)
+        s.synchronize()
+        sampler, fh = _clock_sampler(dev.index or 0, clk_path)
+        _wait_for_samples(clk_path)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t_start = datetime.datetime.now()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(s)
+        with torch.cuda.stream(s):
+            for k in range(args.steps):
+                one(args.warmup + k)
+        stop.record(s)
+        torch.cuda.synchronize()
+        t_stop = datetime.datetime.now()
+        total_ms = start.elapsed_time(stop)
+        if sampler is not None:
+            time.sleep(0.15)  # let the sampler flush the last interval
+            sampler.terminate()
+            sampler.wait()
+            fh.close()
+        sts = [B.ug_ws_status.from_buffer_copy(row.tobytes()) for row in status_log.cpu().numpy()]
+        ok = all([note(x) for x in sts])
+        if world > 1:
+            flag = torch.tensor([0 if ok else 1], device=dev)
+            torch.distributed.all_reduce(flag, op=torch.distributed.ReduceOp.MAX)
+            ok = int(flag.item()) == 0
+        if ok:
+            break
+        print("[bench] capacity overflow in the timed steps: resizing and measuring again",
+              file=sys.stderr)
+        grow()
+    else:
+        raise RuntimeError("capacity overflow in the timed steps")
+    clocks = _clock_summary(clk_path, t_start, t_stop)
     ms_step = total_ms / args.steps
     if world > 1:
         t = torch.tensor([ms_step], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_step = float(t.item())
-    sts = [B.ug_ws_status.from_buffer_copy(row.tobytes()) for row in status_log.cpu().numpy()]
-    bad = [x.status for x in sts if x.status != 0]
-    if bad:
-        raise RuntimeError(f"device status {bad[0]} during the timed steps")
     pairs = float(np.mean([x.box_pixels for x in sts[args.warmup:]]))
     value = pairs * world / (ms_step * 1e-3)
 
     # ---- phase timing: the same W + K steps eagerly, CUDA events on the
-    # launching stream around ug_render and ug_render_backward
-    restore()
-    bwd_ms, fwd_ms, eager_st = [], [], []
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    with torch.cuda.stream(s):
-        for k in range(args.warmup + args.steps):
-            B.ug_preprocess(r.plan, step.g_struct, r.d_planes, r.ws, s)
-            B.ug_bin_sort(r.plan, r.ws, s)
-            e[0].record(s)
-            B.ug_render(r.plan, r.ws, step.image, step.alpha, s)
-            e[1].record(s)
-            B.ug_mse_loss_grad(step.image, step.targets, step.image.numel(), step.grad_image,
-                               step.loss, s)
-            e[2].record(s)
-            B.ug_render_backward(r.plan, step.g_struct, r.d_planes, r.ws, step.image, step.alpha,
-                                 step.grad_image, step.grad_struct, s)
-            e[3].record(s)
-            B.ug_adam_step(step.params, step.grads, step.m, step.v, r.rows, r.n, step.lr_rows,
-                           step.step, T.BETA1, T.BETA2, T.EPS, s)
-            x = read_status()
-            if k >= args.warmup:
-                eager_st.append(x)
-                fwd_ms.append(e[0].elapsed_time(e[1]))
-                bwd_ms.append(e[2].elapsed_time(e[3]))
-    if any(x.status != 0 for x in eager_st):
-        raise RuntimeError("device status error in the phase-timing steps")
+    # launching stream around each call of the step
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+    for attempt in range(3):
+        restore()
+        bwd_ms, fwd_ms, chain_ms, pre_ms, eager_st = [], [], [], [], []
+        ok = True
+        with torch.cuda.stream(s):
+            for k in range(args.warmup + args.steps):
+                reset_on(s)
+                e[0].record(s)
+                B.ug_preprocess(r.plan, step.g_struct, r.d_planes, r.ws, s)
+                B.ug_bin_sort(r.plan, r.ws, s)
+                e[1].record(s)
+                B.ug_render(r.plan, r.ws, step.image, step.alpha, s)
+                e[2].record(s)
+                B.ug_mse_loss_grad(step.image, step.targets, step.image.numel(), step.grad_image,
+                                   step.loss, s)
+                e[3].record(s)
+                B.ug_render_backward_raster(r.plan, r.ws, step.image, step.alpha, step.grad_image,
+                                            s)
+                e[4].record(s)
+                B.ug_preprocess_backward(r.plan, step.g_struct, r.ws, step.grad_struct, s)
+                e[5].record(s)
+                B.ug_adam_step(step.params, step.grads, step.m, step.v, r.rows, r.n,
+                               step.lr_rows, step.step, T.BETA1, T.BETA2, T.EPS, s)
+                x = read_status()
+                if not note(x):
+                    ok = False
+                    break
+                if k >= args.warmup:
+                    eager_st.append(x)
+                    pre_ms.append(e[0].elapsed_time(e[1]))
+                    fwd_ms.append(e[1].elapsed_time(e[2]))
+                    bwd_ms.append(e[3].elapsed_time(e[4]))
+                    chain_ms.append(e[4].elapsed_time(e[5]))
+        if ok:
+            break
+        grow()
+    else:
+        raise RuntimeError("capacity overflow in the phase-timing steps")
 
     # ---- e2e: the public API with host buffers; the step's inputs (targets and
     # plane poses) copied from pinned host memory and the loss read back each step
-    restore()
     h_targets = torch.from_numpy(target).pin_memory()
     h_planes = torch.from_numpy(r.host_planes.view(np.uint8).copy()).pin_memory()
     h_loss = torch.zeros(1, dtype=torch.float32).pin_memory()
-    with torch.cuda.stream(s):
-        for k in range(args.warmup):
-            step.enqueue(s)
-    s.synchronize()
-    e2e_st = []
-    t0 = time.perf_counter()
-    with torch.cuda.stream(s):
-        for k in range(args.steps):
-            step.targets.copy_(h_targets, non_blocking=True)
-            r.d_planes.copy_(h_planes, non_blocking=True)
-            step.enqueue(s)
-            h_loss.copy_(step.loss[:1], non_blocking=True)
-            B.ug_read_status(r.plan, r.ws, st_dev, s)
-            s.synchronize()
-            e2e_st.append(B.ug_ws_status.from_buffer_copy(st_dev.cpu().numpy().tobytes()))
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if any(x.status != 0 for x in e2e_st):
-        raise RuntimeError("device status error in the end-to-end steps")
+    for attempt in range(3):
+        restore()
+        with torch.cuda.stream(s):
+            for k in range(args.warmup):
+                reset_on(s)
+                step.enqueue(s)
+        s.synchronize()
+        e2e_st = []
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s):
+            for k in range(args.steps):
+                step.targets.copy_(h_targets, non_blocking=True)
+                r.d_planes.copy_(h_planes, non_blocking=True)
+                reset_on(s)
+                step.enqueue(s)
+                h_loss.copy_(step.loss[:1], non_blocking=True)
+                B.ug_read_status(r.plan, r.ws, st_dev, s)
+                s.synchronize()
+                e2e_st.append(B.ug_ws_status.from_buffer_copy(st_dev.cpu().numpy().tobytes()))
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if all([note(x) for x in e2e_st]):
+            break
+        grow()
+    else:
+        raise RuntimeError("capacity overflow in the end-to-end steps")
     e2e_pairs = float(np.mean([x.box_pixels for x in e2e_st]))
     e2e = {"value": e2e_pairs * world / e2e_s, "unit": "pairs/s",
            "h2d_bytes_per_step": int(h_targets.numel() * 4 + h_planes.numel()),
            "d2h_bytes_per_step": 4 + 64}
 
-    # ---- roofline of the dominant kernel (backward rasterizer, FP32-pipe bound)
+    # ---- roofline of the dominant kernel: the backward rasterizer (FP32-pipe
+    # bound), timed as the ug_render_backward_raster call (its zeroing of the
+    # per-record gradient buffer included).
     # Unit: one evaluated (pixel, record) pair. Algorithmic FP32-pipe operations
-    # per evaluated pair (an FMA counts once): forward 6 (+1 MUFU.EX2), backward
-    # 16 (+1 MUFU.EX2). Peak from unit counts and clocks: SMs x 128 FP32 lanes x
-    # max SM clock (2070 MHz); EX2 runs at 32/clk/SM and is not binding.
+    # per evaluated pair (an FMA counts once): forward FWD_OPS, backward BWD_OPS,
+    # each plus one MUFU.EX2 (32/clk/SM, not binding at these op counts). Peak
+    # from unit counts and clocks: SMs x 128 FP32 lanes x max SM clock (2070 MHz).
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     fp32_peak = sms * 128 * fmax
     bwd_s = float(np.mean(bwd_ms)) * 1e-3
     fwd_s = float(np.mean(fwd_ms)) * 1e-3
     evaluated = float(np.mean([x.evaluated_pairs for x in eager_st]))
+    evaluated_bwd = float(np.mean([x.evaluated_pairs_bwd for x in eager_st]))
     pairs_eager = float(np.mean([x.box_pixels for x in eager_st]))
-    roof = {"bound": "alu", "kernel": "ug_render_backward (k_render_bwd + chain + gather)",
-            "achieved": 16.0 * evaluated / bwd_s / 1e12, "peak": fp32_peak / 1e12,
-            "unit": "Tops/s (FP32 pipe)", "frac": 16.0 * evaluated / bwd_s / fp32_peak,
-            "traffic": None,
-            "units_per_launch": evaluated, "ops_per_unit": 16,
+    roof = {"bound": "alu", "kernel": "k_render_bwd (ug_render_backward_raster)",
+            "achieved": BWD_OPS * evaluated_bwd / bwd_s / 1e12, "peak": fp32_peak / 1e12,
+            "unit": "Tops/s (FP32 pipe)", "frac": BWD_OPS * evaluated_bwd / bwd_s / fp32_peak,
+            "traffic": BWD_TRAFFIC,
+            "units_per_launch": evaluated_bwd, "ops_per_unit": BWD_OPS,
             "peak_note": "derived: SMs x 128 FP32 lanes x max SM clock",
-            "fwd": {"kernel": "ug_render (k_render_fwd)", "ms": fwd_s * 1e3,
-                    "achieved": 6.0 * evaluated / fwd_s / 1e12,
-                    "frac": 6.0 * evaluated / fwd_s / fp32_peak},
+            "fwd": {"kernel": "k_render_fwd (ug_render)", "ms": fwd_s * 1e3,
+                    "ops_per_unit": FWD_OPS, "units_per_launch": evaluated,
+                    "achieved": FWD_OPS * evaluated / fwd_s / 1e12,
+                    "frac": FWD_OPS * evaluated / fwd_s / fp32_peak},
             "bwd_ms": bwd_s * 1e3, "box_pairs_per_launch": pairs_eager,
-            "evaluated_over_box_pairs": evaluated / pairs_eager}
+            "evaluated_over_box_pairs": evaluated / pairs_eager,
+            "evaluated_bwd_over_box_pairs": evaluated_bwd / pairs_eager,
+            "phases_ms": {"preprocess+bin_sort": float(np.mean(pre_ms)),
+                          "render": fwd_s * 1e3, "render_backward_raster": bwd_s * 1e3,
+                          "preprocess_backward": float(np.mean(chain_ms))}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -357,6 +458,8 @@ def run_ours(args):
                        "variant_bwd": args.variant_bwd, "graph": True,
                        "targets": "hidden 1M-Gaussian volume (seed 1) rendered on the same planes",
                        "l2": "working set > L2 (129 MB); no flush",
+                       "state": "every step starts from the initial parameters and zero Adam "
+                                "moments (device copy inside the timed step)",
                        "parallelism": f"replicas x{world}"},
             "steps_per_s": 1e3 / ms_step,
             "gpu_launches": step.kernels_per_step() * args.steps,
@@ -373,7 +476,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=16)

@@ -145,7 +145,8 @@ typedef struct {
   int64_t evaluated_pairs; /* (pixel, record) pairs the last ug_render evaluated: warp
                               footprints x records that reach them; pairs whose weight is
                               provably an FP32 zero are not evaluated */
-  int64_t reserved[2];
+  int64_t evaluated_pairs_bwd; /* the same count for the last backward rasterizer launch */
+  int64_t reserved[1];
 } ug_ws_status;
 
 /* Adam learning-rate schedule of one parameter row (device array entry):
@@ -238,6 +239,29 @@ ug_status ug_render_backward(const ug_plan* plan, const ug_gaussians* gaussians,
                              const ug_plane* d_planes, void* ws, size_t ws_bytes,
                              const float* image, const float* alpha, const float* grad_image,
                              const ug_gaussian_grads* grads, ug_stream stream);
+
+/* Row a7 alone (the first half of ug_render_backward): per tile, recompute
+ * every included weight and reduce dL/d(record) over the tile's pixels into the
+ * workspace's per-record gradient buffer (8 floats per record: dL/dc, dL/d lw2,
+ * and the sums that give dL/dx*, dL/d(r11, r12, r22)), zeroed first by this
+ * call. image, alpha and grad_image are device arrays of plan->total_pixels
+ * floats laid out as for ug_render. Returns UG_ERR_INVALID_ARGUMENT for a NULL
+ * pointer; device-side failures of the preceding calls propagate through the
+ * workspace status (the kernels then return without work). */
+ug_status ug_render_backward_raster(const ug_plan* plan, void* ws, size_t ws_bytes,
+                                    const float* image, const float* alpha,
+                                    const float* grad_image, ug_stream stream);
+
+/* Row a8 alone (the second half of ug_render_backward): chain the per-record
+ * gradients left in the workspace by ug_render_backward_raster through the
+ * preprocess of rows a1-a2 (plane projection, Sec. 3.1; Eq. tri-param or the
+ * scale-rotation front-end, Sec. 3.2; the cut-off box is a constant) and the
+ * activations (Sec. 3.4), and sum them over planes into *grads (written, not
+ * accumulated; one thread per Gaussian, no atomics). `gaussians` must be the
+ * parameters ug_preprocess ran on. */
+ug_status ug_preprocess_backward(const ug_plan* plan, const ug_gaussians* gaussians, void* ws,
+                                 size_t ws_bytes, const ug_gaussian_grads* grads,
+                                 ug_stream stream);
 
 /* Row a9: one Adam step on `rows` parameter rows of n floats each, all in one
  * contiguous [rows][n] buffer (param, grad, exp_avg, exp_avg_sq alike):

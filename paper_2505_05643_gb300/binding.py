@@ -35,6 +35,7 @@ EXPORTS = (
     "ug_version", "ug_status_string", "ug_num_variants", "ug_config_default", "ug_plan_init",
     "ug_preprocess", "ug_bin_sort", "ug_render", "ug_mse_loss_grad", "ug_render_backward",
     "ug_adam_step", "ug_read_status", "ug_debug_views", "ug_mse_loss_grad_static",
+    "ug_render_backward_raster", "ug_preprocess_backward",
 )
 UG_MSE_STATIC_MAX_N = 1 << 30
 
@@ -77,7 +78,8 @@ class ug_ws_status(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("detail", ctypes.c_int32),
                 ("records", ctypes.c_int64), ("instances", ctypes.c_int64),
                 ("fp64_records", ctypes.c_int64), ("box_pixels", ctypes.c_int64),
-                ("evaluated_pairs", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2)]
+                ("evaluated_pairs", ctypes.c_int64), ("evaluated_pairs_bwd", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 1)]
 
 
 class ug_adam_row(ctypes.Structure):
@@ -110,6 +112,7 @@ def load(build_if_missing: bool = True):
     vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
     P = ctypes.POINTER
     lib.ug_version.restype = i32
+    lib.ug_version.argtypes = []
     lib.ug_status_string.restype = ctypes.c_char_p
     lib.ug_status_string.argtypes = [ctypes.c_int]
     lib.ug_num_variants.restype = i32
@@ -123,12 +126,19 @@ def load(build_if_missing: bool = True):
     lib.ug_mse_loss_grad_static.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.ug_render_backward.argtypes = [P(ug_plan), P(ug_gaussians), vp, vp, ctypes.c_size_t, vp,
                                        vp, vp, P(ug_gaussian_grads), vp]
+    lib.ug_render_backward_raster.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp, vp, vp, vp]
+    lib.ug_preprocess_backward.argtypes = [P(ug_plan), P(ug_gaussians), vp, ctypes.c_size_t,
+                                           P(ug_gaussian_grads), vp]
     lib.ug_adam_step.argtypes = [vp, vp, vp, vp, i32, i64, vp, vp, f32, f32, f32, vp]
     lib.ug_read_status.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp, vp]
     lib.ug_debug_views.argtypes = [P(ug_plan), vp, ctypes.c_size_t, P(vp), P(vp), P(vp), P(vp)]
     for name in EXPORTS:
+        fn = getattr(lib, name)
+        # an undeclared signature would pass Python ints as 32-bit C ints
+        if fn.argtypes is None:
+            raise RuntimeError(f"binding declares no argument types for {name}")
         if name not in ("ug_version", "ug_status_string", "ug_num_variants"):
-            getattr(lib, name).restype = ctypes.c_int
+            fn.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -224,6 +234,19 @@ def ug_render_backward(plan: ug_plan, gaussians: ug_gaussians, d_planes, ws, ima
                                      _ptr(ws), ws.numel(), _ptr(image), _ptr(alpha),
                                      _ptr(grad_image), ctypes.byref(grads), _stream(stream)),
            "ug_render_backward")
+
+
+def ug_render_backward_raster(plan: ug_plan, ws, image, alpha, grad_image, stream=None):
+    _check(load().ug_render_backward_raster(ctypes.byref(plan), _ptr(ws), ws.numel(), _ptr(image),
+                                            _ptr(alpha), _ptr(grad_image), _stream(stream)),
+           "ug_render_backward_raster")
+
+
+def ug_preprocess_backward(plan: ug_plan, gaussians: ug_gaussians, ws,
+                           grads: ug_gaussian_grads, stream=None):
+    _check(load().ug_preprocess_backward(ctypes.byref(plan), ctypes.byref(gaussians), _ptr(ws),
+                                         ws.numel(), ctypes.byref(grads), _stream(stream)),
+           "ug_preprocess_backward")
 
 
 def ug_adam_step(param, grad, exp_avg, exp_avg_sq, rows: int, n: int, d_rows, d_step,

@@ -253,6 +253,36 @@ ug_status ug_render_backward(const ug_plan* plan, const ug_gaussians* gaussians,
                                             reinterpret_cast<cudaStream_t>(stream)));
 }
 
+ug_status ug_render_backward_raster(const ug_plan* plan, void* ws, size_t ws_bytes,
+                                    const float* image, const float* alpha,
+                                    const float* grad_image, ug_stream stream) {
+  ug_status s = check_plan(plan);
+  if (s == UG_OK) s = check_ws(plan, ws, ws_bytes);
+  if (s != UG_OK) return s;
+  if (!image || !alpha || !grad_image) return UG_ERR_INVALID_ARGUMENT;
+  return cuda_status(launch_render_backward_raster(plan, make_view(plan, ws), image, alpha,
+                                                   grad_image,
+                                                   reinterpret_cast<cudaStream_t>(stream)));
+}
+
+ug_status ug_preprocess_backward(const ug_plan* plan, const ug_gaussians* gaussians, void* ws,
+                                 size_t ws_bytes, const ug_gaussian_grads* grads,
+                                 ug_stream stream) {
+  ug_status s = check_plan(plan);
+  if (s == UG_OK) s = check_ws(plan, ws, ws_bytes);
+  if (s == UG_OK) s = check_gaussians(plan, gaussians);
+  if (s != UG_OK) return s;
+  if (!grads) return UG_ERR_INVALID_ARGUMENT;
+  if (plan->n > 0) {
+    if (!grads->mean || !grads->opacity_logit || !grads->intensity) return UG_ERR_INVALID_ARGUMENT;
+    if (plan->cfg.cov_param == UG_COV_TRI && !grads->tri) return UG_ERR_INVALID_ARGUMENT;
+    if (plan->cfg.cov_param == UG_COV_SCALE_ROT && (!grads->log_scale || !grads->quat))
+      return UG_ERR_INVALID_ARGUMENT;
+  }
+  return cuda_status(launch_pre_backward(plan, gaussians, make_view(plan, ws), grads,
+                                         reinterpret_cast<cudaStream_t>(stream)));
+}
+
 ug_status ug_adam_step(float* param, const float* grad, float* exp_avg, float* exp_avg_sq,
                        int32_t rows, int64_t n, const ug_adam_row* d_rows, int32_t* d_step,
                        float beta1, float beta2, float eps, ug_stream stream) {

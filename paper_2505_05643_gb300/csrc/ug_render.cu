@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(Layout<TILE, WW, PPT>::NT)
   // lane -> reduced value index (see warp_reduce8); lanes with (lane & 3) == 0 write
   const int fidx = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
   TileCtx tc;
+  unsigned long long evaluated = 0;
   while (next_tile(v, 1, P, total_tiles, tc, &S.tile, &S.plane)) {
     const int fj0 = tc.tx * TILE + wx * WW, fi0 = tc.ty * TILE + wy * Lay::WH;
     const int j = fj0 + lx;
@@ -303,6 +304,7 @@ __global__ void __launch_bounds__(Layout<TILE, WW, PPT>::NT)
     for (uint32_t b = rg.x; b < rg.y; b += NT) {
       const int cnt = (int)min((uint32_t)NT, rg.y - b);
       const int nl = stage_batch<TILE, WW, PPT, CUT, true>(S, v, vals, b, cnt, tc.tx, tc.ty);
+      evaluated += (unsigned long long)nl;
       for (int e = 0; e < nl; ++e) {
         const uint32_t ent = S.list[warp][e];
         const int r = ent & 0x7fff;
@@ -377,6 +379,9 @@ __global__ void __launch_bounds__(Layout<TILE, WW, PPT>::NT)
       }
     }
   }
+  if (lane == 0 && evaluated)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&v.hdr->st.evaluated_pairs_bwd),
+              evaluated * (unsigned long long)(32 * PPT));
 }
 
 __global__ void k_zero_rec_grad(WsView v, int64_t cap) {
@@ -477,16 +482,23 @@ cudaError_t launch_render(const ug_plan* plan, WsView v, float* image, float* al
                           : dispatch_fwd<0>(plan, v, vals, image, alpha, s);
 }
 
+cudaError_t launch_render_backward_raster(const ug_plan* plan, WsView v, const float* image,
+                                          const float* alpha, const float* grad_image,
+                                          cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&v.hdr->tile_counter[1], 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&v.hdr->st.evaluated_pairs_bwd, 0, sizeof(int64_t), s);
+  if (e != cudaSuccess) return e;
+  k_zero_rec_grad<<<device_sms() * 4, 256, 0, s>>>(v, plan->record_capacity);
+  const uint32_t* vals = v.vals[plan->sort_passes & 1];
+  return plan->cfg.cutoff ? dispatch_bwd<1>(plan, v, vals, image, alpha, grad_image, s)
+                          : dispatch_bwd<0>(plan, v, vals, image, alpha, grad_image, s);
+}
+
 cudaError_t launch_render_backward(const ug_plan* plan, const ug_gaussians* g, WsView v,
                                    const float* image, const float* alpha,
                                    const float* grad_image, const ug_gaussian_grads* grads,
                                    cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(&v.hdr->tile_counter[1], 0, sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
-  k_zero_rec_grad<<<device_sms() * 4, 256, 0, s>>>(v, plan->record_capacity);
-  const uint32_t* vals = v.vals[plan->sort_passes & 1];
-  e = plan->cfg.cutoff ? dispatch_bwd<1>(plan, v, vals, image, alpha, grad_image, s)
-                       : dispatch_bwd<0>(plan, v, vals, image, alpha, grad_image, s);
+  const cudaError_t e = launch_render_backward_raster(plan, v, image, alpha, grad_image, s);
   if (e != cudaSuccess) return e;
   return launch_pre_backward(plan, g, v, grads, s);
 }

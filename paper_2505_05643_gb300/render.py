@@ -141,7 +141,8 @@ class Renderer:
         st = B.ug_ws_status.from_buffer_copy(self._status.numpy().tobytes())
         return dict(status=st.status, detail=st.detail, records=st.records,
                     instances=st.instances, fp64_records=st.fp64_records,
-                    box_pixels=st.box_pixels, evaluated_pairs=st.evaluated_pairs)
+                    box_pixels=st.box_pixels, evaluated_pairs=st.evaluated_pairs,
+                    evaluated_pairs_bwd=st.evaluated_pairs_bwd)
 
     def preprocess(self, params: torch.Tensor, check: bool = True, stream=None):
         assert params.shape == (self.rows, self.n) and params.dtype == torch.float32

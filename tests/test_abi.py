@@ -38,6 +38,26 @@ def test_library_exports_every_declared_symbol(lib):
         assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
 
 
+def declared_arity():
+    src = open(os.path.join(ROOT, "include", "ug.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(ug_\w+)\s*\(([^)]*)\)\s*;", src):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_declares_every_signature(lib):
+    """Every entry point has ctypes argument types with the header's arity
+    (undeclared, ctypes would pass 64-bit pointers as 32-bit ints)."""
+    arity = declared_arity()
+    assert set(arity) == set(B.EXPORTS)
+    for name, k in arity.items():
+        assert getattr(lib, name).argtypes is not None, name
+        assert len(getattr(lib, name).argtypes) == k, name
+
+
 def test_versions_and_strings(lib):
     assert B.ug_version() >= 100
     assert B.status_string(B.UG_ERR_CAPACITY).startswith("record or instance")

@@ -42,7 +42,7 @@ def _check_grads(gpu, ref, gabs, names, what):
     return float((err / tol).max())
 
 
-def _backward_case(g, pl, cfg, target, subset=None):
+def _backward_case(g, pl, cfg, target, subset=None, split=False):
     """GPU gradient with the oracle's dL/dC, C and alpha as inputs (the
     forward's own FP32 error is tested separately; dL/dw = r (c - C) is
     sensitive to C where c is close to C), against the oracle's gradient."""
@@ -53,7 +53,14 @@ def _backward_case(g, pl, cfg, target, subset=None):
     gi = torch.from_numpy(gimg.astype(np.float32)).cuda()
     im_t = torch.from_numpy(ref["image"].astype(np.float32)).cuda()
     al_t = torch.from_numpy(ref["alpha"].astype(np.float32)).cuda()
-    grads = r.backward(params, im_t, al_t, gi)
+    if split:  # rows a7 and a8 through their own entry points
+        grads = torch.empty_like(params)
+        B.ug_render_backward_raster(r.plan, r.ws, im_t, al_t, gi)
+        B.ug_preprocess_backward(r.plan, R.gaussians_struct(params, r.cov), r.ws,
+                                 R.grads_struct(grads, r.cov))
+        assert r.status()["status"] == B.UG_OK
+    else:
+        grads = r.backward(params, im_t, al_t, gi)
     torch.cuda.synchronize()
     gref, gabs, amb = oracle.render_grad(g, pl, ocfg, ref["image"], ref["alpha"], gimg,
                                          subset=subset, with_ambiguity=True)
@@ -78,6 +85,21 @@ def test_grad_small_scene(cov_param, cutoff):
     cfg = R.make_config(cov_param=cov_param, cutoff=cutoff)
     gpu, gref, gabs, _ = _backward_case(g, pl, cfg, target)
     _check_grads(gpu, gref, gabs, oracle.param_names(cov_param), f"small cov{cov_param} cut{cutoff}")
+
+
+@pytest.mark.parametrize("cov_param", [B.UG_COV_SCALE_ROT, B.UG_COV_TRI])
+def test_grad_split_entry_points(cov_param):
+    """ug_render_backward_raster followed by ug_preprocess_backward gives the
+    gradient of ug_render_backward."""
+    rng = np.random.default_rng(36)
+    g = synth.gaussians_scale_rot(rng, 1200, 0.03, 0.15)
+    if cov_param == B.UG_COV_TRI:
+        g = synth.scale_rot_to_tri(g, 1e-4)
+    pl = synth.planes_random(rng, [(64, 64), (45, 61)])
+    target = rng.uniform(0, 1, pl["total_pixels"])
+    cfg = R.make_config(cov_param=cov_param)
+    gpu, gref, gabs, _ = _backward_case(g, pl, cfg, target, split=True)
+    _check_grads(gpu, gref, gabs, oracle.param_names(cov_param), f"split cov{cov_param}")
 
 
 def test_grad_fp64_branch():
