@@ -7,6 +7,7 @@
 // take bit-identical decisions.
 #pragma once
 
+#include "ug_dd.cuh"
 #include "ug_internal.cuh"
 
 namespace ug {
@@ -52,6 +53,28 @@ __device__ __forceinline__ double rsqrt64(double x) {
   r = r * fma(-0.5 * x, r * r, 1.5);
   return r;
 }
+
+// Extended-precision reciprocal and reciprocal square root, by type.
+__device__ __forceinline__ double ext_rcp(double x) { return rcp64(x); }
+__device__ __forceinline__ double ext_rsqrt(double x) { return rsqrt64(x); }
+__device__ __forceinline__ dd ext_rcp(dd x) { return dd_rcp(x); }
+__device__ __forceinline__ dd ext_rsqrt(dd x) { return dd_rsqrt(x); }
+__device__ __forceinline__ float ext_rcp(float x) { return r_div(1.f, x); }
+__device__ __forceinline__ float ext_rsqrt(float x) { return r_div(1.f, r_sqrt(x)); }
+
+__device__ __forceinline__ int to_int(float x) { return (int)x; }
+__device__ __forceinline__ int to_int(double x) { return (int)x; }
+__device__ __forceinline__ int to_int(dd x) { return dd_to_int(x); }
+
+// Whether T is the extended-precision type of the thin-Gaussian branch.
+template <typename T>
+struct is_ext {
+  static constexpr bool value = true;
+};
+template <>
+struct is_ext<float> {
+  static constexpr bool value = false;
+};
 
 template <typename T>
 __device__ __forceinline__ T r_dot3(const T a[3], const T b[3]) {
@@ -115,10 +138,10 @@ __device__ __forceinline__ void make_factor(const GaussParams& p, float beta, Fa
     f.F[2][1] = t4;
     f.F[2][2] = r_fma(t5, t5, b);
     T i00, i11, i22;
-    if (sizeof(T) == 8) {
-      i00 = (T)rcp64((double)f.F[0][0]);
-      i11 = (T)rcp64((double)f.F[1][1]);
-      i22 = (T)rcp64((double)f.F[2][2]);
+    if constexpr (is_ext<T>::value) {
+      i00 = ext_rcp(f.F[0][0]);
+      i11 = ext_rcp(f.F[1][1]);
+      i22 = ext_rcp(f.F[2][2]);
     } else {
       i00 = r_div((T)1, f.F[0][0]);
       i11 = r_div((T)1, f.F[1][1]);
@@ -144,8 +167,8 @@ __device__ __forceinline__ void make_factor(const GaussParams& p, float beta, Fa
     const T q0 = (T)p.cp[3], q1 = (T)p.cp[4], q2 = (T)p.cp[5], q3 = (T)p.cp[6];
     const T nq2 = r_fma(q3, q3, r_fma(q2, q2, r_fma(q1, q1, r_mul(q0, q0))));
     T nq, w, x, y, z;
-    if (sizeof(T) == 8) {
-      const T rq = (T)rsqrt64((double)nq2);
+    if constexpr (is_ext<T>::value) {
+      const T rq = ext_rsqrt(nq2);
       nq = nq2 * rq;
       w = q0 * rq;
       x = q1 * rq;
@@ -284,8 +307,8 @@ __device__ __forceinline__ void pixel_range(T c, T h, T inv_pitch, T shift, int 
   }
   const T lo_c = lo < (T)0 ? (T)0 : lo;
   const T hi_c = hi > (T)(size - 1) ? (T)(size - 1) : hi;
-  a = (int)ceil(lo_c);
-  b = (int)floor(hi_c);
+  a = to_int(ceil(lo_c));
+  b = to_int(floor(hi_c));
 }
 
 // Sec. 3.3-3.4: h_k = sqrt(chi2 Sigma3D_kk); reject unless m3 - h3 <= 0 <=

@@ -211,8 +211,8 @@ __global__ void __launch_bounds__(256)
   {
     float Fi[3][3];
     if (L.use64) {
-      Factor<double> fd;
-      make_factor<double, COV>(L.prm, beta, fd);
+      Factor<dd> fd;
+      make_factor<dd, COV>(L.prm, beta, fd);
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -454,7 +454,7 @@ static void launch_pre_cov(const ug_plan* plan, const ug_gaussians* g, WsView v,
   if (chunks > 0) k_list<<<(unsigned)wblocks, 256, 0, s>>>(P, chunks, v);
   const unsigned lg = list_grid(plan->record_capacity);
   k_records<float, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.chi2, c.beta, v, 0);
-  k_records<double, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.chi2, c.beta, v, 1);
+  k_records<dd, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.chi2, c.beta, v, 1);
   const int64_t rblk = scan_blocks(plan->record_capacity);
   SlotLoad sl{v.inst_off, v.hdr};
   SlotStore ss{v.inst_off, v.hdr};
@@ -702,7 +702,7 @@ static void launch_chain_cov(const ug_plan* plan, const ug_gaussians* g, WsView 
   const ug_config& c = plan->cfg;
   const unsigned lg = list_grid(plan->record_capacity);
   k_chain<float, COV><<<lg, 256, 0, s>>>(*g, plan->n, c.chi2, c.beta, v, 0);
-  k_chain<double, COV><<<lg, 256, 0, s>>>(*g, plan->n, c.chi2, c.beta, v, 1);
+  k_chain<dd, COV><<<lg, 256, 0, s>>>(*g, plan->n, c.chi2, c.beta, v, 1);
   const int64_t chunks = plan->chunks;
   if (chunks > 0)
     k_gather<COV><<<(unsigned)((chunks * 32 + 255) / 256), 256, 0, s>>>(plan->n, plan->num_planes,

@@ -68,7 +68,7 @@ def test_extreme_anisotropy_small():
     assert abs(st["box_pixels"] - ref["pairs"]) <= 1e-3 * ref["pairs"]
 
 
-@pytest.mark.parametrize("tile,variant", [(16, v) for v in range(5)] + [(8, v) for v in range(2)])
+@pytest.mark.parametrize("tile,variant", [(16, v) for v in range(5)] + [(8, 0)])
 def test_ragged_planes_all_variants(tile, variant):
     """Planes whose sizes are not multiples of the tile (ragged tails), several
     sizes in one launch, every compiled rasterizer variant."""
