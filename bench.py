@@ -481,7 +481,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--variant", type=int, default=0, help="forward rasterizer variant")
-    ap.add_argument("--variant-bwd", type=int, default=3, help="backward rasterizer variant")
+    ap.add_argument("--variant-bwd", type=int, default=0, help="backward rasterizer variant")
     ap.add_argument("--cpu-planes", type=int, default=64, help="planes in the CPU oracle sample")
     ap.add_argument("--n", type=int, default=None, help="use the first n Gaussians (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

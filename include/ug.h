@@ -109,9 +109,12 @@ typedef struct {
   int32_t cutoff;    /* UG_CUTOFF_BOX (paper) or UG_CUTOFF_BOX_AND_ELLIPSOID */
   int32_t cov_param; /* UG_COV_TRI (paper) or UG_COV_SCALE_ROT */
   int32_t tile;      /* square tile edge in pixels: 8 or 16 (default 16) */
-  int32_t variant;   /* forward rasterizer variant (ug_num_variants); 0 = default */
-  float fp64_ratio;  /* axis-ratio proxy above which the covariance inverse runs in FP64; 1e3 */
-  int32_t variant_bwd; /* backward rasterizer variant (ug_num_variants); 0 = default */
+  int32_t variant;   /* forward rasterizer variant, 0 .. ug_num_variants(tile) - 1: lane
+                        groups per 8x8 footprint, 0 = 4 (default), 1 = 2, 2 = 1 */
+  float fp64_ratio;  /* axis-ratio proxy above which the per-(plane, Gaussian) geometry runs
+                        in extended (double-word, ~48-bit) precision; default 1e3 */
+  int32_t variant_bwd; /* backward rasterizer variant, 0 or 1: footprint height 8 (default)
+                          or 4 rows */
   int32_t reserved[2];
 } ug_config;
 
@@ -165,7 +168,8 @@ int32_t ug_version(void);
 /* Human-readable name of a status code (static string). */
 const char* ug_status_string(ug_status status);
 
-/* Number of rasterizer variants compiled in for `tile` (0 if unsupported). */
+/* Number of forward rasterizer variants compiled in for `tile` (0 if the
+ * tile size is unsupported); every supported tile has two backward variants. */
 int32_t ug_num_variants(int32_t tile);
 
 /* Fill *cfg with the defaults listed above. */

@@ -30,7 +30,7 @@ ug_status check_config(const ug_config* c) {
     return UG_ERR_INVALID_ARGUMENT;
   if (c->tile != 8 && c->tile != 16) return UG_ERR_NOT_SUPPORTED;
   if (c->variant < 0 || c->variant >= num_render_variants(c->tile)) return UG_ERR_NOT_SUPPORTED;
-  if (c->variant_bwd < 0 || c->variant_bwd >= num_render_variants(c->tile))
+  if (c->variant_bwd < 0 || c->variant_bwd >= num_render_variants_bwd(c->tile))
     return UG_ERR_NOT_SUPPORTED;
   if (!(c->fp64_ratio > 0.f)) return UG_ERR_INVALID_ARGUMENT;  // +inf disables the FP64 branch
   return UG_OK;

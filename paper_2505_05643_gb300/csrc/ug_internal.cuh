@@ -207,5 +207,6 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int32_t ro
                         const ug_adam_row* d_rows, int32_t* d_step, float b1, float b2,
                         float eps, cudaStream_t s);
 int num_render_variants(int tile);
+int num_render_variants_bwd(int tile);
 
 }  // namespace ug

@@ -113,7 +113,7 @@ def test_grad_fp64_branch():
     _check_grads(gpu, gref, gabs, oracle.param_names(0), "fp64 branch")
 
 
-@pytest.mark.parametrize("tile,variant", [(16, 1), (16, 2), (16, 3), (16, 4), (8, 0)])
+@pytest.mark.parametrize("tile,variant", [(16, 1), (8, 0), (8, 1)])
 def test_grad_variants(tile, variant):
     rng = np.random.default_rng(32)
     g = synth.gaussians_scale_rot(rng, 1000, 0.03, 0.15)

@@ -68,14 +68,14 @@ def test_extreme_anisotropy_small():
     assert abs(st["box_pixels"] - ref["pairs"]) <= 1e-3 * ref["pairs"]
 
 
-@pytest.mark.parametrize("tile,variant", [(16, v) for v in range(5)] + [(8, 0)])
+@pytest.mark.parametrize("tile,variant", [(16, v) for v in range(3)] + [(8, v) for v in range(3)])
 def test_ragged_planes_all_variants(tile, variant):
     """Planes whose sizes are not multiples of the tile (ragged tails), several
     sizes in one launch, every compiled rasterizer variant."""
     rng = np.random.default_rng(5)
     g = synth.gaussians_scale_rot(rng, 3000, 0.02, 0.15)
     pl = synth.planes_random(rng, [(70, 45), (33, 97), (128, 16), (1, 1), (17, 3)])
-    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, tile=tile, variant=variant)
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, tile=tile, variant=variant, variant_bwd=0)
     _, _, image, alpha = gpu_render(g, pl, cfg)
     ref = oracle.render(g, pl, oracle_config(cfg))
     assert_forward_parity(image, alpha, ref, f"ragged t{tile} v{variant}")
