@@ -285,11 +285,16 @@ ug_status ug_read_status(const ug_plan* plan, const void* ws, size_t ws_bytes, u
 
 /* Device pointers into the workspace, for inspection and tests: the sorted
  * tile keys and record ids (instance order), the tile ranges (uint32 pairs
- * [start, end) per tile), and the records' pixel boxes (uint32 pairs:
- * j0 | j1 << 16, i0 | i1 << 16). Valid after ug_bin_sort. */
+ * [start, end) per tile), and per record slot its pixel box (uint32 pairs:
+ * j0 | j1 << 16, i0 | i1 << 16; an empty box marks a rejected candidate), its
+ * render data a = (x*_j, x*_i, r11, r12) and b = (r22, lw2, c, ellipsoid
+ * threshold) as 4 floats each, and its plane index. Valid after ug_bin_sort;
+ * any argument may be NULL. A record is binned only to the tiles of its box in
+ * which some weight can be non-zero in FP32. */
 ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_t** sorted_keys,
                          uint32_t** sorted_records, uint32_t** tile_ranges,
-                         uint32_t** record_boxes);
+                         uint32_t** record_boxes, float** record_a, float** record_b,
+                         uint32_t** record_planes);
 
 #ifdef __cplusplus
 }

@@ -131,7 +131,8 @@ def load(build_if_missing: bool = True):
                                            P(ug_gaussian_grads), vp]
     lib.ug_adam_step.argtypes = [vp, vp, vp, vp, i32, i64, vp, vp, f32, f32, f32, vp]
     lib.ug_read_status.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp, vp]
-    lib.ug_debug_views.argtypes = [P(ug_plan), vp, ctypes.c_size_t, P(vp), P(vp), P(vp), P(vp)]
+    lib.ug_debug_views.argtypes = [P(ug_plan), vp, ctypes.c_size_t, P(vp), P(vp), P(vp), P(vp),
+                                   P(vp), P(vp), P(vp)]
     for name in EXPORTS:
         fn = getattr(lib, name)
         # an undeclared signature would pass Python ints as 32-bit C ints
@@ -263,7 +264,7 @@ def ug_read_status(plan: ug_plan, ws, out, stream=None):
 
 
 def ug_debug_views(plan: ug_plan, ws):
-    ptrs = [ctypes.c_void_p() for _ in range(4)]
+    ptrs = [ctypes.c_void_p() for _ in range(7)]
     _check(load().ug_debug_views(ctypes.byref(plan), _ptr(ws), ws.numel(),
                                  *[ctypes.byref(p) for p in ptrs]), "ug_debug_views")
     return [p.value for p in ptrs]

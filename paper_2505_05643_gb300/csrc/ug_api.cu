@@ -307,7 +307,8 @@ ug_status ug_read_status(const ug_plan* plan, const void* ws, size_t ws_bytes, u
 
 ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_t** sorted_keys,
                          uint32_t** sorted_records, uint32_t** tile_ranges,
-                         uint32_t** record_boxes) {
+                         uint32_t** record_boxes, float** record_a, float** record_b,
+                         uint32_t** record_planes) {
   ug_status s = check_plan(plan);
   if (s == UG_OK) s = check_ws(plan, ws, ws_bytes);
   if (s != UG_OK) return s;
@@ -317,6 +318,9 @@ ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_
   if (sorted_records) *sorted_records = v.vals[fin];
   if (tile_ranges) *tile_ranges = reinterpret_cast<uint32_t*>(v.ranges);
   if (record_boxes) *record_boxes = reinterpret_cast<uint32_t*>(v.rec_box);
+  if (record_a) *record_a = reinterpret_cast<float*>(v.rec_a);
+  if (record_b) *record_b = reinterpret_cast<float*>(v.rec_b);
+  if (record_planes) *record_planes = v.rec_plane;
   return UG_OK;
 }
 

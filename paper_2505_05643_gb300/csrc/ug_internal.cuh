@@ -182,6 +182,40 @@ __device__ __forceinline__ float fast_exp2(float x) {
   return y;
 }
 
+// Lower bound of q = t1^2 + t2^2 over the pixel centres of the rectangle
+// [xa, xb] x [ya, yb] (pixel indices) for a record a = (x*_j, x*_i, r11, r12),
+// r22: t1 = r11 dx + r12 dy (r11 >= 0), t2 = r22 dy (r22 >= 0), dx = j + 1/2 -
+// x*_j, dy = i + 1/2 - x*_i; (min |t1|)^2 + (min |t2|)^2 with each minimum at
+// the rectangle's corners (t1 is linear). Explicit round-to-nearest
+// intrinsics: the binning's count and emit kernels and the rasterizers take
+// the same decision from the same floats.
+__device__ __forceinline__ float rect_q_lower_bound(const float4& a, float r22, int xa, int xb,
+                                                    int ya, int yb) {
+  const float dxlo = __fsub_rn(__fadd_rn((float)xa, 0.5f), a.x);
+  const float dxhi = __fsub_rn(__fadd_rn((float)xb, 0.5f), a.x);
+  const float dylo = __fsub_rn(__fadd_rn((float)ya, 0.5f), a.y);
+  const float dyhi = __fsub_rn(__fadd_rn((float)yb, 0.5f), a.y);
+  const float a1 = __fmul_rn(a.w, dylo), a2 = __fmul_rn(a.w, dyhi);
+  const float t1min = __fmaf_rn(a.z, dxlo, fminf(a1, a2));
+  const float t1max = __fmaf_rn(a.z, dxhi, fmaxf(a1, a2));
+  const float m1 = t1min > 0.f ? t1min : (t1max < 0.f ? -t1max : 0.f);
+  const float m2 = dylo > 0.f ? __fmul_rn(r22, dylo) : (dyhi < 0.f ? -__fmul_rn(r22, dyhi) : 0.f);
+  return __fmaf_rn(m1, m1, __fmul_rn(m2, m2));
+}
+
+// Whether a record (a = rec_a, b = rec_b) can have a non-zero weight at any
+// pixel of the rectangle. Below an exponent of -126, 2^e is subnormal and
+// ex2.approx.ftz returns +0; the test uses -127, so the rounding of the bound
+// cannot drop a pixel whose weight is not exactly zero. With cut, pixels
+// beyond the ellipsoid threshold b.w are zero as well.
+__device__ __forceinline__ bool rect_live(const float4& a, const float4& b, int xa, int xb, int ya,
+                                          int yb, int cut) {
+  const float q = rect_q_lower_bound(a, b.x, xa, xb, ya, yb);
+  if (__fsub_rn(b.y, q) < -127.f) return false;
+  if (cut && q > __fmaf_rn(b.w, 1.0001f, 1e-6f)) return false;
+  return true;
+}
+
 // ------------------------------------------------------------------ launchers
 // Each translation unit exposes host launchers; all return cudaGetLastError().
 cudaError_t launch_setup_planes(const ug_plan* plan, const ug_plane* d_planes, WsView v,

@@ -300,24 +300,39 @@ __global__ void __launch_bounds__(256) k_list(int P, int64_t chunks, WsView v) {
 }
 
 // ------------------------------------------------------------------ 4. records
-__device__ __forceinline__ uint32_t tile_count(const PairBox& pb, int ts) {
-  if (!pb.visible) return 0u;
-  return (uint32_t)(((pb.j1 >> ts) - (pb.j0 >> ts) + 1) * ((pb.i1 >> ts) - (pb.i0 >> ts) + 1));
-}
 
 template <typename T>
 __device__ __forceinline__ void write_record(const PairRec<T>& rc, const PlaneDev& pl,
                                              const PairBox& pb, const GaussParams& prm,
-                                             float chi2, WsView& v, uint32_t slot) {
+                                             float chi2, WsView& v, uint32_t slot, float4& ra,
+                                             float4& rb) {
   const float xs_j = (float)(rc.xs1 * (T)pl.inv_pu + (T)pl.half_w);
   const float xs_i = (float)(rc.xs2 * (T)pl.inv_pv + (T)pl.half_h);
   const float q0 = (float)rc.q0;
   const float lw2 = log2_sigmoid(prm.logit) - kHalfLog2e * q0;
   const float ethr = kHalfLog2e * (chi2 - q0);
-  v.rec_a[slot] = make_float4(xs_j, xs_i, (float)rc.r11, (float)rc.r12);
-  v.rec_b[slot] = make_float4((float)rc.r22, lw2, prm.c, ethr);
+  ra = make_float4(xs_j, xs_i, (float)rc.r11, (float)rc.r12);
+  rb = make_float4((float)rc.r22, lw2, prm.c, ethr);
+  v.rec_a[slot] = ra;
+  v.rec_b[slot] = rb;
   v.rec_box[slot] = make_uint2((uint32_t)pb.j0 | ((uint32_t)pb.j1 << 16),
                                (uint32_t)pb.i0 | ((uint32_t)pb.i1 << 16));
+}
+
+// Tiles of a record's box in which some weight can be non-zero (the tiles
+// the record is binned to; the others hold only exact FP32 zeros).
+__device__ __forceinline__ uint32_t live_tile_count(const float4& ra, const float4& rb,
+                                                    const PairBox& pb, int ts, int cut) {
+  const int tile = 1 << ts;
+  uint32_t n = 0;
+  for (int ty = pb.i0 >> ts; ty <= (pb.i1 >> ts); ++ty) {
+    const int ya = max(pb.i0, ty * tile), yb = min(pb.i1, ty * tile + tile - 1);
+    for (int tx = pb.j0 >> ts; tx <= (pb.j1 >> ts); ++tx) {
+      const int xa = max(pb.j0, tx * tile), xb = min(pb.j1, tx * tile + tile - 1);
+      n += rect_live(ra, rb, xa, xb, ya, yb, cut) ? 1u : 0u;
+    }
+  }
+  return n;
 }
 
 __device__ __forceinline__ bool box_empty(uint2 b) {
@@ -326,7 +341,8 @@ __device__ __forceinline__ bool box_empty(uint2 b) {
 
 template <typename T, int COV>
 __global__ void __launch_bounds__(256)
-    k_records(ug_gaussians g, int64_t n, int ts, float chi2, float beta, WsView v, int part) {
+    k_records(ug_gaussians g, int64_t n, int ts, int cut, float chi2, float beta, WsView v,
+              int part) {
   if (dev_failed(v.hdr)) return;
   const uint32_t slots = v.hdr->slots, n64 = v.hdr->slots64;
   const uint32_t begin = part == 0 ? 0u : slots - n64;
@@ -348,8 +364,9 @@ __global__ void __launch_bounds__(256)
     if (pb.visible) {
       PairRec<T> rc;
       pair_record<T, COV>(f, pl, gg, rc);
-      write_record<T>(rc, pl, pb, prm, chi2, v, slot);
-      v.inst_off[slot] = tile_count(pb, ts);
+      float4 ra, rb;
+      write_record<T>(rc, pl, pb, prm, chi2, v, slot, ra, rb);
+      v.inst_off[slot] = live_tile_count(ra, rb, pb, ts, cut);
       npx += (unsigned long long)(pb.j1 - pb.j0 + 1) * (unsigned long long)(pb.i1 - pb.i0 + 1);
       kept++;
     } else {
@@ -384,26 +401,101 @@ struct SlotStore {
 };
 
 // ------------------------------------------------------------------ 5. emit
-__global__ void __launch_bounds__(256) k_emit(int ts, uint32_t inst_cap, WsView v) {
+// A warp emits the instances of 32 consecutive record slots together. The
+// box tiles of those records form one sequence (record by record, row-major
+// within a record); lane k tests tiles k, k + 32, ... of it with the same
+// live-tile test the count used, and the live ones are compacted in sequence
+// order with a ballot. Because the records' instance ranges are contiguous
+// and in the same order (the slot scan), the compacted stream lands exactly on
+// them: coalesced stores, and no lane waits for a record with many tiles.
+__global__ void __launch_bounds__(256) k_emit(int ts, int cut, uint32_t inst_cap, WsView v) {
   if (dev_failed(v.hdr)) return;
   const uint32_t slots = v.hdr->slots;
-  for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < slots;
-       slot += gridDim.x * blockDim.x) {
-    const uint2 bx = v.rec_box[slot];
-    if (box_empty(bx)) continue;
-    const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
-    const PlaneDev& pl = v.planes[v.rec_plane[slot]];
-    const int tiles_x = pl.tiles_x, toff = pl.tile_off;
-    uint32_t o = v.inst_off[slot];
-    for (int ty = i0 >> ts; ty <= (i1 >> ts); ++ty) {
-      const uint32_t row = (uint32_t)(toff + ty * tiles_x);
-      for (int tx = j0 >> ts; tx <= (j1 >> ts); ++tx) {
-        if (o < inst_cap) {
-          v.keys[0][o] = row + (uint32_t)tx;
-          v.vals[0][o] = slot;
-        }
-        ++o;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = lanemask_lt();
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; w0 < slots;
+       w0 += warps * 32u) {
+    const uint32_t slot = w0 + lane;
+    // per lane: its record's box tiles (count, first tile, tiles per box row),
+    // the plane's tile numbering, and the render data for the live test
+    uint32_t nt = 0, nx = 1, tx0 = 0, ty0 = 0, key0 = 0, tiles_x = 0;
+    uint2 bx = make_uint2(1u, 1u);
+    float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+    if (slot < slots) {
+      bx = v.rec_box[slot];
+      if (!box_empty(bx)) {
+        const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
+        const PlaneDev& pl = v.planes[v.rec_plane[slot]];
+        tx0 = (uint32_t)(j0 >> ts);
+        ty0 = (uint32_t)(i0 >> ts);
+        nx = (uint32_t)(j1 >> ts) - tx0 + 1;
+        nt = nx * ((uint32_t)(i1 >> ts) - ty0 + 1);
+        tiles_x = (uint32_t)pl.tiles_x;
+        key0 = (uint32_t)pl.tile_off + ty0 * tiles_x + tx0;
+        ra = v.rec_a[slot];
+        rb = v.rec_b[slot];
       }
+    }
+    // exclusive prefix of the box-tile counts over the lanes
+    uint32_t incl = nt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const uint32_t bpre = incl - nt;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t out = v.inst_off[w0];  // first instance of the warp's records
+    for (uint32_t kb = 0; kb < total; kb += 32u) {
+      const uint32_t k = kb + (uint32_t)lane;
+      // largest lane l with bpre[l] <= k among lanes with tiles (bpre is
+      // non-decreasing; a lane without tiles shares its successor's bpre, and
+      // the search then lands on the later lane, which has the tile)
+      int l = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t p = __shfl_sync(0xffffffffu, bpre, l + step);
+        if (p <= k) l += step;
+      }
+      const uint32_t l_pre = __shfl_sync(0xffffffffu, bpre, l);
+      const uint32_t l_nx = __shfl_sync(0xffffffffu, nx, l);
+      const uint32_t l_tx0 = __shfl_sync(0xffffffffu, tx0, l);
+      const uint32_t l_ty0 = __shfl_sync(0xffffffffu, ty0, l);
+      const uint32_t l_key0 = __shfl_sync(0xffffffffu, key0, l);
+      const uint32_t l_tiles_x = __shfl_sync(0xffffffffu, tiles_x, l);
+      const uint32_t l_bx = __shfl_sync(0xffffffffu, bx.x, l), l_by = __shfl_sync(0xffffffffu, bx.y, l);
+      float4 a, b;
+      a.x = __shfl_sync(0xffffffffu, ra.x, l);
+      a.y = __shfl_sync(0xffffffffu, ra.y, l);
+      a.z = __shfl_sync(0xffffffffu, ra.z, l);
+      a.w = __shfl_sync(0xffffffffu, ra.w, l);
+      b.x = __shfl_sync(0xffffffffu, rb.x, l);
+      b.y = __shfl_sync(0xffffffffu, rb.y, l);
+      b.w = __shfl_sync(0xffffffffu, rb.w, l);
+      b.z = 0.f;
+      bool live = false;
+      uint32_t key = 0;
+      if (k < total) {
+        const uint32_t li = k - l_pre;
+        const uint32_t dy = li / l_nx, dx = li - dy * l_nx;
+        const int tile = 1 << ts;
+        const int tx = (int)(l_tx0 + dx), ty = (int)(l_ty0 + dy);
+        const int j0 = l_bx & 0xffff, j1 = l_bx >> 16, i0 = l_by & 0xffff, i1 = l_by >> 16;
+        const int xa = max(j0, tx * tile), xb = min(j1, tx * tile + tile - 1);
+        const int ya = max(i0, ty * tile), yb = min(i1, ty * tile + tile - 1);
+        live = rect_live(a, b, xa, xb, ya, yb, cut);
+        key = l_key0 + dy * l_tiles_x + dx;
+      }
+      const uint32_t bal = __ballot_sync(0xffffffffu, live);
+      if (live) {
+        const uint32_t o = out + __popc(bal & lt);
+        if (o < inst_cap) {
+          v.keys[0][o] = key;
+          v.vals[0][o] = w0 + (uint32_t)l;
+        }
+      }
+      out += __popc(bal);
     }
   }
 }
@@ -453,8 +545,8 @@ static void launch_pre_cov(const ug_plan* plan, const ug_gaussians* g, WsView v,
         ld, st, entries, v.scan_part, v.hdr);
   if (chunks > 0) k_list<<<(unsigned)wblocks, 256, 0, s>>>(P, chunks, v);
   const unsigned lg = list_grid(plan->record_capacity);
-  k_records<float, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.chi2, c.beta, v, 0);
-  k_records<dd, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.chi2, c.beta, v, 1);
+  k_records<float, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.cutoff, c.chi2, c.beta, v, 0);
+  k_records<dd, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.cutoff, c.chi2, c.beta, v, 1);
   const int64_t rblk = scan_blocks(plan->record_capacity);
   SlotLoad sl{v.inst_off, v.hdr};
   SlotStore ss{v.inst_off, v.hdr};
@@ -463,7 +555,7 @@ static void launch_pre_cov(const ug_plan* plan, const ug_gaussians* g, WsView v,
   k_scan_top<1><<<1, 1024, 0, s>>>(v.slot_part, rblk, v.hdr, 2, plan->instance_capacity, 0);
   k_scan_down<1, SlotLoad, SlotStore><<<(unsigned)rblk, kScanThreads, 0, s>>>(
       sl, ss, plan->record_capacity, v.slot_part, v.hdr);
-  k_emit<<<lg, 256, 0, s>>>(ts, (uint32_t)plan->instance_capacity, v);
+  k_emit<<<lg, 256, 0, s>>>(ts, c.cutoff, (uint32_t)plan->instance_capacity, v);
   k_finish_pre<<<1, 32, 0, s>>>(v);
 }
 
@@ -667,16 +759,35 @@ __global__ void __launch_bounds__(256)
   float acc[12];
 #pragma unroll
   for (int q = 0; q < 12; ++q) acc[q] = 0.f;
-  for (int p = 0; p < P; ++p) {
-    const int64_t e = chunk * P + p;
-    const uint32_t mask = v.mask[e];
-    if (!((mask >> lane) & 1u)) continue;
-    const uint32_t slot = v.slot_base[e] + __popc(mask & lt);
-    const float4* src = reinterpret_cast<const float4*>(v.rec_pgrad + (size_t)slot * 12);
-    const float4 x0 = src[0], x1 = src[1], x2 = src[2];
-    acc[0] += x0.x; acc[1] += x0.y; acc[2] += x0.z; acc[3] += x0.w;
-    acc[4] += x1.x; acc[5] += x1.y; acc[6] += x1.z; acc[7] += x1.w;
-    acc[8] += x2.x; acc[9] += x2.y; acc[10] += x2.z; acc[11] += x2.w;
+  // planes in groups of kG: all loads of a group are issued before the sums
+  // (in plane order) consume them
+  constexpr int kG = 4;
+  for (int p0 = 0; p0 < P; p0 += kG) {
+    uint32_t mask[kG], base[kG];
+#pragma unroll
+    for (int q = 0; q < kG; ++q) {
+      const int64_t e = chunk * P + p0 + q;
+      mask[q] = p0 + q < P ? __ldg(v.mask + e) : 0u;
+      base[q] = p0 + q < P ? __ldg(v.slot_base + e) : 0u;
+    }
+    float4 x[kG][3];
+#pragma unroll
+    for (int q = 0; q < kG; ++q) {
+      const bool on = (mask[q] >> lane) & 1u;
+      const uint32_t slot = on ? base[q] + __popc(mask[q] & lt) : 0u;
+      const float4* src = reinterpret_cast<const float4*>(v.rec_pgrad + (size_t)slot * 12);
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      x[q][0] = on ? __ldg(src) : z;
+      x[q][1] = on ? __ldg(src + 1) : z;
+      x[q][2] = on ? __ldg(src + 2) : z;
+    }
+#pragma unroll
+    for (int q = 0; q < kG; ++q) {
+      if (!((mask[q] >> lane) & 1u)) continue;
+      acc[0] += x[q][0].x; acc[1] += x[q][0].y; acc[2] += x[q][0].z; acc[3] += x[q][0].w;
+      acc[4] += x[q][1].x; acc[5] += x[q][1].y; acc[6] += x[q][1].z; acc[7] += x[q][1].w;
+      acc[8] += x[q][2].x; acc[9] += x[q][2].y; acc[10] += x[q][2].z; acc[11] += x[q][2].w;
+    }
   }
   if (i >= n) return;
 #pragma unroll

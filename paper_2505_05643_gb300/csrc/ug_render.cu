@@ -132,19 +132,6 @@ struct Batch {
   uint32_t mask[NT];  // bit f: live for footprint f; bit 8 + f: box covers footprint f
 };
 
-// Lower bound of t1^2 + t2^2 over the rectangle [dxlo, dxhi] x [dylo, dyhi],
-// t1 = r11 dx + r12 dy (r11 >= 0), t2 = r22 dy (r22 >= 0): (min |t1|)^2 +
-// (min |t2|)^2, each minimum taken at the rectangle's corners (t1 is linear).
-__device__ __forceinline__ float min_q_lower_bound(float r11, float r12, float r22, float dxlo,
-                                                   float dxhi, float dylo, float dyhi) {
-  const float a1 = r12 * dylo, a2 = r12 * dyhi;
-  const float t1min = fmaf(r11, dxlo, fminf(a1, a2));
-  const float t1max = fmaf(r11, dxhi, fmaxf(a1, a2));
-  const float m1 = t1min > 0.f ? t1min : (t1max < 0.f ? -t1max : 0.f);
-  const float m2 = dylo > 0.f ? r22 * dylo : (dyhi < 0.f ? -r22 * dyhi : 0.f);
-  return fmaf(m1, m1, m2 * m2);
-}
-
 __device__ __forceinline__ void footprint_origin(int f, int fx_count, int fh, int tx, int ty,
                                                  int tile, int& fj0, int& fi0) {
   fj0 = tx * tile + (f % fx_count) * 8;
@@ -177,11 +164,7 @@ __device__ __forceinline__ void stage_records(Batch<NT>& B, const WsView& v,
     const int fj1 = fj0 + 7, fi1 = fi0 + FH - 1;
     const int xa = max(fj0, j0), xb = min(fj1, j1), ya = max(fi0, i0), yb = min(fi1, i1);
     if (xa > xb || ya > yb) continue;
-    const float qmin = min_q_lower_bound(a.z, a.w, c.x, (float)xa + 0.5f - a.x,
-                                         (float)xb + 0.5f - a.x, (float)ya + 0.5f - a.y,
-                                         (float)yb + 0.5f - a.y);
-    if (c.y - qmin < -127.f) continue;                   // every weight is an FP32 zero
-    if (CUT && qmin > c.w * 1.0001f + 1e-6f) continue;  // outside the ellipsoid everywhere
+    if (!rect_live(a, c, xa, xb, ya, yb, CUT)) continue;  // every weight is an FP32 zero
     m |= 1u << f;
     if (j0 <= fj0 && j1 >= fj1 && i0 <= fi0 && i1 >= fi1) m |= 1u << (8 + f);
   }
