@@ -29,10 +29,17 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# FP32-pipe operations per evaluated (pixel, record) pair in the formulation the
-# rasterizers implement (derivation in the kernels' header comments).
+# FP32-pipe operations per evaluated (pixel, record) pair, an FMA counting once:
+# the essential per-pixel arithmetic of the formulation the rasterizers
+# implement, without per-row or per-item set-up and without box masking.
+#   forward:  t1 = r11 dx + r12 dy (1, r12 dy per row), e = lw2 - t1^2 - t2^2
+#             (2, t2 per row), S_a += w (1), S_c += w c (1), dy (1)      -> 6
+#   backward: t1 (1), e (1), g = (r c - r C) w (2), sum r w (1), sum g (1),
+#             g t1 (1), sum g t1 (1), sum g t1 dx (1)                      -> 9
+# each plus one MUFU.EX2, which runs at a quarter of the FP32 rate and binds
+# only below 4 FP32 operations per pixel.
 FWD_OPS = 6
-BWD_OPS = 16
+BWD_OPS = 9
 # DRAM bytes (read + write) of one k_render_bwd launch on this workload, from a
 # one-pass ncu capture of the kernel as it stands; None when not measured.
 BWD_TRAFFIC = None
@@ -47,6 +54,29 @@ def _dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Maximum of a per-rank float over all ranks (the step time the bench
+    reports for N > 1); x itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def all_ok_over_ranks(ok: bool, device=None) -> bool:
+    """True when every rank reports ok."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return bool(ok)
+    t = torch.tensor([0 if ok else 1], dtype=torch.int32, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return int(t.item()) == 0
 
 
 def _clock_sampler(gpu_index: int, path: str):
@@ -307,11 +337,7 @@ def run_ours(args):
             sampler.wait()
             fh.close()
         sts = [B.ug_ws_status.from_buffer_copy(row.tobytes()) for row in status_log.cpu().numpy()]
-        ok = all([note(x) for x in sts])
-        if world > 1:
-            flag = torch.tensor([0 if ok else 1], device=dev)
-            torch.distributed.all_reduce(flag, op=torch.distributed.ReduceOp.MAX)
-            ok = int(flag.item()) == 0
+        ok = all_ok_over_ranks(all([note(x) for x in sts]), dev)
         if ok:
             break
         print("[bench] capacity overflow in the timed steps: resizing and measuring again",
@@ -320,11 +346,7 @@ def run_ours(args):
     else:
         raise RuntimeError("capacity overflow in the timed steps")
     clocks = _clock_summary(clk_path, t_start, t_stop)
-    ms_step = total_ms / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(total_ms / args.steps, dev)
     pairs = float(np.mean([x.box_pixels for x in sts[args.warmup:]]))
     value = pairs * world / (ms_step * 1e-3)
 
