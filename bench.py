@@ -230,9 +230,19 @@ def run_ours(args):
     targets = targets.clone()
     target = targets.cpu().numpy()
     del hid
+    params = torch.from_numpy(R.pack_params(g, B.UG_COV_TRI)).to(dev)
+    tuned = None
+    if not args.no_autotune:  # tile edge and variants chosen on this workload (untimed)
+        from paper_2505_05643_gb300 import tune
+        cfg, table = tune.autotune(n, pl, params, targets, B.UG_COV_TRI, B.UG_CUTOFF_BOX)
+        tuned = {"tile": int(cfg.tile), "variant": int(cfg.variant),
+                 "variant_bwd": int(cfg.variant_bwd),
+                 "ms": {str(k): {kk: (round(vv, 4) if isinstance(vv, float) else
+                                      [round(x, 4) for x in vv]) for kk, vv in t.items()}
+                        for k, t in table.items()}}
+        print(f"[bench] autotune: {tuned}", file=sys.stderr)
     renderer = R.Renderer(n, pl, cfg)
     r = renderer
-    params = torch.from_numpy(R.pack_params(g, B.UG_COV_TRI)).to(dev)
     step = T.TrainStep(renderer, params, targets)
     s = torch.cuda.Stream(device=dev)
     st_dev = torch.zeros(64, dtype=torch.uint8, device=dev)
@@ -476,8 +486,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "gaussians": n, "planes": len(pl["size"]),
                        "pixels": int(pl["total_pixels"]), "pairs_per_step": pairs,
-                       "tile": args.tile, "variant": args.variant,
-                       "variant_bwd": args.variant_bwd, "graph": True,
+                       "tile": int(cfg.tile), "variant": int(cfg.variant),
+                       "variant_bwd": int(cfg.variant_bwd), "autotune": tuned, "graph": True,
                        "targets": "hidden 1M-Gaussian volume (seed 1) rendered on the same planes",
                        "l2": "working set > L2 (129 MB); no flush",
                        "state": "every step starts from the initial parameters and zero Adam "
@@ -495,6 +505,209 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------- batching
+def run_train_compare(args):
+    """Training workload (200,000 Gaussians in the paper's initialisation,
+    fitted to a hidden 100,000-Gaussian volume on 32 sweep poses of 256x256 per
+    step): the batched step (all 32 planes per launch, the whole step captured
+    in one CUDA graph) against the plain form (preprocess, sort, render and
+    backward launched plane by plane, gradients summed, then Adam), from the
+    same initial state over the same pose schedule. Reports both step times,
+    the speed-up and the difference of the two loss trajectories."""
+    import torch
+    from paper_2505_05643_gb300 import binding as B
+    from paper_2505_05643_gb300 import render as R
+    from paper_2505_05643_gb300 import synth
+    from paper_2505_05643_gb300 import train as T
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    g, poses, hidden = synth.workload_train_200k()
+    n, P, pool = len(g["logit"]), 32, len(poses["size"])
+    npx = int(poses["size"][0, 0] * poses["size"][0, 1])
+    windows = [[(P * k + j) % pool for j in range(P)] for k in range(pool // P)]
+    cfg = R.make_config(cov_param=B.UG_COV_TRI)
+    # targets on every pose of the pool (untimed)
+    hid = R.Renderer(len(hidden["logit"]), poses, R.make_config(cov_param=B.UG_COV_SCALE_ROT))
+    tpool, _ = hid.forward(torch.from_numpy(R.pack_params(hidden, B.UG_COV_SCALE_ROT)).to(dev))
+    tpool = tpool.clone().view(pool, npx)
+    del hid
+    win_planes = [synth.select_planes(poses, w) for w in windows]
+    win_struct = [torch.from_numpy(synth.planes_to_struct(wp).view(np.uint8).copy()).to(dev)
+                  for wp in win_planes]
+    win_idx = [torch.tensor(w, device=dev) for w in windows]
+    # one-plane structs (pixel offset 0) for the plane-by-plane form
+    one_struct = [[torch.from_numpy(synth.planes_to_struct(synth.select_planes(wp, [p]))
+                                    .view(np.uint8).copy()).to(dev) for p in range(P)]
+                  for wp in win_planes]
+    p0 = torch.from_numpy(R.pack_params(g, B.UG_COV_TRI)).to(dev)
+    s = torch.cuda.Stream(device=dev)
+    K, W = args.steps, args.warmup
+
+    # ---- batched
+    rb = R.Renderer(n, win_planes[0], cfg)
+    targets = torch.empty(P * npx, dtype=torch.float32, device=dev)
+    step = T.TrainStep(rb, p0.clone(), targets)
+
+    def reset(st):
+        st.params.copy_(p0)
+        st.m.zero_()
+        st.v.zero_()
+        st.step.zero_()
+
+    def inputs(k, stream):
+        w = k % len(windows)
+        with torch.cuda.stream(stream):
+            rb.d_planes.copy_(win_struct[w], non_blocking=True)
+            targets.copy_(tpool.index_select(0, win_idx[w]).view(-1), non_blocking=True)
+
+    # sizing: W + K checked eager steps (the records grow as the Gaussians move),
+    # then a 25 % margin for the timed runs' slightly different trajectories
+    need = [0, 0]
+    for attempt in range(8):
+        reset(step)
+        ok = True
+        for k in range(W + K):
+            inputs(k, torch.cuda.current_stream())
+            step.enqueue()
+            st = rb.status()
+            need = [max(need[0], st["records"]), max(need[1], st["instances"])]
+            if st["status"] == B.UG_ERR_CAPACITY:
+                rb._alloc(int(need[0] * 1.3) + 4096, int(need[1] * 1.3) + 65536)
+                step.g_struct = R.gaussians_struct(step.params, rb.cov)
+                ok = False
+                break
+            assert st["status"] == B.UG_OK, st
+        if ok:
+            break
+    rb._alloc(max(int(need[0] * 1.25) + 4096, int(rb.plan.record_capacity)),
+              max(int(need[1] * 1.25) + 65536, int(rb.plan.instance_capacity)))
+    step.g_struct = R.gaussians_struct(step.params, rb.cov)
+    reset(step)
+    torch.cuda.synchronize()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        step.enqueue(s)
+    loss_b = torch.zeros(K, device=dev)
+
+    def batched_run(record):
+        reset(step)
+        torch.cuda.synchronize()
+        for k in range(K):
+            inputs(k, s)
+            with torch.cuda.stream(s):
+                graph.replay()
+                if record:
+                    loss_b[k].copy_(step.loss[0])
+
+    with torch.cuda.stream(s):
+        for k in range(W):
+            inputs(k, s)
+            graph.replay()
+    s.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    batched_run(False)  # warm
+    s.synchronize()
+    reset(step)
+    torch.cuda.synchronize()
+    e0.record(s)
+    batched_run(True)
+    e1.record(s)
+    s.synchronize()
+    ms_b = e0.elapsed_time(e1) / K
+    params_b = step.params.clone()
+    st = rb.status(s)
+    assert st["status"] == B.UG_OK, st
+
+    # ---- per plane
+    rps = [R.Renderer(n, synth.select_planes(win_planes[0], [p]), cfg) for p in range(P)]
+    params = p0.clone()
+    grads = torch.zeros_like(params)
+    gpl = torch.zeros_like(params)
+    m, v = torch.zeros_like(params), torch.zeros_like(params)
+    stp = torch.zeros(1, dtype=torch.int32, device=dev)
+    image, alpha, gimg = (torch.empty(P * npx, device=dev) for _ in range(3))
+    loss = torch.zeros(B.UG_MSE_LOSS_FLOATS, device=dev)
+    lr_rows = step.lr_rows
+    gs = R.gaussians_struct(params, B.UG_COV_TRI)
+    gps = R.grads_struct(gpl, B.UG_COV_TRI)
+
+    def plain_step(k, stream, check):
+        w = k % len(windows)
+        for p, rp in enumerate(rps):
+            rp.d_planes.copy_(one_struct[w][p], non_blocking=True)
+            if check:
+                rp.preprocess(params, check=True)
+            else:
+                B.ug_preprocess(rp.plan, gs, rp.d_planes, rp.ws, stream)
+            B.ug_bin_sort(rp.plan, rp.ws, stream)
+            B.ug_render(rp.plan, rp.ws, image[p * npx:(p + 1) * npx], alpha[p * npx:(p + 1) * npx],
+                        stream)
+        targets.copy_(tpool.index_select(0, win_idx[w]).view(-1), non_blocking=True)
+        B.ug_mse_loss_grad(image, targets, P * npx, gimg, loss, stream)
+        for p, rp in enumerate(rps):
+            B.ug_render_backward(rp.plan, gs, rp.d_planes, rp.ws, image[p * npx:(p + 1) * npx],
+                                 alpha[p * npx:(p + 1) * npx], gimg[p * npx:(p + 1) * npx], gps,
+                                 stream)
+            if p == 0:
+                grads.copy_(gpl)
+            else:
+                grads.add_(gpl)
+        B.ug_adam_step(params, grads, m, v, rb.rows, n, lr_rows, stp, T.BETA1, T.BETA2, T.EPS,
+                       stream)
+
+    def plain_reset():
+        params.copy_(p0)
+        m.zero_()
+        v.zero_()
+        stp.zero_()
+
+    plain_reset()
+    for k in range(W + K):  # sizing (checked) and warm-up
+        plain_step(k, torch.cuda.current_stream(), True)
+    for rp in rps:  # margin for the timed run's slightly different trajectory
+        rp._alloc(int(rp.plan.record_capacity * 1.25) + 1024,
+                  int(rp.plan.instance_capacity * 1.25) + 4096)
+    gs = R.gaussians_struct(params, B.UG_COV_TRI)
+    plain_reset()
+    torch.cuda.synchronize()
+    loss_p = torch.zeros(K, device=dev)
+    with torch.cuda.stream(s):
+        e0.record(s)
+        for k in range(K):
+            plain_step(k, s, False)
+            loss_p[k].copy_(loss[0])
+        e1.record(s)
+    s.synchronize()
+    ms_p = e0.elapsed_time(e1) / K
+    for rp in rps:
+        st = rp.status(s)
+        assert st["status"] == B.UG_OK, st
+    lb, lp = loss_b.cpu().numpy(), loss_p.cpu().numpy()
+    dparam = float((params_b - params).abs().max())
+    moved = float((params_b - p0).abs().max())
+    line = {
+        "metric": "train steps/s, 200k Gaussians, 32 planes of 256x256: batched graph vs "
+                  "one plane per launch",
+        "value": 1e3 / ms_b, "unit": "steps/s", "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": ms_b, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "train_200k: 200,000 Gaussians (paper init), hidden 100,000-"
+                               "Gaussian volume (seed 2), 160 sweep poses, 32 per step",
+                   "tile": int(cfg.tile), "variant": int(cfg.variant),
+                   "variant_bwd": int(cfg.variant_bwd)},
+        "per_plane": {"ms_per_step": ms_p, "steps_per_s": 1e3 / ms_p,
+                      "form": "eager: per plane preprocess, sort, render; one MSE; per plane "
+                              "backward with the gradients summed; Adam"},
+        "speedup": ms_p / ms_b,
+        "accuracy": {"loss_first": [float(lb[0]), float(lp[0])],
+                     "loss_last": [float(lb[-1]), float(lp[-1])],
+                     "max_rel_loss_diff": float(np.max(np.abs(lb - lp) / np.abs(lp))),
+                     "max_param_diff": dparam, "max_param_change": moved},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -507,11 +720,17 @@ def main():
     ap.add_argument("--cpu-planes", type=int, default=64, help="planes in the CPU oracle sample")
     ap.add_argument("--n", type=int, default=None, help="use the first n Gaussians (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="aniso_1m", choices=["aniso_1m", "train_200k"],
+                    help="train_200k: batched graph step against one plane per launch")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use --tile/--variant/--variant-bwd instead of the autotuner's choice")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "train_200k":
+        return run_train_compare(args)
     return run_ours(args)
 
 

@@ -273,3 +273,17 @@ def workload_aniso_1m(seed: int = 0, n: int = 1_000_000, P: int = 64):
     sizes = rng.choice(np.array(RAGGED_SIZES), size=P)
     planes = planes_random(rng, [(int(s), int(s)) for s in sizes])
     return g, planes
+
+
+def workload_train_200k(seed: int = 0, n: int = 200_000, hidden_n: int = 100_000,
+                        pool: int = 160, size: int = 256):
+    """Training workload: 200,000 Gaussians in the paper's initialisation
+    (Sec. 3.4), a hidden 100,000-Gaussian target volume drawn with seed 2 from
+    the fwd_2k distributions, and a pool of 160 sweep poses of size x size
+    pixels; a training step takes 32 consecutive poses of the pool (cyclic).
+    Returns (gaussians, pose pool, hidden gaussians)."""
+    rng = np.random.default_rng(seed)
+    g = gaussians_paper_init(rng, n)
+    poses = planes_sweep_pool(rng, pool, (size, size))
+    hidden = gaussians_scale_rot(np.random.default_rng(2), hidden_n)
+    return g, poses, hidden
