@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -41,8 +42,9 @@ sys.path.insert(0, ROOT)
 FWD_OPS = 6
 BWD_OPS = 9
 # DRAM bytes (read + write) of one k_render_bwd launch on this workload, from a
-# one-pass ncu capture of the kernel as it stands; None when not measured.
-BWD_TRAFFIC = None
+# one-pass ncu capture of the kernel as it stands; None when the kernel has
+# changed since.
+BWD_TRAFFIC = 449278464
 
 METRIC = "Gaussian·pixel evals/s and fwd+bwd train steps/s, 1M Gaussians, 1×GB300"
 WORKLOAD = "aniso_1m: 1,000,000 Gaussians, axis ratios log-uniform to 1e4, 64 planes/launch " \
@@ -307,8 +309,7 @@ def run_ours(args):
     # ---- timed region: K replays of the captured step after W warm-up replays.
     # The backward's atomics make the trajectory differ slightly from the sizing
     # run's; a capacity overflow in the timed steps resizes and measures again.
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                            f".bench_clocks_{rank}.csv")
+    clk_path = os.path.join(tempfile.gettempdir(), f"ug_bench_clocks_{os.getpid()}_{rank}.csv")
     status_log = torch.zeros((args.warmup + args.steps, 64), dtype=torch.uint8, device=dev)
     for attempt in range(3):
         restore()

@@ -40,7 +40,9 @@ CHI2_95_PRINTED = 7.815  # Sec. 3.3: chi^2 for 3 DoF at p = 95 %, as printed
 
 @dataclass
 class Config:
-    """Cut-off and image-formation constants (see the design doc readings)."""
+    """Cut-off and image-formation constants: chi2 = 7.815 as printed (Sec. 3.3);
+    beta, alpha_bg and c_bg are not printed in the paper and take the values
+    1e-4, 1e-3 and 0; cutoff 0 is the paper's box, 1 adds the ellipsoid."""
     chi2: float = CHI2_95_PRINTED
     beta: float = 1e-4
     alpha_bg: float = 1e-3

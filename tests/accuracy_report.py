@@ -1,0 +1,122 @@
+"""Error of every output of the CUDA path against the FP64 oracle, per
+workload: the forward image and alpha (per pixel) and the gradient of every
+parameter row (per Gaussian), as max absolute error, max error relative to the
+stated tolerance, and the fraction within it. Pixels and Gaussians with an
+inclusion decision within rounding of an edge (where either decision is
+correct) are counted apart.
+
+Run on a GPU from the repository root:
+
+    python tests/accuracy_report.py [--out REPORT.md]
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
+
+import oracle  # noqa: E402
+from gpu_helpers import ATOL, RTOL, forward_bound, gpu_render, oracle_config  # noqa: E402
+from paper_2505_05643_gb300 import binding as B  # noqa: E402
+from paper_2505_05643_gb300 import render as R  # noqa: E402
+from paper_2505_05643_gb300 import synth  # noqa: E402
+
+GRAD_RTOL, GRAD_FLOOR = 1e-3, 1e-4  # as in the backward parity tests
+
+
+def forward_rows(name, image, alpha, ref):
+    img_tol, alp_tol = forward_bound(ref)
+    amb = ref["amb"] > 0
+    rows = []
+    for what, got, exp, tol in (("image C", image, ref["image"], img_tol),
+                                ("alpha S_a + a_bg", alpha, ref["alpha"], alp_tol)):
+        err = np.abs(got - exp)
+        rows.append((name, what, got.size, int(amb.sum()), float(err.max()),
+                     float((err / tol).max()), float((err <= tol).mean())))
+    return rows
+
+
+def grad_rows(name, grads_t, cov_param, gref, gabs, amb, subset=None):
+    gpu = grads_t.cpu().numpy().astype(np.float64).T
+    if subset is not None:
+        gpu = gpu[subset]
+    keep = ~amb
+    rows = []
+    for k, pname in enumerate(oracle.param_names(cov_param)):
+        a, b, s = gpu[keep, k], gref[keep, k], gabs[keep, k]
+        tol = GRAD_RTOL * np.abs(b) + GRAD_FLOOR * s + 1e-30
+        err = np.abs(a - b)
+        rows.append((name, f"dL/d{pname}", int(keep.sum()), int(amb.sum()), float(err.max()),
+                     float((err / tol).max()), float((err <= tol).mean())))
+    return rows
+
+
+def case(name, g, pl, cfg, target_seed=7, subset=None):
+    ocfg = oracle_config(cfg)
+    ref = oracle.render(g, pl, ocfg)
+    r, params, image, alpha = gpu_render(g, pl, cfg)
+    rows = forward_rows(name, image, alpha, ref)
+    tgt = np.random.default_rng(target_seed).uniform(0, 1, pl["total_pixels"])
+    _, gimg = oracle.mse_loss_grad(ref["image"], tgt)
+    gi = torch.from_numpy(gimg.astype(np.float32)).cuda()
+    im_t = torch.from_numpy(ref["image"].astype(np.float32)).cuda()
+    al_t = torch.from_numpy(ref["alpha"].astype(np.float32)).cuda()
+    grads = r.backward(params, im_t, al_t, gi)
+    torch.cuda.synchronize()
+    gref, gabs, amb = oracle.render_grad(g, pl, ocfg, ref["image"], ref["alpha"], gimg,
+                                         subset=subset, with_ambiguity=True)
+    rows += grad_rows(name, grads, int(cfg.cov_param), gref, gabs, amb, subset)
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+    t0 = time.time()
+    rows = []
+    g, pl = synth.workload_fwd_2k()
+    for cov, tag in ((B.UG_COV_SCALE_ROT, "scale/rot"), (B.UG_COV_TRI, "tri")):
+        gg = synth.scale_rot_to_tri(g, 1e-4) if cov == B.UG_COV_TRI else g
+        rows += case(f"fwd_2k {tag}", gg, pl, R.make_config(cov_param=cov))
+    g, pl = synth.workload_grad_50k()
+    sub = np.random.default_rng(0).choice(len(g["logit"]), 500, replace=False)
+    rows += case("grad_50k scale/rot (500 Gaussians)", g, pl,
+                 R.make_config(cov_param=B.UG_COV_SCALE_ROT), subset=sub)
+    g, pl = synth.workload_aniso_1m()
+    g = synth.scale_rot_to_tri(g, 1e-4)
+    pl4 = synth.select_planes(pl, [0, 1, 2, 3])
+    sub = np.random.default_rng(0).choice(len(g["logit"]), 2000, replace=False)
+    rows += case("aniso_1m tri, planes 0-3 (2000 Gaussians)", g, pl4,
+                 R.make_config(cov_param=B.UG_COV_TRI), subset=sub)
+    lines = ["| workload | output | n compared | n ambiguous (either decision valid) | max abs err | "
+             "max err / tolerance | fraction within tolerance |", "|---|---|---|---|---|---|---|"]
+    for w, o, n, na, e, et, f in rows:
+        lines.append(f"| {w} | {o} | {n} | {na} | {e:.3e} | {et:.3g} | {f:.5f} |")
+    text = "\n".join(lines)
+    print(text)
+    print(f"({time.time() - t0:.0f} s)")
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write("# Error of every output against the FP64 oracle (GB300)\n\n")
+            f.write("Command (GB300, from the repository root, after `python -c \"import "
+                    "__graft_entry__ as g; g.build()\"`):\n\n")
+            f.write(f"```\npython tests/accuracy_report.py --out {args.out}\n```\n\n")
+            f.write(f"Tolerances: image and alpha |err| <= {ATOL:g} + {RTOL:g} |ref| (plus the "
+                    "bounded effect of ambiguous edge decisions); gradients |err| <= "
+                    f"{GRAD_RTOL:g} |ref| + {GRAD_FLOOR:g} sum |per-pair term| (Gaussians with "
+                    "an ambiguous decision excluded). The GPU gradient is evaluated with the "
+                    "oracle's image and alpha as inputs, so it isolates the backward's error.\n\n")
+            f.write(text + "\n")
+
+
+if __name__ == "__main__":
+    main()
