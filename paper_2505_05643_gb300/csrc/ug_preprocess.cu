@@ -319,22 +319,6 @@ __device__ __forceinline__ void write_record(const PairRec<T>& rc, const PlaneDe
                                (uint32_t)pb.i0 | ((uint32_t)pb.i1 << 16));
 }
 
-// Tiles of a record's box in which some weight can be non-zero (the tiles
-// the record is binned to; the others hold only exact FP32 zeros).
-__device__ __forceinline__ uint32_t live_tile_count(const float4& ra, const float4& rb,
-                                                    const PairBox& pb, int ts, int cut) {
-  const int tile = 1 << ts;
-  uint32_t n = 0;
-  for (int ty = pb.i0 >> ts; ty <= (pb.i1 >> ts); ++ty) {
-    const int ya = max(pb.i0, ty * tile), yb = min(pb.i1, ty * tile + tile - 1);
-    for (int tx = pb.j0 >> ts; tx <= (pb.j1 >> ts); ++tx) {
-      const int xa = max(pb.j0, tx * tile), xb = min(pb.j1, tx * tile + tile - 1);
-      n += rect_live(ra, rb, xa, xb, ya, yb, cut) ? 1u : 0u;
-    }
-  }
-  return n;
-}
-
 __device__ __forceinline__ bool box_empty(uint2 b) {
   return (b.x & 0xffffu) > (b.x >> 16) || (b.y & 0xffffu) > (b.y >> 16);
 }
@@ -366,12 +350,10 @@ __global__ void __launch_bounds__(256)
       pair_record<T, COV>(f, pl, gg, rc);
       float4 ra, rb;
       write_record<T>(rc, pl, pb, prm, chi2, v, slot, ra, rb);
-      v.inst_off[slot] = live_tile_count(ra, rb, pb, ts, cut);
       npx += (unsigned long long)(pb.j1 - pb.j0 + 1) * (unsigned long long)(pb.i1 - pb.i0 + 1);
       kept++;
     } else {
       v.rec_box[slot] = make_uint2(1u, 1u);  // empty: j0 = 1 > j1 = 0
-      v.inst_off[slot] = 0u;
       holes++;
     }
   }
@@ -401,101 +383,213 @@ struct SlotStore {
 };
 
 // ------------------------------------------------------------------ 5. emit
-// A warp emits the instances of 32 consecutive record slots together. The
-// box tiles of those records form one sequence (record by record, row-major
-// within a record); lane k tests tiles k, k + 32, ... of it with the same
-// live-tile test the count used, and the live ones are compacted in sequence
-// order with a ballot. Because the records' instance ranges are contiguous
-// and in the same order (the slot scan), the compacted stream lands exactly on
-// them: coalesced stores, and no lane waits for a record with many tiles.
-__global__ void __launch_bounds__(256) k_emit(int ts, int cut, uint32_t inst_cap, WsView v) {
+// Box-tile geometry of one record slot, for the live-tile pass and the emit.
+struct SlotTiles {
+  uint32_t nt, nx, tx0, ty0;  // box tiles, tiles per box row, first tile column and row
+  uint2 bx;                   // pixel box
+};
+
+__device__ __forceinline__ SlotTiles slot_tiles(uint2 bx, int ts) {
+  SlotTiles q{0u, 1u, 0u, 0u, bx};
+  if (!box_empty(bx)) {
+    const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
+    q.tx0 = (uint32_t)(j0 >> ts);
+    q.ty0 = (uint32_t)(i0 >> ts);
+    q.nx = (uint32_t)(j1 >> ts) - q.tx0 + 1;
+    q.nt = q.nx * ((uint32_t)(i1 >> ts) - q.ty0 + 1);
+  }
+  return q;
+}
+
+// Whether box tile k (row-major within the record's box) can hold a non-zero
+// weight of the record.
+__device__ __forceinline__ bool box_tile_live(const float4& a, const float4& b, uint2 bx,
+                                              uint32_t nx, uint32_t tx0, uint32_t ty0, uint32_t k,
+                                              int ts, int cut) {
+  const uint32_t dy = k / nx, dx = k - dy * nx;
+  const int tile = 1 << ts, tx = (int)(tx0 + dx), ty = (int)(ty0 + dy);
+  const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
+  return rect_live(a, b, max(j0, tx * tile), min(j1, tx * tile + tile - 1), max(i0, ty * tile),
+                   min(i1, ty * tile + tile - 1), cut);
+}
+
+// Largest lane l whose non-decreasing per-lane value pre[l] is <= o.
+__device__ __forceinline__ int warp_search(uint32_t pre, uint32_t o) {
+  int l = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const uint32_t p = __shfl_sync(0xffffffffu, pre, l + step);
+    if (p <= o) l += step;
+  }
+  return l;
+}
+
+// Position of the n-th (0-based) set bit of m (which has more than n set bits).
+__device__ __forceinline__ uint32_t nth_set_bit(unsigned long long m, uint32_t n) {
+  uint32_t pos = 0;
+#pragma unroll
+  for (int w = 32; w >= 1; w >>= 1) {
+    const uint32_t c = (uint32_t)__popcll(m & ((1ull << w) - 1ull));
+    if (n >= c) {
+      n -= c;
+      m >>= w;
+      pos += (uint32_t)w;
+    }
+  }
+  return pos;
+}
+
+constexpr uint32_t kMaskTiles = 64;  // boxes up to this many tiles keep their live-tile mask
+
+// Live-tile pass, one warp per 32 consecutive record slots. The box tiles of
+// those records form one sequence (record by record, row-major within a
+// record); lane k tests tiles k, k + 32, ... of it (no lane waits for a record
+// with many tiles), and every record's lane collects the ballot bits of its own
+// tiles: the count of its live tiles (inst_off, scanned next into the first
+// instance) and, for a box of at most 64 tiles, which ones (kept in the
+// per-record gradient scratch, unused until the backward, for the emit).
+__global__ void __launch_bounds__(256) k_live(int ts, int cut, WsView v) {
+  __shared__ float4 s_a[8][32], s_b[8][32];
+  __shared__ uint4 s_t[8][32];
   if (dev_failed(v.hdr)) return;
   const uint32_t slots = v.hdr->slots;
-  const int lane = threadIdx.x & 31;
-  const uint32_t lt = lanemask_lt();
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long* live_mask = reinterpret_cast<unsigned long long*>(v.rec_pgrad);
   for (uint32_t w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; w0 < slots;
        w0 += warps * 32u) {
     const uint32_t slot = w0 + lane;
-    // per lane: its record's box tiles (count, first tile, tiles per box row),
-    // the plane's tile numbering, and the render data for the live test
-    uint32_t nt = 0, nx = 1, tx0 = 0, ty0 = 0, key0 = 0, tiles_x = 0;
-    uint2 bx = make_uint2(1u, 1u);
-    float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+    SlotTiles q = slot_tiles(make_uint2(1u, 1u), ts);
     if (slot < slots) {
-      bx = v.rec_box[slot];
-      if (!box_empty(bx)) {
-        const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
-        const PlaneDev& pl = v.planes[v.rec_plane[slot]];
-        tx0 = (uint32_t)(j0 >> ts);
-        ty0 = (uint32_t)(i0 >> ts);
-        nx = (uint32_t)(j1 >> ts) - tx0 + 1;
-        nt = nx * ((uint32_t)(i1 >> ts) - ty0 + 1);
-        tiles_x = (uint32_t)pl.tiles_x;
-        key0 = (uint32_t)pl.tile_off + ty0 * tiles_x + tx0;
-        ra = v.rec_a[slot];
-        rb = v.rec_b[slot];
+      q = slot_tiles(v.rec_box[slot], ts);
+      if (q.nt) {
+        s_a[wl][lane] = v.rec_a[slot];
+        s_b[wl][lane] = v.rec_b[slot];
       }
     }
-    // exclusive prefix of the box-tile counts over the lanes
-    uint32_t incl = nt;
+    s_t[wl][lane] = make_uint4(q.bx.x, q.bx.y, q.nx | (q.tx0 << 16), q.ty0);
+    uint32_t incl = q.nt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += t;
     }
-    const uint32_t bpre = incl - nt;
+    const uint32_t bpre = incl - q.nt;
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    uint32_t out = v.inst_off[w0];  // first instance of the warp's records
+    __syncwarp();
+    uint32_t cnt = 0;
+    unsigned long long mask = 0;
     for (uint32_t kb = 0; kb < total; kb += 32u) {
       const uint32_t k = kb + (uint32_t)lane;
-      // largest lane l with bpre[l] <= k among lanes with tiles (bpre is
-      // non-decreasing; a lane without tiles shares its successor's bpre, and
-      // the search then lands on the later lane, which has the tile)
-      int l = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t p = __shfl_sync(0xffffffffu, bpre, l + step);
-        if (p <= k) l += step;
-      }
-      const uint32_t l_pre = __shfl_sync(0xffffffffu, bpre, l);
-      const uint32_t l_nx = __shfl_sync(0xffffffffu, nx, l);
-      const uint32_t l_tx0 = __shfl_sync(0xffffffffu, tx0, l);
-      const uint32_t l_ty0 = __shfl_sync(0xffffffffu, ty0, l);
-      const uint32_t l_key0 = __shfl_sync(0xffffffffu, key0, l);
-      const uint32_t l_tiles_x = __shfl_sync(0xffffffffu, tiles_x, l);
-      const uint32_t l_bx = __shfl_sync(0xffffffffu, bx.x, l), l_by = __shfl_sync(0xffffffffu, bx.y, l);
-      float4 a, b;
-      a.x = __shfl_sync(0xffffffffu, ra.x, l);
-      a.y = __shfl_sync(0xffffffffu, ra.y, l);
-      a.z = __shfl_sync(0xffffffffu, ra.z, l);
-      a.w = __shfl_sync(0xffffffffu, ra.w, l);
-      b.x = __shfl_sync(0xffffffffu, rb.x, l);
-      b.y = __shfl_sync(0xffffffffu, rb.y, l);
-      b.w = __shfl_sync(0xffffffffu, rb.w, l);
-      b.z = 0.f;
+      const int l = warp_search(bpre, k);
+      const uint32_t lpre = __shfl_sync(0xffffffffu, bpre, l);
       bool live = false;
-      uint32_t key = 0;
       if (k < total) {
-        const uint32_t li = k - l_pre;
-        const uint32_t dy = li / l_nx, dx = li - dy * l_nx;
-        const int tile = 1 << ts;
-        const int tx = (int)(l_tx0 + dx), ty = (int)(l_ty0 + dy);
-        const int j0 = l_bx & 0xffff, j1 = l_bx >> 16, i0 = l_by & 0xffff, i1 = l_by >> 16;
-        const int xa = max(j0, tx * tile), xb = min(j1, tx * tile + tile - 1);
-        const int ya = max(i0, ty * tile), yb = min(i1, ty * tile + tile - 1);
-        live = rect_live(a, b, xa, xb, ya, yb, cut);
-        key = l_key0 + dy * l_tiles_x + dx;
+        const uint4 t4 = s_t[wl][l];
+        live = box_tile_live(s_a[wl][l], s_b[wl][l], make_uint2(t4.x, t4.y), t4.z & 0xffffu,
+                             t4.z >> 16, t4.w, k - lpre, ts, cut);
       }
       const uint32_t bal = __ballot_sync(0xffffffffu, live);
-      if (live) {
-        const uint32_t o = out + __popc(bal & lt);
-        if (o < inst_cap) {
-          v.keys[0][o] = key;
-          v.vals[0][o] = w0 + (uint32_t)l;
-        }
+      // this lane's record: its tiles in this window, [lo, hi) of the sequence
+      const uint32_t lo = max(bpre, kb), hi = min(bpre + q.nt, kb + 32u);
+      if (lo < hi) {
+        const uint32_t len = hi - lo;
+        const uint32_t bits = (bal >> (lo - kb)) & (len == 32u ? 0xffffffffu : ((1u << len) - 1u));
+        cnt += (uint32_t)__popc(bits);
+        if (q.nt <= kMaskTiles) mask |= (unsigned long long)bits << (lo - bpre);
       }
-      out += __popc(bal);
+    }
+    if (slot < slots) {
+      v.inst_off[slot] = cnt;
+      live_mask[slot] = mask;
+    }
+    __syncwarp();
+  }
+}
+
+// A warp emits the instances of 32 consecutive record slots together: their
+// instances form one contiguous range (the slot scan), so lane k writes
+// instances k, k + 32, ... of the range (coalesced stores, no lane waits for
+// a record with many tiles); a record's live tiles come from its mask. The
+// few records with more than 64 box tiles are emitted after, one at a time, by
+// the whole warp re-testing their box tiles 32 at a time.
+__global__ void __launch_bounds__(256) k_emit(int ts, int cut, uint32_t inst_cap, WsView v) {
+  if (dev_failed(v.hdr)) return;
+  const uint32_t slots = v.hdr->slots;
+  const uint32_t n_inst = (uint32_t)v.hdr->st.instances;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = lanemask_lt();
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  const unsigned long long* live_mask = reinterpret_cast<const unsigned long long*>(v.rec_pgrad);
+  for (uint32_t w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; w0 < slots;
+       w0 += warps * 32u) {
+    const uint32_t slot = w0 + lane;
+    // per lane: first instance (UINT32_MAX past the last slot, so the search
+    // never picks it), live count, box tiles, key of the first box tile
+    uint32_t pre = 0xffffffffu, cnt = 0, key0 = 0, tiles_x = 0;
+    SlotTiles q = slot_tiles(make_uint2(1u, 1u), ts);
+    unsigned long long mask = 0;
+    if (slot < slots) {
+      pre = v.inst_off[slot];
+      const uint32_t nxt = slot + 1 < slots ? v.inst_off[slot + 1] : n_inst;
+      cnt = nxt - pre;
+      if (cnt) {
+        q = slot_tiles(v.rec_box[slot], ts);
+        const PlaneDev& pl = v.planes[v.rec_plane[slot]];
+        tiles_x = (uint32_t)pl.tiles_x;
+        key0 = (uint32_t)pl.tile_off + q.ty0 * tiles_x + q.tx0;
+        mask = live_mask[slot];
+      }
+    }
+    const int last = (int)min(31u, slots - 1u - w0);
+    const uint32_t base = __shfl_sync(0xffffffffu, pre, 0);
+    const uint32_t end = __shfl_sync(0xffffffffu, pre + cnt, last);
+    for (uint32_t kb = base; kb < end; kb += 32u) {
+      const uint32_t o = kb + (uint32_t)lane;
+      const int l = warp_search(pre, o);
+      const uint32_t l_pre = __shfl_sync(0xffffffffu, pre, l);
+      const uint32_t l_nt = __shfl_sync(0xffffffffu, q.nt, l);
+      const uint32_t l_nx = __shfl_sync(0xffffffffu, q.nx, l);
+      const uint32_t l_key0 = __shfl_sync(0xffffffffu, key0, l);
+      const uint32_t l_tx = __shfl_sync(0xffffffffu, tiles_x, l);
+      const unsigned long long l_mask = __shfl_sync(0xffffffffu, mask, l);
+      if (o < end && l_nt <= kMaskTiles && o < inst_cap) {
+        const uint32_t pos = nth_set_bit(l_mask, o - l_pre);
+        const uint32_t dy = pos / l_nx, dx = pos - dy * l_nx;
+        v.keys[0][o] = l_key0 + dy * l_tx + dx;
+        v.vals[0][o] = w0 + (uint32_t)l;
+      }
+    }
+    // records with more boxes tiles than a mask holds
+    uint32_t big = __ballot_sync(0xffffffffu, cnt > 0 && q.nt > kMaskTiles);
+    while (big) {
+      const int r = __ffs(big) - 1;
+      big &= big - 1;
+      const uint32_t r_slot = w0 + (uint32_t)r;
+      const uint32_t r_nt = __shfl_sync(0xffffffffu, q.nt, r);
+      const uint32_t r_nx = __shfl_sync(0xffffffffu, q.nx, r);
+      const uint32_t r_tx0 = __shfl_sync(0xffffffffu, q.tx0, r);
+      const uint32_t r_ty0 = __shfl_sync(0xffffffffu, q.ty0, r);
+      const uint32_t r_key0 = __shfl_sync(0xffffffffu, key0, r);
+      const uint32_t r_tx = __shfl_sync(0xffffffffu, tiles_x, r);
+      const uint2 r_bx = make_uint2(__shfl_sync(0xffffffffu, q.bx.x, r),
+                                    __shfl_sync(0xffffffffu, q.bx.y, r));
+      const float4 a = v.rec_a[r_slot], b = v.rec_b[r_slot];
+      uint32_t out = __shfl_sync(0xffffffffu, pre, r);
+      for (uint32_t kb = 0; kb < r_nt; kb += 32u) {
+        const uint32_t k = kb + (uint32_t)lane;
+        const bool live = k < r_nt && box_tile_live(a, b, r_bx, r_nx, r_tx0, r_ty0, k, ts, cut);
+        const uint32_t bal = __ballot_sync(0xffffffffu, live);
+        if (live) {
+          const uint32_t o = out + (uint32_t)__popc(bal & lt);
+          if (o < inst_cap) {
+            const uint32_t dy = k / r_nx, dx = k - dy * r_nx;
+            v.keys[0][o] = r_key0 + dy * r_tx + dx;
+            v.vals[0][o] = r_slot;
+          }
+        }
+        out += (uint32_t)__popc(bal);
+      }
     }
   }
 }
@@ -547,6 +641,7 @@ static void launch_pre_cov(const ug_plan* plan, const ug_gaussians* g, WsView v,
   const unsigned lg = list_grid(plan->record_capacity);
   k_records<float, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.cutoff, c.chi2, c.beta, v, 0);
   k_records<dd, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.cutoff, c.chi2, c.beta, v, 1);
+  k_live<<<lg, 256, 0, s>>>(ts, c.cutoff, v);
   const int64_t rblk = scan_blocks(plan->record_capacity);
   SlotLoad sl{v.inst_off, v.hdr};
   SlotStore ss{v.inst_off, v.hdr};

@@ -65,8 +65,8 @@ class TrainStep:
 
     def kernels_per_step(self) -> int:
         """Kernels of this library launched by one step (memsets excluded)."""
-        # preprocess: planes, cull, 3 scan, list, 2 records, 3 scan, emit, finish
-        pre = 13
+        # preprocess: planes, cull, 3 scan, list, 2 records, live tiles, 3 scan, emit, finish
+        pre = 14
         sort = 5 * int(self.r.plan.sort_passes) + 1  # per pass: hist, 3 scan, scatter; ranges
         # render 1, mse 2, backward: zero, raster, 2 chain, gather = 5, adam 2
         return pre + sort + 1 + 2 + 5 + 2
