@@ -709,6 +709,63 @@ def run_train_compare(args):
     return 0
 
 
+# ---------------------------------------------------------------- ablation
+def run_scatter_ablation(args):
+    """Forward of the bench workload two ways from the same records: the tile
+    gather (bin + sort + ug_render) against the paper's phase-2 atomic scatter
+    (ug_render_scatter, no binning); times, speed-up and image difference."""
+    import torch
+    from paper_2505_05643_gb300 import binding as B
+    from paper_2505_05643_gb300 import render as R
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    g, pl, _ = _workload(args.n)
+    cfg = R.make_config(cov_param=B.UG_COV_TRI, cutoff=B.UG_CUTOFF_BOX, tile=args.tile,
+                        variant=args.variant, variant_bwd=args.variant_bwd)
+    n = len(g["logit"])
+    r = R.Renderer(n, pl, cfg)
+    params = torch.from_numpy(R.pack_params(g, B.UG_COV_TRI)).to(dev)
+    st = r.preprocess(params, check=True)
+    s = torch.cuda.current_stream()
+    im_g, al_g, im_s, al_s = (r.new_image() for _ in range(4))
+
+    def gather():
+        B.ug_bin_sort(r.plan, r.ws, s)
+        B.ug_render(r.plan, r.ws, im_g, al_g, s)
+
+    def scatter():
+        B.ug_render_scatter(r.plan, r.ws, im_s, al_s, s)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            fn()
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_g, ms_s = timed(gather), timed(scatter)
+    st2 = r.status()
+    assert st2["status"] == B.UG_OK, st2
+    d = (im_g - im_s).abs()
+    line = {
+        "metric": "forward of the bench workload: tile gather vs the paper's atomic scatter",
+        "value": float(st["box_pixels"]) / (ms_g * 1e-3), "unit": "pairs/s",
+        "ms_gather_bin_sort_render": ms_g, "ms_scatter": ms_s, "speedup": ms_s / ms_g,
+        "box_pairs": int(st["box_pixels"]), "records": int(st["records"]),
+        "max_abs_image_diff": float(d.max()),
+        "max_rel_image_diff": float((d / im_g.abs().clamp_min(1e-6)).max()),
+        "steps": args.steps, "warmup": args.warmup,
+        "config": {"workload": WORKLOAD, "gaussians": n, "tile": int(cfg.tile),
+                   "variant": int(cfg.variant)},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -723,6 +780,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="aniso_1m", choices=["aniso_1m", "train_200k"],
                     help="train_200k: batched graph step against one plane per launch")
+    ap.add_argument("--ablation", default=None, choices=["scatter"],
+                    help="scatter: the forward as the paper's atomic scatter vs the tile gather")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --tile/--variant/--variant-bwd instead of the autotuner's choice")
     args = ap.parse_args()
@@ -732,6 +791,8 @@ def main():
         return run_reference(args)
     if args.workload == "train_200k":
         return run_train_compare(args)
+    if args.ablation == "scatter":
+        return run_scatter_ablation(args)
     return run_ours(args)
 
 

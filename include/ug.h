@@ -205,6 +205,16 @@ ug_status ug_bin_sort(const ug_plan* plan, void* ws, size_t ws_bytes, ug_stream 
 ug_status ug_render(const ug_plan* plan, void* ws, size_t ws_bytes, float* image,
                     float* alpha, ug_stream stream);
 
+/* The paper's own phase 2 (Sec. 3.4), kept as an ablation of ug_render: every
+ * visible record of the last ug_preprocess adds its weight and weighted
+ * intensity to each pixel of its box with atomics (no binning or sort needed),
+ * then C and alpha are formed as in ug_render. Same records and per-pixel
+ * weights as ug_render; the sums run in a different (unspecified) order, so the
+ * result agrees with ug_render to FP32 rounding and is not bit-reproducible.
+ * image and alpha are written as in ug_render (they serve as the accumulators). */
+ug_status ug_render_scatter(const ug_plan* plan, void* ws, size_t ws_bytes, float* image,
+                            float* alpha, ug_stream stream);
+
 /* Floats of device memory the `loss` argument of ug_mse_loss_grad points to. */
 #define UG_MSE_LOSS_FLOATS 1025
 

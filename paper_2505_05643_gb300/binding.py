@@ -35,7 +35,7 @@ EXPORTS = (
     "ug_version", "ug_status_string", "ug_num_variants", "ug_config_default", "ug_plan_init",
     "ug_preprocess", "ug_bin_sort", "ug_render", "ug_mse_loss_grad", "ug_render_backward",
     "ug_adam_step", "ug_read_status", "ug_debug_views", "ug_mse_loss_grad_static",
-    "ug_render_backward_raster", "ug_preprocess_backward",
+    "ug_render_backward_raster", "ug_preprocess_backward", "ug_render_scatter",
 )
 UG_MSE_STATIC_MAX_N = 1 << 30
 
@@ -126,6 +126,7 @@ def load(build_if_missing: bool = True):
     lib.ug_mse_loss_grad_static.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.ug_render_backward.argtypes = [P(ug_plan), P(ug_gaussians), vp, vp, ctypes.c_size_t, vp,
                                        vp, vp, P(ug_gaussian_grads), vp]
+    lib.ug_render_scatter.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp, vp, vp]
     lib.ug_render_backward_raster.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp, vp, vp, vp]
     lib.ug_preprocess_backward.argtypes = [P(ug_plan), P(ug_gaussians), vp, ctypes.c_size_t,
                                            P(ug_gaussian_grads), vp]
@@ -235,6 +236,11 @@ def ug_render_backward(plan: ug_plan, gaussians: ug_gaussians, d_planes, ws, ima
                                      _ptr(ws), ws.numel(), _ptr(image), _ptr(alpha),
                                      _ptr(grad_image), ctypes.byref(grads), _stream(stream)),
            "ug_render_backward")
+
+
+def ug_render_scatter(plan: ug_plan, ws, image, alpha, stream=None):
+    _check(load().ug_render_scatter(ctypes.byref(plan), _ptr(ws), ws.numel(), _ptr(image),
+                                    _ptr(alpha), _stream(stream)), "ug_render_scatter")
 
 
 def ug_render_backward_raster(plan: ug_plan, ws, image, alpha, grad_image, stream=None):

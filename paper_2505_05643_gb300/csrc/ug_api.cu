@@ -253,6 +253,16 @@ ug_status ug_render_backward(const ug_plan* plan, const ug_gaussians* gaussians,
                                             reinterpret_cast<cudaStream_t>(stream)));
 }
 
+ug_status ug_render_scatter(const ug_plan* plan, void* ws, size_t ws_bytes, float* image,
+                            float* alpha, ug_stream stream) {
+  ug_status s = check_plan(plan);
+  if (s == UG_OK) s = check_ws(plan, ws, ws_bytes);
+  if (s != UG_OK) return s;
+  if (!image || !alpha) return UG_ERR_INVALID_ARGUMENT;
+  return cuda_status(launch_render_scatter(plan, make_view(plan, ws), image, alpha,
+                                           reinterpret_cast<cudaStream_t>(stream)));
+}
+
 ug_status ug_render_backward_raster(const ug_plan* plan, void* ws, size_t ws_bytes,
                                     const float* image, const float* alpha,
                                     const float* grad_image, ug_stream stream) {

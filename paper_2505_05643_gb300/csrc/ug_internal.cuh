@@ -225,6 +225,8 @@ cudaError_t launch_preprocess(const ug_plan* plan, const ug_gaussians* g, WsView
 cudaError_t launch_bin_sort(const ug_plan* plan, WsView v, cudaStream_t s);
 cudaError_t launch_render(const ug_plan* plan, WsView v, float* image, float* alpha,
                           cudaStream_t s);
+cudaError_t launch_render_scatter(const ug_plan* plan, WsView v, float* image, float* alpha,
+                                  cudaStream_t s);
 cudaError_t launch_render_backward_raster(const ug_plan* plan, WsView v, const float* image,
                                           const float* alpha, const float* grad_image,
                                           cudaStream_t s);

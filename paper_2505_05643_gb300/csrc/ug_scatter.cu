@@ -1,0 +1,66 @@
+// The paper's own forward, kept as an ablation of the tile gather: phase 2 of
+// Sec. 3.4 loops over every visible (plane, Gaussian) record's pixel box and
+// adds the record's weight and weighted intensity to each pixel with atomics;
+// a last pass forms C = (S_c + a_bg c_bg) / (S_a + a_bg) (Eq. alpha-combine,
+// Eq. colour-combine). Same records and same per-pixel weight formula as the
+// tile rasterizer, so the two differ only in the order of the sums.
+#include "ug_internal.cuh"
+
+namespace ug {
+
+// One warp per record slot (grid-stride); lanes take the box's pixels in
+// row-major order. Zero weights add nothing and issue no atomic.
+__global__ void __launch_bounds__(256) k_scatter(WsView v, int cut, float* __restrict__ sa,
+                                                 float* __restrict__ sc) {
+  if (dev_failed(v.hdr)) return;
+  const uint32_t slots = v.hdr->slots;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < slots; slot += warps) {
+    const uint2 bx = v.rec_box[slot];
+    const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
+    if (j0 > j1 || i0 > i1) continue;
+    const float4 a = v.rec_a[slot], b = v.rec_b[slot];
+    const PlaneDev& pl = v.planes[v.rec_plane[slot]];
+    const uint32_t nx = (uint32_t)(j1 - j0 + 1), npx = nx * (uint32_t)(i1 - i0 + 1);
+    for (uint32_t k = lane; k < npx; k += 32u) {
+      const uint32_t di = k / nx, dj = k - di * nx;
+      const int i = i0 + (int)di, j = j0 + (int)dj;
+      const float dx = ((float)j + 0.5f) - a.x, dy = ((float)i + 0.5f) - a.y;
+      const float t1 = fmaf(a.z, dx, a.w * dy), t2 = b.x * dy;
+      const float q = fmaf(t1, t1, t2 * t2);
+      const bool in = cut == 0 || q <= b.w;
+      const float w = in ? fast_exp2(b.y - q) : 0.f;
+      if (w > 0.f) {
+        const int64_t px = pl.px_off + (int64_t)i * pl.w + j;
+        atomicAdd(sa + px, w);
+        atomicAdd(sc + px, w * b.z);
+      }
+    }
+  }
+}
+
+__global__ void k_scatter_finish(int64_t n, float abg, float cbg, float* __restrict__ image,
+                                 float* __restrict__ alpha) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const float al = alpha[p] + abg;
+    image[p] = (image[p] + abg * cbg) / al;
+    alpha[p] = al;
+  }
+}
+
+cudaError_t launch_render_scatter(const ug_plan* plan, WsView v, float* image, float* alpha,
+                                  cudaStream_t s) {
+  const size_t bytes = sizeof(float) * (size_t)plan->total_pixels;
+  cudaError_t e = cudaMemsetAsync(image, 0, bytes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(alpha, 0, bytes, s);
+  if (e != cudaSuccess) return e;
+  const int sms = device_sms();
+  k_scatter<<<sms * 8, 256, 0, s>>>(v, plan->cfg.cutoff, alpha, image);
+  k_scatter_finish<<<sms * 4, 256, 0, s>>>(plan->total_pixels, plan->cfg.alpha_bg, plan->cfg.c_bg,
+                                           image, alpha);
+  return cudaGetLastError();
+}
+
+}  // namespace ug

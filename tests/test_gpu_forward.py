@@ -192,3 +192,23 @@ def test_forward_is_deterministic():
     a, _ = r.forward(params)
     b, _ = r.forward(params)
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("cutoff", [B.UG_CUTOFF_BOX, B.UG_CUTOFF_BOX_AND_ELLIPSOID])
+def test_scatter_ablation_parity(cutoff):
+    """The paper's phase-2 atomic scatter (kept as an ablation) against the
+    oracle, and against the tile gather to FP32 rounding of the sums."""
+    rng = np.random.default_rng(61)
+    g = synth.gaussians_scale_rot(rng, 3000, 0.02, 0.15)
+    pl = synth.planes_random(rng, [(70, 45), (64, 64), (33, 97)])
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, cutoff=cutoff)
+    r, params, image, alpha = gpu_render(g, pl, cfg)
+    im2, al2 = r.new_image(), r.new_image()
+    B.ug_render_scatter(r.plan, r.ws, im2, al2)
+    assert r.status()["status"] == B.UG_OK
+    im2 = im2.cpu().numpy().astype(np.float64)
+    al2 = al2.cpu().numpy().astype(np.float64)
+    ref = oracle.render(g, pl, oracle_config(cfg))
+    assert_forward_parity(im2, al2, ref, "scatter")
+    assert np.allclose(im2, image, rtol=2e-5, atol=1e-7)
+    assert np.allclose(al2, alpha, rtol=2e-5, atol=1e-7)
