@@ -709,6 +709,148 @@ def run_train_compare(args):
     return 0
 
 
+# ---------------------------------------------------------------- reconstruction
+def run_recon(args):
+    """Reconstruction run: Gaussians in the paper's initialisation fitted to a
+    hidden synthetic volume with MSE and Adam (the paper's learning rates, the
+    means' rate decaying over the run), each step on 32 poses drawn from a pool
+    of training poses; SSIM and PSNR (the evaluator kernel) on held-out poses
+    every --recon-eval steps; the training time to reach SSIM thresholds; then
+    forward-only novel-slice rendering of 512x512 planes, images per second."""
+    import torch
+    from paper_2505_05643_gb300 import binding as B
+    from paper_2505_05643_gb300 import render as R
+    from paper_2505_05643_gb300 import synth
+    from paper_2505_05643_gb300 import train as T
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n, steps, every = args.recon_n, args.recon_steps, args.recon_eval
+    g, hidden, tr, te = synth.workload_recon(n=n, hidden_n=args.recon_hidden)
+    P, size = 32, 256
+    npx = size * size
+    cfg = R.make_config(cov_param=B.UG_COV_TRI)
+    cfg_h = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    hp = torch.from_numpy(R.pack_params(hidden, B.UG_COV_SCALE_ROT)).to(dev)
+
+    def render_targets(planes, chunk=32):
+        outs = []
+        for c0 in range(0, len(planes["size"]), chunk):
+            sub = synth.select_planes(planes, list(range(c0, min(c0 + chunk, len(planes["size"])))))
+            img, _ = R.Renderer(len(hidden["logit"]), sub, cfg_h).forward(hp)
+            outs.append(img.clone())
+        torch.cuda.empty_cache()
+        return torch.cat(outs).view(-1, npx)
+
+    t_train = render_targets(tr)   # (pool, npx)
+    t_test = render_targets(te)    # (held_out, npx)
+    pool = len(tr["size"])
+    rng = np.random.default_rng(6)
+    win_struct = {}
+
+    def pose_struct(idx):
+        key = tuple(idx)
+        if key not in win_struct:
+            win_struct[key] = torch.from_numpy(
+                synth.planes_to_struct(synth.select_planes(tr, list(idx))).view(np.uint8).copy()).to(dev)
+        return win_struct[key]
+
+    params = torch.from_numpy(R.pack_params(g, B.UG_COV_TRI)).to(dev)
+    r = R.Renderer(n, synth.select_planes(tr, list(range(P))), cfg)
+    targets = torch.empty(P * npx, device=dev)
+    step = T.TrainStep(r, params, targets, decay_steps=steps)
+    test_r = [R.Renderer(n, synth.select_planes(te, list(range(c0, min(c0 + 32, len(te["size"]))))), cfg)
+              for c0 in range(0, len(te["size"]), 32)]
+    scratch = torch.empty(B.ug_ssim_scratch_floats(32, size, size), device=dev)
+    ss, ps = torch.empty(32, device=dev), torch.empty(32, device=dev)
+
+    def evaluate():
+        vals_s, vals_p = [], []
+        for k, tr_ in enumerate(test_r):
+            img, _ = tr_.forward(params)
+            m = len(tr_.host_planes)
+            B.ug_ssim(img, t_test[32 * k:32 * k + m].reshape(-1), m, size, size, scratch, ss[:m], ps[:m])
+            vals_s.append(ss[:m].cpu().numpy().copy())
+            vals_p.append(ps[:m].cpu().numpy().copy())
+        return float(np.concatenate(vals_s).mean()), float(np.concatenate(vals_p).mean())
+
+    history = []
+    s0, p0 = evaluate()
+    history.append({"step": 0, "train_s": 0.0, "ssim": s0, "psnr": p0})
+    train_ms = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    order = rng.permutation(pool)
+    for k in range(steps):
+        o = (k * P) % pool
+        if k > 0 and o < P:  # a new epoch: a new order of the training poses
+            order = rng.permutation(pool)
+        idx = np.sort(order[o:o + P]) if o + P <= pool else np.sort(order[:P])
+        r.d_planes.copy_(pose_struct(idx))
+        targets.copy_(t_train.index_select(0, torch.from_numpy(idx).to(dev)).view(-1))
+        e0.record()
+        r.preprocess(params, check=True)  # grows the workspace when the records outgrow it
+        step.g_struct = R.gaussians_struct(params, B.UG_COV_TRI)
+        B.ug_bin_sort(r.plan, r.ws)
+        B.ug_render(r.plan, r.ws, step.image, step.alpha)
+        B.ug_mse_loss_grad(step.image, targets, step.image.numel(), step.grad_image, step.loss)
+        B.ug_render_backward(r.plan, step.g_struct, r.d_planes, r.ws, step.image, step.alpha,
+                             step.grad_image, step.grad_struct)
+        B.ug_adam_step(params, step.grads, step.m, step.v, r.rows, n, step.lr_rows, step.step,
+                       T.BETA1, T.BETA2, T.EPS)
+        e1.record()
+        e1.synchronize()
+        train_ms += e0.elapsed_time(e1)
+        stt = r.status()
+        assert stt["status"] == B.UG_OK, stt
+        if (k + 1) % every == 0 or k + 1 == steps:
+            sv, pv = evaluate()
+            history.append({"step": k + 1, "train_s": train_ms / 1e3, "ssim": sv, "psnr": pv,
+                            "loss": float(step.loss[0])})
+            print(f"[recon] step {k + 1} train {train_ms / 1e3:.2f} s ssim {sv:.4f} psnr {pv:.2f}",
+                  file=sys.stderr)
+
+    def time_to(th):
+        for h in history:
+            if h["ssim"] >= th:
+                return h["train_s"]
+        return None
+
+    # novel-slice rendering: 512 random poses of 512x512, 32 per launch
+    novel = synth.planes_random(np.random.default_rng(7), [(512, 512)] * 512)
+    nr = R.Renderer(n, synth.select_planes(novel, list(range(32))), cfg)
+    nr.forward(params)
+    chunks = [torch.from_numpy(synth.planes_to_struct(synth.select_planes(
+        novel, list(range(c0, c0 + 32)))).view(np.uint8).copy()).to(dev) for c0 in range(0, 512, 32)]
+    for c in chunks:  # sizing pass
+        nr.d_planes.copy_(c)
+        nr.forward(params)
+    img, al = nr.new_image(), nr.new_image()
+    torch.cuda.synchronize()
+    e0.record()
+    for c in chunks:
+        nr.d_planes.copy_(c, non_blocking=True)
+        B.ug_preprocess(nr.plan, R.gaussians_struct(params, B.UG_COV_TRI), nr.d_planes, nr.ws)
+        B.ug_bin_sort(nr.plan, nr.ws)
+        B.ug_render(nr.plan, nr.ws, img, al)
+    e1.record()
+    e1.synchronize()
+    novel_s = e0.elapsed_time(e1) / 1e3
+    assert nr.status()["status"] == B.UG_OK
+    line = {
+        "metric": "reconstruction: training time to held-out SSIM, and novel-slice images/s",
+        "value": 512 / novel_s, "unit": "images/s (512x512 novel slices)",
+        "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"recon: {n} Gaussians (paper init) fitted to a hidden "
+                               f"{args.recon_hidden}-Gaussian volume (seed 3), {steps} steps of 32 "
+                               f"poses from a pool of {pool} at 256x256, {len(te['size'])} "
+                               "held-out poses (seed 4)"},
+        "train_s": train_ms / 1e3, "ms_per_step": train_ms / steps,
+        "time_to_ssim": {str(th): time_to(th) for th in (0.8, 0.9, 0.95, 0.99)},
+        "final": history[-1], "history": history,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- ablation
 def run_scatter_ablation(args):
     """Forward of the bench workload two ways from the same records: the tile
@@ -778,8 +920,13 @@ def main():
     ap.add_argument("--cpu-planes", type=int, default=64, help="planes in the CPU oracle sample")
     ap.add_argument("--n", type=int, default=None, help="use the first n Gaussians (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="aniso_1m", choices=["aniso_1m", "train_200k"],
-                    help="train_200k: batched graph step against one plane per launch")
+    ap.add_argument("--workload", default="aniso_1m", choices=["aniso_1m", "train_200k", "recon"],
+                    help="train_200k: batched graph step against one plane per launch; "
+                         "recon: reconstruction run with SSIM on held-out poses")
+    ap.add_argument("--recon-n", type=int, default=3_000_000)
+    ap.add_argument("--recon-hidden", type=int, default=1_000_000)
+    ap.add_argument("--recon-steps", type=int, default=2000)
+    ap.add_argument("--recon-eval", type=int, default=100)
     ap.add_argument("--ablation", default=None, choices=["scatter"],
                     help="scatter: the forward as the paper's atomic scatter vs the tile gather")
     ap.add_argument("--no-autotune", action="store_true",
@@ -791,6 +938,8 @@ def main():
         return run_reference(args)
     if args.workload == "train_200k":
         return run_train_compare(args)
+    if args.workload == "recon":
+        return run_recon(args)
     if args.ablation == "scatter":
         return run_scatter_ablation(args)
     return run_ours(args)

@@ -205,6 +205,20 @@ ug_status ug_bin_sort(const ug_plan* plan, void* ws, size_t ws_bytes, ug_stream 
 ug_status ug_render(const ug_plan* plan, void* ws, size_t ws_bytes, float* image,
                     float* alpha, ug_stream stream);
 
+/* Evaluation metrics of rendered slices (Sec. 4): for P images of W x H pixels
+ * stored one after the other (row-major, device memory), the mean SSIM of
+ * image against target (Wang et al.: 11 x 11 Gaussian window, sigma 1.5,
+ * C1 = 0.01^2, C2 = 0.03^2, data range 1, every position where the window lies
+ * inside the image) into ssim[P] and PSNR = 10 log10(1 / MSE) into psnr[P]
+ * (either may be NULL, not both). scratch is caller-owned device memory of at
+ * least ug_ssim_scratch_floats(P, W, H) floats. Deterministic. Returns
+ * UG_ERR_INVALID_ARGUMENT for W or H below 11, UG_ERR_WORKSPACE_TOO_SMALL for
+ * too little scratch. ug_ssim_scratch_floats returns 0 for invalid sizes. */
+size_t ug_ssim_scratch_floats(int32_t P, int32_t W, int32_t H);
+ug_status ug_ssim(const float* image, const float* target, int32_t P, int32_t W, int32_t H,
+                  float* scratch, size_t scratch_floats, float* ssim, float* psnr,
+                  ug_stream stream);
+
 /* The paper's own phase 2 (Sec. 3.4), kept as an ablation of ug_render: every
  * visible record of the last ug_preprocess adds its weight and weighted
  * intensity to each pixel of its box with atomics (no binning or sort needed),

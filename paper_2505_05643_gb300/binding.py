@@ -36,6 +36,7 @@ EXPORTS = (
     "ug_preprocess", "ug_bin_sort", "ug_render", "ug_mse_loss_grad", "ug_render_backward",
     "ug_adam_step", "ug_read_status", "ug_debug_views", "ug_mse_loss_grad_static",
     "ug_render_backward_raster", "ug_preprocess_backward", "ug_render_scatter",
+    "ug_ssim_scratch_floats", "ug_ssim",
 )
 UG_MSE_STATIC_MAX_N = 1 << 30
 
@@ -126,6 +127,8 @@ def load(build_if_missing: bool = True):
     lib.ug_mse_loss_grad_static.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.ug_render_backward.argtypes = [P(ug_plan), P(ug_gaussians), vp, vp, ctypes.c_size_t, vp,
                                        vp, vp, P(ug_gaussian_grads), vp]
+    lib.ug_ssim_scratch_floats.argtypes = [i32, i32, i32]
+    lib.ug_ssim.argtypes = [vp, vp, i32, i32, i32, vp, ctypes.c_size_t, vp, vp, vp]
     lib.ug_render_scatter.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp, vp, vp]
     lib.ug_render_backward_raster.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp, vp, vp, vp]
     lib.ug_preprocess_backward.argtypes = [P(ug_plan), P(ug_gaussians), vp, ctypes.c_size_t,
@@ -139,8 +142,10 @@ def load(build_if_missing: bool = True):
         # an undeclared signature would pass Python ints as 32-bit C ints
         if fn.argtypes is None:
             raise RuntimeError(f"binding declares no argument types for {name}")
-        if name not in ("ug_version", "ug_status_string", "ug_num_variants"):
+        if name not in ("ug_version", "ug_status_string", "ug_num_variants",
+                        "ug_ssim_scratch_floats"):
             fn.restype = ctypes.c_int
+    lib.ug_ssim_scratch_floats.restype = ctypes.c_size_t
     _lib = lib
     return lib
 
@@ -236,6 +241,16 @@ def ug_render_backward(plan: ug_plan, gaussians: ug_gaussians, d_planes, ws, ima
                                      _ptr(ws), ws.numel(), _ptr(image), _ptr(alpha),
                                      _ptr(grad_image), ctypes.byref(grads), _stream(stream)),
            "ug_render_backward")
+
+
+def ug_ssim_scratch_floats(P: int, W: int, H: int) -> int:
+    return int(load().ug_ssim_scratch_floats(int(P), int(W), int(H)))
+
+
+def ug_ssim(image, target, P: int, W: int, H: int, scratch, ssim=None, psnr=None, stream=None):
+    """Per-image mean SSIM and PSNR of P images of W x H pixels (device tensors)."""
+    _check(load().ug_ssim(_ptr(image), _ptr(target), int(P), int(W), int(H), _ptr(scratch),
+                          scratch.numel(), _ptr(ssim), _ptr(psnr), _stream(stream)), "ug_ssim")
 
 
 def ug_render_scatter(plan: ug_plan, ws, image, alpha, stream=None):

@@ -253,6 +253,21 @@ ug_status ug_render_backward(const ug_plan* plan, const ug_gaussians* gaussians,
                                             reinterpret_cast<cudaStream_t>(stream)));
 }
 
+size_t ug_ssim_scratch_floats(int32_t P, int32_t W, int32_t H) {
+  if (P < 1 || W < 11 || H < 11) return 0;
+  return ssim_scratch_floats(P, W, H);
+}
+
+ug_status ug_ssim(const float* image, const float* target, int32_t P, int32_t W, int32_t H,
+                  float* scratch, size_t scratch_floats, float* ssim, float* psnr,
+                  ug_stream stream) {
+  if (!image || !target || !scratch || (!ssim && !psnr)) return UG_ERR_INVALID_ARGUMENT;
+  if (P < 1 || W < 11 || H < 11 || W > 16384 || H > 16384) return UG_ERR_INVALID_ARGUMENT;
+  if (scratch_floats < ssim_scratch_floats(P, W, H)) return UG_ERR_WORKSPACE_TOO_SMALL;
+  return cuda_status(launch_ssim(image, target, P, W, H, scratch, ssim, psnr,
+                                 reinterpret_cast<cudaStream_t>(stream)));
+}
+
 ug_status ug_render_scatter(const ug_plan* plan, void* ws, size_t ws_bytes, float* image,
                             float* alpha, ug_stream stream) {
   ug_status s = check_plan(plan);

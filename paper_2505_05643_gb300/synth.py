@@ -287,3 +287,17 @@ def workload_train_200k(seed: int = 0, n: int = 200_000, hidden_n: int = 100_000
     poses = planes_sweep_pool(rng, pool, (size, size))
     hidden = gaussians_scale_rot(np.random.default_rng(2), hidden_n)
     return g, poses, hidden
+
+
+def workload_recon(seed: int = 0, n: int = 3_000_000, hidden_n: int = 1_000_000,
+                   train_pool: int = 320, held_out: int = 128, size: int = 256):
+    """Reconstruction workload: n Gaussians in the paper's initialisation, a
+    hidden target volume of hidden_n Gaussians drawn with seed 3 from the
+    fwd_2k distributions, a pool of train_pool random training poses (seed 5)
+    and held_out random evaluation poses (seed 4), all size x size pixels.
+    Returns (gaussians, hidden gaussians, training poses, held-out poses)."""
+    g = gaussians_paper_init(np.random.default_rng(seed), n)
+    hidden = gaussians_scale_rot(np.random.default_rng(3), hidden_n)
+    train = planes_random(np.random.default_rng(5), [(size, size)] * train_pool)
+    test = planes_random(np.random.default_rng(4), [(size, size)] * held_out)
+    return g, hidden, train, test
