@@ -132,7 +132,7 @@ typedef struct {
   int32_t sort_passes;       /* 8-bit LSD passes */
   int64_t chunks;            /* ceil(n / 32) */
   size_t workspace_bytes;
-  size_t off[24];            /* internal section offsets */
+  size_t off[32];            /* internal section offsets (unused entries 0) */
 } ug_plan;
 
 /* Workspace status (64 bytes), copied out by ug_read_status. */

@@ -52,8 +52,10 @@ def ssim(x: np.ndarray, y: np.ndarray) -> float:
 
 
 def psnr(x: np.ndarray, y: np.ndarray) -> float:
+    """PSNR in dB; +inf for identical images."""
     d = np.asarray(x, np.float64) - np.asarray(y, np.float64)
-    return float(10.0 * np.log10(1.0 / np.mean(d * d)))
+    mse = float(np.mean(d * d))
+    return float("inf") if mse == 0.0 else float(10.0 * np.log10(1.0 / mse))
 
 
 def ssim_planes(image: np.ndarray, target: np.ndarray, P: int, W: int, H: int):

@@ -62,7 +62,7 @@ class ug_plan(ctypes.Structure):
                 ("record_capacity", ctypes.c_int64), ("instance_capacity", ctypes.c_int64),
                 ("key_bits", ctypes.c_int32), ("sort_passes", ctypes.c_int32),
                 ("chunks", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
-                ("off", ctypes.c_size_t * 24)]
+                ("off", ctypes.c_size_t * 32)]
 
 
 class ug_gaussians(ctypes.Structure):

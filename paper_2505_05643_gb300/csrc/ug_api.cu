@@ -184,7 +184,8 @@ ug_status ug_plan_init(const ug_config* cfg, int64_t n, const ug_plane* host_pla
   sz[kOffRanges] = sizeof(uint2) * (size_t)total_tiles;
   sz[kOffRecGrad] = 8 * sizeof(float) * (size_t)rc;
   sz[kOffRecPGrad] = 12 * sizeof(float) * (size_t)rc;
-  static_assert(kOffEnd <= 24, "ug_plan::off holds 24 sections");
+  sz[kOffRecChain] = kChainFloats * sizeof(float) * (size_t)rc;
+  static_assert(kOffEnd <= 32, "ug_plan::off holds 32 sections");
   size_t off = 0;
   for (int k = 0; k < kOffEnd; ++k) {
     plan->off[k] = off;

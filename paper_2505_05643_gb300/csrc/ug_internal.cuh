@@ -16,6 +16,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;    // keys per thread per sort block
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kMseBlocks = 1024;  // partial sums of the MSE loss
+constexpr int kChainFloats = 20;  // per-record inputs of the backward chain
 
 // Workspace sections (indices into ug_plan::off).
 enum WsSection {
@@ -43,6 +44,7 @@ enum WsSection {
   kOffRanges,
   kOffRecGrad,   // per record: 8 accumulators of the backward rasterizer
   kOffRecPGrad,  // per record: gradient of the Gaussian's parameters (12 floats)
+  kOffRecChain,  // per record: geometry the backward chain needs (kChainFloats floats)
   kOffEnd
 };
 
@@ -104,6 +106,7 @@ struct WsView {
   uint2* ranges;
   float* rec_grad;   // 8 floats per record
   float* rec_pgrad;  // 12 floats per record
+  float* rec_chain;  // kChainFloats floats per record
 };
 
 inline WsView make_view(const ug_plan* plan, void* ws) {
@@ -133,6 +136,7 @@ inline WsView make_view(const ug_plan* plan, void* ws) {
   v.ranges = reinterpret_cast<uint2*>(b + plan->off[kOffRanges]);
   v.rec_grad = reinterpret_cast<float*>(b + plan->off[kOffRecGrad]);
   v.rec_pgrad = reinterpret_cast<float*>(b + plan->off[kOffRecPGrad]);
+  v.rec_chain = reinterpret_cast<float*>(b + plan->off[kOffRecChain]);
   return v;
 }
 

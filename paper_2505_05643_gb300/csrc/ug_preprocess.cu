@@ -319,6 +319,43 @@ __device__ __forceinline__ void write_record(const PairRec<T>& rc, const PlaneDe
                                (uint32_t)pb.i0 | ((uint32_t)pb.i1 << 16));
 }
 
+// Inputs of the backward chain of one record (kChainFloats floats). For the
+// extended-precision records the forward keeps them, so the chain does not
+// repeat the double-word geometry; the chain recomputes the others in FP32:
+//   [0..8] b1, b2, b3 = F^T u, F^T v, F^T n;  [9, 10] kappa;  [11] k = m3 / S33;
+//   [12] m3;  [13..18] A11, A12, A22 of the in-plane precision A = [b1 b2]^T
+//   [b1 b2] as double words (high, low; the 2x2 solve of the chain needs them
+//   beyond FP32 for thin Gaussians);  [19] det A.
+__device__ __forceinline__ void split_dw(float x, float* d) {
+  d[0] = x;
+  d[1] = 0.f;
+}
+__device__ __forceinline__ void split_dw(dd x, float* d) {
+  d[0] = x.hi;
+  d[1] = x.lo;
+}
+
+template <typename T>
+__device__ __forceinline__ void chain_inputs(const PairRec<T>& rc, const PairGeo<T>& gg,
+                                             float c[kChainFloats]) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c[3 * j + a] = (float)rc.b[j][a];
+  c[9] = (float)rc.kappa[0];
+  c[10] = (float)rc.kappa[1];
+  c[11] = (float)rc.k;
+  c[12] = (float)gg.m[2];
+  const T* B1 = rc.b[0];
+  const T* B2 = rc.b[1];
+  const T A11 = rc.nb1 * rc.nb1, A12 = B1[0] * B2[0] + B1[1] * B2[1] + B1[2] * B2[2];
+  const T A22 = B2[0] * B2[0] + B2[1] * B2[1] + B2[2] * B2[2];
+  split_dw(A11, c + 13);
+  split_dw(A12, c + 15);
+  split_dw(A22, c + 17);
+  c[19] = (float)(rc.cr * rc.cr);
+}
+
 __device__ __forceinline__ bool box_empty(uint2 b) {
   return (b.x & 0xffffu) > (b.x >> 16) || (b.y & 0xffffu) > (b.y >> 16);
 }
@@ -350,6 +387,14 @@ __global__ void __launch_bounds__(256)
       pair_record<T, COV>(f, pl, gg, rc);
       float4 ra, rb;
       write_record<T>(rc, pl, pb, prm, chi2, v, slot, ra, rb);
+      if (is_ext<T>::value) {  // the chain recomputes normal-precision records in FP32
+        float c[kChainFloats];
+        chain_inputs<T>(rc, gg, c);
+        float4* d4 = reinterpret_cast<float4*>(v.rec_chain + (size_t)slot * kChainFloats);
+#pragma unroll
+        for (int q = 0; q < kChainFloats / 4; ++q)
+          d4[q] = make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
+      }
       npx += (unsigned long long)(pb.j1 - pb.j0 + 1) * (unsigned long long)(pb.i1 - pb.i0 + 1);
       kept++;
     } else {
@@ -678,14 +723,13 @@ struct ChainOut {
 };
 
 // Chain of one record's accumulators to (m, b1, b2, b3) and on to the
-// Gaussian's mean and factor F. The geometry comes in precision T; the chain
-// runs in FP32, except the 2x2 solve gamma = A^-1 dL/dx*, whose matrix is
-// ill-conditioned for thin Gaussians and is solved in T.
-template <typename T>
-__device__ __forceinline__ void chain_record(const PairRec<T>& rc, const PairGeo<T>& gg,
+// Gaussian's mean and factor F, from the record's stored geometry (ch, see
+// write_chain_inputs) and render data (r11, r12, r22). FP32, except the 2x2
+// solve gamma = A^-1 dL/dx*, whose matrix is ill-conditioned for thin
+// Gaussians: its numerators are formed in double words from the stored A.
+__device__ __forceinline__ void chain_record(const float* ch, float r11, float r12, float r22,
                                              const PlaneDev& pl, const float* acc, ChainOut& o) {
   const float ln2 = kLn2;
-  const float r11 = (float)rc.r11, r12 = (float)rc.r12, r22 = (float)rc.r22;
   const float a_p = acc[1], a_t1 = acc[2], a_t2 = acc[3];
   const float a_t1dx = acc[4], a_t1dy = acc[5], a_t2dy = acc[6];
   const float g_r11 = -2.f * ln2 * a_t1dx;
@@ -707,24 +751,20 @@ __device__ __forceinline__ void chain_record(const PairRec<T>& rc, const PairGeo
   const float gM11 = gr11 * i11 * 0.5f;
   float gA11 = c * pu * pu * gM11, gA12 = c * pu * pv * gM12, gA22 = c * pv * pv * gM22;
   // x* = m12 + m3 kappa, kappa = A^-1 s;  q0 = m3^2 (P33 - s^T A^-1 s)
-  const T* B1 = rc.b[0];
-  const T* B2 = rc.b[1];
-  const T A11 = rc.nb1 * rc.nb1, A12 = B1[0] * B2[0] + B1[1] * B2[1] + B1[2] * B2[2];
-  const T A22 = B2[0] * B2[0] + B2[1] * B2[1] + B2[2] * B2[2];
-  const T det = rc.cr * rc.cr;
-  const float gam0 = (float)m_div(A22 * (T)gx1 - A12 * (T)gx2, det);
-  const float gam1 = (float)m_div(A11 * (T)gx2 - A12 * (T)gx1, det);
+  const dd A11(ch[13], ch[14]), A12(ch[15], ch[16]), A22(ch[17], ch[18]);
+  const float det = ch[19];
+  const float gam0 = __fdiv_rn((float)(dd_mul(A22, gx1) - dd_mul(A12, gx2)), det);
+  const float gam1 = __fdiv_rn((float)(dd_mul(A11, gx2) - dd_mul(A12, gx1)), det);
   float b1[3], b2[3], b3[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    b1[a] = (float)rc.b[0][a];
-    b2[a] = (float)rc.b[1][a];
-    b3[a] = (float)rc.b[2][a];
+    b1[a] = ch[a];
+    b2[a] = ch[3 + a];
+    b3[a] = ch[6 + a];
   }
-  const float m3 = (float)gg.m[2];
-  const float kp0 = (float)rc.kappa[0], kp1 = (float)rc.kappa[1];
+  const float kp0 = ch[9], kp1 = ch[10], kk = ch[11], m3 = ch[12];
   const float gm1 = gx1, gm2 = gx2;
-  const float gm3 = gx1 * kp0 + gx2 * kp1 + 2.f * (float)rc.k * g_q0;
+  const float gm3 = gx1 * kp0 + gx2 * kp1 + 2.f * kk * g_q0;
   const float m3sq_gq0 = m3 * m3 * g_q0;
   const float gs0 = m3 * gam0 - 2.f * m3sq_gq0 * kp0;
   const float gs1 = m3 * gam1 - 2.f * m3sq_gq0 * kp1;
@@ -802,7 +842,10 @@ __device__ __forceinline__ void record_param_grad(const ChainOut& o, const Facto
   }
 }
 
-template <typename T, int COV>
+// One thread per record of the list's part (0: normal precision, whose
+// geometry is recomputed here in FP32; 1: extended precision, whose geometry
+// the forward stored).
+template <int COV>
 __global__ void __launch_bounds__(256)
     k_chain(ug_gaussians g, int64_t n, float chi2, float beta, WsView v, int part) {
   if (dev_failed(v.hdr)) return;
@@ -820,18 +863,34 @@ __global__ void __launch_bounds__(256)
       const float4 a0 = *reinterpret_cast<const float4*>(v.rec_grad + (size_t)slot * 8);
       const float4 a1 = *reinterpret_cast<const float4*>(v.rec_grad + (size_t)slot * 8 + 4);
       const float acc[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const PlaneDev pl = v.planes[e.y];
+      const PlaneDev& pl = v.planes[e.y];
       GaussParams prm;
       load_params(g, n, e.x, COV, prm);
-      Factor<T> f;
-      make_factor<T, COV>(prm, beta, f);
-      PairGeo<T> gg;
-      pair_box<T, COV>(f, pl, chi2, gg);
-      PairRec<T> rc;
-      pair_record<T, COV>(f, pl, gg, rc);
+      Factor<float> f;
+      make_factor<float, COV>(prm, beta, f);
+      float ch[kChainFloats];
+      if (part == 0) {
+        PairGeo<float> gg;
+        pair_box<float, COV>(f, pl, chi2, gg);
+        PairRec<float> rc;
+        pair_record<float, COV>(f, pl, gg, rc);
+        chain_inputs<float>(rc, gg, ch);
+      } else {
+        const float4* c4 =
+            reinterpret_cast<const float4*>(v.rec_chain + (size_t)slot * kChainFloats);
+#pragma unroll
+        for (int q = 0; q < kChainFloats / 4; ++q) {
+          const float4 t = c4[q];
+          ch[4 * q] = t.x;
+          ch[4 * q + 1] = t.y;
+          ch[4 * q + 2] = t.z;
+          ch[4 * q + 3] = t.w;
+        }
+      }
+      const float4 ra = v.rec_a[slot], rb = v.rec_b[slot];
       ChainOut o;
-      chain_record<T>(rc, gg, pl, acc, o);
-      record_param_grad<T, COV>(o, f, prm, acc[0], out);
+      chain_record(ch, ra.z, ra.w, rb.x, pl, acc, o);
+      record_param_grad<float, COV>(o, f, prm, acc[0], out);
     }
     float4* dst = reinterpret_cast<float4*>(v.rec_pgrad + (size_t)slot * 12);
     dst[0] = make_float4(out[0], out[1], out[2], out[3]);
@@ -907,8 +966,8 @@ static void launch_chain_cov(const ug_plan* plan, const ug_gaussians* g, WsView 
                              const ug_gaussian_grads* grads, cudaStream_t s) {
   const ug_config& c = plan->cfg;
   const unsigned lg = list_grid(plan->record_capacity);
-  k_chain<float, COV><<<lg, 256, 0, s>>>(*g, plan->n, c.chi2, c.beta, v, 0);
-  k_chain<dd, COV><<<lg, 256, 0, s>>>(*g, plan->n, c.chi2, c.beta, v, 1);
+  k_chain<COV><<<lg, 256, 0, s>>>(*g, plan->n, c.chi2, c.beta, v, 0);
+  k_chain<COV><<<lg, 256, 0, s>>>(*g, plan->n, c.chi2, c.beta, v, 1);
   const int64_t chunks = plan->chunks;
   if (chunks > 0)
     k_gather<COV><<<(unsigned)((chunks * 32 + 255) / 256), 256, 0, s>>>(plan->n, plan->num_planes,
