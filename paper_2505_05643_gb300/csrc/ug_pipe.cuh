@@ -1,0 +1,284 @@
+// Record pipeline of the tile rasterizers: one producer warp per CTA takes
+// tiles from the persistent work counter and gathers each tile's records
+// (sorted instance -> record id -> rec_a, rec_b, rec_box) into a ring of
+// shared-memory stages; the CTA's other warps consume the stages. Full/empty
+// handshakes are mbarriers (arrive: release, try_wait: acquire, CTA scope),
+// so the gathers of the next batches overlap the arithmetic of the current
+// one instead of stalling every warp on two dependent global loads per batch.
+//
+// Every wait is bounded in time: a wait that gives up records
+// UG_ERR_TIMEOUT in the workspace status and the warp leaves the kernel; the
+// waits of the other warps then run out as well, so the kernel always ends.
+#pragma once
+
+#include "ug_internal.cuh"
+
+namespace ug {
+
+constexpr int kBatch = 128;   // records per stage
+constexpr int kStages = 3;    // stages in the ring
+constexpr int kFirst = 1;     // stage flag: first batch of its tile
+constexpr int kLast = 2;      // stage flag: last batch of its tile
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
+constexpr uint32_t kWaitLimitIters = 1u << 30;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the completion of the barrier phase with the given parity; false
+// if it has not completed within kWaitLimitNs (or kWaitLimitIters polls).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < kWaitLimitIters; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) break;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)),
+               "l"(__cvta_generic_to_global(gmem))
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem)),
+               "l"(__cvta_generic_to_global(gmem))
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)),
+               "l"(__cvta_generic_to_global(gmem))
+               : "memory");
+}
+
+// Arrive on the barrier once all of this thread's earlier cp.async copies
+// have completed (the arrival is counted in the barrier's expected count).
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+struct StageHdr {
+  int32_t tile;   // -1: no more tiles
+  int32_t tx, ty, w, h;
+  int32_t cnt;    // records in this stage
+  int32_t flags;  // kFirst | kLast
+  int32_t pad;
+  int64_t px_off;
+};
+
+// One stage: up to kBatch records of one tile; with RAW, the first stage of a
+// tile also carries the tile's pixel inputs of the backward pass (dL/dC,
+// alpha, C; pixels off the plane hold 0, 1, 0).
+template <int TILE, bool RAW>
+struct RecStage {
+  float4 a[kBatch];
+  float4 b[kBatch];
+  uint2 box[kBatch];
+  uint32_t rid[kBatch];
+  StageHdr h;
+  float raw[RAW ? 3 : 1][RAW ? TILE * TILE : 1];
+};
+
+struct PipeBars {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+};
+
+// Planes whose tile data a CTA keeps in shared memory (more planes: looked up
+// in global memory).
+constexpr int kSmemPlanes = 64;
+
+struct TilePlane {
+  int32_t tile_off, tiles_x, w, h;
+  int64_t px_off;
+};
+
+struct PlaneTable {
+  TilePlane pl[kSmemPlanes];
+  int32_t tile_off[kSmemPlanes];
+};
+
+__device__ __forceinline__ int find_plane(const int32_t* tile_off, int P, int t) {
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_off[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Fill the plane table and the barriers; the caller follows with __syncthreads.
+__device__ __forceinline__ void pipe_init(PlaneTable& T, PipeBars& bars, const WsView& v, int P,
+                                          uint32_t consumer_threads) {
+  for (int p = threadIdx.x; p < min(P, kSmemPlanes); p += blockDim.x) {
+    const PlaneDev& d = v.planes[p];
+    T.pl[p] = TilePlane{d.tile_off, d.tiles_x, d.w, d.h, d.px_off};
+    T.tile_off[p] = d.tile_off;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&bars.full[s], 64);  // per producer lane: one plain, one cp.async arrival
+      mbar_init(&bars.empty[s], consumer_threads);
+    }
+  }
+}
+
+// The producer warp. Stage k of the stream goes to slot k % kStages; from
+// k = kStages on, the slot is reused once its consumers have released stage
+// k - kStages. The record ids are read into registers, the records themselves
+// (and the backward's pixel inputs) are copied with cp.async, whose completion
+// arrives on the stage's full barrier, so up to kStages batches of gathers
+// are in flight. RID: the stage also keeps the record ids. EMPTY_TILES: tiles
+// without records still get one stage (the forward pass writes their
+// background pixels).
+template <int TILE, bool RAW, bool RID, bool EMPTY_TILES>
+__device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
+                                        const PlaneTable& T, const WsView& v,
+                                        const uint32_t* __restrict__ vals, int which, int P,
+                                        int total_tiles, const float* __restrict__ grad,
+                                        const float* __restrict__ alpha,
+                                        const float* __restrict__ image) {
+  const int lane = threadIdx.x & 31;
+  constexpr int PER = kBatch / 32;
+  uint32_t k = 0;
+  uint32_t t = 0;
+  if (lane == 0) t = atomicAdd(&v.hdr->tile_counter[which], 1u);
+  t = __shfl_sync(0xffffffffu, t, 0);
+  while ((int)t < total_tiles) {
+    uint32_t pending = 0;
+    if (lane == 0) pending = atomicAdd(&v.hdr->tile_counter[which], 1u);
+    int local, tiles_x, w, h;
+    int64_t px_off;
+    if (P <= kSmemPlanes) {
+      const TilePlane& pl = T.pl[find_plane(T.tile_off, P, (int)t)];
+      local = (int)t - pl.tile_off;
+      tiles_x = pl.tiles_x;
+      w = pl.w;
+      h = pl.h;
+      px_off = pl.px_off;
+    } else {
+      const PlaneDev& pl = v.planes[find_plane(v.tile_off, P, (int)t)];
+      local = (int)t - pl.tile_off;
+      tiles_x = pl.tiles_x;
+      w = pl.w;
+      h = pl.h;
+      px_off = pl.px_off;
+    }
+    const int tx = local % tiles_x, ty = local / tiles_x;
+    const uint2 rg = v.ranges[t];
+    if (EMPTY_TILES || rg.y > rg.x) {
+      for (uint32_t b = rg.x;; b += kBatch) {
+        const int cnt = (int)min((uint32_t)kBatch, rg.y - b);
+        const int s = (int)(k % kStages);
+        if (k >= (uint32_t)kStages && !mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1u)) {
+          dev_fail(v.hdr, UG_ERR_TIMEOUT, 100 + which);
+          cp_async_wait_all();
+          return;
+        }
+        RecStage<TILE, RAW>& S = st[s];
+        uint32_t rid[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          const int r = lane + 32 * q;
+          rid[q] = r < cnt ? __ldg(vals + b + r) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          const int r = lane + 32 * q;
+          if (r < cnt) {
+            cp_async16(&S.a[r], v.rec_a + rid[q]);
+            cp_async16(&S.b[r], v.rec_b + rid[q]);
+            cp_async8(&S.box[r], v.rec_box + rid[q]);
+            if (RID) S.rid[r] = rid[q];
+          }
+        }
+        if constexpr (RAW) {
+          if (b == rg.x) {
+            for (int p = lane; p < TILE * TILE; p += 32) {
+              const int i = ty * TILE + p / TILE, j = tx * TILE + p % TILE;
+              if (i < h && j < w) {
+                const int64_t px = px_off + (int64_t)i * w + j;
+                cp_async4(&S.raw[0][p], grad + px);
+                cp_async4(&S.raw[1][p], alpha + px);
+                cp_async4(&S.raw[2][p], image + px);
+              } else {
+                S.raw[0][p] = 0.f;
+                S.raw[1][p] = 1.f;
+                S.raw[2][p] = 0.f;
+              }
+            }
+          }
+        }
+        if (lane == 0) {
+          StageHdr hd;
+          hd.tile = (int32_t)t;
+          hd.tx = tx;
+          hd.ty = ty;
+          hd.w = w;
+          hd.h = h;
+          hd.cnt = cnt;
+          hd.flags = (b == rg.x ? kFirst : 0) | (b + kBatch >= rg.y ? kLast : 0);
+          hd.pad = 0;
+          hd.px_off = px_off;
+          S.h = hd;
+        }
+        mbar_arrive(&bars.full[s]);      // the plain shared-memory stores above
+        cp_async_arrive(&bars.full[s]);  // this lane's copies, once they have landed
+        ++k;
+        if (b + kBatch >= rg.y) break;
+      }
+    }
+    t = __shfl_sync(0xffffffffu, pending, 0);
+  }
+  const int s = (int)(k % kStages);
+  if (k >= (uint32_t)kStages && !mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1u)) {
+    dev_fail(v.hdr, UG_ERR_TIMEOUT, 100 + which);
+    cp_async_wait_all();
+    return;
+  }
+  if (lane == 0) st[s].h.tile = -1;
+  mbar_arrive(&bars.full[s]);
+  cp_async_arrive(&bars.full[s]);
+  cp_async_wait_all();
+}
+
+}  // namespace ug

@@ -1,11 +1,12 @@
 // Rows a5 and a7: the forward tile rasterizer and its gradient.
 //
-// One CTA owns one TILE x TILE pixel tile at a time and takes tiles from a
-// device work counter (persistent launch over all tiles of all planes, so
-// planes of different sizes share one launch). The tile is cut into
-// footprints of 8 columns x FH rows. The tile's records are staged in shared
-// memory in batches of one record per thread; the staging thread decides,
-// for every footprint, whether the record can touch it:
+// Both kernels are persistent and warp-specialised. One producer warp per CTA
+// takes TILE x TILE pixel tiles from a device work counter (all tiles of all
+// planes, so planes of different sizes share one launch) and gathers each
+// tile's records, kBatch at a time, into a ring of shared-memory stages
+// (ug_pipe.cuh); the other warps consume the stages. The tile is cut into
+// footprints of 8 columns x FH rows. For every (record, footprint) of a stage
+// the consumers decide whether the record can touch the footprint:
 //   - its pixel box must overlap the footprint, and
 //   - a lower bound on t1^2 + t2^2 over the overlap must leave the exponent
 //     above -127: below that every weight in the overlap is exactly 0 in
@@ -19,100 +20,22 @@
 //   w = 2^(lw2 - t1^2 - t2^2)      (= alpha exp(-q/2), Eq. mahalanobis-3d)
 // evaluated in packed FP32x2 arithmetic, two pixels per instruction.
 //
-// Forward: one warp per 8x8 footprint, split into G lane groups that each
-// cover the whole footprint (2G pixels of one column per lane) and take every
-// G-th work item of the warp's list; per pixel S_a += w, S_c += w c, the
-// groups' sums are added at the end of the tile, then C = (S_c + a_bg c_bg) /
-// (S_a + a_bg) (Eq. alpha-combine, Eq. colour-combine). No atomics, fixed
-// summation order.
+// Forward: one consumer warp per 8x8 footprint, which classifies the stage's
+// records for its own footprint and is otherwise independent of the other
+// warps. The warp is split into G lane groups that each cover the whole
+// footprint (2G pixels of one column per lane) and take every G-th work item;
+// per pixel S_a += w, S_c += w c, the groups' sums are added at the end of the
+// tile, then C = (S_c + a_bg c_bg) / (S_a + a_bg) (Eq. alpha-combine, Eq.
+// colour-combine). No atomics, fixed summation order.
 //
 // Backward: one lane per work item. The lane walks the 8 x FH pixels of its
 // footprint and sums the seven per-record quantities of dL/dw over them in
 // registers, so no cross-lane reduction is needed; it then adds them to the
 // record's accumulators with seven atomics.
-#include "ug_internal.cuh"
+#include "ug_pipe.cuh"
 
 namespace ug {
 
-__device__ __forceinline__ int find_plane(const int32_t* tile_off, int P, int t) {
-  int lo = 0, hi = P - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (tile_off[mid] <= t) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-struct TileCtx {
-  int tile, tx, ty, w, h;
-  int64_t px_off;
-};
-
-// Planes whose tile data a block keeps in shared memory (more planes: looked
-// up in global memory).
-constexpr int kSmemPlanes = 64;
-
-struct TilePlane {
-  int32_t tile_off, tiles_x, w, h;
-  int64_t px_off;
-};
-
-// The block's share of the persistent tile queue. The block reserves its next
-// tile while it works on the current one (thread 0 holds the pending atomic's
-// result in a register until the tile ends), so the queue's latency is hidden.
-struct TileQueue {
-  TilePlane pl[kSmemPlanes];
-  int32_t tile_off[kSmemPlanes];
-  int next;
-};
-
-__device__ __forceinline__ void tq_init(TileQueue& Q, const WsView& v, int which, int P) {
-  for (int p = threadIdx.x; p < min(P, kSmemPlanes); p += blockDim.x) {
-    const PlaneDev& d = v.planes[p];
-    Q.pl[p] = TilePlane{d.tile_off, d.tiles_x, d.w, d.h, d.px_off};
-    Q.tile_off[p] = d.tile_off;
-  }
-  if (threadIdx.x == 0) Q.next = (int)atomicAdd(&v.hdr->tile_counter[which], 1u);
-  __syncthreads();
-}
-
-// Start the next tile (false: the queue is empty). Requires a barrier since
-// the last tq_end.
-__device__ __forceinline__ bool tq_begin(const TileQueue& Q, WsView& v, int which, int P,
-                                         int total_tiles, TileCtx& tc, uint32_t& pending) {
-  const int t = Q.next;
-  if (t >= total_tiles) return false;
-  if (threadIdx.x == 0) pending = atomicAdd(&v.hdr->tile_counter[which], 1u);
-  int local, tiles_x;
-  if (P <= kSmemPlanes) {
-    const TilePlane& pl = Q.pl[find_plane(Q.tile_off, P, t)];
-    local = t - pl.tile_off;
-    tiles_x = pl.tiles_x;
-    tc.w = pl.w;
-    tc.h = pl.h;
-    tc.px_off = pl.px_off;
-  } else {
-    const PlaneDev& pl = v.planes[find_plane(v.tile_off, P, t)];
-    local = t - pl.tile_off;
-    tiles_x = pl.tiles_x;
-    tc.w = pl.w;
-    tc.h = pl.h;
-    tc.px_off = pl.px_off;
-  }
-  tc.tx = local % tiles_x;
-  tc.ty = local / tiles_x;
-  tc.tile = t;
-  return true;
-}
-
-__device__ __forceinline__ void tq_end(TileQueue& Q, uint32_t pending) {
-  __syncthreads();  // the tile is done and every thread has read Q.next
-  if (threadIdx.x == 0) Q.next = (int)pending;
-  __syncthreads();
-}
-
-// ------------------------------------------------------------------ staging
 template <int TILE, int FH>
 struct Tiling {
   static constexpr int FW = 8;
@@ -122,53 +45,23 @@ struct Tiling {
   static_assert(NF <= 8, "footprint bits");
 };
 
-// Records of one batch in shared memory.
-template <int NT>
-struct Batch {
-  float4 a[NT];
-  float4 b[NT];
-  uint2 box[NT];
-  uint32_t rid[NT];
-  uint32_t mask[NT];  // bit f: live for footprint f; bit 8 + f: box covers footprint f
-};
-
 __device__ __forceinline__ void footprint_origin(int f, int fx_count, int fh, int tx, int ty,
                                                  int tile, int& fj0, int& fi0) {
   fj0 = tx * tile + (f % fx_count) * 8;
   fi0 = ty * tile + (f / fx_count) * fh;
 }
 
-// Thread t < cnt loads record vals[b + t] into the batch and classifies it
-// for every footprint of the tile (bits of B.mask[t]).
-template <int TILE, int FH, int CUT, int NT>
-__device__ __forceinline__ void stage_records(Batch<NT>& B, const WsView& v,
-                                              const uint32_t* __restrict__ vals, uint32_t b,
-                                              int cnt, int tx, int ty) {
-  using T = Tiling<TILE, FH>;
-  const int tid = threadIdx.x;
-  if (tid >= cnt) return;
-  const uint32_t rid = __ldg(vals + b + tid);
-  const float4 a = __ldg(v.rec_a + rid);
-  const float4 c = __ldg(v.rec_b + rid);
-  const uint2 bx = __ldg(v.rec_box + rid);
-  B.a[tid] = a;
-  B.b[tid] = c;
-  B.box[tid] = bx;
-  B.rid[tid] = rid;
+// Work-item test of one record against the footprint [fj0, fj0 + 7] x [fi0,
+// fi0 + fh - 1]: bit 0 live, bit 1 the box covers the footprint.
+template <int CUT>
+__device__ __forceinline__ uint32_t classify(const float4& a, const float4& c, uint2 bx, int fj0,
+                                             int fi0, int fh) {
   const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
-  uint32_t m = 0;
-#pragma unroll
-  for (int f = 0; f < T::NF; ++f) {
-    int fj0, fi0;
-    footprint_origin(f, T::FX, FH, tx, ty, TILE, fj0, fi0);
-    const int fj1 = fj0 + 7, fi1 = fi0 + FH - 1;
-    const int xa = max(fj0, j0), xb = min(fj1, j1), ya = max(fi0, i0), yb = min(fi1, i1);
-    if (xa > xb || ya > yb) continue;
-    if (!rect_live(a, c, xa, xb, ya, yb, CUT)) continue;  // every weight is an FP32 zero
-    m |= 1u << f;
-    if (j0 <= fj0 && j1 >= fj1 && i0 <= fi0 && i1 >= fi1) m |= 1u << (8 + f);
-  }
-  B.mask[tid] = m;
+  const int fj1 = fj0 + 7, fi1 = fi0 + fh - 1;
+  const int xa = max(fj0, j0), xb = min(fj1, j1), ya = max(fi0, i0), yb = min(fi1, i1);
+  if (xa > xb || ya > yb) return 0u;
+  if (!rect_live(a, c, xa, xb, ya, yb, CUT)) return 0u;  // every weight is an FP32 zero
+  return 1u | ((j0 <= fj0 && j1 >= fj1 && i0 <= fi0 && i1 >= fi1) ? 2u : 0u);
 }
 
 // box ∩ footprint in footprint coordinates, packed cx0 | cx1 << 8 | ry0 << 16 |
@@ -194,20 +87,22 @@ struct FwdChunk {
 template <int TILE, int G>
 struct FwdShape {
   using T = Tiling<TILE, 8>;
-  static constexpr int NW = T::NF;   // one warp per 8x8 footprint
-  static constexpr int NT = 32 * NW;
-  static constexpr int LG = 32 / G;  // lanes per group
-  static constexpr int PPT = 2 * G;  // rows per lane
-  static constexpr int NP = G;       // row pairs per lane
+  static constexpr int NW = T::NF;        // one consumer warp per 8x8 footprint
+  static constexpr int NCT = 32 * NW;     // consumer threads
+  static constexpr int NT = NCT + 32;     // plus the producer warp
+  static constexpr int LG = 32 / G;       // lanes per group
+  static constexpr int PPT = 2 * G;       // rows per lane
+  static constexpr int NP = G;            // row pairs per lane
   static_assert(G == 1 || G == 2 || G == 4, "groups");
 };
 
-template <int NT, int NW>
-struct FwdStage {
-  Batch<NT> B;
-  uint16_t list[NW][NT];  // full items from the front, partial items from the back
+template <int TILE, int NW>
+struct FwdSmem {
+  RecStage<TILE, false> st[kStages];
+  PipeBars bars;
+  uint16_t list[NW][kBatch];  // full items from the front, partial items from the back
   FwdChunk ch[NW];
-  TileQueue Q;
+  PlaneTable T;
 };
 
 // The exponent e = lw2 - t1^2 - t2^2 is formed with negated products so that
@@ -257,103 +152,117 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
     k_render_fwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles, float abg,
                  float cbg, float* __restrict__ image, float* __restrict__ alpha) {
   using Sh = FwdShape<TILE, G>;
-  constexpr int NT = Sh::NT, NW = Sh::NW, LG = Sh::LG, PPT = Sh::PPT, NP = Sh::NP;
-  __shared__ FwdStage<NT, NW> S;
-  if (dev_failed(v.hdr)) return;
+  constexpr int NW = Sh::NW, LG = Sh::LG, PPT = Sh::PPT, NP = Sh::NP;
+  __shared__ FwdSmem<TILE, NW> S;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  pipe_init(S.T, S.bars, v, P, Sh::NCT);
+  if (__syncthreads_or(dev_failed(v.hdr))) return;  // the whole CTA leaves, or none of it
+  if (warp == NW) {
+    produce<TILE, false, false, true>(S.st, S.bars, S.T, v, vals, 0, P, total_tiles, nullptr, nullptr,
+                               nullptr);
+    return;
+  }
   const int grp = lane / LG, gl = lane % LG;
   const int lx = gl & 7, row0 = (gl >> 3) * PPT;  // column and first row of this lane
   const uint32_t lt = lanemask_lt();
-  TileCtx tc;
   unsigned long long evaluated = 0;  // (record, footprint) items of this warp
-  uint32_t pending = 0;
-  tq_init(S.Q, v, 0, P);
-  while (tq_begin(S.Q, v, 0, P, total_tiles, tc, pending)) {
-    int fj0, fi0;
-    footprint_origin(warp, Tiling<TILE, 8>::FX, 8, tc.tx, tc.ty, TILE, fj0, fi0);
-    const int j = fj0 + lx;
-    const float2 pxx = make_float2((float)j + 0.5f, (float)j + 0.5f);
-    float2 py[NP], sa[NP], sc[NP];
+  int fj0 = 0, fi0 = 0, j = 0, tw = 0, th = 0;
+  int64_t tpx = 0;
+  float2 pxx = make_float2(0.f, 0.f), py[NP], sa[NP], sc[NP];
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const float y0 = (float)(fi0 + row0 + 2 * p) + 0.5f;
-      py[p] = make_float2(y0, y0 + 1.f);
-      sa[p] = sc[p] = make_float2(0.f, 0.f);
+  for (int p = 0; p < NP; ++p) py[p] = sa[p] = sc[p] = make_float2(0.f, 0.f);
+  const FwdChunk& C = S.ch[warp];
+  for (uint32_t k = 0;; ++k) {
+    const int s = (int)(k % kStages);
+    if (!mbar_wait(&S.bars.full[s], (k / kStages) & 1u)) {
+      dev_fail(v.hdr, UG_ERR_TIMEOUT, 1);
+      break;
     }
-    const FwdChunk& C = S.ch[warp];
-    const uint2 rg = v.ranges[tc.tile];
-    for (uint32_t b = rg.x; b < rg.y; b += NT) {
-      const int cnt = (int)min((uint32_t)NT, rg.y - b);
-      __syncthreads();  // the previous batch is consumed
-      stage_records<TILE, 8, CUT, NT>(S.B, v, vals, b, cnt, tc.tx, tc.ty);
-      __syncthreads();
-      // this warp's lists: full-box items from the front, partial from the back
-      int nf = 0, np = 0;
-      for (int base = 0; base < cnt; base += 32) {
-        const int r = base + lane;
-        const uint32_t m = r < cnt ? S.B.mask[r] : 0u;
-        const bool live = (m >> warp) & 1u, full = (m >> (8 + warp)) & 1u;
-        const uint32_t bf = __ballot_sync(0xffffffffu, live && full);
-        const uint32_t bp = __ballot_sync(0xffffffffu, live && !full);
-        if (live && full) S.list[warp][nf + __popc(bf & lt)] = (uint16_t)r;
-        if (live && !full) S.list[warp][NT - 1 - (np + __popc(bp & lt))] = (uint16_t)r;
-        nf += __popc(bf);
-        np += __popc(bp);
-      }
-      __syncwarp();
-      evaluated += (unsigned long long)(nf + np);
-#pragma unroll 1
-      for (int part = 0; part < 2; ++part) {
-        const int n = part ? np : nf;
-        for (int base = 0; base < n; base += 32) {
-          if (base + lane < n) {  // lane-parallel chunk build
-            const int r = S.list[warp][part ? NT - 1 - (base + lane) : base + lane];
-            const float4 a = S.B.a[r], bb = S.B.b[r];
-            FwdChunk& W = S.ch[warp];
-            W.nxy[lane] = make_float4(-a.x, -a.x, -a.y, -a.y);
-            W.r1[lane] = make_float4(a.z, a.z, a.w, a.w);
-            W.r2[lane] = make_float4(bb.x, bb.x, bb.y, bb.y);
-            W.cv[lane] = make_float4(bb.z, bb.z, bb.w, 0.f);
-            if (part) W.clip[lane] = clip_box(S.B.box[r], fj0, fi0, 8);
-          }
-          __syncwarp();
-          const int ne = min(32, n - base);
-          if (part) {
-            for (int e = grp; e < ne; e += G)
-              fwd_item<CUT, true, NP>(C, e, pxx, py, lx, row0, sa, sc);
-          } else {
-            for (int e = grp; e < ne; e += G)
-              fwd_item<CUT, false, NP>(C, e, pxx, py, lx, row0, sa, sc);
-          }
-          __syncwarp();
-        }
-      }
-    }
-    // add the groups' sums (fixed order), group 0 writes
-#pragma unroll
-    for (int o = LG; o < 32; o <<= 1)
+    const RecStage<TILE, false>& R = S.st[s];
+    const StageHdr h = R.h;
+    if (h.tile < 0) break;
+    if (h.flags & kFirst) {
+      footprint_origin(warp, Tiling<TILE, 8>::FX, 8, h.tx, h.ty, TILE, fj0, fi0);
+      j = fj0 + lx;
+      tw = h.w;
+      th = h.h;
+      tpx = h.px_off;
+      pxx = make_float2((float)j + 0.5f, (float)j + 0.5f);
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
-        sa[p].x += __shfl_xor_sync(0xffffffffu, sa[p].x, o);
-        sa[p].y += __shfl_xor_sync(0xffffffffu, sa[p].y, o);
-        sc[p].x += __shfl_xor_sync(0xffffffffu, sc[p].x, o);
-        sc[p].y += __shfl_xor_sync(0xffffffffu, sc[p].y, o);
+        const float y0 = (float)(fi0 + row0 + 2 * p) + 0.5f;
+        py[p] = make_float2(y0, y0 + 1.f);
+        sa[p] = sc[p] = make_float2(0.f, 0.f);
       }
-    if (grp == 0 && j < tc.w) {
+    }
+    // this warp's lists: full-box items from the front, partial from the back
+    int nf = 0, np = 0;
+    for (int base = 0; base < h.cnt; base += 32) {
+      const int r = base + lane;
+      const uint32_t m = r < h.cnt ? classify<CUT>(R.a[r], R.b[r], R.box[r], fj0, fi0, 8) : 0u;
+      const bool live = m & 1u, full = m & 2u;
+      const uint32_t bf = __ballot_sync(0xffffffffu, live && full);
+      const uint32_t bp = __ballot_sync(0xffffffffu, live && !full);
+      if (live && full) S.list[warp][nf + __popc(bf & lt)] = (uint16_t)r;
+      if (live && !full) S.list[warp][kBatch - 1 - (np + __popc(bp & lt))] = (uint16_t)r;
+      nf += __popc(bf);
+      np += __popc(bp);
+    }
+    __syncwarp();
+    evaluated += (unsigned long long)(nf + np);
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      const int n = part ? np : nf;
+      for (int base = 0; base < n; base += 32) {
+        if (base + lane < n) {  // lane-parallel chunk build
+          const int r = S.list[warp][part ? kBatch - 1 - (base + lane) : base + lane];
+          const float4 a = R.a[r], bb = R.b[r];
+          FwdChunk& W = S.ch[warp];
+          W.nxy[lane] = make_float4(-a.x, -a.x, -a.y, -a.y);
+          W.r1[lane] = make_float4(a.z, a.z, a.w, a.w);
+          W.r2[lane] = make_float4(bb.x, bb.x, bb.y, bb.y);
+          W.cv[lane] = make_float4(bb.z, bb.z, bb.w, 0.f);
+          if (part) W.clip[lane] = clip_box(R.box[r], fj0, fi0, 8);
+        }
+        __syncwarp();
+        const int ne = min(32, n - base);
+        if (part) {
+          for (int e = grp; e < ne; e += G)
+            fwd_item<CUT, true, NP>(C, e, pxx, py, lx, row0, sa, sc);
+        } else {
+          for (int e = grp; e < ne; e += G)
+            fwd_item<CUT, false, NP>(C, e, pxx, py, lx, row0, sa, sc);
+        }
+        __syncwarp();
+      }
+    }
+    mbar_arrive(&S.bars.empty[s]);  // the stage is no longer read by this thread
+    if (h.flags & kLast) {
+      // add the groups' sums (fixed order), group 0 writes
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        const int i = fi0 + row0 + k;
-        if (i < tc.h) {
-          const int64_t px = tc.px_off + (int64_t)i * tc.w + j;
-          const float sak = (k & 1) ? sa[k >> 1].y : sa[k >> 1].x;
-          const float sck = (k & 1) ? sc[k >> 1].y : sc[k >> 1].x;
-          const float al = sak + abg;
-          image[px] = (sck + abg * cbg) / al;
-          alpha[px] = al;
+      for (int o = LG; o < 32; o <<= 1)
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          sa[p].x += __shfl_xor_sync(0xffffffffu, sa[p].x, o);
+          sa[p].y += __shfl_xor_sync(0xffffffffu, sa[p].y, o);
+          sc[p].x += __shfl_xor_sync(0xffffffffu, sc[p].x, o);
+          sc[p].y += __shfl_xor_sync(0xffffffffu, sc[p].y, o);
+        }
+      if (grp == 0 && j < tw) {
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+          const int i = fi0 + row0 + q;
+          if (i < th) {
+            const int64_t px = tpx + (int64_t)i * tw + j;
+            const float saq = (q & 1) ? sa[q >> 1].y : sa[q >> 1].x;
+            const float scq = (q & 1) ? sc[q >> 1].y : sc[q >> 1].x;
+            const float al = saq + abg;
+            image[px] = (scq + abg * cbg) / al;
+            alpha[px] = al;
+          }
         }
       }
     }
-    tq_end(S.Q, pending);
   }
   if (lane == 0 && evaluated)
     atomicAdd(reinterpret_cast<unsigned long long*>(&v.hdr->st.evaluated_pairs),
@@ -361,22 +270,43 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
 }
 
 // ------------------------------------------------------------------ backward
-constexpr int kBwdThreads = 128;
+constexpr int kBwdConsumers = 128;                // consumer threads (4 warps)
+constexpr int kBwdThreads = kBwdConsumers + 32;   // plus the producer warp
 
 template <int TILE, int FH>
-struct BwdStage {
+struct BwdSmem {
   using T = Tiling<TILE, FH>;
-  Batch<kBwdThreads> B;
-  uint16_t items[kBwdThreads * T::NF];  // record | footprint << 8; full from the front
+  RecStage<TILE, true> st[kStages];
+  PipeBars bars;
+  uint16_t items[kBatch * T::NF];          // record | footprint << 8; full from the front
   // per footprint, row y and column pair cp (index 4 y + cp): r0, r1, -rC0, -rC1;
   // one float4 of padding per footprint so that lanes reading the same (y, cp)
   // of different footprints hit different banks
   float4 pix[T::NF][FH * 4 + 1];
-  uint32_t warp_tot[kBwdThreads / 32];
-  TileQueue Q;
+  uint32_t warp_tot[kBwdConsumers / 32];
+  PlaneTable Tb;
 };
 
-// Exclusive block scan of one value per thread (kBwdThreads threads).
+// Barrier 1 joins the consumer warps only (the producer never takes part).
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kBwdConsumers) : "memory");
+}
+
+// Consumer barrier that also returns whether any consumer thread passed true.
+__device__ __forceinline__ bool consumers_any(bool q) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, c;\n\t"
+      "setp.ne.u32 c, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, %2, c;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)q), "n"(kBwdConsumers)
+      : "memory");
+  return r != 0;
+}
+
+// Exclusive scan over the consumer threads of one value per thread.
 __device__ __forceinline__ uint32_t bwd_block_scan(uint32_t x, uint32_t* warp_tot, uint32_t* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t incl = x;
@@ -386,10 +316,10 @@ __device__ __forceinline__ uint32_t bwd_block_scan(uint32_t x, uint32_t* warp_to
     if (lane >= o) incl += t;
   }
   if (lane == 31) warp_tot[warp] = incl;
-  __syncthreads();
+  consumers_sync();
   uint32_t base = 0, tot = 0;
 #pragma unroll
-  for (int w = 0; w < kBwdThreads / 32; ++w) {
+  for (int w = 0; w < kBwdConsumers / 32; ++w) {
     if (w < warp) base += warp_tot[w];
     tot += warp_tot[w];
   }
@@ -408,11 +338,11 @@ __device__ __forceinline__ uint32_t bwd_block_scan(uint32_t x, uint32_t* warp_to
 // (CUT) get w = 0 through an exponent of -inf, never a NaN: every factor
 // that multiplies w stays finite.
 template <int TILE, int FH, int CUT, bool PARTIAL>
-__device__ __forceinline__ void bwd_item(const BwdStage<TILE, FH>& S, int item, int tx, int ty,
-                                         float* __restrict__ rec_grad) {
+__device__ __forceinline__ void bwd_item(const BwdSmem<TILE, FH>& S, const RecStage<TILE, true>& R,
+                                         int item, int tx, int ty, float* __restrict__ rec_grad) {
   using T = Tiling<TILE, FH>;
   const int r = item & 0xff, f = item >> 8;
-  const float4 a = S.B.a[r], bb = S.B.b[r];
+  const float4 a = R.a[r], bb = R.b[r];
   int fj0, fi0;
   footprint_origin(f, T::FX, FH, tx, ty, TILE, fj0, fi0);
   const float2 r11 = make_float2(a.z, a.z), r12 = make_float2(a.w, a.w);
@@ -427,7 +357,7 @@ __device__ __forceinline__ void bwd_item(const BwdStage<TILE, FH>& S, int item, 
   }
   int ry0 = 0, ry1 = FH - 1;
   if (PARTIAL) {
-    const uint32_t cl = clip_box(S.B.box[r], fj0, fi0, FH);
+    const uint32_t cl = clip_box(R.box[r], fj0, fi0, FH);
     const int cx0 = cl & 0xff, cx1 = (cl >> 8) & 0xff;
     ry0 = (cl >> 16) & 0xff;
     ry1 = cl >> 24;
@@ -474,7 +404,7 @@ __device__ __forceinline__ void bwd_item(const BwdStage<TILE, FH>& S, int item, 
     u2 = fmaf(t2.x, sr, u2);
     a6 = fmaf(t2.x, dyv * sr, a6);
   }
-  const uint32_t rid = S.B.rid[r];
+  const uint32_t rid = R.rid[r];
   float* dst = rec_grad + (size_t)rid * 8;
   atomicAdd(dst + 0, s0.x + s0.y);
   atomicAdd(dst + 1, s1);
@@ -491,67 +421,85 @@ __global__ void __launch_bounds__(kBwdThreads)
                  const float* __restrict__ image, const float* __restrict__ alpha,
                  const float* __restrict__ grad_image) {
   using T = Tiling<TILE, FH>;
-  constexpr int NT = kBwdThreads, NF = T::NF, CAP = kBwdThreads * T::NF;
-  __shared__ BwdStage<TILE, FH> S;
-  if (dev_failed(v.hdr)) return;
+  constexpr int NF = T::NF, CAP = kBatch * T::NF;
+  __shared__ BwdSmem<TILE, FH> S;
   const int tid = threadIdx.x;
-  TileCtx tc;
+  pipe_init(S.Tb, S.bars, v, P, kBwdConsumers);
+  // the whole CTA leaves, or none of it (the consumer barriers need all 128)
+  if (__syncthreads_or(dev_failed(v.hdr))) return;
+  if (tid >= kBwdConsumers) {
+    produce<TILE, true, true, false>(S.st, S.bars, S.Tb, v, vals, 1, P, total_tiles, grad_image, alpha,
+                               image);
+    return;
+  }
   unsigned long long evaluated = 0;
-  uint32_t pending = 0;
-  tq_init(S.Q, v, 1, P);
-  while (tq_begin(S.Q, v, 1, P, total_tiles, tc, pending)) {
-    // per-pixel factors of the tile: r = G / alpha and -r C (0 off the plane)
-    for (int q = tid; q < NF * FH * 4; q += NT) {
-      const int f = q / (FH * 4), y = (q / 4) % FH, cp = q % 4;
-      int fj0, fi0;
-      footprint_origin(f, T::FX, FH, tc.tx, tc.ty, TILE, fj0, fi0);
-      const int i = fi0 + y;
-      float v4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = fj0 + 2 * cp + h;
-        if (j < tc.w && i < tc.h) {
-          const int64_t px = tc.px_off + (int64_t)i * tc.w + j;
-          const float rv = __ldg(grad_image + px) / __ldg(alpha + px);
-          v4[h] = rv;
-          v4[2 + h] = -rv * __ldg(image + px);
-        }
-      }
-      S.pix[f][4 * y + cp] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+  int tx = 0, ty = 0;
+  for (uint32_t k = 0;; ++k) {
+    const int s = (int)(k % kStages);
+    const bool ok = mbar_wait(&S.bars.full[s], (k / kStages) & 1u);
+    // every consumer reaches this barrier, so a wait that gave up in one warp
+    // ends all of them together (and the previous stage's items are consumed)
+    if (consumers_any(!ok)) {
+      if (!ok) dev_fail(v.hdr, UG_ERR_TIMEOUT, 2);
+      break;
     }
-    const uint2 rg = v.ranges[tc.tile];
-    for (uint32_t b = rg.x; b < rg.y; b += NT) {
-      const int cnt = (int)min((uint32_t)NT, rg.y - b);
-      __syncthreads();  // the previous batch is consumed (and the pixel factors are written)
-      stage_records<TILE, FH, CUT, NT>(S.B, v, vals, b, cnt, tc.tx, tc.ty);
-      // work items of this thread's record: full-box ones from the front of the
-      // list, partial ones from the back, positions from one block scan
-      const uint32_t m = tid < cnt ? S.B.mask[tid] : 0u;
-      const uint32_t live = m & 0xffu, full = live & (m >> 8);
-      const uint32_t nfl = __popc(full), npt = __popc(live & ~full);
-      uint32_t tot;
-      const uint32_t pos = bwd_block_scan(nfl | (npt << 16), S.warp_tot, &tot);
-      const int nf_all = tot & 0xffff, np_all = tot >> 16;
-      uint32_t pf = pos & 0xffff, pp = pos >> 16;
+    const RecStage<TILE, true>& R = S.st[s];
+    const StageHdr h = R.h;
+    if (h.tile < 0) break;
+    if (h.flags & kFirst) {
+      // per-pixel factors of the tile: r = G / alpha and -r C (0 off the plane)
+      tx = h.tx;
+      ty = h.ty;
+      for (int q = tid; q < NF * FH * 4; q += kBwdConsumers) {
+        const int f = q / (FH * 4), y = (q / 4) % FH, cp = q % 4;
+        const int p0 = ((f / T::FX) * FH + y) * TILE + (f % T::FX) * 8 + 2 * cp;
+        float v4[4];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const float rv = R.raw[0][p0 + hh] / R.raw[1][p0 + hh];
+          v4[hh] = rv;
+          v4[2 + hh] = -rv * R.raw[2][p0 + hh];
+        }
+        S.pix[f][4 * y + cp] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+      }
+    }
+    // work items of this thread's record: full-box ones from the front of the
+    // list, partial ones from the back, positions from one block scan
+    uint32_t live = 0, full = 0;
+    if (tid < h.cnt) {
+      const float4 a = R.a[tid], c = R.b[tid];
+      const uint2 bx = R.box[tid];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        if (!((live >> f) & 1u)) continue;
-        const uint16_t it = (uint16_t)(tid | (f << 8));
-        if ((full >> f) & 1u) S.items[pf++] = it;
-        else S.items[CAP - 1 - pp++] = it;
-      }
-      __syncthreads();
-      const int n = nf_all + np_all;
-      evaluated += (unsigned long long)n;
-      for (int k = tid; k < n; k += NT) {
-        if (k < nf_all)
-          bwd_item<TILE, FH, CUT, false>(S, S.items[k], tc.tx, tc.ty, v.rec_grad);
-        else
-          bwd_item<TILE, FH, CUT, true>(S, S.items[CAP - 1 - (k - nf_all)], tc.tx, tc.ty,
-                                        v.rec_grad);
+        int fj0, fi0;
+        footprint_origin(f, T::FX, FH, tx, ty, TILE, fj0, fi0);
+        const uint32_t m = classify<CUT>(a, c, bx, fj0, fi0, FH);
+        live |= (m & 1u) << f;
+        full |= ((m >> 1) & 1u) << f;
       }
     }
-    tq_end(S.Q, pending);
+    const uint32_t nfl = __popc(full), npt = __popc(live & ~full);
+    uint32_t tot;
+    const uint32_t pos = bwd_block_scan(nfl | (npt << 16), S.warp_tot, &tot);
+    const int nf_all = tot & 0xffff, np_all = tot >> 16;
+    uint32_t pf = pos & 0xffff, pp = pos >> 16;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      if (!((live >> f) & 1u)) continue;
+      const uint16_t it = (uint16_t)(tid | (f << 8));
+      if ((full >> f) & 1u) S.items[pf++] = it;
+      else S.items[CAP - 1 - pp++] = it;
+    }
+    consumers_sync();
+    const int n = nf_all + np_all;
+    evaluated += (unsigned long long)n;
+    for (int q = tid; q < n; q += kBwdConsumers) {
+      if (q < nf_all)
+        bwd_item<TILE, FH, CUT, false>(S, R, S.items[q], tx, ty, v.rec_grad);
+      else
+        bwd_item<TILE, FH, CUT, true>(S, R, S.items[CAP - 1 - (q - nf_all)], tx, ty, v.rec_grad);
+    }
+    mbar_arrive(&S.bars.empty[s]);
   }
   if (tid == 0 && evaluated)
     atomicAdd(reinterpret_cast<unsigned long long*>(&v.hdr->st.evaluated_pairs_bwd),
