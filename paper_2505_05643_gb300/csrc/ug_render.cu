@@ -270,62 +270,35 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
 }
 
 // ------------------------------------------------------------------ backward
-constexpr int kBwdConsumers = 128;                // consumer threads (4 warps)
-constexpr int kBwdThreads = kBwdConsumers + 32;   // plus the producer warp
+template <int TILE, int FH>
+struct BwdShape {
+  using T = Tiling<TILE, FH>;
+  static constexpr int NW = T::NF;     // one consumer warp per footprint
+  static constexpr int NCT = 32 * NW;  // consumer threads
+  static constexpr int NT = NCT + 32;  // plus the producer warp
+};
+
+constexpr int kBwdQueue = 64;  // work items a consumer warp holds (two rounds)
+
+// A consumer warp's queue of work items (copies of the record, so that the
+// stage can be released before the items are processed), in a ring.
+struct BwdQueue {
+  float4 a[kBwdQueue];
+  float4 b[kBwdQueue];
+  uint32_t clip[kBwdQueue];
+  uint32_t rid[kBwdQueue];
+};
 
 template <int TILE, int FH>
 struct BwdSmem {
-  using T = Tiling<TILE, FH>;
+  using Sh = BwdShape<TILE, FH>;
   RecStage<TILE, true> st[kStages];
   PipeBars bars;
-  uint16_t items[kBatch * T::NF];          // record | footprint << 8; full from the front
-  // per footprint, row y and column pair cp (index 4 y + cp): r0, r1, -rC0, -rC1;
-  // one float4 of padding per footprint so that lanes reading the same (y, cp)
-  // of different footprints hit different banks
-  float4 pix[T::NF][FH * 4 + 1];
-  uint32_t warp_tot[kBwdConsumers / 32];
+  BwdQueue q[Sh::NW];
+  // per footprint, row y and column pair cp (index 4 y + cp): r0, r1, -rC0, -rC1
+  float4 pix[Sh::NW][FH * 4];
   PlaneTable Tb;
 };
-
-// Barrier 1 joins the consumer warps only (the producer never takes part).
-__device__ __forceinline__ void consumers_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kBwdConsumers) : "memory");
-}
-
-// Consumer barrier that also returns whether any consumer thread passed true.
-__device__ __forceinline__ bool consumers_any(bool q) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, c;\n\t"
-      "setp.ne.u32 c, %1, 0;\n\t"
-      "bar.red.or.pred p, 1, %2, c;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)q), "n"(kBwdConsumers)
-      : "memory");
-  return r != 0;
-}
-
-// Exclusive scan over the consumer threads of one value per thread.
-__device__ __forceinline__ uint32_t bwd_block_scan(uint32_t x, uint32_t* warp_tot, uint32_t* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) warp_tot[warp] = incl;
-  consumers_sync();
-  uint32_t base = 0, tot = 0;
-#pragma unroll
-  for (int w = 0; w < kBwdConsumers / 32; ++w) {
-    if (w < warp) base += warp_tot[w];
-    tot += warp_tot[w];
-  }
-  *total = tot;
-  return base + incl - x;
-}
 
 // One lane, one work item: sums over the footprint's 8 x FH pixels of
 //   acc0 = sum r w                (dL/dc),
@@ -334,38 +307,25 @@ __device__ __forceinline__ uint32_t bwd_block_scan(uint32_t x, uint32_t* warp_to
 //   acc4 = sum g t1 dx, acc5 = sum g t1 dy, acc6 = sum g t2 dy,
 // with r = G / alpha and dL/dw = r (c - C) at each pixel (Eq. us-render
 // differentiated, box fixed); the chain kernel turns them into the gradients
-// of x*, r11, r12, r22. Pixels outside the box (PARTIAL) or the ellipsoid
-// (CUT) get w = 0 through an exponent of -inf, never a NaN: every factor
-// that multiplies w stays finite.
-template <int TILE, int FH, int CUT, bool PARTIAL>
-__device__ __forceinline__ void bwd_item(const BwdSmem<TILE, FH>& S, const RecStage<TILE, true>& R,
-                                         int item, int tx, int ty, float* __restrict__ rec_grad) {
-  using T = Tiling<TILE, FH>;
-  const int r = item & 0xff, f = item >> 8;
-  const float4 a = R.a[r], bb = R.b[r];
-  int fj0, fi0;
-  footprint_origin(f, T::FX, FH, tx, ty, TILE, fj0, fi0);
+// of x*, r11, r12, r22. Pixels outside the box or the ellipsoid (CUT) get
+// w = 0 through an exponent of -inf, never a NaN: every factor that
+// multiplies w stays finite.
+template <int FH, int CUT>
+__device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, uint32_t cl,
+                                         uint32_t rid, const float4* __restrict__ pix, int fj0,
+                                         int fi0, float* __restrict__ rec_grad) {
   const float2 r11 = make_float2(a.z, a.z), r12 = make_float2(a.w, a.w);
   const float2 r22 = make_float2(bb.x, bb.x), lw = make_float2(bb.y, bb.y);
   const float2 cc = make_float2(bb.z, bb.z), nx = make_float2(-a.x, -a.x);
-  float2 dx[4], pen[4];
+  const int cx0 = cl & 0xff, cx1 = (cl >> 8) & 0xff, ry0 = (cl >> 16) & 0xff, ry1 = cl >> 24;
+  float2 dx[4], lwc[4];  // lw2 per column pair, -inf outside the box's columns
 #pragma unroll
   for (int cp = 0; cp < 4; ++cp) {
     const float xj = (float)(fj0 + 2 * cp) + 0.5f;
     dx[cp] = __fadd2_rn(make_float2(xj, xj + 1.f), nx);
-    pen[cp] = make_float2(0.f, 0.f);
-  }
-  int ry0 = 0, ry1 = FH - 1;
-  if (PARTIAL) {
-    const uint32_t cl = clip_box(R.box[r], fj0, fi0, FH);
-    const int cx0 = cl & 0xff, cx1 = (cl >> 8) & 0xff;
-    ry0 = (cl >> 16) & 0xff;
-    ry1 = cl >> 24;
-#pragma unroll
-    for (int cp = 0; cp < 4; ++cp) {
-      if (2 * cp < cx0 || 2 * cp > cx1) pen[cp].x = -INFINITY;
-      if (2 * cp + 1 < cx0 || 2 * cp + 1 > cx1) pen[cp].y = -INFINITY;
-    }
+    lwc[cp] = lw;
+    if (2 * cp < cx0 || 2 * cp > cx1) lwc[cp].x = -INFINITY;
+    if (2 * cp + 1 < cx0 || 2 * cp + 1 > cx1) lwc[cp].y = -INFINITY;
   }
   float2 s0 = make_float2(0.f, 0.f), a4 = make_float2(0.f, 0.f);
   float s1 = 0.f, u1 = 0.f, u2 = 0.f, a5 = 0.f, a6 = 0.f;
@@ -375,20 +335,22 @@ __device__ __forceinline__ void bwd_item(const BwdSmem<TILE, FH>& S, const RecSt
     const float2 dy = make_float2(dyv, dyv);
     const float2 r12dy = __fmul2_rn(r12, dy);
     const float2 t2 = __fmul2_rn(r22, dy);
-    float2 c2 = __ffma2_rn(neg2(t2), t2, lw);  // lw2 - t2^2
-    if (PARTIAL && (y < ry0 || y > ry1)) c2 = make_float2(-INFINITY, -INFINITY);
+    const float2 nt2sq = __fmul2_rn(neg2(t2), t2);
+    const bool row_in = y >= ry0 && y <= ry1;
     float2 s1r = make_float2(0.f, 0.f), u1r = make_float2(0.f, 0.f);
 #pragma unroll
     for (int cp = 0; cp < 4; ++cp) {
       const float2 t1 = __ffma2_rn(r11, dx[cp], r12dy);
-      float2 e2 = __ffma2_rn(neg2(t1), t1, PARTIAL ? __fadd2_rn(c2, pen[cp]) : c2);  // lw2 - q
+      // lw2 - t2^2 - t1^2
+      float2 e2 = __ffma2_rn(neg2(t1), t1, __fadd2_rn(lwc[cp], nt2sq));
+      if (!row_in) e2 = make_float2(-INFINITY, -INFINITY);
       if (CUT) {
         const float2 q = __ffma2_rn(t1, t1, __fmul2_rn(t2, t2));
         if (!(q.x <= bb.w)) e2.x = -INFINITY;
         if (!(q.y <= bb.w)) e2.y = -INFINITY;
       }
       const float2 w = make_float2(fast_exp2(e2.x), fast_exp2(e2.y));
-      const float4 px = S.pix[f][4 * y + cp];
+      const float4 px = pix[4 * y + cp];
       const float2 rr = make_float2(px.x, px.y);
       const float2 g = __fmul2_rn(__ffma2_rn(rr, cc, make_float2(px.z, px.w)), w);  // w dL/dw
       s0 = __ffma2_rn(rr, w, s0);
@@ -404,7 +366,6 @@ __device__ __forceinline__ void bwd_item(const BwdSmem<TILE, FH>& S, const RecSt
     u2 = fmaf(t2.x, sr, u2);
     a6 = fmaf(t2.x, dyv * sr, a6);
   }
-  const uint32_t rid = R.rid[r];
   float* dst = rec_grad + (size_t)rid * 8;
   atomicAdd(dst + 0, s0.x + s0.y);
   atomicAdd(dst + 1, s1);
@@ -415,44 +376,50 @@ __device__ __forceinline__ void bwd_item(const BwdSmem<TILE, FH>& S, const RecSt
   atomicAdd(dst + 6, a6);
 }
 
+// Each consumer warp owns one footprint of the tile. It classifies the
+// stage's records for its footprint, copies the live ones into its queue and
+// processes the queue 32 items at a time, one item per lane; the last items
+// of a tile are processed when the tile ends. The warps share no barrier.
 template <int TILE, int FH, int CUT>
-__global__ void __launch_bounds__(kBwdThreads)
+__global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
     k_render_bwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles,
                  const float* __restrict__ image, const float* __restrict__ alpha,
                  const float* __restrict__ grad_image) {
+  using Sh = BwdShape<TILE, FH>;
   using T = Tiling<TILE, FH>;
-  constexpr int NF = T::NF, CAP = kBatch * T::NF;
-  __shared__ BwdSmem<TILE, FH> S;
-  const int tid = threadIdx.x;
-  pipe_init(S.Tb, S.bars, v, P, kBwdConsumers);
-  // the whole CTA leaves, or none of it (the consumer barriers need all 128)
-  if (__syncthreads_or(dev_failed(v.hdr))) return;
-  if (tid >= kBwdConsumers) {
-    produce<TILE, true, true, false>(S.st, S.bars, S.Tb, v, vals, 1, P, total_tiles, grad_image, alpha,
-                               image);
+  constexpr int NW = Sh::NW;
+  extern __shared__ __align__(16) unsigned char bwd_smem[];
+  BwdSmem<TILE, FH>& S = *reinterpret_cast<BwdSmem<TILE, FH>*>(bwd_smem);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  pipe_init(S.Tb, S.bars, v, P, Sh::NCT);
+  if (__syncthreads_or(dev_failed(v.hdr))) return;  // the whole CTA leaves, or none of it
+  if (warp == NW) {
+    produce<TILE, true, true, false>(S.st, S.bars, S.Tb, v, vals, 1, P, total_tiles, grad_image,
+                                     alpha, image);
     return;
   }
+  const uint32_t lt = lanemask_lt();
+  BwdQueue& Q = S.q[warp];
+  const float4* pix = S.pix[warp];
   unsigned long long evaluated = 0;
-  int tx = 0, ty = 0;
+  int fj0 = 0, fi0 = 0;
+  uint32_t head = 0, count = 0;  // queue ring position and fill
   for (uint32_t k = 0;; ++k) {
     const int s = (int)(k % kStages);
-    const bool ok = mbar_wait(&S.bars.full[s], (k / kStages) & 1u);
-    // every consumer reaches this barrier, so a wait that gave up in one warp
-    // ends all of them together (and the previous stage's items are consumed)
-    if (consumers_any(!ok)) {
-      if (!ok) dev_fail(v.hdr, UG_ERR_TIMEOUT, 2);
+    if (!mbar_wait(&S.bars.full[s], (k / kStages) & 1u)) {
+      dev_fail(v.hdr, UG_ERR_TIMEOUT, 2);
       break;
     }
     const RecStage<TILE, true>& R = S.st[s];
     const StageHdr h = R.h;
     if (h.tile < 0) break;
     if (h.flags & kFirst) {
-      // per-pixel factors of the tile: r = G / alpha and -r C (0 off the plane)
-      tx = h.tx;
-      ty = h.ty;
-      for (int q = tid; q < NF * FH * 4; q += kBwdConsumers) {
-        const int f = q / (FH * 4), y = (q / 4) % FH, cp = q % 4;
-        const int p0 = ((f / T::FX) * FH + y) * TILE + (f % T::FX) * 8 + 2 * cp;
+      // per-pixel factors of this warp's footprint: r = G / alpha and -r C
+      // (0 off the plane); the previous tile's items are all processed
+      footprint_origin(warp, T::FX, FH, h.tx, h.ty, TILE, fj0, fi0);
+      for (int q = lane; q < FH * 4; q += 32) {
+        const int y = q / 4, cp = q % 4;
+        const int p0 = ((warp / T::FX) * FH + y) * TILE + (warp % T::FX) * 8 + 2 * cp;
         float v4[4];
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
@@ -460,48 +427,48 @@ __global__ void __launch_bounds__(kBwdThreads)
           v4[hh] = rv;
           v4[2 + hh] = -rv * R.raw[2][p0 + hh];
         }
-        S.pix[f][4 * y + cp] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+        S.pix[warp][q] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+      }
+      __syncwarp();
+    }
+    for (int base = 0; base < h.cnt; base += 32) {
+      const int r = base + lane;
+      float4 a, c;
+      uint2 bx;
+      uint32_t m = 0;
+      if (r < h.cnt) {
+        a = R.a[r];
+        c = R.b[r];
+        bx = R.box[r];
+        m = classify<CUT>(a, c, bx, fj0, fi0, FH);
+      }
+      const uint32_t bl = __ballot_sync(0xffffffffu, m & 1u);
+      if (m & 1u) {
+        const uint32_t slot = (head + count + __popc(bl & lt)) % kBwdQueue;
+        Q.a[slot] = a;
+        Q.b[slot] = c;
+        Q.clip[slot] = clip_box(bx, fj0, fi0, FH);
+        Q.rid[slot] = R.rid[r];
+      }
+      count += __popc(bl);
+      evaluated += __popc(bl);
+      __syncwarp();
+      // full rounds; at the end of the tile also the rest
+      const bool tile_end = (h.flags & kLast) && base + 32 >= h.cnt;
+      while (count >= 32 || (tile_end && count > 0)) {
+        const uint32_t n = min(count, 32u);
+        if (lane < (int)n) {
+          const uint32_t e = (head + lane) % kBwdQueue;
+          bwd_item<FH, CUT>(Q.a[e], Q.b[e], Q.clip[e], Q.rid[e], pix, fj0, fi0, v.rec_grad);
+        }
+        head = (head + n) % kBwdQueue;
+        count -= n;
+        __syncwarp();
       }
     }
-    // work items of this thread's record: full-box ones from the front of the
-    // list, partial ones from the back, positions from one block scan
-    uint32_t live = 0, full = 0;
-    if (tid < h.cnt) {
-      const float4 a = R.a[tid], c = R.b[tid];
-      const uint2 bx = R.box[tid];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        int fj0, fi0;
-        footprint_origin(f, T::FX, FH, tx, ty, TILE, fj0, fi0);
-        const uint32_t m = classify<CUT>(a, c, bx, fj0, fi0, FH);
-        live |= (m & 1u) << f;
-        full |= ((m >> 1) & 1u) << f;
-      }
-    }
-    const uint32_t nfl = __popc(full), npt = __popc(live & ~full);
-    uint32_t tot;
-    const uint32_t pos = bwd_block_scan(nfl | (npt << 16), S.warp_tot, &tot);
-    const int nf_all = tot & 0xffff, np_all = tot >> 16;
-    uint32_t pf = pos & 0xffff, pp = pos >> 16;
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      if (!((live >> f) & 1u)) continue;
-      const uint16_t it = (uint16_t)(tid | (f << 8));
-      if ((full >> f) & 1u) S.items[pf++] = it;
-      else S.items[CAP - 1 - pp++] = it;
-    }
-    consumers_sync();
-    const int n = nf_all + np_all;
-    evaluated += (unsigned long long)n;
-    for (int q = tid; q < n; q += kBwdConsumers) {
-      if (q < nf_all)
-        bwd_item<TILE, FH, CUT, false>(S, R, S.items[q], tx, ty, v.rec_grad);
-      else
-        bwd_item<TILE, FH, CUT, true>(S, R, S.items[CAP - 1 - (q - nf_all)], tx, ty, v.rec_grad);
-    }
-    mbar_arrive(&S.bars.empty[s]);
+    mbar_arrive(&S.bars.empty[s]);  // the stage is no longer read by this thread
   }
-  if (tid == 0 && evaluated)
+  if (lane == 0 && evaluated)
     atomicAdd(reinterpret_cast<unsigned long long*>(&v.hdr->st.evaluated_pairs_bwd),
               evaluated * (unsigned long long)(8 * FH));
 }
@@ -517,9 +484,9 @@ __global__ void k_zero_rec_grad(WsView v, int64_t cap) {
 
 // ------------------------------------------------------------------ variants
 template <typename K>
-static int occupancy_grid(K kernel, int threads) {
+static int occupancy_grid(K kernel, int threads, size_t dyn_smem = 0) {
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, dyn_smem);
   return device_sms() * (occ > 0 ? occ : 1);
 }
 
@@ -538,9 +505,14 @@ template <int TILE, int FH, int CUT>
 static cudaError_t bwd_launch(const ug_plan* plan, WsView v, const uint32_t* vals,
                               const float* image, const float* alpha, const float* grad,
                               cudaStream_t s) {
-  static const int grid = occupancy_grid(k_render_bwd<TILE, FH, CUT>, kBwdThreads);
+  constexpr int NT = BwdShape<TILE, FH>::NT;
+  constexpr size_t SM = sizeof(BwdSmem<TILE, FH>);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k_render_bwd<TILE, FH, CUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
+  if (attr != cudaSuccess) return attr;
+  static const int grid = occupancy_grid(k_render_bwd<TILE, FH, CUT>, NT, SM);
   const int g = min(grid, max(plan->total_tiles, 1));
-  k_render_bwd<TILE, FH, CUT><<<g, kBwdThreads, 0, s>>>(v, vals, plan->num_planes,
+  k_render_bwd<TILE, FH, CUT><<<g, NT, SM, s>>>(v, vals, plan->num_planes,
                                                          plan->total_tiles, image, alpha, grad);
   return cudaGetLastError();
 }
