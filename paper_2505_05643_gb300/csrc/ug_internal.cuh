@@ -56,7 +56,11 @@ struct WsHeader {
   unsigned long long box_pixels;
   uint32_t holes;             // candidates rejected by the exact test (empty slots)
   uint32_t kept64;            // visible records of the FP64 list
-  uint32_t pad1[40];
+  // non-zero: the forward rasterizer has written every sorted instance's 8x8
+  // footprint tests since the last bin/sort (cleared by bin/sort and by the
+  // scatter forward)
+  uint32_t fwd_masks;
+  uint32_t pad1[39];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 

@@ -100,19 +100,21 @@ struct StageHdr {
   int32_t tx, ty, w, h;
   int32_t cnt;    // records in this stage
   int32_t flags;  // kFirst | kLast
-  int32_t pad;
+  uint32_t inst0; // sorted instance of the stage's first record
   int64_t px_off;
 };
 
-// One stage: up to kBatch records of one tile; with RAW, the first stage of a
-// tile also carries the tile's pixel inputs of the backward pass (dL/dC,
-// alpha, C; pixels off the plane hold 0, 1, 0).
+// One stage: up to kBatch records of one tile; with RAW (the backward pass),
+// the first stage of a tile also carries the tile's pixel inputs (dL/dC,
+// alpha, C; pixels off the plane hold 0, 1, 0), and every stage the forward
+// pass's footprint tests of its instances (when they are valid).
 template <int TILE, bool RAW>
 struct RecStage {
   float4 a[kBatch];
   float4 b[kBatch];
   uint2 box[kBatch];
   uint32_t rid[kBatch];
+  uint32_t mask[RAW ? kBatch : 1];
   StageHdr h;
   float raw[RAW ? 3 : 1][RAW ? TILE * TILE : 1];
 };
@@ -167,7 +169,8 @@ __device__ __forceinline__ void pipe_init(PlaneTable& T, PipeBars& bars, const W
 // k - kStages. The record ids are read into registers, the records themselves
 // (and the backward's pixel inputs) are copied with cp.async, whose completion
 // arrives on the stage's full barrier, so up to kStages batches of gathers
-// are in flight. RID: the stage also keeps the record ids. EMPTY_TILES: tiles
+// are in flight. RID: the stage also keeps the record ids. inst_mask (RAW
+// only, may be null): per sorted instance, copied into the stage. EMPTY_TILES: tiles
 // without records still get one stage (the forward pass writes their
 // background pixels).
 template <int TILE, bool RAW, bool RID, bool EMPTY_TILES>
@@ -176,7 +179,8 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
                                         const uint32_t* __restrict__ vals, int which, int P,
                                         int total_tiles, const float* __restrict__ grad,
                                         const float* __restrict__ alpha,
-                                        const float* __restrict__ image) {
+                                        const float* __restrict__ image,
+                                        const uint32_t* __restrict__ inst_mask) {
   const int lane = threadIdx.x & 31;
   constexpr int PER = kBatch / 32;
   uint32_t k = 0;
@@ -229,6 +233,9 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
             cp_async16(&S.b[r], v.rec_b + rid[q]);
             cp_async8(&S.box[r], v.rec_box + rid[q]);
             if (RID) S.rid[r] = rid[q];
+            if constexpr (RAW) {
+              if (inst_mask) cp_async4(&S.mask[r], inst_mask + b + r);
+            }
           }
         }
         if constexpr (RAW) {
@@ -257,7 +264,7 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
           hd.h = h;
           hd.cnt = cnt;
           hd.flags = (b == rg.x ? kFirst : 0) | (b + kBatch >= rg.y ? kLast : 0);
-          hd.pad = 0;
+          hd.inst0 = b;
           hd.px_off = px_off;
           S.h = hd;
         }

@@ -22,7 +22,9 @@
 //
 // Forward: one consumer warp per 8x8 footprint, which classifies the stage's
 // records for its own footprint and is otherwise independent of the other
-// warps. The warp is split into G lane groups that each cover the whole
+// warps. It stores its test of every instance (byte f of a 32-bit word per
+// sorted instance: bit 0 live, bit 1 box covers the footprint), which the
+// backward pass with the same footprints reads instead of testing again. The warp is split into G lane groups that each cover the whole
 // footprint (2G pixels of one column per lane) and take every G-th work item;
 // per pixel S_a += w, S_c += w c, the groups' sums are added at the end of the
 // tile, then C = (S_c + a_bg c_bg) / (S_a + a_bg) (Eq. alpha-combine, Eq.
@@ -150,7 +152,8 @@ __device__ __forceinline__ void fwd_item(const FwdChunk& C, int e, float2 pxx, c
 template <int TILE, int G, int CUT>
 __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
     k_render_fwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles, float abg,
-                 float cbg, float* __restrict__ image, float* __restrict__ alpha) {
+                 float cbg, float* __restrict__ image, float* __restrict__ alpha,
+                 uint8_t* __restrict__ inst_mask) {
   using Sh = FwdShape<TILE, G>;
   constexpr int NW = Sh::NW, LG = Sh::LG, PPT = Sh::PPT, NP = Sh::NP;
   __shared__ FwdSmem<TILE, NW> S;
@@ -158,8 +161,8 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
   pipe_init(S.T, S.bars, v, P, Sh::NCT);
   if (__syncthreads_or(dev_failed(v.hdr))) return;  // the whole CTA leaves, or none of it
   if (warp == NW) {
-    produce<TILE, false, false, true>(S.st, S.bars, S.T, v, vals, 0, P, total_tiles, nullptr, nullptr,
-                               nullptr);
+    produce<TILE, false, false, true>(S.st, S.bars, S.T, v, vals, 0, P, total_tiles, nullptr,
+                                      nullptr, nullptr, nullptr);
     return;
   }
   const int grp = lane / LG, gl = lane % LG;
@@ -200,6 +203,7 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
     for (int base = 0; base < h.cnt; base += 32) {
       const int r = base + lane;
       const uint32_t m = r < h.cnt ? classify<CUT>(R.a[r], R.b[r], R.box[r], fj0, fi0, 8) : 0u;
+      if (r < h.cnt) inst_mask[(size_t)(h.inst0 + r) * 4 + warp] = (uint8_t)m;
       const bool live = m & 1u, full = m & 2u;
       const uint32_t bf = __ballot_sync(0xffffffffu, live && full);
       const uint32_t bp = __ballot_sync(0xffffffffu, live && !full);
@@ -384,7 +388,7 @@ template <int TILE, int FH, int CUT>
 __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
     k_render_bwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles,
                  const float* __restrict__ image, const float* __restrict__ alpha,
-                 const float* __restrict__ grad_image) {
+                 const float* __restrict__ grad_image, const uint32_t* __restrict__ inst_mask) {
   using Sh = BwdShape<TILE, FH>;
   using T = Tiling<TILE, FH>;
   constexpr int NW = Sh::NW;
@@ -393,9 +397,11 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   pipe_init(S.Tb, S.bars, v, P, Sh::NCT);
   if (__syncthreads_or(dev_failed(v.hdr))) return;  // the whole CTA leaves, or none of it
+  // the forward pass's tests apply when its footprints are these (8 rows)
+  const bool use_masks = FH == 8 && *(volatile const uint32_t*)&v.hdr->fwd_masks != 0;
   if (warp == NW) {
     produce<TILE, true, true, false>(S.st, S.bars, S.Tb, v, vals, 1, P, total_tiles, grad_image,
-                                     alpha, image);
+                                     alpha, image, use_masks ? inst_mask : nullptr);
     return;
   }
   const uint32_t lt = lanemask_lt();
@@ -433,21 +439,15 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
     }
     for (int base = 0; base < h.cnt; base += 32) {
       const int r = base + lane;
-      float4 a, c;
-      uint2 bx;
       uint32_t m = 0;
-      if (r < h.cnt) {
-        a = R.a[r];
-        c = R.b[r];
-        bx = R.box[r];
-        m = classify<CUT>(a, c, bx, fj0, fi0, FH);
-      }
+      if (r < h.cnt)
+        m = use_masks ? R.mask[r] >> (8 * warp) : classify<CUT>(R.a[r], R.b[r], R.box[r], fj0, fi0, FH);
       const uint32_t bl = __ballot_sync(0xffffffffu, m & 1u);
       if (m & 1u) {
         const uint32_t slot = (head + count + __popc(bl & lt)) % kBwdQueue;
-        Q.a[slot] = a;
-        Q.b[slot] = c;
-        Q.clip[slot] = clip_box(bx, fj0, fi0, FH);
+        Q.a[slot] = R.a[r];
+        Q.b[slot] = R.b[r];
+        Q.clip[slot] = clip_box(R.box[r], fj0, fi0, FH);
         Q.rid[slot] = R.rid[r];
       }
       count += __popc(bl);
@@ -483,6 +483,13 @@ __global__ void k_zero_rec_grad(WsView v, int64_t cap) {
 }
 
 // ------------------------------------------------------------------ variants
+// The forward pass's per-instance footprint tests live in the key buffer that
+// the radix sort left unused (it held the last pass's input), one 32-bit word
+// per sorted instance; the next bin/sort overwrites it and clears the flag.
+static uint32_t* inst_masks(const ug_plan* plan, const WsView& v) {
+  return v.keys[(plan->sort_passes & 1) ^ 1];
+}
+
 template <typename K>
 static int occupancy_grid(K kernel, int threads, size_t dyn_smem = 0) {
   int occ = 0;
@@ -497,7 +504,8 @@ static cudaError_t fwd_launch(const ug_plan* plan, WsView v, const uint32_t* val
   static const int grid = occupancy_grid(k_render_fwd<TILE, G, CUT>, NT);
   const int g = min(grid, max(plan->total_tiles, 1));
   k_render_fwd<TILE, G, CUT><<<g, NT, 0, s>>>(v, vals, plan->num_planes, plan->total_tiles,
-                                              plan->cfg.alpha_bg, plan->cfg.c_bg, image, alpha);
+                                              plan->cfg.alpha_bg, plan->cfg.c_bg, image, alpha,
+                                              reinterpret_cast<uint8_t*>(inst_masks(plan, v)));
   return cudaGetLastError();
 }
 
@@ -512,8 +520,8 @@ static cudaError_t bwd_launch(const ug_plan* plan, WsView v, const uint32_t* val
   if (attr != cudaSuccess) return attr;
   static const int grid = occupancy_grid(k_render_bwd<TILE, FH, CUT>, NT, SM);
   const int g = min(grid, max(plan->total_tiles, 1));
-  k_render_bwd<TILE, FH, CUT><<<g, NT, SM, s>>>(v, vals, plan->num_planes,
-                                                         plan->total_tiles, image, alpha, grad);
+  k_render_bwd<TILE, FH, CUT><<<g, NT, SM, s>>>(v, vals, plan->num_planes, plan->total_tiles,
+                                                image, alpha, grad, inst_masks(plan, v));
   return cudaGetLastError();
 }
 
@@ -548,10 +556,13 @@ cudaError_t launch_render(const ug_plan* plan, WsView v, float* image, float* al
   if (e != cudaSuccess) return e;
   const uint32_t* vals = v.vals[plan->sort_passes & 1];
   if (plan->cfg.tile == 16)
-    return plan->cfg.cutoff ? dispatch_fwd<16, 1>(plan, v, vals, image, alpha, s)
-                            : dispatch_fwd<16, 0>(plan, v, vals, image, alpha, s);
-  return plan->cfg.cutoff ? dispatch_fwd<8, 1>(plan, v, vals, image, alpha, s)
-                          : dispatch_fwd<8, 0>(plan, v, vals, image, alpha, s);
+    e = plan->cfg.cutoff ? dispatch_fwd<16, 1>(plan, v, vals, image, alpha, s)
+                         : dispatch_fwd<16, 0>(plan, v, vals, image, alpha, s);
+  else
+    e = plan->cfg.cutoff ? dispatch_fwd<8, 1>(plan, v, vals, image, alpha, s)
+                         : dispatch_fwd<8, 0>(plan, v, vals, image, alpha, s);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(&v.hdr->fwd_masks, 0xff, sizeof(uint32_t), s);
 }
 
 cudaError_t launch_render_backward_raster(const ug_plan* plan, WsView v, const float* image,

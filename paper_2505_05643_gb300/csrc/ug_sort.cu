@@ -141,6 +141,8 @@ cudaError_t launch_bin_sort(const ug_plan* plan, WsView v, cudaStream_t s) {
                                                            v.vals[dst], shift, nblk, v);
   }
   cudaError_t e = cudaMemsetAsync(v.ranges, 0, sizeof(uint2) * (size_t)plan->total_tiles, s);
+  // the forward rasterizer's footprint tests belong to the previous order
+  if (e == cudaSuccess) e = cudaMemsetAsync(&v.hdr->fwd_masks, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

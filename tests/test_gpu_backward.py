@@ -124,6 +124,45 @@ def test_grad_variants(tile, variant):
     _check_grads(gpu, gref, gabs, oracle.param_names(1), f"variant t{tile} v{variant}")
 
 
+@pytest.mark.parametrize("tile", [16, 8])
+def test_grad_with_and_without_forward_footprint_tests(tile):
+    """The backward rasterizer reads the forward rasterizer's per-instance
+    footprint tests when they belong to the current sort, and tests the
+    footprints itself otherwise (here: after the scatter forward, which leaves
+    none): both evaluate the same pairs and give the same gradient up to the
+    order of the atomic additions, on an extreme-anisotropy scene with many
+    culled footprints."""
+    rng = np.random.default_rng(37)
+    g, pl = synth.workload_aniso_1m()
+    g = {k: v[..., :20000] for k, v in g.items()}
+    g = synth.scale_rot_to_tri(g, 1e-4)
+    pl = synth.planes_random(rng, [(128, 128), (96, 160)])
+    cfg = R.make_config(cov_param=B.UG_COV_TRI, tile=tile, variant=0, variant_bwd=0)
+    r, params, image, alpha = gpu_render(g, pl, cfg)
+    gi = torch.from_numpy(rng.normal(0, 1, pl["total_pixels"]).astype(np.float32)).cuda()
+    im_t = torch.from_numpy(image.astype(np.float32)).cuda()
+    al_t = torch.from_numpy(alpha.astype(np.float32)).cuda()
+
+    def gradient():
+        grads = torch.empty_like(params)
+        B.ug_render_backward_raster(r.plan, r.ws, im_t, al_t, gi)
+        B.ug_preprocess_backward(r.plan, R.gaussians_struct(params, r.cov), r.ws,
+                                 R.grads_struct(grads, r.cov))
+        torch.cuda.synchronize()
+        st = r.status()
+        assert st["status"] == B.UG_OK
+        return grads.cpu().numpy().astype(np.float64), st["evaluated_pairs_bwd"]
+
+    with_tests, ev1 = gradient()
+    im2, al2 = torch.empty_like(im_t), torch.empty_like(al_t)
+    B.ug_render_scatter(r.plan, r.ws, im2, al2)
+    without, ev2 = gradient()
+    assert ev1 == ev2 > 0
+    scale = np.abs(with_tests).max(axis=1, keepdims=True) + 1e-30  # per parameter row
+    err = np.abs(with_tests - without)
+    assert np.all(err <= 1e-5 * scale + 1e-4 * np.abs(without)), (err / scale).max(axis=1)
+
+
 def test_grad_50k_16_planes_subset_and_fd():
     """50,000 scale/rotation Gaussians, 16 planes of 256x256, MSE against
     targets rendered by the oracle from a separate seed-1 set of 50,000;
