@@ -219,9 +219,8 @@ __device__ __forceinline__ float rect_q_lower_bound(const float4& a, float r22, 
 __device__ __forceinline__ bool rect_live(const float4& a, const float4& b, int xa, int xb, int ya,
                                           int yb, int cut) {
   const float q = rect_q_lower_bound(a, b.x, xa, xb, ya, yb);
-  if (__fsub_rn(b.y, q) < -127.f) return false;
-  if (cut && q > __fmaf_rn(b.w, 1.0001f, 1e-6f)) return false;
-  return true;
+  // without branches (bitwise &): lanes of a warp test different records
+  return !(__fsub_rn(b.y, q) < -127.f) & !((cut != 0) & (q > __fmaf_rn(b.w, 1.0001f, 1e-6f)));
 }
 
 // ------------------------------------------------------------------ launchers

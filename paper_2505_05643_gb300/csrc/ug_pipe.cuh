@@ -21,6 +21,9 @@ constexpr int kFirst = 1;     // stage flag: first batch of its tile
 constexpr int kLast = 2;      // stage flag: last batch of its tile
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
 constexpr uint32_t kWaitLimitIters = 1u << 30;
+// A waiting thread sleeps until the phase completes or this long (ns), so
+// waiting warps take no issue slots from the working ones.
+constexpr uint32_t kSuspendHintNs = 20000;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -46,10 +49,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "n"(kSuspendHintNs)
       : "memory");
   return ok != 0;
 }
@@ -173,6 +176,34 @@ __device__ __forceinline__ void pipe_init(PlaneTable& T, PipeBars& bars, const W
 // only, may be null): per sorted instance, copied into the stage. EMPTY_TILES: tiles
 // without records still get one stage (the forward pass writes their
 // background pixels).
+struct TileCtx {
+  int tx, ty, w, h;
+  int64_t px_off;
+};
+
+__device__ __forceinline__ TileCtx tile_ctx(const PlaneTable& T, const WsView& v, int P, int t) {
+  int local, tiles_x;
+  TileCtx c;
+  if (P <= kSmemPlanes) {
+    const TilePlane& pl = T.pl[find_plane(T.tile_off, P, t)];
+    local = t - pl.tile_off;
+    tiles_x = pl.tiles_x;
+    c.w = pl.w;
+    c.h = pl.h;
+    c.px_off = pl.px_off;
+  } else {
+    const PlaneDev& pl = v.planes[find_plane(v.tile_off, P, t)];
+    local = t - pl.tile_off;
+    tiles_x = pl.tiles_x;
+    c.w = pl.w;
+    c.h = pl.h;
+    c.px_off = pl.px_off;
+  }
+  c.tx = local % tiles_x;
+  c.ty = local / tiles_x;
+  return c;
+}
+
 template <int TILE, bool RAW, bool RID, bool EMPTY_TILES>
 __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
                                         const PlaneTable& T, const WsView& v,
@@ -183,98 +214,117 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
                                         const uint32_t* __restrict__ inst_mask) {
   const int lane = threadIdx.x & 31;
   constexpr int PER = kBatch / 32;
+  const uint32_t total = (uint32_t)total_tiles;
+  uint32_t* counter = &v.hdr->tile_counter[which];
+  // Tile look-ahead: A is the tile being issued, B the next one (its range
+  // load in flight), C the one after (its queue reservation in flight), so
+  // neither the queue's atomic nor the range load stalls a tile change.
+  uint32_t c_pending = 0;
+  if (lane == 0) c_pending = atomicAdd(counter, 1u);
+  uint32_t tA = __shfl_sync(0xffffffffu, c_pending, 0);
+  uint2 rA = tA < total ? v.ranges[tA] : make_uint2(0u, 0u);
+  if (lane == 0) c_pending = atomicAdd(counter, 1u);
+  uint32_t tB = __shfl_sync(0xffffffffu, c_pending, 0);
+  uint2 rB = tB < total ? v.ranges[tB] : make_uint2(0u, 0u);
+  if (lane == 0) c_pending = atomicAdd(counter, 1u);
+  auto next_tile = [&]() {
+    tA = tB;
+    rA = rB;
+    tB = __shfl_sync(0xffffffffu, c_pending, 0);
+    rB = tB < total ? v.ranges[tB] : make_uint2(0u, 0u);
+    if (lane == 0 && tB < total) c_pending = atomicAdd(counter, 1u);
+    if (tB >= total) c_pending = total;
+  };
+  if (!EMPTY_TILES)
+    while (tA < total && rA.y == rA.x) next_tile();
+  TileCtx cA = tA < total ? tile_ctx(T, v, P, (int)tA) : TileCtx{};
+  uint32_t b = rA.x;
+  // record ids of the batch to issue, read one batch ahead
+  uint32_t rid[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const uint32_t r = b + lane + 32 * q;
+    rid[q] = (tA < total && r < rA.y) ? __ldg(vals + r) : 0u;
+  }
   uint32_t k = 0;
-  uint32_t t = 0;
-  if (lane == 0) t = atomicAdd(&v.hdr->tile_counter[which], 1u);
-  t = __shfl_sync(0xffffffffu, t, 0);
-  while ((int)t < total_tiles) {
-    uint32_t pending = 0;
-    if (lane == 0) pending = atomicAdd(&v.hdr->tile_counter[which], 1u);
-    int local, tiles_x, w, h;
-    int64_t px_off;
-    if (P <= kSmemPlanes) {
-      const TilePlane& pl = T.pl[find_plane(T.tile_off, P, (int)t)];
-      local = (int)t - pl.tile_off;
-      tiles_x = pl.tiles_x;
-      w = pl.w;
-      h = pl.h;
-      px_off = pl.px_off;
+  while (tA < total) {
+    // the batch to issue now
+    const uint32_t t = tA, b0 = b;
+    const uint2 rg = rA;
+    const TileCtx c = cA;
+    const int cnt = (int)min((uint32_t)kBatch, rg.y - b0);
+    const bool first = b0 == rg.x, last = b0 + kBatch >= rg.y;
+    // advance the cursor and start reading the next batch's record ids
+    if (!last) {
+      b += kBatch;
     } else {
-      const PlaneDev& pl = v.planes[find_plane(v.tile_off, P, (int)t)];
-      local = (int)t - pl.tile_off;
-      tiles_x = pl.tiles_x;
-      w = pl.w;
-      h = pl.h;
-      px_off = pl.px_off;
+      next_tile();
+      if (!EMPTY_TILES)
+        while (tA < total && rA.y == rA.x) next_tile();
+      if (tA < total) cA = tile_ctx(T, v, P, (int)tA);
+      b = rA.x;
     }
-    const int tx = local % tiles_x, ty = local / tiles_x;
-    const uint2 rg = v.ranges[t];
-    if (EMPTY_TILES || rg.y > rg.x) {
-      for (uint32_t b = rg.x;; b += kBatch) {
-        const int cnt = (int)min((uint32_t)kBatch, rg.y - b);
-        const int s = (int)(k % kStages);
-        if (k >= (uint32_t)kStages && !mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1u)) {
-          dev_fail(v.hdr, UG_ERR_TIMEOUT, 100 + which);
-          cp_async_wait_all();
-          return;
-        }
-        RecStage<TILE, RAW>& S = st[s];
-        uint32_t rid[PER];
+    uint32_t rid_next[PER];
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-          const int r = lane + 32 * q;
-          rid[q] = r < cnt ? __ldg(vals + b + r) : 0u;
-        }
+    for (int q = 0; q < PER; ++q) {
+      const uint32_t r = b + lane + 32 * q;
+      rid_next[q] = (tA < total && r < rA.y) ? __ldg(vals + r) : 0u;
+    }
+    const int s = (int)(k % kStages);
+    if (k >= (uint32_t)kStages && !mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1u)) {
+      dev_fail(v.hdr, UG_ERR_TIMEOUT, 100 + which);
+      cp_async_wait_all();
+      return;
+    }
+    RecStage<TILE, RAW>& S = st[s];
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-          const int r = lane + 32 * q;
-          if (r < cnt) {
-            cp_async16(&S.a[r], v.rec_a + rid[q]);
-            cp_async16(&S.b[r], v.rec_b + rid[q]);
-            cp_async8(&S.box[r], v.rec_box + rid[q]);
-            if (RID) S.rid[r] = rid[q];
-            if constexpr (RAW) {
-              if (inst_mask) cp_async4(&S.mask[r], inst_mask + b + r);
-            }
-          }
-        }
+    for (int q = 0; q < PER; ++q) {
+      const int r = lane + 32 * q;
+      if (r < cnt) {
+        cp_async16(&S.a[r], v.rec_a + rid[q]);
+        cp_async16(&S.b[r], v.rec_b + rid[q]);
+        cp_async8(&S.box[r], v.rec_box + rid[q]);
+        if (RID) S.rid[r] = rid[q];
         if constexpr (RAW) {
-          if (b == rg.x) {
-            for (int p = lane; p < TILE * TILE; p += 32) {
-              const int i = ty * TILE + p / TILE, j = tx * TILE + p % TILE;
-              if (i < h && j < w) {
-                const int64_t px = px_off + (int64_t)i * w + j;
-                cp_async4(&S.raw[0][p], grad + px);
-                cp_async4(&S.raw[1][p], alpha + px);
-                cp_async4(&S.raw[2][p], image + px);
-              } else {
-                S.raw[0][p] = 0.f;
-                S.raw[1][p] = 1.f;
-                S.raw[2][p] = 0.f;
-              }
-            }
-          }
+          if (inst_mask) cp_async4(&S.mask[r], inst_mask + b0 + r);
         }
-        if (lane == 0) {
-          StageHdr hd;
-          hd.tile = (int32_t)t;
-          hd.tx = tx;
-          hd.ty = ty;
-          hd.w = w;
-          hd.h = h;
-          hd.cnt = cnt;
-          hd.flags = (b == rg.x ? kFirst : 0) | (b + kBatch >= rg.y ? kLast : 0);
-          hd.inst0 = b;
-          hd.px_off = px_off;
-          S.h = hd;
-        }
-        mbar_arrive(&bars.full[s]);      // the plain shared-memory stores above
-        cp_async_arrive(&bars.full[s]);  // this lane's copies, once they have landed
-        ++k;
-        if (b + kBatch >= rg.y) break;
       }
     }
-    t = __shfl_sync(0xffffffffu, pending, 0);
+    if constexpr (RAW) {
+      if (first) {
+        for (int p = lane; p < TILE * TILE; p += 32) {
+          const int i = c.ty * TILE + p / TILE, j = c.tx * TILE + p % TILE;
+          if (i < c.h && j < c.w) {
+            const int64_t px = c.px_off + (int64_t)i * c.w + j;
+            cp_async4(&S.raw[0][p], grad + px);
+            cp_async4(&S.raw[1][p], alpha + px);
+            cp_async4(&S.raw[2][p], image + px);
+          } else {
+            S.raw[0][p] = 0.f;
+            S.raw[1][p] = 1.f;
+            S.raw[2][p] = 0.f;
+          }
+        }
+      }
+    }
+    if (lane == 0) {
+      StageHdr hd;
+      hd.tile = (int32_t)t;
+      hd.tx = c.tx;
+      hd.ty = c.ty;
+      hd.w = c.w;
+      hd.h = c.h;
+      hd.cnt = cnt;
+      hd.flags = (first ? kFirst : 0) | (last ? kLast : 0);
+      hd.inst0 = b0;
+      hd.px_off = c.px_off;
+      S.h = hd;
+    }
+    mbar_arrive(&bars.full[s]);      // the plain shared-memory stores above
+    cp_async_arrive(&bars.full[s]);  // this lane's copies, once they have landed
+    ++k;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) rid[q] = rid_next[q];
   }
   const int s = (int)(k % kStages);
   if (k >= (uint32_t)kStages && !mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1u)) {

@@ -55,15 +55,18 @@ __device__ __forceinline__ void footprint_origin(int f, int fx_count, int fh, in
 
 // Work-item test of one record against the footprint [fj0, fj0 + 7] x [fi0,
 // fi0 + fh - 1]: bit 0 live, bit 1 the box covers the footprint.
+// Branch-free: the lanes of a warp test different records.
 template <int CUT>
 __device__ __forceinline__ uint32_t classify(const float4& a, const float4& c, uint2 bx, int fj0,
                                              int fi0, int fh) {
   const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
   const int fj1 = fj0 + 7, fi1 = fi0 + fh - 1;
   const int xa = max(fj0, j0), xb = min(fj1, j1), ya = max(fi0, i0), yb = min(fi1, i1);
-  if (xa > xb || ya > yb) return 0u;
-  if (!rect_live(a, c, xa, xb, ya, yb, CUT)) return 0u;  // every weight is an FP32 zero
-  return 1u | ((j0 <= fj0 && j1 >= fj1 && i0 <= fi0 && i1 >= fi1) ? 2u : 0u);
+  // overlap, and not every weight in it an FP32 zero (the bound of an empty
+  // overlap is finite and ignored)
+  const bool live = (xa <= xb) & (ya <= yb) & rect_live(a, c, xa, xb, ya, yb, CUT);
+  const bool full = (j0 <= fj0) & (j1 >= fj1) & (i0 <= fi0) & (i1 >= fi1);
+  return (uint32_t)live | ((uint32_t)(live & full) << 1);
 }
 
 // box ∩ footprint in footprint coordinates, packed cx0 | cx1 << 8 | ry0 << 16 |
@@ -78,12 +81,16 @@ __device__ __forceinline__ uint32_t clip_box(uint2 bx, int fj0, int fi0, int fh)
 // ------------------------------------------------------------------ forward
 // A warp's current chunk of up to 32 work items (structure of arrays, one
 // slot per lane of the builder; values in pairs for the FP32x2 arithmetic).
+// Slots past the last item, up to a multiple of the lane groups, hold inert
+// items (lw2 = -inf), so that every group runs the same number of items.
 struct FwdChunk {
-  float4 nxy[32];   // -x*_j, -x*_j, -x*_i, -x*_i
-  float4 r1[32];    // r11, r11, r12, r12
-  float4 r2[32];    // r22, r22, lw2, lw2
-  float4 cv[32];    // c, c, ellipsoid threshold, 0
-  uint32_t clip[32];
+  float4 dx[2][32];  // dx of the footprint's columns 0..3 and 4..7
+  float4 p0[32];     // r11, r11, -x*_i, -x*_i
+  float4 p1[32];     // r12, r12, r22, r22
+  float4 p2[32];     // lw2, lw2, c, c
+  float4 lc[2][32];  // partial items: lw2 in the box's columns, -inf outside
+  uint32_t rows[32]; // partial items: bit y set for the box's rows
+  float thr[32];     // ellipsoid threshold (cut-off by ellipsoid)
 };
 
 template <int TILE, int G>
@@ -92,9 +99,8 @@ struct FwdShape {
   static constexpr int NW = T::NF;        // one consumer warp per 8x8 footprint
   static constexpr int NCT = 32 * NW;     // consumer threads
   static constexpr int NT = NCT + 32;     // plus the producer warp
-  static constexpr int LG = 32 / G;       // lanes per group
-  static constexpr int PPT = 2 * G;       // rows per lane
-  static constexpr int NP = G;            // row pairs per lane
+  static constexpr int LG = 32 / G;       // lanes per group: 8 rows x LG / 8 column blocks
+  static constexpr int NP = G;            // column pairs per lane
   static_assert(G == 1 || G == 2 || G == 4, "groups");
 };
 
@@ -112,41 +118,94 @@ struct FwdSmem {
 // (PARTIAL) or the ellipsoid (CUT) get e = -inf, whose ex2 is +0.
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
-template <int CUT, bool PARTIAL, int NP>
-__device__ __forceinline__ void fwd_item(const FwdChunk& C, int e, float2 pxx, const float2* py,
-                                         int lx, int row0, float2* sa, float2* sc) {
-  const float4 nxy = C.nxy[e], r1 = C.r1[e], r2 = C.r2[e], cv = C.cv[e];
-  const float2 dxx = __fadd2_rn(pxx, make_float2(nxy.x, nxy.y));
-  const float2 ny = make_float2(nxy.z, nxy.w);
-  float2 lw = make_float2(r2.z, r2.w);
-  uint32_t rows = 0;
-  if (PARTIAL) {
-    const uint32_t cl = C.clip[e];
-    const int cx0 = cl & 0xff, cx1 = (cl >> 8) & 0xff, ry0 = (cl >> 16) & 0xff, ry1 = cl >> 24;
-    if ((unsigned)(lx - cx0) > (unsigned)(cx1 - cx0)) lw = make_float2(-INFINITY, -INFINITY);
-    // bit k: row row0 + k of this lane lies in [ry0, ry1]
-    rows = (((2u << ry1) - (1u << ry0)) >> row0);
+template <int NP>
+__device__ __forceinline__ void load_pairs(const float4 (&src)[2][32], int e, int cp0,
+                                           float2 (&out)[NP]) {
+  if (NP == 4) {
+    const float4 u = src[0][e], w = src[1][e];
+    out[0] = make_float2(u.x, u.y);
+    out[1] = make_float2(u.z, u.w);
+    out[NP > 2 ? 2 : 0] = make_float2(w.x, w.y);
+    out[NP > 3 ? 3 : 0] = make_float2(w.z, w.w);
+  } else if (NP == 2) {
+    const float4 u = src[cp0 >> 1][e];
+    out[0] = make_float2(u.x, u.y);
+    out[NP > 1 ? 1 : 0] = make_float2(u.z, u.w);
+  } else {
+    const float4 u = src[cp0 >> 1][e];
+    out[0] = (cp0 & 1) ? make_float2(u.z, u.w) : make_float2(u.x, u.y);
   }
+}
+
+// One lane, one work item: row y of the footprint (pixel centre py), column
+// pairs cp0 .. cp0 + NP - 1.
+template <int CUT, bool PARTIAL, int NP>
+__device__ __forceinline__ void fwd_item(const FwdChunk& C, int e, float py, int y, int cp0,
+                                         float2* sa, float2* sc) {
+  const float4 p0 = C.p0[e], p1 = C.p1[e], p2 = C.p2[e];
+  float2 dx[NP];
+  load_pairs<NP>(C.dx, e, cp0, dx);
+  const float2 r11 = make_float2(p0.x, p0.y), r12 = make_float2(p1.x, p1.y);
+  const float2 r22 = make_float2(p1.z, p1.w), cc = make_float2(p2.z, p2.w);
+  const float2 dy = __fadd2_rn(make_float2(py, py), make_float2(p0.z, p0.w));
+  const float2 r12dy = __fmul2_rn(r12, dy);
+  const float2 t2 = __fmul2_rn(r22, dy);
+  float2 c2[NP];  // lw2 - t2^2 per column pair
+  if (PARTIAL) {
+    float2 lw[NP];
+    load_pairs<NP>(C.lc, e, cp0, lw);
+    float2 nt2sq = __fmul2_rn(neg2(t2), t2);
+    if (!((C.rows[e] >> y) & 1u)) nt2sq = make_float2(-INFINITY, -INFINITY);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) c2[p] = __fadd2_rn(lw[p], nt2sq);
+  } else {
+    const float2 c = __ffma2_rn(neg2(t2), t2, make_float2(p2.x, p2.y));
+#pragma unroll
+    for (int p = 0; p < NP; ++p) c2[p] = c;
+  }
+  float thr = 0.f;
+  if (CUT) thr = C.thr[e];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    const float2 dy = __fadd2_rn(py[p], ny);
-    const float2 t1 = __ffma2_rn(make_float2(r1.x, r1.y), dxx,
-                                 __fmul2_rn(make_float2(r1.z, r1.w), dy));
-    const float2 t2 = __fmul2_rn(make_float2(r2.x, r2.y), dy);
-    float2 e2 = __ffma2_rn(neg2(t1), t1, __ffma2_rn(neg2(t2), t2, lw));  // lw2 - q
+    const float2 t1 = __ffma2_rn(r11, dx[p], r12dy);
+    float2 e2 = __ffma2_rn(neg2(t1), t1, c2[p]);  // lw2 - q
     if (CUT) {
       const float2 q = __ffma2_rn(t1, t1, __fmul2_rn(t2, t2));
-      if (!(q.x <= cv.z)) e2.x = -INFINITY;
-      if (!(q.y <= cv.z)) e2.y = -INFINITY;
-    }
-    if (PARTIAL) {
-      if (!((rows >> (2 * p)) & 1u)) e2.x = -INFINITY;
-      if (!((rows >> (2 * p + 1)) & 1u)) e2.y = -INFINITY;
+      if (!(q.x <= thr)) e2.x = -INFINITY;
+      if (!(q.y <= thr)) e2.y = -INFINITY;
     }
     const float2 w = make_float2(fast_exp2(e2.x), fast_exp2(e2.y));
     sa[p] = __fadd2_rn(sa[p], w);
-    sc[p] = __ffma2_rn(w, make_float2(cv.x, cv.y), sc[p]);
+    sc[p] = __ffma2_rn(w, cc, sc[p]);
   }
+}
+
+// Chunk slot `lane` from the record at stage index r; real = false makes the
+// slot inert (lw2 = -inf: every weight is +0).
+template <int CUT, bool PARTIAL>
+__device__ __forceinline__ void fwd_build(FwdChunk& W, int lane, bool real, const float4& a,
+                                          const float4& b, uint2 bx, int fj0, int fi0) {
+  const float lw = real ? b.y : -INFINITY;
+  float d[8];
+  const float x0 = (float)fj0 + 0.5f;  // column centres x0 + c are exact
+#pragma unroll
+  for (int c = 0; c < 8; ++c) d[c] = (x0 + (float)c) - a.x;
+  W.dx[0][lane] = make_float4(d[0], d[1], d[2], d[3]);
+  W.dx[1][lane] = make_float4(d[4], d[5], d[6], d[7]);
+  W.p0[lane] = make_float4(a.z, a.z, -a.y, -a.y);
+  W.p1[lane] = make_float4(a.w, a.w, b.x, b.x);
+  W.p2[lane] = make_float4(lw, lw, b.z, b.z);
+  if (PARTIAL) {
+    const uint32_t cl = clip_box(bx, fj0, fi0, 8);
+    const int cx0 = cl & 0xff, cx1 = (cl >> 8) & 0xff, ry0 = (cl >> 16) & 0xff, ry1 = cl >> 24;
+    float l[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) l[c] = ((c >= cx0) & (c <= cx1)) ? lw : -INFINITY;
+    W.lc[0][lane] = make_float4(l[0], l[1], l[2], l[3]);
+    W.lc[1][lane] = make_float4(l[4], l[5], l[6], l[7]);
+    W.rows[lane] = (2u << ry1) - (1u << ry0);
+  }
+  if (CUT) W.thr[lane] = b.w;
 }
 
 template <int TILE, int G, int CUT>
@@ -155,7 +214,7 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
                  float cbg, float* __restrict__ image, float* __restrict__ alpha,
                  uint8_t* __restrict__ inst_mask) {
   using Sh = FwdShape<TILE, G>;
-  constexpr int NW = Sh::NW, LG = Sh::LG, PPT = Sh::PPT, NP = Sh::NP;
+  constexpr int NW = Sh::NW, LG = Sh::LG, NP = Sh::NP;
   __shared__ FwdSmem<TILE, NW> S;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   pipe_init(S.T, S.bars, v, P, Sh::NCT);
@@ -166,14 +225,15 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
     return;
   }
   const int grp = lane / LG, gl = lane % LG;
-  const int lx = gl & 7, row0 = (gl >> 3) * PPT;  // column and first row of this lane
+  const int y = gl & 7, cp0 = (gl >> 3) * NP;  // this lane's row and first column pair
   const uint32_t lt = lanemask_lt();
   unsigned long long evaluated = 0;  // (record, footprint) items of this warp
-  int fj0 = 0, fi0 = 0, j = 0, tw = 0, th = 0;
+  int fj0 = 0, fi0 = 0, tw = 0, th = 0;
   int64_t tpx = 0;
-  float2 pxx = make_float2(0.f, 0.f), py[NP], sa[NP], sc[NP];
+  float py = 0.f;
+  float2 sa[NP], sc[NP];
 #pragma unroll
-  for (int p = 0; p < NP; ++p) py[p] = sa[p] = sc[p] = make_float2(0.f, 0.f);
+  for (int p = 0; p < NP; ++p) sa[p] = sc[p] = make_float2(0.f, 0.f);
   const FwdChunk& C = S.ch[warp];
   for (uint32_t k = 0;; ++k) {
     const int s = (int)(k % kStages);
@@ -186,24 +246,22 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
     if (h.tile < 0) break;
     if (h.flags & kFirst) {
       footprint_origin(warp, Tiling<TILE, 8>::FX, 8, h.tx, h.ty, TILE, fj0, fi0);
-      j = fj0 + lx;
       tw = h.w;
       th = h.h;
       tpx = h.px_off;
-      pxx = make_float2((float)j + 0.5f, (float)j + 0.5f);
+      py = (float)(fi0 + y) + 0.5f;
 #pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        const float y0 = (float)(fi0 + row0 + 2 * p) + 0.5f;
-        py[p] = make_float2(y0, y0 + 1.f);
-        sa[p] = sc[p] = make_float2(0.f, 0.f);
-      }
+      for (int p = 0; p < NP; ++p) sa[p] = sc[p] = make_float2(0.f, 0.f);
     }
     // this warp's lists: full-box items from the front, partial from the back
     int nf = 0, np = 0;
     for (int base = 0; base < h.cnt; base += 32) {
       const int r = base + lane;
-      const uint32_t m = r < h.cnt ? classify<CUT>(R.a[r], R.b[r], R.box[r], fj0, fi0, 8) : 0u;
-      if (r < h.cnt) inst_mask[(size_t)(h.inst0 + r) * 4 + warp] = (uint8_t)m;
+      const bool in = r < h.cnt;
+      const int rr = in ? r : h.cnt - 1;
+      uint32_t m = classify<CUT>(R.a[rr], R.b[rr], R.box[rr], fj0, fi0, 8);
+      m = in ? m : 0u;
+      if (in) inst_mask[(size_t)(h.inst0 + r) * 4 + warp] = (uint8_t)m;
       const bool live = m & 1u, full = m & 2u;
       const uint32_t bf = __ballot_sync(0xffffffffu, live && full);
       const uint32_t bp = __ballot_sync(0xffffffffu, live && !full);
@@ -214,31 +272,28 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
     }
     __syncwarp();
     evaluated += (unsigned long long)(nf + np);
-#pragma unroll 1
-    for (int part = 0; part < 2; ++part) {
-      const int n = part ? np : nf;
-      for (int base = 0; base < n; base += 32) {
-        if (base + lane < n) {  // lane-parallel chunk build
-          const int r = S.list[warp][part ? kBatch - 1 - (base + lane) : base + lane];
-          const float4 a = R.a[r], bb = R.b[r];
-          FwdChunk& W = S.ch[warp];
-          W.nxy[lane] = make_float4(-a.x, -a.x, -a.y, -a.y);
-          W.r1[lane] = make_float4(a.z, a.z, a.w, a.w);
-          W.r2[lane] = make_float4(bb.x, bb.x, bb.y, bb.y);
-          W.cv[lane] = make_float4(bb.z, bb.z, bb.w, 0.f);
-          if (part) W.clip[lane] = clip_box(R.box[r], fj0, fi0, 8);
-        }
-        __syncwarp();
-        const int ne = min(32, n - base);
-        if (part) {
-          for (int e = grp; e < ne; e += G)
-            fwd_item<CUT, true, NP>(C, e, pxx, py, lx, row0, sa, sc);
-        } else {
-          for (int e = grp; e < ne; e += G)
-            fwd_item<CUT, false, NP>(C, e, pxx, py, lx, row0, sa, sc);
-        }
-        __syncwarp();
+    FwdChunk& W = S.ch[warp];
+    for (int base = 0; base < nf; base += 32) {
+      const int ne = min(32, nf - base), nr = (ne + G - 1) / G * G;
+      if (lane < nr) {  // lane-parallel chunk build
+        const bool real = lane < ne;
+        const int r = real ? (int)S.list[warp][base + lane] : 0;
+        fwd_build<CUT, false>(W, lane, real, R.a[r], R.b[r], R.box[r], fj0, fi0);
       }
+      __syncwarp();
+      for (int e = grp; e < nr; e += G) fwd_item<CUT, false, NP>(C, e, py, y, cp0, sa, sc);
+      __syncwarp();
+    }
+    for (int base = 0; base < np; base += 32) {
+      const int ne = min(32, np - base), nr = (ne + G - 1) / G * G;
+      if (lane < nr) {
+        const bool real = lane < ne;
+        const int r = real ? (int)S.list[warp][kBatch - 1 - (base + lane)] : 0;
+        fwd_build<CUT, true>(W, lane, real, R.a[r], R.b[r], R.box[r], fj0, fi0);
+      }
+      __syncwarp();
+      for (int e = grp; e < nr; e += G) fwd_item<CUT, true, NP>(C, e, py, y, cp0, sa, sc);
+      __syncwarp();
     }
     mbar_arrive(&S.bars.empty[s]);  // the stage is no longer read by this thread
     if (h.flags & kLast) {
@@ -252,11 +307,12 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
           sc[p].x += __shfl_xor_sync(0xffffffffu, sc[p].x, o);
           sc[p].y += __shfl_xor_sync(0xffffffffu, sc[p].y, o);
         }
-      if (grp == 0 && j < tw) {
+      const int i = fi0 + y;
+      if (grp == 0 && i < th) {
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-          const int i = fi0 + row0 + q;
-          if (i < th) {
+        for (int q = 0; q < 2 * NP; ++q) {
+          const int j = fj0 + 2 * cp0 + q;
+          if (j < tw) {
             const int64_t px = tpx + (int64_t)i * tw + j;
             const float saq = (q & 1) ? sa[q >> 1].y : sa[q >> 1].x;
             const float scq = (q & 1) ? sc[q >> 1].y : sc[q >> 1].x;
