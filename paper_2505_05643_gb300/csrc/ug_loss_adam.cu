@@ -91,8 +91,28 @@ __global__ void __launch_bounds__(256)
     const float4* g4 = reinterpret_cast<const float4*>(g + off);
     float4* m4 = reinterpret_cast<float4*>(m + off);
     float4* v4 = reinterpret_cast<float4*>(v + off);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    // two elements of four per thread in flight per iteration
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + stride < n4; i += 2 * stride) {
+      float4 pp = p4[i], gg = g4[i], mm = m4[i], vv = v4[i];
+      float4 pq = p4[i + stride], gq = g4[i + stride], mq = m4[i + stride], vq = v4[i + stride];
+      adam_one(pp.x, gg.x, mm.x, vv.x, b1, b2, eps, a);
+      adam_one(pp.y, gg.y, mm.y, vv.y, b1, b2, eps, a);
+      adam_one(pp.z, gg.z, mm.z, vv.z, b1, b2, eps, a);
+      adam_one(pp.w, gg.w, mm.w, vv.w, b1, b2, eps, a);
+      adam_one(pq.x, gq.x, mq.x, vq.x, b1, b2, eps, a);
+      adam_one(pq.y, gq.y, mq.y, vq.y, b1, b2, eps, a);
+      adam_one(pq.z, gq.z, mq.z, vq.z, b1, b2, eps, a);
+      adam_one(pq.w, gq.w, mq.w, vq.w, b1, b2, eps, a);
+      p4[i] = pp;
+      m4[i] = mm;
+      v4[i] = vv;
+      p4[i + stride] = pq;
+      m4[i + stride] = mq;
+      v4[i + stride] = vq;
+    }
+    for (; i < n4; i += stride) {
       float4 pp = p4[i], gg = g4[i], mm = m4[i], vv = v4[i];
       adam_one(pp.x, gg.x, mm.x, vv.x, b1, b2, eps, a);
       adam_one(pp.y, gg.y, mm.y, vv.y, b1, b2, eps, a);
@@ -123,12 +143,17 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int32_t ro
                         float eps, cudaStream_t s) {
   const bool vec = (n % 4 == 0) && ((uintptr_t)p % 16 == 0) && ((uintptr_t)g % 16 == 0) &&
                    ((uintptr_t)m % 16 == 0) && ((uintptr_t)v % 16 == 0);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // one wave: the SMs' resident blocks shared evenly among the rows
+  static int resident[2] = {0, 0};
+  int& occ = resident[vec ? 1 : 0];
+  if (occ == 0) {
+    if (vec) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adam<true>, 256, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adam<false>, 256, 0);
+    if (occ < 1) occ = 1;
+  }
   const int64_t work = vec ? n / 4 : n;
   int64_t bx = (work + 255) / 256;
-  const int64_t cap = (int64_t)sms * 8 / (rows > 0 ? rows : 1) + 1;
+  const int64_t cap = (int64_t)device_sms() * occ / (rows > 0 ? rows : 1);
   if (bx > cap) bx = cap;
   if (bx < 1) bx = 1;
   dim3 grid((unsigned)bx, (unsigned)rows);

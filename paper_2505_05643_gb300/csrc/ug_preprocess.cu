@@ -288,15 +288,27 @@ __global__ void __launch_bounds__(256) k_list(int P, int64_t chunks, WsView v) {
   const uint32_t n32 = v.hdr->slots - v.hdr->slots64;
   const uint32_t lt = lanemask_lt();
   const uint32_t g = (uint32_t)(chunk * kChunk + lane);
-  for (int p = 0; p < P; ++p) {
-    const int64_t e = chunk * P + p;
-    const uint32_t mask = v.mask[e];
-    if (!((mask >> lane) & 1u)) continue;
-    const uint32_t slot = v.slot_base[e] + __popc(mask & lt);
-    uint32_t idx;
-    if ((fl >> lane) & 1u) idx = n32 + v.f64_base[e] + __popc(mask & fl & lt);
-    else idx = (v.slot_base[e] - v.f64_base[e]) + __popc(mask & ~fl & lt);
-    v.list[idx] = make_uint4(g, (uint32_t)p, slot, 0u);
+  // the chunk's candidate masks and bases, 32 planes at a time, one per lane
+  // (coalesced), then handed round the warp
+  for (int p0 = 0; p0 < P; p0 += 32) {
+    const int pl = p0 + lane;
+    const int64_t e = chunk * P + pl;
+    const uint32_t mq = pl < P ? __ldg(v.mask + e) : 0u;
+    const uint32_t bq = pl < P ? __ldg(v.slot_base + e) : 0u;
+    const uint32_t fq = pl < P ? __ldg(v.f64_base + e) : 0u;
+    const int np = min(32, P - p0);
+    for (int q = 0; q < np; ++q) {
+      const uint32_t mask = __shfl_sync(0xffffffffu, mq, q);
+      if (mask == 0u) continue;  // the same for the whole warp
+      const uint32_t base = __shfl_sync(0xffffffffu, bq, q);
+      const uint32_t b64 = __shfl_sync(0xffffffffu, fq, q);
+      if (!((mask >> lane) & 1u)) continue;
+      const uint32_t slot = base + __popc(mask & lt);
+      uint32_t idx;
+      if ((fl >> lane) & 1u) idx = n32 + b64 + __popc(mask & fl & lt);
+      else idx = (base - b64) + __popc(mask & ~fl & lt);
+      v.list[idx] = make_uint4(g, (uint32_t)(p0 + q), slot, 0u);
+    }
   }
 }
 
@@ -901,47 +913,51 @@ __global__ void __launch_bounds__(256)
 }
 
 // Sum of the per-record parameter gradients of every Gaussian, in plane
-// order (deterministic), written to the gradient rows.
+// order (deterministic), written to the gradient rows. A chunk's records of a
+// group of 32 planes occupy consecutive slots (the scan runs in (chunk, plane)
+// order), so the warp reads them with full-width coalesced loads into a
+// shared-memory window, kGatherWin records at a time, and every lane then adds
+// its own Gaussian's records from the window, planes in ascending order.
+constexpr int kGatherWin = 96;
+
 template <int COV>
 __global__ void __launch_bounds__(256)
     k_gather(int64_t n, int P, int64_t chunks, WsView v, ug_gaussian_grads out) {
+  __shared__ float4 win[256 / 32][kGatherWin * 3];
   if (dev_failed(v.hdr)) return;
   const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (chunk >= chunks) return;
   const int lane = threadIdx.x & 31;
+  float4* W = win[threadIdx.x >> 5];
   const int64_t i = chunk * kChunk + lane;
   const uint32_t lt = lanemask_lt();
   float acc[12];
 #pragma unroll
   for (int q = 0; q < 12; ++q) acc[q] = 0.f;
-  // planes in groups of kG: all loads of a group are issued before the sums
-  // (in plane order) consume them
-  constexpr int kG = 4;
-  for (int p0 = 0; p0 < P; p0 += kG) {
-    uint32_t mask[kG], base[kG];
-#pragma unroll
-    for (int q = 0; q < kG; ++q) {
-      const int64_t e = chunk * P + p0 + q;
-      mask[q] = p0 + q < P ? __ldg(v.mask + e) : 0u;
-      base[q] = p0 + q < P ? __ldg(v.slot_base + e) : 0u;
-    }
-    float4 x[kG][3];
-#pragma unroll
-    for (int q = 0; q < kG; ++q) {
-      const bool on = (mask[q] >> lane) & 1u;
-      const uint32_t slot = on ? base[q] + __popc(mask[q] & lt) : 0u;
-      const float4* src = reinterpret_cast<const float4*>(v.rec_pgrad + (size_t)slot * 12);
-      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-      x[q][0] = on ? __ldg(src) : z;
-      x[q][1] = on ? __ldg(src + 1) : z;
-      x[q][2] = on ? __ldg(src + 2) : z;
-    }
-#pragma unroll
-    for (int q = 0; q < kG; ++q) {
-      if (!((mask[q] >> lane) & 1u)) continue;
-      acc[0] += x[q][0].x; acc[1] += x[q][0].y; acc[2] += x[q][0].z; acc[3] += x[q][0].w;
-      acc[4] += x[q][1].x; acc[5] += x[q][1].y; acc[6] += x[q][1].z; acc[7] += x[q][1].w;
-      acc[8] += x[q][2].x; acc[9] += x[q][2].y; acc[10] += x[q][2].z; acc[11] += x[q][2].w;
+  const float4* pg = reinterpret_cast<const float4*>(v.rec_pgrad);
+  for (int p0 = 0; p0 < P; p0 += 32) {
+    const int pl = p0 + lane, np = min(32, P - p0);
+    const uint32_t mq = pl < P ? __ldg(v.mask + chunk * P + pl) : 0u;
+    const uint32_t bq = pl < P ? __ldg(v.slot_base + chunk * P + pl) : 0u;
+    // this plane group's slots: [first, last)
+    const uint32_t first = __shfl_sync(0xffffffffu, bq, 0);
+    const uint32_t last = __shfl_sync(0xffffffffu, bq + __popc(mq), np - 1);
+    for (uint32_t w0 = first; w0 < last; w0 += kGatherWin) {
+      const int cnt = (int)min((uint32_t)kGatherWin, last - w0);
+      __syncwarp();  // the previous window is consumed
+      for (int k = lane; k < cnt * 3; k += 32) W[k] = __ldg(pg + (size_t)w0 * 3 + k);
+      __syncwarp();
+      for (int q = 0; q < np; ++q) {
+        const uint32_t mask = __shfl_sync(0xffffffffu, mq, q);
+        const uint32_t base = __shfl_sync(0xffffffffu, bq, q);
+        if (!((mask >> lane) & 1u)) continue;
+        const uint32_t r = base + __popc(mask & lt) - w0;  // wraps when below the window
+        if (r >= (uint32_t)cnt) continue;
+        const float4 x0 = W[3 * r], x1 = W[3 * r + 1], x2 = W[3 * r + 2];
+        acc[0] += x0.x; acc[1] += x0.y; acc[2] += x0.z; acc[3] += x0.w;
+        acc[4] += x1.x; acc[5] += x1.y; acc[6] += x1.z; acc[7] += x1.w;
+        acc[8] += x2.x; acc[9] += x2.y; acc[10] += x2.z; acc[11] += x2.w;
+      }
     }
   }
   if (i >= n) return;
