@@ -44,7 +44,7 @@ BWD_OPS = 9
 # DRAM bytes (read + write) of one k_render_bwd launch on this workload, from a
 # one-pass ncu capture of the kernel as it stands; None when the kernel has
 # changed since.
-BWD_TRAFFIC = 449278464
+BWD_TRAFFIC = None
 
 METRIC = "Gaussian·pixel evals/s and fwd+bwd train steps/s, 1M Gaussians, 1×GB300"
 WORKLOAD = "aniso_1m: 1,000,000 Gaussians, axis ratios log-uniform to 1e4, 64 planes/launch " \
