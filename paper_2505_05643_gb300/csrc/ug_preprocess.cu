@@ -149,7 +149,8 @@ struct CullGauss {
   float hb;  // sqrt(chi2) ||Fi||_F: bound of every half-extent
 };
 
-__device__ __forceinline__ bool cull_pair(const CullGauss& c, const PlaneDev& pl, float chi2) {
+template <typename PL>
+__device__ __forceinline__ bool cull_pair(const CullGauss& c, const PL& pl, float chi2) {
   const float eps = 5.9604645e-8f;
   float d[3];
 #pragma unroll
@@ -172,7 +173,7 @@ __device__ __forceinline__ bool cull_pair(const CullGauss& c, const PlaneDev& pl
   const float cj = fmaf(m1, pl.inv_pu, pl.jshift), hj = fmaf(h, pl.inv_pu, 1.f);
   const float ci = fmaf(m2, pl.inv_pv, pl.ishift), hi = fmaf(h, pl.inv_pv, 1.f);
   const bool img = cj + hj >= 0.f && cj - hj <= (float)(pl.w - 1) && ci + hi >= 0.f &&
-                   ci - hi <= (float)(pl.h - 1);
+                   ci - hi <= (float)(pl.h - 1);  // (w - 1, h - 1 exact in FP32)
   return ph1 && img;
 }
 
@@ -195,20 +196,44 @@ __device__ __forceinline__ void lane_setup(const ug_gaussians& g, int64_t n, int
 
 constexpr int kCullPlanesSmem = 64;  // planes staged in shared memory per pass
 
+// The plane fields the cull reads, 19 words (odd: lanes reading different
+// planes hit different banks).
+struct CullPlane {
+  float o[3], u[3], v[3], n[3];
+  float inv_pu, inv_pv, jshift, ishift;
+  int32_t w, h, pad;
+};
+
+// A warp's Gaussians for the second test, structure of arrays.
+struct CullWarp {
+  float mu[3][32];
+  float Fi[9][32];
+  float R2[32], hb[32];
+  uint16_t queue[64];              // (plane << 5) | lane, a ring
+  uint32_t bits[kCullPlanesSmem];  // candidate bits of the current plane group
+};
+
+// Two tests per (Gaussian, plane). The first is the plane distance against the
+// Gaussian's largest extent, |m3| - Bm <= sqrt(chi2 smax) with smax >= S + B:
+// S = |Fi n|^2 <= ||Fi||_F^2 |n|^2 and |n|^2 <= 1.0004 for a valid plane, so it
+// passes every pair that cull_pair passes. Pairs that pass it go into the warp's
+// queue and take the full test 32 at a time, every lane busy.
 template <int COV>
 __global__ void __launch_bounds__(256)
     k_cull(ug_gaussians g, int64_t n, int P, float chi2, float beta, float ratio, int64_t chunks,
            WsView v) {
-  __shared__ PlaneDev s_pl[kCullPlanesSmem];
+  __shared__ CullPlane s_pl[kCullPlanesSmem];
+  __shared__ CullWarp s_w[256 / 32];
   if (dev_failed(v.hdr)) return;
   const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  CullWarp& W = s_w[threadIdx.x >> 5];
   const bool live_warp = chunk < chunks;
   LaneGauss L;
   L.active = false;
   L.use64 = false;
   if (live_warp) lane_setup<COV>(g, n, chunk * kChunk + lane, beta, ratio, L);
-  CullGauss cg;
+  float thr1;  // first test: lo^2 <= thr1
   {
     float Fi[3][3];
     if (L.use64) {
@@ -227,34 +252,90 @@ __global__ void __launch_bounds__(256)
     float R2 = 0.f, fro = 0.f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      cg.mu[i] = L.active ? L.prm.mu[i] : 0.f;
+      W.mu[i][lane] = L.active ? L.prm.mu[i] : 0.f;
       float rs = 0.f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        cg.Fi[i][k] = Fi[i][k];
+        W.Fi[3 * i + k][lane] = Fi[i][k];
         rs += fabsf(Fi[i][k]);
         fro = fmaf(Fi[i][k], Fi[i][k], fro);
       }
       R2 = fmaf(rs, rs, R2);
     }
-    cg.R2 = R2 * 1.001f;
-    cg.hb = sqrtf(chi2 * fro) * 1.001f;
+    R2 *= 1.001f;
+    W.R2[lane] = R2;
+    W.hb[lane] = sqrtf(chi2 * fro) * 1.001f;
+    const float eps = 5.9604645e-8f;
+    const float smax = fro * 1.001f;
+    const float bmax = 5.f * eps * (smax + R2) + 25.f * eps * eps * R2 + 3.f * eps * smax;
+    thr1 = L.active ? chi2 * (smax + bmax) * 1.0021f : -1.f;
   }
   if (live_warp) {
     const uint32_t fl = __ballot_sync(0xffffffffu, L.use64);
     if (lane == 0) v.gflag[chunk] = fl;
   }
+  const float mx = W.mu[0][lane], my = W.mu[1][lane], mz = W.mu[2][lane];
+  const uint32_t lt = lanemask_lt();
   for (int p0 = 0; p0 < P; p0 += kCullPlanesSmem) {
     const int np = min(kCullPlanesSmem, P - p0);
     __syncthreads();
-    for (int q = threadIdx.x; q < np; q += blockDim.x) s_pl[q] = v.planes[p0 + q];
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+      const PlaneDev& d = v.planes[p0 + q];
+      CullPlane c;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        c.o[k] = d.o[k];
+        c.u[k] = d.u[k];
+        c.v[k] = d.v[k];
+        c.n[k] = d.n[k];
+      }
+      c.inv_pu = d.inv_pu;
+      c.inv_pv = d.inv_pv;
+      c.jshift = d.jshift;
+      c.ishift = d.ishift;
+      c.w = d.w;
+      c.h = d.h;
+      c.pad = 0;
+      s_pl[q] = c;
+    }
     __syncthreads();
     if (!live_warp) continue;
+    for (int q = lane; q < kCullPlanesSmem; q += 32) W.bits[q] = 0u;
+    uint32_t head = 0, count = 0;
     for (int q = 0; q < np; ++q) {
-      const bool cand = L.active && cull_pair(cg, s_pl[q], chi2);
-      const uint32_t mask = __ballot_sync(0xffffffffu, cand);
-      if (lane == 0) v.mask[chunk * P + p0 + q] = mask;
+      const CullPlane& pl = s_pl[q];
+      const float d0 = mx - pl.o[0], d1 = my - pl.o[1], d2 = mz - pl.o[2];
+      const float eps = 5.9604645e-8f;
+      const float Bm = 8.f * eps * (fabsf(d0) + fabsf(d1) + fabsf(d2)) * 1.001f + 1e-30f;
+      const float m3 = fmaf(pl.n[2], d2, fmaf(pl.n[1], d1, pl.n[0] * d0));
+      const float lo = fmaxf(fabsf(m3) - Bm, 0.f);
+      const uint32_t bal = __ballot_sync(0xffffffffu, lo * lo <= thr1);
+      if ((bal >> lane) & 1u)
+        W.queue[(head + count + __popc(bal & lt)) % 64u] = (uint16_t)((q << 5) | lane);
+      count += __popc(bal);
+      __syncwarp();
+      const bool flush = q == np - 1;
+      while (count >= 32u || (flush && count > 0u)) {
+        const uint32_t m = min(count, 32u);
+        if ((uint32_t)lane < m) {
+          const uint32_t e = W.queue[(head + lane) % 64u];
+          const int eq = (int)(e >> 5), el = (int)(e & 31u);
+          CullGauss c;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) c.mu[k] = W.mu[k][el];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) c.Fi[k / 3][k % 3] = W.Fi[k][el];
+          c.R2 = W.R2[el];
+          c.hb = W.hb[el];
+          if (cull_pair(c, s_pl[eq], chi2)) atomicOr(&W.bits[eq], 1u << el);
+        }
+        head = (head + m) % 64u;
+        count -= m;
+        __syncwarp();
+      }
     }
+    for (int q = lane; q < np; q += 32) v.mask[chunk * P + p0 + q] = W.bits[q];
+    __syncwarp();
   }
 }
 
