@@ -44,7 +44,8 @@ BWD_OPS = 9
 # DRAM bytes (read + write) of one k_render_bwd launch on this workload, from a
 # one-pass ncu capture of the kernel as it stands; None when the kernel has
 # changed since.
-BWD_TRAFFIC = None
+BWD_TRAFFIC = 482918400  # 409,056,768 read + 73,861,632 written
+FWD_TRAFFIC = 244213504  # 183,179,776 read + 61,033,728 written (k_render_fwd, same capture)
 
 METRIC = "Gaussian·pixel evals/s and fwd+bwd train steps/s, 1M Gaussians, 1×GB300"
 WORKLOAD = "aniso_1m: 1,000,000 Gaussians, axis ratios log-uniform to 1e4, 64 planes/launch " \
@@ -462,7 +463,7 @@ def run_ours(args):
             "fwd": {"kernel": "k_render_fwd (ug_render)", "ms": fwd_s * 1e3,
                     "ops_per_unit": FWD_OPS, "units_per_launch": evaluated,
                     "achieved": FWD_OPS * evaluated / fwd_s / 1e12,
-                    "frac": FWD_OPS * evaluated / fwd_s / fp32_peak},
+                    "frac": FWD_OPS * evaluated / fwd_s / fp32_peak, "traffic": FWD_TRAFFIC},
             "bwd_ms": bwd_s * 1e3, "box_pairs_per_launch": pairs_eager,
             "evaluated_over_box_pairs": evaluated / pairs_eager,
             "evaluated_bwd_over_box_pairs": evaluated_bwd / pairs_eager,

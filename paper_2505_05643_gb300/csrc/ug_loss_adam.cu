@@ -10,14 +10,34 @@ __global__ void __launch_bounds__(256)
           float* __restrict__ grad, float* __restrict__ loss) {
   __shared__ double red[8];
   const float scale = 2.0f / (float)n;
-  double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float d = image[i] - target[i];
-    if (grad) grad[i] = scale * d;
-    acc += (double)d * (double)d;
+  // a thread's few squares are summed in FP32 (FP64 arithmetic runs at a small
+  // fraction of the FP32 rate), the threads' sums in FP64
+  float accf = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool vec = (n % 4 == 0) && ((uintptr_t)image % 16 == 0) && ((uintptr_t)target % 16 == 0) &&
+                   ((uintptr_t)grad % 16 == 0);
+  if (vec) {
+    const float4* im4 = reinterpret_cast<const float4*>(image);
+    const float4* tg4 = reinterpret_cast<const float4*>(target);
+    float4* gr4 = reinterpret_cast<float4*>(grad);
+    for (int64_t i = t0; i < n / 4; i += stride) {
+      const float4 a = im4[i], b = tg4[i];
+      const float4 d = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+      if (grad) gr4[i] = make_float4(scale * d.x, scale * d.y, scale * d.z, scale * d.w);
+      accf = fmaf(d.x, d.x, accf);
+      accf = fmaf(d.y, d.y, accf);
+      accf = fmaf(d.z, d.z, accf);
+      accf = fmaf(d.w, d.w, accf);
+    }
+  } else {
+    for (int64_t i = t0; i < n; i += stride) {
+      const float d = image[i] - target[i];
+      if (grad) grad[i] = scale * d;
+      accf = fmaf(d, d, accf);
+    }
   }
-  acc = warp_sum(acc);
+  double acc = warp_sum((double)accf);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {

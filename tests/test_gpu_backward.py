@@ -242,7 +242,7 @@ def test_autograd_function_matches_direct_call():
 
 def test_mse_loss_kernel():
     rng = np.random.default_rng(34)
-    for n in (1, 1000, 3 * 65536 + 7):
+    for n in (1, 1000, 3 * 65536 + 7, 4 * 65536, 6688768):  # scalar and float4 paths
         img = rng.uniform(0, 1, n).astype(np.float32)
         tgt = rng.uniform(0, 1, n).astype(np.float32)
         it, tt = torch.from_numpy(img).cuda(), torch.from_numpy(tgt).cuda()
