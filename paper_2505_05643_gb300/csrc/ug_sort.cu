@@ -20,9 +20,17 @@ __global__ void __launch_bounds__(kSortThreads)
   hist[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  for (int k = 0; k < kSortItems; ++k) {
-    const int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&hist[(__ldg(keys + i) >> shift) & 0xffu], 1u);
+  if (base < n) {
+    // all loads first (in flight together), then the counts
+    uint32_t d[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+      const int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
+      d[k] = i < n ? (__ldg(keys + i) >> shift) & 0xffu : 256u;
+    }
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k)
+      if (d[k] < 256u) atomicAdd(&hist[d[k]], 1u);
   }
   __syncthreads();
   v.sort_hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = hist[threadIdx.x];
@@ -34,7 +42,7 @@ __global__ void __launch_bounds__(kSortThreads)
 // order, equal digits found with __match_any_sync). The block then places its
 // keys in shared memory in digit order and writes them out so that consecutive
 // threads write consecutive addresses of each digit's output run.
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 3)
     k_sort_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int shift,
                    int64_t nblk, WsView v) {
