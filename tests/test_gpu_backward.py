@@ -163,6 +163,26 @@ def test_grad_with_and_without_forward_footprint_tests(tile):
     assert np.all(err <= 1e-5 * scale + 1e-4 * np.abs(without)), (err / scale).max(axis=1)
 
 
+def test_grad_many_planes_and_dense_tiles():
+    """Gradient parity with 80 planes in one launch (planes beyond the
+    rasterizers' 64-plane shared table; plane groups of the cull, list and
+    gather) and, on a dense plane, tiles spanning several record stages."""
+    rng = np.random.default_rng(43)
+    g = synth.gaussians_scale_rot(rng, 2500, 0.03, 0.15)
+    sizes = [(24 + (k % 5) * 7, 20 + (k % 3) * 9) for k in range(79)] + [(40, 40)]
+    pl = synth.planes_random(rng, sizes)
+    target = rng.uniform(0, 1, pl["total_pixels"])
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    gpu, gref, gabs, _ = _backward_case(g, pl, cfg, target)
+    _check_grads(gpu, gref, gabs, oracle.param_names(1), "80 planes")
+    rng = np.random.default_rng(44)
+    g = synth.gaussians_scale_rot(rng, 4000, 0.05, 0.3)
+    pl = synth.planes_random(rng, [(40, 40), (33, 21)], origin_range=0.05)
+    target = rng.uniform(0, 1, pl["total_pixels"])
+    gpu, gref, gabs, _ = _backward_case(g, pl, cfg, target)
+    _check_grads(gpu, gref, gabs, oracle.param_names(1), "dense tiles")
+
+
 def test_grad_50k_16_planes_subset_and_fd():
     """50,000 scale/rotation Gaussians, 16 planes of 256x256, MSE against
     targets rendered by the oracle from a separate seed-1 set of 50,000;

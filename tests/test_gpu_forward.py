@@ -68,6 +68,37 @@ def test_extreme_anisotropy_small():
     assert abs(st["box_pixels"] - ref["pairs"]) <= 1e-3 * ref["pairs"]
 
 
+def test_more_planes_than_shared_memory_table():
+    """80 planes in one launch (the rasterizers keep 64 planes' tile data in
+    shared memory and look the rest up in global memory; the cull stages planes
+    64 at a time; the list and gather kernels walk planes 32 at a time)."""
+    rng = np.random.default_rng(41)
+    g = synth.gaussians_scale_rot(rng, 3000, 0.03, 0.15)
+    sizes = [(24 + (k % 5) * 7, 20 + (k % 3) * 9) for k in range(80)]
+    pl = synth.planes_random(rng, sizes)
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    r, _, image, alpha = gpu_render(g, pl, cfg)
+    ref = oracle.render(g, pl, oracle_config(cfg))
+    assert ref["pairs"] > 20000
+    assert_forward_parity(image, alpha, ref, "80 planes")
+    assert r.status()["status"] == 0
+
+
+def test_dense_tiles_span_many_stages():
+    """5,000 Gaussians on one 40x40 plane: most tiles hold several hundred
+    records, so a tile spans several 128-record stages of the rasterizers'
+    record pipeline and the backward's item queue wraps many times."""
+    rng = np.random.default_rng(42)
+    g = synth.gaussians_scale_rot(rng, 5000, 0.05, 0.3)
+    pl = synth.planes_random(rng, [(40, 40)], origin_range=0.05)
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    r, _, image, alpha = gpu_render(g, pl, cfg)
+    ref = oracle.render(g, pl, oracle_config(cfg))
+    st = r.status()
+    assert st["instances"] / 9 > 400  # 9 tiles of 16x16
+    assert_forward_parity(image, alpha, ref, "dense tiles")
+
+
 @pytest.mark.parametrize("tile,variant", [(16, v) for v in range(3)] + [(8, v) for v in range(3)])
 def test_ragged_planes_all_variants(tile, variant):
     """Planes whose sizes are not multiples of the tile (ragged tails), several
