@@ -409,6 +409,8 @@ def run_ours(args):
     h_targets = torch.from_numpy(target).pin_memory()
     h_planes = torch.from_numpy(r.host_planes.view(np.uint8).copy()).pin_memory()
     h_loss = torch.zeros(1, dtype=torch.float32).pin_memory()
+    copy_s = torch.cuda.Stream()
+    targets_in = torch.cuda.Event()
     for attempt in range(3):
         restore()
         with torch.cuda.stream(s):
@@ -420,10 +422,14 @@ def run_ours(args):
         t0 = time.perf_counter()
         with torch.cuda.stream(s):
             for k in range(args.steps):
-                step.targets.copy_(h_targets, non_blocking=True)
+                # the targets travel on their own stream while the step renders;
+                # the loss waits for them
+                with torch.cuda.stream(copy_s):
+                    step.targets.copy_(h_targets, non_blocking=True)
+                    targets_in.record(copy_s)
                 r.d_planes.copy_(h_planes, non_blocking=True)
                 reset_on(s)
-                step.enqueue(s)
+                step.enqueue(s, targets_ready=targets_in)
                 h_loss.copy_(step.loss[:1], non_blocking=True)
                 B.ug_read_status(r.plan, r.ws, st_dev, s)
                 s.synchronize()

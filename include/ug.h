@@ -320,6 +320,16 @@ ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_
                          uint32_t** record_boxes, float** record_a, float** record_b,
                          uint32_t** record_planes);
 
+/* Test hook for the rasterizers' bounded waits (rows a5, a7). With on != 0
+ * the producer warps of ug_render and ug_render_backward_raster issue no
+ * stage, so every consumer wait runs out after its time limit (about one
+ * second): the launch then ends with UG_ERR_TIMEOUT in the workspace status,
+ * and the context stays usable. on = 0 restores normal operation, and so does
+ * ug_preprocess, which clears the flag: set it after the preprocess of the
+ * launch to be tested. Written on `stream`. */
+ug_status ug_debug_stall_pipeline(const ug_plan* plan, void* ws, size_t ws_bytes, int32_t on,
+                                  ug_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

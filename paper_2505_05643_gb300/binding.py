@@ -35,6 +35,7 @@ EXPORTS = (
     "ug_version", "ug_status_string", "ug_num_variants", "ug_config_default", "ug_plan_init",
     "ug_preprocess", "ug_bin_sort", "ug_render", "ug_mse_loss_grad", "ug_render_backward",
     "ug_adam_step", "ug_read_status", "ug_debug_views", "ug_mse_loss_grad_static",
+    "ug_debug_stall_pipeline",
     "ug_render_backward_raster", "ug_preprocess_backward", "ug_render_scatter",
     "ug_ssim_scratch_floats", "ug_ssim",
 )
@@ -135,6 +136,7 @@ def load(build_if_missing: bool = True):
                                            P(ug_gaussian_grads), vp]
     lib.ug_adam_step.argtypes = [vp, vp, vp, vp, i32, i64, vp, vp, f32, f32, f32, vp]
     lib.ug_read_status.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp, vp]
+    lib.ug_debug_stall_pipeline.argtypes = [P(ug_plan), vp, ctypes.c_size_t, i32, vp]
     lib.ug_debug_views.argtypes = [P(ug_plan), vp, ctypes.c_size_t, P(vp), P(vp), P(vp), P(vp),
                                    P(vp), P(vp), P(vp)]
     for name in EXPORTS:
@@ -282,6 +284,13 @@ def ug_read_status(plan: ug_plan, ws, out, stream=None):
     """Copy the workspace status into `out` (a 64-byte pinned host or device tensor)."""
     _check(load().ug_read_status(ctypes.byref(plan), _ptr(ws), ws.numel(), out.data_ptr(),
                                  _stream(stream)), "ug_read_status")
+
+
+def ug_debug_stall_pipeline(plan: ug_plan, ws, on: bool, stream=None):
+    """Test hook: with on, the rasterizers' producers issue nothing, so their
+    consumers' bounded waits run out (UG_ERR_TIMEOUT in the status)."""
+    _check(load().ug_debug_stall_pipeline(ctypes.byref(plan), _ptr(ws), ws.numel(), int(bool(on)),
+                                          _stream(stream)), "ug_debug_stall_pipeline")
 
 
 def ug_debug_views(plan: ug_plan, ws):

@@ -350,4 +350,14 @@ ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_
   return UG_OK;
 }
 
+ug_status ug_debug_stall_pipeline(const ug_plan* plan, void* ws, size_t ws_bytes, int32_t on,
+                                  ug_stream stream) {
+  ug_status s = check_plan(plan);
+  if (s == UG_OK) s = check_ws(plan, ws, ws_bytes);
+  if (s != UG_OK) return s;
+  WsView v = make_view(plan, ws);
+  return cuda_status(cudaMemsetAsync(&v.hdr->stall_test, on ? 0xff : 0, sizeof(uint32_t),
+                                     reinterpret_cast<cudaStream_t>(stream)));
+}
+
 }  // extern "C"

@@ -60,7 +60,9 @@ struct WsHeader {
   // footprint tests since the last bin/sort (cleared by bin/sort and by the
   // scatter forward)
   uint32_t fwd_masks;
-  uint32_t pad1[39];
+  uint32_t stall_test;        // non-zero: the rasterizers' producers issue nothing (test hook;
+                              // cleared by the preprocess)
+  uint32_t pad1[38];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 

@@ -20,7 +20,7 @@ constexpr int kStages = 3;    // stages in the ring
 constexpr int kFirst = 1;     // stage flag: first batch of its tile
 constexpr int kLast = 2;      // stage flag: last batch of its tile
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
-constexpr uint32_t kWaitLimitIters = 1u << 30;
+constexpr uint32_t kWaitLimitIters = 1u << 20;
 // A waiting thread sleeps until the phase completes or this long (ns), so
 // waiting warps take no issue slots from the working ones.
 constexpr uint32_t kSuspendHintNs = 20000;
@@ -214,6 +214,8 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
                                         const uint32_t* __restrict__ inst_mask) {
   const int lane = threadIdx.x & 31;
   constexpr int PER = kBatch / 32;
+  // test hook: issue nothing, so that the consumers' bounded waits run out
+  if (*(volatile const uint32_t*)&v.hdr->stall_test != 0) return;
   const uint32_t total = (uint32_t)total_tiles;
   uint32_t* counter = &v.hdr->tile_counter[which];
   // Tile look-ahead: A is the tile being issued, B the next one (its range

@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(256)
     h->box_pixels = 0;
     h->holes = 0;
     h->fwd_masks = 0;
+    h->stall_test = 0;
     h->kept64 = 0;
     s_run = 0;
   }

@@ -50,12 +50,17 @@ class TrainStep:
         self.grad_struct = R.grads_struct(self.grads, renderer.cov)
         self.graph = None
 
-    def enqueue(self, stream=None):
-        """Issue the six calls of one step on `stream` (no host synchronisation)."""
+    def enqueue(self, stream=None, targets_ready=None):
+        """Issue the six calls of one step on `stream` (no host synchronisation).
+        targets_ready: an event recorded after the step's targets were written
+        (e.g. by a host-to-device copy on another stream); the loss waits for it,
+        the preprocess, sort and forward do not."""
         r = self.r
         B.ug_preprocess(r.plan, self.g_struct, r.d_planes, r.ws, stream)
         B.ug_bin_sort(r.plan, r.ws, stream)
         B.ug_render(r.plan, r.ws, self.image, self.alpha, stream)
+        if targets_ready is not None:
+            (stream or torch.cuda.current_stream()).wait_event(targets_ready)
         B.ug_mse_loss_grad(self.image, self.targets, self.image.numel(), self.grad_image,
                            self.loss, stream)
         B.ug_render_backward(r.plan, self.g_struct, r.d_planes, r.ws, self.image, self.alpha,

@@ -201,6 +201,37 @@ def test_invalid_plane_in_device_memory_sets_status():
     assert e.value.status == B.UG_ERR_INVALID_PLANE
 
 
+def test_bounded_waits_run_out_and_report():
+    """The rasterizers' waits are bounded: with the test hook set, no stage is
+    ever issued, every consumer wait runs out (about a second), the launch ends
+    with UG_ERR_TIMEOUT in the status (detail 1: forward, 2: backward), and the
+    context stays usable: clearing the hook gives the same image as before."""
+    import time
+    g, pl = synth.workload_fwd_2k()
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    r, params, image0, _ = gpu_render(g, pl, cfg)
+    im = torch.empty(pl["total_pixels"], device="cuda")
+    al = torch.empty_like(im)
+    B.ug_debug_stall_pipeline(r.plan, r.ws, True)
+    t0 = time.time()
+    B.ug_render(r.plan, r.ws, im, al)
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 30.0
+    st = r.status()
+    assert st["status"] == B.UG_ERR_TIMEOUT and st["detail"] == 1, st
+    # the backward's consumers (status cleared by hand: it keeps the first failure)
+    r.ws[:4].zero_()
+    B.ug_render_backward_raster(r.plan, r.ws, im, al, torch.zeros_like(im))
+    torch.cuda.synchronize()
+    st = r.status()
+    assert st["status"] == B.UG_ERR_TIMEOUT and st["detail"] == 2, st
+    B.ug_debug_stall_pipeline(r.plan, r.ws, False)
+    image1, _ = r.forward(params)
+    torch.cuda.synchronize()
+    assert r.status()["status"] == B.UG_OK
+    assert np.array_equal(image1.cpu().numpy().astype(np.float64), image0)
+
+
 def test_capacity_overflow_is_reported_and_recovered():
     g, pl = synth.workload_fwd_2k()
     cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
