@@ -387,23 +387,26 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, uint
     if (2 * cp < cx0 || 2 * cp > cx1) lwc[cp].x = -INFINITY;
     if (2 * cp + 1 < cx0 || 2 * cp + 1 > cx1) lwc[cp].y = -INFINITY;
   }
+  // packed sums over the footprint; the row-level ones keep the two pixel
+  // columns of a pair apart and are added at the end
   float2 s0 = make_float2(0.f, 0.f), a4 = make_float2(0.f, 0.f);
-  float s1 = 0.f, u1 = 0.f, u2 = 0.f, a5 = 0.f, a6 = 0.f;
+  float2 s1p = make_float2(0.f, 0.f), u1p = make_float2(0.f, 0.f), u2p = make_float2(0.f, 0.f);
+  float2 a5p = make_float2(0.f, 0.f), a6p = make_float2(0.f, 0.f);
+  const float fy0 = (float)fi0 + 0.5f;  // row centres fy0 + y are exact
 #pragma unroll
   for (int y = 0; y < FH; ++y) {
-    const float dyv = ((float)(fi0 + y) + 0.5f) - a.y;
+    const float dyv = (fy0 + (float)y) - a.y;
     const float2 dy = make_float2(dyv, dyv);
     const float2 r12dy = __fmul2_rn(r12, dy);
     const float2 t2 = __fmul2_rn(r22, dy);
-    const float2 nt2sq = __fmul2_rn(neg2(t2), t2);
-    const bool row_in = y >= ry0 && y <= ry1;
+    float2 nt2sq = __fmul2_rn(neg2(t2), t2);
+    if (y < ry0 || y > ry1) nt2sq = make_float2(-INFINITY, -INFINITY);  // row outside the box
     float2 s1r = make_float2(0.f, 0.f), u1r = make_float2(0.f, 0.f);
 #pragma unroll
     for (int cp = 0; cp < 4; ++cp) {
       const float2 t1 = __ffma2_rn(r11, dx[cp], r12dy);
       // lw2 - t2^2 - t1^2
       float2 e2 = __ffma2_rn(neg2(t1), t1, __fadd2_rn(lwc[cp], nt2sq));
-      if (!row_in) e2 = make_float2(-INFINITY, -INFINITY);
       if (CUT) {
         const float2 q = __ffma2_rn(t1, t1, __fmul2_rn(t2, t2));
         if (!(q.x <= bb.w)) e2.x = -INFINITY;
@@ -419,13 +422,14 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, uint
       u1r = __fadd2_rn(u1r, gu);
       a4 = __ffma2_rn(gu, dx[cp], a4);
     }
-    const float sr = s1r.x + s1r.y, ur = u1r.x + u1r.y;
-    s1 += sr;
-    u1 += ur;
-    a5 = fmaf(dyv, ur, a5);
-    u2 = fmaf(t2.x, sr, u2);
-    a6 = fmaf(t2.x, dyv * sr, a6);
+    s1p = __fadd2_rn(s1p, s1r);
+    u1p = __fadd2_rn(u1p, u1r);
+    a5p = __ffma2_rn(dy, u1r, a5p);
+    u2p = __ffma2_rn(t2, s1r, u2p);
+    a6p = __ffma2_rn(__fmul2_rn(t2, dy), s1r, a6p);
   }
+  const float s1 = s1p.x + s1p.y, u1 = u1p.x + u1p.y, u2 = u2p.x + u2p.y;
+  const float a5 = a5p.x + a5p.y, a6 = a6p.x + a6p.y;
   float* dst = rec_grad + (size_t)rid * 8;
   atomicAdd(dst + 0, s0.x + s0.y);
   atomicAdd(dst + 1, s1);
