@@ -922,6 +922,96 @@ def run_scatter_ablation(args):
     return 0
 
 
+# ---------------------------------------------------------------- densify (row f2)
+def run_densify(args):
+    """Resampling and the densify / prune step on the bench workload's 1M
+    Gaussians (triangular front-end): synthetic densify statistics (a third of
+    the Gaussians above the gradient threshold, a tenth below the opacity
+    floor), standard normal draws from a seeded generator. Times ug_densify (the
+    whole step: decision, output scan, emit) and ug_sample (1M draws) with CUDA
+    events; both are memory-bound, so each reports its algorithmic bytes per
+    call against the measured HBM copy bandwidth."""
+    import torch
+
+    from paper_2505_05643_gb300 import binding as B
+    from paper_2505_05643_gb300 import render as R
+    from paper_2505_05643_gb300 import synth
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    g, _ = synth.workload_aniso_1m()
+    if args.n:
+        g = {k: v[..., :args.n] for k, v in g.items()}
+    g = synth.scale_rot_to_tri(g, 1e-4)
+    cov = B.UG_COV_TRI
+    P = torch.from_numpy(R.pack_params(g, cov)).cuda()
+    rows, n = P.shape
+    rng = np.random.default_rng(5)
+    faded = torch.from_numpy(rng.random(n) < 0.1).cuda()
+    P[9][faded] = float(np.log(0.002 / 0.998))
+    cnt = torch.from_numpy(rng.integers(0, 5, n).astype(np.float32)).cuda()
+    busy = torch.from_numpy(rng.random(n) < 0.35).cuda()
+    stats = torch.stack([torch.where(busy, 1e-3, 1e-5) * cnt, cnt]).contiguous()
+    m = torch.from_numpy(rng.normal(size=(rows, n)).astype(np.float32)).cuda()
+    v = torch.from_numpy(rng.random((rows, n)).astype(np.float32)).cuda()
+    z = torch.from_numpy(rng.normal(size=(6, n)).astype(np.float32)).cuda()
+    cap = 2 * n
+    po = torch.empty((rows, cap), device="cuda")
+    mo, vo = torch.empty_like(po), torch.empty_like(po)
+    n_out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    scratch = torch.empty(B.ug_densify_scratch_bytes(n), dtype=torch.uint8, device="cuda")
+    cfg = R.make_config(cov_param=cov)
+    dc = B.ug_densify_config_default()
+    idx = torch.arange(n, dtype=torch.int32, device="cuda")
+    y = torch.empty((3, n), device="cuda")
+
+    def timed(fn, reps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(1, args.steps)
+    ms_d = timed(lambda: B.ug_densify(cfg, dc, P, m, v, n, stats, z, cap, po, mo, vo, n_out,
+                                      scratch), reps)
+    ms_s = timed(lambda: B.ug_sample(cfg, P, n, idx, n, z, y), reps)
+    n_o = int(n_out.item())
+    # algorithmic bytes (a lower bound: the draws read for the split Gaussians
+    # are not counted): densify reads params, moments and stats and writes the
+    # outputs (params and moments); ug_sample reads an index, the mean and
+    # factor rows (9 floats) and three draws, and writes three floats per draw
+    bytes_d = n * (3 * rows * 4 + 8) + n_o * 3 * rows * 4
+    bytes_s = n * (4 + 9 * 4 + 12 + 12)
+    line = {
+        "metric": "densify / prune step and resampling, 1M Gaussians (TRI)",
+        "value": n / (ms_d * 1e-3), "unit": "Gaussians/s (densify step)", "n_gpus": 1,
+        "steps": reps, "warmup": max(3, args.warmup), "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "aniso_1m parameters, TRI; a third busy, a tenth faded",
+                   "n": n, "n_out": n_o},
+        "densify_ms": ms_d, "sample_ms": ms_s, "samples_per_s": n / (ms_s * 1e-3),
+        "roofline": {"bound": "hbm", "unit": "GB/s", "peak": hbm,
+                     "densify": {"achieved": bytes_d / (ms_d * 1e-3) / 1e9,
+                                 "frac": bytes_d / (ms_d * 1e-3) / 1e9 / hbm,
+                                 "bytes_per_call": bytes_d},
+                     "sample": {"achieved": bytes_s / (ms_s * 1e-3) / 1e9,
+                                "frac": bytes_s / (ms_s * 1e-3) / 1e9 / hbm,
+                                "bytes_per_call": bytes_s}},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -934,9 +1024,11 @@ def main():
     ap.add_argument("--cpu-planes", type=int, default=64, help="planes in the CPU oracle sample")
     ap.add_argument("--n", type=int, default=None, help="use the first n Gaussians (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="aniso_1m", choices=["aniso_1m", "train_200k", "recon"],
+    ap.add_argument("--workload", default="aniso_1m",
+                    choices=["aniso_1m", "train_200k", "recon", "densify"],
                     help="train_200k: batched graph step against one plane per launch; "
-                         "recon: reconstruction run with SSIM on held-out poses")
+                         "recon: reconstruction run with SSIM on held-out poses; "
+                         "densify: the densify / prune step and resampling")
     ap.add_argument("--recon-n", type=int, default=3_000_000)
     ap.add_argument("--recon-hidden", type=int, default=1_000_000)
     ap.add_argument("--recon-steps", type=int, default=2000)
@@ -954,6 +1046,8 @@ def main():
         return run_train_compare(args)
     if args.workload == "recon":
         return run_recon(args)
+    if args.workload == "densify":
+        return run_densify(args)
     if args.ablation == "scatter":
         return run_scatter_ablation(args)
     return run_ours(args)

@@ -320,6 +320,60 @@ ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_
                          uint32_t** record_boxes, float** record_a, float** record_b,
                          uint32_t** record_planes);
 
+/* Row f2: resampling and the densify / prune step (Sec. 3.2 sampling
+ * y = mu + L^-T z; Sec. 3.5 takes the densification heuristics over from Kerbl
+ * et al. without stating them, so the decision quantities below are this
+ * library's reading). Parameters are one [rows][n] FP32 buffer in the packed
+ * row order (mean 3, then tri 6 = l11 l21 l31 l22 l32 l33, or log_scale 3 +
+ * quat 4, then opacity logit, intensity), as ug_adam_step takes them. */
+typedef struct {
+  float grad_threshold; /* densify when the mean |dL/dmu| over the counted steps exceeds
+                           this; default 2e-4 */
+  float min_opacity;    /* prune when sigmoid(logit) < this (decided on the logit);
+                           default 0.005 */
+  float size_threshold; /* split when the extent exceeds this, else clone; the extent is
+                           sqrt(trace Sigma) (TRI) or the largest scale (SCALE_ROT);
+                           default 0.01 */
+  float split_factor;   /* phi > 1: a split's two children have covariance Sigma / phi^2;
+                           default 1.6 */
+  int32_t reserved[4];
+} ug_densify_config;
+
+ug_status ug_densify_config_default(ug_densify_config* dc);
+
+/* y = mu + L^-T z (TRI, by back substitution with L^T, L_kk = l_kk^2 + beta) or
+ * y = mu + R S z (SCALE_ROT) for the m Gaussians idx[k] of the [rows][n]
+ * parameter buffer; z and y are [3][m] (z: standard normal draws supplied by
+ * the caller). cfg gives cov_param and beta. Device pointers; m = 0 is a no-op. */
+ug_status ug_sample(const ug_config* cfg, const float* params, int64_t n, const int32_t* idx,
+                    int64_t m, const float* z, float* y, ug_stream stream);
+
+/* Densify statistics of one step: for every Gaussian with dL/dmu != 0,
+ * stats[0][i] += |dL/dmu_i| and stats[1][i] += 1 (grad_mean: [3][n], the mean
+ * rows of the gradient; stats: [2][n], zeroed by the caller when a new
+ * interval starts). */
+ug_status ug_densify_stats(const float* grad_mean, int64_t n, float* stats, ug_stream stream);
+
+/* Bytes of device scratch ug_densify needs for n Gaussians. */
+size_t ug_densify_scratch_bytes(int64_t n);
+
+/* One densify / prune step, in input order: a Gaussian with sigmoid(logit) <
+ * min_opacity is removed; else, with mean |dL/dmu| = stats[0][i] / stats[1][i]
+ * (0 when never counted) above grad_threshold, it is cloned (itself and an
+ * identical copy) when its extent is at most size_threshold and split into two
+ * children otherwise (means mu + L^-T z with z = z_rows[0..2][i] and
+ * z_rows[3..5][i], covariance Sigma / phi^2, same opacity and intensity);
+ * the rest are kept. Kept Gaussians keep their Adam moments, clones and
+ * children get zero moments. Outputs are [rows][capacity] buffers (params,
+ * exp_avg, exp_avg_sq); *n_out (device) receives the number of outputs, and
+ * when it exceeds capacity nothing past capacity is written. z: [6][n].
+ * Device pointers; scratch of ug_densify_scratch_bytes(n) bytes. */
+ug_status ug_densify(const ug_config* cfg, const ug_densify_config* dc, const float* params,
+                     const float* exp_avg, const float* exp_avg_sq, int64_t n, const float* stats,
+                     const float* z, int64_t capacity, float* params_out, float* exp_avg_out,
+                     float* exp_avg_sq_out, int64_t* n_out, void* scratch, size_t scratch_bytes,
+                     ug_stream stream);
+
 /* Test hook for the rasterizers' bounded waits (rows a5, a7). With on != 0
  * the producer warps of ug_render and ug_render_backward_raster issue no
  * stage, so every consumer wait runs out after its time limit (about one

@@ -38,6 +38,8 @@ EXPORTS = (
     "ug_debug_stall_pipeline",
     "ug_render_backward_raster", "ug_preprocess_backward", "ug_render_scatter",
     "ug_ssim_scratch_floats", "ug_ssim",
+    "ug_densify_config_default", "ug_sample", "ug_densify_stats", "ug_densify_scratch_bytes",
+    "ug_densify",
 )
 UG_MSE_STATIC_MAX_N = 1 << 30
 
@@ -55,6 +57,12 @@ class ug_config(ctypes.Structure):
                 ("tile", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("fp64_ratio", ctypes.c_float), ("variant_bwd", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 2)]
+
+
+class ug_densify_config(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("min_opacity", ctypes.c_float),
+                ("size_threshold", ctypes.c_float), ("split_factor", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class ug_plan(ctypes.Structure):
@@ -137,6 +145,12 @@ def load(build_if_missing: bool = True):
     lib.ug_adam_step.argtypes = [vp, vp, vp, vp, i32, i64, vp, vp, f32, f32, f32, vp]
     lib.ug_read_status.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp, vp]
     lib.ug_debug_stall_pipeline.argtypes = [P(ug_plan), vp, ctypes.c_size_t, i32, vp]
+    lib.ug_densify_config_default.argtypes = [P(ug_densify_config)]
+    lib.ug_sample.argtypes = [P(ug_config), vp, i64, vp, i64, vp, vp, vp]
+    lib.ug_densify_stats.argtypes = [vp, i64, vp, vp]
+    lib.ug_densify_scratch_bytes.argtypes = [i64]
+    lib.ug_densify.argtypes = [P(ug_config), P(ug_densify_config), vp, vp, vp, i64, vp, vp, i64,
+                               vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.ug_debug_views.argtypes = [P(ug_plan), vp, ctypes.c_size_t, P(vp), P(vp), P(vp), P(vp),
                                    P(vp), P(vp), P(vp)]
     for name in EXPORTS:
@@ -145,9 +159,10 @@ def load(build_if_missing: bool = True):
         if fn.argtypes is None:
             raise RuntimeError(f"binding declares no argument types for {name}")
         if name not in ("ug_version", "ug_status_string", "ug_num_variants",
-                        "ug_ssim_scratch_floats"):
+                        "ug_ssim_scratch_floats", "ug_densify_scratch_bytes"):
             fn.restype = ctypes.c_int
     lib.ug_ssim_scratch_floats.restype = ctypes.c_size_t
+    lib.ug_densify_scratch_bytes.restype = ctypes.c_size_t
     _lib = lib
     return lib
 
@@ -278,6 +293,37 @@ def ug_adam_step(param, grad, exp_avg, exp_avg_sq, rows: int, n: int, d_rows, d_
     _check(load().ug_adam_step(_ptr(param), _ptr(grad), _ptr(exp_avg), _ptr(exp_avg_sq),
                                int(rows), int(n), _ptr(d_rows), _ptr(d_step), float(beta1),
                                float(beta2), float(eps), _stream(stream)), "ug_adam_step")
+
+
+def ug_densify_config_default() -> ug_densify_config:
+    dc = ug_densify_config()
+    _check(load().ug_densify_config_default(ctypes.byref(dc)), "ug_densify_config_default")
+    return dc
+
+
+def ug_sample(cfg: ug_config, params, n: int, idx, m: int, z, y, stream=None):
+    """y[3][m] = mu + L^-T z (or mu + R S z) for the Gaussians idx[m] of params[rows][n]."""
+    _check(load().ug_sample(ctypes.byref(cfg), _ptr(params), int(n), _ptr(idx), int(m), _ptr(z),
+                            _ptr(y), _stream(stream)), "ug_sample")
+
+
+def ug_densify_stats(grad_mean, n: int, stats, stream=None):
+    _check(load().ug_densify_stats(_ptr(grad_mean), int(n), _ptr(stats), _stream(stream)),
+           "ug_densify_stats")
+
+
+def ug_densify_scratch_bytes(n: int) -> int:
+    return int(load().ug_densify_scratch_bytes(int(n)))
+
+
+def ug_densify(cfg: ug_config, dc: ug_densify_config, params, exp_avg, exp_avg_sq, n: int, stats,
+               z, capacity: int, params_out, exp_avg_out, exp_avg_sq_out, n_out, scratch,
+               stream=None):
+    _check(load().ug_densify(ctypes.byref(cfg), ctypes.byref(dc), _ptr(params), _ptr(exp_avg),
+                             _ptr(exp_avg_sq), int(n), _ptr(stats), _ptr(z), int(capacity),
+                             _ptr(params_out), _ptr(exp_avg_out), _ptr(exp_avg_sq_out),
+                             _ptr(n_out), _ptr(scratch), scratch.numel() * scratch.element_size(),
+                             _stream(stream)), "ug_densify")
 
 
 def ug_read_status(plan: ug_plan, ws, out, stream=None):

@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cmath>
+
 #include "ug_internal.cuh"
 
 using namespace ug;
@@ -348,6 +350,66 @@ ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_
   if (record_b) *record_b = reinterpret_cast<float*>(v.rec_b);
   if (record_planes) *record_planes = v.rec_plane;
   return UG_OK;
+}
+
+ug_status ug_densify_config_default(ug_densify_config* dc) {
+  if (!dc) return UG_ERR_INVALID_ARGUMENT;
+  *dc = ug_densify_config{};
+  dc->grad_threshold = 2e-4f;
+  dc->min_opacity = 0.005f;
+  dc->size_threshold = 0.01f;
+  dc->split_factor = 1.6f;
+  return UG_OK;
+}
+
+static bool cov_ok(const ug_config* cfg) {
+  return cfg && (cfg->cov_param == UG_COV_TRI || cfg->cov_param == UG_COV_SCALE_ROT) &&
+         cfg->beta > 0.f && std::isfinite(cfg->beta);
+}
+
+ug_status ug_sample(const ug_config* cfg, const float* params, int64_t n, const int32_t* idx,
+                    int64_t m, const float* z, float* y, ug_stream stream) {
+  if (!cov_ok(cfg) || n < 1 || m < 0) return UG_ERR_INVALID_ARGUMENT;
+  if (m > 0 && (!params || !idx || !z || !y)) return UG_ERR_INVALID_ARGUMENT;
+  return cuda_status(launch_sample(cfg->cov_param, params, n, cfg->beta, idx, m, z, y,
+                                   reinterpret_cast<cudaStream_t>(stream)));
+}
+
+ug_status ug_densify_stats(const float* grad_mean, int64_t n, float* stats, ug_stream stream) {
+  if (n < 1 || !grad_mean || !stats) return UG_ERR_INVALID_ARGUMENT;
+  return cuda_status(launch_densify_stats(grad_mean, n, stats,
+                                          reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t ug_densify_scratch_bytes(int64_t n) { return n < 1 ? 0 : densify_scratch_bytes(n); }
+
+ug_status ug_densify(const ug_config* cfg, const ug_densify_config* dc, const float* params,
+                     const float* exp_avg, const float* exp_avg_sq, int64_t n, const float* stats,
+                     const float* z, int64_t capacity, float* params_out, float* exp_avg_out,
+                     float* exp_avg_sq_out, int64_t* n_out, void* scratch, size_t scratch_bytes,
+                     ug_stream stream) {
+  if (!cov_ok(cfg) || !dc || n < 1 || n >= ((int64_t)1 << 31) || capacity < 1) return UG_ERR_INVALID_ARGUMENT;
+  if (!params || !exp_avg || !exp_avg_sq || !stats || !z || !params_out || !exp_avg_out ||
+      !exp_avg_sq_out || !n_out || !scratch)
+    return UG_ERR_INVALID_ARGUMENT;
+  if (!(dc->min_opacity > 0.f && dc->min_opacity < 1.f) || !(dc->split_factor > 1.f) ||
+      !(dc->size_threshold > 0.f) || !std::isfinite(dc->grad_threshold) ||
+      !std::isfinite(dc->size_threshold) || !std::isfinite(dc->split_factor))
+    return UG_ERR_INVALID_ARGUMENT;
+  if (scratch_bytes < densify_scratch_bytes(n)) return UG_ERR_WORKSPACE_TOO_SMALL;
+  const double p = dc->min_opacity, sz = dc->size_threshold;
+  DensifyThresholds t;
+  t.logit_min = (float)std::log(p / (1.0 - p));
+  t.grad_threshold = dc->grad_threshold;
+  t.size2 = (float)(sz * sz);
+  t.log_size = (float)std::log(sz);
+  t.beta = cfg->beta;
+  t.phi = dc->split_factor;
+  t.log_phi = (float)std::log((double)dc->split_factor);
+  const int rows = cfg->cov_param == UG_COV_TRI ? 11 : 12;
+  return cuda_status(launch_densify(cfg->cov_param, rows, params, exp_avg, exp_avg_sq, n, stats, z,
+                                    t, capacity, params_out, exp_avg_out, exp_avg_sq_out, n_out,
+                                    scratch, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 ug_status ug_debug_stall_pipeline(const ug_plan* plan, void* ws, size_t ws_bytes, int32_t on,

@@ -254,6 +254,23 @@ cudaError_t launch_mse(const float* image, const float* target, int64_t n, float
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int32_t rows, int64_t n,
                         const ug_adam_row* d_rows, int32_t* d_step, float b1, float b2,
                         float eps, cudaStream_t s);
+// Row f2 (ug_densify.cu). Decision thresholds in FP32, derived on the host.
+struct DensifyThresholds {
+  float logit_min;       // prune when logit < logit_min (sigmoid(logit) < min_opacity)
+  float grad_threshold;  // densify when mean |dL/dmu| > grad_threshold
+  float size2;           // TRI: split when trace Sigma > size2
+  float log_size;        // SCALE_ROT: split when the largest log scale > log_size
+  float beta, phi, log_phi;
+};
+size_t densify_scratch_bytes(int64_t n);
+cudaError_t launch_sample(int cov, const float* params, int64_t n, float beta, const int32_t* idx,
+                          int64_t m, const float* z, float* y, cudaStream_t s);
+cudaError_t launch_densify_stats(const float* gmean, int64_t n, float* stats, cudaStream_t s);
+cudaError_t launch_densify(int cov, int rows, const float* params, const float* m, const float* v,
+                           int64_t n, const float* stats, const float* z,
+                           const DensifyThresholds& t, int64_t cap, float* params_out,
+                           float* m_out, float* v_out, int64_t* n_out, void* scratch,
+                           cudaStream_t s);
 int num_render_variants(int tile);
 int num_render_variants_bwd(int tile);
 
