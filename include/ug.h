@@ -2,7 +2,7 @@
  * ug.h — C ABI of the GB300 UltraGauss plane rasterizer.
  *
  * UltraGauss (arXiv 2505.05643) renders an ultrasound image as the
- * intersection of anisotropic 3D Gaussians with a probe plane (Sec. 3.1):
+ * intersection of anisotropic 3D Gaussians with a probe plane (Sec. 4.1):
  * each pixel x of the plane is lifted to x_|0 = [x1, x2, 0] in the probe frame
  * and takes
  *
@@ -11,9 +11,9 @@
  *
  * (Eq. alpha-combine, Eq. colour-combine, Eq. us-render, Eq. mahalanobis-3d),
  * summed only over pixels inside each Gaussian's chi^2 bounding box
- * (Sec. 3.3, Eq. ellipsoid and Eq. boundary) and only for Gaussians whose
- * box meets the plane (Sec. 3.4). Covariances use the paper's triangular
- * precision factor Sigma^-1 = L L^T with diagonal l_kk^2 + beta (Sec. 3.2,
+ * (Sec. 4.3, Eq. ellipsoid and Eq. boundary) and only for Gaussians whose
+ * box meets the plane (Sec. 4.4). Covariances use the paper's triangular
+ * precision factor Sigma^-1 = L L^T with diagonal l_kk^2 + beta (Sec. 4.2,
  * Eq. tri-param) or, as a second front-end, Sigma = R diag(s^2) R^T.
  *
  * Conventions shared by every call:
@@ -64,7 +64,7 @@ enum { UG_CUTOFF_BOX = 0, UG_CUTOFF_BOX_AND_ELLIPSOID = 1 };
  * [6][n] = l11, l21, l31, l22, l32, l33 and log_scale/quat are unused; for
  * UG_COV_SCALE_ROT `log_scale` is [3][n] (s = exp(log_scale)) and `quat` is
  * [4][n] = w, x, y, z (normalised inside; need not be unit). mean is [3][n];
- * opacity_logit and intensity are [n] (alpha = sigmoid(logit), Sec. 3.4). */
+ * opacity_logit and intensity are [n] (alpha = sigmoid(logit), Sec. 4.5). */
 typedef struct {
   const float* mean;
   const float* tri;
@@ -102,7 +102,7 @@ typedef struct {
 
 /* Cut-off and image-formation constants, tile shape and kernel variant. */
 typedef struct {
-  float chi2;        /* chi^2_3 bound of the cut-off ellipsoid; 7.815 (p = 95 %, Sec. 3.3) */
+  float chi2;        /* chi^2_3 bound of the cut-off ellipsoid; 7.815 (p = 95 %, Sec. 4.3) */
   float beta;        /* diagonal offset of Eq. tri-param, > 0; default 1e-4 */
   float alpha_bg;    /* background coefficient a_bg > 0 (Eq. alpha-combine); default 1e-3 */
   float c_bg;        /* background intensity; default 0 */
@@ -154,7 +154,7 @@ typedef struct {
 
 /* Adam learning-rate schedule of one parameter row (device array entry):
  * lr(t) = lr_init * (lr_final / lr_init)^min(t / decay_steps, 1); decay_steps
- * <= 0 keeps lr_init (Sec. 3.4: 0.05 for all rows, the means' rows decay from
+ * <= 0 keeps lr_init (Sec. 4.5: 0.05 for all rows, the means' rows decay from
  * 1.6e-4). */
 typedef struct {
   float lr_init, lr_final;
@@ -184,7 +184,7 @@ ug_status ug_plan_init(const ug_config* cfg, int64_t n, const ug_plane* host_pla
                        int32_t num_planes, int64_t record_capacity,
                        int64_t instance_capacity, ug_plan* plan);
 
-/* Rows a1-a3 (Sec. 3.2-3.4): per (plane, Gaussian) activation, probe-frame
+/* Rows a1-a3 (Sec. 4.2-4.4): per (plane, Gaussian) activation, probe-frame
  * mean, Sigma3D by forward substitution, chi^2 box, phase-1 rejection, pixel
  * box, in-plane conic and peak weight; then the records of the visible pairs
  * in (Gaussian chunk, plane, Gaussian) order and their (tile, record)
@@ -205,7 +205,7 @@ ug_status ug_bin_sort(const ug_plan* plan, void* ws, size_t ws_bytes, ug_stream 
 ug_status ug_render(const ug_plan* plan, void* ws, size_t ws_bytes, float* image,
                     float* alpha, ug_stream stream);
 
-/* Evaluation metrics of rendered slices (Sec. 4): for P images of W x H pixels
+/* Evaluation metrics of rendered slices (Sec. 5): for P images of W x H pixels
  * stored one after the other (row-major, device memory), the mean SSIM of
  * image against target (Wang et al.: 11 x 11 Gaussian window, sigma 1.5,
  * C1 = 0.01^2, C2 = 0.03^2, data range 1, every position where the window lies
@@ -219,7 +219,7 @@ ug_status ug_ssim(const float* image, const float* target, int32_t P, int32_t W,
                   float* scratch, size_t scratch_floats, float* ssim, float* psnr,
                   ug_stream stream);
 
-/* The paper's own phase 2 (Sec. 3.4), kept as an ablation of ug_render: every
+/* The paper's own phase 2 (Sec. 4.4), kept as an ablation of ug_render: every
  * visible record of the last ug_preprocess adds its weight and weighted
  * intensity to each pixel of its box with atomics (no binning or sort needed),
  * then C and alpha are formed as in ug_render. Same records and per-pixel
@@ -282,9 +282,9 @@ ug_status ug_render_backward_raster(const ug_plan* plan, void* ws, size_t ws_byt
 
 /* Row a8 alone (the second half of ug_render_backward): chain the per-record
  * gradients left in the workspace by ug_render_backward_raster through the
- * preprocess of rows a1-a2 (plane projection, Sec. 3.1; Eq. tri-param or the
- * scale-rotation front-end, Sec. 3.2; the cut-off box is a constant) and the
- * activations (Sec. 3.4), and sum them over planes into *grads (written, not
+ * preprocess of rows a1-a2 (plane projection, Sec. 4.1; Eq. tri-param or the
+ * scale-rotation front-end, Sec. 4.2; the cut-off box is a constant) and the
+ * activations (Sec. 4.5), and sum them over planes into *grads (written, not
  * accumulated; one thread per Gaussian, no atomics). `gaussians` must be the
  * parameters ug_preprocess ran on. */
 ug_status ug_preprocess_backward(const ug_plan* plan, const ug_gaussians* gaussians, void* ws,
@@ -320,8 +320,8 @@ ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_
                          uint32_t** record_boxes, float** record_a, float** record_b,
                          uint32_t** record_planes);
 
-/* Row f2: resampling and the densify / prune step (Sec. 3.2 sampling
- * y = mu + L^-T z; Sec. 3.5 takes the densification heuristics over from Kerbl
+/* Row f2: resampling and the densify / prune step (Sec. 4.2 sampling
+ * y = mu + L^-T z; Sec. 4.5 takes the densification heuristics over from Kerbl
  * et al. without stating them, so the decision quantities below are this
  * library's reading). Parameters are one [rows][n] FP32 buffer in the packed
  * row order (mean 3, then tri 6 = l11 l21 l31 l22 l32 l33, or log_scale 3 +

@@ -9,16 +9,16 @@ Functions and what they follow (section / equation of the paper):
 
 * :func:`render`      Eq. alpha-combine, Eq. colour-combine, Eq. us-render,
                       Eq. mahalanobis-3d, Eq. ellipsoid / Eq. boundary cut-off
-                      with the two-phase rule of Sec. 3.4; dense (every pixel x
+                      with the two-phase rule of Sec. 4.4; dense (every pixel x
                       every Gaussian) or scatter (same numbers, fewer pairs).
-* :func:`render_grad` analytic FP64 gradient of the same formulas (Sec. 3.5).
+* :func:`render_grad` analytic FP64 gradient of the same formulas (Sec. 4.5).
 * :func:`geometry`    probe-frame means, box half-extents, phase-1 flags and
-                      exact pixel boxes (Sec. 3.3 - 3.4).
+                      exact pixel boxes (Sec. 4.3 - 3.4).
 * :func:`covariance`  Eq. tri-param (triangular precision) or the
-                      scale/rotation form quoted in Sec. 3.2.
+                      scale/rotation form quoted in Sec. 4.2.
 * :func:`contrib`     the included pairs of one Gaussian (for finite
                       differences).
-* :mod:`oracle.adam`  Adam (Sec. 3.5 uses Adam; textbook update).
+* :mod:`oracle.adam`  Adam (Sec. 4.5 uses Adam; textbook update).
 """
 from __future__ import annotations
 
@@ -35,12 +35,12 @@ _SRC = os.path.join(_HERE, "ug_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 
-CHI2_95_PRINTED = 7.815  # Sec. 3.3: chi^2 for 3 DoF at p = 95 %, as printed
+CHI2_95_PRINTED = 7.815  # Sec. 4.3: chi^2 for 3 DoF at p = 95 %, as printed
 
 
 @dataclass
 class Config:
-    """Cut-off and image-formation constants: chi2 = 7.815 as printed (Sec. 3.3);
+    """Cut-off and image-formation constants: chi2 = 7.815 as printed (Sec. 4.3);
     beta, alpha_bg and c_bg are not printed in the paper and take the values
     1e-4, 1e-3 and 0; cutoff 0 is the paper's box, 1 adds the ellipsoid."""
     chi2: float = CHI2_95_PRINTED

@@ -1,6 +1,6 @@
 """Adam in FP64 NumPy (test infrastructure).
 
-The paper trains with Adam (Sec. 3.4: learning rate 0.05 for all Gaussian
+The paper trains with Adam (Sec. 4.5: learning rate 0.05 for all Gaussian
 parameters, means from 0.00016 with exponential decay). This is the textbook
 update with bias correction, written out step by step:
 

@@ -1,14 +1,14 @@
 """Resampling and the densify / prune step in NumPy (test infrastructure; only
 tests, the smoke check and the bench's CPU legs use it).
 
-Sampling (Sec. 3.2): with the triangular precision factor, Sigma^-1 = L L^T,
+Sampling (Sec. 4.2): with the triangular precision factor, Sigma^-1 = L L^T,
 L = [[l11^2 + beta, 0, 0], [l21, l22^2 + beta, 0], [l31, l32, l33^2 + beta]],
 a draw of N(mu, Sigma) is y = mu + L^-T z with z standard normal: Sigma =
 L^-T L^-1, so Cov(L^-T z) = Sigma. Here w = L^-T z is the solution of the
 upper-triangular system L^T w = z, by back substitution in FP64. For the
 scale/rotation front-end Sigma = R S^2 R^T and y = mu + R S z.
 
-Densify / prune (Sec. 3.5 takes the heuristics over from Kerbl et al. without
+Densify / prune (Sec. 4.5 takes the heuristics over from Kerbl et al. without
 stating them; the reading is the library's, see ug_densify in ug.h): per
 Gaussian, in input order,
   - prune  when sigmoid(logit) < min_opacity (decided as logit < logit(min_opacity));

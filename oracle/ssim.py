@@ -2,7 +2,7 @@
 tests, the smoke check and the bench's CPU legs use it).
 
 The paper evaluates reconstructions with SSIM (Wang et al., 2004) and PSNR
-(Sec. 4). Its window parameters are not printed; this follows the original
+(Sec. 5). Its window parameters are not printed; this follows the original
 definition: an 11 x 11 Gaussian window with sigma 1.5 (normalised to sum 1),
 C1 = (0.01 L)^2 and C2 = (0.03 L)^2 with data range L = 1, evaluated at every
 position where the window lies inside the image ("valid" positions), and the

@@ -7,19 +7,19 @@
  * It is the plain definition, with no tiling and no sorting:
  *
  *   covariance   Sigma^-1 = L L^T, L lower triangular with diagonal
- *                l_kk^2 + beta (Sec. 3.2, Eq. tri-param), or
+ *                l_kk^2 + beta (Sec. 4.2, Eq. tri-param), or
  *                Sigma = R diag(s^2) R^T from a normalised quaternion and
- *                s = exp(log_scale) (Sec. 3.2, the Kerbl et al. form);
- *   opacity      alpha_i = sigmoid(logit_i) (Sec. 3.4);
+ *                s = exp(log_scale) (Sec. 4.2, the Kerbl et al. form);
+ *   opacity      alpha_i = sigmoid(logit_i) (Sec. 4.5);
  *   probe frame  mu3D = W mu (rows u, v, n = u x v, origin o), Sigma3D =
- *                W Sigma W^T (Sec. 3.1, Eq. mahalanobis-3d and the line after);
- *   cut-off      half-extents from the p% ellipsoid (Sec. 3.3, Eq. ellipsoid
+ *                W Sigma W^T (Sec. 4.1, Eq. mahalanobis-3d and the line after);
+ *   cut-off      half-extents from the p% ellipsoid (Sec. 4.3, Eq. ellipsoid
  *                and Eq. boundary): the printed cofactor/determinant formula
  *                applied to the matrix of the quadratic form, the precision
  *                P3D = (Sigma3D)^-1, i.e. h_k = sqrt(chi2 * cof_kk(P3D) /
  *                det(P3D));
  *   phase 1      a Gaussian is rejected on a plane iff m3 - h3 > 0 or
- *                m3 + h3 < 0 (Sec. 3.4 load balancing, item 1);
+ *                m3 + h3 < 0 (Sec. 4.4 load balancing, item 1);
  *   phase 2      pixel x is inside iff m1 - h1 <= x1 <= m1 + h1 and
  *                m2 - h2 <= x2 <= m2 + h2 (item 2); in the optional
  *                ellipsoid mode additionally q <= chi2;

@@ -1,11 +1,11 @@
 // Row f2: resampling and the densify / prune step.
 //
 // Resampling draws a point of a Gaussian as y = mu + L^-T z with z standard
-// normal (Sec. 3.2: the triangular precision factor makes this one back
+// normal (Sec. 4.2: the triangular precision factor makes this one back
 // substitution with L^T); for the scale/rotation front-end y = mu + R S z.
 //
 // The densify / prune step follows the heuristics the paper takes over from
-// Kerbl et al. (Sec. 3.5), with the decision quantities read as stated in the
+// Kerbl et al. (Sec. 4.5), with the decision quantities read as stated in the
 // ug_densify_config documentation: prune when the opacity is below a minimum;
 // densify when the mean norm of dL/dmu over the counted steps exceeds a
 // threshold; a densified Gaussian whose extent is at most the size threshold is

@@ -107,7 +107,7 @@ __device__ __forceinline__ void load_params(const ug_gaussians& g, int64_t n, in
 }
 
 // Covariance factor of one Gaussian: Sigma^-1 = F F^T, Fi = F^-1.
-// Triangular (Sec. 3.2, Eq. tri-param): F = L lower triangular with diagonal
+// Triangular (Sec. 4.2, Eq. tri-param): F = L lower triangular with diagonal
 // l_kk^2 + beta; Fi by forward substitution. Scale/rotation: F = R diag(1/s),
 // Fi = diag(s) R^T with R from the normalised quaternion.
 template <typename T>
@@ -311,7 +311,7 @@ __device__ __forceinline__ void pixel_range(T c, T h, T inv_pitch, T shift, int 
   b = to_int(floor(hi_c));
 }
 
-// Sec. 3.3-3.4: h_k = sqrt(chi2 Sigma3D_kk); reject unless m3 - h3 <= 0 <=
+// Sec. 4.3-4.4: h_k = sqrt(chi2 Sigma3D_kk); reject unless m3 - h3 <= 0 <=
 // m3 + h3; pixel j is inside iff m1 - h1 <= (j + 1/2 - W/2) pitch_u <= m1 + h1.
 template <typename T, int COV>
 __device__ __forceinline__ PairBox pair_box(const Factor<T>& f, const PlaneDev& pl, float chi2,

@@ -1,5 +1,5 @@
 // The paper's own forward, kept as an ablation of the tile gather: phase 2 of
-// Sec. 3.4 loops over every visible (plane, Gaussian) record's pixel box and
+// Sec. 4.4 loops over every visible (plane, Gaussian) record's pixel box and
 // adds the record's weight and weighted intensity to each pixel with atomics;
 // a last pass forms C = (S_c + a_bg c_bg) / (S_a + a_bg) (Eq. alpha-combine,
 // Eq. colour-combine). Same records and same per-pixel weight formula as the

@@ -1,5 +1,5 @@
 // SSIM and PSNR of rendered slices against targets (the paper's evaluation
-// metrics, Sec. 4): 11 x 11 Gaussian window with sigma 1.5 normalised to sum
+// metrics, Sec. 5): 11 x 11 Gaussian window with sigma 1.5 normalised to sum
 // 1, C1 = (0.01)^2, C2 = (0.03)^2 (data range 1), every position where the
 // window lies inside the image, mean over those positions; PSNR = 10
 // log10(1 / MSE) per image.

@@ -5,10 +5,10 @@ rasterizer's arithmetic, and it is the one module that both the FP64 oracle
 side (tests, CPU baseline) and the CUDA side (binding, bench) use.
 
 The paper's datasets (fetal-brain volumes of 160^3 voxels at 0.6 mm, and
-freehand sweeps of 160x160 frames; Sec. 4.1) are not available, so every
+freehand sweeps of 160x160 frames; Sec. 5.1) are not available, so every
 input here is synthetic: the cube [-1, 1]^3 stands in for the imaged volume
-and each probe plane spans 2 x 2 units, as in the paper's Sec. 3.4
-initialisation ("means uniformly at random within the imaged volume").
+and each probe plane spans 2 x 2 units; the Gaussians' means start uniform over the
+imaged volume, as in the paper's initialisation (Sec. 4.5).
 
 Gaussian parameters are returned in "row" layout (one row per scalar
 parameter, n columns), float32, which is the structure-of-arrays layout the
@@ -78,7 +78,7 @@ def gaussians_scale_rot(rng: np.random.Generator, n: int, scale_lo: float = 0.01
     in [scale_lo, scale_hi], uniform random unit quaternions, intensities U[0,1].
 
     Draw order: mean, scale, rotation, intensity. The opacity logit is fixed
-    (sigmoid(1) = 0.731 is the paper's initial opacity, Sec. 3.4).
+    (sigmoid(1) = 0.731 is the paper's initial opacity, Sec. 4.5).
     """
     mean = rng.uniform(-1.0, 1.0, (3, n))
     log_scale = rng.uniform(np.log(scale_lo), np.log(scale_hi), (3, n))
@@ -120,7 +120,7 @@ def gaussians_anisotropic(rng: np.random.Generator, n: int, smax_lo: float = 0.0
 
 
 def gaussians_paper_init(rng: np.random.Generator, n: int) -> dict:
-    """The paper's initialisation (Sec. 3.4): means uniform in the volume,
+    """The paper's initialisation (Sec. 4.5): means uniform in the volume,
     c_i = 0.5, opacity 0.731 (logit 1), and the six triangular parameters
     uniform in [4, 5)."""
     mean = rng.uniform(-1.0, 1.0, (3, n))
@@ -194,7 +194,7 @@ def planes_sweep_pool(rng: np.random.Generator, pool: int = 160, size=(256, 256)
     +travel*d; the base frame has normal d; every pose is then turned by
     independent angles U(-jitter, +jitter) about its own u and v axes
     (a stand-in for the paper's 160-slice sweeps with +-5 degree jitter,
-    Sec. 4.2)."""
+    Sec. 5.2)."""
     d = rng.standard_normal(3)
     d /= np.linalg.norm(d)
     a = np.array([1.0, 0.0, 0.0]) if abs(d[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
@@ -278,7 +278,7 @@ def workload_aniso_1m(seed: int = 0, n: int = 1_000_000, P: int = 64):
 def workload_train_200k(seed: int = 0, n: int = 200_000, hidden_n: int = 100_000,
                         pool: int = 160, size: int = 256):
     """Training workload: 200,000 Gaussians in the paper's initialisation
-    (Sec. 3.4), a hidden 100,000-Gaussian target volume drawn with seed 2 from
+    (Sec. 4.5), a hidden 100,000-Gaussian target volume drawn with seed 2 from
     the fwd_2k distributions, and a pool of 160 sweep poses of size x size
     pixels; a training step takes 32 consecutive poses of the pool (cyclic).
     Returns (gaussians, pose pool, hidden gaussians)."""

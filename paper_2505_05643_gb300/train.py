@@ -15,7 +15,7 @@ import torch
 from . import binding as B
 from . import render as R
 
-# Sec. 3.4: Adam, lr 0.05 for all Gaussian parameters except the means, whose
+# Sec. 4.5: Adam, lr 0.05 for all Gaussian parameters except the means, whose
 # lr starts at 1.6e-4 and decays exponentially (to 1.6e-6 over the run here).
 LR_DEFAULT = 0.05
 LR_MEAN_INIT = 1.6e-4

@@ -113,7 +113,7 @@ def test_ragged_planes_all_variants(tile, variant):
 
 
 def test_fwd_paper_init_triangular():
-    """The paper's initialisation (Sec. 3.4): l_ij in [4, 5), c = 0.5, alpha = 0.731."""
+    """The paper's initialisation (Sec. 4.5): l_ij in [4, 5), c = 0.5, alpha = 0.731."""
     rng = np.random.default_rng(11)
     g = synth.gaussians_paper_init(rng, 4000)
     pl = synth.planes_random(rng, [(96, 96), (64, 80)])

@@ -216,7 +216,7 @@ def test_K4_box_is_the_ellipsoid_aabb():
 
 
 def test_phase1_reject_rule():
-    """A Gaussian is kept on a plane iff |m3| <= h3 (Sec. 3.4, item 1)."""
+    """A Gaussian is kept on a plane iff |m3| <= h3 (Sec. 4.4, item 1)."""
     rng = np.random.default_rng(10)
     g = synth.gaussians_scale_rot(rng, 3000)
     pl = synth.planes_random(rng, [(32, 32)] * 3)
