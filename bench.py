@@ -1012,6 +1012,70 @@ def run_densify(args):
     return 0
 
 
+# ---------------------------------------------------------------- L1 + D-SSIM loss (row f4)
+def run_loss(args):
+    """The fused L1 + D-SSIM loss and its gradient on a training step's images
+    (32 planes of 256 x 256, synthetic image and target), timed with CUDA events
+    against the MSE kernel on the same images; both are memory-bound, so the
+    line reports the algorithmic bytes per call against the measured HBM copy
+    bandwidth (D-SSIM: images read, five window maps and three gradient maps
+    written and read, gradient written)."""
+    import torch
+
+    from paper_2505_05643_gb300 import binding as B
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    P, W, H = 32, 256, 256
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    x = torch.rand(P * H * W, device="cuda", generator=gen)
+    t = (x + 0.1 * torch.randn(P * H * W, device="cuda", generator=gen)).clamp(0, 1)
+    scratch = torch.empty(B.ug_l1_dssim_scratch_floats(P, W, H), device="cuda")
+    grad = torch.empty_like(x)
+    loss = torch.empty(1, device="cuda")
+    mse_loss = torch.empty(B.UG_MSE_LOSS_FLOATS, device="cuda")
+
+    def timed(fn, reps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(1, args.steps)
+    ms_d = timed(lambda: B.ug_l1_dssim_loss_grad(x, t, P, W, H, 0.2, scratch, grad, loss), reps)
+    ms_m = timed(lambda: B.ug_mse_loss_grad(x, t, x.numel(), grad, mse_loss), reps)
+    n = P * W * H
+    Wv, Hv = W - 10, H - 10
+    bytes_d = 4 * (2 * n + 2 * 5 * P * H * Wv + 2 * 3 * P * Hv * Wv + 2 * 3 * P * Hv * W + 2 * n + n)
+    bytes_m = 12 * n
+    line = {
+        "metric": "L1 + D-SSIM loss and gradient, 32 planes of 256x256",
+        "value": n / (ms_d * 1e-3), "unit": "pixels/s", "n_gpus": 1, "steps": reps,
+        "warmup": max(3, args.warmup), "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": "32 planes of 256x256, lambda 0.2"},
+        "l1_dssim_ms": ms_d, "mse_ms": ms_m, "loss": float(loss.item()),
+        "roofline": {"bound": "hbm", "unit": "GB/s", "peak": hbm,
+                     "l1_dssim": {"achieved": bytes_d / (ms_d * 1e-3) / 1e9,
+                                  "frac": bytes_d / (ms_d * 1e-3) / 1e9 / hbm,
+                                  "bytes_per_call": bytes_d},
+                     "mse": {"achieved": bytes_m / (ms_m * 1e-3) / 1e9,
+                             "frac": bytes_m / (ms_m * 1e-3) / 1e9 / hbm,
+                             "bytes_per_call": bytes_m}},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1025,10 +1089,11 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="use the first n Gaussians (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="aniso_1m",
-                    choices=["aniso_1m", "train_200k", "recon", "densify"],
+                    choices=["aniso_1m", "train_200k", "recon", "densify", "loss"],
                     help="train_200k: batched graph step against one plane per launch; "
                          "recon: reconstruction run with SSIM on held-out poses; "
-                         "densify: the densify / prune step and resampling")
+                         "densify: the densify / prune step and resampling; "
+                         "loss: the L1 + D-SSIM loss and gradient")
     ap.add_argument("--recon-n", type=int, default=3_000_000)
     ap.add_argument("--recon-hidden", type=int, default=1_000_000)
     ap.add_argument("--recon-steps", type=int, default=2000)
@@ -1048,6 +1113,8 @@ def main():
         return run_recon(args)
     if args.workload == "densify":
         return run_densify(args)
+    if args.workload == "loss":
+        return run_loss(args)
     if args.ablation == "scatter":
         return run_scatter_ablation(args)
     return run_ours(args)

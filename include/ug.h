@@ -320,6 +320,20 @@ ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_
                          uint32_t** record_boxes, float** record_a, float** record_b,
                          uint32_t** record_planes);
 
+/* Row f4 (the loss half): the training loss of Kerbl et al., which Sec. 4.5
+ * takes over, for P planes of W x H pixels stored one after the other:
+ *   L = (1 - lambda) mean|x - y| + lambda (1 - SSIM),
+ * SSIM the mean over the planes of each plane's mean SSIM (the ug_ssim
+ * definition), and dL/dx for every pixel (the L1 term's derivative is taken
+ * as 0 where x = y). *loss and grad are device memory; scratch holds at least
+ * ug_l1_dssim_scratch_floats(P, W, H) floats. Deterministic. Returns
+ * UG_ERR_INVALID_ARGUMENT for W or H below 11 or lambda outside [0, 1],
+ * UG_ERR_WORKSPACE_TOO_SMALL for too little scratch. */
+size_t ug_l1_dssim_scratch_floats(int32_t P, int32_t W, int32_t H);
+ug_status ug_l1_dssim_loss_grad(const float* image, const float* target, int32_t P, int32_t W,
+                                int32_t H, float lambda, float* scratch, size_t scratch_floats,
+                                float* grad, float* loss, ug_stream stream);
+
 /* Row f2: resampling and the densify / prune step (Sec. 4.2 sampling
  * y = mu + L^-T z; Sec. 4.5 takes the densification heuristics over from Kerbl
  * et al. without stating them, so the decision quantities below are this

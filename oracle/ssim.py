@@ -65,3 +65,61 @@ def ssim_planes(image: np.ndarray, target: np.ndarray, P: int, W: int, H: int):
     b = np.asarray(target, np.float64).reshape(P, H, W)
     return (np.array([ssim(a[p], b[p]) for p in range(P)]),
             np.array([psnr(a[p], b[p]) for p in range(P)]))
+
+
+def ssim_grad(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """d(mean SSIM)/dx of one H x W image (FP64), from the chain rule over every
+    valid window position p: with A1 = 2 mu_x mu_y + C1, A2 = 2 s_xy + C2,
+    B1 = mu_x^2 + mu_y^2 + C1, B2 = s_x^2 + s_y^2 + C2 and S = A1 A2 / (B1 B2),
+      dS/dmu_x = 2 A2 (mu_y B1 - A1 mu_x) / (B1^2 B2),  dS/ds_x^2 = -S / B2,
+      dS/ds_xy = 2 A1 / (B1 B2);
+    pixel q of the window at p enters mu_x with weight w(q - p), s_x^2 with
+    w(q - p)(2 x_q - 2 mu_x) and s_xy with w(q - p)(y_q - mu_y), so
+      dS(p)/dx_q = w(q - p) (a(p) + b(p) x_q + c(p) y_q),
+      a = dS/dmu_x - 2 mu_x dS/ds_x^2 - mu_y dS/ds_xy,  b = 2 dS/ds_x^2,  c = dS/ds_xy,
+    summed over the positions whose window holds q and divided by their count."""
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    w = window()
+    from numpy.lib.stride_tricks import sliding_window_view
+    px = sliding_window_view(x, (WIN, WIN))
+    py = sliding_window_view(y, (WIN, WIN))
+    mx = np.einsum("ijab,ab->ij", px, w)
+    my = np.einsum("ijab,ab->ij", py, w)
+    vx = np.einsum("ijab,ab->ij", px * px, w) - mx * mx
+    vy = np.einsum("ijab,ab->ij", py * py, w) - my * my
+    cxy = np.einsum("ijab,ab->ij", px * py, w) - mx * my
+    A1, A2 = 2 * mx * my + C1, 2 * cxy + C2
+    B1, B2 = mx * mx + my * my + C1, vx + vy + C2
+    S = A1 * A2 / (B1 * B2)
+    d_mx = 2 * A2 * (my * B1 - A1 * mx) / (B1 * B1 * B2)
+    d_vx = -S / B2
+    d_cxy = 2 * A1 / (B1 * B2)
+    a = d_mx - 2 * mx * d_vx - my * d_cxy
+    b = 2 * d_vx
+    c = d_cxy
+    Hv, Wv = S.shape
+    ga, gb, gc = (np.zeros_like(x) for _ in range(3))
+    for i in range(WIN):
+        for j in range(WIN):
+            ga[i:i + Hv, j:j + Wv] += w[i, j] * a
+            gb[i:i + Hv, j:j + Wv] += w[i, j] * b
+            gc[i:i + Hv, j:j + Wv] += w[i, j] * c
+    return (ga + x * gb + y * gc) / S.size
+
+
+def l1_dssim_loss_grad(image: np.ndarray, target: np.ndarray, P: int, W: int, H: int,
+                       lam: float = 0.2):
+    """The training loss Kerbl et al. use, which the paper takes over (Sec. 4.5):
+    L = (1 - lam) mean|x - y| + lam (1 - SSIM), SSIM the mean over the P planes
+    of each plane's mean SSIM; returns (L, dL/dx) in FP64. The L1 term's
+    derivative at x = y is taken as 0."""
+    x = np.asarray(image, np.float64).reshape(P, H, W)
+    t = np.asarray(target, np.float64).reshape(P, H, W)
+    n = x.size
+    s = np.array([ssim(x[p], t[p]) for p in range(P)])
+    L = (1 - lam) * np.abs(x - t).mean() + lam * (1 - s.mean())
+    g = (1 - lam) * np.sign(x - t) / n
+    for p in range(P):
+        g[p] -= lam / P * ssim_grad(x[p], t[p])
+    return float(L), g.reshape(-1)

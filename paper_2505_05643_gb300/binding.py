@@ -39,7 +39,7 @@ EXPORTS = (
     "ug_render_backward_raster", "ug_preprocess_backward", "ug_render_scatter",
     "ug_ssim_scratch_floats", "ug_ssim",
     "ug_densify_config_default", "ug_sample", "ug_densify_stats", "ug_densify_scratch_bytes",
-    "ug_densify",
+    "ug_densify", "ug_l1_dssim_scratch_floats", "ug_l1_dssim_loss_grad",
 )
 UG_MSE_STATIC_MAX_N = 1 << 30
 
@@ -145,6 +145,9 @@ def load(build_if_missing: bool = True):
     lib.ug_adam_step.argtypes = [vp, vp, vp, vp, i32, i64, vp, vp, f32, f32, f32, vp]
     lib.ug_read_status.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp, vp]
     lib.ug_debug_stall_pipeline.argtypes = [P(ug_plan), vp, ctypes.c_size_t, i32, vp]
+    lib.ug_l1_dssim_scratch_floats.argtypes = [i32, i32, i32]
+    lib.ug_l1_dssim_loss_grad.argtypes = [vp, vp, i32, i32, i32, f32, vp, ctypes.c_size_t, vp, vp,
+                                          vp]
     lib.ug_densify_config_default.argtypes = [P(ug_densify_config)]
     lib.ug_sample.argtypes = [P(ug_config), vp, i64, vp, i64, vp, vp, vp]
     lib.ug_densify_stats.argtypes = [vp, i64, vp, vp]
@@ -159,10 +162,12 @@ def load(build_if_missing: bool = True):
         if fn.argtypes is None:
             raise RuntimeError(f"binding declares no argument types for {name}")
         if name not in ("ug_version", "ug_status_string", "ug_num_variants",
-                        "ug_ssim_scratch_floats", "ug_densify_scratch_bytes"):
+                        "ug_ssim_scratch_floats", "ug_densify_scratch_bytes",
+                        "ug_l1_dssim_scratch_floats"):
             fn.restype = ctypes.c_int
     lib.ug_ssim_scratch_floats.restype = ctypes.c_size_t
     lib.ug_densify_scratch_bytes.restype = ctypes.c_size_t
+    lib.ug_l1_dssim_scratch_floats.restype = ctypes.c_size_t
     _lib = lib
     return lib
 
@@ -293,6 +298,18 @@ def ug_adam_step(param, grad, exp_avg, exp_avg_sq, rows: int, n: int, d_rows, d_
     _check(load().ug_adam_step(_ptr(param), _ptr(grad), _ptr(exp_avg), _ptr(exp_avg_sq),
                                int(rows), int(n), _ptr(d_rows), _ptr(d_step), float(beta1),
                                float(beta2), float(eps), _stream(stream)), "ug_adam_step")
+
+
+def ug_l1_dssim_scratch_floats(P: int, W: int, H: int) -> int:
+    return int(load().ug_l1_dssim_scratch_floats(int(P), int(W), int(H)))
+
+
+def ug_l1_dssim_loss_grad(image, target, P: int, W: int, H: int, lam: float, scratch, grad, loss,
+                          stream=None):
+    """L = (1 - lam) mean|x - y| + lam (1 - SSIM) into loss[0], dL/dx into grad."""
+    _check(load().ug_l1_dssim_loss_grad(_ptr(image), _ptr(target), int(P), int(W), int(H),
+                                        float(lam), _ptr(scratch), scratch.numel(), _ptr(grad),
+                                        _ptr(loss), _stream(stream)), "ug_l1_dssim_loss_grad")
 
 
 def ug_densify_config_default() -> ug_densify_config:

@@ -352,6 +352,22 @@ ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_
   return UG_OK;
 }
 
+size_t ug_l1_dssim_scratch_floats(int32_t P, int32_t W, int32_t H) {
+  if (P < 1 || W < 11 || H < 11) return 0;
+  return dssim_scratch_floats(P, W, H);
+}
+
+ug_status ug_l1_dssim_loss_grad(const float* image, const float* target, int32_t P, int32_t W,
+                                int32_t H, float lambda, float* scratch, size_t scratch_floats,
+                                float* grad, float* loss, ug_stream stream) {
+  if (!image || !target || !scratch || !grad || !loss) return UG_ERR_INVALID_ARGUMENT;
+  if (P < 1 || W < 11 || H < 11 || W > 16384 || H > 16384) return UG_ERR_INVALID_ARGUMENT;
+  if (!(lambda >= 0.f && lambda <= 1.f)) return UG_ERR_INVALID_ARGUMENT;
+  if (scratch_floats < dssim_scratch_floats(P, W, H)) return UG_ERR_WORKSPACE_TOO_SMALL;
+  return cuda_status(launch_l1_dssim(image, target, P, W, H, lambda, scratch, grad, loss,
+                                     reinterpret_cast<cudaStream_t>(stream)));
+}
+
 ug_status ug_densify_config_default(ug_densify_config* dc) {
   if (!dc) return UG_ERR_INVALID_ARGUMENT;
   *dc = ug_densify_config{};

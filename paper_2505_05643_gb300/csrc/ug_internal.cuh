@@ -235,6 +235,10 @@ cudaError_t launch_bin_sort(const ug_plan* plan, WsView v, cudaStream_t s);
 cudaError_t launch_render(const ug_plan* plan, WsView v, float* image, float* alpha,
                           cudaStream_t s);
 size_t ssim_scratch_floats(int32_t P, int32_t W, int32_t H);
+size_t dssim_scratch_floats(int32_t P, int32_t W, int32_t H);
+cudaError_t launch_l1_dssim(const float* image, const float* target, int32_t P, int32_t W,
+                            int32_t H, float lam, float* scratch, float* grad, float* loss,
+                            cudaStream_t s);
 cudaError_t launch_ssim(const float* image, const float* target, int32_t P, int32_t W, int32_t H,
                         float* scratch, float* ssim, float* psnr, cudaStream_t s);
 cudaError_t launch_render_scatter(const ug_plan* plan, WsView v, float* image, float* alpha,

@@ -54,3 +54,32 @@ def test_ssim_rejects_small_images():
     out = torch.empty(1, dtype=torch.float32, device="cuda")
     with pytest.raises(B.UgError):
         B.ug_ssim(x, x, 1, 10, 40, scratch, out)
+
+
+@pytest.mark.parametrize("lam", [0.2, 1.0, 0.0])
+def test_l1_dssim_loss_grad_parity(lam):
+    """The fused L1 + D-SSIM loss and its gradient against the FP64 oracle on
+    three ragged-sized planes (images with structure, targets perturbed)."""
+    from oracle import ssim as S
+    rng = np.random.default_rng(60)
+    P, W, H = 3, 70, 45
+    x = rng.uniform(0, 1, (P, H, W))
+    x = (x + np.roll(x, 1, 2) + np.roll(x, 1, 1)) / 3  # some spatial correlation
+    t = np.clip(x + rng.normal(0, 0.1, x.shape), 0, 1)
+    x, t = x.astype(np.float32).reshape(-1), t.astype(np.float32).reshape(-1)
+    L, g = S.l1_dssim_loss_grad(x, t, P, W, H, lam)
+    xt, tt = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    scratch = torch.empty(B.ug_l1_dssim_scratch_floats(P, W, H), device="cuda")
+    grad = torch.empty_like(xt)
+    loss = torch.empty(1, device="cuda")
+    B.ug_l1_dssim_loss_grad(xt, tt, P, W, H, lam, scratch, grad, loss)
+    torch.cuda.synchronize()
+    assert abs(loss.item() - L) <= 1e-5 * abs(L) + 1e-7
+    gg = grad.cpu().numpy().astype(np.float64)
+    err = np.abs(gg - g)
+    # FP32 window sums and SSIM terms: 1e-4 of the largest SSIM-part gradient
+    ssim_part = np.abs(g - (1 - lam) * np.sign(x.astype(np.float64) - t) / x.size).max()
+    assert np.all(err <= 1e-4 * ssim_part + 1e-9), (err.max(), ssim_part)
+    grad2 = torch.empty_like(grad)
+    B.ug_l1_dssim_loss_grad(xt, tt, P, W, H, lam, scratch, grad2, loss)
+    assert torch.equal(grad, grad2)  # deterministic

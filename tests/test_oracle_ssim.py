@@ -69,3 +69,49 @@ def test_psnr_closed_form():
     x = np.zeros((10, 10))
     y = np.full((10, 10), 0.1)
     assert abs(S.psnr(x, y) - 20.0) < 1e-12  # MSE 0.01 -> 20 dB
+
+
+def test_ssim_grad_central_differences():
+    """The analytic gradient of the mean SSIM against central differences of
+    ssim() itself on a 16 x 14 image (interior, edge and corner pixels)."""
+    from oracle import ssim as S
+    rng = np.random.default_rng(50)
+    x = rng.uniform(0, 1, (14, 16))
+    y = np.clip(x + rng.normal(0, 0.2, x.shape), 0, 1)
+    g = S.ssim_grad(x, y)
+    h = 1e-6
+    for (i, j) in [(0, 0), (0, 7), (5, 5), (13, 15), (7, 12), (10, 0)]:
+        xp, xm = x.copy(), x.copy()
+        xp[i, j] += h
+        xm[i, j] -= h
+        fd = (S.ssim(xp, y) - S.ssim(xm, y)) / (2 * h)
+        assert abs(fd - g[i, j]) <= 1e-7 + 1e-5 * abs(fd), (i, j, fd, g[i, j])
+
+
+def test_ssim_grad_vanishes_at_equality():
+    """SSIM is at its maximum 1 where the images are equal: zero gradient."""
+    from oracle import ssim as S
+    rng = np.random.default_rng(51)
+    x = rng.uniform(0, 1, (20, 23))
+    assert np.abs(S.ssim_grad(x, x)).max() < 1e-12
+
+
+def test_l1_dssim_loss_central_differences():
+    from oracle import ssim as S
+    rng = np.random.default_rng(52)
+    P, W, H = 2, 13, 12
+    x = rng.uniform(0, 1, P * H * W)
+    t = rng.uniform(0, 1, P * H * W)
+    L, g = S.l1_dssim_loss_grad(x, t, P, W, H, 0.2)
+    # L1 part alone at lam = 0: sign / n
+    L0, g0 = S.l1_dssim_loss_grad(x, t, P, W, H, 0.0)
+    np.testing.assert_allclose(g0, np.sign(x - t) / x.size)
+    assert abs(L0 - np.abs(x - t).mean()) < 1e-15
+    h = 1e-6
+    for k in [0, 5, 100, 200, 311]:
+        xp, xm = x.copy(), x.copy()
+        xp[k] += h
+        xm[k] -= h
+        fd = (S.l1_dssim_loss_grad(xp, t, P, W, H, 0.2)[0]
+              - S.l1_dssim_loss_grad(xm, t, P, W, H, 0.2)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-8 + 1e-5 * abs(fd), (k, fd, g[k])
