@@ -275,3 +275,40 @@ def test_mse_loss_kernel():
         loss2 = torch.empty_like(loss)
         B.ug_mse_loss_grad(it, tt, n, grad, loss2)
         assert loss2[0].item() == loss[0].item()  # deterministic
+
+
+def test_gaussian_sharded_render_and_gradient_on_one_gpu():
+    """The Gaussian decomposition with the library's own entry points: two
+    halves of the Gaussians rendered separately, their partial sums S_a =
+    alpha - a_bg and S_c = C alpha - a_bg c_bg added, the image formed from the
+    sums, and each half's gradient taken with the global image and alpha:
+    the same image and gradient as rendering all Gaussians at once (up to FP32
+    rounding and the order of the backward's atomic sums)."""
+    rng = np.random.default_rng(45)
+    g = synth.gaussians_scale_rot(rng, 3000, 0.03, 0.15)
+    pl = synth.planes_random(rng, [(64, 64), (48, 40)])
+    target = torch.from_numpy(rng.uniform(0, 1, pl["total_pixels"]).astype(np.float32)).cuda()
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
+    abg, cbg = cfg.alpha_bg, cfg.c_bg
+    r_full, p_full, image_f, alpha_f = gpu_render(g, pl, cfg)
+    halves = [np.arange(0, 3000, 2), np.arange(1, 3000, 2)]
+    parts = []
+    for h in halves:
+        gh = {k: v[..., h] for k, v in g.items()}
+        r, p, im, al = gpu_render(gh, pl, cfg)
+        parts.append((r, p, im, al))
+    S_a = sum(al - abg for _, _, _, al in parts)
+    S_c = sum(im * al - abg * cbg for _, _, im, al in parts)
+    alpha = S_a + abg
+    image = (S_c + abg * cbg) / alpha
+    np.testing.assert_allclose(alpha, alpha_f, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(image, image_f, rtol=1e-5, atol=1e-6)
+    im_t = torch.from_numpy(image.astype(np.float32)).cuda()
+    al_t = torch.from_numpy(alpha.astype(np.float32)).cuda()
+    gi = 2 * (im_t - target) / im_t.numel()
+    full = r_full.backward(p_full, im_t, al_t, gi).cpu().numpy()
+    sharded = np.zeros_like(full)
+    for h, (r, p, _, _) in zip(halves, parts):
+        sharded[:, h] = r.backward(p, im_t, al_t, gi).cpu().numpy()
+    scale = np.abs(full).max(axis=1, keepdims=True) + 1e-30
+    assert np.all(np.abs(sharded - full) <= 1e-5 * scale + 1e-4 * np.abs(full))
