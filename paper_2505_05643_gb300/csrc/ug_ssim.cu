@@ -11,7 +11,8 @@
 //      and the per-row sum of squared differences;
 //   2. vertical 11-tap sums at every valid position, the SSIM there, and the sum
 //      over each valid row (a fixed-order block reduction);
-//   3. per image, the rows' sums in order: mean SSIM and PSNR (deterministic).
+//   3. per image (one block each), the rows' sums in a fixed order: mean SSIM
+//      and PSNR (deterministic).
 #include <cmath>
 
 #include "ug_internal.cuh"
@@ -119,17 +120,36 @@ __global__ void k_ssim_cols(const float* __restrict__ maps, int W, int H,
   if (threadIdx.x == 0) row_ssim[(int64_t)p * Hv + iv] = (float)red[0];
 }
 
+// Fixed-order block sum of one value per thread (256 threads).
+__device__ __forceinline__ double block_sum256(double v) {
+  __shared__ double red[256];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Per image (one block each): mean SSIM over the valid positions and PSNR,
+// from the rows' sums in a fixed order.
 __global__ void k_ssim_final(const float* __restrict__ row_ssim, const float* __restrict__ row_sse,
                              int P, int W, int H, float* __restrict__ ssim,
                              float* __restrict__ psnr) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
+  const int p = blockIdx.x;
   const int Wv = W - (kWin - 1), Hv = H - (kWin - 1);
   double s = 0.0, e = 0.0;
-  for (int i = 0; i < Hv; ++i) s += (double)row_ssim[(int64_t)p * Hv + i];
-  for (int i = 0; i < H; ++i) e += (double)row_sse[(int64_t)p * H + i];
-  if (ssim) ssim[p] = (float)(s / ((double)Hv * (double)Wv));
-  if (psnr) psnr[p] = (float)(10.0 * log10((double)W * (double)H / e));
+  for (int i = threadIdx.x; i < Hv; i += blockDim.x) s += (double)row_ssim[(int64_t)p * Hv + i];
+  for (int i = threadIdx.x; i < H; i += blockDim.x) e += (double)row_sse[(int64_t)p * H + i];
+  s = block_sum256(s);
+  e = block_sum256(e);
+  if (threadIdx.x == 0) {
+    if (ssim) ssim[p] = (float)(s / ((double)Hv * (double)Wv));
+    if (psnr) psnr[p] = (float)(10.0 * log10((double)W * (double)H / e));
+  }
 }
 
 // ---------------------------------------------------------------- L1 + D-SSIM loss
@@ -257,20 +277,6 @@ __global__ void k_dssim_grad(const float* __restrict__ x, const float* __restric
   if (threadIdx.x == 0) row_l1[(int64_t)p * H + i] = (float)red[0];
 }
 
-// Fixed-order block sum of one value per thread (256 threads).
-__device__ __forceinline__ double block_sum256(double v) {
-  __shared__ double red[256];
-  red[threadIdx.x] = v;
-  __syncthreads();
-  for (int k = 128; k > 0; k >>= 1) {
-    if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-    __syncthreads();
-  }
-  const double r = red[0];
-  __syncthreads();
-  return r;
-}
-
 // Per plane (one block each): its mean SSIM and its sum of |x - y|.
 __global__ void k_dssim_plane(const float* __restrict__ row_ssim, const float* __restrict__ row_l1,
                               int W, int H, double* __restrict__ plane) {
@@ -357,7 +363,7 @@ cudaError_t launch_ssim(const float* image, const float* target, int32_t P, int3
   k_ssim_rows<<<dim3((unsigned)((Wv + 255) / 256), (unsigned)H, (unsigned)P), 256, 0, s>>>(
       image, target, W, H, maps, row_sse);
   k_ssim_cols<<<dim3((unsigned)Hv, (unsigned)P), 256, 0, s>>>(maps, W, H, row_ssim);
-  k_ssim_final<<<(unsigned)((P + 127) / 128), 128, 0, s>>>(row_ssim, row_sse, P, W, H, ssim, psnr);
+  k_ssim_final<<<(unsigned)P, 256, 0, s>>>(row_ssim, row_sse, P, W, H, ssim, psnr);
   return cudaGetLastError();
 }
 
