@@ -771,7 +771,8 @@ def run_recon(args):
     params = torch.from_numpy(R.pack_params(g, B.UG_COV_TRI)).to(dev)
     r = R.Renderer(n, synth.select_planes(tr, list(range(P))), cfg)
     targets = torch.empty(P * npx, device=dev)
-    step = T.TrainStep(r, params, targets, decay_steps=steps)
+    step = T.TrainStep(r, params, targets, decay_steps=steps, loss=args.recon_loss,
+                       plane_shape=(size, size))
     test_r = [R.Renderer(n, synth.select_planes(te, list(range(c0, min(c0 + 32, len(te["size"]))))), cfg)
               for c0 in range(0, len(te["size"]), 32)]
     scratch = torch.empty(B.ug_ssim_scratch_floats(32, size, size), device=dev)
@@ -805,7 +806,11 @@ def run_recon(args):
         step.g_struct = R.gaussians_struct(params, B.UG_COV_TRI)
         B.ug_bin_sort(r.plan, r.ws)
         B.ug_render(r.plan, r.ws, step.image, step.alpha)
-        B.ug_mse_loss_grad(step.image, targets, step.image.numel(), step.grad_image, step.loss)
+        if args.recon_loss == "mse":
+            B.ug_mse_loss_grad(step.image, targets, step.image.numel(), step.grad_image, step.loss)
+        else:
+            B.ug_l1_dssim_loss_grad(step.image, targets, *step.dssim_shape, T.DSSIM_LAMBDA,
+                                    step.dssim_scratch, step.grad_image, step.loss)
         B.ug_render_backward(r.plan, step.g_struct, r.d_planes, r.ws, step.image, step.alpha,
                              step.grad_image, step.grad_struct)
         B.ug_adam_step(params, step.grads, step.m, step.v, r.rows, n, step.lr_rows, step.step,
@@ -828,15 +833,26 @@ def run_recon(args):
                 return h["train_s"]
         return None
 
-    # novel-slice rendering: 512 random poses of 512x512, 32 per launch
+    # novel-slice rendering: 512 random poses of 512x512, 32 per launch (fewer
+    # when a launch would hold more than 2^31 tile instances)
     novel = synth.planes_random(np.random.default_rng(7), [(512, 512)] * 512)
-    nr = R.Renderer(n, synth.select_planes(novel, list(range(32))), cfg)
-    nr.forward(params)
-    chunks = [torch.from_numpy(synth.planes_to_struct(synth.select_planes(
-        novel, list(range(c0, c0 + 32)))).view(np.uint8).copy()).to(dev) for c0 in range(0, 512, 32)]
-    for c in chunks:  # sizing pass
-        nr.d_planes.copy_(c)
-        nr.forward(params)
+    per = 32
+    while True:
+        try:
+            nr = R.Renderer(n, synth.select_planes(novel, list(range(per))), cfg)
+            chunks = [torch.from_numpy(synth.planes_to_struct(synth.select_planes(
+                novel, list(range(c0, c0 + per)))).view(np.uint8).copy()).to(dev)
+                for c0 in range(0, 512, per)]
+            for c in chunks:  # sizing pass
+                nr.d_planes.copy_(c)
+                nr.forward(params)
+            break
+        except B.UgError as err:
+            if err.status != B.UG_ERR_CAPACITY or per == 1:
+                raise
+            per //= 2
+            nr = None
+            torch.cuda.empty_cache()
     img, al = nr.new_image(), nr.new_image()
     torch.cuda.synchronize()
     e0.record()
@@ -853,10 +869,11 @@ def run_recon(args):
         "metric": "reconstruction: training time to held-out SSIM, and novel-slice images/s",
         "value": 512 / novel_s, "unit": "images/s (512x512 novel slices)",
         "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "novel_planes_per_launch": per,
         "config": {"workload": f"recon: {n} Gaussians (paper init) fitted to a hidden "
                                f"{args.recon_hidden}-Gaussian volume (seed 3), {steps} steps of 32 "
                                f"poses from a pool of {pool} at 256x256, {len(te['size'])} "
-                               "held-out poses (seed 4)"},
+                               "held-out poses (seed 4)", "loss": args.recon_loss},
         "train_s": train_ms / 1e3, "ms_per_step": train_ms / steps,
         "time_to_ssim": {str(th): time_to(th) for th in (0.8, 0.9, 0.95, 0.99)},
         "final": history[-1], "history": history,
@@ -1098,6 +1115,8 @@ def main():
     ap.add_argument("--recon-hidden", type=int, default=1_000_000)
     ap.add_argument("--recon-steps", type=int, default=2000)
     ap.add_argument("--recon-eval", type=int, default=100)
+    ap.add_argument("--recon-loss", default="mse", choices=["mse", "l1_dssim"],
+                    help="training loss of the reconstruction run")
     ap.add_argument("--ablation", default=None, choices=["scatter"],
                     help="scatter: the forward as the paper's atomic scatter vs the tile gather")
     ap.add_argument("--no-autotune", action="store_true",

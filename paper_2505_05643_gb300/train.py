@@ -23,13 +23,29 @@ LR_MEAN_FINAL = 1.6e-6
 BETA1, BETA2, EPS = 0.9, 0.999, 1e-15
 
 
+DSSIM_LAMBDA = 0.2  # weight of the D-SSIM term in Kerbl et al.'s loss
+
+
 class TrainStep:
     def __init__(self, renderer: R.Renderer, params: torch.Tensor, targets: torch.Tensor,
-                 decay_steps: int = 30000, lr: float = LR_DEFAULT):
+                 decay_steps: int = 30000, lr: float = LR_DEFAULT, loss: str = "mse",
+                 plane_shape: tuple | None = None):
+        """loss: "mse" (the bench's loss) or "l1_dssim" ((1 - 0.2) L1 + 0.2 (1 - SSIM),
+        Kerbl et al.'s loss; needs every plane of the same plane_shape = (W, H))."""
         self.r = renderer
         self.params = params
         self.targets = targets
         dev = params.device
+        if loss not in ("mse", "l1_dssim"):
+            raise ValueError(f"unknown loss {loss}")
+        self.loss_kind = loss
+        if loss == "l1_dssim":
+            if plane_shape is None:
+                raise ValueError("the L1 + D-SSIM loss needs planes of one shape (W, H)")
+            W, H = plane_shape
+            self.dssim_shape = (renderer.plan.num_planes, int(W), int(H))
+            self.dssim_scratch = torch.empty(B.ug_l1_dssim_scratch_floats(*self.dssim_shape),
+                                             dtype=torch.float32, device=dev)
         self.grads = torch.zeros_like(params)
         self.m = torch.zeros_like(params)
         self.v = torch.zeros_like(params)
@@ -61,8 +77,13 @@ class TrainStep:
         B.ug_render(r.plan, r.ws, self.image, self.alpha, stream)
         if targets_ready is not None:
             (stream or torch.cuda.current_stream()).wait_event(targets_ready)
-        B.ug_mse_loss_grad(self.image, self.targets, self.image.numel(), self.grad_image,
-                           self.loss, stream)
+        if self.loss_kind == "mse":
+            B.ug_mse_loss_grad(self.image, self.targets, self.image.numel(), self.grad_image,
+                               self.loss, stream)
+        else:
+            P, W, H = self.dssim_shape
+            B.ug_l1_dssim_loss_grad(self.image, self.targets, P, W, H, DSSIM_LAMBDA,
+                                    self.dssim_scratch, self.grad_image, self.loss, stream)
         B.ug_render_backward(r.plan, self.g_struct, r.d_planes, r.ws, self.image, self.alpha,
                              self.grad_image, self.grad_struct, stream)
         B.ug_adam_step(self.params, self.grads, self.m, self.v, r.rows, r.n, self.lr_rows,
