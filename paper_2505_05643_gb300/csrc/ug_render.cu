@@ -33,7 +33,7 @@
 // Backward: one lane per work item. The lane walks the 8 x FH pixels of its
 // footprint and sums the seven per-record quantities of dL/dw over them in
 // registers, so no cross-lane reduction is needed; it then adds them to the
-// record's accumulators with seven atomics.
+// record's accumulators with two vector reductions.
 #include "ug_pipe.cuh"
 
 namespace ug {
@@ -360,6 +360,13 @@ struct BwdSmem {
   PlaneTable Tb;
 };
 
+// Vector reduction of four floats into 16-byte aligned global memory.
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(__cvta_generic_to_global(p)),
+               "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
 // One lane, one work item: sums over the footprint's 8 x FH pixels of
 //   acc0 = sum r w                (dL/dc),
 //   acc1 = sum g,   g = w dL/dw   (dL/dlw2 / ln 2),
@@ -430,14 +437,11 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, uint
   }
   const float s1 = s1p.x + s1p.y, u1 = u1p.x + u1p.y, u2 = u2p.x + u2p.y;
   const float a5 = a5p.x + a5p.y, a6 = a6p.x + a6p.y;
+  // the record's 8-float accumulator block (32-byte aligned): two vector
+  // reductions instead of seven scalar atomics
   float* dst = rec_grad + (size_t)rid * 8;
-  atomicAdd(dst + 0, s0.x + s0.y);
-  atomicAdd(dst + 1, s1);
-  atomicAdd(dst + 2, u1);
-  atomicAdd(dst + 3, u2);
-  atomicAdd(dst + 4, a4.x + a4.y);
-  atomicAdd(dst + 5, a5);
-  atomicAdd(dst + 6, a6);
+  red_add_v4(dst, s0.x + s0.y, s1, u1, u2);
+  red_add_v4(dst + 4, a4.x + a4.y, a5, a6, 0.f);
 }
 
 // Each consumer warp owns one footprint of the tile. It classifies the
