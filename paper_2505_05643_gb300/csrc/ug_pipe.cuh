@@ -94,6 +94,15 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
                : "memory");
 }
 
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Wait until at most one of this thread's committed copy groups is pending.
+__device__ __forceinline__ void cp_async_wait_prev() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -107,17 +116,18 @@ struct StageHdr {
   int64_t px_off;
 };
 
-// One stage: up to kBatch records of one tile; with RAW (the backward pass),
-// the first stage of a tile also carries the tile's pixel inputs (dL/dC,
-// alpha, C; pixels off the plane hold 0, 1, 0), and every stage the forward
-// pass's footprint tests of its instances (when they are valid).
+// One stage: up to kBatch records of one tile and one 32-bit word per record
+// of footprint tests (written by the producer's finishing step, or copied
+// from the forward pass's tests); with RAW (the backward pass), the first
+// stage of a tile also carries the tile's pixel inputs (dL/dC, alpha, C;
+// pixels off the plane hold 0, 1, 0).
 template <int TILE, bool RAW>
 struct RecStage {
   float4 a[kBatch];
   float4 b[kBatch];
   uint2 box[kBatch];
   uint32_t rid[kBatch];
-  uint32_t mask[RAW ? kBatch : 1];
+  uint32_t mask[kBatch];
   StageHdr h;
   float raw[RAW ? 3 : 1][RAW ? TILE * TILE : 1];
 };
@@ -153,7 +163,7 @@ __device__ __forceinline__ int find_plane(const int32_t* tile_off, int P, int t)
 
 // Fill the plane table and the barriers; the caller follows with __syncthreads.
 __device__ __forceinline__ void pipe_init(PlaneTable& T, PipeBars& bars, const WsView& v, int P,
-                                          uint32_t consumer_threads) {
+                                          uint32_t consumer_threads, uint32_t full_arrivals = 64) {
   for (int p = threadIdx.x; p < min(P, kSmemPlanes); p += blockDim.x) {
     const PlaneDev& d = v.planes[p];
     T.pl[p] = TilePlane{d.tile_off, d.tiles_x, d.w, d.h, d.px_off};
@@ -161,7 +171,9 @@ __device__ __forceinline__ void pipe_init(PlaneTable& T, PipeBars& bars, const W
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&bars.full[s], 64);  // per producer lane: one plain, one cp.async arrival
+      // per producer lane: one plain arrival, and one cp.async arrival unless
+      // the producer finishes the stage itself (then 32)
+      mbar_init(&bars.full[s], full_arrivals);
       mbar_init(&bars.empty[s], consumer_threads);
     }
   }
@@ -204,14 +216,22 @@ __device__ __forceinline__ TileCtx tile_ctx(const PlaneTable& T, const WsView& v
   return c;
 }
 
-template <int TILE, bool RAW, bool RID, bool EMPTY_TILES>
+// No finishing step: the stage is complete when its copies have landed.
+struct NoPrep {
+  static constexpr bool kDefer = false;
+  template <class S>
+  __device__ void operator()(S&, int) const {}
+};
+
+template <int TILE, bool RAW, bool RID, bool EMPTY_TILES, class Prep = NoPrep>
 __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
                                         const PlaneTable& T, const WsView& v,
                                         const uint32_t* __restrict__ vals, int which, int P,
                                         int total_tiles, const float* __restrict__ grad,
                                         const float* __restrict__ alpha,
                                         const float* __restrict__ image,
-                                        const uint32_t* __restrict__ inst_mask) {
+                                        const uint32_t* __restrict__ inst_mask,
+                                        Prep prep = Prep()) {
   const int lane = threadIdx.x & 31;
   constexpr int PER = kBatch / 32;
   // test hook: issue nothing, so that the consumers' bounded waits run out
@@ -322,11 +342,33 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
       hd.px_off = c.px_off;
       S.h = hd;
     }
-    mbar_arrive(&bars.full[s]);      // the plain shared-memory stores above
-    cp_async_arrive(&bars.full[s]);  // this lane's copies, once they have landed
+    if constexpr (Prep::kDefer) {
+      // finish the previous stage (its copies, issued by this lane for the
+      // records this lane finishes, have landed) and hand it over
+      cp_async_commit();
+      if (k > 0) {
+        cp_async_wait_prev();
+        __syncwarp();
+        const int sp = (int)((k - 1) % kStages);
+        prep(st[sp], lane);
+        mbar_arrive(&bars.full[sp]);
+      }
+    } else {
+      mbar_arrive(&bars.full[s]);      // the plain shared-memory stores above
+      cp_async_arrive(&bars.full[s]);  // this lane's copies, once they have landed
+    }
     ++k;
 #pragma unroll
     for (int q = 0; q < PER; ++q) rid[q] = rid_next[q];
+  }
+  if constexpr (Prep::kDefer) {
+    if (k > 0) {
+      cp_async_wait_all();
+      __syncwarp();
+      const int sp = (int)((k - 1) % kStages);
+      prep(st[sp], lane);
+      mbar_arrive(&bars.full[sp]);
+    }
   }
   const int s = (int)(k % kStages);
   if (k >= (uint32_t)kStages && !mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1u)) {
@@ -336,7 +378,7 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
   }
   if (lane == 0) st[s].h.tile = -1;
   mbar_arrive(&bars.full[s]);
-  cp_async_arrive(&bars.full[s]);
+  if constexpr (!Prep::kDefer) cp_async_arrive(&bars.full[s]);
   cp_async_wait_all();
 }
 

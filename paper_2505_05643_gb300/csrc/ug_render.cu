@@ -20,11 +20,12 @@
 //   w = 2^(lw2 - t1^2 - t2^2)      (= alpha exp(-q/2), Eq. mahalanobis-3d)
 // evaluated in packed FP32x2 arithmetic, two pixels per instruction.
 //
-// Forward: one consumer warp per 8x8 footprint, which classifies the stage's
-// records for its own footprint and is otherwise independent of the other
-// warps. It stores its test of every instance (byte f of a 32-bit word per
-// sorted instance: bit 0 live, bit 1 box covers the footprint), which the
-// backward pass with the same footprints reads instead of testing again. The warp is split into G lane groups that each cover the whole
+// Forward: the producer warp also tests every record of a stage against the
+// tile's 8x8 footprints once its copies have landed (byte f of a 32-bit word
+// per record: bit 0 live, bit 1 box covers the footprint) and stores the words
+// per sorted instance, which the backward pass with the same footprints reads
+// instead of testing again. One consumer warp per footprint, otherwise
+// independent of the other warps. The warp is split into G lane groups that each cover the whole
 // footprint (2G pixels of one column per lane) and take every G-th work item;
 // per pixel S_a += w, S_c += w c, the groups' sums are added at the end of the
 // tile, then C = (S_c + a_bg c_bg) / (S_a + a_bg) (Eq. alpha-combine, Eq.
@@ -208,20 +209,52 @@ __device__ __forceinline__ void fwd_build(FwdChunk& W, int lane, bool real, cons
   if (CUT) W.thr[lane] = b.w;
 }
 
+// The producer's finishing step of a forward stage: every record against
+// every 8x8 footprint of the tile (one lane per record, the record read once),
+// byte f of the record's word the test of footprint f, written to the stage
+// and, for the backward pass, per sorted instance.
+template <int TILE, int CUT>
+struct FwdPrep {
+  static constexpr bool kDefer = true;
+  uint32_t* inst_mask;
+  __device__ void operator()(RecStage<TILE, false>& S, int lane) const {
+    using T = Tiling<TILE, 8>;
+    const StageHdr h = S.h;
+#pragma unroll
+    for (int q = 0; q < kBatch / 32; ++q) {
+      const int r = lane + 32 * q;
+      if (r < h.cnt) {
+        const float4 a = S.a[r], c = S.b[r];
+        const uint2 bx = S.box[r];
+        uint32_t m = 0;
+#pragma unroll
+        for (int f = 0; f < T::NF; ++f) {
+          int fj0, fi0;
+          footprint_origin(f, T::FX, 8, h.tx, h.ty, TILE, fj0, fi0);
+          m |= classify<CUT>(a, c, bx, fj0, fi0, 8) << (8 * f);
+        }
+        S.mask[r] = m;
+        inst_mask[h.inst0 + r] = m;
+      }
+    }
+  }
+};
+
 template <int TILE, int G, int CUT>
 __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
     k_render_fwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles, float abg,
                  float cbg, float* __restrict__ image, float* __restrict__ alpha,
-                 uint8_t* __restrict__ inst_mask) {
+                 uint32_t* __restrict__ inst_mask) {
   using Sh = FwdShape<TILE, G>;
   constexpr int NW = Sh::NW, LG = Sh::LG, NP = Sh::NP;
   __shared__ FwdSmem<TILE, NW> S;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  pipe_init(S.T, S.bars, v, P, Sh::NCT);
+  pipe_init(S.T, S.bars, v, P, Sh::NCT, 32);
   if (__syncthreads_or(dev_failed(v.hdr))) return;  // the whole CTA leaves, or none of it
   if (warp == NW) {
     produce<TILE, false, false, true>(S.st, S.bars, S.T, v, vals, 0, P, total_tiles, nullptr,
-                                      nullptr, nullptr, nullptr);
+                                      nullptr, nullptr, nullptr,
+                                      FwdPrep<TILE, CUT>{inst_mask});
     return;
   }
   const int grp = lane / LG, gl = lane % LG;
@@ -257,11 +290,7 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
     int nf = 0, np = 0;
     for (int base = 0; base < h.cnt; base += 32) {
       const int r = base + lane;
-      const bool in = r < h.cnt;
-      const int rr = in ? r : h.cnt - 1;
-      uint32_t m = classify<CUT>(R.a[rr], R.b[rr], R.box[rr], fj0, fi0, 8);
-      m = in ? m : 0u;
-      if (in) inst_mask[(size_t)(h.inst0 + r) * 4 + warp] = (uint8_t)m;
+      const uint32_t m = r < h.cnt ? (R.mask[r] >> (8 * warp)) & 0xffu : 0u;
       const bool live = m & 1u, full = m & 2u;
       const uint32_t bf = __ballot_sync(0xffffffffu, live && full);
       const uint32_t bp = __ballot_sync(0xffffffffu, live && !full);
@@ -569,7 +598,7 @@ static cudaError_t fwd_launch(const ug_plan* plan, WsView v, const uint32_t* val
   const int g = min(grid, max(plan->total_tiles, 1));
   k_render_fwd<TILE, G, CUT><<<g, NT, 0, s>>>(v, vals, plan->num_planes, plan->total_tiles,
                                               plan->cfg.alpha_bg, plan->cfg.c_bg, image, alpha,
-                                              reinterpret_cast<uint8_t*>(inst_masks(plan, v)));
+                                              inst_masks(plan, v));
   return cudaGetLastError();
 }
 
