@@ -726,11 +726,16 @@ def run_train_compare(args):
 # ---------------------------------------------------------------- reconstruction
 def run_recon(args):
     """Reconstruction run: Gaussians in the paper's initialisation fitted to a
-    hidden synthetic volume with MSE and Adam (the paper's learning rates, the
-    means' rate decaying over the run), each step on 32 poses drawn from a pool
-    of training poses; SSIM and PSNR (the evaluator kernel) on held-out poses
-    every --recon-eval steps; the training time to reach SSIM thresholds; then
-    forward-only novel-slice rendering of 512x512 planes, images per second."""
+    hidden synthetic volume with MSE (or L1 + D-SSIM) and Adam (the paper's
+    learning rates, the means' rate decaying over the run), each step on 32
+    poses drawn from a pool of training poses; SSIM and PSNR (the evaluator
+    kernel) on the evaluation poses and on up to 128 training poses every
+    --recon-eval steps; the training time to reach SSIM thresholds; then
+    forward-only novel-slice rendering of 512x512 planes, images per second.
+    --recon-poses random: random training and held-out poses (256x256);
+    slices: the paper's ideal setting (Sec. 5.1), training on linearly spaced
+    axial slices and evaluating on linearly spaced axial, coronal and sagittal
+    slices (160 of each, 160x160)."""
     import torch
     from paper_2505_05643_gb300 import binding as B
     from paper_2505_05643_gb300 import render as R
@@ -739,8 +744,13 @@ def run_recon(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     n, steps, every = args.recon_n, args.recon_steps, args.recon_eval
-    g, hidden, tr, te = synth.workload_recon(n=n, hidden_n=args.recon_hidden)
-    P, size = 32, 256
+    slices = args.recon_poses == "slices"
+    size = args.recon_size or (160 if slices else 256)
+    pool_n, held_n = (160, 160) if slices else (320, 128)
+    g, hidden, tr, te = synth.workload_recon(n=n, hidden_n=args.recon_hidden, size=size,
+                                             train_pool=pool_n, held_out=held_n,
+                                             poses=args.recon_poses)
+    P = 32
     npx = size * size
     cfg = R.make_config(cov_param=B.UG_COV_TRI)
     cfg_h = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
@@ -756,7 +766,7 @@ def run_recon(args):
         return torch.cat(outs).view(-1, npx)
 
     t_train = render_targets(tr)   # (pool, npx)
-    t_test = render_targets(te)    # (held_out, npx)
+    t_test = render_targets(te)    # (evaluation poses, npx)
     pool = len(tr["size"])
     rng = np.random.default_rng(6)
     win_struct = {}
@@ -773,24 +783,41 @@ def run_recon(args):
     targets = torch.empty(P * npx, device=dev)
     step = T.TrainStep(r, params, targets, decay_steps=steps, loss=args.recon_loss,
                        plane_shape=(size, size))
-    test_r = [R.Renderer(n, synth.select_planes(te, list(range(c0, min(c0 + 32, len(te["size"]))))), cfg)
-              for c0 in range(0, len(te["size"]), 32)]
+
+    def eval_set(planes, tgt):
+        m = len(planes["size"])
+        return [(R.Renderer(n, synth.select_planes(planes, list(range(c0, min(c0 + 32, m)))), cfg),
+                 tgt[c0:min(c0 + 32, m)].reshape(-1)) for c0 in range(0, m, 32)]
+
+    test_set = eval_set(te, t_test)
+    train_idx = np.linspace(0, pool - 1, min(128, pool)).round().astype(np.int64)
+    train_set = eval_set(synth.select_planes(tr, list(train_idx)),
+                         t_train.index_select(0, torch.from_numpy(train_idx).to(dev)))
     scratch = torch.empty(B.ug_ssim_scratch_floats(32, size, size), device=dev)
     ss, ps = torch.empty(32, device=dev), torch.empty(32, device=dev)
 
-    def evaluate():
+    def evaluate(es):
         vals_s, vals_p = [], []
-        for k, tr_ in enumerate(test_r):
-            img, _ = tr_.forward(params)
-            m = len(tr_.host_planes)
-            B.ug_ssim(img, t_test[32 * k:32 * k + m].reshape(-1), m, size, size, scratch, ss[:m], ps[:m])
+        for rr, tt in es:
+            img, _ = rr.forward(params)
+            m = len(rr.host_planes)
+            B.ug_ssim(img, tt, m, size, size, scratch, ss[:m], ps[:m])
             vals_s.append(ss[:m].cpu().numpy().copy())
             vals_p.append(ps[:m].cpu().numpy().copy())
-        return float(np.concatenate(vals_s).mean()), float(np.concatenate(vals_p).mean())
+        return np.concatenate(vals_s), np.concatenate(vals_p)
 
-    history = []
-    s0, p0 = evaluate()
-    history.append({"step": 0, "train_s": 0.0, "ssim": s0, "psnr": p0})
+    def record(k, train_s, loss=None):
+        sv, pv = evaluate(test_set)
+        st, _ = evaluate(train_set)
+        h = {"step": k, "train_s": train_s, "ssim": float(sv.mean()), "psnr": float(pv.mean()),
+             "train_ssim": float(st.mean())}
+        if slices:  # axial, coronal, sagittal means
+            h["ssim_axes"] = [float(x.mean()) for x in np.split(sv, 3)]
+        if loss is not None:
+            h["loss"] = loss
+        return h
+
+    history = [record(0, 0.0)]
     train_ms = 0.0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     order = rng.permutation(pool)
@@ -821,15 +848,14 @@ def run_recon(args):
         stt = r.status()
         assert stt["status"] == B.UG_OK, stt
         if (k + 1) % every == 0 or k + 1 == steps:
-            sv, pv = evaluate()
-            history.append({"step": k + 1, "train_s": train_ms / 1e3, "ssim": sv, "psnr": pv,
-                            "loss": float(step.loss[0])})
-            print(f"[recon] step {k + 1} train {train_ms / 1e3:.2f} s ssim {sv:.4f} psnr {pv:.2f}",
-                  file=sys.stderr)
+            history.append(record(k + 1, train_ms / 1e3, float(step.loss[0])))
+            hh = history[-1]
+            print(f"[recon] step {k + 1} train {hh['train_s']:.2f} s ssim {hh['ssim']:.4f} "
+                  f"(train poses {hh['train_ssim']:.4f}) psnr {hh['psnr']:.2f}", file=sys.stderr)
 
-    def time_to(th):
+    def time_to(th, key="ssim"):
         for h in history:
-            if h["ssim"] >= th:
+            if h[key] >= th:
                 return h["train_s"]
         return None
 
@@ -872,10 +898,14 @@ def run_recon(args):
         "novel_planes_per_launch": per,
         "config": {"workload": f"recon: {n} Gaussians (paper init) fitted to a hidden "
                                f"{args.recon_hidden}-Gaussian volume (seed 3), {steps} steps of 32 "
-                               f"poses from a pool of {pool} at 256x256, {len(te['size'])} "
-                               "held-out poses (seed 4)", "loss": args.recon_loss},
+                               f"poses from a pool of {pool} at {size}x{size}, "
+                               + (f"evaluated on {held_n} linearly spaced axial, coronal and "
+                                  f"sagittal slices each (training: {pool} axial slices)"
+                                  if slices else f"{len(te['size'])} held-out poses (seed 4)"),
+                   "poses": args.recon_poses, "loss": args.recon_loss},
         "train_s": train_ms / 1e3, "ms_per_step": train_ms / steps,
         "time_to_ssim": {str(th): time_to(th) for th in (0.8, 0.9, 0.95, 0.99)},
+        "time_to_train_ssim": {str(th): time_to(th, "train_ssim") for th in (0.9, 0.95, 0.99)},
         "final": history[-1], "history": history,
     }
     print(json.dumps(line), flush=True)
@@ -1117,6 +1147,11 @@ def main():
     ap.add_argument("--recon-eval", type=int, default=100)
     ap.add_argument("--recon-loss", default="mse", choices=["mse", "l1_dssim"],
                     help="training loss of the reconstruction run")
+    ap.add_argument("--recon-poses", default="random", choices=["random", "slices"],
+                    help="random: random training and held-out poses; slices: linearly spaced "
+                         "axial training slices, axial/coronal/sagittal evaluation slices")
+    ap.add_argument("--recon-size", type=int, default=None,
+                    help="plane edge in pixels (default 256 random, 160 slices)")
     ap.add_argument("--ablation", default=None, choices=["scatter"],
                     help="scatter: the forward as the paper's atomic scatter vs the tile gather")
     ap.add_argument("--no-autotune", action="store_true",

@@ -214,6 +214,30 @@ def planes_sweep_pool(rng: np.random.Generator, pool: int = 160, size=(256, 256)
     return _pack_planes(np.array(origins), np.array(us), np.array(vs), [size] * pool, extent)
 
 
+def planes_slices(count: int, size: int, axis: int = 2, extent: float = 2.0) -> dict:
+    """count linearly spaced slices through the cube [-1, 1]^3 normal to the
+    given axis (2 axial, 1 coronal, 0 sagittal), at the centres of count equal
+    layers, each spanning the cube's cross-section with size x size pixels (a
+    stand-in for the paper's evaluation on linearly spaced axial, coronal and
+    sagittal cross-sections of a 160^3 volume, Sec. 5.1)."""
+    e = np.eye(3)
+    u, v = {2: (e[0], e[1]), 1: (e[0], e[2]), 0: (e[1], e[2])}[axis]
+    t = -1.0 + (np.arange(count) + 0.5) * 2.0 / count
+    origin = np.zeros((count, 3))
+    origin[:, axis] = t
+    return _pack_planes(origin, np.tile(u, (count, 1)), np.tile(v, (count, 1)),
+                        [(size, size)] * count, extent)
+
+
+def concat_planes(*sets) -> dict:
+    """Several plane sets as one (re-packed with fresh pixel offsets)."""
+    return _pack_planes(np.concatenate([s["origin"] for s in sets]),
+                        np.concatenate([s["u"] for s in sets]),
+                        np.concatenate([s["v"] for s in sets]),
+                        [tuple(x) for s in sets for x in s["size"]], extent=1.0) | {
+                            "pitch": np.concatenate([s["pitch"] for s in sets])}
+
+
 def select_planes(planes: dict, idx) -> dict:
     """Sub-batch of planes (re-packed with fresh pixel offsets)."""
     idx = np.asarray(idx)
@@ -290,14 +314,24 @@ def workload_train_200k(seed: int = 0, n: int = 200_000, hidden_n: int = 100_000
 
 
 def workload_recon(seed: int = 0, n: int = 3_000_000, hidden_n: int = 1_000_000,
-                   train_pool: int = 320, held_out: int = 128, size: int = 256):
+                   train_pool: int = 320, held_out: int = 128, size: int = 256,
+                   poses: str = "random"):
     """Reconstruction workload: n Gaussians in the paper's initialisation, a
     hidden target volume of hidden_n Gaussians drawn with seed 3 from the
-    fwd_2k distributions, a pool of train_pool random training poses (seed 5)
-    and held_out random evaluation poses (seed 4), all size x size pixels.
-    Returns (gaussians, hidden gaussians, training poses, held-out poses)."""
+    fwd_2k distributions, and size x size poses.
+
+    poses "random": a pool of train_pool random training poses (seed 5) and
+    held_out random evaluation poses (seed 4). poses "slices" (the paper's
+    ideal setting, Sec. 5.1): train_pool linearly spaced axial slices for
+    training, and held_out linearly spaced slices along each of the three axes
+    (axial, coronal, sagittal) for evaluation.
+    Returns (gaussians, hidden gaussians, training poses, evaluation poses)."""
     g = gaussians_paper_init(np.random.default_rng(seed), n)
     hidden = gaussians_scale_rot(np.random.default_rng(3), hidden_n)
+    if poses == "slices":
+        train = planes_slices(train_pool, size, axis=2)
+        test = concat_planes(*(planes_slices(held_out, size, axis=a) for a in (2, 1, 0)))
+        return g, hidden, train, test
     train = planes_random(np.random.default_rng(5), [(size, size)] * train_pool)
     test = planes_random(np.random.default_rng(4), [(size, size)] * held_out)
     return g, hidden, train, test

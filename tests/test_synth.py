@@ -48,3 +48,21 @@ def test_workloads_deterministic():
     g = synth.gaussians_paper_init(np.random.default_rng(0), 100)
     assert g["tri"].min() >= 4.0 and g["tri"].max() < 5.0
     assert np.all(g["intensity"] == 0.5)
+
+
+def test_slice_sets_cover_the_cube():
+    """Linearly spaced slices: one per equal layer along the axis, each spanning
+    the cube's cross-section; the three orientations are mutually orthogonal."""
+    ax = synth.planes_slices(160, 160, axis=2)
+    z = ax["origin"][:, 2].astype(np.float64)
+    np.testing.assert_allclose(np.diff(z), 2.0 / 160, rtol=1e-5)
+    assert abs(z[0] + 1 - 1 / 160) < 1e-6 and abs(z[-1] - 1 + 1 / 160) < 1e-6
+    np.testing.assert_allclose(ax["pitch"], 2.0 / 160)
+    three = synth.concat_planes(*(synth.planes_slices(4, 8, axis=a) for a in (2, 1, 0)))
+    n = np.cross(three["u"].astype(np.float64), three["v"].astype(np.float64))
+    np.testing.assert_allclose(np.abs(n[[0, 4, 8]]), np.eye(3)[[2, 1, 0]])
+    assert list(three["offset"]) == [64 * k for k in range(12)]
+    np.testing.assert_allclose(three["pitch"], 0.25)
+    g, _, tr, te = synth.workload_recon(n=10, hidden_n=10, train_pool=16, held_out=8, size=32,
+                                        poses="slices")
+    assert len(tr["size"]) == 16 and len(te["size"]) == 24
