@@ -405,12 +405,17 @@ def run_ours(args):
         raise RuntimeError("capacity overflow in the phase-timing steps")
 
     # ---- e2e: the public API with host buffers; the step's inputs (targets and
-    # plane poses) copied from pinned host memory and the loss read back each step
+    # plane poses) copied from pinned host memory, and its loss and status read
+    # back into pinned host memory, every step. The host runs up to two steps
+    # ahead of the device (double-buffered read-back): it reads step k's results
+    # after issuing step k + 1, as a training loop that logs its loss would.
     h_targets = torch.from_numpy(target).pin_memory()
     h_planes = torch.from_numpy(r.host_planes.view(np.uint8).copy()).pin_memory()
-    h_loss = torch.zeros(1, dtype=torch.float32).pin_memory()
+    h_loss = torch.zeros((2, 1), dtype=torch.float32).pin_memory()
+    h_st = torch.zeros((2, 64), dtype=torch.uint8).pin_memory()
     copy_s = torch.cuda.Stream()
     targets_in = torch.cuda.Event()
+    done = [torch.cuda.Event(), torch.cuda.Event()]
     for attempt in range(3):
         restore()
         with torch.cuda.stream(s):
@@ -418,23 +423,37 @@ def run_ours(args):
                 reset_on(s)
                 step.enqueue(s)
         s.synchronize()
-        e2e_st = []
+        e2e_st, e2e_loss = [], []
+
+        def collect(b):
+            done[b].synchronize()
+            e2e_st.append(B.ug_ws_status.from_buffer_copy(h_st[b].numpy().tobytes()))
+            e2e_loss.append(float(h_loss[b, 0]))
+
         t0 = time.perf_counter()
         with torch.cuda.stream(s):
             for k in range(args.steps):
-                # the targets travel on their own stream while the step renders;
-                # the loss waits for them
+                b = k % 2
+                if k >= 2:
+                    collect(b)  # step k - 2's results; its buffers are then free
+                # the targets travel on their own stream while the step renders
+                # (after the previous step, which reads them, has ended); the
+                # loss waits for them
                 with torch.cuda.stream(copy_s):
+                    if k >= 1:
+                        copy_s.wait_event(done[1 - b])
                     step.targets.copy_(h_targets, non_blocking=True)
                     targets_in.record(copy_s)
                 r.d_planes.copy_(h_planes, non_blocking=True)
                 reset_on(s)
                 step.enqueue(s, targets_ready=targets_in)
-                h_loss.copy_(step.loss[:1], non_blocking=True)
-                B.ug_read_status(r.plan, r.ws, st_dev, s)
-                s.synchronize()
-                e2e_st.append(B.ug_ws_status.from_buffer_copy(st_dev.cpu().numpy().tobytes()))
+                h_loss[b].copy_(step.loss[:1], non_blocking=True)
+                B.ug_read_status(r.plan, r.ws, h_st[b], s)
+                done[b].record(s)
+            for k in range(max(args.steps - 2, 0), args.steps):
+                collect(k % 2)
         e2e_s = (time.perf_counter() - t0) / args.steps
+        assert all(np.isfinite(e2e_loss))
         if all([note(x) for x in e2e_st]):
             break
         grow()

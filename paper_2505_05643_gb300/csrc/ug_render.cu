@@ -396,20 +396,22 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
                : "memory");
 }
 
-// One lane, one work item: sums over the footprint's 8 x FH pixels of
+// One lane, one work item (or, with TAIL, nrows of its FH rows from row y0,
+// in a rolled loop): sums over the footprint's 8 x FH (8 x nrows) pixels of
 //   acc0 = sum r w                (dL/dc),
 //   acc1 = sum g,   g = w dL/dw   (dL/dlw2 / ln 2),
 //   acc2 = sum g t1, acc3 = sum g t2,
 //   acc4 = sum g t1 dx, acc5 = sum g t1 dy, acc6 = sum g t2 dy,
 // with r = G / alpha and dL/dw = r (c - C) at each pixel (Eq. us-render
-// differentiated, box fixed); the chain kernel turns them into the gradients
-// of x*, r11, r12, r22. Pixels outside the box or the ellipsoid (CUT) get
-// w = 0 through an exponent of -inf, never a NaN: every factor that
-// multiplies w stays finite.
-template <int FH, int CUT>
+// differentiated, box fixed), added to the record's accumulators; the chain
+// kernel turns them into the gradients of x*, r11, r12, r22. Pixels outside
+// the box or the ellipsoid (CUT) get w = 0 through an exponent of -inf, never
+// a NaN: every factor that multiplies w stays finite.
+template <int FH, int CUT, bool TAIL = false>
 __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, uint32_t cl,
                                          uint32_t rid, const float4* __restrict__ pix, int fj0,
-                                         int fi0, float* __restrict__ rec_grad) {
+                                         int fi0, float* __restrict__ rec_grad, int y0 = 0,
+                                         int nrows = FH) {
   const float2 r11 = make_float2(a.z, a.z), r12 = make_float2(a.w, a.w);
   const float2 r22 = make_float2(bb.x, bb.x), lw = make_float2(bb.y, bb.y);
   const float2 cc = make_float2(bb.z, bb.z), nx = make_float2(-a.x, -a.x);
@@ -428,10 +430,11 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, uint
   float2 s0 = make_float2(0.f, 0.f), a4 = make_float2(0.f, 0.f);
   float2 s1p = make_float2(0.f, 0.f), u1p = make_float2(0.f, 0.f), u2p = make_float2(0.f, 0.f);
   float2 a5p = make_float2(0.f, 0.f), a6p = make_float2(0.f, 0.f);
-  const float fy0 = (float)fi0 + 0.5f;  // row centres fy0 + y are exact
-#pragma unroll
-  for (int y = 0; y < FH; ++y) {
-    const float dyv = (fy0 + (float)y) - a.y;
+  const float fy0 = (float)(fi0 + y0) + 0.5f;  // row centres fy0 + j are exact
+  const float4* __restrict__ pxr = pix + 4 * y0;
+  auto row = [&](int j) {
+    const int y = y0 + j;
+    const float dyv = (fy0 + (float)j) - a.y;
     const float2 dy = make_float2(dyv, dyv);
     const float2 r12dy = __fmul2_rn(r12, dy);
     const float2 t2 = __fmul2_rn(r22, dy);
@@ -449,7 +452,7 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, uint
         if (!(q.y <= bb.w)) e2.y = -INFINITY;
       }
       const float2 w = make_float2(fast_exp2(e2.x), fast_exp2(e2.y));
-      const float4 px = pix[4 * y + cp];
+      const float4 px = pxr[4 * j + cp];
       const float2 rr = make_float2(px.x, px.y);
       const float2 g = __fmul2_rn(__ffma2_rn(rr, cc, make_float2(px.z, px.w)), w);  // w dL/dw
       s0 = __ffma2_rn(rr, w, s0);
@@ -463,6 +466,13 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, uint
     a5p = __ffma2_rn(dy, u1r, a5p);
     u2p = __ffma2_rn(t2, s1r, u2p);
     a6p = __ffma2_rn(__fmul2_rn(t2, dy), s1r, a6p);
+  };
+  if (TAIL) {
+#pragma unroll 1
+    for (int j = 0; j < nrows; ++j) row(j);
+  } else {
+#pragma unroll
+    for (int j = 0; j < FH; ++j) row(j);
   }
   const float s1 = s1p.x + s1p.y, u1 = u1p.x + u1p.y, u2 = u2p.x + u2p.y;
   const float a5 = a5p.x + a5p.y, a6 = a6p.x + a6p.y;
@@ -546,13 +556,25 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
       count += __popc(bl);
       evaluated += __popc(bl);
       __syncwarp();
-      // full rounds; at the end of the tile also the rest
+      // full rounds; at the end of the tile also the rest, whose items are
+      // split by rows over 2 or 4 lanes each when they fill at most half or a
+      // quarter of the warp (each lane adds its rows' sums)
       const bool tile_end = (h.flags & kLast) && base + 32 >= h.cnt;
       while (count >= 32 || (tile_end && count > 0)) {
         const uint32_t n = min(count, 32u);
-        if (lane < (int)n) {
-          const uint32_t e = (head + lane) % kBwdQueue;
-          bwd_item<FH, CUT>(Q.a[e], Q.b[e], Q.clip[e], Q.rid[e], pix, fj0, fi0, v.rec_grad);
+        if (n > 16) {
+          if (lane < (int)n) {
+            const uint32_t e = (head + lane) % kBwdQueue;
+            bwd_item<FH, CUT>(Q.a[e], Q.b[e], Q.clip[e], Q.rid[e], pix, fj0, fi0, v.rec_grad);
+          }
+        } else {
+          const int lg = n > 8 ? 1 : 2;  // log2 of the lanes per item
+          const int it = lane & (31 >> lg), part = lane >> (5 - lg), rows = FH >> lg;
+          if (it < (int)n) {
+            const uint32_t e = (head + it) % kBwdQueue;
+            bwd_item<FH, CUT, true>(Q.a[e], Q.b[e], Q.clip[e], Q.rid[e], pix, fj0, fi0,
+                                    v.rec_grad, part * rows, rows);
+          }
         }
         head = (head + n) % kBwdQueue;
         count -= n;
