@@ -367,15 +367,13 @@ struct BwdShape {
   static constexpr int NT = NCT + 32;  // plus the producer warp
 };
 
-constexpr int kBwdQueue = 64;  // work items a consumer warp holds (two rounds)
+constexpr int kBwdQueue = 256;  // > the items a warp can hold: 31 left over + one stage's 128
 
-// A consumer warp's queue of work items (copies of the record, so that the
-// stage can be released before the items are processed), in a ring.
+// A consumer warp's queue of work items, in a ring: (stage << 7) | record
+// index. The items are read from the stages themselves, so a stage is
+// released only once the warp has processed all of its items.
 struct BwdQueue {
-  float4 a[kBwdQueue];
-  float4 b[kBwdQueue];
-  uint32_t clip[kBwdQueue];
-  uint32_t rid[kBwdQueue];
+  uint16_t idx[kBwdQueue];
 };
 
 template <int TILE, int FH>
@@ -483,10 +481,14 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, uint
   red_add_v4(dst + 4, a4.x + a4.y, a5, a6, 0.f);
 }
 
-// Each consumer warp owns one footprint of the tile. It classifies the
-// stage's records for its footprint, copies the live ones into its queue and
-// processes the queue 32 items at a time, one item per lane; the last items
-// of a tile are processed when the tile ends. The warps share no barrier.
+// Each consumer warp owns one footprint of the tile. It queues the indices of
+// the stage's records that are live for its footprint and processes the queue
+// 32 items at a time, one item per lane, reading each item's record from its
+// stage; the last items of a tile are processed when the tile ends. A stage is
+// released when all of its items are processed, and at the latest before the
+// wait that reuses its slot (the items still queued are processed first, so
+// the producer never waits for a stage that a consumer holds). The warps share
+// no barrier.
 template <int TILE, int FH, int CUT>
 __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
     k_render_bwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles,
@@ -495,6 +497,7 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
   using Sh = BwdShape<TILE, FH>;
   using T = Tiling<TILE, FH>;
   constexpr int NW = Sh::NW;
+  static_assert(kStages <= 3 && kBatch == 128, "queue entries hold a stage (2 bits) and a record (7)");
   extern __shared__ __align__(16) unsigned char bwd_smem[];
   BwdSmem<TILE, FH>& S = *reinterpret_cast<BwdSmem<TILE, FH>*>(bwd_smem);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -508,13 +511,53 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
     return;
   }
   const uint32_t lt = lanemask_lt();
-  BwdQueue& Q = S.q[warp];
+  uint16_t* Q = S.q[warp].idx;
   const float4* pix = S.pix[warp];
   unsigned long long evaluated = 0;
   int fj0 = 0, fi0 = 0;
-  uint32_t head = 0, count = 0;  // queue ring position and fill
+  uint32_t qhead = 0, qtail = 0;  // items processed / queued so far
+  uint32_t qe0 = 0, qe1 = 0, qe2 = 0;  // qtail after each held stage's items, by slot
+  auto qend = [&](uint32_t slot) { return slot == 0 ? qe0 : slot == 1 ? qe1 : qe2; };
+  uint32_t krel = 0;                    // the stages before krel are released
+  // item i of the queue (0 = its oldest) from row y0: its record read from its stage
+  auto item = [&](uint32_t i, int y0, int rows, bool part) {
+    const uint32_t e = Q[(qhead + i) % kBwdQueue];
+    const RecStage<TILE, true>& Rs = S.st[e >> 7];
+    const int r = (int)(e & 127u);
+    const uint32_t cl = clip_box(Rs.box[r], fj0, fi0, FH);
+    if (part)
+      bwd_item<FH, CUT, true>(Rs.a[r], Rs.b[r], cl, Rs.rid[r], pix, fj0, fi0, v.rec_grad, y0, rows);
+    else
+      bwd_item<FH, CUT>(Rs.a[r], Rs.b[r], cl, Rs.rid[r], pix, fj0, fi0, v.rec_grad);
+  };
+  // one round: the oldest min(queued, 32) items; fewer than 17 are split by
+  // rows over 2 or 4 lanes each (each lane adds its rows' sums)
+  auto round = [&]() {
+    const uint32_t n = min(qtail - qhead, 32u);
+    if (n > 16) {
+      if (lane < (int)n) item(lane, 0, FH, false);
+    } else {
+      const int lg = n > 8 ? 1 : 2;  // log2 of the lanes per item
+      const int it = lane & (31 >> lg), part = lane >> (5 - lg), rows = FH >> lg;
+      if (it < (int)n) item(it, part * rows, rows, true);
+    }
+    qhead += n;
+    __syncwarp();  // every lane has read its records
+  };
+  // release the held stages up to `last` whose items are all processed, in order
+  auto release = [&](uint32_t last) {
+    while (krel <= last && qend(krel % kStages) <= qhead) {
+      mbar_arrive(&S.bars.empty[krel % kStages]);
+      ++krel;
+    }
+  };
   for (uint32_t k = 0;; ++k) {
     const int s = (int)(k % kStages);
+    if (k >= (uint32_t)kStages && krel + kStages <= k) {
+      // this wait reuses the slot of stage k - kStages: process its items
+      while (qhead < qend(s)) round();
+      release(k - 1);
+    }
     if (!mbar_wait(&S.bars.full[s], (k / kStages) & 1u)) {
       dev_fail(v.hdr, UG_ERR_TIMEOUT, 2);
       break;
@@ -540,48 +583,33 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
       }
       __syncwarp();
     }
-    for (int base = 0; base < h.cnt; base += 32) {
-      const int r = base + lane;
-      uint32_t m = 0;
+    // queue the stage's live records for this footprint, in record order
+    uint32_t m[kBatch / 32];
+#pragma unroll
+    for (int q = 0; q < kBatch / 32; ++q) {
+      const int r = 32 * q + lane;
+      m[q] = 0;
       if (r < h.cnt)
-        m = use_masks ? R.mask[r] >> (8 * warp) : classify<CUT>(R.a[r], R.b[r], R.box[r], fj0, fi0, FH);
-      const uint32_t bl = __ballot_sync(0xffffffffu, m & 1u);
-      if (m & 1u) {
-        const uint32_t slot = (head + count + __popc(bl & lt)) % kBwdQueue;
-        Q.a[slot] = R.a[r];
-        Q.b[slot] = R.b[r];
-        Q.clip[slot] = clip_box(R.box[r], fj0, fi0, FH);
-        Q.rid[slot] = R.rid[r];
-      }
-      count += __popc(bl);
-      evaluated += __popc(bl);
-      __syncwarp();
-      // full rounds; at the end of the tile also the rest, whose items are
-      // split by rows over 2 or 4 lanes each when they fill at most half or a
-      // quarter of the warp (each lane adds its rows' sums)
-      const bool tile_end = (h.flags & kLast) && base + 32 >= h.cnt;
-      while (count >= 32 || (tile_end && count > 0)) {
-        const uint32_t n = min(count, 32u);
-        if (n > 16) {
-          if (lane < (int)n) {
-            const uint32_t e = (head + lane) % kBwdQueue;
-            bwd_item<FH, CUT>(Q.a[e], Q.b[e], Q.clip[e], Q.rid[e], pix, fj0, fi0, v.rec_grad);
-          }
-        } else {
-          const int lg = n > 8 ? 1 : 2;  // log2 of the lanes per item
-          const int it = lane & (31 >> lg), part = lane >> (5 - lg), rows = FH >> lg;
-          if (it < (int)n) {
-            const uint32_t e = (head + it) % kBwdQueue;
-            bwd_item<FH, CUT, true>(Q.a[e], Q.b[e], Q.clip[e], Q.rid[e], pix, fj0, fi0,
-                                    v.rec_grad, part * rows, rows);
-          }
-        }
-        head = (head + n) % kBwdQueue;
-        count -= n;
-        __syncwarp();
-      }
+        m[q] = use_masks ? R.mask[r] >> (8 * warp)
+                         : classify<CUT>(R.a[r], R.b[r], R.box[r], fj0, fi0, FH);
     }
-    mbar_arrive(&S.bars.empty[s]);  // the stage is no longer read by this thread
+    const uint32_t q0 = qtail;
+#pragma unroll
+    for (int q = 0; q < kBatch / 32; ++q) {
+      const uint32_t bl = __ballot_sync(0xffffffffu, m[q] & 1u);
+      if (m[q] & 1u)
+        Q[(qtail + __popc(bl & lt)) % kBwdQueue] = (uint16_t)((s << 7) | (32 * q + lane));
+      qtail += __popc(bl);
+    }
+    evaluated += qtail - q0;
+    if (s == 0) qe0 = qtail;
+    else if (s == 1) qe1 = qtail;
+    else qe2 = qtail;
+    __syncwarp();
+    // full rounds; at the end of the tile also the rest
+    const bool tile_end = h.flags & kLast;
+    while (qtail - qhead >= 32u || (tile_end && qtail > qhead)) round();
+    release(k);
   }
   if (lane == 0 && evaluated)
     atomicAdd(reinterpret_cast<unsigned long long*>(&v.hdr->st.evaluated_pairs_bwd),
