@@ -287,11 +287,18 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
       for (int p = 0; p < NP; ++p) sa[p] = sc[p] = make_float2(0.f, 0.f);
     }
     // this warp's lists: full-box items from the front, partial from the back
+    // (the stage's tests read first, all four groups of 32 at once)
+    uint32_t mq[kBatch / 32];
+#pragma unroll
+    for (int q = 0; q < kBatch / 32; ++q) {
+      const int r = 32 * q + lane;
+      mq[q] = r < h.cnt ? R.mask[r] >> (8 * warp) : 0u;
+    }
     int nf = 0, np = 0;
-    for (int base = 0; base < h.cnt; base += 32) {
-      const int r = base + lane;
-      const uint32_t m = r < h.cnt ? (R.mask[r] >> (8 * warp)) & 0xffu : 0u;
-      const bool live = m & 1u, full = m & 2u;
+#pragma unroll
+    for (int q = 0; q < kBatch / 32; ++q) {
+      const int r = 32 * q + lane;
+      const bool live = mq[q] & 1u, full = mq[q] & 2u;
       const uint32_t bf = __ballot_sync(0xffffffffu, live && full);
       const uint32_t bp = __ballot_sync(0xffffffffu, live && !full);
       if (live && full) S.list[warp][nf + __popc(bf & lt)] = (uint16_t)r;
