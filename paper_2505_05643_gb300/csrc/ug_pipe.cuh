@@ -132,9 +132,11 @@ struct RecStage {
   float raw[RAW ? 3 : 1][RAW ? TILE * TILE : 1];
 };
 
+template <int NS = kStages>
 struct PipeBars {
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
+  static constexpr int kN = NS;  // stages in the ring
+  uint64_t full[NS];
+  uint64_t empty[NS];
 };
 
 // Planes whose tile data a CTA keeps in shared memory (more planes: looked up
@@ -162,7 +164,8 @@ __device__ __forceinline__ int find_plane(const int32_t* tile_off, int P, int t)
 }
 
 // Fill the plane table and the barriers; the caller follows with __syncthreads.
-__device__ __forceinline__ void pipe_init(PlaneTable& T, PipeBars& bars, const WsView& v, int P,
+template <class Bars>
+__device__ __forceinline__ void pipe_init(PlaneTable& T, Bars& bars, const WsView& v, int P,
                                           uint32_t consumer_threads, uint32_t full_arrivals = 64) {
   for (int p = threadIdx.x; p < min(P, kSmemPlanes); p += blockDim.x) {
     const PlaneDev& d = v.planes[p];
@@ -170,7 +173,7 @@ __device__ __forceinline__ void pipe_init(PlaneTable& T, PipeBars& bars, const W
     T.tile_off[p] = d.tile_off;
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < Bars::kN; ++s) {
       // per producer lane: one plain arrival, and one cp.async arrival unless
       // the producer finishes the stage itself (then 32)
       mbar_init(&bars.full[s], full_arrivals);
@@ -179,11 +182,11 @@ __device__ __forceinline__ void pipe_init(PlaneTable& T, PipeBars& bars, const W
   }
 }
 
-// The producer warp. Stage k of the stream goes to slot k % kStages; from
-// k = kStages on, the slot is reused once its consumers have released stage
-// k - kStages. The record ids are read into registers, the records themselves
+// The producer warp. Stage k of the stream goes to slot k % NS (NS stages in
+// the ring); from k = NS on, the slot is reused once its consumers have
+// released stage k - NS. The record ids are read into registers, the records themselves
 // (and the backward's pixel inputs) are copied with cp.async, whose completion
-// arrives on the stage's full barrier, so up to kStages batches of gathers
+// arrives on the stage's full barrier, so up to NS batches of gathers
 // are in flight. RID: the stage also keeps the record ids. inst_mask (RAW
 // only, may be null): per sorted instance, copied into the stage. EMPTY_TILES: tiles
 // without records still get one stage (the forward pass writes their
@@ -223,8 +226,8 @@ struct NoPrep {
   __device__ void operator()(S&, int) const {}
 };
 
-template <int TILE, bool RAW, bool RID, bool EMPTY_TILES, class Prep = NoPrep>
-__device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
+template <int TILE, bool RAW, bool RID, bool EMPTY_TILES, class Prep = NoPrep, int NS = kStages>
+__device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars<NS>& bars,
                                         const PlaneTable& T, const WsView& v,
                                         const uint32_t* __restrict__ vals, int which, int P,
                                         int total_tiles, const float* __restrict__ grad,
@@ -292,8 +295,8 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
       const uint32_t r = b + lane + 32 * q;
       rid_next[q] = (tA < total && r < rA.y) ? __ldg(vals + r) : 0u;
     }
-    const int s = (int)(k % kStages);
-    if (k >= (uint32_t)kStages && !mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1u)) {
+    const int s = (int)(k % NS);
+    if (k >= (uint32_t)NS && !mbar_wait(&bars.empty[s], ((k / NS) - 1) & 1u)) {
       dev_fail(v.hdr, UG_ERR_TIMEOUT, 100 + which);
       cp_async_wait_all();
       return;
@@ -349,7 +352,7 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
       if (k > 0) {
         cp_async_wait_prev();
         __syncwarp();
-        const int sp = (int)((k - 1) % kStages);
+        const int sp = (int)((k - 1) % NS);
         prep(st[sp], lane);
         mbar_arrive(&bars.full[sp]);
       }
@@ -365,13 +368,13 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars& bars,
     if (k > 0) {
       cp_async_wait_all();
       __syncwarp();
-      const int sp = (int)((k - 1) % kStages);
+      const int sp = (int)((k - 1) % NS);
       prep(st[sp], lane);
       mbar_arrive(&bars.full[sp]);
     }
   }
-  const int s = (int)(k % kStages);
-  if (k >= (uint32_t)kStages && !mbar_wait(&bars.empty[s], ((k / kStages) - 1) & 1u)) {
+  const int s = (int)(k % NS);
+  if (k >= (uint32_t)NS && !mbar_wait(&bars.empty[s], ((k / NS) - 1) & 1u)) {
     dev_fail(v.hdr, UG_ERR_TIMEOUT, 100 + which);
     cp_async_wait_all();
     return;

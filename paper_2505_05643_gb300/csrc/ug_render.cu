@@ -108,7 +108,7 @@ struct FwdShape {
 template <int TILE, int NW>
 struct FwdSmem {
   RecStage<TILE, false> st[kStages];
-  PipeBars bars;
+  PipeBars<kStages> bars;
   uint16_t list[NW][kBatch];  // full items from the front, partial items from the back
   FwdChunk ch[NW];
   PlaneTable T;
@@ -375,6 +375,9 @@ struct BwdShape {
 };
 
 constexpr int kBwdQueue = 256;  // > the items a warp can hold: 31 left over + one stage's 128
+// Stages in the backward's ring: one more than the forward's, because a
+// consumer warp holds a stage until it has processed the stage's items.
+constexpr int kBwdStages = 4;
 
 // A consumer warp's queue of work items, in a ring: (stage << 7) | record
 // index. The items are read from the stages themselves, so a stage is
@@ -386,8 +389,8 @@ struct BwdQueue {
 template <int TILE, int FH>
 struct BwdSmem {
   using Sh = BwdShape<TILE, FH>;
-  RecStage<TILE, true> st[kStages];
-  PipeBars bars;
+  RecStage<TILE, true> st[kBwdStages];
+  PipeBars<kBwdStages> bars;
   BwdQueue q[Sh::NW];
   // per footprint, row y and column pair cp (index 4 y + cp): r0, r1, -rC0, -rC1
   float4 pix[Sh::NW][FH * 4];
@@ -504,7 +507,7 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
   using Sh = BwdShape<TILE, FH>;
   using T = Tiling<TILE, FH>;
   constexpr int NW = Sh::NW;
-  static_assert(kStages <= 3 && kBatch == 128, "queue entries hold a stage (2 bits) and a record (7)");
+  static_assert(kBwdStages <= 4 && kBatch == 128, "queue entries hold a stage (2 bits) and a record (7)");
   extern __shared__ __align__(16) unsigned char bwd_smem[];
   BwdSmem<TILE, FH>& S = *reinterpret_cast<BwdSmem<TILE, FH>*>(bwd_smem);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -523,8 +526,10 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
   unsigned long long evaluated = 0;
   int fj0 = 0, fi0 = 0;
   uint32_t qhead = 0, qtail = 0;  // items processed / queued so far
-  uint32_t qe0 = 0, qe1 = 0, qe2 = 0;  // qtail after each held stage's items, by slot
-  auto qend = [&](uint32_t slot) { return slot == 0 ? qe0 : slot == 1 ? qe1 : qe2; };
+  uint32_t qe0 = 0, qe1 = 0, qe2 = 0, qe3 = 0;  // qtail after each held stage's items, by slot
+  auto qend = [&](uint32_t slot) {
+    return slot == 0 ? qe0 : slot == 1 ? qe1 : slot == 2 ? qe2 : qe3;
+  };
   uint32_t krel = 0;                    // the stages before krel are released
   // item i of the queue (0 = its oldest) from row y0: its record read from its stage
   auto item = [&](uint32_t i, int y0, int rows, bool part) {
@@ -553,19 +558,19 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
   };
   // release the held stages up to `last` whose items are all processed, in order
   auto release = [&](uint32_t last) {
-    while (krel <= last && qend(krel % kStages) <= qhead) {
-      mbar_arrive(&S.bars.empty[krel % kStages]);
+    while (krel <= last && qend(krel % kBwdStages) <= qhead) {
+      mbar_arrive(&S.bars.empty[krel % kBwdStages]);
       ++krel;
     }
   };
   for (uint32_t k = 0;; ++k) {
-    const int s = (int)(k % kStages);
-    if (k >= (uint32_t)kStages && krel + kStages <= k) {
-      // this wait reuses the slot of stage k - kStages: process its items
+    const int s = (int)(k % kBwdStages);
+    if (k >= (uint32_t)kBwdStages && krel + kBwdStages <= k) {
+      // this wait reuses the slot of stage k - kBwdStages: process its items
       while (qhead < qend(s)) round();
       release(k - 1);
     }
-    if (!mbar_wait(&S.bars.full[s], (k / kStages) & 1u)) {
+    if (!mbar_wait(&S.bars.full[s], (k / kBwdStages) & 1u)) {
       dev_fail(v.hdr, UG_ERR_TIMEOUT, 2);
       break;
     }
@@ -611,7 +616,8 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
     evaluated += qtail - q0;
     if (s == 0) qe0 = qtail;
     else if (s == 1) qe1 = qtail;
-    else qe2 = qtail;
+    else if (s == 2) qe2 = qtail;
+    else qe3 = qtail;
     __syncwarp();
     // full rounds; at the end of the tile also the rest
     const bool tile_end = h.flags & kLast;
