@@ -129,13 +129,19 @@ struct PosStore {
   __device__ void operator()(int64_t e, const uint32_t ex[1]) const { pos[e] = ex[0]; }
 };
 
+// The rows of one parameter set are a compile-time count (11 TRI, 12
+// SCALE_ROT), so that a thread's loads of its Gaussian's rows are all in
+// flight together.
+template <int COV>
 __global__ void __launch_bounds__(256)
-    k_densify_emit(int cov, int rows, const float* __restrict__ params,
-                   const float* __restrict__ m, const float* __restrict__ v, int64_t n,
-                   const float* __restrict__ z, const uint32_t* __restrict__ action,
-                   const uint32_t* __restrict__ pos, DensifyThresholds t, int64_t cap,
-                   float* __restrict__ params_out, float* __restrict__ m_out,
-                   float* __restrict__ v_out, int64_t* __restrict__ n_out) {
+    k_densify_emit(const float* __restrict__ params, const float* __restrict__ m,
+                   const float* __restrict__ v, int64_t n, const float* __restrict__ z,
+                   const uint32_t* __restrict__ action, const uint32_t* __restrict__ pos,
+                   DensifyThresholds t, int64_t cap, float* __restrict__ params_out,
+                   float* __restrict__ m_out, float* __restrict__ v_out,
+                   int64_t* __restrict__ n_out) {
+  constexpr int cov = COV;
+  constexpr int rows = COV == UG_COV_TRI ? 11 : 12;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t a = action[i];
@@ -144,17 +150,26 @@ __global__ void __launch_bounds__(256)
     if (i == n - 1) *n_out = o + cnt;
     if (cnt == 0u || o + cnt > cap) continue;
     if (a == 1u || a == 2u) {  // the original, with its moments
+      float pr[rows], mr[rows], vr[rows];
+#pragma unroll
       for (int r = 0; r < rows; ++r) {
-        params_out[r * cap + o] = params[r * n + i];
-        m_out[r * cap + o] = m[r * n + i];
-        v_out[r * cap + o] = v[r * n + i];
+        pr[r] = params[r * n + i];
+        mr[r] = m[r * n + i];
+        vr[r] = v[r * n + i];
       }
-    }
-    if (a == 2u) {  // an identical copy with zero moments
+#pragma unroll
       for (int r = 0; r < rows; ++r) {
-        params_out[r * cap + o + 1] = params[r * n + i];
-        m_out[r * cap + o + 1] = 0.f;
-        v_out[r * cap + o + 1] = 0.f;
+        params_out[r * cap + o] = pr[r];
+        m_out[r * cap + o] = mr[r];
+        v_out[r * cap + o] = vr[r];
+      }
+      if (a == 2u) {  // an identical copy with zero moments
+#pragma unroll
+        for (int r = 0; r < rows; ++r) {
+          params_out[r * cap + o + 1] = pr[r];
+          m_out[r * cap + o + 1] = 0.f;
+          v_out[r * cap + o + 1] = 0.f;
+        }
       }
     }
     if (a == 3u) {  // two children drawn from the parent, covariance / phi^2
@@ -164,7 +179,7 @@ __global__ void __launch_bounds__(256)
         float w[3];
         sample_offset(cov, params + i, n, t.beta, zz, w);
         for (int k = 0; k < 3; ++k) params_out[k * cap + oc] = __fadd_rn(params[k * n + i], w[k]);
-        if (cov == UG_COV_TRI) {
+        if constexpr (cov == UG_COV_TRI) {
           // L' = phi L: L'_kk = phi (l_kk^2 + beta) = l'_kk^2 + beta, l'_jk = phi l_jk
           const int diag[3] = {3, 6, 8};
           for (int d = 0; d < 3; ++d) {
@@ -181,7 +196,9 @@ __global__ void __launch_bounds__(256)
             params_out[k * cap + oc] = __fsub_rn(params[k * n + i], t.log_phi);
           for (int k = 6; k < 10; ++k) params_out[k * cap + oc] = params[k * n + i];
         }
+#pragma unroll
         for (int r = rows - 2; r < rows; ++r) params_out[r * cap + oc] = params[r * n + i];
+#pragma unroll
         for (int r = 0; r < rows; ++r) {
           m_out[r * cap + oc] = 0.f;
           v_out[r * cap + oc] = 0.f;
@@ -246,8 +263,12 @@ cudaError_t launch_densify(int cov, int rows, const float* params, const float* 
   k_scan_top<1><<<1, 1024, 0, s>>>(part, nblk, nullptr, 0, 0, 0);
   k_scan_down<1, ActLoad, PosStore><<<(unsigned)nblk, kScanThreads, 0, s>>>(ld, st, n, part,
                                                                               nullptr);
-  k_densify_emit<<<g, 256, 0, s>>>(cov, rows, params, m, v, n, z, action, pos, t, cap, params_out,
-                                   m_out, v_out, n_out);
+  if (cov == UG_COV_TRI)
+    k_densify_emit<UG_COV_TRI><<<g, 256, 0, s>>>(params, m, v, n, z, action, pos, t, cap,
+                                                 params_out, m_out, v_out, n_out);
+  else
+    k_densify_emit<UG_COV_SCALE_ROT><<<g, 256, 0, s>>>(params, m, v, n, z, action, pos, t, cap,
+                                                       params_out, m_out, v_out, n_out);
   return cudaGetLastError();
 }
 

@@ -42,6 +42,24 @@ GaussInit gauss_taps() {
   return t;
 }
 
+// Fixed-order sum of one float per thread of a 256-thread block, returned to
+// thread 0: a pairwise tree within each warp (shuffles), then the eight warp
+// sums in order. FP64 arithmetic runs at 1/64 of the FP32 rate on GB300, so
+// the per-row sums stay in FP32; their pairwise order keeps the error near
+// log2(256) roundings.
+__device__ __forceinline__ float block_sum256f(float v) {
+  __shared__ float ws[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = 0.f;
+  if (threadIdx.x == 0) {
+    r = ((ws[0] + ws[1]) + (ws[2] + ws[3])) + ((ws[4] + ws[5]) + (ws[6] + ws[7]));
+  }
+  return r;
+}
+
 __global__ void k_ssim_rows(const float* __restrict__ x, const float* __restrict__ y, int W, int H,
                             float* __restrict__ maps, float* __restrict__ row_sse) {
   const int p = blockIdx.z, i = blockIdx.y;
@@ -69,19 +87,13 @@ __global__ void k_ssim_rows(const float* __restrict__ x, const float* __restrict
   }
   // sum of squared differences of row i (one block per row does it)
   if (blockIdx.x == 0) {
-    double s = 0.0;
+    float s = 0.f;
     for (int j = threadIdx.x; j < W; j += blockDim.x) {
-      const double d = (double)__ldg(x + img + j) - (double)__ldg(y + img + j);
-      s += d * d;
+      const float d = __ldg(x + img + j) - __ldg(y + img + j);
+      s = fmaf(d, d, s);
     }
-    __shared__ double red[256];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) row_sse[(int64_t)p * H + i] = (float)red[0];
+    s = block_sum256f(s);
+    if (threadIdx.x == 0) row_sse[(int64_t)p * H + i] = s;
   }
 }
 
@@ -91,7 +103,7 @@ __global__ void k_ssim_cols(const float* __restrict__ maps, int W, int H,
   const int Wv = W - (kWin - 1), Hv = H - (kWin - 1);
   const int64_t plane_maps = (int64_t)H * Wv;
   const float* m = maps + (int64_t)p * 5 * plane_maps;
-  double s = 0.0;
+  float s = 0.f;
   for (int jv = threadIdx.x; jv < Wv; jv += blockDim.x) {
     float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
 #pragma unroll
@@ -108,16 +120,10 @@ __global__ void k_ssim_cols(const float* __restrict__ maps, int W, int H,
     const float ux = mx + 0.5f, uy = my + 0.5f;
     const float num = (2.f * ux * uy + kC1) * (2.f * cxy + kC2);
     const float den = (ux * ux + uy * uy + kC1) * (vx + vy + kC2);
-    s += (double)(num / den);
+    s += num / den;
   }
-  __shared__ double red[256];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) row_ssim[(int64_t)p * Hv + iv] = (float)red[0];
+  s = block_sum256f(s);
+  if (threadIdx.x == 0) row_ssim[(int64_t)p * Hv + iv] = s;
 }
 
 // Fixed-order block sum of one value per thread (256 threads).
@@ -170,7 +176,7 @@ __global__ void k_dssim_cols(const float* __restrict__ maps, int W, int H,
   const int64_t plane_maps = (int64_t)H * Wv, plane_abc = (int64_t)Hv * Wv;
   const float* m = maps + (int64_t)p * 5 * plane_maps;
   float* o = abc + (int64_t)p * 3 * plane_abc + (int64_t)iv * Wv;
-  double s = 0.0;
+  float s = 0.f;
   for (int jv = threadIdx.x; jv < Wv; jv += blockDim.x) {
     float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
 #pragma unroll
@@ -194,16 +200,10 @@ __global__ void k_dssim_cols(const float* __restrict__ maps, int W, int H,
     o[jv] = d_ux - 2.f * mx * d_vx - my * d_cxy;
     o[plane_abc + jv] = 2.f * d_vx;
     o[2 * plane_abc + jv] = d_cxy;
-    s += (double)S;
+    s += S;
   }
-  __shared__ double red[256];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) row_ssim[(int64_t)p * Hv + iv] = (float)red[0];
+  s = block_sum256f(s);
+  if (threadIdx.x == 0) row_ssim[(int64_t)p * Hv + iv] = s;
 }
 
 // Transposed horizontal pass: T_f(iv, j) = sum_a w_a f(iv, j - a) over the
@@ -236,17 +236,14 @@ __global__ void k_dssim_trows(const float* __restrict__ abc, int W, int H, float
 //   dL/dx = (1 - lam) sign(x - y) / N - lam / P * (Ga + x' Gb + y' Gc) / (Hv Wv),
 // and the row's sum of |x - y| (one block per row, fixed order).
 __global__ void k_dssim_grad(const float* __restrict__ x, const float* __restrict__ y,
-                             const float* __restrict__ t, int P, int W, int H, float lam,
+                             const float* __restrict__ t, int W, int H, float k1, float k2,
                              float* __restrict__ grad, float* __restrict__ row_l1) {
   const int p = blockIdx.y, i = blockIdx.x;
   const int Wv = W - (kWin - 1), Hv = H - (kWin - 1);
   const int64_t plane_t = (int64_t)Hv * W;
   const float* tp = t + (int64_t)p * 3 * plane_t;
   const int64_t row = (int64_t)p * W * H + (int64_t)i * W;
-  const double n = (double)P * (double)W * (double)H;
-  const float k1 = (float)((1.0 - lam) / n);
-  const float k2 = (float)(lam / ((double)P * (double)Hv * (double)Wv));
-  double s = 0.0;
+  float s = 0.f;
   for (int j = threadIdx.x; j < W; j += blockDim.x) {
     float ga = 0.f, gb = 0.f, gc = 0.f;
 #pragma unroll
@@ -265,16 +262,10 @@ __global__ void k_dssim_grad(const float* __restrict__ x, const float* __restric
     const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
     const float gs = fmaf(yv - 0.5f, gc, fmaf(xv - 0.5f, gb, ga));
     grad[row + j] = fmaf(k1, sg, -k2 * gs);
-    s += (double)fabsf(d);
+    s += fabsf(d);
   }
-  __shared__ double red[256];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) row_l1[(int64_t)p * H + i] = (float)red[0];
+  s = block_sum256f(s);
+  if (threadIdx.x == 0) row_l1[(int64_t)p * H + i] = s;
 }
 
 // Per plane (one block each): its mean SSIM and its sum of |x - y|.
@@ -336,7 +327,11 @@ cudaError_t launch_l1_dssim(const float* image, const float* target, int32_t P, 
   k_dssim_cols<<<dim3((unsigned)Hv, (unsigned)P), 256, 0, s>>>(maps, W, H, abc, row_ssim);
   k_dssim_trows<<<dim3((unsigned)((W + 255) / 256), (unsigned)Hv, (unsigned)P), 256, 0, s>>>(
       abc, W, H, t);
-  k_dssim_grad<<<dim3((unsigned)H, (unsigned)P), 256, 0, s>>>(image, target, t, P, W, H, lam, grad,
+  // the gradient's two constant factors, formed once here in FP64
+  const double npx = (double)P * (double)W * (double)H;
+  const float k1 = (float)((1.0 - (double)lam) / npx);
+  const float k2 = (float)((double)lam / ((double)P * (double)Hv * (double)Wv));
+  k_dssim_grad<<<dim3((unsigned)H, (unsigned)P), 256, 0, s>>>(image, target, t, W, H, k1, k2, grad,
                                                               row_l1);
   double* plane = reinterpret_cast<double*>(
       (reinterpret_cast<uintptr_t>(row_l1 + (size_t)P * (size_t)H) + 7) & ~uintptr_t(7));
