@@ -60,13 +60,15 @@ __global__ void __launch_bounds__(256)
   const float scale = 2.0f / (float)n;
   const int64_t begin = (int64_t)blockIdx.x * kStaticChunk;
   const int64_t end = min(begin + (int64_t)kStaticChunk, n);
-  double acc = 0.0;
+  // a thread's few squares are summed in FP32 (FP64 arithmetic runs at a small
+  // fraction of the FP32 rate), the threads' sums in FP64
+  float accf = 0.f;
   for (int64_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
     const float d = image[i] - target[i];
     if (grad) grad[i] = scale * d;
-    acc += (double)d * (double)d;
+    accf = fmaf(d, d, accf);
   }
-  acc = warp_sum(acc);
+  const double acc = warp_sum((double)accf);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
