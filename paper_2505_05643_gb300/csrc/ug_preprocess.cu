@@ -465,9 +465,13 @@ __global__ void __launch_bounds__(256)
   const uint32_t end = part == 0 ? slots - n64 : slots;
   unsigned long long npx = 0;
   uint32_t holes = 0, kept = 0;
-  for (uint32_t k = begin + blockIdx.x * blockDim.x + threadIdx.x; k < end;
-       k += gridDim.x * blockDim.x) {
-    const uint4 e = v.list[k];
+  // the next entry of the list is read one iteration ahead
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t k = begin + blockIdx.x * blockDim.x + threadIdx.x;
+  uint4 e_next = k < end ? v.list[k] : make_uint4(0u, 0u, 0u, 0u);
+  for (; k < end; k += stride) {
+    const uint4 e = e_next;
+    if (k + stride < end) e_next = v.list[k + stride];
     const uint32_t slot = e.z;
     const PlaneDev pl = v.planes[e.y];
     GaussParams prm;
