@@ -422,9 +422,8 @@ ug_status ug_densify(const ug_config* cfg, const ug_densify_config* dc, const fl
   t.beta = cfg->beta;
   t.phi = dc->split_factor;
   t.log_phi = (float)std::log((double)dc->split_factor);
-  const int rows = cfg->cov_param == UG_COV_TRI ? 11 : 12;
-  return cuda_status(launch_densify(cfg->cov_param, rows, params, exp_avg, exp_avg_sq, n, stats, z,
-                                    t, capacity, params_out, exp_avg_out, exp_avg_sq_out, n_out,
+  return cuda_status(launch_densify(cfg->cov_param, params, exp_avg, exp_avg_sq, n, stats, z, t,
+                                    capacity, params_out, exp_avg_out, exp_avg_sq_out, n_out,
                                     scratch, reinterpret_cast<cudaStream_t>(stream)));
 }
 

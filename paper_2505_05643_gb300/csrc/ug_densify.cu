@@ -245,7 +245,7 @@ cudaError_t launch_densify_stats(const float* gmean, int64_t n, float* stats, cu
   return cudaGetLastError();
 }
 
-cudaError_t launch_densify(int cov, int rows, const float* params, const float* m, const float* v,
+cudaError_t launch_densify(int cov, const float* params, const float* m, const float* v,
                            int64_t n, const float* stats, const float* z,
                            const DensifyThresholds& t, int64_t cap, float* params_out,
                            float* m_out, float* v_out, int64_t* n_out, void* scratch,

@@ -270,7 +270,7 @@ size_t densify_scratch_bytes(int64_t n);
 cudaError_t launch_sample(int cov, const float* params, int64_t n, float beta, const int32_t* idx,
                           int64_t m, const float* z, float* y, cudaStream_t s);
 cudaError_t launch_densify_stats(const float* gmean, int64_t n, float* stats, cudaStream_t s);
-cudaError_t launch_densify(int cov, int rows, const float* params, const float* m, const float* v,
+cudaError_t launch_densify(int cov, const float* params, const float* m, const float* v,
                            int64_t n, const float* stats, const float* z,
                            const DensifyThresholds& t, int64_t cap, float* params_out,
                            float* m_out, float* v_out, int64_t* n_out, void* scratch,
