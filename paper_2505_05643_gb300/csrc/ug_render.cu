@@ -508,6 +508,7 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
   using T = Tiling<TILE, FH>;
   constexpr int NW = Sh::NW;
   static_assert(kBwdStages <= 4 && kBatch == 128, "queue entries hold a stage (2 bits) and a record (7)");
+  static_assert(kBwdQueue >= 31 + kBatch, "the queue holds a round's remainder and a whole stage");
   extern __shared__ __align__(16) unsigned char bwd_smem[];
   BwdSmem<TILE, FH>& S = *reinterpret_cast<BwdSmem<TILE, FH>*>(bwd_smem);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;

@@ -1,0 +1,123 @@
+"""Host model of the backward rasterizer's record pipeline (no GPU): one
+producer fills a ring of NS stages, each consumer warp queues the indices of
+its live records, processes them 32 at a time, and releases a stage once all of
+the stage's items are processed, at the latest before the wait that reuses the
+stage's slot. The model follows the kernel's rules step by step on random
+per-stage item counts (dense, sparse and empty footprints, tiles of one or
+many stages) and checks what the kernel relies on: every warp always makes
+progress (no wait for a slot that a consumer still holds), every stage is
+released exactly once by every consumer, every item is processed exactly once
+and only while its stage is held, and the queue never holds more than a
+round's remainder plus one stage."""
+import numpy as np
+import pytest
+
+BATCH = 128
+
+
+def _simulate(ns, tiles, warps, rng):
+    """tiles: list of per-tile stage counts; returns the largest queue fill."""
+    # the stream of stages: (tile end?, per-warp live item counts)
+    stages = []
+    for n_st in tiles:
+        for j in range(n_st):
+            cnt = [int(rng.choice([0, rng.integers(0, 8), rng.integers(0, BATCH + 1)]))
+                   for _ in range(warps)]
+            stages.append((j == n_st - 1, cnt))
+    total = len(stages)
+    released = [[False] * total for _ in range(warps)]  # by warp, by stage
+    filled = [False] * total
+    # producer: stage k may be filled once every warp released stage k - ns
+    produced = 0
+
+    def produce():
+        nonlocal produced
+        while produced < total and (produced < ns or
+                                    all(released[w][produced - ns] for w in range(warps))):
+            filled[produced] = True
+            produced += 1
+
+    state = []
+    for w in range(warps):
+        state.append(dict(k=0, qhead=0, qtail=0, qend={}, krel=0, items=[], done=False))
+    max_fill = 0
+    processed = [set() for _ in range(warps)]
+
+    def round_(w):
+        st = state[w]
+        n = min(st["qtail"] - st["qhead"], 32)
+        for i in range(st["qhead"], st["qhead"] + n):
+            stage, item = st["items"][i]
+            assert not released[w][stage], "item read after its stage was released"
+            assert (stage, item) not in processed[w]
+            processed[w].add((stage, item))
+        st["qhead"] += n
+
+    def release(w, last):
+        st = state[w]
+        while st["krel"] <= last and st["qend"][st["krel"]] <= st["qhead"]:
+            assert not released[w][st["krel"]]
+            released[w][st["krel"]] = True
+            st["krel"] += 1
+
+    produce()
+    steps = 0
+    while not all(s["done"] for s in state):
+        progressed = False
+        for w in range(warps):
+            st = state[w]
+            if st["done"]:
+                continue
+            k = st["k"]
+            if k == total:
+                st["done"] = True
+                progressed = True
+                continue
+            if k >= ns and st["krel"] + ns <= k:
+                # the wait reuses the slot of stage k - ns: process its items first
+                while st["qhead"] < st["qend"][k - ns]:
+                    round_(w)
+                release(w, k - 1)
+                progressed = True
+            if not filled[k]:
+                continue  # waits for the producer
+            tile_end, cnt = stages[k]
+            for i in range(cnt[w]):
+                st["items"].append((k, i))
+            st["qtail"] += cnt[w]
+            st["qend"][k] = st["qtail"]
+            max_fill = max(max_fill, st["qtail"] - st["qhead"])
+            while st["qtail"] - st["qhead"] >= 32 or (tile_end and st["qtail"] > st["qhead"]):
+                round_(w)
+            release(w, k)
+            st["k"] = k + 1
+            progressed = True
+        produce()
+        steps += 1
+        assert progressed or all(s["done"] for s in state), "no warp can make progress"
+        assert steps < 100000
+    for w in range(warps):
+        assert all(released[w]), "a stage was never released"
+        assert len(processed[w]) == sum(c[w] for _, c in stages)
+    return max_fill
+
+
+@pytest.mark.parametrize("ns", [2, 3, 4])
+def test_release_protocol_progresses_and_releases_every_stage(ns):
+    rng = np.random.default_rng(ns)
+    worst = 0
+    for _ in range(60):
+        tiles = [int(rng.integers(1, 6)) for _ in range(int(rng.integers(1, 12)))]
+        worst = max(worst, _simulate(ns, tiles, warps=4, rng=rng))
+    assert worst <= 31 + BATCH
+
+
+def test_queue_capacity_in_the_kernel_covers_the_bound():
+    """The kernel's queue (a ring of kBwdQueue entries) holds the model's bound."""
+    import re
+    from pathlib import Path
+    src = (Path(__file__).resolve().parents[1] / "paper_2505_05643_gb300" / "csrc" /
+           "ug_render.cu").read_text()
+    q = int(re.search(r"constexpr int kBwdQueue = (\d+);", src).group(1))
+    ns = int(re.search(r"constexpr int kBwdStages = (\d+);", src).group(1))
+    assert q >= 31 + BATCH and 2 <= ns <= 4
