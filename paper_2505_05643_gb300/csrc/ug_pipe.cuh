@@ -116,18 +116,25 @@ struct StageHdr {
   int64_t px_off;
 };
 
-// One stage: up to kBatch records of one tile and one 32-bit word per record
-// of footprint tests (written by the producer's finishing step, or copied
-// from the forward pass's tests); with RAW (the backward pass), the first
-// stage of a tile also carries the tile's pixel inputs (dL/dC, alpha, C;
-// pixels off the plane hold 0, 1, 0).
+// 8x8 footprints of a tile whose item lists a forward stage carries.
+constexpr int kMaxFootprints = 4;
+
+// One stage: up to kBatch records of one tile. Forward (not RAW): per 8x8
+// footprint, the indices of the records live there (those whose box covers
+// the footprint from the front, the others from the back) and their counts,
+// written by the producer's finishing step. Backward (RAW): one 32-bit word
+// per record of the forward pass's footprint tests, and with the first stage
+// of a tile the tile's pixel inputs (dL/dC, alpha, C; pixels off the plane
+// hold 0, 1, 0).
 template <int TILE, bool RAW>
 struct RecStage {
   float4 a[kBatch];
   float4 b[kBatch];
   uint2 box[kBatch];
   uint32_t rid[kBatch];
-  uint32_t mask[kBatch];
+  uint32_t mask[RAW ? kBatch : 1];
+  uint8_t list[RAW ? 1 : kMaxFootprints][RAW ? 1 : kBatch];
+  uint8_t nfull[RAW ? 1 : kMaxFootprints], npart[RAW ? 1 : kMaxFootprints];
   StageHdr h;
   float raw[RAW ? 3 : 1][RAW ? TILE * TILE : 1];
 };

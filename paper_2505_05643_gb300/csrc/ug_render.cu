@@ -103,13 +103,16 @@ struct FwdShape {
   static constexpr int LG = 32 / G;       // lanes per group: 8 rows x LG / 8 column blocks
   static constexpr int NP = G;            // column pairs per lane
   static_assert(G == 1 || G == 2 || G == 4, "groups");
+  // resident blocks asked of the compiler (at most 64 registers a thread for
+  // the 16x16 tile's 160 threads, so that shared memory, not registers,
+  // limits the blocks per SM)
+  static constexpr int kMinBlocks = NT >= 160 ? 6 : 1;
 };
 
 template <int TILE, int NW>
 struct FwdSmem {
   RecStage<TILE, false> st[kStages];
   PipeBars<kStages> bars;
-  uint16_t list[NW][kBatch];  // full items from the front, partial items from the back
   FwdChunk ch[NW];
   PlaneTable T;
 };
@@ -211,37 +214,62 @@ __device__ __forceinline__ void fwd_build(FwdChunk& W, int lane, bool real, cons
 
 // The producer's finishing step of a forward stage: every record against
 // every 8x8 footprint of the tile (one lane per record, the record read once),
-// byte f of the record's word the test of footprint f, written to the stage
-// and, for the backward pass, per sorted instance.
+// byte f of the record's word the test of footprint f, written per sorted
+// instance for the backward pass; then, per footprint, the compacted lists of
+// its live records (box covering the footprint from the front, the others
+// from the back) and their counts, written to the stage for the consumers.
 template <int TILE, int CUT>
 struct FwdPrep {
   static constexpr bool kDefer = true;
   uint32_t* inst_mask;
   __device__ void operator()(RecStage<TILE, false>& S, int lane) const {
     using T = Tiling<TILE, 8>;
+    static_assert(T::NF <= kMaxFootprints, "a stage carries the lists of four footprints");
     const StageHdr h = S.h;
+    uint32_t mq[kBatch / 32];
 #pragma unroll
     for (int q = 0; q < kBatch / 32; ++q) {
       const int r = lane + 32 * q;
+      uint32_t m = 0;
       if (r < h.cnt) {
         const float4 a = S.a[r], c = S.b[r];
         const uint2 bx = S.box[r];
-        uint32_t m = 0;
 #pragma unroll
         for (int f = 0; f < T::NF; ++f) {
           int fj0, fi0;
           footprint_origin(f, T::FX, 8, h.tx, h.ty, TILE, fj0, fi0);
           m |= classify<CUT>(a, c, bx, fj0, fi0, 8) << (8 * f);
         }
-        S.mask[r] = m;
         inst_mask[h.inst0 + r] = m;
+      }
+      mq[q] = m;
+    }
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int f = 0; f < T::NF; ++f) {
+      int nf = 0, np = 0;
+#pragma unroll
+      for (int q = 0; q < kBatch / 32; ++q) {
+        const uint32_t mf = mq[q] >> (8 * f);
+        const bool live = mf & 1u, full = mf & 2u;
+        const uint32_t bf = __ballot_sync(0xffffffffu, live && full);
+        const uint32_t bp = __ballot_sync(0xffffffffu, live && !full);
+        const int r = lane + 32 * q;
+        if (live && full) S.list[f][nf + __popc(bf & lt)] = (uint8_t)r;
+        if (live && !full) S.list[f][kBatch - 1 - (np + __popc(bp & lt))] = (uint8_t)r;
+        nf += __popc(bf);
+        np += __popc(bp);
+      }
+      if (lane == 0) {
+        S.nfull[f] = (uint8_t)nf;
+        S.npart[f] = (uint8_t)np;
       }
     }
   }
 };
 
 template <int TILE, int G, int CUT>
-__global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
+__global__ void __launch_bounds__(FwdShape<TILE, G>::NT, FwdShape<TILE, G>::kMinBlocks)
     k_render_fwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles, float abg,
                  float cbg, float* __restrict__ image, float* __restrict__ alpha,
                  uint32_t* __restrict__ inst_mask) {
@@ -259,7 +287,6 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
   }
   const int grp = lane / LG, gl = lane % LG;
   const int y = gl & 7, cp0 = (gl >> 3) * NP;  // this lane's row and first column pair
-  const uint32_t lt = lanemask_lt();
   unsigned long long evaluated = 0;  // (record, footprint) items of this warp
   int fj0 = 0, fi0 = 0, tw = 0, th = 0;
   int64_t tpx = 0;
@@ -286,34 +313,16 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
 #pragma unroll
       for (int p = 0; p < NP; ++p) sa[p] = sc[p] = make_float2(0.f, 0.f);
     }
-    // this warp's lists: full-box items from the front, partial from the back
-    // (the stage's tests read first, all four groups of 32 at once)
-    uint32_t mq[kBatch / 32];
-#pragma unroll
-    for (int q = 0; q < kBatch / 32; ++q) {
-      const int r = 32 * q + lane;
-      mq[q] = r < h.cnt ? R.mask[r] >> (8 * warp) : 0u;
-    }
-    int nf = 0, np = 0;
-#pragma unroll
-    for (int q = 0; q < kBatch / 32; ++q) {
-      const int r = 32 * q + lane;
-      const bool live = mq[q] & 1u, full = mq[q] & 2u;
-      const uint32_t bf = __ballot_sync(0xffffffffu, live && full);
-      const uint32_t bp = __ballot_sync(0xffffffffu, live && !full);
-      if (live && full) S.list[warp][nf + __popc(bf & lt)] = (uint16_t)r;
-      if (live && !full) S.list[warp][kBatch - 1 - (np + __popc(bp & lt))] = (uint16_t)r;
-      nf += __popc(bf);
-      np += __popc(bp);
-    }
-    __syncwarp();
+    // this warp's lists, compacted by the producer: full-box items from the
+    // front, partial from the back
+    const int nf = R.nfull[warp], np = R.npart[warp];
     evaluated += (unsigned long long)(nf + np);
     FwdChunk& W = S.ch[warp];
     for (int base = 0; base < nf; base += 32) {
       const int ne = min(32, nf - base), nr = (ne + G - 1) / G * G;
       if (lane < nr) {  // lane-parallel chunk build
         const bool real = lane < ne;
-        const int r = real ? (int)S.list[warp][base + lane] : 0;
+        const int r = real ? (int)R.list[warp][base + lane] : 0;
         fwd_build<CUT, false>(W, lane, real, R.a[r], R.b[r], R.box[r], fj0, fi0);
       }
       __syncwarp();
@@ -324,7 +333,7 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT)
       const int ne = min(32, np - base), nr = (ne + G - 1) / G * G;
       if (lane < nr) {
         const bool real = lane < ne;
-        const int r = real ? (int)S.list[warp][kBatch - 1 - (base + lane)] : 0;
+        const int r = real ? (int)R.list[warp][kBatch - 1 - (base + lane)] : 0;
         fwd_build<CUT, true>(W, lane, real, R.a[r], R.b[r], R.box[r], fj0, fi0);
       }
       __syncwarp();

@@ -239,7 +239,7 @@ __global__ void k_dssim_grad(const float* __restrict__ x, const float* __restric
                              const float* __restrict__ t, int W, int H, float k1, float k2,
                              float* __restrict__ grad, float* __restrict__ row_l1) {
   const int p = blockIdx.y, i = blockIdx.x;
-  const int Wv = W - (kWin - 1), Hv = H - (kWin - 1);
+  const int Hv = H - (kWin - 1);
   const int64_t plane_t = (int64_t)Hv * W;
   const float* tp = t + (int64_t)p * 3 * plane_t;
   const int64_t row = (int64_t)p * W * H + (int64_t)i * W;
