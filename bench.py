@@ -44,8 +44,8 @@ BWD_OPS = 9
 # DRAM bytes (read + write) of one k_render_bwd launch on this workload, from a
 # one-pass ncu capture of the kernel as it stands; None when the kernel has
 # changed since.
-BWD_TRAFFIC = 549517824  # 470,051,328 read + 79,466,496 written
-FWD_TRAFFIC = 248411648  # 186,532,096 read + 61,879,552 written (k_render_fwd, same capture)
+BWD_TRAFFIC = 549937408  # 470,391,552 read + 79,545,856 written
+FWD_TRAFFIC = 252912384  # 190,099,968 read + 62,812,416 written (k_render_fwd, same capture)
 
 METRIC = "Gaussian·pixel evals/s and fwd+bwd train steps/s, 1M Gaussians, 1×GB300"
 WORKLOAD = "aniso_1m: 1,000,000 Gaussians, axis ratios log-uniform to 1e4, 64 planes/launch " \
