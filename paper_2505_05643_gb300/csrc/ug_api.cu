@@ -404,7 +404,8 @@ ug_status ug_densify(const ug_config* cfg, const ug_densify_config* dc, const fl
                      const float* z, int64_t capacity, float* params_out, float* exp_avg_out,
                      float* exp_avg_sq_out, int64_t* n_out, void* scratch, size_t scratch_bytes,
                      ug_stream stream) {
-  if (!cov_ok(cfg) || !dc || n < 1 || n >= ((int64_t)1 << 31) || capacity < 1) return UG_ERR_INVALID_ARGUMENT;
+  if (!cov_ok(cfg) || !dc || n < 1 || n >= ((int64_t)1 << 31) || capacity < 1)
+    return UG_ERR_INVALID_ARGUMENT;
   if (!params || !exp_avg || !exp_avg_sq || !stats || !z || !params_out || !exp_avg_out ||
       !exp_avg_sq_out || !n_out || !scratch)
     return UG_ERR_INVALID_ARGUMENT;

@@ -125,3 +125,82 @@ def test_calls_reject_null_and_small_workspace(lib):
     assert st == B.UG_ERR_INVALID_ARGUMENT
     st = lib.ug_adam_step(None, None, None, None, 1, 10, None, None, 0.9, 0.999, 1e-15, None)
     assert st == B.UG_ERR_INVALID_ARGUMENT
+
+
+def test_loss_and_evaluator_calls_check_their_arguments(lib):
+    """SSIM, L1 + D-SSIM: sizes below the 11 x 11 window, a weight outside
+    [0, 1], missing pointers and short scratch are refused before any launch."""
+    nz = ctypes.c_void_p(256)  # never dereferenced: every call below returns first
+    assert lib.ug_ssim_scratch_floats(0, 16, 16) == 0
+    assert lib.ug_ssim_scratch_floats(1, 10, 40) == 0
+    assert lib.ug_ssim_scratch_floats(1, 11, 11) > 0
+    assert lib.ug_l1_dssim_scratch_floats(1, 40, 10) == 0
+    need = lib.ug_l1_dssim_scratch_floats(2, 32, 24)
+    assert need >= 2 * 32 * 24
+    ok = [nz, nz, 2, 32, 24, ctypes.c_float(0.2), nz, need, nz, nz, None]
+    for i, bad in ((0, None), (1, None), (6, None), (8, None), (9, None)):
+        args = list(ok)
+        args[i] = bad
+        assert lib.ug_l1_dssim_loss_grad(*args) == B.UG_ERR_INVALID_ARGUMENT
+    for lam in (-0.1, 1.5, float("nan")):
+        args = list(ok)
+        args[5] = ctypes.c_float(lam)
+        assert lib.ug_l1_dssim_loss_grad(*args) == B.UG_ERR_INVALID_ARGUMENT
+    args = list(ok)
+    args[3] = 10
+    assert lib.ug_l1_dssim_loss_grad(*args) == B.UG_ERR_INVALID_ARGUMENT
+    args = list(ok)
+    args[7] = need - 1
+    assert lib.ug_l1_dssim_loss_grad(*args) == B.UG_ERR_WORKSPACE_TOO_SMALL
+    s_need = lib.ug_ssim_scratch_floats(2, 32, 24)
+    assert lib.ug_ssim(nz, nz, 2, 32, 24, nz, s_need, None, None, None) == B.UG_ERR_INVALID_ARGUMENT
+    assert lib.ug_ssim(nz, nz, 2, 32, 24, nz, s_need - 1, nz, nz, None) == \
+        B.UG_ERR_WORKSPACE_TOO_SMALL
+
+
+def test_densify_and_sample_calls_check_their_arguments(lib):
+    """Resampling and densify / prune: bad parametrisation or beta, negative or
+    out-of-range counts, missing pointers, thresholds outside their domain and
+    short scratch are refused before any launch; the defaults are the
+    documented ones."""
+    nz = ctypes.c_void_p(256)
+    dc = B.ug_densify_config()
+    assert lib.ug_densify_config_default(None) == B.UG_ERR_INVALID_ARGUMENT
+    assert lib.ug_densify_config_default(ctypes.byref(dc)) == B.UG_OK
+    assert (dc.min_opacity, dc.split_factor) == (np.float32(0.005), np.float32(1.6))
+    cfg = B.ug_config_default()
+    bad_cov = B.ug_config_default()
+    bad_cov.cov_param = 7
+    bad_beta = B.ug_config_default()
+    bad_beta.beta = 0.0
+    for c in (bad_cov, bad_beta):
+        assert lib.ug_sample(ctypes.byref(c), nz, 10, nz, 4, nz, nz, None) == \
+            B.UG_ERR_INVALID_ARGUMENT
+    assert lib.ug_sample(ctypes.byref(cfg), nz, 10, nz, -1, nz, nz, None) == \
+        B.UG_ERR_INVALID_ARGUMENT
+    assert lib.ug_sample(ctypes.byref(cfg), nz, 10, None, 4, nz, nz, None) == \
+        B.UG_ERR_INVALID_ARGUMENT
+    assert lib.ug_densify_stats(nz, 0, nz, None) == B.UG_ERR_INVALID_ARGUMENT
+    assert lib.ug_densify_stats(None, 5, nz, None) == B.UG_ERR_INVALID_ARGUMENT
+    assert lib.ug_densify_scratch_bytes(0) == 0
+    n = 1000
+    need = lib.ug_densify_scratch_bytes(n)
+    assert need >= 8 * n
+
+    def densify(c=cfg, d=dc, n_=n, cap=2 * n, scratch=nz, sbytes=need, params=nz):
+        return lib.ug_densify(ctypes.byref(c), ctypes.byref(d), params, nz, nz, n_, nz, nz, cap,
+                              nz, nz, nz, nz, scratch, sbytes, None)
+
+    assert densify(n_=0) == B.UG_ERR_INVALID_ARGUMENT
+    assert densify(n_=1 << 31) == B.UG_ERR_INVALID_ARGUMENT
+    assert densify(cap=0) == B.UG_ERR_INVALID_ARGUMENT
+    assert densify(c=bad_cov) == B.UG_ERR_INVALID_ARGUMENT
+    assert densify(params=None) == B.UG_ERR_INVALID_ARGUMENT
+    assert densify(scratch=None) == B.UG_ERR_INVALID_ARGUMENT
+    for field, value in (("min_opacity", 0.0), ("min_opacity", 1.0), ("split_factor", 1.0),
+                         ("size_threshold", 0.0), ("grad_threshold", float("nan"))):
+        d = B.ug_densify_config()
+        lib.ug_densify_config_default(ctypes.byref(d))
+        setattr(d, field, value)
+        assert densify(d=d) == B.UG_ERR_INVALID_ARGUMENT, field
+    assert densify(sbytes=need - 1) == B.UG_ERR_WORKSPACE_TOO_SMALL
