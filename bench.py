@@ -12,6 +12,17 @@ step rate. Every step starts from the same state (initial parameters, zero Adam
 moments), restored by a device copy inside the step, so the workload does not
 drift with the number of steps. `--impl reference` times the FP64 CPU oracle (the only other
 implementation of this method) on a bounded sample of the same workload.
+
+Beside `value`: `e2e` (the same step through the public API with the targets
+and poses copied from pinned host memory and the loss and status read back every
+step), `roofline` (the backward rasterizer's FP32-pipe fraction, the forward's
+beside it, and every phase's time), `cpu_baseline` (the FP64 oracle on the host
+cores), `clocks` (SM clock and throttle reasons sampled during the timed
+region) and `gpu_launches`. Other modes: `--workload train_200k` (the batched
+graph step against one plane per launch), `--workload recon` (reconstruction
+run: SSIM over time, novel-slice images per second), `--workload densify`,
+`--workload loss`, and `--ablation scatter` (the paper's atomic scatter forward
+against the tile gather).
 """
 from __future__ import annotations
 
