@@ -115,7 +115,12 @@ typedef struct {
                         in extended (double-word, ~48-bit) precision; default 1e3 */
   int32_t variant_bwd; /* backward rasterizer variant, 0 or 1: footprint height 8 (default)
                           or 4 rows */
-  int32_t reserved[2];
+  float fp32_reach;  /* the geometry also runs in extended precision when ||F||_F (|mu| +
+                        max |o|) exceeds this (F the Gaussian's precision factor, o the plane
+                        origins): FP32 differences mu - o then lose the bits that thin or
+                        distant Gaussians need; default 20. Both this and fp64_ratio +inf:
+                        FP32 geometry throughout */
+  int32_t reserved;
 } ug_config;
 
 /* Sizes, capacities and the workspace layout of one rendering problem.
@@ -311,14 +316,18 @@ ug_status ug_read_status(const ug_plan* plan, const void* ws, size_t ws_bytes, u
  * tile keys and record ids (instance order), the tile ranges (uint32 pairs
  * [start, end) per tile), and per record slot its pixel box (uint32 pairs:
  * j0 | j1 << 16, i0 | i1 << 16; an empty box marks a rejected candidate), its
- * render data a = (x*_j, x*_i, r11, r12) and b = (r22, lw2, c, ellipsoid
- * threshold) as 4 floats each, and its plane index. Valid after ug_bin_sort;
- * any argument may be NULL. A record is binned only to the tiles of its box in
+ * render data as 4 floats each: a = (X, Y, r11, kappa), b = (r22, lw2, c,
+ * ellipsoid threshold), c = (X', Y', kappa', 0), the low parts of X, Y, kappa,
+ * where (X + X', Y + Y') is the in-plane peak in pixel units relative to the
+ * box's first column and row (pixel (i, j) centred at (j - j0 + 1/2, i - i0 +
+ * 1/2)) and the weight at a pixel is 2^(lw2 - t1^2 - t2^2), t1 = r11 (dx +
+ * kappa dy), t2 = r22 dy; and its plane index. Valid after ug_bin_sort; any
+ * argument may be NULL. A record is binned only to the tiles of its box in
  * which some weight can be non-zero in FP32. */
 ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_t** sorted_keys,
                          uint32_t** sorted_records, uint32_t** tile_ranges,
                          uint32_t** record_boxes, float** record_a, float** record_b,
-                         uint32_t** record_planes);
+                         float** record_c, uint32_t** record_planes);
 
 /* Row f4 (the loss half): the training loss of Kerbl et al., which Sec. 4.5
  * takes over, for P planes of W x H pixels stored one after the other:

@@ -56,7 +56,7 @@ class ug_config(ctypes.Structure):
                 ("cutoff", ctypes.c_int32), ("cov_param", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("fp64_ratio", ctypes.c_float), ("variant_bwd", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("fp32_reach", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
 class ug_densify_config(ctypes.Structure):
@@ -155,7 +155,7 @@ def load(build_if_missing: bool = True):
     lib.ug_densify.argtypes = [P(ug_config), P(ug_densify_config), vp, vp, vp, i64, vp, vp, i64,
                                vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.ug_debug_views.argtypes = [P(ug_plan), vp, ctypes.c_size_t, P(vp), P(vp), P(vp), P(vp),
-                                   P(vp), P(vp), P(vp)]
+                                   P(vp), P(vp), P(vp), P(vp)]
     for name in EXPORTS:
         fn = getattr(lib, name)
         # an undeclared signature would pass Python ints as 32-bit C ints
@@ -357,7 +357,7 @@ def ug_debug_stall_pipeline(plan: ug_plan, ws, on: bool, stream=None):
 
 
 def ug_debug_views(plan: ug_plan, ws):
-    ptrs = [ctypes.c_void_p() for _ in range(7)]
+    ptrs = [ctypes.c_void_p() for _ in range(8)]
     _check(load().ug_debug_views(ctypes.byref(plan), _ptr(ws), ws.numel(),
                                  *[ctypes.byref(p) for p in ptrs]), "ug_debug_views")
     return [p.value for p in ptrs]

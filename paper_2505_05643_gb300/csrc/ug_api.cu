@@ -34,7 +34,8 @@ ug_status check_config(const ug_config* c) {
   if (c->variant < 0 || c->variant >= num_render_variants(c->tile)) return UG_ERR_NOT_SUPPORTED;
   if (c->variant_bwd < 0 || c->variant_bwd >= num_render_variants_bwd(c->tile))
     return UG_ERR_NOT_SUPPORTED;
-  if (!(c->fp64_ratio > 0.f)) return UG_ERR_INVALID_ARGUMENT;  // +inf disables the FP64 branch
+  if (!(c->fp64_ratio > 0.f)) return UG_ERR_INVALID_ARGUMENT;
+  if (!(c->fp32_reach > 0.f)) return UG_ERR_INVALID_ARGUMENT;  // both +inf: FP32 only
   return UG_OK;
 }
 
@@ -102,6 +103,7 @@ ug_status ug_config_default(ug_config* cfg) {
   cfg->variant = 0;
   cfg->variant_bwd = 0;
   cfg->fp64_ratio = 1e3f;
+  cfg->fp32_reach = 20.f;
   return UG_OK;
 }
 
@@ -173,6 +175,7 @@ ug_status ug_plan_init(const ug_config* cfg, int64_t n, const ug_plane* host_pla
   sz[kOffList] = sizeof(uint4) * (size_t)rc;
   sz[kOffRecA] = sizeof(float4) * (size_t)rc;
   sz[kOffRecB] = sizeof(float4) * (size_t)rc;
+  sz[kOffRecC] = sizeof(float4) * (size_t)rc;
   sz[kOffRecBox] = sizeof(uint2) * (size_t)rc;
   sz[kOffRecPlane] = sizeof(uint32_t) * (size_t)rc;
   sz[kOffInstOff] = sizeof(uint32_t) * (size_t)rc;
@@ -336,7 +339,7 @@ ug_status ug_read_status(const ug_plan* plan, const void* ws, size_t ws_bytes, u
 ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_t** sorted_keys,
                          uint32_t** sorted_records, uint32_t** tile_ranges,
                          uint32_t** record_boxes, float** record_a, float** record_b,
-                         uint32_t** record_planes) {
+                         float** record_c, uint32_t** record_planes) {
   ug_status s = check_plan(plan);
   if (s == UG_OK) s = check_ws(plan, ws, ws_bytes);
   if (s != UG_OK) return s;
@@ -348,6 +351,7 @@ ug_status ug_debug_views(const ug_plan* plan, void* ws, size_t ws_bytes, uint32_
   if (record_boxes) *record_boxes = reinterpret_cast<uint32_t*>(v.rec_box);
   if (record_a) *record_a = reinterpret_cast<float*>(v.rec_a);
   if (record_b) *record_b = reinterpret_cast<float*>(v.rec_b);
+  if (record_c) *record_c = reinterpret_cast<float*>(v.rec_c);
   if (record_planes) *record_planes = v.rec_plane;
   return UG_OK;
 }

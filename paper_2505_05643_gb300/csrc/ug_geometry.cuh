@@ -288,6 +288,7 @@ struct PairBox {
 
 template <typename T>
 struct PairGeo {
+  T d[3];     // mu - o (world)
   T m[3];     // probe-frame mean
   T z[3][3];  // Fi u, Fi v, Fi n
   T S11, S22, S33;
@@ -324,7 +325,7 @@ __device__ __forceinline__ PairBox pair_box(const Factor<T>& f, const PlaneDev& 
   pb.i1 = 0;
   Frame<T> fr;
   load_frame(pl, fr);
-  T d[3];
+  T* d = g.d;
 #pragma unroll
   for (int k = 0; k < 3; ++k) d[k] = r_sub(f.mu[k], fr.o[k]);
   g.m[2] = r_dot3(fr.r[2], d);
@@ -347,48 +348,79 @@ __device__ __forceinline__ PairBox pair_box(const Factor<T>& f, const PlaneDev& 
   return pb;
 }
 
-// Full record of a visible pair (render-side form, see ug_internal.cuh).
+// Render-side geometry of a visible pair in the plane's own coordinates. With
+// X_w = o + x1 u + x2 v a point of the plane (x1, x2 in world units), the
+// quadratic form of Eq. mahalanobis-3d is q = |F^T (X_w - mu)|^2 = |B x - c|^2,
+// B = [F^T u, F^T v] (3 x 2), c = F^T (mu - o): a linear least-squares
+// residual in x = (x1, x2). Gram-Schmidt B = [q1 q2] R (R upper triangular)
+// gives
+//   x* = R^-1 (q1.c, q2.c),  q = q0 + |R (x - x*)|^2,  q0 = (nh.c)^2,
+// nh = q1 x q2. Unlike the conditional-Gaussian form through the probe frame,
+// this uses u and v as given (the plane's FP32 axes are orthonormal only to
+// about 1e-8, which thin Gaussians amplify beyond the output tolerance), so x*
+// and q0 match the definition for any input pose.
 template <typename T>
-struct PairRec {
-  T xs1, xs2;      // in-plane peak x* (world units)
-  T kappa[2];      // x* = m12 + m3 kappa, kappa = -(S13, S23) / S33
-  T k;             // m3 / S33
-  T q0;            // m3^2 / S33
-  T b[3][3];       // F^T u, F^T v, F^T n
-  T nb1, cr;       // |b1|, |b1 x b2|
-  T r11, r12, r22; // Cholesky of (log2 e / 2) D A D
+struct PairLsq {
+  T X, Y;          // x* in pixel units (pixel (i, j) centred at (j + 1/2, i + 1/2))
+  T kappa;         // r12 / r11 of the pixel-unit factor
+  float r11, r22;  // pixel-unit factor of (log2 e / 2) D A D (see ug_internal.cuh)
+  float rho3;      // nh.c: q0 = rho3^2
+  float q1[3], q2[3], nh[3];  // orthonormal frame of the residual (backward chain)
+  float ew[3];     // X_w(x*) - mu in world units (backward chain)
 };
 
+template <typename T>
+__device__ __forceinline__ float to_f(T x) {
+  return (float)x;
+}
+
 template <typename T, int COV>
-__device__ __forceinline__ void pair_record(const Factor<T>& f, const PlaneDev& pl,
-                                            const PairGeo<T>& g, PairRec<T>& rc) {
+__device__ __forceinline__ void pair_lsq(const Factor<T>& f, const PlaneDev& pl,
+                                         const PairGeo<T>& g, PairLsq<T>& o) {
   Frame<T> fr;
   load_frame(pl, fr);
-  const T S13 = r_dot3(g.z[0], g.z[2]);
-  const T S23 = r_dot3(g.z[1], g.z[2]);
-  rc.k = m_div(g.m[2], g.S33);
-  rc.kappa[0] = -m_div(S13, g.S33);
-  rc.kappa[1] = -m_div(S23, g.S33);
-  rc.xs1 = r_fma(g.m[2], rc.kappa[0], g.m[0]);
-  rc.xs2 = r_fma(g.m[2], rc.kappa[1], g.m[1]);
-  rc.q0 = r_mul(g.m[2], rc.k);
+  T b1[3], b2[3], c[3];
+  apply_ft<T, COV>(f, fr.r[0], b1);
+  apply_ft<T, COV>(f, fr.r[1], b2);
+  apply_ft<T, COV>(f, g.d, c);
+  const T A11 = r_dot3(b1, b1);
+  const T ir11 = ext_rsqrt(A11);
+  const T r11 = r_mul(A11, ir11);
+  T q1[3], q2[3], b2p[3], nh[3];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) apply_ft<T, COV>(f, fr.r[j], rc.b[j]);
-  // A = [b1 b2]^T [b1 b2]; R of (c D A D) with c = log2(e)/2 from b1, b2:
-  //   r11 = sqrt(c) pu |b1|, r12 = sqrt(c) pv (b1.b2)/|b1|, r22 = sqrt(c) pv |b1 x b2|/|b1|
-  const T* b1 = rc.b[0];
-  const T* b2 = rc.b[1];
-  T cx[3];
-  cx[0] = r_fma(b1[1], b2[2], -r_mul(b1[2], b2[1]));
-  cx[1] = r_fma(b1[2], b2[0], -r_mul(b1[0], b2[2]));
-  cx[2] = r_fma(b1[0], b2[1], -r_mul(b1[1], b2[0]));
-  rc.nb1 = m_sqrt(r_dot3(b1, b1));
-  rc.cr = m_sqrt(r_dot3(cx, cx));
-  const T sc = (T)0.84932180028801904272;  // sqrt(log2(e) / 2)
-  const T pu = (T)pl.pu, pv = (T)pl.pv;
-  rc.r11 = sc * pu * rc.nb1;
-  rc.r12 = sc * pv * m_div(r_dot3(b1, b2), rc.nb1);
-  rc.r22 = sc * pv * m_div(rc.cr, rc.nb1);
+  for (int a = 0; a < 3; ++a) q1[a] = r_mul(b1[a], ir11);
+  const T r12 = r_dot3(q1, b2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) b2p[a] = r_fma(-r12, q1[a], b2[a]);
+  const T A22 = r_dot3(b2p, b2p);
+  const T ir22 = ext_rsqrt(A22);
+  const T r22 = r_mul(A22, ir22);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) q2[a] = r_mul(b2p[a], ir22);
+  const T y = r_mul(r_dot3(q2, c), ir22);               // x2*
+  const T x = r_mul(r_fma(-r12, y, r_dot3(q1, c)), ir11);  // x1*
+  nh[0] = r_fma(q1[1], q2[2], -r_mul(q1[2], q2[1]));
+  nh[1] = r_fma(q1[2], q2[0], -r_mul(q1[0], q2[2]));
+  nh[2] = r_fma(q1[0], q2[1], -r_mul(q1[1], q2[0]));
+  const T rho3 = r_dot3(nh, c);
+  const T ipu = ext_rcp((T)pl.pu), ipv = ext_rcp((T)pl.pv);
+  o.X = r_fma(x, ipu, (T)pl.half_w);
+  o.Y = r_fma(y, ipv, (T)pl.half_h);
+  // kappa = (r12 pv) / (r11 pu)
+  o.kappa = r_mul(r_mul(r_mul(r12, ir11), (T)pl.pv), ipu);
+  const float sc = 0.84932180028801904272f;  // sqrt(log2(e) / 2)
+  o.r11 = __fmul_rn(__fmul_rn(sc, pl.pu), to_f(r11));
+  o.r22 = __fmul_rn(__fmul_rn(sc, pl.pv), to_f(r22));
+  o.rho3 = to_f(rho3);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    o.q1[a] = to_f(q1[a]);
+    o.q2[a] = to_f(q2[a]);
+    o.nh[a] = to_f(nh[a]);
+    // X_w(x*) - mu = x1* u + x2* v - (mu - o): the terms cancel to about the
+    // Gaussian's extent, so this stays in T
+    o.ew[a] = to_f(r_fma(x, fr.r[0][a], r_fma(y, fr.r[1][a], -g.d[a])));
+  }
 }
 
 constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2

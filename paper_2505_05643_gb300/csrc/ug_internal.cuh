@@ -16,7 +16,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;    // keys per thread per sort block
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kMseBlocks = 1024;  // partial sums of the MSE loss
-constexpr int kChainFloats = 20;  // per-record inputs of the backward chain
+constexpr int kChainFloats = 16;  // per-record inputs of the backward chain
 
 // Workspace sections (indices into ug_plan::off).
 enum WsSection {
@@ -31,6 +31,7 @@ enum WsSection {
   kOffList,      // record work list: uint4 (gaussian, plane, slot, 0); FP32 part then FP64 part
   kOffRecA,
   kOffRecB,
+  kOffRecC,
   kOffRecBox,
   kOffRecPlane,
   kOffInstOff,   // per record: tile count, scanned in place to the first instance
@@ -62,7 +63,8 @@ struct WsHeader {
   uint32_t fwd_masks;
   uint32_t stall_test;        // non-zero: the rasterizers' producers issue nothing (test hook;
                               // cleared by the preprocess)
-  uint32_t pad1[38];
+  float origin_reach;         // largest |o| over the planes (set by the plane set-up)
+  uint32_t pad1[37];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
@@ -79,15 +81,25 @@ struct PlaneDev {
 };
 static_assert(sizeof(PlaneDev) == 128, "plane size");
 
-// Render-side record of one visible (plane, Gaussian) pair.
-//  a = (xs_j, xs_i, r11, r12): peak position x* in pixel units (pixel j has
-//      its centre at j + 1/2) and the upper Cholesky factor R of
-//      (log2 e / 2) D A D, D = diag(pitch_u, pitch_v), A the in-plane precision;
+// Render-side record of one visible (plane, Gaussian) pair: three float4 and
+// the pixel box. Pixel coordinates put the centre of pixel (i, j) at
+// (j + 1/2, i + 1/2); X, Y below are relative to the box's first column j0 and
+// row i0, so pixel (i, j) sits at (j - j0 + 1/2, i - i0 + 1/2).
+//  a = (X, Y, r11, kappa)   high parts,
+//  c = (X', Y', kappa', 0)  low parts (|low| <= ulp(high) / 2): the in-plane
+//      peak x* = (X + X', Y + Y') and kappa + kappa' = r12 / r11 to double-word
+//      accuracy;
 //  b = (r22, lw2, c, e_thr): lw2 = log2(alpha) - (log2 e / 2) q0, intensity,
 //      ellipsoid threshold (log2 e / 2)(chi2 - q0);
 //  box = (j0 | j1 << 16, i0 | i1 << 16).
-// Weight at pixel (i, j): w = exp2(lw2 - t1^2 - t2^2), t1 = r11 dx + r12 dy,
-// t2 = r22 dy, dx = j + 1/2 - xs_j, dy = i + 1/2 - xs_i.
+// (r11, r12, r22) is the upper Cholesky factor of (log2 e / 2) D A D, D =
+// diag(pitch_u, pitch_v), A the in-plane precision. Weight at pixel (i, j):
+//   w = exp2(lw2 - t1^2 - t2^2),  t1 = r11 (dx + kappa dy),  t2 = r22 dy,
+//   dx = j - j0 + 1/2 - X,  dy = i - i0 + 1/2 - Y.
+// For a thin Gaussian r11 dx and r11 kappa dy are far larger than t1 and
+// cancel; the rasterizers therefore form t1 = r11 (x - S(y)) from the row's
+// crossing S(y) = X - kappa (y - Y), which they hold to double-word accuracy
+// (item_geo below).
 
 struct WsView {
   WsHeader* hdr;
@@ -101,6 +113,7 @@ struct WsView {
   uint4* list;
   float4* rec_a;
   float4* rec_b;
+  float4* rec_c;
   uint2* rec_box;
   uint32_t* rec_plane;
   uint32_t* inst_off;
@@ -129,6 +142,7 @@ inline WsView make_view(const ug_plan* plan, void* ws) {
   v.list = reinterpret_cast<uint4*>(b + plan->off[kOffList]);
   v.rec_a = reinterpret_cast<float4*>(b + plan->off[kOffRecA]);
   v.rec_b = reinterpret_cast<float4*>(b + plan->off[kOffRecB]);
+  v.rec_c = reinterpret_cast<float4*>(b + plan->off[kOffRecC]);
   v.rec_box = reinterpret_cast<uint2*>(b + plan->off[kOffRecBox]);
   v.rec_plane = reinterpret_cast<uint32_t*>(b + plan->off[kOffRecPlane]);
   v.inst_off = reinterpret_cast<uint32_t*>(b + plan->off[kOffInstOff]);
@@ -193,36 +207,106 @@ __device__ __forceinline__ float fast_exp2(float x) {
 }
 
 // Lower bound of q = t1^2 + t2^2 over the pixel centres of the rectangle
-// [xa, xb] x [ya, yb] (pixel indices) for a record a = (x*_j, x*_i, r11, r12),
-// r22: t1 = r11 dx + r12 dy (r11 >= 0), t2 = r22 dy (r22 >= 0), dx = j + 1/2 -
-// x*_j, dy = i + 1/2 - x*_i; (min |t1|)^2 + (min |t2|)^2 with each minimum at
-// the rectangle's corners (t1 is linear). Explicit round-to-nearest
-// intrinsics: the binning's count and emit kernels and the rasterizers take
-// the same decision from the same floats.
-__device__ __forceinline__ float rect_q_lower_bound(const float4& a, float r22, int xa, int xb,
-                                                    int ya, int yb) {
-  const float dxlo = __fsub_rn(__fadd_rn((float)xa, 0.5f), a.x);
-  const float dxhi = __fsub_rn(__fadd_rn((float)xb, 0.5f), a.x);
-  const float dylo = __fsub_rn(__fadd_rn((float)ya, 0.5f), a.y);
-  const float dyhi = __fsub_rn(__fadd_rn((float)yb, 0.5f), a.y);
-  const float a1 = __fmul_rn(a.w, dylo), a2 = __fmul_rn(a.w, dyhi);
-  const float t1min = __fmaf_rn(a.z, dxlo, fminf(a1, a2));
-  const float t1max = __fmaf_rn(a.z, dxhi, fmaxf(a1, a2));
-  const float m1 = t1min > 0.f ? t1min : (t1max < 0.f ? -t1max : 0.f);
-  const float m2 = dylo > 0.f ? __fmul_rn(r22, dylo) : (dyhi < 0.f ? -__fmul_rn(r22, dyhi) : 0.f);
-  return __fmaf_rn(m1, m1, __fmul_rn(m2, m2));
+// [xa, xb] x [ya, yb] (pixel indices) for a record (a = rec_a, r22) whose box
+// starts at (j0, i0). Along a row y, t1 / r11 = x - S(y) with the crossing
+// S(y) = X - kappa (y - Y); t1 is linear, so its range over the rectangle
+// comes from the corners, and min |t2| from the first and last row. The FP32
+// evaluation uses the high parts only; e1 and e2 bound its rounding errors and
+// the omitted low parts (each at most 2^-24 of its high part), so the result
+// is a lower bound for the exact record values, which the rasterizers
+// reproduce to a few ulps. Explicit round-to-nearest intrinsics: the binning's
+// passes and the rasterizers take the same decision from the same floats.
+__device__ __forceinline__ float rect_q_lower_bound(const float4& a, float r22, int j0, int i0,
+                                                    int xa, int xb, int ya, int yb) {
+  const float eps = 5.9604645e-8f;  // 2^-24
+  const float xlo = __fadd_rn((float)(xa - j0), 0.5f), xhi = __fadd_rn((float)(xb - j0), 0.5f);
+  const float ylo = __fadd_rn((float)(ya - i0), 0.5f), yhi = __fadd_rn((float)(yb - i0), 0.5f);
+  const float dylo = __fsub_rn(ylo, a.y), dyhi = __fsub_rn(yhi, a.y);
+  const float slo = __fmaf_rn(-a.w, dylo, a.x), shi = __fmaf_rn(-a.w, dyhi, a.x);
+  const float u00 = __fsub_rn(xlo, slo), u10 = __fsub_rn(xhi, slo);
+  const float u01 = __fsub_rn(xlo, shi), u11 = __fsub_rn(xhi, shi);
+  const float umin = fminf(fminf(u00, u10), fminf(u01, u11));
+  const float umax = fmaxf(fmaxf(u00, u10), fmaxf(u01, u11));
+  const float ady = fmaxf(fabsf(dylo), fabsf(dyhi)), ay = fabsf(a.y);
+  const float e1 = __fmul_rn(
+      4.f * eps, __fadd_rn(__fadd_rn(fmaxf(fabsf(umin), fabsf(umax)), fmaxf(fabsf(slo), fabsf(shi))),
+                           __fadd_rn(fabsf(a.x), __fmul_rn(fabsf(a.w), __fadd_rn(2.f * ady, ay)))));
+  const float e2 = __fmul_rn(4.f * eps, __fadd_rn(ady, ay));
+  const float m1 = umin > e1 ? __fsub_rn(umin, e1) : (umax < -e1 ? __fsub_rn(-umax, e1) : 0.f);
+  const float m2 = dylo > e2 ? __fsub_rn(dylo, e2) : (dyhi < -e2 ? __fsub_rn(-dyhi, e2) : 0.f);
+  const float t1 = __fmul_rn(a.z, m1), t2 = __fmul_rn(r22, m2);
+  return __fmaf_rn(t1, t1, __fmul_rn(t2, t2));
 }
 
-// Whether a record (a = rec_a, b = rec_b) can have a non-zero weight at any
-// pixel of the rectangle. Below an exponent of -126, 2^e is subnormal and
-// ex2.approx.ftz returns +0; the test uses -127, so the rounding of the bound
-// cannot drop a pixel whose weight is not exactly zero. With cut, pixels
-// beyond the ellipsoid threshold b.w are zero as well.
-__device__ __forceinline__ bool rect_live(const float4& a, const float4& b, int xa, int xb, int ya,
-                                          int yb, int cut) {
-  const float q = rect_q_lower_bound(a, b.x, xa, xb, ya, yb);
+// Whether a record (a = rec_a, b = rec_b, box origin (j0, i0)) can have a
+// non-zero weight at any pixel of the rectangle. Below an exponent of -126,
+// 2^e is subnormal and ex2.approx.ftz returns +0; the test uses -127, so the
+// rounding of the rasterizers' q cannot bring a dropped pixel's weight above
+// zero. With cut, pixels beyond the ellipsoid threshold b.w are zero as well.
+__device__ __forceinline__ bool rect_live(const float4& a, const float4& b, int j0, int i0, int xa,
+                                          int xb, int ya, int yb, int cut) {
+  const float q = rect_q_lower_bound(a, b.x, j0, i0, xa, xb, ya, yb);
   // without branches (bitwise &): lanes of a warp test different records
   return !(__fsub_rn(b.y, q) < -127.f) & !((cut != 0) & (q > __fmaf_rn(b.w, 1.0001f, 1e-6f)));
+}
+
+// Constants of one record over one footprint of at most 8 x 8 pixels whose
+// first pixel is (fi0, fj0). With col, row the pixel's offsets in the
+// footprint:
+//   t1 = r11 (col + nsh(row)) + nrs(row),  t2 = r22 dy(row),
+//   nsh(row) = kq row - s0q,  nrs(row) = a1 row + a0,  dy(row) = (row + nyh) + nyl.
+// S0 = s0q + s0l is the crossing at row 0 in double words (the footprint's
+// anchor is subtracted first, so S0 stays small), and kappa = kq + kl. s0q and
+// kq are rounded to the grid G = 2^(E - 21), E = floor(log2 B), B >= |S0| +
+// 8 |kappa| + 8: every nsh(row) and col + nsh(row) is then a multiple of G
+// below 2^22 G, so both are exact in FP32, and the low parts (s0l, kl, at most
+// G / 2 plus the double word's own) enter through nrs in FP32. t1 thus carries
+// a few ulps of relative error whatever r11 dx and r11 kappa dy are (see the
+// record comment above).
+struct ItemGeo {
+  float r11, kq, ns0q, a1, a0, nyh, nyl, r22;
+};
+
+__device__ __forceinline__ ItemGeo item_geo(const float4& a, const float4& b, const float4& c,
+                                            uint2 bx, int fj0, int fi0) {
+  const int j0 = bx.x & 0xffff, i0 = bx.y & 0xffff;
+  const float ox = __fadd_rn((float)(fj0 - j0), 0.5f), oy = __fadd_rn((float)(fi0 - i0), 0.5f);
+  // Xf = X - ox, Yf = Y - oy in double words (Knuth's 2Sum)
+  auto two_sum = [](float p, float q, float& s, float& e) {
+    s = __fadd_rn(p, q);
+    const float pp = __fsub_rn(s, q), qq = __fsub_rn(s, pp);
+    e = __fadd_rn(__fsub_rn(p, pp), __fsub_rn(q, qq));
+  };
+  float xh, xe, yh, ye;
+  two_sum(a.x, -ox, xh, xe);
+  two_sum(a.y, -oy, yh, ye);
+  const float xl = __fadd_rn(c.x, xe), yl = __fadd_rn(c.y, ye);
+  // S0 = Xf + kappa Yf: 2Prod of the high parts, the cross terms in FP32
+  const float ph = __fmul_rn(a.w, yh);
+  float pl = __fmaf_rn(a.w, yh, -ph);
+  pl = __fmaf_rn(a.w, yl, pl);
+  pl = __fmaf_rn(c.z, yh, pl);
+  float sh, se;
+  two_sum(xh, ph, sh, se);
+  const float sl = __fadd_rn(__fadd_rn(xl, pl), se);
+  // the grid: M = 1.5 * 2^23 * G rounds a value below 2^22 G to a multiple of G
+  const float B = __fadd_rn(__fadd_rn(fabsf(sh), __fmul_rn(8.f, fabsf(a.w))), 8.f);
+  const uint32_t eb = min(__float_as_uint(B) >> 23, 250u);
+  const float M = __uint_as_float(((eb + 2u) << 23) | (1u << 22));
+  const float s0q = __fsub_rn(__fadd_rn(sh, M), M);
+  const float kq = __fsub_rn(__fadd_rn(a.w, M), M);
+  const float s0l = __fadd_rn(sl, __fsub_rn(sh, s0q));
+  const float kl = __fadd_rn(c.z, __fsub_rn(a.w, kq));
+  ItemGeo g;
+  g.r11 = a.z;
+  g.kq = kq;
+  g.ns0q = -s0q;
+  g.a1 = __fmul_rn(a.z, kl);
+  g.a0 = -__fmul_rn(a.z, s0l);
+  g.nyh = -yh;
+  g.nyl = -yl;
+  g.r22 = b.x;
+  return g;
 }
 
 // ------------------------------------------------------------------ launchers

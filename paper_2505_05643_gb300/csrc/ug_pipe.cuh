@@ -1,6 +1,6 @@
 // Record pipeline of the tile rasterizers: one producer warp per CTA takes
 // tiles from the persistent work counter and gathers each tile's records
-// (sorted instance -> record id -> rec_a, rec_b, rec_box) into a ring of
+// (sorted instance -> record id -> rec_a, rec_b, rec_c, rec_box) into a ring of
 // shared-memory stages; the CTA's other warps consume the stages. Full/empty
 // handshakes are mbarriers (arrive: release, try_wait: acquire, CTA scope),
 // so the gathers of the next batches overlap the arithmetic of the current
@@ -130,6 +130,7 @@ template <int TILE, bool RAW>
 struct RecStage {
   float4 a[kBatch];
   float4 b[kBatch];
+  float4 c[kBatch];
   uint2 box[kBatch];
   uint32_t rid[kBatch];
   uint32_t mask[RAW ? kBatch : 1];
@@ -315,6 +316,7 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars<NS>& b
       if (r < cnt) {
         cp_async16(&S.a[r], v.rec_a + rid[q]);
         cp_async16(&S.b[r], v.rec_b + rid[q]);
+        cp_async16(&S.c[r], v.rec_c + rid[q]);
         cp_async8(&S.box[r], v.rec_box + rid[q]);
         if (RID) S.rid[r] = rid[q];
         if constexpr (RAW) {

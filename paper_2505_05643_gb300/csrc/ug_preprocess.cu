@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(256)
     h->fwd_masks = 0;
     h->stall_test = 0;
     h->kept64 = 0;
+    h->origin_reach = 0.f;
     s_run = 0;
   }
   __syncthreads();
@@ -85,6 +86,12 @@ __global__ void __launch_bounds__(256)
       ok = ok && q.width >= 1 && q.height >= 1 && q.width <= 16384 && q.height <= 16384;
       ok = ok && q.pixel_offset >= 0 && q.pixel_offset + (int64_t)q.width * q.height <= total_px;
       if (!ok) dev_fail(v.hdr, UG_ERR_INVALID_PLANE, p);
+      if (ok) {  // |o| rounded up (non-negative floats order like their bits)
+        const float r = __fsqrt_ru(__fmaf_ru(q.origin[2], q.origin[2],
+                                             __fmaf_ru(q.origin[1], q.origin[1],
+                                                       __fmul_ru(q.origin[0], q.origin[0]))));
+        atomicMax(reinterpret_cast<int*>(&v.hdr->origin_reach), __float_as_int(r));
+      }
       PlaneDev d;
       for (int k = 0; k < 3; ++k) {
         d.o[k] = q.origin[k];
@@ -184,15 +191,29 @@ struct LaneGauss {
   bool active, use64;
 };
 
+// The extended-precision branch takes a Gaussian when its axis-ratio proxy
+// exceeds `ratio`, or when ||F||_F (|mu| + the planes' largest |o|) exceeds
+// `reach`: the latter bounds, in units of the Gaussian's smallest scale, how
+// far the FP32 difference mu - o and the products F^T (mu - o) are from the
+// numbers they cancel to near the Gaussian, so it bounds the FP32 geometry's
+// error in t (a few 1e-7 times the bound).
 template <int COV>
 __device__ __forceinline__ void lane_setup(const ug_gaussians& g, int64_t n, int64_t i, float beta,
-                                           float ratio, LaneGauss& L) {
+                                           float ratio, float reach, float oreach, LaneGauss& L) {
   L.active = i < n;
   L.use64 = false;
   if (!L.active) return;
   load_params(g, n, i, COV, L.prm);
   make_factor<float, COV>(L.prm, beta, L.ff);
-  L.use64 = !(axis_ratio_proxy<COV>(L.ff) <= ratio);
+  float fro = 0.f;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) fro = fmaf(L.ff.F[r][k], L.ff.F[r][k], fro);
+  const float mu = sqrtf(fmaf(L.prm.mu[2], L.prm.mu[2],
+                              fmaf(L.prm.mu[1], L.prm.mu[1], L.prm.mu[0] * L.prm.mu[0])));
+  const float size = sqrtf(fro) * (mu + oreach) * 1.001f;
+  L.use64 = !(axis_ratio_proxy<COV>(L.ff) <= ratio) || !(size <= reach);
 }
 
 constexpr int kCullPlanesSmem = 64;  // planes staged in shared memory per pass
@@ -221,8 +242,8 @@ struct CullWarp {
 // queue and take the full test 32 at a time, every lane busy.
 template <int COV>
 __global__ void __launch_bounds__(256)
-    k_cull(ug_gaussians g, int64_t n, int P, float chi2, float beta, float ratio, int64_t chunks,
-           WsView v) {
+    k_cull(ug_gaussians g, int64_t n, int P, float chi2, float beta, float ratio, float reach,
+           int64_t chunks, WsView v) {
   __shared__ CullPlane s_pl[kCullPlanesSmem];
   __shared__ CullWarp s_w[256 / 32];
   if (dev_failed(v.hdr)) return;
@@ -233,7 +254,8 @@ __global__ void __launch_bounds__(256)
   LaneGauss L;
   L.active = false;
   L.use64 = false;
-  if (live_warp) lane_setup<COV>(g, n, chunk * kChunk + lane, beta, ratio, L);
+  if (live_warp)
+    lane_setup<COV>(g, n, chunk * kChunk + lane, beta, ratio, reach, v.hdr->origin_reach, L);
   float thr1;  // first test: lo^2 <= thr1
   {
     float Fi[3][3];
@@ -396,59 +418,50 @@ __global__ void __launch_bounds__(256) k_list(int P, int64_t chunks, WsView v) {
 
 // ------------------------------------------------------------------ 4. records
 
+// Split of x - n (n an integer) into a high part and the remainder.
+__device__ __forceinline__ void split_rel(float x, int n, float& h, float& l) {
+  const float b = -(float)n;
+  h = __fadd_rn(x, b);
+  const float xp = __fsub_rn(h, b), bp = __fsub_rn(h, xp);
+  l = __fadd_rn(__fsub_rn(x, xp), __fsub_rn(b, bp));
+}
+__device__ __forceinline__ void split_rel(dd x, int n, float& h, float& l) {
+  const dd r = dd_add(x, dd((float)(-n)));
+  h = r.hi;
+  l = r.lo;
+}
+__device__ __forceinline__ void split_hl(float x, float& h, float& l) {
+  h = x;
+  l = 0.f;
+}
+__device__ __forceinline__ void split_hl(dd x, float& h, float& l) {
+  h = x.hi;
+  l = x.lo;
+}
+
+// The record (see ug_internal.cuh) and the inputs of the backward chain
+// (kChainFloats floats: q1[3], q2[3], nh[3], rho3, ew[3], 0, 0, 0).
 template <typename T>
-__device__ __forceinline__ void write_record(const PairRec<T>& rc, const PlaneDev& pl,
-                                             const PairBox& pb, const GaussParams& prm,
-                                             float chi2, WsView& v, uint32_t slot, float4& ra,
-                                             float4& rb) {
-  const float xs_j = (float)(rc.xs1 * (T)pl.inv_pu + (T)pl.half_w);
-  const float xs_i = (float)(rc.xs2 * (T)pl.inv_pv + (T)pl.half_h);
-  const float q0 = (float)rc.q0;
+__device__ __forceinline__ void write_record(const PairLsq<T>& L, const PairBox& pb,
+                                             const GaussParams& prm, float chi2, WsView& v,
+                                             uint32_t slot) {
+  float xh, xl, yh, yl, kh, kl;
+  split_rel(L.X, pb.j0, xh, xl);
+  split_rel(L.Y, pb.i0, yh, yl);
+  split_hl(L.kappa, kh, kl);
+  const float q0 = __fmul_rn(L.rho3, L.rho3);
   const float lw2 = log2_sigmoid(prm.logit) - kHalfLog2e * q0;
   const float ethr = kHalfLog2e * (chi2 - q0);
-  ra = make_float4(xs_j, xs_i, (float)rc.r11, (float)rc.r12);
-  rb = make_float4((float)rc.r22, lw2, prm.c, ethr);
-  v.rec_a[slot] = ra;
-  v.rec_b[slot] = rb;
+  v.rec_a[slot] = make_float4(xh, yh, L.r11, kh);
+  v.rec_b[slot] = make_float4(L.r22, lw2, prm.c, ethr);
+  v.rec_c[slot] = make_float4(xl, yl, kl, 0.f);
   v.rec_box[slot] = make_uint2((uint32_t)pb.j0 | ((uint32_t)pb.j1 << 16),
                                (uint32_t)pb.i0 | ((uint32_t)pb.i1 << 16));
-}
-
-// Inputs of the backward chain of one record (kChainFloats floats). For the
-// extended-precision records the forward keeps them, so the chain does not
-// repeat the double-word geometry; the chain recomputes the others in FP32:
-//   [0..8] b1, b2, b3 = F^T u, F^T v, F^T n;  [9, 10] kappa;  [11] k = m3 / S33;
-//   [12] m3;  [13..18] A11, A12, A22 of the in-plane precision A = [b1 b2]^T
-//   [b1 b2] as double words (high, low; the 2x2 solve of the chain needs them
-//   beyond FP32 for thin Gaussians);  [19] det A.
-__device__ __forceinline__ void split_dw(float x, float* d) {
-  d[0] = x;
-  d[1] = 0.f;
-}
-__device__ __forceinline__ void split_dw(dd x, float* d) {
-  d[0] = x.hi;
-  d[1] = x.lo;
-}
-
-template <typename T>
-__device__ __forceinline__ void chain_inputs(const PairRec<T>& rc, const PairGeo<T>& gg,
-                                             float c[kChainFloats]) {
-#pragma unroll
-  for (int j = 0; j < 3; ++j)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) c[3 * j + a] = (float)rc.b[j][a];
-  c[9] = (float)rc.kappa[0];
-  c[10] = (float)rc.kappa[1];
-  c[11] = (float)rc.k;
-  c[12] = (float)gg.m[2];
-  const T* B1 = rc.b[0];
-  const T* B2 = rc.b[1];
-  const T A11 = rc.nb1 * rc.nb1, A12 = B1[0] * B2[0] + B1[1] * B2[1] + B1[2] * B2[2];
-  const T A22 = B2[0] * B2[0] + B2[1] * B2[1] + B2[2] * B2[2];
-  split_dw(A11, c + 13);
-  split_dw(A12, c + 15);
-  split_dw(A22, c + 17);
-  c[19] = (float)(rc.cr * rc.cr);
+  float4* d4 = reinterpret_cast<float4*>(v.rec_chain + (size_t)slot * kChainFloats);
+  d4[0] = make_float4(L.q1[0], L.q1[1], L.q1[2], L.q2[0]);
+  d4[1] = make_float4(L.q2[1], L.q2[2], L.nh[0], L.nh[1]);
+  d4[2] = make_float4(L.nh[2], L.rho3, L.ew[0], L.ew[1]);
+  d4[3] = make_float4(L.ew[2], 0.f, 0.f, 0.f);
 }
 
 __device__ __forceinline__ bool box_empty(uint2 b) {
@@ -482,18 +495,9 @@ __global__ void __launch_bounds__(256)
     const PairBox pb = pair_box<T, COV>(f, pl, chi2, gg);
     v.rec_plane[slot] = e.y;
     if (pb.visible) {
-      PairRec<T> rc;
-      pair_record<T, COV>(f, pl, gg, rc);
-      float4 ra, rb;
-      write_record<T>(rc, pl, pb, prm, chi2, v, slot, ra, rb);
-      if (is_ext<T>::value) {  // the chain recomputes normal-precision records in FP32
-        float c[kChainFloats];
-        chain_inputs<T>(rc, gg, c);
-        float4* d4 = reinterpret_cast<float4*>(v.rec_chain + (size_t)slot * kChainFloats);
-#pragma unroll
-        for (int q = 0; q < kChainFloats / 4; ++q)
-          d4[q] = make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
-      }
+      PairLsq<T> L;
+      pair_lsq<T, COV>(f, pl, gg, L);
+      write_record<T>(L, pb, prm, chi2, v, slot);
       npx += (unsigned long long)(pb.j1 - pb.j0 + 1) * (unsigned long long)(pb.i1 - pb.i0 + 1);
       kept++;
     } else {
@@ -553,8 +557,8 @@ __device__ __forceinline__ bool box_tile_live(const float4& a, const float4& b, 
   const uint32_t dy = k / nx, dx = k - dy * nx;
   const int tile = 1 << ts, tx = (int)(tx0 + dx), ty = (int)(ty0 + dy);
   const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
-  return rect_live(a, b, max(j0, tx * tile), min(j1, tx * tile + tile - 1), max(i0, ty * tile),
-                   min(i1, ty * tile + tile - 1), cut);
+  return rect_live(a, b, j0, i0, max(j0, tx * tile), min(j1, tx * tile + tile - 1),
+                   max(i0, ty * tile), min(i1, ty * tile + tile - 1), cut);
 }
 
 // Largest lane l whose non-decreasing per-lane value pre[l] is <= o.
@@ -769,7 +773,7 @@ static void launch_pre_cov(const ug_plan* plan, const ug_gaussians* g, WsView v,
   const int64_t wblocks = (chunks * 32 + 255) / 256;
   if (chunks > 0)
     k_cull<COV><<<(unsigned)wblocks, 256, 0, s>>>(*g, plan->n, P, c.chi2, c.beta, c.fp64_ratio,
-                                                  chunks, v);
+                                                  c.fp32_reach, chunks, v);
   const int64_t entries = chunks * P;
   const int64_t nblk = scan_blocks(entries);
   CandLoad ld{v.mask, v.gflag, P};
@@ -806,86 +810,48 @@ cudaError_t launch_preprocess(const ug_plan* plan, const ug_gaussians* g, WsView
 }
 
 // ------------------------------------------------------------------ backward chain
-// Per-record accumulators written by the backward rasterizer (8 floats):
-//   [0] sum r w        (dL/dc)
-//   [1] sum gw w       (gw = dL/dw = r (c - C))
-//   [2] sum gw w t1    [3] sum gw w t2
-//   [4] sum gw w t1 dx [5] sum gw w t1 dy [6] sum gw w t2 dy
-// With w = 2^(lw2 - t1^2 - t2^2) these give
-//   dL/dlw2 = ln2 [1];  dL/dr11 = -2 ln2 [4];  dL/dr12 = -2 ln2 [5];
-//   dL/dr22 = -2 ln2 [6];  dL/dxs_j = 2 ln2 r11 [2];
-//   dL/dxs_i = 2 ln2 (r12 [2] + r22 [3]).
+// Per-record accumulators written by the backward rasterizer (8 floats), with
+// g = w dL/dw at each pixel (dL/dw = r (c - C)):
+//   [0] sum r w  (dL/dc)   [1] sum g   [2] sum g t1   [3] sum g t2
+//   [4] sum g t1^2         [5] sum g t1 t2            [6] sum g t2^2
+// In the record's least-squares frame (ug_geometry.cuh) the residual of a
+// pixel is rho = F^T (X_w - mu) = (q1 t1 + q2 t2) / sc - rho3 nh, sc =
+// sqrt(log2(e) / 2), and w = alpha exp(-|rho|^2 / 2), so
+//   dL/dmu = F sum g rho,
+//   dL/dF  = -sum g (X_w - mu) rho^T,  X_w - mu = pu dx u + pv dy v + ew,
+// with (dx, dy) = R^-1 (t1, t2) for the pixel-unit factor R = [[r11, r12],
+// [0, r22]]; every sum is a combination of the seven above.
 struct ChainOut {
   float gmu[3];
   float gF[3][3];
   float glw2;
 };
 
-// Chain of one record's accumulators to (m, b1, b2, b3) and on to the
-// Gaussian's mean and factor F, from the record's stored geometry (ch, see
-// write_chain_inputs) and render data (r11, r12, r22). FP32, except the 2x2
-// solve gamma = A^-1 dL/dx*, whose matrix is ill-conditioned for thin
-// Gaussians: its numerators are formed in double words from the stored A.
 __device__ __forceinline__ void chain_record(const float* ch, float r11, float r12, float r22,
-                                             const PlaneDev& pl, const float* acc, ChainOut& o) {
-  const float ln2 = kLn2;
-  const float a_p = acc[1], a_t1 = acc[2], a_t2 = acc[3];
-  const float a_t1dx = acc[4], a_t1dy = acc[5], a_t2dy = acc[6];
-  const float g_r11 = -2.f * ln2 * a_t1dx;
-  const float g_r12 = -2.f * ln2 * a_t1dy;
-  const float g_r22 = -2.f * ln2 * a_t2dy;
-  const float g_xsj = 2.f * ln2 * r11 * a_t1;
-  const float g_xsi = 2.f * ln2 * (r12 * a_t1 + r22 * a_t2);
-  const float g_lw2 = ln2 * a_p;
-  const float pu = pl.pu, pv = pl.pv;
-  const float gx1 = g_xsj * pl.inv_pu, gx2 = g_xsi * pl.inv_pv;
-  const float c = kHalfLog2e;
-  const float g_q0 = -c * g_lw2;
-  // Cholesky backward of M = c D A D (M11 = r11^2, M12 = r11 r12, M22 = r12^2 + r22^2)
-  const float i22 = 1.f / r22, i11 = 1.f / r11;
-  const float gM22 = g_r22 * i22 * 0.5f;
-  const float gr12 = g_r12 - g_r22 * r12 * i22;
-  const float gM12 = gr12 * i11;
-  const float gr11 = g_r11 - gr12 * r12 * i11;
-  const float gM11 = gr11 * i11 * 0.5f;
-  float gA11 = c * pu * pu * gM11, gA12 = c * pu * pv * gM12, gA22 = c * pv * pv * gM22;
-  // x* = m12 + m3 kappa, kappa = A^-1 s;  q0 = m3^2 (P33 - s^T A^-1 s)
-  const dd A11(ch[13], ch[14]), A12(ch[15], ch[16]), A22(ch[17], ch[18]);
-  const float det = ch[19];
-  const float gam0 = __fdiv_rn((float)(dd_mul(A22, gx1) - dd_mul(A12, gx2)), det);
-  const float gam1 = __fdiv_rn((float)(dd_mul(A11, gx2) - dd_mul(A12, gx1)), det);
-  float b1[3], b2[3], b3[3];
+                                             const PlaneDev& pl, const float* F, const float* acc,
+                                             ChainOut& o) {
+  const float isc = 1.17741002251547469101f;  // 1 / sqrt(log2(e) / 2)
+  const float q1[3] = {ch[0], ch[1], ch[2]}, q2[3] = {ch[3], ch[4], ch[5]};
+  const float nh[3] = {ch[6], ch[7], ch[8]}, rho3 = ch[9];
+  const float ew[3] = {ch[10], ch[11], ch[12]};
+  const float Sg = acc[1], S1 = acc[2], S2 = acc[3], S11 = acc[4], S12 = acc[5], S22 = acc[6];
+  float G[3], G1[3], G2[3], Gx[3], Gy[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    b1[a] = ch[a];
-    b2[a] = ch[3 + a];
-    b3[a] = ch[6 + a];
-  }
-  const float kp0 = ch[9], kp1 = ch[10], kk = ch[11], m3 = ch[12];
-  const float gm1 = gx1, gm2 = gx2;
-  const float gm3 = gx1 * kp0 + gx2 * kp1 + 2.f * kk * g_q0;
-  const float m3sq_gq0 = m3 * m3 * g_q0;
-  const float gs0 = m3 * gam0 - 2.f * m3sq_gq0 * kp0;
-  const float gs1 = m3 * gam1 - 2.f * m3sq_gq0 * kp1;
-  const float gP33 = m3sq_gq0;
-  gA11 += -m3 * gam0 * kp0 + m3sq_gq0 * kp0 * kp0;
-  gA12 += -m3 * (gam0 * kp1 + gam1 * kp0) + 2.f * m3sq_gq0 * kp0 * kp1;
-  gA22 += -m3 * gam1 * kp1 + m3sq_gq0 * kp1 * kp1;
-  float gb1[3], gb2[3], gb3[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    gb1[a] = 2.f * gA11 * b1[a] + gA12 * b2[a] + gs0 * b3[a];
-    gb2[a] = gA12 * b1[a] + 2.f * gA22 * b2[a] + gs1 * b3[a];
-    gb3[a] = gs0 * b1[a] + gs1 * b2[a] + 2.f * gP33 * b3[a];
+    G[a] = fmaf(isc, fmaf(q1[a], S1, q2[a] * S2), -rho3 * nh[a] * Sg);    // sum g rho
+    G1[a] = fmaf(isc, fmaf(q1[a], S11, q2[a] * S12), -rho3 * nh[a] * S1);  // sum g rho t1
+    G2[a] = fmaf(isc, fmaf(q1[a], S12, q2[a] * S22), -rho3 * nh[a] * S2);  // sum g rho t2
+    Gy[a] = G2[a] / r22;                                                    // sum g rho dy
+    Gx[a] = (G1[a] - r12 * Gy[a]) / r11;                                    // sum g rho dx
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const float u = pl.u[k], vv = pl.v[k], nn = pl.n[k];
-    o.gmu[k] = gm1 * u + gm2 * vv + gm3 * nn;
+    o.gmu[k] = fmaf(F[3 * k + 2], G[2], fmaf(F[3 * k + 1], G[1], F[3 * k] * G[0]));
+    const float pu_u = pl.pu * pl.u[k], pv_v = pl.pv * pl.v[k];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) o.gF[k][a] = u * gb1[a] + vv * gb2[a] + nn * gb3[a];
+    for (int a = 0; a < 3; ++a) o.gF[k][a] = -fmaf(pu_u, Gx[a], fmaf(pv_v, Gy[a], ew[k] * G[a]));
   }
-  o.glw2 = g_lw2;
+  o.glw2 = kLn2 * Sg;
 }
 
 // Parameter gradient of one record (12 floats: mean[3], tri[6] or
@@ -941,17 +907,14 @@ __device__ __forceinline__ void record_param_grad(const ChainOut& o, const Facto
   }
 }
 
-// One thread per record of the list's part (0: normal precision, whose
-// geometry is recomputed here in FP32; 1: extended precision, whose geometry
-// the forward stored).
+// One thread per record (both parts of the work list), from the chain inputs
+// the record kernels stored.
 template <int COV>
 __global__ void __launch_bounds__(256)
-    k_chain(ug_gaussians g, int64_t n, float chi2, float beta, WsView v, int part) {
+    k_chain(ug_gaussians g, int64_t n, float beta, WsView v) {
   if (dev_failed(v.hdr)) return;
-  const uint32_t slots = v.hdr->slots, n64 = v.hdr->slots64;
-  const uint32_t begin = part == 0 ? 0u : slots - n64;
-  const uint32_t end = part == 0 ? slots - n64 : slots;
-  for (uint32_t k = begin + blockIdx.x * blockDim.x + threadIdx.x; k < end;
+  const uint32_t slots = v.hdr->slots;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < slots;
        k += gridDim.x * blockDim.x) {
     const uint4 e = v.list[k];
     const uint32_t slot = e.z;
@@ -968,27 +931,21 @@ __global__ void __launch_bounds__(256)
       Factor<float> f;
       make_factor<float, COV>(prm, beta, f);
       float ch[kChainFloats];
-      if (part == 0) {
-        PairGeo<float> gg;
-        pair_box<float, COV>(f, pl, chi2, gg);
-        PairRec<float> rc;
-        pair_record<float, COV>(f, pl, gg, rc);
-        chain_inputs<float>(rc, gg, ch);
-      } else {
-        const float4* c4 =
-            reinterpret_cast<const float4*>(v.rec_chain + (size_t)slot * kChainFloats);
+      const float4* c4 = reinterpret_cast<const float4*>(v.rec_chain + (size_t)slot * kChainFloats);
 #pragma unroll
-        for (int q = 0; q < kChainFloats / 4; ++q) {
-          const float4 t = c4[q];
-          ch[4 * q] = t.x;
-          ch[4 * q + 1] = t.y;
-          ch[4 * q + 2] = t.z;
-          ch[4 * q + 3] = t.w;
-        }
+      for (int q = 0; q < kChainFloats / 4; ++q) {
+        const float4 t = c4[q];
+        ch[4 * q] = t.x;
+        ch[4 * q + 1] = t.y;
+        ch[4 * q + 2] = t.z;
+        ch[4 * q + 3] = t.w;
       }
+      float F[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) F[q] = f.F[q / 3][q % 3];
       const float4 ra = v.rec_a[slot], rb = v.rec_b[slot];
       ChainOut o;
-      chain_record(ch, ra.z, ra.w, rb.x, pl, acc, o);
+      chain_record(ch, ra.z, ra.z * ra.w, rb.x, pl, F, acc, o);
       record_param_grad<float, COV>(o, f, prm, acc[0], out);
     }
     float4* dst = reinterpret_cast<float4*>(v.rec_pgrad + (size_t)slot * 12);
@@ -1069,8 +1026,7 @@ static void launch_chain_cov(const ug_plan* plan, const ug_gaussians* g, WsView 
                              const ug_gaussian_grads* grads, cudaStream_t s) {
   const ug_config& c = plan->cfg;
   const unsigned lg = list_grid(plan->record_capacity);
-  k_chain<COV><<<lg, 256, 0, s>>>(*g, plan->n, c.chi2, c.beta, v, 0);
-  k_chain<COV><<<lg, 256, 0, s>>>(*g, plan->n, c.chi2, c.beta, v, 1);
+  k_chain<COV><<<lg, 256, 0, s>>>(*g, plan->n, c.beta, v);
   const int64_t chunks = plan->chunks;
   if (chunks > 0)
     k_gather<COV><<<(unsigned)((chunks * 32 + 255) / 256), 256, 0, s>>>(plan->n, plan->num_planes,

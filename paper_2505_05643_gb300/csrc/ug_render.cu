@@ -15,10 +15,12 @@
 // and whether the box covers the whole footprint (then no per-pixel box test
 // is needed). Each (record, footprint) that passes is one work item.
 //
-// Per pixel and record:
-//   dx = j + 1/2 - xs_j, dy = i + 1/2 - xs_i, t1 = r11 dx + r12 dy, t2 = r22 dy,
-//   w = 2^(lw2 - t1^2 - t2^2)      (= alpha exp(-q/2), Eq. mahalanobis-3d)
-// evaluated in packed FP32x2 arithmetic, two pixels per instruction.
+// Per pixel and record (see the record and item_geo in ug_internal.cuh):
+//   t1 = r11 (col - S(row)) with the row's crossing S(row) held in two parts,
+//   t2 = r22 dy(row),  w = 2^(lw2 - t1^2 - t2^2)  (= alpha exp(-q/2), Eq.
+//   mahalanobis-3d),
+// evaluated in packed FP32x2 arithmetic, two pixels per instruction; col and
+// row are the pixel's offsets in its footprint.
 //
 // Forward: the producer warp also tests every record of a stage against the
 // tile's 8x8 footprints once its copies have landed (byte f of a 32-bit word
@@ -58,14 +60,14 @@ __device__ __forceinline__ void footprint_origin(int f, int fx_count, int fh, in
 // fi0 + fh - 1]: bit 0 live, bit 1 the box covers the footprint.
 // Branch-free: the lanes of a warp test different records.
 template <int CUT>
-__device__ __forceinline__ uint32_t classify(const float4& a, const float4& c, uint2 bx, int fj0,
+__device__ __forceinline__ uint32_t classify(const float4& a, const float4& b, uint2 bx, int fj0,
                                              int fi0, int fh) {
   const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
   const int fj1 = fj0 + 7, fi1 = fi0 + fh - 1;
   const int xa = max(fj0, j0), xb = min(fj1, j1), ya = max(fi0, i0), yb = min(fi1, i1);
   // overlap, and not every weight in it an FP32 zero (the bound of an empty
   // overlap is finite and ignored)
-  const bool live = (xa <= xb) & (ya <= yb) & rect_live(a, c, xa, xb, ya, yb, CUT);
+  const bool live = (xa <= xb) & (ya <= yb) & rect_live(a, b, j0, i0, xa, xb, ya, yb, CUT);
   const bool full = (j0 <= fj0) & (j1 >= fj1) & (i0 <= fi0) & (i1 >= fi1);
   return (uint32_t)live | ((uint32_t)(live & full) << 1);
 }
@@ -81,14 +83,16 @@ __device__ __forceinline__ uint32_t clip_box(uint2 bx, int fj0, int fi0, int fh)
 
 // ------------------------------------------------------------------ forward
 // A warp's current chunk of up to 32 work items (structure of arrays, one
-// slot per lane of the builder; values in pairs for the FP32x2 arithmetic).
-// Slots past the last item, up to a multiple of the lane groups, hold inert
-// items (lw2 = -inf), so that every group runs the same number of items.
+// slot per lane of the builder; the item_geo constants in pairs for the
+// FP32x2 arithmetic). Slots past the last item, up to a multiple of the lane
+// groups, hold inert items (lw2 = -inf), so that every group runs the same
+// number of items.
 struct FwdChunk {
-  float4 dx[2][32];  // dx of the footprint's columns 0..3 and 4..7
-  float4 p0[32];     // r11, r11, -x*_i, -x*_i
-  float4 p1[32];     // r12, r12, r22, r22
-  float4 p2[32];     // lw2, lw2, c, c
+  float4 p0[32];     // r11, r11, kq, kq
+  float4 p1[32];     // -s0q, -s0q, a1, a1
+  float4 p2[32];     // a0, a0, nyh, nyh
+  float4 p3[32];     // nyl, nyl, r22, r22
+  float4 p4[32];     // lw2, lw2, c, c
   float4 lc[2][32];  // partial items: lw2 in the box's columns, -inf outside
   uint32_t rows[32]; // partial items: bit y set for the box's rows
   float thr[32];     // ellipsoid threshold (cut-off by ellipsoid)
@@ -106,7 +110,7 @@ struct FwdShape {
   // resident blocks asked of the compiler (at most 64 registers a thread for
   // the 16x16 tile's 160 threads, so that shared memory, not registers,
   // limits the blocks per SM)
-  static constexpr int kMinBlocks = NT >= 160 ? 6 : 1;
+  static constexpr int kMinBlocks = NT >= 160 ? 5 : 1;
 };
 
 template <int TILE, int NW>
@@ -121,49 +125,35 @@ struct FwdSmem {
 // the special-function unit takes it as is: w = 2^e. Pixels outside the box
 // (PARTIAL) or the ellipsoid (CUT) get e = -inf, whose ex2 is +0.
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); }
 
-template <int NP>
-__device__ __forceinline__ void load_pairs(const float4 (&src)[2][32], int e, int cp0,
-                                           float2 (&out)[NP]) {
-  if (NP == 4) {
-    const float4 u = src[0][e], w = src[1][e];
-    out[0] = make_float2(u.x, u.y);
-    out[1] = make_float2(u.z, u.w);
-    out[NP > 2 ? 2 : 0] = make_float2(w.x, w.y);
-    out[NP > 3 ? 3 : 0] = make_float2(w.z, w.w);
-  } else if (NP == 2) {
-    const float4 u = src[cp0 >> 1][e];
-    out[0] = make_float2(u.x, u.y);
-    out[NP > 1 ? 1 : 0] = make_float2(u.z, u.w);
-  } else {
-    const float4 u = src[cp0 >> 1][e];
-    out[0] = (cp0 & 1) ? make_float2(u.z, u.w) : make_float2(u.x, u.y);
-  }
-}
-
-// One lane, one work item: row y of the footprint (pixel centre py), column
-// pairs cp0 .. cp0 + NP - 1.
+// One lane, one work item: footprint row k2 = (row, row), column pairs cp0 ..
+// cp0 + NP - 1 (col2[p] = their two column offsets).
 template <int CUT, bool PARTIAL, int NP>
-__device__ __forceinline__ void fwd_item(const FwdChunk& C, int e, float py, int y, int cp0,
-                                         float2* sa, float2* sc) {
-  const float4 p0 = C.p0[e], p1 = C.p1[e], p2 = C.p2[e];
-  float2 dx[NP];
-  load_pairs<NP>(C.dx, e, cp0, dx);
-  const float2 r11 = make_float2(p0.x, p0.y), r12 = make_float2(p1.x, p1.y);
-  const float2 r22 = make_float2(p1.z, p1.w), cc = make_float2(p2.z, p2.w);
-  const float2 dy = __fadd2_rn(make_float2(py, py), make_float2(p0.z, p0.w));
-  const float2 r12dy = __fmul2_rn(r12, dy);
-  const float2 t2 = __fmul2_rn(r22, dy);
+__device__ __forceinline__ void fwd_item(const FwdChunk& C, int e, float2 k2, int y, int cp0,
+                                         const float2* col2, float2* sa, float2* sc) {
+  const float4 p0 = C.p0[e], p1 = C.p1[e], p2 = C.p2[e], p3 = C.p3[e], p4 = C.p4[e];
+  const float2 r11 = lo2(p0), cc = hi2(p4);
+  const float2 nsh = __ffma2_rn(hi2(p0), k2, lo2(p1));  // kq row - s0q (exact)
+  const float2 nrs = __ffma2_rn(hi2(p1), k2, lo2(p2));  // a1 row + a0
+  const float2 dy = __fadd2_rn(__fadd2_rn(k2, hi2(p2)), lo2(p3));
+  const float2 t2 = __fmul2_rn(hi2(p3), dy);
   float2 c2[NP];  // lw2 - t2^2 per column pair
   if (PARTIAL) {
-    float2 lw[NP];
-    load_pairs<NP>(C.lc, e, cp0, lw);
+    float4 lw4[2];
+    lw4[0] = C.lc[0][e];
+    lw4[1] = C.lc[1][e];
     float2 nt2sq = __fmul2_rn(neg2(t2), t2);
     if (!((C.rows[e] >> y) & 1u)) nt2sq = make_float2(-INFINITY, -INFINITY);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) c2[p] = __fadd2_rn(lw[p], nt2sq);
+    for (int p = 0; p < NP; ++p) {
+      const int q = cp0 + p;
+      const float4 l = lw4[q >> 1];
+      c2[p] = __fadd2_rn((q & 1) ? hi2(l) : lo2(l), nt2sq);
+    }
   } else {
-    const float2 c = __ffma2_rn(neg2(t2), t2, make_float2(p2.x, p2.y));
+    const float2 c = __ffma2_rn(neg2(t2), t2, lo2(p4));
 #pragma unroll
     for (int p = 0; p < NP; ++p) c2[p] = c;
   }
@@ -171,7 +161,8 @@ __device__ __forceinline__ void fwd_item(const FwdChunk& C, int e, float py, int
   if (CUT) thr = C.thr[e];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    const float2 t1 = __ffma2_rn(r11, dx[p], r12dy);
+    const float2 d = __fadd2_rn(col2[p], nsh);  // col - S(row), exact
+    const float2 t1 = __ffma2_rn(r11, d, nrs);
     float2 e2 = __ffma2_rn(neg2(t1), t1, c2[p]);  // lw2 - q
     if (CUT) {
       const float2 q = __ffma2_rn(t1, t1, __fmul2_rn(t2, t2));
@@ -184,27 +175,25 @@ __device__ __forceinline__ void fwd_item(const FwdChunk& C, int e, float py, int
   }
 }
 
-// Chunk slot `lane` from the record at stage index r; real = false makes the
-// slot inert (lw2 = -inf: every weight is +0).
+// Chunk slot `lane` from the record (a, b, c, bx); real = false makes the slot
+// inert (lw2 = -inf: every weight is +0).
 template <int CUT, bool PARTIAL>
 __device__ __forceinline__ void fwd_build(FwdChunk& W, int lane, bool real, const float4& a,
-                                          const float4& b, uint2 bx, int fj0, int fi0) {
+                                          const float4& b, const float4& c, uint2 bx, int fj0,
+                                          int fi0) {
   const float lw = real ? b.y : -INFINITY;
-  float d[8];
-  const float x0 = (float)fj0 + 0.5f;  // column centres x0 + c are exact
-#pragma unroll
-  for (int c = 0; c < 8; ++c) d[c] = (x0 + (float)c) - a.x;
-  W.dx[0][lane] = make_float4(d[0], d[1], d[2], d[3]);
-  W.dx[1][lane] = make_float4(d[4], d[5], d[6], d[7]);
-  W.p0[lane] = make_float4(a.z, a.z, -a.y, -a.y);
-  W.p1[lane] = make_float4(a.w, a.w, b.x, b.x);
-  W.p2[lane] = make_float4(lw, lw, b.z, b.z);
+  const ItemGeo g = item_geo(a, b, c, bx, fj0, fi0);
+  W.p0[lane] = make_float4(g.r11, g.r11, g.kq, g.kq);
+  W.p1[lane] = make_float4(g.ns0q, g.ns0q, g.a1, g.a1);
+  W.p2[lane] = make_float4(g.a0, g.a0, g.nyh, g.nyh);
+  W.p3[lane] = make_float4(g.nyl, g.nyl, g.r22, g.r22);
+  W.p4[lane] = make_float4(lw, lw, b.z, b.z);
   if (PARTIAL) {
     const uint32_t cl = clip_box(bx, fj0, fi0, 8);
     const int cx0 = cl & 0xff, cx1 = (cl >> 8) & 0xff, ry0 = (cl >> 16) & 0xff, ry1 = cl >> 24;
     float l[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) l[c] = ((c >= cx0) & (c <= cx1)) ? lw : -INFINITY;
+    for (int q = 0; q < 8; ++q) l[q] = ((q >= cx0) & (q <= cx1)) ? lw : -INFINITY;
     W.lc[0][lane] = make_float4(l[0], l[1], l[2], l[3]);
     W.lc[1][lane] = make_float4(l[4], l[5], l[6], l[7]);
     W.rows[lane] = (2u << ry1) - (1u << ry0);
@@ -232,13 +221,13 @@ struct FwdPrep {
       const int r = lane + 32 * q;
       uint32_t m = 0;
       if (r < h.cnt) {
-        const float4 a = S.a[r], c = S.b[r];
+        const float4 a = S.a[r], b = S.b[r];
         const uint2 bx = S.box[r];
 #pragma unroll
         for (int f = 0; f < T::NF; ++f) {
           int fj0, fi0;
           footprint_origin(f, T::FX, 8, h.tx, h.ty, TILE, fj0, fi0);
-          m |= classify<CUT>(a, c, bx, fj0, fi0, 8) << (8 * f);
+          m |= classify<CUT>(a, b, bx, fj0, fi0, 8) << (8 * f);
         }
         inst_mask[h.inst0 + r] = m;
       }
@@ -287,10 +276,13 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT, FwdShape<TILE, G>::kMin
   }
   const int grp = lane / LG, gl = lane % LG;
   const int y = gl & 7, cp0 = (gl >> 3) * NP;  // this lane's row and first column pair
+  const float2 k2 = make_float2((float)y, (float)y);
+  float2 col2[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) col2[p] = make_float2((float)(2 * (cp0 + p)), (float)(2 * (cp0 + p) + 1));
   unsigned long long evaluated = 0;  // (record, footprint) items of this warp
   int fj0 = 0, fi0 = 0, tw = 0, th = 0;
   int64_t tpx = 0;
-  float py = 0.f;
   float2 sa[NP], sc[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) sa[p] = sc[p] = make_float2(0.f, 0.f);
@@ -309,7 +301,6 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT, FwdShape<TILE, G>::kMin
       tw = h.w;
       th = h.h;
       tpx = h.px_off;
-      py = (float)(fi0 + y) + 0.5f;
 #pragma unroll
       for (int p = 0; p < NP; ++p) sa[p] = sc[p] = make_float2(0.f, 0.f);
     }
@@ -323,10 +314,10 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT, FwdShape<TILE, G>::kMin
       if (lane < nr) {  // lane-parallel chunk build
         const bool real = lane < ne;
         const int r = real ? (int)R.list[warp][base + lane] : 0;
-        fwd_build<CUT, false>(W, lane, real, R.a[r], R.b[r], R.box[r], fj0, fi0);
+        fwd_build<CUT, false>(W, lane, real, R.a[r], R.b[r], R.c[r], R.box[r], fj0, fi0);
       }
       __syncwarp();
-      for (int e = grp; e < nr; e += G) fwd_item<CUT, false, NP>(C, e, py, y, cp0, sa, sc);
+      for (int e = grp; e < nr; e += G) fwd_item<CUT, false, NP>(C, e, k2, y, cp0, col2, sa, sc);
       __syncwarp();
     }
     for (int base = 0; base < np; base += 32) {
@@ -334,10 +325,10 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT, FwdShape<TILE, G>::kMin
       if (lane < nr) {
         const bool real = lane < ne;
         const int r = real ? (int)R.list[warp][kBatch - 1 - (base + lane)] : 0;
-        fwd_build<CUT, true>(W, lane, real, R.a[r], R.b[r], R.box[r], fj0, fi0);
+        fwd_build<CUT, true>(W, lane, real, R.a[r], R.b[r], R.c[r], R.box[r], fj0, fi0);
       }
       __syncwarp();
-      for (int e = grp; e < nr; e += G) fwd_item<CUT, true, NP>(C, e, py, y, cp0, sa, sc);
+      for (int e = grp; e < nr; e += G) fwd_item<CUT, true, NP>(C, e, k2, y, cp0, col2, sa, sc);
       __syncwarp();
     }
     mbar_arrive(&S.bars.empty[s]);  // the stage is no longer read by this thread
@@ -415,29 +406,32 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
 
 // One lane, one work item (or, with TAIL, nrows of its FH rows from row y0,
 // in a rolled loop): sums over the footprint's 8 x FH (8 x nrows) pixels of
-//   acc0 = sum r w                (dL/dc),
-//   acc1 = sum g,   g = w dL/dw   (dL/dlw2 / ln 2),
-//   acc2 = sum g t1, acc3 = sum g t2,
-//   acc4 = sum g t1 dx, acc5 = sum g t1 dy, acc6 = sum g t2 dy,
+//   acc0 = sum r w        (dL/dc),
+//   acc1 = sum g,  g = w dL/dw   (dL/dlw2 / ln 2),
+//   acc2 = sum g t1,    acc3 = sum g t2,
+//   acc4 = sum g t1^2,  acc5 = sum g t1 t2,  acc6 = sum g t2^2,
 // with r = G / alpha and dL/dw = r (c - C) at each pixel (Eq. us-render
 // differentiated, box fixed), added to the record's accumulators; the chain
-// kernel turns them into the gradients of x*, r11, r12, r22. Pixels outside
-// the box or the ellipsoid (CUT) get w = 0 through an exponent of -inf, never
-// a NaN: every factor that multiplies w stays finite.
+// kernel turns them into the gradients of the Gaussian's parameters. Pixels
+// outside the box or the ellipsoid (CUT) get w = 0 through an exponent of
+// -inf, never a NaN: every factor that multiplies w stays finite.
 template <int FH, int CUT, bool TAIL = false>
-__device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, uint32_t cl,
-                                         uint32_t rid, const float4* __restrict__ pix, int fj0,
-                                         int fi0, float* __restrict__ rec_grad, int y0 = 0,
+__device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, const float4& cr,
+                                         uint2 bx, uint32_t cl, uint32_t rid,
+                                         const float4* __restrict__ pix, int fj0, int fi0,
+                                         float* __restrict__ rec_grad, int y0 = 0,
                                          int nrows = FH) {
-  const float2 r11 = make_float2(a.z, a.z), r12 = make_float2(a.w, a.w);
-  const float2 r22 = make_float2(bb.x, bb.x), lw = make_float2(bb.y, bb.y);
-  const float2 cc = make_float2(bb.z, bb.z), nx = make_float2(-a.x, -a.x);
+  const ItemGeo ig = item_geo(a, bb, cr, bx, fj0, fi0);
+  const float2 r11 = make_float2(ig.r11, ig.r11), kq = make_float2(ig.kq, ig.kq);
+  const float2 ns0q = make_float2(ig.ns0q, ig.ns0q), a1 = make_float2(ig.a1, ig.a1);
+  const float2 a0 = make_float2(ig.a0, ig.a0), nyh = make_float2(ig.nyh, ig.nyh);
+  const float2 nyl = make_float2(ig.nyl, ig.nyl), r22 = make_float2(ig.r22, ig.r22);
+  const float2 lw = make_float2(bb.y, bb.y), cc = make_float2(bb.z, bb.z);
   const int cx0 = cl & 0xff, cx1 = (cl >> 8) & 0xff, ry0 = (cl >> 16) & 0xff, ry1 = cl >> 24;
-  float2 dx[4], lwc[4];  // lw2 per column pair, -inf outside the box's columns
+  float2 col[4], lwc[4];  // column offsets; lw2 per column pair, -inf outside the box's columns
 #pragma unroll
   for (int cp = 0; cp < 4; ++cp) {
-    const float xj = (float)(fj0 + 2 * cp) + 0.5f;
-    dx[cp] = __fadd2_rn(make_float2(xj, xj + 1.f), nx);
+    col[cp] = make_float2((float)(2 * cp), (float)(2 * cp + 1));
     lwc[cp] = lw;
     if (2 * cp < cx0 || 2 * cp > cx1) lwc[cp].x = -INFINITY;
     if (2 * cp + 1 < cx0 || 2 * cp + 1 > cx1) lwc[cp].y = -INFINITY;
@@ -447,20 +441,20 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, uint
   float2 s0 = make_float2(0.f, 0.f), a4 = make_float2(0.f, 0.f);
   float2 s1p = make_float2(0.f, 0.f), u1p = make_float2(0.f, 0.f), u2p = make_float2(0.f, 0.f);
   float2 a5p = make_float2(0.f, 0.f), a6p = make_float2(0.f, 0.f);
-  const float fy0 = (float)(fi0 + y0) + 0.5f;  // row centres fy0 + j are exact
   const float4* __restrict__ pxr = pix + 4 * y0;
   auto row = [&](int j) {
     const int y = y0 + j;
-    const float dyv = (fy0 + (float)j) - a.y;
-    const float2 dy = make_float2(dyv, dyv);
-    const float2 r12dy = __fmul2_rn(r12, dy);
+    const float2 k2 = make_float2((float)y, (float)y);
+    const float2 nsh = __ffma2_rn(kq, k2, ns0q);  // kq row - s0q (exact)
+    const float2 nrs = __ffma2_rn(a1, k2, a0);
+    const float2 dy = __fadd2_rn(__fadd2_rn(k2, nyh), nyl);
     const float2 t2 = __fmul2_rn(r22, dy);
     float2 nt2sq = __fmul2_rn(neg2(t2), t2);
     if (y < ry0 || y > ry1) nt2sq = make_float2(-INFINITY, -INFINITY);  // row outside the box
     float2 s1r = make_float2(0.f, 0.f), u1r = make_float2(0.f, 0.f);
 #pragma unroll
     for (int cp = 0; cp < 4; ++cp) {
-      const float2 t1 = __ffma2_rn(r11, dx[cp], r12dy);
+      const float2 t1 = __ffma2_rn(r11, __fadd2_rn(col[cp], nsh), nrs);
       // lw2 - t2^2 - t1^2
       float2 e2 = __ffma2_rn(neg2(t1), t1, __fadd2_rn(lwc[cp], nt2sq));
       if (CUT) {
@@ -476,13 +470,13 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, uint
       s1r = __fadd2_rn(s1r, g);
       const float2 gu = __fmul2_rn(g, t1);
       u1r = __fadd2_rn(u1r, gu);
-      a4 = __ffma2_rn(gu, dx[cp], a4);
+      a4 = __ffma2_rn(gu, t1, a4);
     }
     s1p = __fadd2_rn(s1p, s1r);
     u1p = __fadd2_rn(u1p, u1r);
-    a5p = __ffma2_rn(dy, u1r, a5p);
+    a5p = __ffma2_rn(t2, u1r, a5p);
     u2p = __ffma2_rn(t2, s1r, u2p);
-    a6p = __ffma2_rn(__fmul2_rn(t2, dy), s1r, a6p);
+    a6p = __ffma2_rn(__fmul2_rn(t2, t2), s1r, a6p);
   };
   if (TAIL) {
 #pragma unroll 1
@@ -546,11 +540,13 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
     const uint32_t e = Q[(qhead + i) % kBwdQueue];
     const RecStage<TILE, true>& Rs = S.st[e >> 7];
     const int r = (int)(e & 127u);
-    const uint32_t cl = clip_box(Rs.box[r], fj0, fi0, FH);
+    const uint2 bx = Rs.box[r];
+    const uint32_t cl = clip_box(bx, fj0, fi0, FH);
     if (part)
-      bwd_item<FH, CUT, true>(Rs.a[r], Rs.b[r], cl, Rs.rid[r], pix, fj0, fi0, v.rec_grad, y0, rows);
+      bwd_item<FH, CUT, true>(Rs.a[r], Rs.b[r], Rs.c[r], bx, cl, Rs.rid[r], pix, fj0, fi0,
+                              v.rec_grad, y0, rows);
     else
-      bwd_item<FH, CUT>(Rs.a[r], Rs.b[r], cl, Rs.rid[r], pix, fj0, fi0, v.rec_grad);
+      bwd_item<FH, CUT>(Rs.a[r], Rs.b[r], Rs.c[r], bx, cl, Rs.rid[r], pix, fj0, fi0, v.rec_grad);
   };
   // one round: the oldest min(queued, 32) items; fewer than 17 are split by
   // rows over 2 or 4 lanes each (each lane adds its rows' sums)

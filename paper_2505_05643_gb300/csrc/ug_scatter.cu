@@ -8,8 +8,9 @@
 
 namespace ug {
 
-// One warp per record slot (grid-stride); lanes take the box's pixels in
-// row-major order. Zero weights add nothing and issue no atomic.
+// One warp per record slot (grid-stride); lanes take the box's rows in
+// segments of up to 8 pixels (each segment one item of item_geo, anchored at
+// its first pixel). Zero weights add nothing and issue no atomic.
 __global__ void __launch_bounds__(256) k_scatter(WsView v, int cut, float* __restrict__ sa,
                                                  float* __restrict__ sc) {
   if (dev_failed(v.hdr)) return;
@@ -20,21 +21,25 @@ __global__ void __launch_bounds__(256) k_scatter(WsView v, int cut, float* __res
     const uint2 bx = v.rec_box[slot];
     const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
     if (j0 > j1 || i0 > i1) continue;
-    const float4 a = v.rec_a[slot], b = v.rec_b[slot];
+    const float4 a = v.rec_a[slot], b = v.rec_b[slot], c = v.rec_c[slot];
     const PlaneDev& pl = v.planes[v.rec_plane[slot]];
-    const uint32_t nx = (uint32_t)(j1 - j0 + 1), npx = nx * (uint32_t)(i1 - i0 + 1);
-    for (uint32_t k = lane; k < npx; k += 32u) {
-      const uint32_t di = k / nx, dj = k - di * nx;
-      const int i = i0 + (int)di, j = j0 + (int)dj;
-      const float dx = ((float)j + 0.5f) - a.x, dy = ((float)i + 0.5f) - a.y;
-      const float t1 = fmaf(a.z, dx, a.w * dy), t2 = b.x * dy;
-      const float q = fmaf(t1, t1, t2 * t2);
-      const bool in = cut == 0 || q <= b.w;
-      const float w = in ? fast_exp2(b.y - q) : 0.f;
-      if (w > 0.f) {
-        const int64_t px = pl.px_off + (int64_t)i * pl.w + j;
-        atomicAdd(sa + px, w);
-        atomicAdd(sc + px, w * b.z);
+    const uint32_t nsx = (uint32_t)(j1 - j0 + 8) / 8u, nseg = nsx * (uint32_t)(i1 - i0 + 1);
+    for (uint32_t k = lane; k < nseg; k += 32u) {
+      const uint32_t di = k / nsx, ds = k - di * nsx;
+      const int i = i0 + (int)di, fj0 = j0 + 8 * (int)ds;
+      const ItemGeo g = item_geo(a, b, c, bx, fj0, i);
+      const float t2 = b.x * __fadd_rn(g.nyh, g.nyl);
+      const int64_t row = pl.px_off + (int64_t)i * pl.w;
+      for (int q = 0; q < 8 && fj0 + q <= j1; ++q) {
+        const float t1 = __fmaf_rn(g.r11, __fadd_rn((float)q, g.ns0q), g.a0);
+        const float e = __fsub_rn(__fmaf_rn(-t1, t1, b.y), __fmul_rn(t2, t2));
+        const float qq = __fmaf_rn(t1, t1, __fmul_rn(t2, t2));
+        const bool in = cut == 0 || qq <= b.w;
+        const float w = in ? fast_exp2(e) : 0.f;
+        if (w > 0.f) {
+          atomicAdd(sa + row + fj0 + q, w);
+          atomicAdd(sc + row + fj0 + q, w * b.z);
+        }
       }
     }
   }

@@ -193,7 +193,7 @@ class Renderer:
         records' boxes, render data and planes of the last ug_bin_sort."""
         st = self.status()
         n_inst, n_rec = st["instances"], st["records"]
-        kp, vp, rp, bp, ap, bbp, pp = B.ug_debug_views(self.plan, self.ws)
+        kp, vp, rp, bp, ap, bbp, cp, pp = B.ug_debug_views(self.plan, self.ws)
 
         def grab(ptr, count, width=1):
             if count == 0:
@@ -206,7 +206,8 @@ class Renderer:
         return dict(keys=grab(kp, n_inst), records=grab(vp, n_inst),
                     ranges=grab(rp, int(self.plan.total_tiles), 2),
                     boxes=grab(bp, n_rec, 2), rec_a=grab(ap, n_rec, 4).view(np.float32),
-                    rec_b=grab(bbp, n_rec, 4).view(np.float32), rec_plane=grab(pp, n_rec),
+                    rec_b=grab(bbp, n_rec, 4).view(np.float32),
+                    rec_c=grab(cp, n_rec, 4).view(np.float32), rec_plane=grab(pp, n_rec),
                     status=st)
 
 

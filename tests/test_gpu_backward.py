@@ -113,6 +113,23 @@ def test_grad_fp64_branch():
     _check_grads(gpu, gref, gabs, oracle.param_names(0), "fp64 branch")
 
 
+def test_grad_extreme_anisotropy():
+    """The first 20,000 Gaussians of the bench workload (axis ratios log-uniform
+    to 1e4, triangular front-end) on four of its planes (up to 512^2): every
+    gradient entry of 2,000 Gaussians within rel 1e-3 plus the abs-sum floor."""
+    g, pl = synth.workload_aniso_1m()
+    n = 20000
+    g = synth.scale_rot_to_tri({k: np.ascontiguousarray(v[..., :n]) for k, v in g.items()}, 1e-4)
+    pl = synth.select_planes(pl, [0, 1, 2, 3])
+    rng = np.random.default_rng(37)
+    target = rng.uniform(0, 1, pl["total_pixels"])
+    sub = np.sort(rng.choice(n, 2000, replace=False))
+    cfg = R.make_config(cov_param=B.UG_COV_TRI)
+    gpu, gref, gabs, _ = _backward_case(g, pl, cfg, target, subset=sub)
+    assert np.count_nonzero(np.abs(gref).sum(1)) > 200  # Gaussians that reach a pixel
+    _check_grads(gpu, gref, gabs, oracle.param_names(0), "aniso cut")
+
+
 @pytest.mark.parametrize("tile,variant", [(16, 1), (8, 0), (8, 1)])
 def test_grad_variants(tile, variant):
     rng = np.random.default_rng(32)

@@ -31,41 +31,57 @@ def test_fwd_2k_parity(cov_param, cutoff):
     assert st["status"] == 0 and st["records"] > 500
 
 
-@pytest.mark.parametrize("fp64_ratio", [1e3, 1.0])
-def test_fwd_2k_fp64_branch(fp64_ratio):
-    """The triangular front-end with every Gaussian sent down the FP64 branch
-    (fp64_ratio = 1) gives the same parity as the FP32 branch."""
+@pytest.mark.parametrize("fp64_ratio,fp32_reach", [(1e3, float("inf")), (1.0, 20.0)])
+def test_fwd_2k_fp64_branch(fp64_ratio, fp32_reach):
+    """The triangular front-end with every Gaussian on the FP32 geometry
+    (fp32_reach = inf; axis ratios here are below 1e3) and with every Gaussian
+    on the extended-precision branch (fp64_ratio = 1) gives the same parity."""
     g, pl = synth.workload_fwd_2k()
     g = synth.scale_rot_to_tri(g, 1e-4)
-    cfg = R.make_config(cov_param=B.UG_COV_TRI, fp64_ratio=fp64_ratio)
+    cfg = R.make_config(cov_param=B.UG_COV_TRI, fp64_ratio=fp64_ratio, fp32_reach=fp32_reach)
     r, _, image, alpha = gpu_render(g, pl, cfg)
     ref = oracle.render(g, pl, oracle_config(cfg))
-    assert_forward_parity(image, alpha, ref, f"fp64_ratio {fp64_ratio}")
+    assert_forward_parity(image, alpha, ref, f"fp64_ratio {fp64_ratio} fp32_reach {fp32_reach}")
     st = r.status()
-    if fp64_ratio == 1.0:
-        assert st["fp64_records"] > 500
+    if fp64_ratio == 1.0:  # every visible record (records also counts rejected candidates)
+        assert st["fp64_records"] > 0.8 * st["records"] and st["fp64_records"] > 500
+    else:
+        assert st["fp64_records"] == 0
 
 
-def test_extreme_anisotropy_small():
-    """Axis ratios up to 1e4 (triangular front-end, FP64 branch for ratios
-    above 1e3). FP32 pixel coordinates limit the accuracy of the thinnest
-    Gaussians (a pixel-centre rounding of 1e-7 units moves q by up to
-    (1e-7 / sigma_min)^2 ~ 1e-2), so this case is checked statistically: 99 %
-    of pixels within the stated tolerance and none off by more than 1e-2."""
-    rng = np.random.default_rng(3)
-    g = synth.scale_rot_to_tri(synth.gaussians_anisotropic(rng, 20000), 1e-4)
-    pl = synth.planes_random(rng, [(128, 128), (256, 256)])
+def _aniso_cut(n=20000, planes=(0, 1, 2, 3)):
+    """The first n Gaussians of the bench workload (axis ratios log-uniform to
+    1e4, triangular front-end) and some of its planes (sizes from {128, 192,
+    256, 384, 512}^2)."""
+    g, pl = synth.workload_aniso_1m()
+    g = {k: np.ascontiguousarray(v[..., :n]) for k, v in g.items()}
+    return synth.scale_rot_to_tri(g, 1e-4), synth.select_planes(pl, list(planes))
+
+
+def test_fwd_extreme_anisotropy_parity():
+    """Axis ratios up to 1e4 (needles and discs far thinner than a pixel) on
+    planes up to 512^2: every pixel within the stated tolerance (Sec. 4.2's
+    stable parameterisation at the bench workload's anisotropy)."""
+    g, pl = _aniso_cut()
+    assert int(pl["size"].max()) >= 384
     cfg = R.make_config(cov_param=B.UG_COV_TRI)
     r, _, image, alpha = gpu_render(g, pl, cfg)
     ref = oracle.render(g, pl, oracle_config(cfg))
-    from gpu_helpers import forward_bound
-    img_tol, _ = forward_bound(ref)
-    err = np.abs(image - ref["image"])
-    assert (err <= img_tol).mean() >= 0.99
-    assert err.max() <= 1e-2
+    assert_forward_parity(image, alpha, ref, "aniso cut")
     st = r.status()
-    assert st["fp64_records"] > 100
+    assert st["fp64_records"] > 0.8 * st["records"]  # records also counts rejected candidates
     assert abs(st["box_pixels"] - ref["pairs"]) <= 1e-3 * ref["pairs"]
+
+
+def test_fwd_extreme_anisotropy_random_planes():
+    """The same shapes on random planes with a ratio of 1e4 everywhere."""
+    rng = np.random.default_rng(3)
+    g = synth.scale_rot_to_tri(synth.gaussians_anisotropic(rng, 20000), 1e-4)
+    pl = synth.planes_random(rng, [(128, 128), (256, 256), (512, 512)])
+    cfg = R.make_config(cov_param=B.UG_COV_TRI)
+    r, _, image, alpha = gpu_render(g, pl, cfg)
+    ref = oracle.render(g, pl, oracle_config(cfg))
+    assert_forward_parity(image, alpha, ref, "aniso random planes")
 
 
 def test_more_planes_than_shared_memory_table():

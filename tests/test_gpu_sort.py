@@ -50,15 +50,17 @@ def _edge_ambiguous(geo, planes, p, g, amb=1e-5):
     return bool(geo["amb_plane"][p, g])
 
 
-def _max_exponent(a, b, j0, j1, i0, i1):
+def _max_exponent(a, b, c, box, j0, j1, i0, i1):
     """FP64 max over the pixel centres of [j0, j1] x [i0, i1] of the weight
-    exponent lw2 - t1^2 - t2^2 of a record (a = x*_j, x*_i, r11, r12; b = r22,
-    lw2, ...)."""
-    a = a.astype(np.float64)
-    b = b.astype(np.float64)
-    jj, ii = np.meshgrid(np.arange(j0, j1 + 1) + 0.5, np.arange(i0, i1 + 1) + 0.5)
-    dx, dy = jj - a[0], ii - a[1]
-    t1 = a[2] * dx + a[3] * dy
+    exponent lw2 - t1^2 - t2^2 of a record (a = X, Y, r11, kappa; c = their
+    low parts; b = r22, lw2, ...; X, Y relative to the box's first column and
+    row): t1 = r11 (dx + kappa dy), t2 = r22 dy."""
+    a, b, c = a.astype(np.float64), b.astype(np.float64), c.astype(np.float64)
+    X, Y, kap = a[0] + c[0], a[1] + c[1], a[3] + c[2]
+    bj0, bi0 = int(box[0] & 0xFFFF), int(box[1] & 0xFFFF)
+    jj, ii = np.meshgrid(np.arange(j0, j1 + 1) - bj0 + 0.5, np.arange(i0, i1 + 1) - bi0 + 0.5)
+    dx, dy = jj - X, ii - Y
+    t1 = a[2] * (dx + kap * dy)
     t2 = b[0] * dy
     return float((b[1] - t1 * t1 - t2 * t2).max())
 
@@ -67,11 +69,13 @@ def _check_tile_lists(r, pl, tile):
     """The GPU's sorted instances against a CPU replay from the GPU's own
     records: for every tile, its records are those whose box meets the tile,
     in ascending record id, minus only pairs whose weights are all exact FP32
-    zeros (binning drops those); the ranges delimit the tiles. Returns the
+    zeros (binning drops those: the record's exact weight exponent is below
+    -126.5 at every pixel of the pair); the ranges delimit the tiles. Returns the
     numbers of kept and dropped (record, tile) pairs."""
     dv = r.debug_views()
     keys, recs, ranges, boxes = dv["keys"], dv["records"], dv["ranges"], dv["boxes"]
-    rec_a, rec_b, rec_plane = dv["rec_a"], dv["rec_b"], dv["rec_plane"].astype(np.int64)
+    rec_a, rec_b, rec_c = dv["rec_a"], dv["rec_b"], dv["rec_c"]
+    rec_plane = dv["rec_plane"].astype(np.int64)
     n_rec = dv["status"]["records"]
     assert len(boxes) == n_rec
     off, tx = _tile_offsets(pl, tile)
@@ -96,7 +100,7 @@ def _check_tile_lists(r, pl, tile):
                     kept += 1
                     continue
                 dropped += 1
-                e = _max_exponent(rec_a[rid], rec_b[rid], max(j0, txx * tile),
+                e = _max_exponent(rec_a[rid], rec_b[rid], rec_c[rid], boxes[rid], max(j0, txx * tile),
                                   min(j1, txx * tile + tile - 1), max(i0, ty * tile),
                                   min(i1, ty * tile + tile - 1))
                 assert e < -126.5, (rid, key, e)  # 2^e underflows to +0 in FP32 (ftz)
