@@ -82,6 +82,17 @@ def max_over_ranks(x: float, device=None) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(x: float, device=None) -> float:
+    """Sum of a per-rank float over all ranks; x itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def all_ok_over_ranks(ok: bool, device=None) -> bool:
     """True when every rank reports ok."""
     import torch
@@ -100,7 +111,7 @@ def _clock_sampler(gpu_index: int, path: str):
     try:
         f = open(path, "w")
         p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={fields}",
-                              "--format=csv,noheader,nounits", "-lms", "100"],
+                              "--format=csv,noheader,nounits", "-lms", "50"],
                              stdout=f, stderr=subprocess.DEVNULL)
         return p, f
     except Exception:
@@ -233,8 +244,15 @@ def run_ours(args):
     except Exception:
         pass
 
-    # every rank trains its own replica of the workload (weak scaling, no collective)
+    # Plane split (weak scaling): every rank renders its own 64 planes (rank 0
+    # the workload's planes, rank r > 0 planes of the same sizes in other
+    # random poses) against a replica of the Gaussians; the per-Gaussian
+    # gradients are summed over the ranks (one all-reduce) before Adam.
     g, pl, hidden = _workload(args.n)
+    if world > 1 and rank > 0:
+        from paper_2505_05643_gb300 import synth
+        pl = synth.planes_random(np.random.default_rng(1000 + rank),
+                                 [tuple(int(x) for x in sz) for sz in pl["size"]])
     cfg = R.make_config(cov_param=B.UG_COV_TRI, cutoff=B.UG_CUTOFF_BOX, tile=args.tile,
                         variant=args.variant, variant_bwd=args.variant_bwd)
     n = len(g["logit"])
@@ -257,7 +275,12 @@ def run_ours(args):
         print(f"[bench] autotune: {tuned}", file=sys.stderr)
     renderer = R.Renderer(n, pl, cfg)
     r = renderer
-    step = T.TrainStep(renderer, params, targets)
+    if world > 1:
+        from paper_2505_05643_gb300 import parallel
+        total_px = parallel.global_count(renderer.total_pixels, dev)
+        step = parallel.PlaneSplitStep(renderer, params, targets, total_px)
+    else:
+        step = T.TrainStep(renderer, params, targets)
     s = torch.cuda.Stream(device=dev)
     st_dev = torch.zeros(64, dtype=torch.uint8, device=dev)
 
@@ -329,10 +352,15 @@ def run_ours(args):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=s):
             reset_on(s)
-            step.enqueue(s)
+            if world > 1:
+                step.enqueue_local(s)  # the all-reduce runs eagerly after the replay
+            else:
+                step.enqueue(s)
 
         def one(k):
             graph.replay()
+            if world > 1:
+                step.enqueue_update(s)
             B.ug_read_status(renderer.plan, renderer.ws, status_log[k], s)
 
         with torch.cuda.stream(s):
@@ -345,15 +373,22 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         t_start = datetime.datetime.now()
-        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        start.record(s)
+        # events at the start, at every quarter of the K steps and at the end
+        # (recorded between replays on the launching stream): the quarters give
+        # the spread of the step time within the one timed region
+        cuts = sorted({0, args.steps} | {args.steps * q // 4 for q in range(1, 4)})
+        ev = {c: torch.cuda.Event(enable_timing=True) for c in cuts}
+        ev[0].record(s)
         with torch.cuda.stream(s):
             for k in range(args.steps):
                 one(args.warmup + k)
-        stop.record(s)
+                if k + 1 in ev:
+                    ev[k + 1].record(s)
         torch.cuda.synchronize()
         t_stop = datetime.datetime.now()
-        total_ms = start.elapsed_time(stop)
+        total_ms = ev[0].elapsed_time(ev[args.steps])
+        segments = [ev[a].elapsed_time(ev[b]) / (b - a) for a, b in zip(cuts[:-1], cuts[1:])
+                    if b > a]
         if sampler is not None:
             time.sleep(0.15)  # let the sampler flush the last interval
             sampler.terminate()
@@ -370,8 +405,16 @@ def run_ours(args):
         raise RuntimeError("capacity overflow in the timed steps")
     clocks = _clock_summary(clk_path, t_start, t_stop)
     ms_step = max_over_ranks(total_ms / args.steps, dev)
+    timing = {"timed_s": total_ms * 1e-3, "segments_ms_per_step": segments,
+              "spread": (max(segments) - min(segments)) / statistics.median(segments)}
+    if clocks.get("sm_mhz"):
+        # step time in SM clock cycles at the median sampled clock, and the
+        # step time that cycle count would take at the maximum clock
+        timing["mcycles_per_step"] = ms_step * clocks["sm_mhz"] * 1e-3
+        if clocks.get("sm_max_mhz"):
+            timing["ms_per_step_at_max_clock"] = ms_step * clocks["sm_mhz"] / clocks["sm_max_mhz"]
     pairs = float(np.mean([x.box_pixels for x in sts[args.warmup:]]))
-    value = pairs * world / (ms_step * 1e-3)
+    value = sum_over_ranks(pairs, dev) / (ms_step * 1e-3)
 
     # ---- phase timing: the same W + K steps eagerly, CUDA events on the
     # launching stream around each call of the step
@@ -389,16 +432,23 @@ def run_ours(args):
                 e[1].record(s)
                 B.ug_render(r.plan, r.ws, step.image, step.alpha, s)
                 e[2].record(s)
-                B.ug_mse_loss_grad(step.image, step.targets, step.image.numel(), step.grad_image,
-                                   step.loss, s)
+                if world > 1:
+                    B.ug_mse_loss_grad_part(step.image, step.targets, step.image.numel(),
+                                            step.total_pixels, step.grad_image, step.loss, s)
+                else:
+                    B.ug_mse_loss_grad(step.image, step.targets, step.image.numel(),
+                                       step.grad_image, step.loss, s)
                 e[3].record(s)
                 B.ug_render_backward_raster(r.plan, r.ws, step.image, step.alpha, step.grad_image,
                                             s)
                 e[4].record(s)
                 B.ug_preprocess_backward(r.plan, step.g_struct, r.ws, step.grad_struct, s)
                 e[5].record(s)
-                B.ug_adam_step(step.params, step.grads, step.m, step.v, r.rows, r.n,
-                               step.lr_rows, step.step, T.BETA1, T.BETA2, T.EPS, s)
+                if world > 1:
+                    step.enqueue_update(s)  # all-reduce of the gradients, then Adam
+                else:
+                    B.ug_adam_step(step.params, step.grads, step.m, step.v, r.rows, r.n,
+                                   step.lr_rows, step.step, T.BETA1, T.BETA2, T.EPS, s)
                 x = read_status()
                 if not note(x):
                     ok = False
@@ -471,7 +521,8 @@ def run_ours(args):
     else:
         raise RuntimeError("capacity overflow in the end-to-end steps")
     e2e_pairs = float(np.mean([x.box_pixels for x in e2e_st]))
-    e2e = {"value": e2e_pairs * world / e2e_s, "unit": "pairs/s",
+    e2e = {"value": sum_over_ranks(e2e_pairs, dev) / max_over_ranks(e2e_s, dev),
+           "unit": "pairs/s",
            "h2d_bytes_per_step": int(h_targets.numel() * 4 + h_planes.numel()),
            "d2h_bytes_per_step": 4 + 64}
 
@@ -503,6 +554,18 @@ def run_ours(args):
             "bwd_ms": bwd_s * 1e3, "box_pairs_per_launch": pairs_eager,
             "evaluated_over_box_pairs": evaluated / pairs_eager,
             "evaluated_bwd_over_box_pairs": evaluated_bwd / pairs_eager,
+            # the same launches per useful pair (the box cut-off's pairs,
+            # counted exactly), with the same op counts: the rate of the
+            # paper's work unit, the pairs the kernels skip as exact FP32 zeros
+            # included
+            "per_useful_pair": {
+                "units_per_launch": pairs_eager,
+                "bwd": {"ops_per_unit": BWD_OPS,
+                        "achieved": BWD_OPS * pairs_eager / bwd_s / 1e12,
+                        "frac": BWD_OPS * pairs_eager / bwd_s / fp32_peak},
+                "fwd": {"ops_per_unit": FWD_OPS,
+                        "achieved": FWD_OPS * pairs_eager / fwd_s / 1e12,
+                        "frac": FWD_OPS * pairs_eager / fwd_s / fp32_peak}},
             "phases_ms": {"preprocess+bin_sort": float(np.mean(pre_ms)),
                           "render": fwd_s * 1e3, "render_backward_raster": bwd_s * 1e3,
                           "preprocess_backward": float(np.mean(chain_ms))}}
@@ -516,6 +579,26 @@ def run_ours(args):
                "sample": f"FP64 oracle scatter forward + analytic backward on planes "
                          f"0..{len(sample) - 1} of 64 ({cp} pairs) with all {n} Gaussians "
                          f"(initial parameters), {dt:.1f} s"}
+    launches = step.kernels_per_step() * args.steps
+    batching = None
+    if rank == 0 and world == 1 and not args.no_train_compare:
+        # the batched graph-captured step against one plane per launch on the
+        # 200k training workload (its own Gaussians, poses and targets)
+        del step, renderer, r, graph
+        torch.cuda.empty_cache()
+        tc = train_compare(args.compare_steps, 3)
+        acc = tc["accuracy"]
+        lm = acc["loss_mean_last"]
+        batching = {"workload": tc["config"]["workload"], "steps": tc["steps"],
+                    "batched_ms_per_step": tc["ms_per_step"],
+                    "per_plane_ms_per_step": tc["per_plane"]["ms_per_step"],
+                    "factor": tc["speedup"],
+                    "first_step_grad_rel_l2_diff": acc["first_step_grad_rel_l2_diff"],
+                    "loss_mean_last": lm, "loss_mean_last_steps": acc["loss_mean_last_steps"],
+                    "rel_diff_loss_mean_last": abs(lm[0] - lm[1]) / abs(lm[1]),
+                    "note": "Adam (eps 1e-15) takes full steps on gradients that are rounding "
+                            "noise, so the two trajectories part after a few steps; accuracy "
+                            "is compared on the first step's gradient and the late loss level"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
@@ -530,10 +613,13 @@ def run_ours(args):
                        "l2": "working set > L2 (129 MB); no flush",
                        "state": "every step starts from the initial parameters and zero Adam "
                                 "moments (device copy inside the timed step)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": (f"plane split x{world}: each rank its own 64 planes, "
+                                       "one all-reduce of the per-Gaussian gradients per step"
+                                       if world > 1 else "single GPU")},
             "steps_per_s": 1e3 / ms_step,
-            "gpu_launches": step.kernels_per_step() * args.steps,
+            "gpu_launches": launches,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "timing": timing, "batched_vs_per_plane": batching,
             "fp64_records": int(sts[-1].fp64_records), "records": int(sts[-1].records),
             "instances": int(sts[-1].instances),
         }
@@ -545,6 +631,11 @@ def run_ours(args):
 
 # ---------------------------------------------------------------- batching
 def run_train_compare(args):
+    print(json.dumps(train_compare(args.steps, args.warmup)), flush=True)
+    return 0
+
+
+def train_compare(K, W):
     """Training workload (200,000 Gaussians in the paper's initialisation,
     fitted to a hidden 100,000-Gaussian volume on 32 sweep poses of 256x256 per
     step): the batched step (all 32 planes per launch, the whole step captured
@@ -579,7 +670,6 @@ def run_train_compare(args):
                   for wp in win_planes]
     p0 = torch.from_numpy(R.pack_params(g, B.UG_COV_TRI)).to(dev)
     s = torch.cuda.Stream(device=dev)
-    K, W = args.steps, args.warmup
 
     # ---- batched
     rb = R.Renderer(n, win_planes[0], cfg)
@@ -627,6 +717,7 @@ def run_train_compare(args):
     with torch.cuda.graph(graph, stream=s):
         step.enqueue(s)
     loss_b = torch.zeros(K, device=dev)
+    grad_b0 = torch.zeros_like(step.grads)
 
     def batched_run(record):
         reset(step)
@@ -637,6 +728,8 @@ def run_train_compare(args):
                 graph.replay()
                 if record:
                     loss_b[k].copy_(step.loss[0])
+                    if k == 0:
+                        grad_b0.copy_(step.grads)
 
     with torch.cuda.stream(s):
         for k in range(W):
@@ -710,11 +803,14 @@ def run_train_compare(args):
     plain_reset()
     torch.cuda.synchronize()
     loss_p = torch.zeros(K, device=dev)
+    grad_p0 = torch.zeros_like(grads)
     with torch.cuda.stream(s):
         e0.record(s)
         for k in range(K):
             plain_step(k, s, False)
             loss_p[k].copy_(loss[0])
+            if k == 0:
+                grad_p0.copy_(grads)
         e1.record(s)
     s.synchronize()
     ms_p = e0.elapsed_time(e1) / K
@@ -723,6 +819,11 @@ def run_train_compare(args):
         assert st["status"] == B.UG_OK, st
     lb, lp = loss_b.cpu().numpy(), loss_p.cpu().numpy()
     rel = np.abs(lb - lp) / np.abs(lp)
+    # the first step starts both forms from the same parameters: their
+    # gradients agree up to FP32 summation order
+    gb0, gp0 = grad_b0.double(), grad_p0.double()
+    grad_rel = float((gb0 - gp0).norm() / gp0.norm())
+    tail = max(1, min(20, K // 4))  # whole cycles of the 5 pose windows when K >= 100
     dparam = float((params_b - params).abs().max())
     moved = float((params_b - p0).abs().max())
     line = {
@@ -741,7 +842,10 @@ def run_train_compare(args):
         # both forms sum the same terms in different orders (and the backward's
         # atomics in no fixed order), so their trajectories part slowly; Adam
         # (normalised steps) lets the rounding differences grow over the run
-        "accuracy": {"loss_first": [float(lb[0]), float(lp[0])],
+        "accuracy": {"first_step_grad_rel_l2_diff": grad_rel,
+                     "loss_mean_last": [float(lb[-tail:].mean()), float(lp[-tail:].mean())],
+                     "loss_mean_last_steps": tail,
+                     "loss_first": [float(lb[0]), float(lp[0])],
                      "loss_last": [float(lb[-1]), float(lp[-1])],
                      "max_rel_loss_diff": float(np.max(rel)),
                      "max_rel_loss_diff_first_20": float(np.max(rel[:20])),
@@ -749,8 +853,7 @@ def run_train_compare(args):
                                           if k < len(rel)},
                      "max_param_diff": dparam, "max_param_change": moved},
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 # ---------------------------------------------------------------- reconstruction
@@ -1156,7 +1259,7 @@ def run_loss(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=16)
@@ -1165,6 +1268,10 @@ def main():
     ap.add_argument("--cpu-planes", type=int, default=64, help="planes in the CPU oracle sample")
     ap.add_argument("--n", type=int, default=None, help="use the first n Gaussians (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-train-compare", action="store_true",
+                    help="skip the batched vs one-plane-per-launch comparison (train_200k)")
+    ap.add_argument("--compare-steps", type=int, default=200,
+                    help="steps of the batched vs one-plane-per-launch comparison")
     ap.add_argument("--workload", default="aniso_1m",
                     choices=["aniso_1m", "train_200k", "recon", "densify", "loss"],
                     help="train_200k: batched graph step against one plane per launch; "

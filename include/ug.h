@@ -110,11 +110,16 @@ typedef struct {
   int32_t cov_param; /* UG_COV_TRI (paper) or UG_COV_SCALE_ROT */
   int32_t tile;      /* square tile edge in pixels: 8 or 16 (default 16) */
   int32_t variant;   /* forward rasterizer variant, 0 .. ug_num_variants(tile) - 1: lane
-                        groups per 8x8 footprint, 0 = 4 (default), 1 = 2, 2 = 1 */
+                        groups per 8x8 footprint (pixels per lane), stages in the record
+                        ring and records per stage: 0 = 4 groups, 3 stages of 128 (default),
+                        1 = 2 groups, 2 = 1 group; tile 16 also 3 = stages of 64 records,
+                        4 = 2 stages of 256, 5 = 4 stages of 128 */
   float fp64_ratio;  /* axis-ratio proxy above which the per-(plane, Gaussian) geometry runs
                         in extended (double-word, ~48-bit) precision; default 1e3 */
-  int32_t variant_bwd; /* backward rasterizer variant, 0 or 1: footprint height 8 (default)
-                          or 4 rows */
+  int32_t variant_bwd; /* backward rasterizer variant, 0 .. ug_num_variants_bwd(tile) - 1:
+                          0 = 8-row footprints, 4 stages of 128 records (default), 1 = 4-row
+                          footprints; tile 16 also 2 = 3 stages of 128 (more resident
+                          blocks), 3 = 4 stages of 64, 4 = 3 stages of 256 */
   float fp32_reach;  /* the geometry also runs in extended precision when ||F||_F (|mu| +
                         max |o|) exceeds this (F the Gaussian's precision factor, o the plane
                         origins): FP32 differences mu - o then lose the bits that thin or
@@ -173,9 +178,13 @@ int32_t ug_version(void);
 /* Human-readable name of a status code (static string). */
 const char* ug_status_string(ug_status status);
 
-/* Number of forward rasterizer variants compiled in for `tile` (0 if the
- * tile size is unsupported); every supported tile has two backward variants. */
+/* Number of forward (ug_num_variants) and backward (ug_num_variants_bwd)
+ * rasterizer variants compiled in for `tile` (0 if the tile size is
+ * unsupported). The variants compute the same result; they differ in how the
+ * work is laid out (see ug_config.variant and .variant_bwd), and the fastest
+ * depends on the workload. */
 int32_t ug_num_variants(int32_t tile);
+int32_t ug_num_variants_bwd(int32_t tile);
 
 /* Fill *cfg with the defaults listed above. */
 ug_status ug_config_default(ug_config* cfg);
@@ -244,6 +253,18 @@ ug_status ug_render_scatter(const ug_plan* plan, void* ws, size_t ws_bytes, floa
  * depend on scheduling (deterministic). */
 ug_status ug_mse_loss_grad(const float* image, const float* target, int64_t n,
                            float* grad_image, float* loss, ug_stream stream);
+
+/* Row a6 for one part of a larger set of images (the planes one rank of a
+ * plane-split run renders): writes grad_image[n] = 2 (image - target) / n_total
+ * and loss[0] = sum((image - target)^2) / n_total over this part's n pixels,
+ * so that the parts' gradients and losses, summed over all parts (one
+ * all-reduce of the per-Gaussian gradients), are those of the mean squared
+ * error over all n_total pixels. Same buffers and determinism as
+ * ug_mse_loss_grad, which equals this call with n_total = n. Returns
+ * UG_ERR_INVALID_ARGUMENT for a NULL input, n < 1 or n_total < n. */
+ug_status ug_mse_loss_grad_part(const float* image, const float* target, int64_t n,
+                                int64_t n_total, float* grad_image, float* loss,
+                                ug_stream stream);
 
 /* Largest n accepted by ug_mse_loss_grad_static (2^30 pixels). */
 #define UG_MSE_STATIC_MAX_N (1LL << 30)
@@ -396,6 +417,25 @@ ug_status ug_densify(const ug_config* cfg, const ug_densify_config* dc, const fl
                      const float* z, int64_t capacity, float* params_out, float* exp_avg_out,
                      float* exp_avg_sq_out, int64_t* n_out, void* scratch, size_t scratch_bytes,
                      ug_stream stream);
+
+/* Gaussian split across ranks (row a5; Sec. 4.1, Eq. alpha-combine and Eq.
+ * colour-combine): S_a = sum_i w_i and S_c = sum_i w_i c_i are sums over
+ * Gaussians in no particular order, so the partial sums of shards of the
+ * Gaussians add up to the full ones. ug_shard_sums turns a shard's ug_render
+ * output (image, alpha of n pixels, rendered with the given alpha_bg and c_bg)
+ * into its partial sums: sums[2 i] = alpha[i] - alpha_bg, sums[2 i + 1] =
+ * image[i] alpha[i] - alpha_bg c_bg (an interleaved [n][2] float array, 8-byte
+ * aligned). After the caller sums `sums` over the shards (one all-reduce of two
+ * floats per pixel), ug_composite writes alpha[i] = sums[2 i] + alpha_bg and
+ * image[i] = (sums[2 i + 1] + alpha_bg c_bg) / alpha[i], the image and alpha of
+ * all Gaussians, which each rank's ug_render_backward for its own shard then
+ * takes as inputs (its gradients need no further exchange). Returns
+ * UG_ERR_INVALID_ARGUMENT for a NULL pointer, n < 1, a misaligned `sums` or
+ * alpha_bg <= 0. */
+ug_status ug_shard_sums(const float* image, const float* alpha, int64_t n, float alpha_bg,
+                        float c_bg, float* sums, ug_stream stream);
+ug_status ug_composite(const float* sums, int64_t n, float alpha_bg, float c_bg, float* image,
+                       float* alpha, ug_stream stream);
 
 /* Test hook for the rasterizers' bounded waits (rows a5, a7). With on != 0
  * the producer warps of ug_render and ug_render_backward_raster issue no

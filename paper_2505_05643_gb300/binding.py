@@ -32,9 +32,11 @@ UG_MSE_LOSS_FLOATS = 1025
 
 # Every exported symbol declared in include/ug.h.
 EXPORTS = (
-    "ug_version", "ug_status_string", "ug_num_variants", "ug_config_default", "ug_plan_init",
+    "ug_version", "ug_status_string", "ug_num_variants", "ug_num_variants_bwd",
+    "ug_config_default", "ug_plan_init",
     "ug_preprocess", "ug_bin_sort", "ug_render", "ug_mse_loss_grad", "ug_render_backward",
     "ug_adam_step", "ug_read_status", "ug_debug_views", "ug_mse_loss_grad_static",
+    "ug_mse_loss_grad_part", "ug_shard_sums", "ug_composite",
     "ug_debug_stall_pipeline",
     "ug_render_backward_raster", "ug_preprocess_backward", "ug_render_scatter",
     "ug_ssim_scratch_floats", "ug_ssim",
@@ -127,6 +129,8 @@ def load(build_if_missing: bool = True):
     lib.ug_status_string.argtypes = [ctypes.c_int]
     lib.ug_num_variants.restype = i32
     lib.ug_num_variants.argtypes = [i32]
+    lib.ug_num_variants_bwd.restype = i32
+    lib.ug_num_variants_bwd.argtypes = [i32]
     lib.ug_config_default.argtypes = [P(ug_config)]
     lib.ug_plan_init.argtypes = [P(ug_config), i64, vp, i32, i64, i64, P(ug_plan)]
     lib.ug_preprocess.argtypes = [P(ug_plan), P(ug_gaussians), vp, vp, ctypes.c_size_t, vp]
@@ -134,6 +138,9 @@ def load(build_if_missing: bool = True):
     lib.ug_render.argtypes = [P(ug_plan), vp, ctypes.c_size_t, vp, vp, vp]
     lib.ug_mse_loss_grad.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.ug_mse_loss_grad_static.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.ug_mse_loss_grad_part.argtypes = [vp, vp, i64, i64, vp, vp, vp]
+    lib.ug_shard_sums.argtypes = [vp, vp, i64, f32, f32, vp, vp]
+    lib.ug_composite.argtypes = [vp, i64, f32, f32, vp, vp, vp]
     lib.ug_render_backward.argtypes = [P(ug_plan), P(ug_gaussians), vp, vp, ctypes.c_size_t, vp,
                                        vp, vp, P(ug_gaussian_grads), vp]
     lib.ug_ssim_scratch_floats.argtypes = [i32, i32, i32]
@@ -214,6 +221,10 @@ def ug_num_variants(tile: int) -> int:
     return int(load().ug_num_variants(tile))
 
 
+def ug_num_variants_bwd(tile: int) -> int:
+    return int(load().ug_num_variants_bwd(tile))
+
+
 def ug_config_default() -> ug_config:
     cfg = ug_config()
     _check(load().ug_config_default(ctypes.byref(cfg)), "ug_config_default")
@@ -248,6 +259,25 @@ def ug_render(plan: ug_plan, ws, image, alpha, stream=None):
 def ug_mse_loss_grad(image, target, n: int, grad_image, loss, stream=None):
     _check(load().ug_mse_loss_grad(_ptr(image), _ptr(target), int(n), _ptr(grad_image),
                                    _ptr(loss), _stream(stream)), "ug_mse_loss_grad")
+
+
+def ug_mse_loss_grad_part(image, target, n: int, n_total: int, grad_image, loss, stream=None):
+    """MSE part of a larger image set: sums divided by n_total instead of n."""
+    _check(load().ug_mse_loss_grad_part(_ptr(image), _ptr(target), int(n), int(n_total),
+                                        _ptr(grad_image), _ptr(loss), _stream(stream)),
+           "ug_mse_loss_grad_part")
+
+
+def ug_shard_sums(image, alpha, n: int, alpha_bg: float, c_bg: float, sums, stream=None):
+    """Partial sums (S_a, S_c) per pixel of a Gaussian shard's render."""
+    _check(load().ug_shard_sums(_ptr(image), _ptr(alpha), int(n), float(alpha_bg), float(c_bg),
+                                _ptr(sums), _stream(stream)), "ug_shard_sums")
+
+
+def ug_composite(sums, n: int, alpha_bg: float, c_bg: float, image, alpha, stream=None):
+    """Image and alpha from the summed (S_a, S_c) of all shards."""
+    _check(load().ug_composite(_ptr(sums), int(n), float(alpha_bg), float(c_bg), _ptr(image),
+                               _ptr(alpha), _stream(stream)), "ug_composite")
 
 
 def ug_mse_loss_grad_static(image, target, n: int, grad_image, loss, stream=None):

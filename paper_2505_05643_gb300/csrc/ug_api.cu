@@ -89,6 +89,7 @@ const char* ug_status_string(ug_status s) {
 }
 
 int32_t ug_num_variants(int32_t tile) { return num_render_variants(tile); }
+int32_t ug_num_variants_bwd(int32_t tile) { return num_render_variants_bwd(tile); }
 
 ug_status ug_config_default(ug_config* cfg) {
   if (!cfg) return UG_ERR_INVALID_ARGUMENT;
@@ -234,7 +235,15 @@ ug_status ug_render(const ug_plan* plan, void* ws, size_t ws_bytes, float* image
 ug_status ug_mse_loss_grad(const float* image, const float* target, int64_t n, float* grad_image,
                            float* loss, ug_stream stream) {
   if (!image || !target || !loss || n < 1) return UG_ERR_INVALID_ARGUMENT;
-  return cuda_status(launch_mse(image, target, n, grad_image, loss,
+  return cuda_status(launch_mse(image, target, n, n, grad_image, loss,
+                                reinterpret_cast<cudaStream_t>(stream)));
+}
+
+ug_status ug_mse_loss_grad_part(const float* image, const float* target, int64_t n,
+                                int64_t n_total, float* grad_image, float* loss,
+                                ug_stream stream) {
+  if (!image || !target || !loss || n < 1 || n_total < n) return UG_ERR_INVALID_ARGUMENT;
+  return cuda_status(launch_mse(image, target, n, n_total, grad_image, loss,
                                 reinterpret_cast<cudaStream_t>(stream)));
 }
 

@@ -337,8 +337,8 @@ cudaError_t launch_render_backward(const ug_plan* plan, const ug_gaussians* g, W
 cudaError_t launch_pre_backward(const ug_plan* plan, const ug_gaussians* g, WsView v,
                                 const ug_gaussian_grads* grads, cudaStream_t s);
 int device_sms();
-cudaError_t launch_mse(const float* image, const float* target, int64_t n, float* grad,
-                       float* loss, cudaStream_t s);
+cudaError_t launch_mse(const float* image, const float* target, int64_t n, int64_t denom,
+                       float* grad, float* loss, cudaStream_t s);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int32_t rows, int64_t n,
                         const ug_adam_row* d_rows, int32_t* d_step, float b1, float b2,
                         float eps, cudaStream_t s);

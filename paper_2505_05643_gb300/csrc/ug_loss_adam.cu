@@ -7,9 +7,9 @@ namespace ug {
 // ------------------------------------------------------------------ MSE
 __global__ void __launch_bounds__(256)
     k_mse(const float* __restrict__ image, const float* __restrict__ target, int64_t n,
-          float* __restrict__ grad, float* __restrict__ loss) {
+          int64_t denom, float* __restrict__ grad, float* __restrict__ loss) {
   __shared__ double red[8];
-  const float scale = 2.0f / (float)n;
+  const float scale = 2.0f / (float)denom;
   // a thread's few squares are summed in FP32 (FP64 arithmetic runs at a small
   // fraction of the FP32 rate), the threads' sums in FP64
   float accf = 0.f;
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-__global__ void k_mse_final(float* loss, int64_t n) {
+__global__ void k_mse_final(float* loss, int64_t denom) {
   __shared__ double red[kMseBlocks];
   for (int b = threadIdx.x; b < kMseBlocks; b += blockDim.x) red[b] = (double)loss[1 + b];
   __syncthreads();
@@ -55,13 +55,15 @@ __global__ void k_mse_final(float* loss, int64_t n) {
     for (int b = threadIdx.x; b < w; b += blockDim.x) red[b] += red[b + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) loss[0] = (float)(red[0] / (double)n);
+  if (threadIdx.x == 0) loss[0] = (float)(red[0] / (double)denom);
 }
 
-cudaError_t launch_mse(const float* image, const float* target, int64_t n, float* grad,
-                       float* loss, cudaStream_t s) {
-  k_mse<<<kMseBlocks, 256, 0, s>>>(image, target, n, grad, loss);
-  k_mse_final<<<1, 256, 0, s>>>(loss, n);
+// Sum of squared differences over n pixels divided by denom (denom = n: the
+// mean), and its gradient 2 (image - target) / denom.
+cudaError_t launch_mse(const float* image, const float* target, int64_t n, int64_t denom,
+                       float* grad, float* loss, cudaStream_t s) {
+  k_mse<<<kMseBlocks, 256, 0, s>>>(image, target, n, denom, grad, loss);
+  k_mse_final<<<1, 256, 0, s>>>(loss, denom);
   return cudaGetLastError();
 }
 

@@ -15,8 +15,8 @@
 
 namespace ug {
 
-constexpr int kBatch = 128;   // records per stage
-constexpr int kStages = 3;    // stages in the ring
+constexpr int kBatch = 128;   // records per stage (default; a template parameter)
+constexpr int kStages = 3;    // stages in the ring (default; a template parameter)
 constexpr int kFirst = 1;     // stage flag: first batch of its tile
 constexpr int kLast = 2;      // stage flag: last batch of its tile
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
@@ -119,23 +119,24 @@ struct StageHdr {
 // 8x8 footprints of a tile whose item lists a forward stage carries.
 constexpr int kMaxFootprints = 4;
 
-// One stage: up to kBatch records of one tile. Forward (not RAW): per 8x8
+// One stage: up to BATCH records of one tile. Forward (not RAW): per 8x8
 // footprint, the indices of the records live there (those whose box covers
 // the footprint from the front, the others from the back) and their counts,
 // written by the producer's finishing step. Backward (RAW): one 32-bit word
 // per record of the forward pass's footprint tests, and with the first stage
 // of a tile the tile's pixel inputs (dL/dC, alpha, C; pixels off the plane
 // hold 0, 1, 0).
-template <int TILE, bool RAW>
+template <int TILE, bool RAW, int BATCH = kBatch>
 struct RecStage {
-  float4 a[kBatch];
-  float4 b[kBatch];
-  float4 c[kBatch];
-  uint2 box[kBatch];
-  uint32_t rid[kBatch];
-  uint32_t mask[RAW ? kBatch : 1];
-  uint8_t list[RAW ? 1 : kMaxFootprints][RAW ? 1 : kBatch];
-  uint8_t nfull[RAW ? 1 : kMaxFootprints], npart[RAW ? 1 : kMaxFootprints];
+  static_assert(BATCH % 32 == 0 && BATCH <= 256, "records per stage: a multiple of 32, <= 256");
+  float4 a[BATCH];
+  float4 b[BATCH];
+  float4 c[BATCH];
+  uint2 box[BATCH];
+  uint32_t rid[BATCH];
+  uint32_t mask[RAW ? BATCH : 1];
+  uint8_t list[RAW ? 1 : kMaxFootprints][RAW ? 1 : BATCH];  // record indices (< 256)
+  uint16_t nfull[RAW ? 1 : kMaxFootprints], npart[RAW ? 1 : kMaxFootprints];
   StageHdr h;
   float raw[RAW ? 3 : 1][RAW ? TILE * TILE : 1];
 };
@@ -234,8 +235,9 @@ struct NoPrep {
   __device__ void operator()(S&, int) const {}
 };
 
-template <int TILE, bool RAW, bool RID, bool EMPTY_TILES, class Prep = NoPrep, int NS = kStages>
-__device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars<NS>& bars,
+template <int TILE, bool RAW, bool RID, bool EMPTY_TILES, class Prep = NoPrep, int NS = kStages,
+          int BATCH = kBatch>
+__device__ __forceinline__ void produce(RecStage<TILE, RAW, BATCH>* st, PipeBars<NS>& bars,
                                         const PlaneTable& T, const WsView& v,
                                         const uint32_t* __restrict__ vals, int which, int P,
                                         int total_tiles, const float* __restrict__ grad,
@@ -244,7 +246,7 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars<NS>& b
                                         const uint32_t* __restrict__ inst_mask,
                                         Prep prep = Prep()) {
   const int lane = threadIdx.x & 31;
-  constexpr int PER = kBatch / 32;
+  constexpr int PER = BATCH / 32;
   // test hook: issue nothing, so that the consumers' bounded waits run out
   if (*(volatile const uint32_t*)&v.hdr->stall_test != 0) return;
   const uint32_t total = (uint32_t)total_tiles;
@@ -285,11 +287,11 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars<NS>& b
     const uint32_t t = tA, b0 = b;
     const uint2 rg = rA;
     const TileCtx c = cA;
-    const int cnt = (int)min((uint32_t)kBatch, rg.y - b0);
-    const bool first = b0 == rg.x, last = b0 + kBatch >= rg.y;
+    const int cnt = (int)min((uint32_t)BATCH, rg.y - b0);
+    const bool first = b0 == rg.x, last = b0 + BATCH >= rg.y;
     // advance the cursor and start reading the next batch's record ids
     if (!last) {
-      b += kBatch;
+      b += BATCH;
     } else {
       next_tile();
       if (!EMPTY_TILES)
@@ -309,7 +311,7 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW>* st, PipeBars<NS>& b
       cp_async_wait_all();
       return;
     }
-    RecStage<TILE, RAW>& S = st[s];
+    RecStage<TILE, RAW, BATCH>& S = st[s];
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int r = lane + 32 * q;

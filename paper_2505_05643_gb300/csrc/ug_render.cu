@@ -3,7 +3,7 @@
 // Both kernels are persistent and warp-specialised. One producer warp per CTA
 // takes TILE x TILE pixel tiles from a device work counter (all tiles of all
 // planes, so planes of different sizes share one launch) and gathers each
-// tile's records, kBatch at a time, into a ring of shared-memory stages
+// tile's records, BATCH at a time, into a ring of shared-memory stages
 // (ug_pipe.cuh); the other warps consume the stages. The tile is cut into
 // footprints of 8 columns x FH rows. For every (record, footprint) of a stage
 // the consumers decide whether the record can touch the footprint:
@@ -98,7 +98,7 @@ struct FwdChunk {
   float thr[32];     // ellipsoid threshold (cut-off by ellipsoid)
 };
 
-template <int TILE, int G>
+template <int TILE, int G, int MINB = 0>
 struct FwdShape {
   using T = Tiling<TILE, 8>;
   static constexpr int NW = T::NF;        // one consumer warp per 8x8 footprint
@@ -107,16 +107,16 @@ struct FwdShape {
   static constexpr int LG = 32 / G;       // lanes per group: 8 rows x LG / 8 column blocks
   static constexpr int NP = G;            // column pairs per lane
   static_assert(G == 1 || G == 2 || G == 4, "groups");
-  // resident blocks asked of the compiler (at most 64 registers a thread for
-  // the 16x16 tile's 160 threads, so that shared memory, not registers,
-  // limits the blocks per SM)
-  static constexpr int kMinBlocks = NT >= 160 ? 5 : 1;
+  // resident blocks asked of the compiler (MINB, or by default 5 for the
+  // 16x16 tile's 160 threads: at most 80 registers a thread, so that shared
+  // memory, not registers, limits the blocks per SM)
+  static constexpr int kMinBlocks = MINB > 0 ? MINB : (NT >= 160 ? 5 : 1);
 };
 
-template <int TILE, int NW>
+template <int TILE, int NW, int NS, int BATCH>
 struct FwdSmem {
-  RecStage<TILE, false> st[kStages];
-  PipeBars<kStages> bars;
+  RecStage<TILE, false, BATCH> st[NS];
+  PipeBars<NS> bars;
   FwdChunk ch[NW];
   PlaneTable T;
 };
@@ -207,17 +207,17 @@ __device__ __forceinline__ void fwd_build(FwdChunk& W, int lane, bool real, cons
 // instance for the backward pass; then, per footprint, the compacted lists of
 // its live records (box covering the footprint from the front, the others
 // from the back) and their counts, written to the stage for the consumers.
-template <int TILE, int CUT>
+template <int TILE, int CUT, int BATCH>
 struct FwdPrep {
   static constexpr bool kDefer = true;
   uint32_t* inst_mask;
-  __device__ void operator()(RecStage<TILE, false>& S, int lane) const {
+  __device__ void operator()(RecStage<TILE, false, BATCH>& S, int lane) const {
     using T = Tiling<TILE, 8>;
     static_assert(T::NF <= kMaxFootprints, "a stage carries the lists of four footprints");
     const StageHdr h = S.h;
-    uint32_t mq[kBatch / 32];
+    uint32_t mq[BATCH / 32];
 #pragma unroll
-    for (int q = 0; q < kBatch / 32; ++q) {
+    for (int q = 0; q < BATCH / 32; ++q) {
       const int r = lane + 32 * q;
       uint32_t m = 0;
       if (r < h.cnt) {
@@ -238,40 +238,41 @@ struct FwdPrep {
     for (int f = 0; f < T::NF; ++f) {
       int nf = 0, np = 0;
 #pragma unroll
-      for (int q = 0; q < kBatch / 32; ++q) {
+      for (int q = 0; q < BATCH / 32; ++q) {
         const uint32_t mf = mq[q] >> (8 * f);
         const bool live = mf & 1u, full = mf & 2u;
         const uint32_t bf = __ballot_sync(0xffffffffu, live && full);
         const uint32_t bp = __ballot_sync(0xffffffffu, live && !full);
         const int r = lane + 32 * q;
         if (live && full) S.list[f][nf + __popc(bf & lt)] = (uint8_t)r;
-        if (live && !full) S.list[f][kBatch - 1 - (np + __popc(bp & lt))] = (uint8_t)r;
+        if (live && !full) S.list[f][BATCH - 1 - (np + __popc(bp & lt))] = (uint8_t)r;
         nf += __popc(bf);
         np += __popc(bp);
       }
       if (lane == 0) {
-        S.nfull[f] = (uint8_t)nf;
-        S.npart[f] = (uint8_t)np;
+        S.nfull[f] = (uint16_t)nf;
+        S.npart[f] = (uint16_t)np;
       }
     }
   }
 };
 
-template <int TILE, int G, int CUT>
-__global__ void __launch_bounds__(FwdShape<TILE, G>::NT, FwdShape<TILE, G>::kMinBlocks)
+template <int TILE, int G, int CUT, int NS = kStages, int BATCH = kBatch, int MINB = 0>
+__global__ void __launch_bounds__(FwdShape<TILE, G, MINB>::NT, FwdShape<TILE, G, MINB>::kMinBlocks)
     k_render_fwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles, float abg,
                  float cbg, float* __restrict__ image, float* __restrict__ alpha,
                  uint32_t* __restrict__ inst_mask) {
-  using Sh = FwdShape<TILE, G>;
+  using Sh = FwdShape<TILE, G, MINB>;
   constexpr int NW = Sh::NW, LG = Sh::LG, NP = Sh::NP;
-  __shared__ FwdSmem<TILE, NW> S;
+  extern __shared__ __align__(16) unsigned char fwd_smem[];
+  FwdSmem<TILE, NW, NS, BATCH>& S = *reinterpret_cast<FwdSmem<TILE, NW, NS, BATCH>*>(fwd_smem);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   pipe_init(S.T, S.bars, v, P, Sh::NCT, 32);
   if (__syncthreads_or(dev_failed(v.hdr))) return;  // the whole CTA leaves, or none of it
   if (warp == NW) {
-    produce<TILE, false, false, true>(S.st, S.bars, S.T, v, vals, 0, P, total_tiles, nullptr,
-                                      nullptr, nullptr, nullptr,
-                                      FwdPrep<TILE, CUT>{inst_mask});
+    produce<TILE, false, false, true, FwdPrep<TILE, CUT, BATCH>, NS, BATCH>(
+        S.st, S.bars, S.T, v, vals, 0, P, total_tiles, nullptr, nullptr, nullptr, nullptr,
+        FwdPrep<TILE, CUT, BATCH>{inst_mask});
     return;
   }
   const int grp = lane / LG, gl = lane % LG;
@@ -288,12 +289,12 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT, FwdShape<TILE, G>::kMin
   for (int p = 0; p < NP; ++p) sa[p] = sc[p] = make_float2(0.f, 0.f);
   const FwdChunk& C = S.ch[warp];
   for (uint32_t k = 0;; ++k) {
-    const int s = (int)(k % kStages);
-    if (!mbar_wait(&S.bars.full[s], (k / kStages) & 1u)) {
+    const int s = (int)(k % NS);
+    if (!mbar_wait(&S.bars.full[s], (k / NS) & 1u)) {
       dev_fail(v.hdr, UG_ERR_TIMEOUT, 1);
       break;
     }
-    const RecStage<TILE, false>& R = S.st[s];
+    const RecStage<TILE, false, BATCH>& R = S.st[s];
     const StageHdr h = R.h;
     if (h.tile < 0) break;
     if (h.flags & kFirst) {
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(FwdShape<TILE, G>::NT, FwdShape<TILE, G>::kMin
       const int ne = min(32, np - base), nr = (ne + G - 1) / G * G;
       if (lane < nr) {
         const bool real = lane < ne;
-        const int r = real ? (int)R.list[warp][kBatch - 1 - (base + lane)] : 0;
+        const int r = real ? (int)R.list[warp][BATCH - 1 - (base + lane)] : 0;
         fwd_build<CUT, true>(W, lane, real, R.a[r], R.b[r], R.c[r], R.box[r], fj0, fi0);
       }
       __syncwarp();
@@ -374,25 +375,31 @@ struct BwdShape {
   static constexpr int NT = NCT + 32;  // plus the producer warp
 };
 
-constexpr int kBwdQueue = 256;  // > the items a warp can hold: 31 left over + one stage's 128
-// Stages in the backward's ring: one more than the forward's, because a
-// consumer warp holds a stage until it has processed the stage's items.
+// Stages in the backward's ring by default: one more than the forward's,
+// because a consumer warp holds a stage until it has processed the stage's
+// items.
 constexpr int kBwdStages = 4;
 
-// A consumer warp's queue of work items, in a ring: (stage << 7) | record
-// index. The items are read from the stages themselves, so a stage is
-// released only once the warp has processed all of its items.
+// A consumer warp's queue of work items, in a ring of a power-of-two length
+// above the items a warp can hold (31 left over from a round plus one stage's
+// BATCH): (stage << 8) | record index. The items are read from the stages
+// themselves, so a stage is released only once the warp has processed all of
+// its items.
+template <int BATCH>
 struct BwdQueue {
-  uint16_t idx[kBwdQueue];
+  static constexpr int kLen = BATCH <= 128 ? 256 : 512;
+  static_assert(kLen >= 31 + BATCH, "the queue holds a round's remainder and a whole stage");
+  uint16_t idx[kLen];
 };
 
-template <int TILE, int FH>
+template <int TILE, int FH, int NS, int BATCH>
 struct BwdSmem {
   using Sh = BwdShape<TILE, FH>;
-  RecStage<TILE, true> st[kBwdStages];
-  PipeBars<kBwdStages> bars;
-  BwdQueue q[Sh::NW];
-  // per footprint, row y and column pair cp (index 4 y + cp): r0, r1, -rC0, -rC1
+  RecStage<TILE, true, BATCH> st[NS];
+  PipeBars<NS> bars;
+  BwdQueue<BATCH> q[Sh::NW];
+  // per footprint, row pair rp and column c (index 8 rp + c): r, r', -rC, -rC'
+  // of rows 2 rp and 2 rp + 1
   float4 pix[Sh::NW][FH * 4];
   PlaneTable Tb;
 };
@@ -404,23 +411,34 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
                : "memory");
 }
 
+// Column offset that stands for a column outside a partial item's box: t1 =
+// r11 (kFarCol + nsh) + nrs is then so large that t1^2 overflows or the
+// exponent is far below -127, so the weight is exactly +0, while t1 stays
+// finite for any r11 below 2^88 (0 * t1 is 0, never a NaN).
+constexpr float kFarCol = 1099511627776.f;  // 2^40
+
 // One lane, one work item (or, with TAIL, nrows of its FH rows from row y0,
-// in a rolled loop): sums over the footprint's 8 x FH (8 x nrows) pixels of
+// in a rolled loop; nrows even): sums over the footprint's 8 x FH (8 x nrows)
+// pixels of
 //   acc0 = sum r w        (dL/dc),
 //   acc1 = sum g,  g = w dL/dw   (dL/dlw2 / ln 2),
 //   acc2 = sum g t1,    acc3 = sum g t2,
 //   acc4 = sum g t1^2,  acc5 = sum g t1 t2,  acc6 = sum g t2^2,
 // with r = G / alpha and dL/dw = r (c - C) at each pixel (Eq. us-render
 // differentiated, box fixed), added to the record's accumulators; the chain
-// kernel turns them into the gradients of the Gaussian's parameters. Pixels
-// outside the box or the ellipsoid (CUT) get w = 0 through an exponent of
-// -inf, never a NaN: every factor that multiplies w stays finite.
+// kernel turns them into the gradients of the Gaussian's parameters. The
+// FP32x2 arithmetic pairs two ROWS of one column, so the per-row terms (the
+// row's crossing, t2, lw2 - t2^2 and the row sums) are computed once per row
+// and not duplicated. Pixels outside the box (rows: lw2 - t2^2 = -inf;
+// columns: kFarCol) or the ellipsoid (CUT) get w = 0, never a NaN: every
+// factor that multiplies w stays finite.
 template <int FH, int CUT, bool TAIL = false>
 __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, const float4& cr,
                                          uint2 bx, uint32_t cl, uint32_t rid,
                                          const float4* __restrict__ pix, int fj0, int fi0,
                                          float* __restrict__ rec_grad, int y0 = 0,
                                          int nrows = FH) {
+  static_assert(FH % 2 == 0, "rows are processed in pairs");
   const ItemGeo ig = item_geo(a, bb, cr, bx, fj0, fi0);
   const float2 r11 = make_float2(ig.r11, ig.r11), kq = make_float2(ig.kq, ig.kq);
   const float2 ns0q = make_float2(ig.ns0q, ig.ns0q), a1 = make_float2(ig.a1, ig.a1);
@@ -428,42 +446,38 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, cons
   const float2 nyl = make_float2(ig.nyl, ig.nyl), r22 = make_float2(ig.r22, ig.r22);
   const float2 lw = make_float2(bb.y, bb.y), cc = make_float2(bb.z, bb.z);
   const int cx0 = cl & 0xff, cx1 = (cl >> 8) & 0xff, ry0 = (cl >> 16) & 0xff, ry1 = cl >> 24;
-  float2 col[4], lwc[4];  // column offsets; lw2 per column pair, -inf outside the box's columns
+  float colv[8];  // column offsets; columns outside the box far away
 #pragma unroll
-  for (int cp = 0; cp < 4; ++cp) {
-    col[cp] = make_float2((float)(2 * cp), (float)(2 * cp + 1));
-    lwc[cp] = lw;
-    if (2 * cp < cx0 || 2 * cp > cx1) lwc[cp].x = -INFINITY;
-    if (2 * cp + 1 < cx0 || 2 * cp + 1 > cx1) lwc[cp].y = -INFINITY;
-  }
-  // packed sums over the footprint; the row-level ones keep the two pixel
-  // columns of a pair apart and are added at the end
+  for (int c = 0; c < 8; ++c) colv[c] = (c >= cx0 && c <= cx1) ? (float)c : kFarCol;
+  // packed sums over the footprint (.x even rows, .y odd rows, added at the end)
   float2 s0 = make_float2(0.f, 0.f), a4 = make_float2(0.f, 0.f);
   float2 s1p = make_float2(0.f, 0.f), u1p = make_float2(0.f, 0.f), u2p = make_float2(0.f, 0.f);
   float2 a5p = make_float2(0.f, 0.f), a6p = make_float2(0.f, 0.f);
+  // pixel factors of row pair rp, column c: pix[8 rp + c] = (r, r', -rC, -rC')
   const float4* __restrict__ pxr = pix + 4 * y0;
-  auto row = [&](int j) {
-    const int y = y0 + j;
-    const float2 k2 = make_float2((float)y, (float)y);
+  auto row_pair = [&](int j) {
+    const int y = y0 + 2 * j;
+    const float2 k2 = make_float2((float)y, (float)(y + 1));
     const float2 nsh = __ffma2_rn(kq, k2, ns0q);  // kq row - s0q (exact)
     const float2 nrs = __ffma2_rn(a1, k2, a0);
     const float2 dy = __fadd2_rn(__fadd2_rn(k2, nyh), nyl);
     const float2 t2 = __fmul2_rn(r22, dy);
-    float2 nt2sq = __fmul2_rn(neg2(t2), t2);
-    if (y < ry0 || y > ry1) nt2sq = make_float2(-INFINITY, -INFINITY);  // row outside the box
+    const float2 t2sq = __fmul2_rn(t2, t2);
+    float2 crow = __fadd2_rn(lw, neg2(t2sq));  // lw2 - t2^2
+    if (y < ry0 || y > ry1) crow.x = -INFINITY;  // row outside the box
+    if (y + 1 < ry0 || y + 1 > ry1) crow.y = -INFINITY;
     float2 s1r = make_float2(0.f, 0.f), u1r = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int cp = 0; cp < 4; ++cp) {
-      const float2 t1 = __ffma2_rn(r11, __fadd2_rn(col[cp], nsh), nrs);
-      // lw2 - t2^2 - t1^2
-      float2 e2 = __ffma2_rn(neg2(t1), t1, __fadd2_rn(lwc[cp], nt2sq));
+    for (int c = 0; c < 8; ++c) {
+      const float2 t1 = __ffma2_rn(r11, __fadd2_rn(make_float2(colv[c], colv[c]), nsh), nrs);
+      float2 e2 = __ffma2_rn(neg2(t1), t1, crow);  // lw2 - t2^2 - t1^2
       if (CUT) {
-        const float2 q = __ffma2_rn(t1, t1, __fmul2_rn(t2, t2));
+        const float2 q = __ffma2_rn(t1, t1, t2sq);
         if (!(q.x <= bb.w)) e2.x = -INFINITY;
         if (!(q.y <= bb.w)) e2.y = -INFINITY;
       }
       const float2 w = make_float2(fast_exp2(e2.x), fast_exp2(e2.y));
-      const float4 px = pxr[4 * j + cp];
+      const float4 px = pxr[8 * j + c];
       const float2 rr = make_float2(px.x, px.y);
       const float2 g = __fmul2_rn(__ffma2_rn(rr, cc, make_float2(px.z, px.w)), w);  // w dL/dw
       s0 = __ffma2_rn(rr, w, s0);
@@ -476,14 +490,14 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, cons
     u1p = __fadd2_rn(u1p, u1r);
     a5p = __ffma2_rn(t2, u1r, a5p);
     u2p = __ffma2_rn(t2, s1r, u2p);
-    a6p = __ffma2_rn(__fmul2_rn(t2, t2), s1r, a6p);
+    a6p = __ffma2_rn(t2sq, s1r, a6p);
   };
   if (TAIL) {
 #pragma unroll 1
-    for (int j = 0; j < nrows; ++j) row(j);
+    for (int j = 0; j < nrows / 2; ++j) row_pair(j);
   } else {
 #pragma unroll
-    for (int j = 0; j < FH; ++j) row(j);
+    for (int j = 0; j < FH / 2; ++j) row_pair(j);
   }
   const float s1 = s1p.x + s1p.y, u1 = u1p.x + u1p.y, u2 = u2p.x + u2p.y;
   const float a5 = a5p.x + a5p.y, a6 = a6p.x + a6p.y;
@@ -502,26 +516,28 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, cons
 // wait that reuses its slot (the items still queued are processed first, so
 // the producer never waits for a stage that a consumer holds). The warps share
 // no barrier.
-template <int TILE, int FH, int CUT>
-__global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
+template <int TILE, int FH, int CUT, int NS = kBwdStages, int BATCH = kBatch, int MINB = 4>
+__global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
     k_render_bwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles,
                  const float* __restrict__ image, const float* __restrict__ alpha,
                  const float* __restrict__ grad_image, const uint32_t* __restrict__ inst_mask) {
   using Sh = BwdShape<TILE, FH>;
   using T = Tiling<TILE, FH>;
   constexpr int NW = Sh::NW;
-  static_assert(kBwdStages <= 4 && kBatch == 128, "queue entries hold a stage (2 bits) and a record (7)");
-  static_assert(kBwdQueue >= 31 + kBatch, "the queue holds a round's remainder and a whole stage");
+  constexpr uint32_t QL = BwdQueue<BATCH>::kLen;
+  static_assert(NS >= 2 && NS <= 4 && BATCH <= 256,
+                "queue entries hold a stage (2 bits) and a record index (8 bits)");
   extern __shared__ __align__(16) unsigned char bwd_smem[];
-  BwdSmem<TILE, FH>& S = *reinterpret_cast<BwdSmem<TILE, FH>*>(bwd_smem);
+  BwdSmem<TILE, FH, NS, BATCH>& S = *reinterpret_cast<BwdSmem<TILE, FH, NS, BATCH>*>(bwd_smem);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   pipe_init(S.Tb, S.bars, v, P, Sh::NCT);
   if (__syncthreads_or(dev_failed(v.hdr))) return;  // the whole CTA leaves, or none of it
   // the forward pass's tests apply when its footprints are these (8 rows)
   const bool use_masks = FH == 8 && *(volatile const uint32_t*)&v.hdr->fwd_masks != 0;
   if (warp == NW) {
-    produce<TILE, true, true, false>(S.st, S.bars, S.Tb, v, vals, 1, P, total_tiles, grad_image,
-                                     alpha, image, use_masks ? inst_mask : nullptr);
+    produce<TILE, true, true, false, NoPrep, NS, BATCH>(S.st, S.bars, S.Tb, v, vals, 1, P,
+                                                        total_tiles, grad_image, alpha, image,
+                                                        use_masks ? inst_mask : nullptr);
     return;
   }
   const uint32_t lt = lanemask_lt();
@@ -537,9 +553,9 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
   uint32_t krel = 0;                    // the stages before krel are released
   // item i of the queue (0 = its oldest) from row y0: its record read from its stage
   auto item = [&](uint32_t i, int y0, int rows, bool part) {
-    const uint32_t e = Q[(qhead + i) % kBwdQueue];
-    const RecStage<TILE, true>& Rs = S.st[e >> 7];
-    const int r = (int)(e & 127u);
+    const uint32_t e = Q[(qhead + i) % QL];
+    const RecStage<TILE, true, BATCH>& Rs = S.st[e >> 8];
+    const int r = (int)(e & 255u);
     const uint2 bx = Rs.box[r];
     const uint32_t cl = clip_box(bx, fj0, fi0, FH);
     if (part)
@@ -555,7 +571,8 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
     if (n > 16) {
       if (lane < (int)n) item(lane, 0, FH, false);
     } else {
-      const int lg = n > 8 ? 1 : 2;  // log2 of the lanes per item
+      // log2 of the lanes per item (each lane an even number of rows)
+      const int lg = (n > 8 || FH < 8) ? 1 : 2;
       const int it = lane & (31 >> lg), part = lane >> (5 - lg), rows = FH >> lg;
       if (it < (int)n) item(it, part * rows, rows, true);
     }
@@ -564,47 +581,49 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
   };
   // release the held stages up to `last` whose items are all processed, in order
   auto release = [&](uint32_t last) {
-    while (krel <= last && qend(krel % kBwdStages) <= qhead) {
-      mbar_arrive(&S.bars.empty[krel % kBwdStages]);
+    while (krel <= last && qend(krel % NS) <= qhead) {
+      mbar_arrive(&S.bars.empty[krel % NS]);
       ++krel;
     }
   };
   for (uint32_t k = 0;; ++k) {
-    const int s = (int)(k % kBwdStages);
-    if (k >= (uint32_t)kBwdStages && krel + kBwdStages <= k) {
-      // this wait reuses the slot of stage k - kBwdStages: process its items
+    const int s = (int)(k % NS);
+    if (k >= (uint32_t)NS && krel + NS <= k) {
+      // this wait reuses the slot of stage k - NS: process its items
       while (qhead < qend(s)) round();
       release(k - 1);
     }
-    if (!mbar_wait(&S.bars.full[s], (k / kBwdStages) & 1u)) {
+    if (!mbar_wait(&S.bars.full[s], (k / NS) & 1u)) {
       dev_fail(v.hdr, UG_ERR_TIMEOUT, 2);
       break;
     }
-    const RecStage<TILE, true>& R = S.st[s];
+    const RecStage<TILE, true, BATCH>& R = S.st[s];
     const StageHdr h = R.h;
     if (h.tile < 0) break;
     if (h.flags & kFirst) {
       // per-pixel factors of this warp's footprint: r = G / alpha and -r C
       // (0 off the plane); the previous tile's items are all processed
       footprint_origin(warp, T::FX, FH, h.tx, h.ty, TILE, fj0, fi0);
+      // layout: entry 8 rp + c holds rows 2 rp and 2 rp + 1 of column c
       for (int q = lane; q < FH * 4; q += 32) {
-        const int y = q / 4, cp = q % 4;
-        const int p0 = ((warp / T::FX) * FH + y) * TILE + (warp % T::FX) * 8 + 2 * cp;
+        const int rp = q / 8, c = q % 8;
+        const int p0 = ((warp / T::FX) * FH + 2 * rp) * TILE + (warp % T::FX) * 8 + c;
         float v4[4];
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
-          const float rv = R.raw[0][p0 + hh] / R.raw[1][p0 + hh];
+          const int pp = p0 + hh * TILE;
+          const float rv = R.raw[0][pp] / R.raw[1][pp];
           v4[hh] = rv;
-          v4[2 + hh] = -rv * R.raw[2][p0 + hh];
+          v4[2 + hh] = -rv * R.raw[2][pp];
         }
         S.pix[warp][q] = make_float4(v4[0], v4[1], v4[2], v4[3]);
       }
       __syncwarp();
     }
     // queue the stage's live records for this footprint, in record order
-    uint32_t m[kBatch / 32];
+    uint32_t m[BATCH / 32];
 #pragma unroll
-    for (int q = 0; q < kBatch / 32; ++q) {
+    for (int q = 0; q < BATCH / 32; ++q) {
       const int r = 32 * q + lane;
       m[q] = 0;
       if (r < h.cnt)
@@ -613,10 +632,10 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT)
     }
     const uint32_t q0 = qtail;
 #pragma unroll
-    for (int q = 0; q < kBatch / 32; ++q) {
+    for (int q = 0; q < BATCH / 32; ++q) {
       const uint32_t bl = __ballot_sync(0xffffffffu, m[q] & 1u);
       if (m[q] & 1u)
-        Q[(qtail + __popc(bl & lt)) % kBwdQueue] = (uint16_t)((s << 7) | (32 * q + lane));
+        Q[(qtail + __popc(bl & lt)) % QL] = (uint16_t)((s << 8) | (32 * q + lane));
       qtail += __popc(bl);
     }
     evaluated += qtail - q0;
@@ -659,57 +678,96 @@ static int occupancy_grid(K kernel, int threads, size_t dyn_smem = 0) {
   return device_sms() * (occ > 0 ? occ : 1);
 }
 
-template <int TILE, int G, int CUT>
+template <int TILE, int G, int CUT, int NS, int BATCH, int MINB>
 static cudaError_t fwd_launch(const ug_plan* plan, WsView v, const uint32_t* vals, float* image,
                               float* alpha, cudaStream_t s) {
-  constexpr int NT = FwdShape<TILE, G>::NT;
-  static const int grid = occupancy_grid(k_render_fwd<TILE, G, CUT>, NT);
+  constexpr int NT = FwdShape<TILE, G, MINB>::NT;
+  constexpr size_t SM = sizeof(FwdSmem<TILE, FwdShape<TILE, G, MINB>::NW, NS, BATCH>);
+  auto kern = k_render_fwd<TILE, G, CUT, NS, BATCH, MINB>;
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
+  if (attr != cudaSuccess) return attr;
+  static const int grid = occupancy_grid(kern, NT, SM);
   const int g = min(grid, max(plan->total_tiles, 1));
-  k_render_fwd<TILE, G, CUT><<<g, NT, 0, s>>>(v, vals, plan->num_planes, plan->total_tiles,
-                                              plan->cfg.alpha_bg, plan->cfg.c_bg, image, alpha,
-                                              inst_masks(plan, v));
+  kern<<<g, NT, SM, s>>>(v, vals, plan->num_planes, plan->total_tiles, plan->cfg.alpha_bg,
+                         plan->cfg.c_bg, image, alpha, inst_masks(plan, v));
   return cudaGetLastError();
 }
 
-template <int TILE, int FH, int CUT>
+template <int TILE, int FH, int CUT, int NS, int BATCH, int MINB>
 static cudaError_t bwd_launch(const ug_plan* plan, WsView v, const uint32_t* vals,
                               const float* image, const float* alpha, const float* grad,
                               cudaStream_t s) {
   constexpr int NT = BwdShape<TILE, FH>::NT;
-  constexpr size_t SM = sizeof(BwdSmem<TILE, FH>);
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      k_render_bwd<TILE, FH, CUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
+  constexpr size_t SM = sizeof(BwdSmem<TILE, FH, NS, BATCH>);
+  auto kern = k_render_bwd<TILE, FH, CUT, NS, BATCH, MINB>;
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
   if (attr != cudaSuccess) return attr;
-  static const int grid = occupancy_grid(k_render_bwd<TILE, FH, CUT>, NT, SM);
+  static const int grid = occupancy_grid(kern, NT, SM);
   const int g = min(grid, max(plan->total_tiles, 1));
-  k_render_bwd<TILE, FH, CUT><<<g, NT, SM, s>>>(v, vals, plan->num_planes, plan->total_tiles,
-                                                image, alpha, grad, inst_masks(plan, v));
+  kern<<<g, NT, SM, s>>>(v, vals, plan->num_planes, plan->total_tiles, image, alpha, grad,
+                         inst_masks(plan, v));
   return cudaGetLastError();
 }
 
-// Forward variants: lane groups per 8x8 footprint, 0 = 4 groups (8 rows per
-// lane), 1 = 2 groups (4 rows), 2 = 1 group (2 rows). Backward variants:
-// footprint height, 0 = 8 rows, 1 = 4 rows.
+// Forward variants (G lane groups per 8x8 footprint, NS stages in the ring,
+// BATCH records per stage, MINB resident blocks asked of the compiler, 0 =
+// the default):
+//   0: G 4 (8 pixels of one row per lane), NS 3, BATCH 128
+//   1: G 2 (4 pixels), 2: G 1 (2 pixels)
+//   3: G 4, BATCH 64, MINB 6     4: G 4, NS 2, BATCH 256     5: G 4, NS 4, MINB 4
+// (3-5 for the 16 x 16 tile only).
 template <int TILE, int CUT>
 static cudaError_t dispatch_fwd(const ug_plan* plan, WsView v, const uint32_t* vals, float* image,
                                 float* alpha, cudaStream_t s) {
   switch (plan->cfg.variant) {
-    case 0: return fwd_launch<TILE, 4, CUT>(plan, v, vals, image, alpha, s);
-    case 1: return fwd_launch<TILE, 2, CUT>(plan, v, vals, image, alpha, s);
-    default: return fwd_launch<TILE, 1, CUT>(plan, v, vals, image, alpha, s);
+    case 0: return fwd_launch<TILE, 4, CUT, 3, 128, 0>(plan, v, vals, image, alpha, s);
+    case 1: return fwd_launch<TILE, 2, CUT, 3, 128, 0>(plan, v, vals, image, alpha, s);
+    case 2: return fwd_launch<TILE, 1, CUT, 3, 128, 0>(plan, v, vals, image, alpha, s);
+    default: break;
   }
+  if constexpr (TILE == 16) {
+    switch (plan->cfg.variant) {
+      case 3: return fwd_launch<TILE, 4, CUT, 3, 64, 6>(plan, v, vals, image, alpha, s);
+      case 4: return fwd_launch<TILE, 4, CUT, 2, 256, 0>(plan, v, vals, image, alpha, s);
+      case 5: return fwd_launch<TILE, 4, CUT, 4, 128, 4>(plan, v, vals, image, alpha, s);
+      default: break;
+    }
+  }
+  return cudaErrorInvalidValue;
 }
 
+// Backward variants (FH footprint rows, NS stages, BATCH records per stage,
+// MINB resident blocks asked of the compiler, which bounds its registers):
+//   0: FH 8, NS 4, BATCH 128, MINB 4     1: FH 4, NS 4, BATCH 128, MINB 2 (tile 16)
+//   2: FH 8, NS 3, BATCH 128, MINB 5     3: FH 8, NS 4, BATCH 64, MINB 5
+//   4: FH 8, NS 3, BATCH 256, MINB 3
+// (2-4 for the 16 x 16 tile only).
 template <int TILE, int CUT>
 static cudaError_t dispatch_bwd(const ug_plan* plan, WsView v, const uint32_t* vals,
                                 const float* image, const float* alpha, const float* grad,
                                 cudaStream_t s) {
-  if (plan->cfg.variant_bwd == 0) return bwd_launch<TILE, 8, CUT>(plan, v, vals, image, alpha, grad, s);
-  return bwd_launch<TILE, 4, CUT>(plan, v, vals, image, alpha, grad, s);
+  switch (plan->cfg.variant_bwd) {
+    case 0: return bwd_launch<TILE, 8, CUT, 4, 128, 4>(plan, v, vals, image, alpha, grad, s);
+    case 1:  // twice the consumer warps per block: half the resident blocks
+      return bwd_launch<TILE, 4, CUT, 4, 128, TILE == 16 ? 2 : 4>(plan, v, vals, image, alpha,
+                                                                 grad, s);
+    default: break;
+  }
+  if constexpr (TILE == 16) {
+    switch (plan->cfg.variant_bwd) {
+      case 2: return bwd_launch<TILE, 8, CUT, 3, 128, 5>(plan, v, vals, image, alpha, grad, s);
+      case 3: return bwd_launch<TILE, 8, CUT, 4, 64, 5>(plan, v, vals, image, alpha, grad, s);
+      case 4: return bwd_launch<TILE, 8, CUT, 3, 256, 3>(plan, v, vals, image, alpha, grad, s);
+      default: break;
+    }
+  }
+  return cudaErrorInvalidValue;
 }
 
-int num_render_variants(int tile) { return tile == 16 || tile == 8 ? 3 : 0; }
-int num_render_variants_bwd(int tile) { return tile == 16 || tile == 8 ? 2 : 0; }
+int num_render_variants(int tile) { return tile == 16 ? 6 : tile == 8 ? 3 : 0; }
+int num_render_variants_bwd(int tile) { return tile == 16 ? 5 : tile == 8 ? 2 : 0; }
 
 cudaError_t launch_render(const ug_plan* plan, WsView v, float* image, float* alpha,
                           cudaStream_t s) {

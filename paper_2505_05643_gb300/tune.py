@@ -2,8 +2,11 @@
 timing them on the device (the workload's own records and tile lists):
 
 - tile edge: 16 or 8 pixels (binning and sort cost against culling granularity);
-- forward variant: lane groups per 8x8 footprint, i.e. pixels per lane (8, 4, 2);
-- backward variant: footprint height (8 or 4 rows).
+- forward variant: lane groups per 8x8 footprint, i.e. pixels per lane (8, 4, 2),
+  and for the 16-pixel tile the record pipeline's shape: records per
+  shared-memory stage (64, 128, 256) and stages in the ring (2, 3, 4);
+- backward variant: footprint height (8 or 4 rows), and for the 16-pixel tile
+  stages (3, 4) and records per stage (64, 128, 256).
 
 The forward and backward variants do not interact, so each is timed on its
 own, per tile edge, between CUDA events on the launching stream; a tile edge
@@ -34,7 +37,7 @@ def _time(fn, stream, warmup: int, reps: int) -> float:
 
 
 def autotune(n: int, planes: dict, params: torch.Tensor, targets: torch.Tensor, cov_param: int,
-             cutoff: int = B.UG_CUTOFF_BOX, tiles=(16, 8), warmup: int = 2, reps: int = 3,
+             cutoff: int = B.UG_CUTOFF_BOX, tiles=(16, 8), warmup: int = 2, reps: int = 7,
              **cfg_kw):
     """Returns (config, table): the fastest configuration for rendering `params`
     on `planes` with MSE against `targets`, and the measured milliseconds
@@ -42,7 +45,7 @@ def autotune(n: int, planes: dict, params: torch.Tensor, targets: torch.Tensor, 
     stream = torch.cuda.current_stream()
     table, best = {}, None
     for tile in tiles:
-        nf, nb = B.ug_num_variants(tile), 2
+        nf, nb = B.ug_num_variants(tile), B.ug_num_variants_bwd(tile)
         if nf == 0:
             continue
         cfg = R.make_config(cov_param=cov_param, cutoff=cutoff, tile=tile, variant=0,

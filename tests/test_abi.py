@@ -62,6 +62,8 @@ def test_versions_and_strings(lib):
     assert B.ug_version() >= 100
     assert B.status_string(B.UG_ERR_CAPACITY).startswith("record or instance")
     assert B.ug_num_variants(16) >= 1 and B.ug_num_variants(8) >= 1 and B.ug_num_variants(12) == 0
+    assert B.ug_num_variants_bwd(16) >= 2 and B.ug_num_variants_bwd(8) >= 2
+    assert B.ug_num_variants_bwd(12) == 0
 
 
 def _planes(sizes=((64, 64), (70, 45))):

@@ -12,10 +12,10 @@ round's remainder plus one stage."""
 import numpy as np
 import pytest
 
-BATCH = 128
+BATCHES = (64, 128, 256)  # records per stage of the compiled backward variants
 
 
-def _simulate(ns, tiles, warps, rng):
+def _simulate(ns, tiles, warps, rng, BATCH=128):
     """tiles: list of per-tile stage counts; returns the largest queue fill."""
     # the stream of stages: (tile end?, per-warp live item counts)
     stages = []
@@ -103,21 +103,30 @@ def _simulate(ns, tiles, warps, rng):
 
 
 @pytest.mark.parametrize("ns", [2, 3, 4])
-def test_release_protocol_progresses_and_releases_every_stage(ns):
-    rng = np.random.default_rng(ns)
+@pytest.mark.parametrize("batch", BATCHES)
+def test_release_protocol_progresses_and_releases_every_stage(ns, batch):
+    rng = np.random.default_rng(ns * 1000 + batch)
     worst = 0
     for _ in range(60):
         tiles = [int(rng.integers(1, 6)) for _ in range(int(rng.integers(1, 12)))]
-        worst = max(worst, _simulate(ns, tiles, warps=4, rng=rng))
-    assert worst <= 31 + BATCH
+        worst = max(worst, _simulate(ns, tiles, warps=4, rng=rng, BATCH=batch))
+    assert worst <= 31 + batch
 
 
 def test_queue_capacity_in_the_kernel_covers_the_bound():
-    """The kernel's queue (a ring of kBwdQueue entries) holds the model's bound."""
+    """The kernel's queue (a ring of BwdQueue<BATCH>::kLen entries) holds the
+    model's bound for every records-per-stage count, and the kernel asserts it
+    at compile time; the stage count fits the queue entries' two bits."""
     import re
     from pathlib import Path
     src = (Path(__file__).resolve().parents[1] / "paper_2505_05643_gb300" / "csrc" /
            "ug_render.cu").read_text()
-    q = int(re.search(r"constexpr int kBwdQueue = (\d+);", src).group(1))
+    m = re.search(r"kLen = BATCH <= (\d+) \? (\d+) : (\d+);", src)
+    cut, small, large = (int(x) for x in m.groups())
+    for batch in BATCHES:
+        assert (small if batch <= cut else large) >= 31 + batch
+    assert "static_assert(kLen >= 31 + BATCH" in src
     ns = int(re.search(r"constexpr int kBwdStages = (\d+);", src).group(1))
-    assert q >= 31 + BATCH and 2 <= ns <= 4
+    assert 2 <= ns <= 4
+    for v_ns, v_batch in re.findall(r"bwd_launch<TILE, \d, CUT, (\d), (\d+),", src):
+        assert 2 <= int(v_ns) <= 4 and int(v_batch) in BATCHES

@@ -130,13 +130,17 @@ def test_grad_extreme_anisotropy():
     _check_grads(gpu, gref, gabs, oracle.param_names(0), "aniso cut")
 
 
-@pytest.mark.parametrize("tile,variant", [(16, 1), (8, 0), (8, 1)])
+@pytest.mark.parametrize("tile,variant", [(16, v) for v in range(1, 5)] + [(8, 0), (8, 1)])
 def test_grad_variants(tile, variant):
+    """Every compiled backward variant (footprint height, stages, records per
+    stage) against the oracle's gradient; the stages of 64 records make tiles
+    span several stages."""
     rng = np.random.default_rng(32)
     g = synth.gaussians_scale_rot(rng, 1000, 0.03, 0.15)
     pl = synth.planes_random(rng, [(40, 33), (64, 64)])
     target = rng.uniform(0, 1, pl["total_pixels"])
-    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, tile=tile, variant=variant)
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, tile=tile, variant=min(variant, 2),
+                        variant_bwd=variant)
     gpu, gref, gabs, _ = _backward_case(g, pl, cfg, target)
     _check_grads(gpu, gref, gabs, oracle.param_names(1), f"variant t{tile} v{variant}")
 
@@ -204,7 +208,8 @@ def test_grad_50k_16_planes_subset_and_fd():
     """50,000 scale/rotation Gaussians, 16 planes of 256x256, MSE against
     targets rendered by the oracle from a separate seed-1 set of 50,000;
     gradients of a random subset of 500 Gaussians against the FP64 oracle
-    gradient, and a sample against FP64 central differences with h = 1e-3."""
+    gradient, and a sample against Richardson-extrapolated FP64 central
+    differences at rel 1e-3."""
     g, pl = synth.workload_grad_50k(seed=0)
     g_t, _ = synth.workload_grad_50k(seed=1)
     cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT)
@@ -218,44 +223,54 @@ def test_grad_50k_16_planes_subset_and_fd():
     gpu, gref, gabs, _ = _backward_case(g, pl, cfg, target, subset=subset)
     names = oracle.param_names(1)
     _check_grads(gpu, gref, gabs, names, "grad_50k")
-    # central differences of the FP64 oracle loss, h = 1e-3, on parameters whose
-    # pixel sets do not change at theta +- h; truncation error is O(h^2 / sigma^2)
+    # Central differences of the FP64 oracle loss on parameters whose pixel sets
+    # do not change at theta +- h and theta +- h/2, Richardson-extrapolated:
+    # D(h) = (L(theta + h) - L(theta - h)) / 2h = L' + c h^2 + O(h^4), so
+    # (4 D(h/2) - D(h)) / 3 = L' + O(h^4). Each parameter's step is scaled to
+    # its natural size (the means by the Gaussian's smallest scale), which puts
+    # the truncation error far below the GPU's tolerance of rel 1e-3.
     base = oracle.render(g, pl, ocfg)
     covp = oracle.covp_rows(g, 1)
     keys = [("mean", r) for r in range(3)] + [("log_scale", r) for r in range(3)] + \
         [("quat", r) for r in range(4)] + [("logit", None), ("intensity", None)]
-    h = 1e-3
     checked = 0
-    for si in range(6):
+
+    def loss_at(k, key, row, delta, pix0, w0):
+        gg = {kk: vv[..., k:k + 1].astype(np.float64).copy() for kk, vv in g.items()}
+        if row is None:
+            gg[key][0] += delta
+        else:
+            gg[key][row, 0] += delta
+        pix, w = oracle.contrib(gg["mean"][:, 0], oracle.covp_rows(gg, 1)[0],
+                                gg["logit"][0], gg["intensity"][0], pl, ocfg)
+        sa = base["sa"].copy()
+        sc = base["sc"].copy()
+        np.subtract.at(sa, pix0, w0)
+        np.subtract.at(sc, pix0, w0 * float(g["intensity"][k]))
+        np.add.at(sa, pix, w)
+        np.add.at(sc, pix, w * float(gg["intensity"][0]))
+        C = (sc + ocfg.alpha_bg * ocfg.c_bg) / (sa + ocfg.alpha_bg)
+        return np.mean((C - target) ** 2), np.array_equal(pix, pix0)
+
+    for si in range(12):
         k = int(subset[si])
         pix0, w0 = oracle.contrib(g["mean"][:, k], covp[k], g["logit"][k], g["intensity"][k], pl, ocfg)
         if len(pix0) < 20:
             continue
+        smin = float(np.exp(g["log_scale"][:, k].min()))
         for pi, (key, row) in enumerate(keys):
-            losses = []
-            same = True
-            for sgn in (1, -1):
-                gg = {kk: vv[..., k:k + 1].astype(np.float64).copy() for kk, vv in g.items()}
-                if row is None:
-                    gg[key][0] += sgn * h
-                else:
-                    gg[key][row, 0] += sgn * h
-                pix, w = oracle.contrib(gg["mean"][:, 0], oracle.covp_rows(gg, 1)[0],
-                                        gg["logit"][0], gg["intensity"][0], pl, ocfg)
-                same &= np.array_equal(pix, pix0)
-                sa = base["sa"].copy()
-                sc = base["sc"].copy()
-                np.subtract.at(sa, pix0, w0)
-                np.subtract.at(sc, pix0, w0 * float(g["intensity"][k]))
-                np.add.at(sa, pix, w)
-                np.add.at(sc, pix, w * float(gg["intensity"][0]))
-                C = (sc + ocfg.alpha_bg * ocfg.c_bg) / (sa + ocfg.alpha_bg)
-                losses.append(np.mean((C - target) ** 2))
+            h = 1e-2 * smin if key == "mean" else 1e-3
+            d, same = [], True
+            for hh in (h, h / 2):
+                lp, s1 = loss_at(k, key, row, hh, pix0, w0)
+                lm, s2 = loss_at(k, key, row, -hh, pix0, w0)
+                same &= s1 and s2
+                d.append((lp - lm) / (2 * hh))
             if not same:
                 continue
-            fd = (losses[0] - losses[1]) / (2 * h)
-            assert abs(fd - gpu[si, pi]) <= 5e-2 * abs(fd) + 1e-3 * gabs[si, pi] + 1e-14, \
-                (k, key, row, fd, gpu[si, pi])
+            fd = (4 * d[1] - d[0]) / 3
+            assert abs(fd - gpu[si, pi]) <= 1e-3 * abs(fd) + 1e-4 * gabs[si, pi] + 1e-15, \
+                (k, key, row, fd, gpu[si, pi], d)
             checked += 1
     assert checked >= 20
 

@@ -115,7 +115,7 @@ def test_dense_tiles_span_many_stages():
     assert_forward_parity(image, alpha, ref, "dense tiles")
 
 
-@pytest.mark.parametrize("tile,variant", [(16, v) for v in range(3)] + [(8, v) for v in range(3)])
+@pytest.mark.parametrize("tile,variant", [(16, v) for v in range(6)] + [(8, v) for v in range(3)])
 def test_ragged_planes_all_variants(tile, variant):
     """Planes whose sizes are not multiples of the tile (ragged tails), several
     sizes in one launch, every compiled rasterizer variant."""

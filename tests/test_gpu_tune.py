@@ -20,11 +20,12 @@ def test_autotune_choice_renders_the_same_image():
     targets = torch.from_numpy(synth.target_images(rng, pl["total_pixels"])).cuda()
     cfg, table = tune.autotune(len(g["logit"]), pl, params, targets, B.UG_COV_TRI)
     assert set(table) == {16, 8}
-    for t in table.values():
-        assert len(t["fwd"]) == B.ug_num_variants(16) and len(t["bwd"]) == 2
+    for tile, t in table.items():
+        assert len(t["fwd"]) == B.ug_num_variants(tile)
+        assert len(t["bwd"]) == B.ug_num_variants_bwd(tile)
         assert all(x > 0 for x in t["fwd"] + t["bwd"]) and t["pre_sort"] > 0
     assert cfg.tile in (8, 16) and 0 <= cfg.variant < B.ug_num_variants(cfg.tile)
-    assert cfg.variant_bwd in (0, 1)
+    assert 0 <= cfg.variant_bwd < B.ug_num_variants_bwd(cfg.tile)
     best = min(table, key=lambda k: table[k]["total"])
     assert cfg.tile == best
     img_t, _ = R.Renderer(len(g["logit"]), pl, cfg).forward(params)
