@@ -64,6 +64,18 @@ __device__ __forceinline__ dd dd_add(dd x, dd y) {
   return fast_two_sum(v.hi, w);
 }
 
+// SloppyDWPlusDW (Joldes, Muller and Popescu): 11 operations instead of 20.
+// Its error is bounded relative to the operands, |err| <= 2u^2 (|x| + |y|)
+// roughly, not to the result; that is all the geometry's sums need (their
+// operands already carry errors of that size), and it is the bound of the
+// accurate form's dot products as well.
+__device__ __forceinline__ dd dd_add_sloppy(dd x, dd y) {
+  const dd s = two_sum(x.hi, y.hi);
+  const float v = __fadd_rn(x.lo, y.lo);
+  const float w = __fadd_rn(s.lo, v);
+  return fast_two_sum(s.hi, w);
+}
+
 // DWTimesDW3
 __device__ __forceinline__ dd dd_mul(dd x, dd y) {
   const dd c = two_prod(x.hi, y.hi);
@@ -95,11 +107,42 @@ __device__ __forceinline__ bool operator<=(dd a, dd b) {
 }
 __device__ __forceinline__ bool operator>=(dd a, dd b) { return b <= a; }
 
-// The geometry's exact-rounding vocabulary for double words.
-__device__ __forceinline__ dd r_add(dd a, dd b) { return dd_add(a, b); }
-__device__ __forceinline__ dd r_sub(dd a, dd b) { return dd_add(a, -b); }
+// Compensated three-term dot products (the scheme of Ogita, Rump and Oishi's
+// Dot2, kept as a double word): the high parts' products by 2Prod and summed
+// by 2Sum, every error term and every low-part product summed in FP32, one
+// Fast2Sum at the end. |err| <= about 6u^2 sum |a_k b_k|, as for the chain of
+// double-word FMAs it replaces, at a third of the operations.
+__device__ __forceinline__ dd dd_dot3(const dd a[3], const float b[3]) {
+  const dd p0 = two_prod(a[0].hi, b[0]), p1 = two_prod(a[1].hi, b[1]),
+           p2 = two_prod(a[2].hi, b[2]);
+  float e = __fmaf_rn(a[0].lo, b[0], p0.lo);
+  e = __fmaf_rn(a[1].lo, b[1], __fadd_rn(e, p1.lo));
+  e = __fmaf_rn(a[2].lo, b[2], __fadd_rn(e, p2.lo));
+  const dd s = two_sum(p0.hi, p1.hi);
+  const dd t = two_sum(s.hi, p2.hi);
+  e = __fadd_rn(e, __fadd_rn(s.lo, t.lo));
+  return fast_two_sum(t.hi, e);
+}
+__device__ __forceinline__ dd dd_dot3(const dd a[3], const dd b[3]) {
+  const dd p0 = two_prod(a[0].hi, b[0].hi), p1 = two_prod(a[1].hi, b[1].hi),
+           p2 = two_prod(a[2].hi, b[2].hi);
+  float e = __fmaf_rn(a[0].hi, b[0].lo, __fmaf_rn(a[0].lo, b[0].hi, p0.lo));
+  e = __fadd_rn(e, __fmaf_rn(a[1].hi, b[1].lo, __fmaf_rn(a[1].lo, b[1].hi, p1.lo)));
+  e = __fadd_rn(e, __fmaf_rn(a[2].hi, b[2].lo, __fmaf_rn(a[2].lo, b[2].hi, p2.lo)));
+  const dd s = two_sum(p0.hi, p1.hi);
+  const dd t = two_sum(s.hi, p2.hi);
+  e = __fadd_rn(e, __fadd_rn(s.lo, t.lo));
+  return fast_two_sum(t.hi, e);
+}
+
+// The geometry's exact-rounding vocabulary for double words (sums by the
+// sloppy addition; a double word times an FP32 number by DWTimesFP3).
+__device__ __forceinline__ dd r_add(dd a, dd b) { return dd_add_sloppy(a, b); }
+__device__ __forceinline__ dd r_sub(dd a, dd b) { return dd_add_sloppy(a, -b); }
 __device__ __forceinline__ dd r_mul(dd a, dd b) { return dd_mul(a, b); }
-__device__ __forceinline__ dd r_fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
+__device__ __forceinline__ dd r_mul(dd a, float b) { return dd_mul(a, b); }
+__device__ __forceinline__ dd r_fma(dd a, dd b, dd c) { return dd_add_sloppy(dd_mul(a, b), c); }
+__device__ __forceinline__ dd r_fma(dd a, float b, dd c) { return dd_add_sloppy(dd_mul(a, b), c); }
 
 // Division and square root of values that are already accurate run in FP32
 // (see the FP32 and FP64 overloads beside the geometry).

@@ -80,6 +80,10 @@ template <typename T>
 __device__ __forceinline__ T r_dot3(const T a[3], const T b[3]) {
   return r_fma(a[2], b[2], r_fma(a[1], b[1], r_mul(a[0], b[0])));
 }
+// double words: the compensated dot products (ug_dd.cuh)
+__device__ __forceinline__ dd r_dot3(const dd a[3], const dd b[3]) { return dd_dot3(a, b); }
+__device__ __forceinline__ dd r_dot3(const dd a[3], const float b[3]) { return dd_dot3(a, b); }
+__device__ __forceinline__ dd r_dot3(const float b[3], const dd a[3]) { return dd_dot3(a, b); }
 
 // Parameters of one Gaussian as loaded from the structure-of-arrays rows.
 struct GaussParams {
@@ -236,8 +240,8 @@ __device__ __forceinline__ float axis_ratio_proxy(const Factor<float>& f) {
 }
 
 // z = Fi r (Sigma3D_jk = z_j . z_k).
-template <typename T, int COV>
-__device__ __forceinline__ void apply_fi(const Factor<T>& f, const T r[3], T z[3]) {
+template <typename T, int COV, typename R>
+__device__ __forceinline__ void apply_fi(const Factor<T>& f, const R r[3], T z[3]) {
   if (COV == UG_COV_TRI) {
     z[0] = r_mul(f.Fi[0][0], r[0]);
     z[1] = r_fma(f.Fi[1][1], r[1], r_mul(f.Fi[1][0], r[0]));
@@ -250,8 +254,8 @@ __device__ __forceinline__ void apply_fi(const Factor<T>& f, const T r[3], T z[3
 }
 
 // b = F^T r (probe-frame precision P3D_jk = b_j . b_k).
-template <typename T, int COV>
-__device__ __forceinline__ void apply_ft(const Factor<T>& f, const T r[3], T b[3]) {
+template <typename T, int COV, typename R>
+__device__ __forceinline__ void apply_ft(const Factor<T>& f, const R r[3], T b[3]) {
   if (COV == UG_COV_TRI) {
     b[0] = r_fma(f.F[2][0], r[2], r_fma(f.F[1][0], r[1], r_mul(f.F[0][0], r[0])));
     b[1] = r_fma(f.F[2][1], r[2], r_mul(f.F[1][1], r[1]));
@@ -263,21 +267,30 @@ __device__ __forceinline__ void apply_ft(const Factor<T>& f, const T r[3], T b[3
   }
 }
 
-// Plane axes in precision T.
-template <typename T>
+// Plane axes: FP32 numbers as given (products with double words then take
+// the cheaper double word x FP32 form).
 struct Frame {
-  T o[3], r[3][3];  // rows u, v, n
+  float o[3], r[3][3];  // rows u, v, n
 };
 
-template <typename T>
-__device__ __forceinline__ void load_frame(const PlaneDev& pl, Frame<T>& fr) {
+__device__ __forceinline__ void load_frame(const PlaneDev& pl, Frame& fr) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    fr.o[k] = (T)pl.o[k];
-    fr.r[0][k] = (T)pl.u[k];
-    fr.r[1][k] = (T)pl.v[k];
-    fr.r[2][k] = (T)pl.n[k];
+    fr.o[k] = pl.o[k];
+    fr.r[0][k] = pl.u[k];
+    fr.r[1][k] = pl.v[k];
+    fr.r[2][k] = pl.n[k];
   }
+}
+
+// mu - o: exact as a double word (2Sum), rounded once in FP32.
+__device__ __forceinline__ void mean_offset(const float mu[3], const float o[3], dd d[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = two_sum(mu[k], -o[k]);
+}
+__device__ __forceinline__ void mean_offset(const float mu[3], const float o[3], float d[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = __fsub_rn(mu[k], o[k]);
 }
 
 // Phase 1 and the pixel box of one (plane, Gaussian) pair.
@@ -323,11 +336,11 @@ __device__ __forceinline__ PairBox pair_box(const Factor<T>& f, const PlaneDev& 
   pb.j1 = 0;
   pb.i0 = 1;
   pb.i1 = 0;
-  Frame<T> fr;
+  Frame fr;
   load_frame(pl, fr);
   T* d = g.d;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) d[k] = r_sub(f.mu[k], fr.o[k]);
+  for (int k = 0; k < 3; ++k) d[k] = r_sub(f.mu[k], (T)fr.o[k]);
   g.m[2] = r_dot3(fr.r[2], d);
   apply_fi<T, COV>(f, fr.r[2], g.z[2]);
   g.S33 = r_dot3(g.z[2], g.z[2]);
@@ -346,6 +359,31 @@ __device__ __forceinline__ PairBox pair_box(const Factor<T>& f, const PlaneDev& 
   pixel_range<T>(g.m[1], h2, (T)pl.inv_pv, (T)pl.ishift, pl.h, pb.i0, pb.i1);
   pb.visible = (pb.j0 <= pb.j1) && (pb.i0 <= pb.i1);
   return pb;
+}
+
+// The phase-1 test and pixel box of a pair in FP32 from any factor: the mean
+// and the inverse factor rounded to FP32 (for a double-word factor, its
+// inverse computed in double words, then rounded once). The decisions only
+// need absolute accuracy (the oracle's ambiguity margins): the rounding of
+// Fi r is a few ulps of |Fi| |r| whatever Fi's condition, and that of
+// mu - o a few ulps of the scene's coordinates.
+template <typename T, int COV>
+__device__ __forceinline__ PairBox pair_box_f32(const Factor<T>& f, const PlaneDev& pl,
+                                                float chi2) {
+  if constexpr (!is_ext<T>::value) {
+    PairGeo<float> g;
+    return pair_box<float, COV>(f, pl, chi2, g);
+  } else {
+    Factor<float> ff;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ff.mu[k] = (float)f.mu[k];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) ff.Fi[k][j] = (float)f.Fi[k][j];
+    }
+    PairGeo<float> g;
+    return pair_box<float, COV>(ff, pl, chi2, g);
+  }
 }
 
 // Render-side geometry of a visible pair in the plane's own coordinates. With
@@ -377,7 +415,7 @@ __device__ __forceinline__ float to_f(T x) {
 template <typename T, int COV>
 __device__ __forceinline__ void pair_lsq(const Factor<T>& f, const PlaneDev& pl,
                                          const PairGeo<T>& g, PairLsq<T>& o) {
-  Frame<T> fr;
+  Frame fr;
   load_frame(pl, fr);
   T b1[3], b2[3], c[3];
   apply_ft<T, COV>(f, fr.r[0], b1);
@@ -407,7 +445,7 @@ __device__ __forceinline__ void pair_lsq(const Factor<T>& f, const PlaneDev& pl,
   o.X = r_fma(x, ipu, (T)pl.half_w);
   o.Y = r_fma(y, ipv, (T)pl.half_h);
   // kappa = (r12 pv) / (r11 pu)
-  o.kappa = r_mul(r_mul(r_mul(r12, ir11), (T)pl.pv), ipu);
+  o.kappa = r_mul(r_mul(r_mul(r12, ir11), pl.pv), ipu);
   const float sc = 0.84932180028801904272f;  // sqrt(log2(e) / 2)
   o.r11 = __fmul_rn(__fmul_rn(sc, pl.pu), to_f(r11));
   o.r22 = __fmul_rn(__fmul_rn(sc, pl.pv), to_f(r22));

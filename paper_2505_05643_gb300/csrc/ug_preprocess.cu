@@ -491,10 +491,13 @@ __global__ void __launch_bounds__(256)
     load_params(g, n, e.x, COV, prm);
     Factor<T> f;
     make_factor<T, COV>(prm, beta, f);
-    PairGeo<T> gg;
-    const PairBox pb = pair_box<T, COV>(f, pl, chi2, gg);
+    // the decisions (phase 1, pixel box) in FP32 for both branches; the render
+    // geometry in T from the exact mean offset
+    const PairBox pb = pair_box_f32<T, COV>(f, pl, chi2);
     v.rec_plane[slot] = e.y;
     if (pb.visible) {
+      PairGeo<T> gg;
+      mean_offset(prm.mu, pl.o, gg.d);
       PairLsq<T> L;
       pair_lsq<T, COV>(f, pl, gg, L);
       write_record<T>(L, pb, prm, chi2, v, slot);

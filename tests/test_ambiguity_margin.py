@@ -9,7 +9,9 @@ decision quantities are reproduced operation by operation in NumPy float32
 (the probe-frame mean m = R (mu - o), the half-extents h = sqrt(chi2 |F^-1 r|^2)
 with F^-1 by forward substitution, and the pixel-unit box edges (m1 -+ h1) /
 pitch + W/2 - 1/2), for the Gaussians the kernel sends down its FP32 geometry,
-and compared with FP64. Every error must stay well inside the margin, and the
+and compared with FP64. The extended-precision branch takes the same FP32
+decisions from its inverse factor computed in double words and rounded once
+(emulated by the FP64 inverse rounded to FP32), also checked here. Every error must stay well inside the margin, and the
 absolute term must be needed: the relative one alone is too small."""
 import numpy as np
 
@@ -33,17 +35,34 @@ def dot3(a, b):
     return fma(a[2], b[2], fma(a[1], b[1], (a[0] * b[0]).astype(f32)))
 
 
-def kernel_decisions(tri, mu, pl_o, pl_u, pl_v, pu, W):
+def _fp64_inverse(tri):
+    t = tri.astype(np.float64)
+    b = float(BETA)
+    L = np.zeros((t.shape[1], 3, 3))
+    L[:, 0, 0], L[:, 1, 1], L[:, 2, 2] = t[0] ** 2 + b, t[3] ** 2 + b, t[5] ** 2 + b
+    L[:, 1, 0], L[:, 2, 0], L[:, 2, 1] = t[1], t[2], t[4]
+    return np.linalg.inv(L)
+
+
+def kernel_decisions(tri, mu, pl_o, pl_u, pl_v, pu, W, extended=False):
     """FP32 decision quantities as the record kernel computes them for the
     triangular front-end: the plane test margin h3 - |m3| and the first and
-    last pixel-unit box edge along u."""
-    t = [tri[k].astype(f32) for k in range(6)]
-    F00, F11, F22 = fma(t[0], t[0], BETA), fma(t[3], t[3], BETA), fma(t[5], t[5], BETA)
-    F10, F20, F21 = t[1], t[2], t[4]
-    i00, i11, i22 = (f32(1) / F00).astype(f32), (f32(1) / F11).astype(f32), (f32(1) / F22).astype(f32)
-    i10 = -((F10 * i00).astype(f32) * i11).astype(f32)
-    i21 = -((F21 * i11).astype(f32) * i22).astype(f32)
-    i20 = -(fma(F21, i10, (F20 * i00).astype(f32)) * i22).astype(f32)
+    last pixel-unit box edge along u. extended: the inverse factor of the
+    extended-precision branch (accurate, rounded once to FP32) instead of the
+    FP32 forward substitution."""
+    if extended:
+        Li = _fp64_inverse(tri).astype(f32)
+        i00, i11, i22 = Li[:, 0, 0], Li[:, 1, 1], Li[:, 2, 2]
+        i10, i20, i21 = Li[:, 1, 0], Li[:, 2, 0], Li[:, 2, 1]
+    else:
+        t = [tri[k].astype(f32) for k in range(6)]
+        F00, F11, F22 = fma(t[0], t[0], BETA), fma(t[3], t[3], BETA), fma(t[5], t[5], BETA)
+        F10, F20, F21 = t[1], t[2], t[4]
+        i00, i11, i22 = ((f32(1) / F00).astype(f32), (f32(1) / F11).astype(f32),
+                         (f32(1) / F22).astype(f32))
+        i10 = -((F10 * i00).astype(f32) * i11).astype(f32)
+        i21 = -((F21 * i11).astype(f32) * i22).astype(f32)
+        i20 = -(fma(F21, i10, (F20 * i00).astype(f32)) * i22).astype(f32)
     u, v, o = pl_u.astype(f32), pl_v.astype(f32), pl_o.astype(f32)
     n = np.stack([fma(u[1], v[2], -(u[2] * v[1]).astype(f32)),
                   fma(u[2], v[0], -(u[0] * v[2]).astype(f32)),
@@ -95,11 +114,11 @@ def exact_decisions(tri, mu, pl_o, pl_u, pl_v, pu, W):
     return h3 - np.abs(m3), (m1 - h1) / p + shift, (m1 + h1) / p + shift, h3
 
 
-def _check(g_tri, mu, planes, select):
+def _check(g_tri, mu, planes, select, extended=False):
     o, u, v = planes["origin"].T, planes["u"].T, planes["v"].T
     pu = planes["pitch"][:, 0].astype(np.float64)
     W = planes["size"][:, 0]
-    k_pl, k_lo, k_hi = kernel_decisions(g_tri, mu, o, u, v, pu, W)
+    k_pl, k_lo, k_hi = kernel_decisions(g_tri, mu, o, u, v, pu, W, extended)
     e_pl, e_lo, e_hi, h3 = exact_decisions(g_tri, mu, o, u, v, pu, W)
     sel = np.broadcast_to(select[None, :], k_pl.shape)
     plane_err = np.abs(k_pl - e_pl)[sel]
@@ -159,6 +178,25 @@ def test_margins_cover_fp32_decisions_of_paper_init_and_default_criterion():
             continue
         r_pl, r_edge, *_ = _check(g["tri"], g["mean"], pl, sel)
         assert r_pl < 0.5 and r_edge < 0.5, (r_pl, r_edge)
+
+
+def test_margins_cover_fp32_decisions_of_the_extended_branch():
+    """The bench workload's extreme anisotropy (axis ratios to 1e4): the
+    Gaussians the default criterion sends down the extended-precision branch
+    take their decisions in FP32 from the accurately computed inverse factor,
+    rounded once; every error stays well inside the margins."""
+    rng = np.random.default_rng(74)
+    g = synth.scale_rot_to_tri(synth.gaussians_anisotropic(rng, 100_000), float(BETA))
+    pl = _planes(rng)
+    sel = ~_fp32_branch(g["tri"], g["mean"], pl)
+    assert sel.mean() > 0.9
+    r_pl, r_edge, abs_pl, abs_edge, _ = _check(g["tri"], g["mean"], pl, sel, extended=True)
+    assert r_pl < 0.5 and r_edge < 0.5, (r_pl, r_edge)
+    assert abs_edge < AMB_ABS and abs_pl < AMB_ABS
+    # the FP32 forward substitution would not do for these (its error grows
+    # with the factor's condition)
+    r_pl32, r_edge32, *_ = _check(g["tri"], g["mean"], pl, sel, extended=False)
+    assert max(r_pl32, r_edge32) > max(r_pl, r_edge)
 
 
 def test_emulation_detects_a_planted_error():
