@@ -863,8 +863,9 @@ def run_recon(args):
     learning rates, the means' rate decaying over the run), each step on 32
     poses drawn from a pool of training poses; SSIM and PSNR (the evaluator
     kernel) on the evaluation poses and on up to 128 training poses every
-    --recon-eval steps; the training time to reach SSIM thresholds; then
-    forward-only novel-slice rendering of 512x512 planes, images per second.
+    --recon-eval steps; the training time to reach SSIM thresholds, without
+    and with the densify / prune step (--recon-densify); then forward-only
+    novel-slice rendering of 512x512 planes, images per second.
     --recon-poses random: random training and held-out poses (256x256);
     slices: the paper's ideal setting (Sec. 5.1), training on linearly spaced
     axial slices and evaluating on linearly spaced axial, coronal and sagittal
@@ -911,25 +912,19 @@ def run_recon(args):
                 synth.planes_to_struct(synth.select_planes(tr, list(idx))).view(np.uint8).copy()).to(dev)
         return win_struct[key]
 
-    params = torch.from_numpy(R.pack_params(g, B.UG_COV_TRI)).to(dev)
-    r = R.Renderer(n, synth.select_planes(tr, list(range(P))), cfg)
-    targets = torch.empty(P * npx, device=dev)
-    step = T.TrainStep(r, params, targets, decay_steps=steps, loss=args.recon_loss,
-                       plane_shape=(size, size))
-
-    def eval_set(planes, tgt):
-        m = len(planes["size"])
-        return [(R.Renderer(n, synth.select_planes(planes, list(range(c0, min(c0 + 32, m)))), cfg),
-                 tgt[c0:min(c0 + 32, m)].reshape(-1)) for c0 in range(0, m, 32)]
-
-    test_set = eval_set(te, t_test)
-    train_idx = np.linspace(0, pool - 1, min(128, pool)).round().astype(np.int64)
-    train_set = eval_set(synth.select_planes(tr, list(train_idx)),
-                         t_train.index_select(0, torch.from_numpy(train_idx).to(dev)))
+    p_init = torch.from_numpy(R.pack_params(g, B.UG_COV_TRI)).to(dev)
     scratch = torch.empty(B.ug_ssim_scratch_floats(32, size, size), device=dev)
     ss, ps = torch.empty(32, device=dev), torch.empty(32, device=dev)
+    train_idx = np.linspace(0, pool - 1, min(128, pool)).round().astype(np.int64)
+    train_eval_planes = synth.select_planes(tr, list(train_idx))
+    train_eval_tgt = t_train.index_select(0, torch.from_numpy(train_idx).to(dev))
 
-    def evaluate(es):
+    def eval_set(planes, tgt, nn):
+        m = len(planes["size"])
+        return [(R.Renderer(nn, synth.select_planes(planes, list(range(c0, min(c0 + 32, m)))), cfg),
+                 tgt[c0:min(c0 + 32, m)].reshape(-1)) for c0 in range(0, m, 32)]
+
+    def evaluate(es, params):
         vals_s, vals_p = [], []
         for rr, tt in es:
             img, _ = rr.forward(params)
@@ -939,58 +934,143 @@ def run_recon(args):
             vals_p.append(ps[:m].cpu().numpy().copy())
         return np.concatenate(vals_s), np.concatenate(vals_p)
 
-    def record(k, train_s, loss=None):
-        sv, pv = evaluate(test_set)
-        st, _ = evaluate(train_set)
-        h = {"step": k, "train_s": train_s, "ssim": float(sv.mean()), "psnr": float(pv.mean()),
-             "train_ssim": float(st.mean())}
-        if slices:  # axial, coronal, sagittal means
-            h["ssim_axes"] = [float(x.mean()) for x in np.split(sv, 3)]
-        if loss is not None:
-            h["loss"] = loss
-        return h
+    def train(densify):
+        """One training run from the initial Gaussians; with densify, the
+        densify / prune step (ug_densify_stats every step, ug_densify every
+        --densify-every steps in [--densify-every, steps / 2], up to
+        --densify-max times the initial count), Adam moments carried."""
+        params = p_init.clone()
+        nn = n
+        r = R.Renderer(nn, synth.select_planes(tr, list(range(P))), cfg)
+        targets = torch.empty(P * npx, device=dev)
+        step = T.TrainStep(r, params, targets, decay_steps=steps, loss=args.recon_loss,
+                           plane_shape=(size, size))
+        sets = {}
 
-    history = [record(0, 0.0)]
-    train_ms = 0.0
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    order = rng.permutation(pool)
-    for k in range(steps):
-        o = (k * P) % pool
-        if k > 0 and o < P:  # a new epoch: a new order of the training poses
-            order = rng.permutation(pool)
-        idx = np.sort(order[o:o + P]) if o + P <= pool else np.sort(order[:P])
-        r.d_planes.copy_(pose_struct(idx))
-        targets.copy_(t_train.index_select(0, torch.from_numpy(idx).to(dev)).view(-1))
-        e0.record()
-        r.preprocess(params, check=True)  # grows the workspace when the records outgrow it
-        step.g_struct = R.gaussians_struct(params, B.UG_COV_TRI)
-        B.ug_bin_sort(r.plan, r.ws)
-        B.ug_render(r.plan, r.ws, step.image, step.alpha)
-        if args.recon_loss == "mse":
-            B.ug_mse_loss_grad(step.image, targets, step.image.numel(), step.grad_image, step.loss)
-        else:
-            B.ug_l1_dssim_loss_grad(step.image, targets, *step.dssim_shape, T.DSSIM_LAMBDA,
-                                    step.dssim_scratch, step.grad_image, step.loss)
-        B.ug_render_backward(r.plan, step.g_struct, r.d_planes, r.ws, step.image, step.alpha,
-                             step.grad_image, step.grad_struct)
-        B.ug_adam_step(params, step.grads, step.m, step.v, r.rows, n, step.lr_rows, step.step,
-                       T.BETA1, T.BETA2, T.EPS)
-        e1.record()
-        e1.synchronize()
-        train_ms += e0.elapsed_time(e1)
-        stt = r.status()
-        assert stt["status"] == B.UG_OK, stt
-        if (k + 1) % every == 0 or k + 1 == steps:
-            history.append(record(k + 1, train_ms / 1e3, float(step.loss[0])))
-            hh = history[-1]
-            print(f"[recon] step {k + 1} train {hh['train_s']:.2f} s ssim {hh['ssim']:.4f} "
-                  f"(train poses {hh['train_ssim']:.4f}) psnr {hh['psnr']:.2f}", file=sys.stderr)
+        def record(k, train_s, loss=None):
+            if nn not in sets:  # evaluation renderers for this Gaussian count
+                sets.clear()
+                torch.cuda.empty_cache()
+                sets[nn] = (eval_set(te, t_test, nn), eval_set(train_eval_planes, train_eval_tgt, nn))
+            sv, pv = evaluate(sets[nn][0], params)
+            st, _ = evaluate(sets[nn][1], params)
+            h = {"step": k, "train_s": train_s, "ssim": float(sv.mean()), "psnr": float(pv.mean()),
+                 "train_ssim": float(st.mean()), "gaussians": nn}
+            if slices:  # axial, coronal, sagittal means
+                h["ssim_axes"] = [float(x.mean()) for x in np.split(sv, 3)]
+            if loss is not None:
+                h["loss"] = loss
+            return h
 
-    def time_to(th, key="ssim"):
+        history = [record(0, 0.0)]
+        train_ms = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        rng = np.random.default_rng(6)
+        order = rng.permutation(pool)
+        dcfg = B.ug_densify_config_default()
+        stats = torch.zeros((2, nn), device=dev) if densify else None
+        zgen = torch.Generator(device=dev)
+        zgen.manual_seed(8)
+        dlog = []
+        for k in range(steps):
+            o = (k * P) % pool
+            if k > 0 and o < P:  # a new epoch: a new order of the training poses
+                order = rng.permutation(pool)
+            idx = np.sort(order[o:o + P]) if o + P <= pool else np.sort(order[:P])
+            r.d_planes.copy_(pose_struct(idx))
+            targets.copy_(t_train.index_select(0, torch.from_numpy(idx).to(dev)).view(-1))
+            e0.record()
+            r.preprocess(params, check=True)  # grows the workspace when the records outgrow it
+            step.g_struct = R.gaussians_struct(params, B.UG_COV_TRI)
+            B.ug_bin_sort(r.plan, r.ws)
+            B.ug_render(r.plan, r.ws, step.image, step.alpha)
+            if args.recon_loss == "mse":
+                B.ug_mse_loss_grad(step.image, targets, step.image.numel(), step.grad_image,
+                                   step.loss)
+            else:
+                B.ug_l1_dssim_loss_grad(step.image, targets, *step.dssim_shape, T.DSSIM_LAMBDA,
+                                        step.dssim_scratch, step.grad_image, step.loss)
+            B.ug_render_backward(r.plan, step.g_struct, r.d_planes, r.ws, step.image, step.alpha,
+                                 step.grad_image, step.grad_struct)
+            if densify:
+                B.ug_densify_stats(step.grads, nn, stats)  # the mean rows come first
+            B.ug_adam_step(params, step.grads, step.m, step.v, r.rows, nn, step.lr_rows, step.step,
+                           T.BETA1, T.BETA2, T.EPS)
+            if densify and (k + 1) % args.densify_every == 0 and k + 1 <= steps // 2 \
+                    and nn < args.densify_max * n:
+                if dcfg.grad_threshold == B.ug_densify_config_default().grad_threshold:
+                    # the threshold, fixed at the first interval: the level of
+                    # the top 2 % of the counted Gaussians' mean |dL/dmu|
+                    st_h = stats.cpu().numpy()
+                    cnt = st_h[1] > 0
+                    mean = st_h[0][cnt] / st_h[1][cnt]
+                    dcfg.grad_threshold = float(np.quantile(mean, 0.98)) if mean.size else 1.0
+                cap = 2 * nn
+                po = torch.empty((r.rows, cap), device=dev)
+                mo, vo = torch.empty_like(po), torch.empty_like(po)
+                n_out = torch.zeros(1, dtype=torch.int64, device=dev)
+                z = torch.randn((6, nn), device=dev, generator=zgen)
+                scr = torch.empty(B.ug_densify_scratch_bytes(nn), dtype=torch.uint8, device=dev)
+                B.ug_densify(cfg, dcfg, params, step.m, step.v, nn, stats, z, cap, po, mo, vo,
+                             n_out, scr)
+                new_n = int(n_out.item())
+                assert 0 < new_n <= cap
+                params = po[:, :new_n].contiguous()
+                m_new, v_new = mo[:, :new_n].contiguous(), vo[:, :new_n].contiguous()
+                stp = step.step.clone()
+                del po, mo, vo, scr, z, step, r
+                torch.cuda.empty_cache()
+                dlog.append({"step": k + 1, "before": nn, "after": new_n})
+                nn = new_n
+                r = R.Renderer(nn, synth.select_planes(tr, list(range(P))), cfg)
+                step = T.TrainStep(r, params, targets, decay_steps=steps, loss=args.recon_loss,
+                                   plane_shape=(size, size))
+                step.m.copy_(m_new)
+                step.v.copy_(v_new)
+                step.step.copy_(stp)
+                stats = torch.zeros((2, nn), device=dev)
+            e1.record()
+            e1.synchronize()
+            train_ms += e0.elapsed_time(e1)
+            stt = r.status()
+            assert stt["status"] == B.UG_OK, stt
+            if (k + 1) % every == 0 or k + 1 == steps:
+                history.append(record(k + 1, train_ms / 1e3, float(step.loss[0])))
+                hh = history[-1]
+                print(f"[recon{' densify' if densify else ''}] step {k + 1} train "
+                      f"{hh['train_s']:.2f} s ssim {hh['ssim']:.4f} (train poses "
+                      f"{hh['train_ssim']:.4f}) psnr {hh['psnr']:.2f} gaussians {nn}",
+                      file=sys.stderr)
+        sets.clear()
+        return history, params, train_ms, nn, dlog, dcfg.grad_threshold
+
+    def time_to(history, th, key="ssim"):
         for h in history:
             if h[key] >= th:
                 return h["train_s"]
         return None
+
+    runs = {}
+    modes = {"off": [False], "on": [True], "both": [False, True]}[args.recon_densify]
+    for densify in modes:
+        history, params_run, train_ms, n_final, dlog, thr = train(densify)
+        runs["densify" if densify else "plain"] = {
+            "train_s": train_ms / 1e3, "ms_per_step": train_ms / steps,
+            "gaussians_final": n_final,
+            "time_to_ssim": {str(th): time_to(history, th) for th in (0.8, 0.9, 0.95, 0.99)},
+            "time_to_train_ssim": {str(th): time_to(history, th, "train_ssim")
+                                   for th in (0.9, 0.95, 0.99)},
+            "final": history[-1], "history": history,
+            **({"densify_steps": dlog, "grad_threshold": thr,
+                "densify_every": args.densify_every, "densify_max": args.densify_max}
+               if densify else {})}
+        if not densify or "plain" not in runs:
+            params = params_run  # the novel-slice rendering below uses the plain run's model
+        else:
+            del params_run
+        torch.cuda.empty_cache()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = int(params.shape[1])
 
     # novel-slice rendering: 512 random poses of 512x512, 32 per launch (fewer
     # when a launch would hold more than 2^31 tile instances)
@@ -1036,10 +1116,8 @@ def run_recon(args):
                                   f"sagittal slices each (training: {pool} axial slices)"
                                   if slices else f"{len(te['size'])} held-out poses (seed 4)"),
                    "poses": args.recon_poses, "loss": args.recon_loss},
-        "train_s": train_ms / 1e3, "ms_per_step": train_ms / steps,
-        "time_to_ssim": {str(th): time_to(th) for th in (0.8, 0.9, 0.95, 0.99)},
-        "time_to_train_ssim": {str(th): time_to(th, "train_ssim") for th in (0.9, 0.95, 0.99)},
-        "final": history[-1], "history": history,
+        "runs": runs,
+        "novel_slice_model": "plain" if "plain" in runs else "densify",
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -1287,6 +1365,12 @@ def main():
     ap.add_argument("--recon-poses", default="random", choices=["random", "slices"],
                     help="random: random training and held-out poses; slices: linearly spaced "
                          "axial training slices, axial/coronal/sagittal evaluation slices")
+    ap.add_argument("--recon-densify", default="both", choices=["off", "on", "both"],
+                    help="reconstruction run without and/or with the densify / prune step")
+    ap.add_argument("--densify-every", type=int, default=100,
+                    help="steps between densify / prune steps (up to half the run)")
+    ap.add_argument("--densify-max", type=float, default=2.0,
+                    help="no densify step once the count exceeds this times the initial one")
     ap.add_argument("--recon-size", type=int, default=None,
                     help="plane edge in pixels (default 256 random, 160 slices)")
     ap.add_argument("--ablation", default=None, choices=["scatter"],

@@ -192,7 +192,9 @@ ug_status ug_config_default(ug_config* cfg);
 /* Validate a configuration and the HOST copy of the planes (sizes, pixel
  * offsets, finite orthonormal poses) and fill *plan: tile counts, key bits,
  * and the workspace size for the given capacities. record_capacity and
- * instance_capacity must be >= 1; instance_capacity < 2^31. The plane poses
+ * instance_capacity must be >= 1; instance_capacity < 2^31. The planes may
+ * hold at most 2^24 tiles in all (UG_ERR_NOT_SUPPORTED beyond: a sort key
+ * keeps its top byte for the instance's footprint tests). The plane poses
  * may change later in device memory; their sizes may not. */
 ug_status ug_plan_init(const ug_config* cfg, int64_t n, const ug_plane* host_planes,
                        int32_t num_planes, int64_t record_capacity,
@@ -334,7 +336,11 @@ ug_status ug_read_status(const ug_plan* plan, const void* ws, size_t ws_bytes, u
                          ug_stream stream);
 
 /* Device pointers into the workspace, for inspection and tests: the sorted
- * tile keys and record ids (instance order), the tile ranges (uint32 pairs
+ * tile keys and record ids (instance order; a key's low 24 bits are the
+ * (plane, tile) id, its top byte the instance's tests against the tile's 8x8
+ * footprints in row-major order: bit 2f set if the record can have a non-zero
+ * FP32 weight in footprint f, bit 2f + 1 if its box also covers the whole
+ * footprint), the tile ranges (uint32 pairs
  * [start, end) per tile), and per record slot its pixel box (uint32 pairs:
  * j0 | j1 << 16, i0 | i1 << 16; an empty box marks a rejected candidate), its
  * render data as 4 floats each: a = (X, Y, r11, kappa), b = (r22, lw2, c,

@@ -155,6 +155,7 @@ ug_status ug_plan_init(const ug_config* cfg, int64_t n, const ug_plane* host_pla
   plan->instance_capacity = instance_capacity;
   int bits = 1;
   while (((int64_t)1 << bits) < total_tiles) ++bits;
+  if (bits > kKeyTileBits) return UG_ERR_NOT_SUPPORTED;  // the key's top byte is taken
   plan->key_bits = bits;
   plan->sort_passes = (bits + 7) / 8;
   plan->chunks = (n + kChunk - 1) / kChunk;

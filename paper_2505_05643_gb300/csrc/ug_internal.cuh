@@ -57,10 +57,7 @@ struct WsHeader {
   unsigned long long box_pixels;
   uint32_t holes;             // candidates rejected by the exact test (empty slots)
   uint32_t kept64;            // visible records of the FP64 list
-  // non-zero: the forward rasterizer has written every sorted instance's 8x8
-  // footprint tests since the last bin/sort (cleared by bin/sort and by the
-  // scatter forward)
-  uint32_t fwd_masks;
+  uint32_t pad0;
   uint32_t stall_test;        // non-zero: the rasterizers' producers issue nothing (test hook;
                               // cleared by the preprocess)
   float origin_reach;         // largest |o| over the planes (set by the plane set-up)
@@ -248,6 +245,89 @@ __device__ __forceinline__ bool rect_live(const float4& a, const float4& b, int 
   const float q = rect_q_lower_bound(a, b.x, j0, i0, xa, xb, ya, yb);
   // without branches (bitwise &): lanes of a warp test different records
   return !(__fsub_rn(b.y, q) < -127.f) & !((cut != 0) & (q > __fmaf_rn(b.w, 1.0001f, 1e-6f)));
+}
+
+// Sorted instance keys: the (plane, tile) id in the low kKeyTileBits bits;
+// the top byte holds the instance's footprint tests, computed once by the
+// binning for both rasterizers: for the f-th 8 x 8 footprint of the tile (row
+// major), bit 2f says the record can have a non-zero weight there and bit
+// 2f + 1 that its box covers the whole footprint. The sort's digits come from
+// the low bits only, so the tests travel with their instance.
+constexpr int kKeyTileBits = 24;
+constexpr uint32_t kKeyTileMask = (1u << kKeyTileBits) - 1u;
+
+// Work-item test of one record (a = rec_a, b = rec_b, pixel box bx) against
+// the footprint [fj0, fj0 + 7] x [fi0, fi0 + fh - 1]: bit 0 live (the box
+// overlaps it and not every weight there is an FP32 zero), bit 1 the box
+// covers it. Branch-free: the lanes of a warp test different records.
+__device__ __forceinline__ uint32_t footprint_bits(const float4& a, const float4& b, uint2 bx,
+                                                   int fj0, int fi0, int fh, int cut) {
+  const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
+  const int fj1 = fj0 + 7, fi1 = fi0 + fh - 1;
+  const int xa = max(fj0, j0), xb = min(fj1, j1), ya = max(fi0, i0), yb = min(fi1, i1);
+  // overlap, and not every weight in it an FP32 zero (the bound of an empty
+  // overlap is finite and ignored)
+  const bool live = (xa <= xb) & (ya <= yb) & rect_live(a, b, j0, i0, xa, xb, ya, yb, cut);
+  const bool full = (j0 <= fj0) & (j1 >= fj1) & (i0 <= fi0) & (i1 >= fi1);
+  return (uint32_t)live | ((uint32_t)(live & full) << 1);
+}
+
+// footprint_bits for the four 8x8 footprints of the 16x16 tile whose first
+// pixel is (tj, ti), bits 2f and 2f + 1 for footprint f (row major): the
+// terms that depend only on a footprint row (the crossings S at its first and
+// last row, t2, the rounding bounds) or column are computed once, and each
+// footprint combines them with the operations of rect_q_lower_bound, in the
+// same order, so every test gives footprint_bits' result.
+__device__ __forceinline__ uint32_t tile_footprints16(const float4& a, const float4& b, uint2 bx,
+                                                      int tj, int ti, int cut) {
+  const float eps = 5.9604645e-8f;  // 2^-24
+  const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
+  const float ay = fabsf(a.y), ax = fabsf(a.x), aw = fabsf(a.w);
+  const float thr = __fmaf_rn(b.w, 1.0001f, 1e-6f);
+  float xlo[2], xhi[2];
+  bool xok[2], xfull[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int f0 = tj + 8 * k, xa = max(f0, j0), xb = min(f0 + 7, j1);
+    xok[k] = xa <= xb;
+    xfull[k] = (j0 <= f0) & (j1 >= f0 + 7);
+    xlo[k] = __fadd_rn((float)(xa - j0), 0.5f);
+    xhi[k] = __fadd_rn((float)(xb - j0), 0.5f);
+  }
+  uint32_t fm = 0;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int f0 = ti + 8 * r, ya = max(f0, i0), yb = min(f0 + 7, i1);
+    const bool yok = ya <= yb, yfull = (i0 <= f0) & (i1 >= f0 + 7);
+    const float ylo = __fadd_rn((float)(ya - i0), 0.5f), yhi = __fadd_rn((float)(yb - i0), 0.5f);
+    const float dylo = __fsub_rn(ylo, a.y), dyhi = __fsub_rn(yhi, a.y);
+    const float slo = __fmaf_rn(-a.w, dylo, a.x), shi = __fmaf_rn(-a.w, dyhi, a.x);
+    const float ady = fmaxf(fabsf(dylo), fabsf(dyhi));
+    const float smax = fmaxf(fabsf(slo), fabsf(shi));
+    const float es = __fadd_rn(ax, __fmul_rn(aw, __fadd_rn(2.f * ady, ay)));
+    const float e2 = __fmul_rn(4.f * eps, __fadd_rn(ady, ay));
+    const float m2 = dylo > e2 ? __fsub_rn(dylo, e2) : (dyhi < -e2 ? __fsub_rn(-dyhi, e2) : 0.f);
+    const float t2 = __fmul_rn(b.x, m2);
+    const float t2sq = __fmul_rn(t2, t2);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float u00 = __fsub_rn(xlo[k], slo), u10 = __fsub_rn(xhi[k], slo);
+      const float u01 = __fsub_rn(xlo[k], shi), u11 = __fsub_rn(xhi[k], shi);
+      const float umin = fminf(fminf(u00, u10), fminf(u01, u11));
+      const float umax = fmaxf(fmaxf(u00, u10), fmaxf(u01, u11));
+      const float e1 =
+          __fmul_rn(4.f * eps, __fadd_rn(__fadd_rn(fmaxf(fabsf(umin), fabsf(umax)), smax), es));
+      const float m1 =
+          umin > e1 ? __fsub_rn(umin, e1) : (umax < -e1 ? __fsub_rn(-umax, e1) : 0.f);
+      const float t1 = __fmul_rn(a.z, m1);
+      const float q = __fmaf_rn(t1, t1, t2sq);
+      const bool live = xok[k] & yok & !(__fsub_rn(b.y, q) < -127.f) &
+                        !((cut != 0) & (q > thr));
+      const uint32_t bits = (uint32_t)live | ((uint32_t)(live & xfull[k] & yfull) << 1);
+      fm |= bits << (2 * (2 * r + k));
+    }
+  }
+  return fm;
 }
 
 // Constants of one record over one footprint of at most 8 x 8 pixels whose

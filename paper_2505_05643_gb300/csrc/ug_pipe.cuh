@@ -119,13 +119,13 @@ struct StageHdr {
 // 8x8 footprints of a tile whose item lists a forward stage carries.
 constexpr int kMaxFootprints = 4;
 
-// One stage: up to BATCH records of one tile. Forward (not RAW): per 8x8
+// One stage: up to BATCH records of one tile, with each instance's sorted key
+// (the binning's footprint tests in its top byte). Forward (not RAW): per 8x8
 // footprint, the indices of the records live there (those whose box covers
 // the footprint from the front, the others from the back) and their counts,
-// written by the producer's finishing step. Backward (RAW): one 32-bit word
-// per record of the forward pass's footprint tests, and with the first stage
-// of a tile the tile's pixel inputs (dL/dC, alpha, C; pixels off the plane
-// hold 0, 1, 0).
+// written by the producer's finishing step. Backward (RAW): with the first
+// stage of a tile the tile's pixel inputs (dL/dC, alpha, C; pixels off the
+// plane hold 0, 1, 0).
 template <int TILE, bool RAW, int BATCH = kBatch>
 struct RecStage {
   static_assert(BATCH % 32 == 0 && BATCH <= 256, "records per stage: a multiple of 32, <= 256");
@@ -134,7 +134,7 @@ struct RecStage {
   float4 c[BATCH];
   uint2 box[BATCH];
   uint32_t rid[BATCH];
-  uint32_t mask[RAW ? BATCH : 1];
+  uint32_t mask[BATCH];  // the instances' sorted keys (footprint tests in the top byte)
   uint8_t list[RAW ? 1 : kMaxFootprints][RAW ? 1 : BATCH];  // record indices (< 256)
   uint16_t nfull[RAW ? 1 : kMaxFootprints], npart[RAW ? 1 : kMaxFootprints];
   StageHdr h;
@@ -196,8 +196,8 @@ __device__ __forceinline__ void pipe_init(PlaneTable& T, Bars& bars, const WsVie
 // released stage k - NS. The record ids are read into registers, the records themselves
 // (and the backward's pixel inputs) are copied with cp.async, whose completion
 // arrives on the stage's full barrier, so up to NS batches of gathers
-// are in flight. RID: the stage also keeps the record ids. inst_mask (RAW
-// only, may be null): per sorted instance, copied into the stage. EMPTY_TILES: tiles
+// are in flight. RID: the stage also keeps the record ids. inst_mask (may be
+// null): per sorted instance (the sorted keys), copied into the stage. EMPTY_TILES: tiles
 // without records still get one stage (the forward pass writes their
 // background pixels).
 struct TileCtx {
@@ -321,9 +321,7 @@ __device__ __forceinline__ void produce(RecStage<TILE, RAW, BATCH>* st, PipeBars
         cp_async16(&S.c[r], v.rec_c + rid[q]);
         cp_async8(&S.box[r], v.rec_box + rid[q]);
         if (RID) S.rid[r] = rid[q];
-        if constexpr (RAW) {
-          if (inst_mask) cp_async4(&S.mask[r], inst_mask + b0 + r);
-        }
+        if (inst_mask) cp_async4(&S.mask[r], inst_mask + b0 + r);
       }
     }
     if constexpr (RAW) {

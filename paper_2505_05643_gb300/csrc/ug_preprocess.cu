@@ -60,7 +60,6 @@ __global__ void __launch_bounds__(256)
     h->slots64 = 0;
     h->box_pixels = 0;
     h->holes = 0;
-    h->fwd_masks = 0;
     h->stall_test = 0;
     h->kept64 = 0;
     h->origin_reach = 0.f;
@@ -658,6 +657,20 @@ __global__ void __launch_bounds__(256) k_live(int ts, int cut, WsView v) {
   }
 }
 
+// The footprint tests of one (record, tile) instance (the key's top byte):
+// every 8 x 8 footprint of the tile (tx, ty) in row-major order.
+__device__ __forceinline__ uint32_t instance_footprints(const float4& a, const float4& b,
+                                                       uint2 bx, int tx, int ty, int ts,
+                                                       int cut) {
+  const int tile = 1 << ts, fx = tile >> 3;
+  if (tile == 16) return tile_footprints16(a, b, bx, tx * 16, ty * 16, cut);
+  uint32_t fm = 0;
+  for (int f = 0; f < fx * fx; ++f)
+    fm |= footprint_bits(a, b, bx, tx * tile + (f % fx) * 8, ty * tile + (f / fx) * 8, 8, cut)
+          << (2 * f);
+  return fm;
+}
+
 // A warp emits the instances of 32 consecutive record slots together: their
 // instances form one contiguous range (the slot scan), so lane k writes
 // instances k, k + 32, ... of the range (coalesced stores, no lane waits for
@@ -665,10 +678,14 @@ __global__ void __launch_bounds__(256) k_live(int ts, int cut, WsView v) {
 // few records with more than 64 box tiles are emitted after, one at a time, by
 // the whole warp re-testing their box tiles 32 at a time.
 __global__ void __launch_bounds__(256) k_emit(int ts, int cut, uint32_t inst_cap, WsView v) {
+  // the warp's 32 records' render data, read once (coalesced) for the
+  // footprint tests of all their instances
+  __shared__ float4 s_a[8][32], s_b[8][32];
+  __shared__ uint2 s_bx[8][32];
   if (dev_failed(v.hdr)) return;
   const uint32_t slots = v.hdr->slots;
   const uint32_t n_inst = (uint32_t)v.hdr->st.instances;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   const unsigned long long* live_mask = reinterpret_cast<const unsigned long long*>(v.rec_pgrad);
@@ -690,8 +707,12 @@ __global__ void __launch_bounds__(256) k_emit(int ts, int cut, uint32_t inst_cap
         tiles_x = (uint32_t)pl.tiles_x;
         key0 = (uint32_t)pl.tile_off + q.ty0 * tiles_x + q.tx0;
         mask = live_mask[slot];
+        s_a[wl][lane] = v.rec_a[slot];
+        s_b[wl][lane] = v.rec_b[slot];
+        s_bx[wl][lane] = q.bx;
       }
     }
+    __syncwarp();
     const int last = (int)min(31u, slots - 1u - w0);
     const uint32_t base = __shfl_sync(0xffffffffu, pre, 0);
     const uint32_t end = __shfl_sync(0xffffffffu, pre + cnt, last);
@@ -704,11 +725,16 @@ __global__ void __launch_bounds__(256) k_emit(int ts, int cut, uint32_t inst_cap
       const uint32_t l_key0 = __shfl_sync(0xffffffffu, key0, l);
       const uint32_t l_tx = __shfl_sync(0xffffffffu, tiles_x, l);
       const unsigned long long l_mask = __shfl_sync(0xffffffffu, mask, l);
+      const uint32_t l_tx0 = __shfl_sync(0xffffffffu, q.tx0, l);
+      const uint32_t l_ty0 = __shfl_sync(0xffffffffu, q.ty0, l);
       if (o < end && l_nt <= kMaskTiles && o < inst_cap) {
         const uint32_t pos = nth_set_bit(l_mask, o - l_pre);
         const uint32_t dy = pos / l_nx, dx = pos - dy * l_nx;
-        v.keys[0][o] = l_key0 + dy * l_tx + dx;
-        v.vals[0][o] = w0 + (uint32_t)l;
+        const uint32_t l_slot = w0 + (uint32_t)l;
+        const uint32_t fm = instance_footprints(s_a[wl][l], s_b[wl][l], s_bx[wl][l],
+                                                (int)(l_tx0 + dx), (int)(l_ty0 + dy), ts, cut);
+        v.keys[0][o] = (l_key0 + dy * l_tx + dx) | (fm << kKeyTileBits);
+        v.vals[0][o] = l_slot;
       }
     }
     // records with more boxes tiles than a mask holds
@@ -725,7 +751,7 @@ __global__ void __launch_bounds__(256) k_emit(int ts, int cut, uint32_t inst_cap
       const uint32_t r_tx = __shfl_sync(0xffffffffu, tiles_x, r);
       const uint2 r_bx = make_uint2(__shfl_sync(0xffffffffu, q.bx.x, r),
                                     __shfl_sync(0xffffffffu, q.bx.y, r));
-      const float4 a = v.rec_a[r_slot], b = v.rec_b[r_slot];
+      const float4 a = s_a[wl][r], b = s_b[wl][r];
       uint32_t out = __shfl_sync(0xffffffffu, pre, r);
       for (uint32_t kb = 0; kb < r_nt; kb += 32u) {
         const uint32_t k = kb + (uint32_t)lane;
@@ -735,13 +761,16 @@ __global__ void __launch_bounds__(256) k_emit(int ts, int cut, uint32_t inst_cap
           const uint32_t o = out + (uint32_t)__popc(bal & lt);
           if (o < inst_cap) {
             const uint32_t dy = k / r_nx, dx = k - dy * r_nx;
-            v.keys[0][o] = r_key0 + dy * r_tx + dx;
+            const uint32_t fm = instance_footprints(a, b, r_bx, (int)(r_tx0 + dx),
+                                                    (int)(r_ty0 + dy), ts, cut);
+            v.keys[0][o] = (r_key0 + dy * r_tx + dx) | (fm << kKeyTileBits);
             v.vals[0][o] = r_slot;
           }
         }
         out += (uint32_t)__popc(bal);
       }
     }
+    __syncwarp();  // the shared records are read; the next slots may overwrite them
   }
 }
 

@@ -6,7 +6,7 @@
 // tile's records, BATCH at a time, into a ring of shared-memory stages
 // (ug_pipe.cuh); the other warps consume the stages. The tile is cut into
 // footprints of 8 columns x FH rows. For every (record, footprint) of a stage
-// the consumers decide whether the record can touch the footprint:
+// a test decides whether the record can touch the footprint:
 //   - its pixel box must overlap the footprint, and
 //   - a lower bound on t1^2 + t2^2 over the overlap must leave the exponent
 //     above -127: below that every weight in the overlap is exactly 0 in
@@ -22,12 +22,13 @@
 // evaluated in packed FP32x2 arithmetic, two pixels per instruction; col and
 // row are the pixel's offsets in its footprint.
 //
-// Forward: the producer warp also tests every record of a stage against the
-// tile's 8x8 footprints once its copies have landed (byte f of a 32-bit word
-// per record: bit 0 live, bit 1 box covers the footprint) and stores the words
-// per sorted instance, which the backward pass with the same footprints reads
-// instead of testing again. One consumer warp per footprint, otherwise
-// independent of the other warps. The warp is split into G lane groups that each cover the whole
+// The binning computes every instance's tests against the tile's 8x8
+// footprints (the key's top byte: live, box covers the footprint); the
+// stages carry the keys, so neither pass tests 8x8 footprints again (the
+// backward's 8x4-footprint variant tests its own).
+// Forward: once a stage's copies have landed, the producer warp compacts each
+// footprint's live records into lists. One consumer warp per footprint,
+// otherwise independent of the other warps. The warp is split into G lane groups that each cover the whole
 // footprint (2G pixels of one column per lane) and take every G-th work item;
 // per pixel S_a += w, S_c += w c, the groups' sums are added at the end of the
 // tile, then C = (S_c + a_bg c_bg) / (S_a + a_bg) (Eq. alpha-combine, Eq.
@@ -57,19 +58,13 @@ __device__ __forceinline__ void footprint_origin(int f, int fx_count, int fh, in
 }
 
 // Work-item test of one record against the footprint [fj0, fj0 + 7] x [fi0,
-// fi0 + fh - 1]: bit 0 live, bit 1 the box covers the footprint.
-// Branch-free: the lanes of a warp test different records.
+// fi0 + fh - 1] (see footprint_bits): bit 0 live, bit 1 the box covers the
+// footprint. The 8x8 footprints' tests come with the sorted keys; this is for
+// the backward's 8x4 footprints.
 template <int CUT>
 __device__ __forceinline__ uint32_t classify(const float4& a, const float4& b, uint2 bx, int fj0,
                                              int fi0, int fh) {
-  const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
-  const int fj1 = fj0 + 7, fi1 = fi0 + fh - 1;
-  const int xa = max(fj0, j0), xb = min(fj1, j1), ya = max(fi0, i0), yb = min(fi1, i1);
-  // overlap, and not every weight in it an FP32 zero (the bound of an empty
-  // overlap is finite and ignored)
-  const bool live = (xa <= xb) & (ya <= yb) & rect_live(a, b, j0, i0, xa, xb, ya, yb, CUT);
-  const bool full = (j0 <= fj0) & (j1 >= fj1) & (i0 <= fi0) & (i1 >= fi1);
-  return (uint32_t)live | ((uint32_t)(live & full) << 1);
+  return footprint_bits(a, b, bx, fj0, fi0, fh, CUT);
 }
 
 // box ∩ footprint in footprint coordinates, packed cx0 | cx1 << 8 | ry0 << 16 |
@@ -201,37 +196,23 @@ __device__ __forceinline__ void fwd_build(FwdChunk& W, int lane, bool real, cons
   if (CUT) W.thr[lane] = b.w;
 }
 
-// The producer's finishing step of a forward stage: every record against
-// every 8x8 footprint of the tile (one lane per record, the record read once),
-// byte f of the record's word the test of footprint f, written per sorted
-// instance for the backward pass; then, per footprint, the compacted lists of
-// its live records (box covering the footprint from the front, the others
-// from the back) and their counts, written to the stage for the consumers.
-template <int TILE, int CUT, int BATCH>
+// The producer's finishing step of a forward stage: per 8x8 footprint of the
+// tile, the compacted lists of its live records (box covering the footprint
+// from the front, the others from the back) and their counts, from the
+// binning's footprint tests (the top byte of each instance's key), written to
+// the stage for the consumers.
+template <int TILE, int BATCH>
 struct FwdPrep {
   static constexpr bool kDefer = true;
-  uint32_t* inst_mask;
   __device__ void operator()(RecStage<TILE, false, BATCH>& S, int lane) const {
     using T = Tiling<TILE, 8>;
     static_assert(T::NF <= kMaxFootprints, "a stage carries the lists of four footprints");
-    const StageHdr h = S.h;
+    const int cnt = S.h.cnt;
     uint32_t mq[BATCH / 32];
 #pragma unroll
     for (int q = 0; q < BATCH / 32; ++q) {
       const int r = lane + 32 * q;
-      uint32_t m = 0;
-      if (r < h.cnt) {
-        const float4 a = S.a[r], b = S.b[r];
-        const uint2 bx = S.box[r];
-#pragma unroll
-        for (int f = 0; f < T::NF; ++f) {
-          int fj0, fi0;
-          footprint_origin(f, T::FX, 8, h.tx, h.ty, TILE, fj0, fi0);
-          m |= classify<CUT>(a, b, bx, fj0, fi0, 8) << (8 * f);
-        }
-        inst_mask[h.inst0 + r] = m;
-      }
-      mq[q] = m;
+      mq[q] = r < cnt ? S.mask[r] >> kKeyTileBits : 0u;
     }
     const uint32_t lt = lanemask_lt();
 #pragma unroll
@@ -239,7 +220,7 @@ struct FwdPrep {
       int nf = 0, np = 0;
 #pragma unroll
       for (int q = 0; q < BATCH / 32; ++q) {
-        const uint32_t mf = mq[q] >> (8 * f);
+        const uint32_t mf = mq[q] >> (2 * f);
         const bool live = mf & 1u, full = mf & 2u;
         const uint32_t bf = __ballot_sync(0xffffffffu, live && full);
         const uint32_t bp = __ballot_sync(0xffffffffu, live && !full);
@@ -261,7 +242,7 @@ template <int TILE, int G, int CUT, int NS = kStages, int BATCH = kBatch, int MI
 __global__ void __launch_bounds__(FwdShape<TILE, G, MINB>::NT, FwdShape<TILE, G, MINB>::kMinBlocks)
     k_render_fwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles, float abg,
                  float cbg, float* __restrict__ image, float* __restrict__ alpha,
-                 uint32_t* __restrict__ inst_mask) {
+                 const uint32_t* __restrict__ sorted_keys) {
   using Sh = FwdShape<TILE, G, MINB>;
   constexpr int NW = Sh::NW, LG = Sh::LG, NP = Sh::NP;
   extern __shared__ __align__(16) unsigned char fwd_smem[];
@@ -270,9 +251,9 @@ __global__ void __launch_bounds__(FwdShape<TILE, G, MINB>::NT, FwdShape<TILE, G,
   pipe_init(S.T, S.bars, v, P, Sh::NCT, 32);
   if (__syncthreads_or(dev_failed(v.hdr))) return;  // the whole CTA leaves, or none of it
   if (warp == NW) {
-    produce<TILE, false, false, true, FwdPrep<TILE, CUT, BATCH>, NS, BATCH>(
-        S.st, S.bars, S.T, v, vals, 0, P, total_tiles, nullptr, nullptr, nullptr, nullptr,
-        FwdPrep<TILE, CUT, BATCH>{inst_mask});
+    produce<TILE, false, false, true, FwdPrep<TILE, BATCH>, NS, BATCH>(
+        S.st, S.bars, S.T, v, vals, 0, P, total_tiles, nullptr, nullptr, nullptr, sorted_keys,
+        FwdPrep<TILE, BATCH>{});
     return;
   }
   const int grp = lane / LG, gl = lane % LG;
@@ -520,7 +501,7 @@ template <int TILE, int FH, int CUT, int NS = kBwdStages, int BATCH = kBatch, in
 __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
     k_render_bwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles,
                  const float* __restrict__ image, const float* __restrict__ alpha,
-                 const float* __restrict__ grad_image, const uint32_t* __restrict__ inst_mask) {
+                 const float* __restrict__ grad_image, const uint32_t* __restrict__ sorted_keys) {
   using Sh = BwdShape<TILE, FH>;
   using T = Tiling<TILE, FH>;
   constexpr int NW = Sh::NW;
@@ -532,12 +513,12 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   pipe_init(S.Tb, S.bars, v, P, Sh::NCT);
   if (__syncthreads_or(dev_failed(v.hdr))) return;  // the whole CTA leaves, or none of it
-  // the forward pass's tests apply when its footprints are these (8 rows)
-  const bool use_masks = FH == 8 && *(volatile const uint32_t*)&v.hdr->fwd_masks != 0;
+  // the binning's footprint tests apply when the footprints are 8x8
+  constexpr bool use_masks = FH == 8;
   if (warp == NW) {
     produce<TILE, true, true, false, NoPrep, NS, BATCH>(S.st, S.bars, S.Tb, v, vals, 1, P,
                                                         total_tiles, grad_image, alpha, image,
-                                                        use_masks ? inst_mask : nullptr);
+                                                        use_masks ? sorted_keys : nullptr);
     return;
   }
   const uint32_t lt = lanemask_lt();
@@ -627,7 +608,7 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
       const int r = 32 * q + lane;
       m[q] = 0;
       if (r < h.cnt)
-        m[q] = use_masks ? R.mask[r] >> (8 * warp)
+        m[q] = use_masks ? R.mask[r] >> (kKeyTileBits + 2 * warp)
                          : classify<CUT>(R.a[r], R.b[r], R.box[r], fj0, fi0, FH);
     }
     const uint32_t q0 = qtail;
@@ -664,11 +645,9 @@ __global__ void k_zero_rec_grad(WsView v, int64_t cap) {
 }
 
 // ------------------------------------------------------------------ variants
-// The forward pass's per-instance footprint tests live in the key buffer that
-// the radix sort left unused (it held the last pass's input), one 32-bit word
-// per sorted instance; the next bin/sort overwrites it and clears the flag.
-static uint32_t* inst_masks(const ug_plan* plan, const WsView& v) {
-  return v.keys[(plan->sort_passes & 1) ^ 1];
+// The sorted keys, whose top byte holds each instance's footprint tests.
+static const uint32_t* sorted_keys(const ug_plan* plan, const WsView& v) {
+  return v.keys[plan->sort_passes & 1];
 }
 
 template <typename K>
@@ -690,7 +669,7 @@ static cudaError_t fwd_launch(const ug_plan* plan, WsView v, const uint32_t* val
   static const int grid = occupancy_grid(kern, NT, SM);
   const int g = min(grid, max(plan->total_tiles, 1));
   kern<<<g, NT, SM, s>>>(v, vals, plan->num_planes, plan->total_tiles, plan->cfg.alpha_bg,
-                         plan->cfg.c_bg, image, alpha, inst_masks(plan, v));
+                         plan->cfg.c_bg, image, alpha, sorted_keys(plan, v));
   return cudaGetLastError();
 }
 
@@ -707,7 +686,7 @@ static cudaError_t bwd_launch(const ug_plan* plan, WsView v, const uint32_t* val
   static const int grid = occupancy_grid(kern, NT, SM);
   const int g = min(grid, max(plan->total_tiles, 1));
   kern<<<g, NT, SM, s>>>(v, vals, plan->num_planes, plan->total_tiles, image, alpha, grad,
-                         inst_masks(plan, v));
+                         sorted_keys(plan, v));
   return cudaGetLastError();
 }
 
@@ -781,8 +760,7 @@ cudaError_t launch_render(const ug_plan* plan, WsView v, float* image, float* al
   else
     e = plan->cfg.cutoff ? dispatch_fwd<8, 1>(plan, v, vals, image, alpha, s)
                          : dispatch_fwd<8, 0>(plan, v, vals, image, alpha, s);
-  if (e != cudaSuccess) return e;
-  return cudaMemsetAsync(&v.hdr->fwd_masks, 0xff, sizeof(uint32_t), s);
+  return e;
 }
 
 cudaError_t launch_render_backward_raster(const ug_plan* plan, WsView v, const float* image,

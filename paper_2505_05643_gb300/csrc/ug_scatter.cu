@@ -61,7 +61,6 @@ cudaError_t launch_render_scatter(const ug_plan* plan, WsView v, float* image, f
   cudaError_t e = cudaMemsetAsync(image, 0, bytes, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(alpha, 0, bytes, s);
   // this forward leaves no footprint tests for the backward rasterizer
-  if (e == cudaSuccess) e = cudaMemsetAsync(&v.hdr->fwd_masks, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   const int sms = device_sms();
   k_scatter<<<sms * 8, 256, 0, s>>>(v, plan->cfg.cutoff, alpha, image);

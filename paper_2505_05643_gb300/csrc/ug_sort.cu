@@ -117,9 +117,9 @@ __global__ void k_tile_ranges(const uint32_t* __restrict__ keys, WsView v) {
   const int64_t n = v.hdr->st.instances;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = keys[i];
-    if (i == 0 || keys[i - 1] != k) v.ranges[k].x = (uint32_t)i;
-    if (i == n - 1 || keys[i + 1] != k) v.ranges[k].y = (uint32_t)(i + 1);
+    const uint32_t k = keys[i] & kKeyTileMask;
+    if (i == 0 || (keys[i - 1] & kKeyTileMask) != k) v.ranges[k].x = (uint32_t)i;
+    if (i == n - 1 || (keys[i + 1] & kKeyTileMask) != k) v.ranges[k].y = (uint32_t)(i + 1);
   }
 }
 
@@ -149,8 +149,6 @@ cudaError_t launch_bin_sort(const ug_plan* plan, WsView v, cudaStream_t s) {
                                                            v.vals[dst], shift, nblk, v);
   }
   cudaError_t e = cudaMemsetAsync(v.ranges, 0, sizeof(uint2) * (size_t)plan->total_tiles, s);
-  // the forward rasterizer's footprint tests belong to the previous order
-  if (e == cudaSuccess) e = cudaMemsetAsync(&v.hdr->fwd_masks, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

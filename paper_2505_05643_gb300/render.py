@@ -189,8 +189,9 @@ class Renderer:
         return grads
 
     def debug_views(self):
-        """Host copies of the sorted keys, record ids, tile ranges, and the
-        records' boxes, render data and planes of the last ug_bin_sort."""
+        """Host copies of the sorted keys (tile ids, with each instance's
+        footprint-test byte apart), record ids, tile ranges, and the records'
+        boxes, render data and planes of the last ug_bin_sort."""
         st = self.status()
         n_inst, n_rec = st["instances"], st["records"]
         kp, vp, rp, bp, ap, bbp, cp, pp = B.ug_debug_views(self.plan, self.ws)
@@ -203,7 +204,9 @@ class Renderer:
             t = self.ws[off:off + 4 * count * width].view(torch.int32).cpu().numpy().view(np.uint32)
             return t.reshape(-1, width) if width > 1 else t
 
-        return dict(keys=grab(kp, n_inst), records=grab(vp, n_inst),
+        raw = grab(kp, n_inst)
+        return dict(keys=raw & np.uint32(0x00FFFFFF), footprints=raw >> np.uint32(24),
+                    records=grab(vp, n_inst),
                     ranges=grab(rp, int(self.plan.total_tiles), 2),
                     boxes=grab(bp, n_rec, 2), rec_a=grab(ap, n_rec, 4).view(np.float32),
                     rec_b=grab(bbp, n_rec, 4).view(np.float32),

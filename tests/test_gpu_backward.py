@@ -146,13 +146,13 @@ def test_grad_variants(tile, variant):
 
 
 @pytest.mark.parametrize("tile", [16, 8])
-def test_grad_with_and_without_forward_footprint_tests(tile):
-    """The backward rasterizer reads the forward rasterizer's per-instance
-    footprint tests when they belong to the current sort, and tests the
-    footprints itself otherwise (here: after the scatter forward, which leaves
-    none): both evaluate the same pairs and give the same gradient up to the
-    order of the atomic additions, on an extreme-anisotropy scene with many
-    culled footprints."""
+def test_grad_binning_footprint_tests_against_own_tests(tile):
+    """The 8x8-footprint backward takes its footprint tests from the binning
+    (the sorted keys' top byte); the 8x4-footprint variant tests its own. On
+    an extreme-anisotropy scene with many culled footprints both give the same
+    gradient up to the order of the atomic additions, with or without a
+    forward pass between bin/sort and the backward, and the same gradient
+    after the scatter forward (which leaves the keys as they are)."""
     rng = np.random.default_rng(37)
     g, pl = synth.workload_aniso_1m()
     g = {k: v[..., :20000] for k, v in g.items()}
@@ -164,7 +164,8 @@ def test_grad_with_and_without_forward_footprint_tests(tile):
     im_t = torch.from_numpy(image.astype(np.float32)).cuda()
     al_t = torch.from_numpy(alpha.astype(np.float32)).cuda()
 
-    def gradient():
+    def gradient(variant_bwd):
+        r.plan.cfg.variant_bwd = variant_bwd
         grads = torch.empty_like(params)
         B.ug_render_backward_raster(r.plan, r.ws, im_t, al_t, gi)
         B.ug_preprocess_backward(r.plan, R.gaussians_struct(params, r.cov), r.ws,
@@ -174,14 +175,21 @@ def test_grad_with_and_without_forward_footprint_tests(tile):
         assert st["status"] == B.UG_OK
         return grads.cpu().numpy().astype(np.float64), st["evaluated_pairs_bwd"]
 
-    with_tests, ev1 = gradient()
+    binned, ev1 = gradient(0)
+    own, ev2 = gradient(1)
+    assert ev1 > 0 and ev2 > 0
+    # bin/sort again and run the backward with no forward in between
+    B.ug_preprocess(r.plan, R.gaussians_struct(params, r.cov), r.d_planes, r.ws)
+    B.ug_bin_sort(r.plan, r.ws)
+    no_fwd, ev3 = gradient(0)
     im2, al2 = torch.empty_like(im_t), torch.empty_like(al_t)
     B.ug_render_scatter(r.plan, r.ws, im2, al2)
-    without, ev2 = gradient()
-    assert ev1 == ev2 > 0
-    scale = np.abs(with_tests).max(axis=1, keepdims=True) + 1e-30  # per parameter row
-    err = np.abs(with_tests - without)
-    assert np.all(err <= 1e-5 * scale + 1e-4 * np.abs(without)), (err / scale).max(axis=1)
+    after_scatter, ev4 = gradient(0)
+    assert ev1 == ev3 == ev4
+    scale = np.abs(binned).max(axis=1, keepdims=True) + 1e-30  # per parameter row
+    for other in (own, no_fwd, after_scatter):
+        err = np.abs(binned - other)
+        assert np.all(err <= 1e-5 * scale + 1e-4 * np.abs(other)), (err / scale).max(axis=1)
 
 
 def test_grad_many_planes_and_dense_tiles():

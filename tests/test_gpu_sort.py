@@ -65,12 +65,50 @@ def _max_exponent(a, b, c, box, j0, j1, i0, i1):
     return float((b[1] - t1 * t1 - t2 * t2).max())
 
 
+def _check_footprints(dv, pl, tile, off, tx):
+    """Each instance's footprint-test byte against a CPU replay from the GPU's
+    own record: for every 8x8 footprint of the tile, the 'covers' bit is set
+    exactly when the footprint is live and the box covers it, and a footprint
+    marked not live holds only exact FP32 zeros of the record (or lies outside
+    its box). Returns the numbers of live and culled (instance, footprint)
+    pairs inside boxes."""
+    keys, recs, fps, boxes = dv["keys"], dv["records"], dv["footprints"], dv["boxes"]
+    rec_a, rec_b, rec_c = dv["rec_a"], dv["rec_b"], dv["rec_c"]
+    rec_plane = dv["rec_plane"].astype(np.int64)
+    fx = tile // 8
+    n_live = n_cut = 0
+    assert np.all(fps >> (2 * fx * fx) == 0)  # no bits beyond the tile's footprints
+    for key, rid, fp in zip(keys.tolist(), recs.tolist(), fps.tolist()):
+        p = int(rec_plane[rid])
+        local = key - int(off[p])
+        ty, txx = divmod(local, int(tx[p]))
+        j0, j1 = int(boxes[rid, 0] & 0xFFFF), int(boxes[rid, 0] >> 16)
+        i0, i1 = int(boxes[rid, 1] & 0xFFFF), int(boxes[rid, 1] >> 16)
+        for f in range(fx * fx):
+            fj0, fi0 = txx * tile + (f % fx) * 8, ty * tile + (f // fx) * 8
+            live, full = (fp >> (2 * f)) & 1, (fp >> (2 * f + 1)) & 1
+            xa, xb, ya, yb = max(fj0, j0), min(fj0 + 7, j1), max(fi0, i0), min(fi0 + 7, i1)
+            covers = j0 <= fj0 and j1 >= fj0 + 7 and i0 <= fi0 and i1 >= fi0 + 7
+            assert full == (live and covers), (rid, key, f, fp)
+            if xa > xb or ya > yb:
+                assert not live, (rid, key, f, fp)
+                continue
+            if live:
+                n_live += 1
+            else:
+                n_cut += 1
+                e = _max_exponent(rec_a[rid], rec_b[rid], rec_c[rid], boxes[rid], xa, xb, ya, yb)
+                assert e < -126.5, (rid, key, f, e)
+    return n_live, n_cut
+
+
 def _check_tile_lists(r, pl, tile):
     """The GPU's sorted instances against a CPU replay from the GPU's own
     records: for every tile, its records are those whose box meets the tile,
     in ascending record id, minus only pairs whose weights are all exact FP32
     zeros (binning drops those: the record's exact weight exponent is below
-    -126.5 at every pixel of the pair); the ranges delimit the tiles. Returns the
+    -126.5 at every pixel of the pair); the ranges delimit the tiles; every
+    instance's footprint tests hold (see _check_footprints). Returns the
     numbers of kept and dropped (record, tile) pairs."""
     dv = r.debug_views()
     keys, recs, ranges, boxes = dv["keys"], dv["records"], dv["ranges"], dv["boxes"]
@@ -112,6 +150,9 @@ def _check_tile_lists(r, pl, tile):
         if hi > lo:
             exp_ranges[t] = (lo, hi)
     assert np.array_equal(ranges, exp_ranges)
+    n_live, n_cut = _check_footprints(dv, pl, tile, off, tx)
+    assert n_live > 0
+    dv["footprints_live_culled"] = (n_live, n_cut)
     return dv, live, kept, dropped
 
 
@@ -150,8 +191,10 @@ def test_tile_lists_thin_gaussians_drop_zero_tiles():
     pl = synth.planes_random(rng, [(128, 128), (96, 160)])
     cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, tile=16)
     r, _, image, alpha = gpu_render(g, pl, cfg)
-    _, _, kept, dropped = _check_tile_lists(r, pl, 16)
+    dv, _, kept, dropped = _check_tile_lists(r, pl, 16)
     assert kept > 100 and dropped > 0.1 * kept, (kept, dropped)
+    n_live, n_cut = dv["footprints_live_culled"]
+    assert n_cut > 0.05 * n_live, (n_live, n_cut)  # footprints of kept tiles culled too
 
 
 def test_sort_multi_pass_keys():
