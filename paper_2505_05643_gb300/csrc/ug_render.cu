@@ -30,9 +30,10 @@
 // footprint's live records into lists. One consumer warp per footprint,
 // otherwise independent of the other warps. The warp is split into G lane groups that each cover the whole
 // footprint (2G pixels of one column per lane) and take every G-th work item;
-// per pixel S_a += w, S_c += w c, the groups' sums are added at the end of the
-// tile, then C = (S_c + a_bg c_bg) / (S_a + a_bg) (Eq. alpha-combine, Eq.
-// colour-combine). No atomics, fixed summation order.
+// per pixel S_a += w, S_c += w c; at the end of the tile the groups' sums are
+// reduce-scattered (every lane ends with two pixels' full sums), then C = (S_c
+// + a_bg c_bg) / (S_a + a_bg) (Eq. alpha-combine, Eq. colour-combine). No
+// atomics, fixed summation order.
 //
 // Backward: one lane per work item. The lane walks the 8 x FH pixels of its
 // footprint and sums the seven per-record quantities of dL/dw over them in
@@ -315,27 +316,35 @@ __global__ void __launch_bounds__(FwdShape<TILE, G, MINB>::NT, FwdShape<TILE, G,
     }
     mbar_arrive(&S.bars.empty[s]);  // the stage is no longer read by this thread
     if (h.flags & kLast) {
-      // add the groups' sums (fixed order), group 0 writes
+      // Reduce-scatter the groups' sums (fixed order): at each level a lane
+      // keeps half of its column pairs and adds the partner group's sums of
+      // that half, so in the end every lane holds the full sums of one column
+      // pair (two pixels) and forms those two pixels.
+      int cpk = 0;  // the kept column pair, relative to this lane's first
 #pragma unroll
-      for (int o = LG; o < 32; o <<= 1)
+      for (int l = 0; (LG << l) < 32; ++l) {
+        const int o = LG << l, hh = NP >> (l + 1);
+        const bool up = (lane & o) != 0;
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          sa[p].x += __shfl_xor_sync(0xffffffffu, sa[p].x, o);
-          sa[p].y += __shfl_xor_sync(0xffffffffu, sa[p].y, o);
-          sc[p].x += __shfl_xor_sync(0xffffffffu, sc[p].x, o);
-          sc[p].y += __shfl_xor_sync(0xffffffffu, sc[p].y, o);
+        for (int p = 0; p < hh; ++p) {
+          const float2 ka = up ? sa[p + hh] : sa[p], kc = up ? sc[p + hh] : sc[p];
+          const float2 ga = up ? sa[p] : sa[p + hh], gc = up ? sc[p] : sc[p + hh];
+          sa[p] = make_float2(ka.x + __shfl_xor_sync(0xffffffffu, ga.x, o),
+                              ka.y + __shfl_xor_sync(0xffffffffu, ga.y, o));
+          sc[p] = make_float2(kc.x + __shfl_xor_sync(0xffffffffu, gc.x, o),
+                              kc.y + __shfl_xor_sync(0xffffffffu, gc.y, o));
         }
+        if (up) cpk += hh;
+      }
       const int i = fi0 + y;
-      if (grp == 0 && i < th) {
+      if (i < th) {
 #pragma unroll
-        for (int q = 0; q < 2 * NP; ++q) {
-          const int j = fj0 + 2 * cp0 + q;
+        for (int q = 0; q < 2; ++q) {
+          const int j = fj0 + 2 * (cp0 + cpk) + q;
           if (j < tw) {
             const int64_t px = tpx + (int64_t)i * tw + j;
-            const float saq = (q & 1) ? sa[q >> 1].y : sa[q >> 1].x;
-            const float scq = (q & 1) ? sc[q >> 1].y : sc[q >> 1].x;
-            const float al = saq + abg;
-            image[px] = (scq + abg * cbg) / al;
+            const float al = (q ? sa[0].y : sa[0].x) + abg;
+            image[px] = ((q ? sc[0].y : sc[0].x) + abg * cbg) / al;
             alpha[px] = al;
           }
         }
