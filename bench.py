@@ -52,11 +52,11 @@ sys.path.insert(0, ROOT)
 # only below 4 FP32 operations per pixel.
 FWD_OPS = 6
 BWD_OPS = 9
-# DRAM bytes (read + write) of one k_render_bwd launch on this workload, from a
-# one-pass ncu capture of the kernel as it stands; None when the kernel has
-# changed since.
-BWD_TRAFFIC = 549937408  # 470,391,552 read + 79,545,856 written
-FWD_TRAFFIC = 252912384  # 190,099,968 read + 62,812,416 written (k_render_fwd, same capture)
+# DRAM bytes (read + write) of one launch of each rasterizer on this workload,
+# from a one-pass ncu capture of the kernel as it stands; None when the kernel has
+# changed since the counters were taken.
+BWD_TRAFFIC = 681061632  # 594,883,328 read + 86,178,304 written (k_render_bwd, variant 0)
+FWD_TRAFFIC = 330480896  # 286,015,744 read + 44,465,152 written (k_render_fwd, variant 0)
 
 METRIC = "Gaussian·pixel evals/s and fwd+bwd train steps/s, 1M Gaussians, 1×GB300"
 WORKLOAD = "aniso_1m: 1,000,000 Gaussians, axis ratios log-uniform to 1e4, 64 planes/launch " \

@@ -203,6 +203,15 @@ __device__ __forceinline__ float fast_exp2(float x) {
   return y;
 }
 
+// 2^-x on the special-function unit (the negation is exact; +inf gives +0).
+__device__ __forceinline__ float fast_exp2_neg(float x) {
+  float y;
+  asm("{\n\t.reg .f32 t;\n\tneg.f32 t, %1;\n\tex2.approx.ftz.f32 %0, t;\n\t}"
+      : "=f"(y)
+      : "f"(x));
+  return y;
+}
+
 // Lower bound of q = t1^2 + t2^2 over the pixel centres of the rectangle
 // [xa, xb] x [ya, yb] (pixel indices) for a record (a = rec_a, r22) whose box
 // starts at (j0, i0). Along a row y, t1 / r11 = x - S(y) with the crossing
@@ -330,25 +339,27 @@ __device__ __forceinline__ uint32_t tile_footprints16(const float4& a, const flo
   return fm;
 }
 
-// Constants of one record over one footprint of at most 8 x 8 pixels whose
-// first pixel is (fi0, fj0). With col, row the pixel's offsets in the
-// footprint:
+// Constants of one record over a region of at most SPAN x SPAN pixels (a
+// footprint or a whole tile) whose first pixel is (fi0, fj0). With col, row
+// the pixel's offsets in the region:
 //   t1 = r11 (col + nsh(row)) + nrs(row),  t2 = r22 dy(row),
 //   nsh(row) = kq row - s0q,  nrs(row) = a1 row + a0,  dy(row) = (row + nyh) + nyl.
-// S0 = s0q + s0l is the crossing at row 0 in double words (the footprint's
+// S0 = s0q + s0l is the crossing at row 0 in double words (the region's
 // anchor is subtracted first, so S0 stays small), and kappa = kq + kl. s0q and
 // kq are rounded to the grid G = 2^(E - 21), E = floor(log2 B), B >= |S0| +
-// 8 |kappa| + 8: every nsh(row) and col + nsh(row) is then a multiple of G
-// below 2^22 G, so both are exact in FP32, and the low parts (s0l, kl, at most
-// G / 2 plus the double word's own) enter through nrs in FP32. t1 thus carries
-// a few ulps of relative error whatever r11 dx and r11 kappa dy are (see the
-// record comment above).
+// SPAN |kappa| + SPAN: every nsh(row) and col + nsh(row) is then a multiple of
+// G below 2^22 G, so both are exact in FP32, and the low parts (s0l, kl, at
+// most G / 2 plus the double word's own) enter through nrs in FP32. t1 thus
+// carries a few ulps of relative error whatever r11 dx and r11 kappa dy are
+// (see the record comment above).
 struct ItemGeo {
   float r11, kq, ns0q, a1, a0, nyh, nyl, r22;
 };
 
+template <int SPAN = 8>
 __device__ __forceinline__ ItemGeo item_geo(const float4& a, const float4& b, const float4& c,
                                             uint2 bx, int fj0, int fi0) {
+  static_assert(SPAN == 8 || SPAN == 16, "region edge");
   const int j0 = bx.x & 0xffff, i0 = bx.y & 0xffff;
   const float ox = __fadd_rn((float)(fj0 - j0), 0.5f), oy = __fadd_rn((float)(fi0 - i0), 0.5f);
   // Xf = X - ox, Yf = Y - oy in double words (Knuth's 2Sum)
@@ -370,7 +381,8 @@ __device__ __forceinline__ ItemGeo item_geo(const float4& a, const float4& b, co
   two_sum(xh, ph, sh, se);
   const float sl = __fadd_rn(__fadd_rn(xl, pl), se);
   // the grid: M = 1.5 * 2^23 * G rounds a value below 2^22 G to a multiple of G
-  const float B = __fadd_rn(__fadd_rn(fabsf(sh), __fmul_rn(8.f, fabsf(a.w))), 8.f);
+  const float B =
+      __fadd_rn(__fadd_rn(fabsf(sh), __fmul_rn((float)SPAN, fabsf(a.w))), (float)SPAN);
   const uint32_t eb = min(__float_as_uint(B) >> 23, 250u);
   const float M = __uint_as_float(((eb + 2u) << 23) | (1u << 22));
   const float s0q = __fsub_rn(__fadd_rn(sh, M), M);

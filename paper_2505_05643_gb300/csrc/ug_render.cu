@@ -81,15 +81,15 @@ __device__ __forceinline__ uint32_t clip_box(uint2 bx, int fj0, int fi0, int fh)
 // A warp's current chunk of up to 32 work items (structure of arrays, one
 // slot per lane of the builder; the item_geo constants in pairs for the
 // FP32x2 arithmetic). Slots past the last item, up to a multiple of the lane
-// groups, hold inert items (lw2 = -inf), so that every group runs the same
+// groups, hold inert items (-lw2 = +inf), so that every group runs the same
 // number of items.
 struct FwdChunk {
   float4 p0[32];     // r11, r11, kq, kq
   float4 p1[32];     // -s0q, -s0q, a1, a1
   float4 p2[32];     // a0, a0, nyh, nyh
   float4 p3[32];     // nyl, nyl, r22, r22
-  float4 p4[32];     // lw2, lw2, c, c
-  float4 lc[2][32];  // partial items: lw2 in the box's columns, -inf outside
+  float4 p4[32];     // -lw2, -lw2, c, c
+  float4 lc[2][32];  // partial items: -lw2 in the box's columns, +inf outside
   uint32_t rows[32]; // partial items: bit y set for the box's rows
   float thr[32];     // ellipsoid threshold (cut-off by ellipsoid)
 };
@@ -117,15 +117,16 @@ struct FwdSmem {
   PlaneTable T;
 };
 
-// The exponent e = lw2 - t1^2 - t2^2 is formed with negated products so that
-// the special-function unit takes it as is: w = 2^e. Pixels outside the box
-// (PARTIAL) or the ellipsoid (CUT) get e = -inf, whose ex2 is +0.
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// The weight is w = 2^-n with n = t1^2 + (t2^2 - lw2) >= 0 formed by plain
+// (un-negated) fused multiply-adds; the special-function unit takes the
+// negation. Pixels outside the box (PARTIAL) or the ellipsoid (CUT), and inert
+// items, get n = +inf, whose weight is +0.
 __device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
 __device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); }
 
-// One lane, one work item: footprint row k2 = (row, row), column pairs cp0 ..
-// cp0 + NP - 1 (col2[p] = their two column offsets).
+// One lane, one work item: the lane's footprint row y, k2 = (its row in the
+// tile) twice, column pairs cp0 .. cp0 + NP - 1 of the footprint (col2[p] =
+// their two columns in the tile).
 template <int CUT, bool PARTIAL, int NP>
 __device__ __forceinline__ void fwd_item(const FwdChunk& C, int e, float2 k2, int y, int cp0,
                                          const float2* col2, float2* sa, float2* sc) {
@@ -135,21 +136,21 @@ __device__ __forceinline__ void fwd_item(const FwdChunk& C, int e, float2 k2, in
   const float2 nrs = __ffma2_rn(hi2(p1), k2, lo2(p2));  // a1 row + a0
   const float2 dy = __fadd2_rn(__fadd2_rn(k2, hi2(p2)), lo2(p3));
   const float2 t2 = __fmul2_rn(hi2(p3), dy);
-  float2 c2[NP];  // lw2 - t2^2 per column pair
+  float2 c2[NP];  // t2^2 - lw2 per column pair
   if (PARTIAL) {
     float4 lw4[2];
     lw4[0] = C.lc[0][e];
     lw4[1] = C.lc[1][e];
-    float2 nt2sq = __fmul2_rn(neg2(t2), t2);
-    if (!((C.rows[e] >> y) & 1u)) nt2sq = make_float2(-INFINITY, -INFINITY);
+    float2 t2sq = __fmul2_rn(t2, t2);
+    if (!((C.rows[e] >> y) & 1u)) t2sq = make_float2(INFINITY, INFINITY);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       const int q = cp0 + p;
       const float4 l = lw4[q >> 1];
-      c2[p] = __fadd2_rn((q & 1) ? hi2(l) : lo2(l), nt2sq);
+      c2[p] = __fadd2_rn((q & 1) ? hi2(l) : lo2(l), t2sq);
     }
   } else {
-    const float2 c = __ffma2_rn(neg2(t2), t2, lo2(p4));
+    const float2 c = __ffma2_rn(t2, t2, lo2(p4));
 #pragma unroll
     for (int p = 0; p < NP; ++p) c2[p] = c;
   }
@@ -159,37 +160,38 @@ __device__ __forceinline__ void fwd_item(const FwdChunk& C, int e, float2 k2, in
   for (int p = 0; p < NP; ++p) {
     const float2 d = __fadd2_rn(col2[p], nsh);  // col - S(row), exact
     const float2 t1 = __ffma2_rn(r11, d, nrs);
-    float2 e2 = __ffma2_rn(neg2(t1), t1, c2[p]);  // lw2 - q
+    float2 n2 = __ffma2_rn(t1, t1, c2[p]);  // q - lw2
     if (CUT) {
       const float2 q = __ffma2_rn(t1, t1, __fmul2_rn(t2, t2));
-      if (!(q.x <= thr)) e2.x = -INFINITY;
-      if (!(q.y <= thr)) e2.y = -INFINITY;
+      if (!(q.x <= thr)) n2.x = INFINITY;
+      if (!(q.y <= thr)) n2.y = INFINITY;
     }
-    const float2 w = make_float2(fast_exp2(e2.x), fast_exp2(e2.y));
+    const float2 w = make_float2(fast_exp2_neg(n2.x), fast_exp2_neg(n2.y));
     sa[p] = __fadd2_rn(sa[p], w);
     sc[p] = __ffma2_rn(w, cc, sc[p]);
   }
 }
 
-// Chunk slot `lane` from the record (a, b, c, bx); real = false makes the slot
-// inert (lw2 = -inf: every weight is +0).
+// Chunk slot `lane` from the record's tile-anchored constants (g0 = r11, kq,
+// -s0q, a1; g1 = a0, -yh, -yl, r22; see stage_tile_geo), b and box bx, with
+// -lw2 where the weight's exponent needs it; real = false makes the slot inert
+// (-lw2 = +inf: every weight is +0).
 template <int CUT, bool PARTIAL>
-__device__ __forceinline__ void fwd_build(FwdChunk& W, int lane, bool real, const float4& a,
-                                          const float4& b, const float4& c, uint2 bx, int fj0,
+__device__ __forceinline__ void fwd_build(FwdChunk& W, int lane, bool real, const float4& g0,
+                                          const float4& b, const float4& g1, uint2 bx, int fj0,
                                           int fi0) {
-  const float lw = real ? b.y : -INFINITY;
-  const ItemGeo g = item_geo(a, b, c, bx, fj0, fi0);
-  W.p0[lane] = make_float4(g.r11, g.r11, g.kq, g.kq);
-  W.p1[lane] = make_float4(g.ns0q, g.ns0q, g.a1, g.a1);
-  W.p2[lane] = make_float4(g.a0, g.a0, g.nyh, g.nyh);
-  W.p3[lane] = make_float4(g.nyl, g.nyl, g.r22, g.r22);
-  W.p4[lane] = make_float4(lw, lw, b.z, b.z);
+  const float nlw = real ? -b.y : INFINITY;
+  W.p0[lane] = make_float4(g0.x, g0.x, g0.y, g0.y);
+  W.p1[lane] = make_float4(g0.z, g0.z, g0.w, g0.w);
+  W.p2[lane] = make_float4(g1.x, g1.x, g1.y, g1.y);
+  W.p3[lane] = make_float4(g1.z, g1.z, g1.w, g1.w);
+  W.p4[lane] = make_float4(nlw, nlw, b.z, b.z);
   if (PARTIAL) {
     const uint32_t cl = clip_box(bx, fj0, fi0, 8);
     const int cx0 = cl & 0xff, cx1 = (cl >> 8) & 0xff, ry0 = (cl >> 16) & 0xff, ry1 = cl >> 24;
     float l[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) l[q] = ((q >= cx0) & (q <= cx1)) ? lw : -INFINITY;
+    for (int q = 0; q < 8; ++q) l[q] = ((q >= cx0) & (q <= cx1)) ? nlw : INFINITY;
     W.lc[0][lane] = make_float4(l[0], l[1], l[2], l[3]);
     W.lc[1][lane] = make_float4(l[4], l[5], l[6], l[7]);
     W.rows[lane] = (2u << ry1) - (1u << ry0);
@@ -197,11 +199,31 @@ __device__ __forceinline__ void fwd_build(FwdChunk& W, int lane, bool real, cons
   if (CUT) W.thr[lane] = b.w;
 }
 
+// The record constants of a stage anchored at the tile's first pixel
+// (item_geo over the whole TILE x TILE region), computed once per record by
+// the producer warp for all of the tile's footprints and written over the
+// record words that only they were derived from: a <- (r11, kq, -s0q, a1), c
+// <- (a0, -yh, -yl, r22). A consumer adds its footprint's offset in the tile
+// to the pixel's column and row.
+template <int TILE, bool RAW, int BATCH>
+__device__ __forceinline__ void stage_tile_geo(RecStage<TILE, RAW, BATCH>& S, int lane) {
+  const int cnt = S.h.cnt, tj = S.h.tx * TILE, ti = S.h.ty * TILE;
+#pragma unroll
+  for (int q = 0; q < BATCH / 32; ++q) {
+    const int r = lane + 32 * q;
+    if (r < cnt) {
+      const ItemGeo g = item_geo<TILE>(S.a[r], S.b[r], S.c[r], S.box[r], tj, ti);
+      S.a[r] = make_float4(g.r11, g.kq, g.ns0q, g.a1);
+      S.c[r] = make_float4(g.a0, g.nyh, g.nyl, g.r22);
+    }
+  }
+}
+
 // The producer's finishing step of a forward stage: per 8x8 footprint of the
 // tile, the compacted lists of its live records (box covering the footprint
 // from the front, the others from the back) and their counts, from the
 // binning's footprint tests (the top byte of each instance's key), written to
-// the stage for the consumers.
+// the stage for the consumers; then the records' tile-anchored constants.
 template <int TILE, int BATCH>
 struct FwdPrep {
   static constexpr bool kDefer = true;
@@ -236,6 +258,7 @@ struct FwdPrep {
         S.npart[f] = (uint16_t)np;
       }
     }
+    stage_tile_geo(S, lane);
   }
 };
 
@@ -259,10 +282,14 @@ __global__ void __launch_bounds__(FwdShape<TILE, G, MINB>::NT, FwdShape<TILE, G,
   }
   const int grp = lane / LG, gl = lane % LG;
   const int y = gl & 7, cp0 = (gl >> 3) * NP;  // this lane's row and first column pair
-  const float2 k2 = make_float2((float)y, (float)y);
+  // the record constants are anchored at the tile: this footprint's offset in
+  // it goes into the lane's row and columns
+  const int dx0 = (warp % Tiling<TILE, 8>::FX) * 8, dy0 = (warp / Tiling<TILE, 8>::FX) * 8;
+  const float2 k2 = make_float2((float)(y + dy0), (float)(y + dy0));
   float2 col2[NP];
 #pragma unroll
-  for (int p = 0; p < NP; ++p) col2[p] = make_float2((float)(2 * (cp0 + p)), (float)(2 * (cp0 + p) + 1));
+  for (int p = 0; p < NP; ++p)
+    col2[p] = make_float2((float)(2 * (cp0 + p) + dx0), (float)(2 * (cp0 + p) + 1 + dx0));
   unsigned long long evaluated = 0;  // (record, footprint) items of this warp
   int fj0 = 0, fi0 = 0, tw = 0, th = 0;
   int64_t tpx = 0;
@@ -434,11 +461,14 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, cons
   const float2 ns0q = make_float2(ig.ns0q, ig.ns0q), a1 = make_float2(ig.a1, ig.a1);
   const float2 a0 = make_float2(ig.a0, ig.a0), nyh = make_float2(ig.nyh, ig.nyh);
   const float2 nyl = make_float2(ig.nyl, ig.nyl), r22 = make_float2(ig.r22, ig.r22);
-  const float2 lw = make_float2(bb.y, bb.y), cc = make_float2(bb.z, bb.z);
+  const float2 nlw = make_float2(-bb.y, -bb.y), cc = make_float2(bb.z, bb.z);
   const int cx0 = cl & 0xff, cx1 = (cl >> 8) & 0xff, ry0 = (cl >> 16) & 0xff, ry1 = cl >> 24;
-  float colv[8];  // column offsets; columns outside the box far away
+  float2 colv[8];  // column offsets as FP32x2 pairs; columns outside the box far away
 #pragma unroll
-  for (int c = 0; c < 8; ++c) colv[c] = (c >= cx0 && c <= cx1) ? (float)c : kFarCol;
+  for (int c = 0; c < 8; ++c) {
+    const float cv = (c >= cx0 && c <= cx1) ? (float)c : kFarCol;
+    colv[c] = make_float2(cv, cv);
+  }
   // packed sums over the footprint (.x even rows, .y odd rows, added at the end)
   float2 s0 = make_float2(0.f, 0.f), a4 = make_float2(0.f, 0.f);
   float2 s1p = make_float2(0.f, 0.f), u1p = make_float2(0.f, 0.f), u2p = make_float2(0.f, 0.f);
@@ -453,20 +483,20 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, cons
     const float2 dy = __fadd2_rn(__fadd2_rn(k2, nyh), nyl);
     const float2 t2 = __fmul2_rn(r22, dy);
     const float2 t2sq = __fmul2_rn(t2, t2);
-    float2 crow = __fadd2_rn(lw, neg2(t2sq));  // lw2 - t2^2
-    if (y < ry0 || y > ry1) crow.x = -INFINITY;  // row outside the box
-    if (y + 1 < ry0 || y + 1 > ry1) crow.y = -INFINITY;
+    float2 crow = __fadd2_rn(t2sq, nlw);  // t2^2 - lw2
+    if (y < ry0 || y > ry1) crow.x = INFINITY;  // row outside the box
+    if (y + 1 < ry0 || y + 1 > ry1) crow.y = INFINITY;
     float2 s1r = make_float2(0.f, 0.f), u1r = make_float2(0.f, 0.f);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      const float2 t1 = __ffma2_rn(r11, __fadd2_rn(make_float2(colv[c], colv[c]), nsh), nrs);
-      float2 e2 = __ffma2_rn(neg2(t1), t1, crow);  // lw2 - t2^2 - t1^2
+      const float2 t1 = __ffma2_rn(r11, __fadd2_rn(colv[c], nsh), nrs);
+      float2 n2 = __ffma2_rn(t1, t1, crow);  // t1^2 + t2^2 - lw2
       if (CUT) {
         const float2 q = __ffma2_rn(t1, t1, t2sq);
-        if (!(q.x <= bb.w)) e2.x = -INFINITY;
-        if (!(q.y <= bb.w)) e2.y = -INFINITY;
+        if (!(q.x <= bb.w)) n2.x = INFINITY;
+        if (!(q.y <= bb.w)) n2.y = INFINITY;
       }
-      const float2 w = make_float2(fast_exp2(e2.x), fast_exp2(e2.y));
+      const float2 w = make_float2(fast_exp2_neg(n2.x), fast_exp2_neg(n2.y));
       const float4 px = pxr[8 * j + c];
       const float2 rr = make_float2(px.x, px.y);
       const float2 g = __fmul2_rn(__ffma2_rn(rr, cc, make_float2(px.z, px.w)), w);  // w dL/dw
@@ -522,7 +552,8 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   pipe_init(S.Tb, S.bars, v, P, Sh::NCT);
   if (__syncthreads_or(dev_failed(v.hdr))) return;  // the whole CTA leaves, or none of it
-  // the binning's footprint tests apply when the footprints are 8x8
+  // the binning's footprint tests apply when the footprints are 8x8 (the
+  // 8x4-footprint variant tests its own)
   constexpr bool use_masks = FH == 8;
   if (warp == NW) {
     produce<TILE, true, true, false, NoPrep, NS, BATCH>(S.st, S.bars, S.Tb, v, vals, 1, P,

@@ -133,11 +133,12 @@ def test_grad_extreme_anisotropy():
 @pytest.mark.parametrize("tile,variant", [(16, v) for v in range(1, 5)] + [(8, 0), (8, 1)])
 def test_grad_variants(tile, variant):
     """Every compiled backward variant (footprint height, stages, records per
-    stage) against the oracle's gradient; the stages of 64 records make tiles
-    span several stages."""
+    stage) against the oracle's gradient, on dense tiles that span several
+    stages (items stay queued across stages, so the stage-release rule is
+    exercised) and on a sparse plane."""
     rng = np.random.default_rng(32)
-    g = synth.gaussians_scale_rot(rng, 1000, 0.03, 0.15)
-    pl = synth.planes_random(rng, [(40, 33), (64, 64)])
+    g = synth.gaussians_scale_rot(rng, 4000, 0.05, 0.3)
+    pl = synth.planes_random(rng, [(40, 33), (64, 64)], origin_range=0.05)
     target = rng.uniform(0, 1, pl["total_pixels"])
     cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, tile=tile, variant=min(variant, 2),
                         variant_bwd=variant)
