@@ -677,7 +677,7 @@ __device__ __forceinline__ uint32_t instance_footprints(const float4& a, const f
 // a record with many tiles); a record's live tiles come from its mask. The
 // few records with more than 64 box tiles are emitted after, one at a time, by
 // the whole warp re-testing their box tiles 32 at a time.
-__global__ void __launch_bounds__(256) k_emit(int ts, int cut, uint32_t inst_cap, WsView v) {
+__global__ void __launch_bounds__(256, 4) k_emit(int ts, int cut, uint32_t inst_cap, WsView v) {
   // the warp's 32 records' render data, read once (coalesced) for the
   // footprint tests of all their instances
   __shared__ float4 s_a[8][32], s_b[8][32];

@@ -3,6 +3,7 @@ CPU replay of the integer key derivation from the GPU's own pixel boxes, and
 the records and boxes match the oracle's FP64 decisions."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from paper_2505_05643_gb300 import binding as B
@@ -210,3 +211,84 @@ def test_sort_multi_pass_keys():
     assert np.all(np.diff(keys) >= 0)
     same = np.diff(keys) == 0
     assert np.all(np.diff(recs)[same] > 0)  # stable: ascending record id within a tile
+
+
+def _grab_u32(r, ptr, count):
+    off = ptr - r.ws.data_ptr()
+    return r.ws[off:off + 4 * count].view(torch.int32).cpu().numpy().view(np.uint32).copy()
+
+
+def test_sort_many_tiles_matches_stable_argsort():
+    """The one-sweep passes at a size that spans hundreds of sort tiles (their
+    digit offsets come from the look-back over every earlier tile): the sorted
+    (key, record) pairs are exactly NumPy's stable sort of the binning's output
+    by tile key, and the ranges delimit the tiles."""
+    g, pl = synth.workload_aniso_1m(n=200_000)
+    g = synth.scale_rot_to_tri(g, 1e-4)
+    cfg = R.make_config(cov_param=B.UG_COV_TRI, tile=16)
+    params = torch.from_numpy(R.pack_params(g, cfg.cov_param)).cuda()
+    r = R.Renderer(len(g["logit"]), pl, cfg)
+    r.preprocess(params)  # sizes the workspace
+    assert r.plan.sort_passes == 2  # the binning writes the buffers the last pass writes
+    kp, vp, rp, bp, *_ = B.ug_debug_views(r.plan, r.ws)
+    cap = int(r.plan.instance_capacity)
+    for ptr in (kp, vp):  # unwritten instances would read as all ones
+        off = ptr - r.ws.data_ptr()
+        r.ws[off:off + 4 * cap].fill_(255)
+    st = r.preprocess(params)
+    n = st["instances"]
+    assert n > 300 * 4096, n
+    keys0, vals0 = _grab_u32(r, kp, n), _grab_u32(r, vp, n)
+    # the binning's output (its groups' ranges come from the look-back): record
+    # slots ascending, each record's tiles ascending, every tile in the box
+    tk0 = (keys0 & np.uint32(0x00FFFFFF)).astype(np.int64)
+    v0 = vals0.astype(np.int64)
+    assert np.all(np.diff(v0) >= 0)
+    same_rec = np.diff(v0) == 0
+    assert np.all(np.diff(tk0)[same_rec] > 0)
+    boxes = _grab_u32(r, bp, 2 * st["records"]).reshape(-1, 2).astype(np.int64)
+    rec_plane = _grab_u32(r, B.ug_debug_views(r.plan, r.ws)[7], st["records"]).astype(np.int64)
+    off, tx = _tile_offsets(pl, 16)
+    local = tk0 - off[rec_plane[v0]]
+    ty, txx = local // tx[rec_plane[v0]], local % tx[rec_plane[v0]]
+    b = boxes[v0]
+    assert np.all(((b[:, 0] & 0xFFFF) >> 4 <= txx) & (txx <= (b[:, 0] >> 16) >> 4))
+    assert np.all(((b[:, 1] & 0xFFFF) >> 4 <= ty) & (ty <= (b[:, 1] >> 16) >> 4))
+    B.ug_bin_sort(r.plan, r.ws, None)
+    assert r.status()["status"] == B.UG_OK
+    keys1, vals1 = _grab_u32(r, kp, n), _grab_u32(r, vp, n)
+    order = np.argsort(keys0 & np.uint32(0x00FFFFFF), kind="stable")
+    assert np.array_equal(keys1, keys0[order])
+    assert np.array_equal(vals1, vals0[order])
+    ranges = _grab_u32(r, rp, 2 * int(r.plan.total_tiles)).reshape(-1, 2)
+    tk = keys1 & np.uint32(0x00FFFFFF)
+    t = np.arange(int(r.plan.total_tiles))
+    lo, hi = np.searchsorted(tk, t, "left"), np.searchsorted(tk, t, "right")
+    exp = np.where((hi > lo)[:, None], np.stack([lo, hi], 1), 0).astype(np.uint32)
+    assert np.array_equal(ranges, exp)
+    # a second sort of the same instances gives the same bits (deterministic)
+    r.preprocess(params)
+    B.ug_bin_sort(r.plan, r.ws, None)
+    assert np.array_equal(_grab_u32(r, kp, n), keys1)
+    assert np.array_equal(_grab_u32(r, vp, n), vals1)
+
+
+def test_sort_three_passes():
+    """More than 65,536 tiles: three 8-bit passes; order and ranges stay exact."""
+    rng = np.random.default_rng(24)
+    g = synth.gaussians_scale_rot(rng, 60_000, 0.01, 0.05)
+    pl = synth.planes_random(rng, [(512, 512)] * 17, origin_range=0.3)
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, tile=8)
+    r, _, _, _ = gpu_render(g, pl, cfg)
+    assert r.plan.sort_passes == 3
+    dv = r.debug_views()
+    keys, recs = dv["keys"].astype(np.int64), dv["records"].astype(np.int64)
+    assert len(keys) > 100_000
+    assert np.all(np.diff(keys) >= 0)
+    same = np.diff(keys) == 0
+    assert np.all(np.diff(recs)[same] > 0)
+    assert len(set(zip(keys.tolist(), recs.tolist()))) == len(keys)
+    t = np.arange(int(r.plan.total_tiles))
+    lo, hi = np.searchsorted(keys, t, "left"), np.searchsorted(keys, t, "right")
+    exp = np.where((hi > lo)[:, None], np.stack([lo, hi], 1), 0).astype(np.uint32)
+    assert np.array_equal(dv["ranges"], exp)
