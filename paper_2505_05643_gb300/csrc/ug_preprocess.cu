@@ -237,13 +237,19 @@ struct CullWarp {
 // Two tests per (Gaussian, plane). The first is the plane distance against the
 // Gaussian's largest extent, |m3| - Bm <= sqrt(chi2 smax) with smax >= S + B:
 // S = |Fi n|^2 <= ||Fi||_F^2 |n|^2 and |n|^2 <= 1.0004 for a valid plane, so it
-// passes every pair that cull_pair passes. Pairs that pass it go into the warp's
-// queue and take the full test 32 at a time, every lane busy.
+// passes every pair that cull_pair passes. It is evaluated as m3 = n.mu - n.o
+// with n.o per plane: three roundings in n.mu and in n.o (|n_k| <= 1.0001) and
+// one in the difference keep |m3 - n.(mu - o)| below 4.01 eps (|mu|_1 + |o|_1),
+// so with Bm = 8 eps (|mu|_1 + sqrt(3) max|o|) the test |m3| <= sqrt(thr1) + Bm
+// (one threshold per Gaussian, rounded up) passes every pair the exact distance
+// passes. Pairs that pass it go into the warp's queue and take the full test 32
+// at a time, every lane busy.
 template <int COV>
 __global__ void __launch_bounds__(256)
     k_cull(ug_gaussians g, int64_t n, int P, float chi2, float beta, float ratio, float reach,
            int64_t chunks, WsView v) {
   __shared__ CullPlane s_pl[kCullPlanesSmem];
+  __shared__ float4 s_no[kCullPlanesSmem];  // (n, n.o) of each plane, for the first test
   __shared__ CullWarp s_w[256 / 32];
   if (dev_failed(v.hdr)) return;
   const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -292,6 +298,16 @@ __global__ void __launch_bounds__(256)
     const float bmax = 5.f * eps * (smax + R2) + 25.f * eps * eps * R2 + 3.f * eps * smax;
     thr1 = L.active ? chi2 * (smax + bmax) * 1.0021f : -1.f;
   }
+  // first test |m3| <= T (inactive lanes: T < 0, never passes)
+  float T = -1.f;
+  if (L.active) {
+    const float eps = 5.9604645e-8f;
+    const float mu1 = __fadd_ru(__fadd_ru(fabsf(L.prm.mu[0]), fabsf(L.prm.mu[1])),
+                                fabsf(L.prm.mu[2]));
+    const float o1 = __fmul_ru(1.7320509f, v.hdr->origin_reach);
+    const float Bm = __fadd_ru(__fmul_ru(__fmul_ru(8.f * eps, __fadd_ru(mu1, o1)), 1.001f), 1e-30f);
+    T = __fadd_ru(__fsqrt_ru(thr1), Bm);
+  }
   if (live_warp) {
     const uint32_t fl = __ballot_sync(0xffffffffu, L.use64);
     if (lane == 0) v.gflag[chunk] = fl;
@@ -319,19 +335,18 @@ __global__ void __launch_bounds__(256)
       c.h = d.h;
       c.pad = 0;
       s_pl[q] = c;
+      s_no[q] = make_float4(d.n[0], d.n[1], d.n[2],
+                            fmaf(d.n[2], d.o[2], fmaf(d.n[1], d.o[1], d.n[0] * d.o[0])));
     }
     __syncthreads();
     if (!live_warp) continue;
     for (int q = lane; q < kCullPlanesSmem; q += 32) W.bits[q] = 0u;
     uint32_t head = 0, count = 0;
     for (int q = 0; q < np; ++q) {
-      const CullPlane& pl = s_pl[q];
-      const float d0 = mx - pl.o[0], d1 = my - pl.o[1], d2 = mz - pl.o[2];
-      const float eps = 5.9604645e-8f;
-      const float Bm = 8.f * eps * (fabsf(d0) + fabsf(d1) + fabsf(d2)) * 1.001f + 1e-30f;
-      const float m3 = fmaf(pl.n[2], d2, fmaf(pl.n[1], d1, pl.n[0] * d0));
-      const float lo = fmaxf(fabsf(m3) - Bm, 0.f);
-      const uint32_t bal = __ballot_sync(0xffffffffu, lo * lo <= thr1);
+      const float4 nq = s_no[q];
+      const float m3 = __fsub_rn(__fmaf_rn(nq.z, mz, __fmaf_rn(nq.y, my, __fmul_rn(nq.x, mx))),
+                                 nq.w);
+      const uint32_t bal = __ballot_sync(0xffffffffu, fabsf(m3) <= T);
       if ((bal >> lane) & 1u)
         W.queue[(head + count + __popc(bal & lt)) % 64u] = (uint16_t)((q << 5) | lane);
       count += __popc(bal);
