@@ -13,11 +13,21 @@
  *   opacity      alpha_i = sigmoid(logit_i) (Sec. 4.5);
  *   probe frame  mu3D = W mu (rows u, v, n = u x v, origin o), Sigma3D =
  *                W Sigma W^T (Sec. 4.1, Eq. mahalanobis-3d and the line after);
- *   cut-off      half-extents from the p% ellipsoid (Sec. 4.3, Eq. ellipsoid
- *                and Eq. boundary): the printed cofactor/determinant formula
- *                applied to the matrix of the quadratic form, the precision
- *                P3D = (Sigma3D)^-1, i.e. h_k = sqrt(chi2 * cof_kk(P3D) /
- *                det(P3D));
+ *   cut-off      half-extents of the p% ellipsoid (Sec. 4.3, Eq. ellipsoid
+ *                and Eq. boundary): the box is the ellipsoid's axis-aligned
+ *                bound in the probe frame, h_k = the largest probe coordinate
+ *                r_k . (X - mu) over {(X - mu)^T Sigma^-1 (X - mu) <= chi2},
+ *                i.e. h_k = sqrt(chi2 * r_k^T Sigma r_k) for the frame rows
+ *                r_k = u, v, n. For an orthonormal frame this is the printed
+ *                cofactor/determinant formula applied to the matrix of the
+ *                quadratic form, P3D = (Sigma3D)^-1: sqrt(chi2 * cof_kk(P3D) /
+ *                det(P3D)). The inputs' frames are FP32 (orthonormal to about
+ *                1e-7), and the cofactor form of W Sigma^-1 W^T then differs
+ *                from the ellipsoid's bound by up to (s_max / s_min)^2 * 1e-7
+ *                (per cent at axis ratios of 1e4), so the oracle evaluates the
+ *                bound itself: r_k^T Sigma r_k = |L^-1 r_k|^2 by forward
+ *                substitution (triangular form) or sum_a s_a^2 (R_a . r_k)^2
+ *                (scale and rotation), sums of squares without cancellation;
  *   phase 1      a Gaussian is rejected on a plane iff m3 - h3 > 0 or
  *                m3 + h3 < 0 (Sec. 4.4 load balancing, item 1);
  *   phase 2      pixel x is inside iff m1 - h1 <= x1 <= m1 + h1 and
@@ -139,6 +149,28 @@ static void precision(const double* covp, int cov_param, double beta, double Pi[
   }
 }
 
+/* r^T Sigma r of one Gaussian (Sigma = (L L^T)^-1 or R diag(s^2) R^T) for a
+ * direction r, as a sum of squares: |y|^2 with L y = r by forward
+ * substitution, or sum_a s_a^2 (R_a . r)^2 with R_a the a-th principal axis. */
+static double sigma_quad(const double* covp, int cov_param, double beta, const double r[3]) {
+  if (cov_param == 0) {
+    double L[3][3];
+    tri_factor(covp, beta, L);
+    const double y0 = r[0] / L[0][0];
+    const double y1 = (r[1] - L[1][0] * y0) / L[1][1];
+    const double y2 = (r[2] - L[2][0] * y0 - L[2][1] * y1) / L[2][2];
+    return y0 * y0 + y1 * y1 + y2 * y2;
+  }
+  double R[3][3];
+  quat_rotation(covp + 3, R, NULL, NULL);
+  double s = 0;
+  for (int a = 0; a < 3; ++a) {
+    const double p = R[0][a] * r[0] + R[1][a] * r[1] + R[2][a] * r[2];
+    s += exp(2.0 * covp[a]) * p * p;
+  }
+  return s;
+}
+
 /* Cofactor matrix and determinant of a 3x3 matrix. */
 static double cofactors(const double A[3][3], double C[3][3]) {
   C[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
@@ -175,19 +207,8 @@ static void pg_compute(const or_plane* pl, const double* mean, const double* cov
   const double* rows[3] = {pl->u, pl->v, pl->n};
   double d[3] = {mean[0] - pl->o[0], mean[1] - pl->o[1], mean[2] - pl->o[2]};
   for (int j = 0; j < 3; ++j) g->m[j] = rows[j][0] * d[0] + rows[j][1] * d[1] + rows[j][2] * d[2];
-  /* P3D = Wr Pi Wr^T */
-  double P3[3][3];
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) {
-      double s = 0;
-      for (int i = 0; i < 3; ++i)
-        for (int k = 0; k < 3; ++k) s += rows[a][i] * g->Pi[i][k] * rows[b][k];
-      P3[a][b] = s;
-    }
-  double C[3][3];
-  double det = cofactors(P3, C);
-  double lam = cfg->chi2 / det;
-  for (int k = 0; k < 3; ++k) g->h[k] = sqrt(lam * C[k][k]);
+  /* the ellipsoid's bound along each frame row: sqrt(chi2 r_k^T Sigma r_k) */
+  for (int k = 0; k < 3; ++k) g->h[k] = sqrt(cfg->chi2 * sigma_quad(covp, cfg->cov_param, cfg->beta, rows[k]));
   /* phase 1: reject iff b3min > 0 or b3max < 0 */
   double bmin = g->m[2] - g->h[2], bmax = g->m[2] + g->h[2];
   g->visible = !(bmin > 0.0 || bmax < 0.0);

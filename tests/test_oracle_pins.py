@@ -215,6 +215,56 @@ def test_K4_box_is_the_ellipsoid_aabb():
             np.testing.assert_allclose(abs(xa[a]), h[a], rtol=1e-10)
 
 
+@pytest.mark.parametrize("cov_param", [0, 1])
+def test_box_is_the_ellipsoid_bound_for_fp32_frames_and_needles(cov_param):
+    """The box half-extent is the largest probe coordinate r_k . (X - mu) over
+    the chi2 ellipsoid, sqrt(chi2 r_k^T Sigma r_k) (Sec. 4.3, Eq. boundary),
+    also when the frame rows are FP32 (orthonormal only to about 1e-7) and
+    the Gaussians are needles and discs with axis ratios up to 1e4: the
+    oracle's half-extents against the definition evaluated with 50 digits
+    from the same inputs (Sigma from the factor, u and v as given, n = u x v).
+    The cofactor form of W Sigma^-1 W^T, exact only for an orthonormal frame,
+    is off by up to per cent here."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    rng = np.random.default_rng(19)
+    g = synth.gaussians_anisotropic(rng, 40)  # axis ratios log-uniform to 1e4
+    if cov_param == 0:
+        g = synth.scale_rot_to_tri(g, 1e-4)
+    pl = synth.planes_random(rng, [(64, 64)] * 3)  # FP32 axes
+    cfg = oracle.Config(cov_param=cov_param)
+    geo = oracle.geometry(g, pl, cfg)
+    chi2 = mp.mpf(cfg.chi2)
+    worst = 0.0
+    for k in range(40):
+        if cov_param == 0:
+            t = [mp.mpf(float(x)) for x in g["tri"][:, k]]
+            b = mp.mpf(cfg.beta)
+            L = mp.matrix([[t[0] ** 2 + b, 0, 0], [t[1], t[3] ** 2 + b, 0],
+                           [t[2], t[4], t[5] ** 2 + b]])
+            Li = L ** -1
+            S = Li.T * Li
+        else:
+            q = [mp.mpf(float(x)) for x in g["quat"][:, k]]
+            nq = mp.sqrt(sum(x * x for x in q))
+            w, x, y, z = (c / nq for c in q)
+            R = mp.matrix([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                           [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                           [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+            D = mp.diag([mp.exp(2 * mp.mpf(float(s))) for s in g["log_scale"][:, k]])
+            S = R * D * R.T
+        for p in range(3):
+            u = [mp.mpf(float(c)) for c in pl["u"][p]]
+            v = [mp.mpf(float(c)) for c in pl["v"][p]]
+            n = [u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]]
+            for a, r in enumerate((u, v, n)):
+                rv = mp.matrix(r)
+                h = mp.sqrt(chi2 * (rv.T * S * rv)[0])
+                rel = abs(geo["h"][p, k, a] - float(h)) / float(h)
+                worst = max(worst, rel)
+    assert worst < 1e-12, worst
+
+
 def test_phase1_reject_rule():
     """A Gaussian is kept on a plane iff |m3| <= h3 (Sec. 4.4, item 1)."""
     rng = np.random.default_rng(10)
