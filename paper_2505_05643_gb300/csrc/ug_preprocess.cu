@@ -454,7 +454,9 @@ __device__ __forceinline__ void split_hl(dd x, float& h, float& l) {
 }
 
 // The record (see ug_internal.cuh) and the inputs of the backward chain
-// (kChainFloats floats: q1[3], q2[3], nh[3], rho3, ew[3], 0, 0, 0).
+// (kChainFloats floats: q1[3], q2[3], nh[3], rho3, ew[3], r11, r12, r22, with
+// r12 = r11 kappa formed in FP32 from the record's high parts, so the chain
+// reads the pixel-unit factor from here instead of the render words).
 template <typename T>
 __device__ __forceinline__ void write_record(const PairLsq<T>& L, const PairBox& pb,
                                              const GaussParams& prm, float chi2, WsView& v,
@@ -475,7 +477,7 @@ __device__ __forceinline__ void write_record(const PairLsq<T>& L, const PairBox&
   d4[0] = make_float4(L.q1[0], L.q1[1], L.q1[2], L.q2[0]);
   d4[1] = make_float4(L.q2[1], L.q2[2], L.nh[0], L.nh[1]);
   d4[2] = make_float4(L.nh[2], L.rho3, L.ew[0], L.ew[1]);
-  d4[3] = make_float4(L.ew[2], 0.f, 0.f, 0.f);
+  d4[3] = make_float4(L.ew[2], L.r11, __fmul_rn(L.r11, kh), L.r22);
 }
 
 __device__ __forceinline__ bool box_empty(uint2 b) {
@@ -990,9 +992,8 @@ __global__ void __launch_bounds__(256)
       float F[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) F[q] = f.F[q / 3][q % 3];
-      const float4 ra = v.rec_a[slot], rb = v.rec_b[slot];
       ChainOut o;
-      chain_record(ch, ra.z, ra.z * ra.w, rb.x, pl, F, acc, o);
+      chain_record(ch, ch[13], ch[14], ch[15], pl, F, acc, o);
       record_param_grad<float, COV>(o, f, prm, acc[0], out);
     }
     float4* dst = reinterpret_cast<float4*>(v.rec_pgrad + (size_t)slot * 12);
