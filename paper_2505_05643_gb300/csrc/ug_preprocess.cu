@@ -237,13 +237,15 @@ struct CullWarp {
 // Two tests per (Gaussian, plane). The first is the plane distance against the
 // Gaussian's largest extent, |m3| - Bm <= sqrt(chi2 smax) with smax >= S + B:
 // S = |Fi n|^2 <= ||Fi||_F^2 |n|^2 and |n|^2 <= 1.0004 for a valid plane, so it
-// passes every pair that cull_pair passes. It is evaluated as m3 = n.mu - n.o
+// passes every pair that cull_pair passes. It is evaluated as m3' = n.mu - n.o
 // with n.o per plane: three roundings in n.mu and in n.o (|n_k| <= 1.0001) and
-// one in the difference keep |m3 - n.(mu - o)| below 4.01 eps (|mu|_1 + |o|_1),
-// so with Bm = 8 eps (|mu|_1 + sqrt(3) max|o|) the test |m3| <= sqrt(thr1) + Bm
-// (one threshold per Gaussian, rounded up) passes every pair the exact distance
-// passes. Pairs that pass it go into the warp's queue and take the full test 32
-// at a time, every lane busy.
+// one in the difference keep |m3' - n.(mu - o)| below 4.01 eps (|mu|_1 + |o|_1).
+// cull_pair passes only if |m3| <= sqrt(thr1) + Bm with its own m3 within Bm =
+// 8.008 eps |mu - o|_1 of n.(mu - o), so |m3'| <= sqrt(thr1) + 2 Bm + 4.01 eps
+// (|mu|_1 + |o|_1) <= sqrt(thr1) + 20.03 eps (|mu|_1 + |o|_1): the test |m3'| <=
+// sqrt(thr1) + 24 eps (|mu|_1 + sqrt(3) max|o|) (one threshold per Gaussian,
+// rounded up) passes every pair that cull_pair passes. Pairs that pass it go
+// into the warp's queue and take the full test 32 at a time, every lane busy.
 template <int COV>
 __global__ void __launch_bounds__(256)
     k_cull(ug_gaussians g, int64_t n, int P, float chi2, float beta, float ratio, float reach,
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(256)
     const float mu1 = __fadd_ru(__fadd_ru(fabsf(L.prm.mu[0]), fabsf(L.prm.mu[1])),
                                 fabsf(L.prm.mu[2]));
     const float o1 = __fmul_ru(1.7320509f, v.hdr->origin_reach);
-    const float Bm = __fadd_ru(__fmul_ru(__fmul_ru(8.f * eps, __fadd_ru(mu1, o1)), 1.001f), 1e-30f);
+    const float Bm = __fadd_ru(__fmul_ru(__fmul_ru(24.f * eps, __fadd_ru(mu1, o1)), 1.001f), 1e-30f);
     T = __fadd_ru(__fsqrt_ru(thr1), Bm);
   }
   if (live_warp) {

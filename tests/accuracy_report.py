@@ -101,10 +101,9 @@ def main():
                  R.make_config(cov_param=B.UG_COV_SCALE_ROT), subset=sub)
     g, pl = synth.workload_aniso_1m()
     g = synth.scale_rot_to_tri(g, 1e-4)
-    pl4 = synth.select_planes(pl, [0, 1, 2, 3])
     sub = np.random.default_rng(0).choice(len(g["logit"]), 2000, replace=False)
-    rows += case("aniso_1m tri, planes 0-3 (2000 Gaussians)", g, pl4,
-                 R.make_config(cov_param=B.UG_COV_TRI), subset=sub)
+    rows += case("aniso_1m tri, all 64 planes (gradients: 2000 Gaussians)", g, pl,
+                 R.make_config(cov_param=B.UG_COV_TRI, variant=5, variant_bwd=0), subset=sub)
     lines = ["| workload | output | n compared | n ambiguous (either decision valid) | max abs err | "
              "max err / tolerance, clear decisions | max err / tolerance, ambiguous pixels | "
              "fraction within tolerance |", "|---|---|---|---|---|---|---|---|"]
