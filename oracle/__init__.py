@@ -88,7 +88,8 @@ def _lib():
         lib.or_geometry.restype = None
         lib.or_geometry.argtypes = [i64, P, P, P, P, i32, P, P, P, P, P, P, P, P]
         lib.or_render_grad.restype = None
-        lib.or_render_grad.argtypes = [i64, P, P, P, P, i32, P, P, P, P, P, P, P, i64, P, P, P, i32]
+        lib.or_render_grad.argtypes = [i64, P, P, P, P, i32, P, P, P, P, P, P, P, i64, P, P, P, P,
+                                       i32]
         lib.or_contrib.restype = i64
         lib.or_contrib.argtypes = [P, P, ctypes.c_double, ctypes.c_double, i32, P, P, P, P, P, i64]
         lib.or_covariance.restype = None
@@ -174,11 +175,14 @@ def geometry(g: dict, planes: dict, cfg: Config) -> dict:
 
 
 def render_grad(g: dict, planes: dict, cfg: Config, image, alpha, grad_image, subset=None,
-                threads: int = 0, with_ambiguity: bool = False):
+                threads: int = 0, with_ambiguity: bool = False, with_pre: bool = False):
     """Analytic FP64 gradient. Returns (grads, grads_abs), each (k, nparam)
     with nparam = 3 + (6|7) + 2 in the order mean, covp, logit, intensity;
-    with_ambiguity=True also returns a (k,) bool array: the Gaussian has an
-    inclusion decision within the ambiguity margin."""
+    grads_abs is the sum of |per-pair term|. with_ambiguity=True also returns a
+    (k,) bool array: the Gaussian has an inclusion decision within the
+    ambiguity margin. with_pre=True also returns (last) the same sums with
+    |c - C| in dL/dw = G (c - C) / alpha replaced by |c| + |C|: the size of the
+    per-pair terms before the cancellation in c - C."""
     mean, covp, logit, inten = _gauss(g, cfg.cov_param)
     P, pl, sz, _ = _planes(planes)
     nc = 6 if cfg.cov_param == 0 else 7
@@ -195,14 +199,14 @@ def render_grad(g: dict, planes: dict, cfg: Config, image, alpha, grad_image, su
         sub_ptr, nsub = _ptr(subset), k
     grads = np.zeros((k, npar), np.float64)
     gabs = np.zeros((k, npar), np.float64)
+    gpre = np.zeros((k, npar), np.float64) if with_pre else None
     amb = np.zeros(k, np.int32)
     _lib().or_render_grad(len(logit), _ptr(mean), _ptr(covp), _ptr(logit), _ptr(inten), P,
                           _ptr(pl), _ptr(sz), ctypes.byref(_cfg(cfg)), _ptr(image), _ptr(alpha),
-                          _ptr(grad_image), sub_ptr, nsub, _ptr(grads), _ptr(gabs), _ptr(amb),
-                          threads)
-    if with_ambiguity:
-        return grads, gabs, amb.astype(bool)
-    return grads, gabs
+                          _ptr(grad_image), sub_ptr, nsub, _ptr(grads), _ptr(gabs),
+                          _ptr(gpre) if with_pre else None, _ptr(amb), threads)
+    out = (grads, gabs) + ((amb.astype(bool),) if with_ambiguity else ())
+    return out + ((gpre,) if with_pre else ())
 
 
 def contrib(mean3, covp_row, logit: float, intensity: float, planes: dict, cfg: Config):

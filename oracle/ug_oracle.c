@@ -523,7 +523,8 @@ void or_render_grad(int64_t n, const double* mean, const double* covp, const dou
                     const double* intensity, int32_t P, const double* planes, const int64_t* sizes,
                     const or_config* cfg, const double* image, const double* alpha,
                     const double* grad_image, const int64_t* subset, int64_t nsub, double* grads,
-                    double* grads_abs, int32_t* amb_gauss, int32_t nthreads) {
+                    double* grads_abs, double* grads_abs_pre, int32_t* amb_gauss,
+                    int32_t nthreads) {
   const int nc = ncovp(cfg->cov_param);
   const int np = 3 + nc + 2;
   const int64_t count = subset ? nsub : n;
@@ -533,9 +534,9 @@ void or_render_grad(int64_t n, const double* mean, const double* covp, const dou
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t s = 0; s < count; ++s) {
     int64_t g = subset ? subset[s] : s;
-    double gmu[3] = {0, 0, 0}, amu[3] = {0, 0, 0};
-    double gPi[3][3] = {{0}}, aPi[3][3] = {{0}};
-    double glogit = 0, alogit = 0, gc = 0, ac = 0;
+    double gmu[3] = {0, 0, 0}, amu[3] = {0, 0, 0}, pmu[3] = {0, 0, 0};
+    double gPi[3][3] = {{0}}, aPi[3][3] = {{0}}, pPi[3][3] = {{0}};
+    double glogit = 0, alogit = 0, plogit = 0, gc = 0, ac = 0;
     int any_amb = 0;
     for (int32_t pi = 0; pi < P; ++pi) {
       or_plane pl;
@@ -572,21 +573,26 @@ void or_render_grad(int64_t n, const double* mean, const double* covp, const dou
           double w = G.alpha * exp(-0.5 * q);
           double Gp = grad_image[o], A = alpha[o], C = image[o];
           double dLdw = Gp * (G.c - C) / A;
+          /* |dL/dw| before the cancellation in c - C */
+          double pdLdw = fabs(Gp / A) * (fabs(G.c) + fabs(C));
           gc += Gp * w / A;
           ac += fabs(Gp * w / A);
-          double dLdq = -0.5 * w * dLdw;
+          double dLdq = -0.5 * w * dLdw, pdLdq = 0.5 * w * pdLdw;
           double Pd[3];
           for (int a = 0; a < 3; ++a) Pd[a] = G.Pi[a][0] * dl[0] + G.Pi[a][1] * dl[1] + G.Pi[a][2] * dl[2];
           for (int a = 0; a < 3; ++a) {
             gmu[a] += dLdq * (-2.0 * Pd[a]);
             amu[a] += fabs(dLdq * 2.0 * Pd[a]);
+            pmu[a] += pdLdq * fabs(2.0 * Pd[a]);
             for (int b = 0; b < 3; ++b) {
               gPi[a][b] += dLdq * dl[a] * dl[b];
               aPi[a][b] += fabs(dLdq * dl[a] * dl[b]);
+              pPi[a][b] += pdLdq * fabs(dl[a] * dl[b]);
             }
           }
           glogit += dLdw * w * (1.0 - G.alpha);
           alogit += fabs(dLdw * w * (1.0 - G.alpha));
+          plogit += pdLdw * w * (1.0 - G.alpha);
         }
       }
     }
@@ -602,6 +608,13 @@ void or_render_grad(int64_t n, const double* mean, const double* covp, const dou
     aout[3 + nc] = alogit;
     out[4 + nc] = gc;
     aout[4 + nc] = ac;
+    if (grads_abs_pre) {
+      double* pout = grads_abs_pre + np * s;
+      for (int a = 0; a < 3; ++a) pout[a] = pmu[a];
+      chain_covp_abs(covp + nc * g, cfg, pPi, pout + 3);
+      pout[3 + nc] = plogit;
+      pout[4 + nc] = ac; /* dL/dc = sum G w / alpha has no c - C */
+    }
     if (amb_gauss) amb_gauss[s] = any_amb;
   }
 }

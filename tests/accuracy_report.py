@@ -24,12 +24,12 @@ sys.path.insert(0, ROOT)
 sys.path.insert(0, os.path.join(ROOT, "tests"))
 
 import oracle  # noqa: E402
-from gpu_helpers import ATOL, RTOL, forward_bound, gpu_render, oracle_config  # noqa: E402
+from gpu_helpers import (ATOL, GRAD_FLOOR, GRAD_PRE, GRAD_RTOL, RTOL, forward_bound,  # noqa: E402
+                         fp32_inputs, gpu_render, grad_floor_scale, oracle_config)
 from paper_2505_05643_gb300 import binding as B  # noqa: E402
 from paper_2505_05643_gb300 import render as R  # noqa: E402
 from paper_2505_05643_gb300 import synth  # noqa: E402
 
-GRAD_RTOL, GRAD_FLOOR = 1e-3, 1e-4  # as in the backward parity tests
 
 
 def forward_rows(name, image, alpha, ref):
@@ -74,14 +74,16 @@ def case(name, g, pl, cfg, target_seed=7, subset=None):
     rows = forward_rows(name, image, alpha, ref)
     tgt = np.random.default_rng(target_seed).uniform(0, 1, pl["total_pixels"])
     _, gimg = oracle.mse_loss_grad(ref["image"], tgt)
-    gi = torch.from_numpy(gimg.astype(np.float32)).cuda()
-    im_t = torch.from_numpy(ref["image"].astype(np.float32)).cuda()
-    al_t = torch.from_numpy(ref["alpha"].astype(np.float32)).cuda()
+    im64, al64, gi64 = fp32_inputs(ref["image"], ref["alpha"], gimg)
+    gi = torch.from_numpy(gi64.astype(np.float32)).cuda()
+    im_t = torch.from_numpy(im64.astype(np.float32)).cuda()
+    al_t = torch.from_numpy(al64.astype(np.float32)).cuda()
     grads = r.backward(params, im_t, al_t, gi)
     torch.cuda.synchronize()
-    gref, gabs, amb = oracle.render_grad(g, pl, ocfg, ref["image"], ref["alpha"], gimg,
-                                         subset=subset, with_ambiguity=True)
-    rows += grad_rows(name, grads, int(cfg.cov_param), gref, gabs, amb, subset)
+    gref, gabs, amb, gpre = oracle.render_grad(g, pl, ocfg, im64, al64, gi64, subset=subset,
+                                               with_ambiguity=True, with_pre=True)
+    rows += grad_rows(name, grads, int(cfg.cov_param), gref, grad_floor_scale(gabs, gpre), amb,
+                      subset)
     return rows
 
 
@@ -124,9 +126,11 @@ def main():
                     "involve: a flipped decision there moves the value by at most A, so the "
                     "ambiguous pixels' ratio is below 1 by construction and the clear pixels' "
                     "ratio measures the arithmetic); gradients |err| <= "
-                    f"{GRAD_RTOL:g} |ref| + {GRAD_FLOOR:g} sum |per-pair term| (Gaussians with "
+                    f"{GRAD_RTOL:g} |ref| + {GRAD_FLOOR:g} sum |per-pair term| + {GRAD_PRE:.3g} "
+                    "sum |per-pair term before the cancellation in c - C| (Gaussians with "
                     "an ambiguous decision excluded). The GPU gradient is evaluated with the "
-                    "oracle's image and alpha as inputs, so it isolates the backward's error.\n\n")
+                    "oracle's image and alpha as inputs (rounded to FP32, as the GPU receives them; the "
+                    "oracle's gradient at the same inputs), so it isolates the backward's error.\n\n")
             f.write(text + "\n")
 
 

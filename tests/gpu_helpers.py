@@ -12,6 +12,32 @@ from paper_2505_05643_gb300 import render as R
 RTOL = 1e-4
 ATOL = 1e-6
 
+# Gradient tolerance: |gpu - ref| <= GRAD_RTOL |ref| + GRAD_FLOOR S + GRAD_PRE S_pre.
+# S is the oracle's sum of |per-pair term| (the scale of FP32 rounding in a sum
+# that cancels): relative 1e-3 as stated for the gradient, and a floor of 1e-4
+# of the absolute sum (FP32 sums of 1e3-1e5 terms carry a relative error of the
+# absolute sum of about sqrt(n) * 6e-8 <= 2e-5). S_pre is the same sum with |c -
+# C| in dL/dw = G (c - C) / alpha replaced by |c| + |C|: the backward forms
+# G c / alpha and G C / alpha in FP32 (C itself is the forward's FP32 output),
+# so where an intensity c is close to the image value C (every c is 0.5 in the
+# paper's initialisation) a per-pair term carries a few FP32 ulps of its size
+# before that cancellation: GRAD_PRE = 8 ulps of it.
+GRAD_RTOL = 1e-3
+GRAD_FLOOR = 1e-4
+GRAD_PRE = 8 * 2.0 ** -24
+
+
+def grad_floor_scale(gabs, gpre):
+    """Per entry, the scale S of the GRAD_FLOOR term that also carries the
+    GRAD_PRE term: GRAD_FLOOR * S = GRAD_FLOOR * gabs + GRAD_PRE * gpre."""
+    return gabs + (GRAD_PRE / GRAD_FLOOR) * gpre
+
+
+def fp32_inputs(*arrays):
+    """Arrays as the GPU receives them (rounded to FP32) and back in FP64: the
+    oracle's gradient is evaluated at the same C, alpha and dL/dC."""
+    return tuple(np.asarray(np.asarray(a, np.float32), np.float64) for a in arrays)
+
 
 def oracle_config(cfg: B.ug_config) -> oracle.Config:
     return oracle.Config(chi2=float(np.float32(cfg.chi2)), beta=float(np.float32(cfg.beta)),

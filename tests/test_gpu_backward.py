@@ -10,17 +10,10 @@ from paper_2505_05643_gb300 import binding as B
 from paper_2505_05643_gb300 import render as R
 from paper_2505_05643_gb300 import synth
 
-from gpu_helpers import gpu_render, oracle_config
+from gpu_helpers import (GRAD_FLOOR, GRAD_RTOL, fp32_inputs, gpu_render, grad_floor_scale,
+                         oracle_config)
 
 pytestmark = pytest.mark.gpu
-
-# Gradient tolerance: |gpu - ref| <= GRAD_RTOL |ref| + GRAD_FLOOR * S, where S is
-# the oracle's sum of |per-pair term| (the scale of FP32 rounding in a sum that
-# cancels): relative 1e-3 as stated for the gradient, and a floor of 1e-4 of
-# the absolute sum (FP32 sums of 1e3-1e5 terms carry a relative error of the
-# absolute sum of about sqrt(n) * 6e-8 <= 2e-5).
-GRAD_RTOL = 1e-3
-GRAD_FLOOR = 1e-4
 
 
 def _grad_rows(grads_t, cov_param, subset=None):
@@ -45,14 +38,17 @@ def _check_grads(gpu, ref, gabs, names, what):
 def _backward_case(g, pl, cfg, target, subset=None, split=False):
     """GPU gradient with the oracle's dL/dC, C and alpha as inputs (the
     forward's own FP32 error is tested separately; dL/dw = r (c - C) is
-    sensitive to C where c is close to C), against the oracle's gradient."""
+    sensitive to C where c is close to C), against the oracle's gradient at
+    the same inputs as the GPU receives them (FP32). Returns the compared
+    rows, the reference, the floor scale (grad_floor_scale) and the gradient."""
     ocfg = oracle_config(cfg)
     ref = oracle.render(g, pl, ocfg)
     _, gimg = oracle.mse_loss_grad(ref["image"], target)
+    im64, al64, gi64 = fp32_inputs(ref["image"], ref["alpha"], gimg)
     r, params, image, alpha = gpu_render(g, pl, cfg)
-    gi = torch.from_numpy(gimg.astype(np.float32)).cuda()
-    im_t = torch.from_numpy(ref["image"].astype(np.float32)).cuda()
-    al_t = torch.from_numpy(ref["alpha"].astype(np.float32)).cuda()
+    gi = torch.from_numpy(gi64.astype(np.float32)).cuda()
+    im_t = torch.from_numpy(im64.astype(np.float32)).cuda()
+    al_t = torch.from_numpy(al64.astype(np.float32)).cuda()
     if split:  # rows a7 and a8 through their own entry points
         grads = torch.empty_like(params)
         B.ug_render_backward_raster(r.plan, r.ws, im_t, al_t, gi)
@@ -62,14 +58,14 @@ def _backward_case(g, pl, cfg, target, subset=None, split=False):
     else:
         grads = r.backward(params, im_t, al_t, gi)
     torch.cuda.synchronize()
-    gref, gabs, amb = oracle.render_grad(g, pl, ocfg, ref["image"], ref["alpha"], gimg,
-                                         subset=subset, with_ambiguity=True)
+    gref, gabs, amb, gpre = oracle.render_grad(g, pl, ocfg, im64, al64, gi64, subset=subset,
+                                               with_ambiguity=True, with_pre=True)
     gpu = _grad_rows(grads, cfg.cov_param, subset)
     # a Gaussian with an inclusion decision within rounding of an edge may
     # include or drop that pixel (either is correct): compare the others
     keep = ~amb
     assert keep.mean() > 0.9, keep.mean()
-    return gpu[keep], gref[keep], gabs[keep], grads
+    return gpu[keep], gref[keep], grad_floor_scale(gabs, gpre)[keep], grads
 
 
 @pytest.mark.parametrize("cov_param", [B.UG_COV_SCALE_ROT, B.UG_COV_TRI])

@@ -166,3 +166,33 @@ def test_grad_matches_torch_autograd(cov_param):
         ref.append(gr[row] if row is not None else gr)
     ref = np.stack(ref, axis=1)
     np.testing.assert_allclose(grads, ref, rtol=1e-8, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("cov_param", [0, 1])
+def test_pre_cancellation_sums(cov_param):
+    """The absolute sums before the cancellation in c - C: the gradient and the
+    plain absolute sums are unchanged by asking for them; they bound the plain
+    sums from above (|c - C| <= |c| + |C|) and equal them for the intensity row
+    (dL/dc has no c - C); with every intensity equal to the image value they
+    stay positive while the plain sums of the rows through dL/dw vanish."""
+    g, pl, target = _scene(cov_param, seed=5)
+    cfg = oracle.Config(cov_param=cov_param)
+    _, out = _loss(g, pl, cfg, target)
+    _, gimg = oracle.mse_loss_grad(out["image"], target)
+    sub = np.arange(0, len(g["logit"]), 7)
+    grads, gabs = oracle.render_grad(g, pl, cfg, out["image"], out["alpha"], gimg, subset=sub)
+    grads2, gabs2, gpre = oracle.render_grad(g, pl, cfg, out["image"], out["alpha"], gimg,
+                                             subset=sub, with_pre=True)
+    assert np.array_equal(grads, grads2) and np.array_equal(gabs, gabs2)
+    assert np.all(gpre >= gabs * (1 - 1e-12))
+    np.testing.assert_array_equal(gpre[:, -1], gabs[:, -1])
+    # c = C everywhere: an image of constant value with every intensity equal to it
+    flat = np.full_like(out["image"], 0.25)
+    g2 = dict(g)
+    g2["intensity"] = np.full_like(g["intensity"], 0.25)
+    _, gabs3, gpre3 = oracle.render_grad(g2, pl, cfg, flat, out["alpha"], gimg, subset=sub,
+                                         with_pre=True)
+    reach = gabs3[:, -1] > 0  # Gaussians that reach a pixel
+    assert reach.any()
+    assert np.all(gabs3[reach, :-1] == 0)
+    assert np.all(gpre3[reach, :3].sum(1) > 0)
