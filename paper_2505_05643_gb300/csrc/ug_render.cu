@@ -415,9 +415,9 @@ struct BwdSmem {
   RecStage<TILE, true, BATCH> st[NS];
   PipeBars<NS> bars;
   BwdQueue<BATCH> q[Sh::NW];
-  // per footprint, row pair rp and column c (index 8 rp + c): r, r', -rC, -rC'
-  // of rows 2 rp and 2 rp + 1
-  float4 pix[Sh::NW][FH * 4];
+  // per footprint and tile parity, row pair rp and column c (index 8 rp + c):
+  // r, r', -rC, -rC' of rows 2 rp and 2 rp + 1
+  float4 pix[Sh::NW][2][FH * 4];
   PlaneTable Tb;
 };
 
@@ -531,11 +531,15 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, cons
 // Each consumer warp owns one footprint of the tile. It queues the indices of
 // the stage's records that are live for its footprint and processes the queue
 // 32 items at a time, one item per lane, reading each item's record from its
-// stage; the last items of a tile are processed when the tile ends. A stage is
-// released when all of its items are processed, and at the latest before the
-// wait that reuses its slot (the items still queued are processed first, so
-// the producer never waits for a stage that a consumer holds). The warps share
-// no barrier.
+// stage. Items are carried across tiles (a round may hold the end of one tile
+// and the start of the next): the pixel factors are kept for two tiles (by
+// tile parity), each item names its parity, and before a tile writes its
+// factors the items of the tile before the previous one are processed; only
+// the queue's last items, at the kernel's end, run as a partial round. A
+// stage is released when all of its items are processed, and at the latest
+// before the wait that reuses its slot (the items still queued are processed
+// first, so the producer never waits for a stage that a consumer holds). The
+// warps share no barrier.
 template <int TILE, int FH, int CUT, int NS = kBwdStages, int BATCH = kBatch, int MINB = 4>
 __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
     k_render_bwd(WsView v, const uint32_t* __restrict__ vals, int P, int total_tiles,
@@ -563,27 +567,34 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
   }
   const uint32_t lt = lanemask_lt();
   uint16_t* Q = S.q[warp].idx;
-  const float4* pix = S.pix[warp];
   unsigned long long evaluated = 0;
-  int fj0 = 0, fi0 = 0;
+  int fj0 = 0, fi0 = 0;           // this footprint's origin in the current tile
+  uint32_t tpar = 1;              // parity of the current tile (of this warp's tiles)
+  uint32_t qmark0 = 0, qmark1 = 0;  // queue end of the last tile of each parity
   uint32_t qhead = 0, qtail = 0;  // items processed / queued so far
   uint32_t qe0 = 0, qe1 = 0, qe2 = 0, qe3 = 0;  // qtail after each held stage's items, by slot
   auto qend = [&](uint32_t slot) {
     return slot == 0 ? qe0 : slot == 1 ? qe1 : slot == 2 ? qe2 : qe3;
   };
   uint32_t krel = 0;                    // the stages before krel are released
-  // item i of the queue (0 = its oldest) from row y0: its record read from its stage
+  // item i of the queue (0 = its oldest) from row y0: its record read from its
+  // stage, its footprint's origin from the stage's tile; queue entries: record
+  // index (bits 0-7), stage slot (8-9), tile parity (10)
   auto item = [&](uint32_t i, int y0, int rows, bool part) {
     const uint32_t e = Q[(qhead + i) % QL];
-    const RecStage<TILE, true, BATCH>& Rs = S.st[e >> 8];
+    const RecStage<TILE, true, BATCH>& Rs = S.st[(e >> 8) & 3u];
     const int r = (int)(e & 255u);
+    const float4* pix = S.pix[warp][(e >> 10) & 1u];
+    int ij0, ii0;
+    footprint_origin(warp, T::FX, FH, Rs.h.tx, Rs.h.ty, TILE, ij0, ii0);
     const uint2 bx = Rs.box[r];
-    const uint32_t cl = clip_box(bx, fj0, fi0, FH);
+    const uint32_t cl = clip_box(bx, ij0, ii0, FH);
     if (part)
-      bwd_item<FH, CUT, true>(Rs.a[r], Rs.b[r], Rs.c[r], bx, cl, Rs.rid[r], pix, fj0, fi0,
+      bwd_item<FH, CUT, true>(Rs.a[r], Rs.b[r], Rs.c[r], bx, cl, Rs.rid[r], pix, ij0, ii0,
                               v.rec_grad, y0, rows);
     else
-      bwd_item<FH, CUT>(Rs.a[r], Rs.b[r], Rs.c[r], bx, cl, Rs.rid[r], pix, fj0, fi0, v.rec_grad);
+      bwd_item<FH, CUT>(Rs.a[r], Rs.b[r], Rs.c[r], bx, cl, Rs.rid[r], pix, ij0, ii0,
+                        v.rec_grad);
   };
   // one round: the oldest min(queued, 32) items; fewer than 17 are split by
   // rows over 2 or 4 lanes each (each lane adds its rows' sums)
@@ -607,6 +618,7 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
       ++krel;
     }
   };
+  bool failed = false;
   for (uint32_t k = 0;; ++k) {
     const int s = (int)(k % NS);
     if (k >= (uint32_t)NS && krel + NS <= k) {
@@ -616,14 +628,21 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
     }
     if (!mbar_wait(&S.bars.full[s], (k / NS) & 1u)) {
       dev_fail(v.hdr, UG_ERR_TIMEOUT, 2);
+      failed = true;
       break;
     }
     const RecStage<TILE, true, BATCH>& R = S.st[s];
     const StageHdr h = R.h;
     if (h.tile < 0) break;
     if (h.flags & kFirst) {
+      // the current tile's items end here; the new tile takes the other
+      // parity, whose factors the items of the tile before are still using
+      if (tpar) qmark1 = qtail;
+      else qmark0 = qtail;
+      tpar ^= 1u;
+      while (qhead < (tpar ? qmark1 : qmark0)) round();
       // per-pixel factors of this warp's footprint: r = G / alpha and -r C
-      // (0 off the plane); the previous tile's items are all processed
+      // (0 off the plane)
       footprint_origin(warp, T::FX, FH, h.tx, h.ty, TILE, fj0, fi0);
       // layout: entry 8 rp + c holds rows 2 rp and 2 rp + 1 of column c
       for (int q = lane; q < FH * 4; q += 32) {
@@ -637,7 +656,7 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
           v4[hh] = rv;
           v4[2 + hh] = -rv * R.raw[2][pp];
         }
-        S.pix[warp][q] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+        S.pix[warp][tpar][q] = make_float4(v4[0], v4[1], v4[2], v4[3]);
       }
       __syncwarp();
     }
@@ -656,7 +675,7 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
     for (int q = 0; q < BATCH / 32; ++q) {
       const uint32_t bl = __ballot_sync(0xffffffffu, m[q] & 1u);
       if (m[q] & 1u)
-        Q[(qtail + __popc(bl & lt)) % QL] = (uint16_t)((s << 8) | (32 * q + lane));
+        Q[(qtail + __popc(bl & lt)) % QL] = (uint16_t)((tpar << 10) | (s << 8) | (32 * q + lane));
       qtail += __popc(bl);
     }
     evaluated += qtail - q0;
@@ -665,11 +684,11 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
     else if (s == 2) qe2 = qtail;
     else qe3 = qtail;
     __syncwarp();
-    // full rounds; at the end of the tile also the rest
-    const bool tile_end = h.flags & kLast;
-    while (qtail - qhead >= 32u || (tile_end && qtail > qhead)) round();
+    while (qtail - qhead >= 32u) round();  // full rounds
     release(k);
   }
+  if (!failed)
+    while (qtail > qhead) round();  // the queue's last items
   if (lane == 0 && evaluated)
     atomicAdd(reinterpret_cast<unsigned long long*>(&v.hdr->st.evaluated_pairs_bwd),
               evaluated * (unsigned long long)(8 * FH));

@@ -1,14 +1,17 @@
 """Host model of the backward rasterizer's record pipeline (no GPU): one
 producer fills a ring of NS stages, each consumer warp queues the indices of
-its live records, processes them 32 at a time, and releases a stage once all of
-the stage's items are processed, at the latest before the wait that reuses the
-stage's slot. The model follows the kernel's rules step by step on random
-per-stage item counts (dense, sparse and empty footprints, tiles of one or
-many stages) and checks what the kernel relies on: every warp always makes
-progress (no wait for a slot that a consumer still holds), every stage is
-released exactly once by every consumer, every item is processed exactly once
-and only while its stage is held, and the queue never holds more than a
-round's remainder plus one stage."""
+its live records, processes them 32 at a time (carrying items across tiles),
+and releases a stage once all of the stage's items are processed, at the latest
+before the wait that reuses the stage's slot; at a tile's first stage it first
+processes the items of the tile before the previous one (the pixel factors
+are kept for two tiles), and at the end the queue's last items. The model
+follows the kernel's rules step by step on random per-stage item counts
+(dense, sparse and empty footprints, tiles of one or many stages) and checks
+what the kernel relies on: every warp always makes progress (no wait for a slot
+that a consumer still holds), every stage is released exactly once by every
+consumer, every item is processed exactly once, only while its stage is held
+and while its tile's pixel factors are kept, and the queue never holds more
+than a round's remainder plus one stage."""
 import numpy as np
 import pytest
 
@@ -17,13 +20,13 @@ BATCHES = (64, 128, 256)  # records per stage of the compiled backward variants
 
 def _simulate(ns, tiles, warps, rng, BATCH=128):
     """tiles: list of per-tile stage counts; returns the largest queue fill."""
-    # the stream of stages: (tile end?, per-warp live item counts)
+    # the stream of stages: (tile index, first stage of its tile?, per-warp live item counts)
     stages = []
-    for n_st in tiles:
+    for t, n_st in enumerate(tiles):
         for j in range(n_st):
             cnt = [int(rng.choice([0, rng.integers(0, 8), rng.integers(0, BATCH + 1)]))
                    for _ in range(warps)]
-            stages.append((j == n_st - 1, cnt))
+            stages.append((t, j == 0, cnt))
     total = len(stages)
     released = [[False] * total for _ in range(warps)]  # by warp, by stage
     filled = [False] * total
@@ -39,7 +42,8 @@ def _simulate(ns, tiles, warps, rng, BATCH=128):
 
     state = []
     for w in range(warps):
-        state.append(dict(k=0, qhead=0, qtail=0, qend={}, krel=0, items=[], done=False))
+        state.append(dict(k=0, qhead=0, qtail=0, qend={}, krel=0, items=[], done=False,
+                          tile=-1, qmark={0: 0, 1: 0}))
     max_fill = 0
     processed = [set() for _ in range(warps)]
 
@@ -50,6 +54,7 @@ def _simulate(ns, tiles, warps, rng, BATCH=128):
             stage, item = st["items"][i]
             assert not released[w][stage], "item read after its stage was released"
             assert (stage, item) not in processed[w]
+            assert st["tile"] - stages[stage][0] <= 1, "item read after its factors were replaced"
             processed[w].add((stage, item))
         st["qhead"] += n
 
@@ -70,6 +75,9 @@ def _simulate(ns, tiles, warps, rng, BATCH=128):
                 continue
             k = st["k"]
             if k == total:
+                while st["qtail"] > st["qhead"]:  # the queue's last items
+                    round_(w)
+                release(w, total - 1)  # (the kernel leaves these unreleased: the producer is done)
                 st["done"] = True
                 progressed = True
                 continue
@@ -81,13 +89,19 @@ def _simulate(ns, tiles, warps, rng, BATCH=128):
                 progressed = True
             if not filled[k]:
                 continue  # waits for the producer
-            tile_end, cnt = stages[k]
+            tile, first, cnt = stages[k]
+            if first:
+                if st["tile"] >= 0:
+                    st["qmark"][st["tile"] & 1] = st["qtail"]
+                while st["qhead"] < st["qmark"][tile & 1]:  # the tile before the previous one
+                    round_(w)
+                st["tile"] = tile  # its pixel factors replace those of tile - 2
             for i in range(cnt[w]):
                 st["items"].append((k, i))
             st["qtail"] += cnt[w]
             st["qend"][k] = st["qtail"]
             max_fill = max(max_fill, st["qtail"] - st["qhead"])
-            while st["qtail"] - st["qhead"] >= 32 or (tile_end and st["qtail"] > st["qhead"]):
+            while st["qtail"] - st["qhead"] >= 32:
                 round_(w)
             release(w, k)
             st["k"] = k + 1
@@ -98,7 +112,7 @@ def _simulate(ns, tiles, warps, rng, BATCH=128):
         assert steps < 100000
     for w in range(warps):
         assert all(released[w]), "a stage was never released"
-        assert len(processed[w]) == sum(c[w] for _, c in stages)
+        assert len(processed[w]) == sum(c[w] for _, _, c in stages)
     return max_fill
 
 
