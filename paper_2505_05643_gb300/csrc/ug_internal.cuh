@@ -158,7 +158,7 @@ inline WsView make_view(const ug_plan* plan, void* ws) {
 }
 
 // Number of blocks of the count scan and of a sort pass.
-inline int64_t scan_blocks(int64_t entries) { return (entries + kScanItems - 1) / kScanItems; }
+__host__ __device__ inline int64_t scan_blocks(int64_t entries) { return (entries + kScanItems - 1) / kScanItems; }
 inline int64_t sort_blocks(int64_t capacity) { return (capacity + kSortTile - 1) / kSortTile; }
 
 // ------------------------------------------------------------------ device helpers

@@ -43,7 +43,7 @@ int device_sms() {
 // ------------------------------------------------------------------ planes
 __global__ void __launch_bounds__(256)
     k_setup_planes(const ug_plane* planes, int P, int tile, int total_tiles,
-                   int64_t total_px, WsView v) {
+                   int64_t total_px, int64_t cand_blocks, int64_t rec_blocks, WsView v) {
   __shared__ int s_run;
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -65,6 +65,9 @@ __global__ void __launch_bounds__(256)
     h->origin_reach = 0.f;
     s_run = 0;
   }
+  // the count scans' block partials, added to by the cull and the live-tile pass
+  for (int64_t k = tid; k < 2 * cand_blocks; k += blockDim.x) v.scan_part[k] = 0;
+  for (int64_t k = tid; k < rec_blocks; k += blockDim.x) v.slot_part[k] = 0;
   __syncthreads();
   for (int base = 0; base < P; base += 256) {
     const int p = base + tid;
@@ -310,8 +313,9 @@ __global__ void __launch_bounds__(256)
     const float Bm = __fadd_ru(__fmul_ru(__fmul_ru(24.f * eps, __fadd_ru(mu1, o1)), 1.001f), 1e-30f);
     T = __fadd_ru(__fsqrt_ru(thr1), Bm);
   }
+  uint32_t fl = 0;  // the chunk's Gaussians on the extended branch
   if (live_warp) {
-    const uint32_t fl = __ballot_sync(0xffffffffu, L.use64);
+    fl = __ballot_sync(0xffffffffu, L.use64);
     if (lane == 0) v.gflag[chunk] = fl;
   }
   const float mx = W.mu[0][lane], my = W.mu[1][lane], mz = W.mu[2][lane];
@@ -374,6 +378,25 @@ __global__ void __launch_bounds__(256)
       }
     }
     for (int q = lane; q < np; q += 32) v.mask[chunk * P + p0 + q] = W.bits[q];
+    // the candidate scan's block partials (records, FP64 records): this
+    // group's entries are consecutive, so they fall into at most two scan
+    // blocks; the counts (at most 64 x 32 each) travel as 16-bit halves
+    {
+      const int64_t e0 = chunk * P + p0, b0 = e0 / kScanItems;
+      const int split = (int)min((int64_t)np, (b0 + 1) * kScanItems - e0);
+      uint32_t c_all = 0, c_64 = 0;
+      for (int q = lane; q < np; q += 32) {
+        const uint32_t m = W.bits[q], sh = q < split ? 0u : 16u;
+        c_all += (uint32_t)__popc(m) << sh;
+        c_64 += (uint32_t)__popc(m & fl) << sh;
+      }
+      c_all = warp_sum(c_all);
+      c_64 = warp_sum(c_64);
+      if (lane < 4) {
+        const uint32_t x = ((lane & 1) ? c_64 : c_all) >> (lane < 2 ? 0 : 16) & 0xffffu;
+        if (x) atomicAdd(&v.scan_part[(b0 + (lane >> 1)) * 2 + (lane & 1)], (unsigned long long)x);
+      }
+    }
     __syncwarp();
   }
 }
@@ -672,6 +695,9 @@ __global__ void __launch_bounds__(256) k_live(int ts, int cut, WsView v) {
       v.inst_off[slot] = cnt;
       live_mask[slot] = mask;
     }
+    // the record scan's block partial (the 32 slots lie in one scan block)
+    const uint32_t wsum = warp_sum(cnt);
+    if (lane == 0 && wsum) atomicAdd(&v.slot_part[w0 / kScanItems], (unsigned long long)wsum);
     __syncwarp();
   }
 }
@@ -805,7 +831,8 @@ static int tile_shift(int tile) { return tile == 8 ? 3 : 4; }
 cudaError_t launch_setup_planes(const ug_plan* plan, const ug_plane* d_planes, WsView v,
                                 cudaStream_t s) {
   k_setup_planes<<<1, 256, 0, s>>>(d_planes, plan->num_planes, plan->cfg.tile, plan->total_tiles,
-                                    plan->total_pixels, v);
+                                    plan->total_pixels, scan_blocks(plan->chunks * plan->num_planes),
+                                    scan_blocks(plan->record_capacity), v);
   return cudaGetLastError();
 }
 
@@ -822,6 +849,8 @@ static void launch_pre_cov(const ug_plan* plan, const ug_gaussians* g, WsView v,
   const int ts = tile_shift(plan->cfg.tile);
   const ug_config& c = plan->cfg;
   const int64_t wblocks = (chunks * 32 + 255) / 256;
+  // the cull adds the candidate scan's block partials, the down-sweep scans
+  // them (no cull without Gaussians: the header's counts stay zero)
   if (chunks > 0)
     k_cull<COV><<<(unsigned)wblocks, 256, 0, s>>>(*g, plan->n, P, c.chi2, c.beta, c.fp64_ratio,
                                                   c.fp32_reach, chunks, v);
@@ -830,25 +859,20 @@ static void launch_pre_cov(const ug_plan* plan, const ug_gaussians* g, WsView v,
   CandLoad ld{v.mask, v.gflag, P};
   CandStore st{v.slot_base, v.f64_base};
   if (nblk > 0)
-    k_scan_partial<2, CandLoad><<<(unsigned)nblk, kScanThreads, 0, s>>>(ld, entries, v.scan_part,
-                                                                        v.hdr);
-  k_scan_top<2><<<1, 1024, 0, s>>>(v.scan_part, nblk, v.hdr, 1, plan->record_capacity, 0);
-  if (nblk > 0)
-    k_scan_down<2, CandLoad, CandStore><<<(unsigned)nblk, kScanThreads, 0, s>>>(
-        ld, st, entries, v.scan_part, v.hdr);
+    k_scan_down<2, CandLoad, CandStore, true><<<(unsigned)nblk, kScanThreads, 0, s>>>(
+        ld, st, entries, v.scan_part, v.hdr, nblk, 1, plan->record_capacity);
   if (chunks > 0) k_list<<<(unsigned)wblocks, 256, 0, s>>>(P, chunks, v);
   const unsigned lg = list_grid(plan->record_capacity);
   k_records<float, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.cutoff, c.chi2, c.beta, v, 0);
   k_records<dd, COV><<<lg, 256, 0, s>>>(*g, plan->n, ts, c.cutoff, c.chi2, c.beta, v, 1);
+  // the live-tile pass adds the record scan's block partials, the down-sweep
+  // scans them
   k_live<<<lg, 256, 0, s>>>(ts, c.cutoff, v);
   const int64_t rblk = scan_blocks(plan->record_capacity);
   SlotLoad sl{v.inst_off, v.hdr};
   SlotStore ss{v.inst_off, v.hdr};
-  k_scan_partial<1, SlotLoad><<<(unsigned)rblk, kScanThreads, 0, s>>>(
-      sl, plan->record_capacity, v.slot_part, v.hdr);
-  k_scan_top<1><<<1, 1024, 0, s>>>(v.slot_part, rblk, v.hdr, 2, plan->instance_capacity, 0);
-  k_scan_down<1, SlotLoad, SlotStore><<<(unsigned)rblk, kScanThreads, 0, s>>>(
-      sl, ss, plan->record_capacity, v.slot_part, v.hdr);
+  k_scan_down<1, SlotLoad, SlotStore, true><<<(unsigned)rblk, kScanThreads, 0, s>>>(
+      sl, ss, plan->record_capacity, v.slot_part, v.hdr, rblk, 2, plan->instance_capacity);
   k_emit<<<lg, 256, 0, s>>>(ts, c.cutoff, (uint32_t)plan->instance_capacity, v);
   k_finish_pre<<<1, 32, 0, s>>>(v);
 }

@@ -91,11 +91,11 @@ class TrainStep:
 
     def kernels_per_step(self) -> int:
         """Kernels of this library launched by one step (memsets excluded)."""
-        # preprocess: planes, cull, 3 scan, list, 2 records, live tiles, 3 scan, emit, finish
-        pre = 14
+        # preprocess: planes, cull, scan, list, 2 records, live tiles, scan, emit, finish
+        pre = 10
         sort = 5 * int(self.r.plan.sort_passes) + 1  # per pass: hist, 3 scan, scatter; ranges
-        # render 1, mse 2, backward: zero, raster, 2 chain, gather = 5, adam 2
-        return pre + sort + 1 + 2 + 5 + 2
+        # render 1, mse 2, backward: zero, raster, chain, gather = 4, adam 2
+        return pre + sort + 1 + 2 + 4 + 2
 
     def ensure_capacity(self):
         """Run one checked forward so the workspace holds this step's records."""
