@@ -422,34 +422,53 @@ struct CandStore {
 };
 
 // ------------------------------------------------------------------ 3. list
+// Transpose of a 32 x 32 bit matrix held one row per lane (bit c of lane r's
+// word is element (r, c)): afterwards lane c holds column c. Five butterfly
+// steps swap the off-diagonal blocks of ever smaller block pairs.
+__device__ __forceinline__ uint32_t warp_bit_transpose(uint32_t x, int lane) {
+  const uint32_t m[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int j = 16 >> k;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? (x & ~m[k]) | ((y >> j) & m[k]) : (x & m[k]) | ((y & m[k]) << j);
+  }
+  return x;
+}
+
+// One warp per chunk of 32 Gaussians, 32 planes at a time: the lanes load the
+// planes' candidate masks and bases (one plane per lane, coalesced), the
+// masks are transposed so that every lane holds its own Gaussian's planes, and
+// each lane writes the list entries of its candidates (its record slot and its
+// place in the FP32 or the FP64 part) with the planes' data from shared memory.
 __global__ void __launch_bounds__(256) k_list(int P, int64_t chunks, WsView v) {
+  __shared__ uint32_t s_m[8][32], s_b[8][32], s_f[8][32];
   if (dev_failed(v.hdr)) return;
   const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (chunk >= chunks) return;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const uint32_t fl = v.gflag[chunk];
   const uint32_t n32 = v.hdr->slots - v.hdr->slots64;
   const uint32_t lt = lanemask_lt();
+  const bool ext = (fl >> lane) & 1u;
   const uint32_t g = (uint32_t)(chunk * kChunk + lane);
-  // the chunk's candidate masks and bases, 32 planes at a time, one per lane
-  // (coalesced), then handed round the warp
   for (int p0 = 0; p0 < P; p0 += 32) {
     const int pl = p0 + lane;
     const int64_t e = chunk * P + pl;
     const uint32_t mq = pl < P ? __ldg(v.mask + e) : 0u;
-    const uint32_t bq = pl < P ? __ldg(v.slot_base + e) : 0u;
-    const uint32_t fq = pl < P ? __ldg(v.f64_base + e) : 0u;
-    const int np = min(32, P - p0);
-    for (int q = 0; q < np; ++q) {
-      const uint32_t mask = __shfl_sync(0xffffffffu, mq, q);
-      if (mask == 0u) continue;  // the same for the whole warp
-      const uint32_t base = __shfl_sync(0xffffffffu, bq, q);
-      const uint32_t b64 = __shfl_sync(0xffffffffu, fq, q);
-      if (!((mask >> lane) & 1u)) continue;
+    __syncwarp();  // the previous group's planes are read
+    s_m[wl][lane] = mq;
+    s_b[wl][lane] = pl < P ? __ldg(v.slot_base + e) : 0u;
+    s_f[wl][lane] = pl < P ? __ldg(v.f64_base + e) : 0u;
+    uint32_t mine = warp_bit_transpose(mq, lane);  // bit q: candidate on plane p0 + q
+    __syncwarp();
+    while (mine) {
+      const int q = __ffs(mine) - 1;
+      mine &= mine - 1u;
+      const uint32_t mask = s_m[wl][q], base = s_b[wl][q], b64 = s_f[wl][q];
       const uint32_t slot = base + __popc(mask & lt);
-      uint32_t idx;
-      if ((fl >> lane) & 1u) idx = n32 + b64 + __popc(mask & fl & lt);
-      else idx = (base - b64) + __popc(mask & ~fl & lt);
+      const uint32_t idx = ext ? n32 + b64 + __popc(mask & fl & lt)
+                               : (base - b64) + __popc(mask & ~fl & lt);
       v.list[idx] = make_uint4(g, (uint32_t)(p0 + q), slot, 0u);
     }
   }
@@ -1033,19 +1052,22 @@ __global__ void __launch_bounds__(256)
 // order (deterministic), written to the gradient rows. A chunk's records of a
 // group of 32 planes occupy consecutive slots (the scan runs in (chunk, plane)
 // order), so the warp reads them with full-width coalesced loads into a
-// shared-memory window, kGatherWin records at a time, and every lane then adds
-// its own Gaussian's records from the window, planes in ascending order.
+// shared-memory window, kGatherWin records at a time. Every lane holds its own
+// Gaussian's planes (the group's candidate masks transposed) and adds its
+// records from each window, planes in ascending order: its slots ascend with
+// the plane, so it stops at the first record beyond the window.
 constexpr int kGatherWin = 96;
 
 template <int COV>
 __global__ void __launch_bounds__(256)
     k_gather(int64_t n, int P, int64_t chunks, WsView v, ug_gaussian_grads out) {
   __shared__ float4 win[256 / 32][kGatherWin * 3];
+  __shared__ uint32_t s_m[256 / 32][32], s_b[256 / 32][32];
   if (dev_failed(v.hdr)) return;
   const int64_t chunk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (chunk >= chunks) return;
-  const int lane = threadIdx.x & 31;
-  float4* W = win[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  float4* W = win[wl];
   const int64_t i = chunk * kChunk + lane;
   const uint32_t lt = lanemask_lt();
   float acc[12];
@@ -1059,17 +1081,20 @@ __global__ void __launch_bounds__(256)
     // this plane group's slots: [first, last)
     const uint32_t first = __shfl_sync(0xffffffffu, bq, 0);
     const uint32_t last = __shfl_sync(0xffffffffu, bq + __popc(mq), np - 1);
+    __syncwarp();  // the previous group's planes are read
+    s_m[wl][lane] = mq;
+    s_b[wl][lane] = bq;
+    uint32_t mine = warp_bit_transpose(mq, lane);  // bit q: a record on plane p0 + q
     for (uint32_t w0 = first; w0 < last; w0 += kGatherWin) {
       const int cnt = (int)min((uint32_t)kGatherWin, last - w0);
       __syncwarp();  // the previous window is consumed
       for (int k = lane; k < cnt * 3; k += 32) W[k] = __ldg(pg + (size_t)w0 * 3 + k);
       __syncwarp();
-      for (int q = 0; q < np; ++q) {
-        const uint32_t mask = __shfl_sync(0xffffffffu, mq, q);
-        const uint32_t base = __shfl_sync(0xffffffffu, bq, q);
-        if (!((mask >> lane) & 1u)) continue;
-        const uint32_t r = base + __popc(mask & lt) - w0;  // wraps when below the window
-        if (r >= (uint32_t)cnt) continue;
+      while (mine) {
+        const int q = __ffs(mine) - 1;
+        const uint32_t r = s_b[wl][q] + __popc(s_m[wl][q] & lt) - w0;
+        if (r >= (uint32_t)cnt) break;  // this record and the later ones: a later window
+        mine &= mine - 1u;
         const float4 x0 = W[3 * r], x1 = W[3 * r + 1], x2 = W[3 * r + 2];
         acc[0] += x0.x; acc[1] += x0.y; acc[2] += x0.z; acc[3] += x0.w;
         acc[4] += x1.x; acc[5] += x1.y; acc[6] += x1.z; acc[7] += x1.w;

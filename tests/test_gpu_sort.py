@@ -184,6 +184,51 @@ def test_tile_lists_exact(tile):
         assert abs(len(exp) - len(live_ids)) <= sum(_edge_ambiguous(geo, pl, p, gg) for p, gg in exp)
 
 
+def test_tile_lists_exact_many_scan_blocks():
+    """80 planes (2,048-entry scan blocks then end inside a chunk's run of
+    planes) and 6,000 Gaussians: the candidate scan spans 8 blocks and the
+    record scan several, their partials added by the cull and the live-tile
+    pass; the records are the oracle's visible pairs in (chunk, plane,
+    Gaussian) order and the tile lists are exact."""
+    rng = np.random.default_rng(25)
+    n = 6000
+    g = synth.gaussians_scale_rot(rng, n, 0.02, 0.1)
+    pl = synth.planes_random(rng, [(24, 24), (20, 31)] * 40)
+    P = len(pl["size"])
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, tile=16)
+    r, _, _, _ = gpu_render(g, pl, cfg)
+    assert ((n + 31) // 32) * P > 7 * 2048
+    dv, live, kept, dropped = _check_tile_lists(r, pl, 16)
+    assert dv["status"]["records"] > 4 * 2048, dv["status"]["records"]
+    geo = oracle.geometry(g, pl, oracle_config(cfg))
+    exp = _expected_records(geo, n, P)
+    E = [(p, tuple(int(x) for x in geo["box"][p, gg])) for p, gg in exp]
+    boxes = dv["boxes"].astype(np.int64)
+    G = [(int(dv["rec_plane"][rid]), (int(boxes[rid, 0] & 0xFFFF), int(boxes[rid, 0] >> 16),
+                                      int(boxes[rid, 1] & 0xFFFF), int(boxes[rid, 1] >> 16)))
+         for rid in np.flatnonzero(live)]
+    # pairs whose decision may go either way: a box edge within rounding of a
+    # pixel boundary, or the plane test within rounding (visible or not)
+    amb = sum(_edge_ambiguous(geo, pl, p, gg) for p, gg in exp)
+    amb += int((geo["amb_plane"] & ~geo["visible"]).sum())
+    # walk both sequences; every difference is one ambiguous pair (a box that
+    # differs, a record only one side has)
+    i = j = diff = 0
+    while i < len(E) and j < len(G):
+        if E[i] == G[j]:
+            i, j = i + 1, j + 1
+        elif E[i][0] == G[j][0] and E[i + 1:i + 3] == G[j + 1:j + 3]:
+            i, j, diff = i + 1, j + 1, diff + 1
+        elif E[i + 1:i + 2] == G[j:j + 1]:
+            i, diff = i + 1, diff + 1
+        elif E[i:i + 1] == G[j + 1:j + 2]:
+            j, diff = j + 1, diff + 1
+        else:
+            raise AssertionError(f"records differ at {i} / {j}: {E[i:i + 3]} vs {G[j:j + 3]}")
+    diff += (len(E) - i) + (len(G) - j)
+    assert diff <= amb, (diff, amb)
+
+
 def test_tile_lists_thin_gaussians_drop_zero_tiles():
     """Needle- and disc-like Gaussians: their boxes cover many tiles that hold
     only exact zeros; binning drops those (and only those)."""
@@ -219,10 +264,12 @@ def _grab_u32(r, ptr, count):
 
 
 def test_sort_many_tiles_matches_stable_argsort():
-    """The one-sweep passes at a size that spans hundreds of sort tiles (their
-    digit offsets come from the look-back over every earlier tile): the sorted
-    (key, record) pairs are exactly NumPy's stable sort of the binning's output
-    by tile key, and the ranges delimit the tiles."""
+    """The radix passes at a size that spans hundreds of sort tiles (each
+    tile's digit offsets come from the scan over every earlier tile), and the
+    count scans at hundreds of scan blocks (their partials added atomically by
+    the cull and the live-tile pass): the sorted (key, record) pairs are exactly
+    NumPy's stable sort of the binning's output by tile key, and the ranges
+    delimit the tiles."""
     g, pl = synth.workload_aniso_1m(n=200_000)
     g = synth.scale_rot_to_tri(g, 1e-4)
     cfg = R.make_config(cov_param=B.UG_COV_TRI, tile=16)
@@ -239,8 +286,9 @@ def test_sort_many_tiles_matches_stable_argsort():
     n = st["instances"]
     assert n > 300 * 4096, n
     keys0, vals0 = _grab_u32(r, kp, n), _grab_u32(r, vp, n)
-    # the binning's output (its groups' ranges come from the look-back): record
-    # slots ascending, each record's tiles ascending, every tile in the box
+    # the binning's output (each record's first instance from the record
+    # scan): record slots ascending, each record's tiles ascending, every tile
+    # in the box
     tk0 = (keys0 & np.uint32(0x00FFFFFF)).astype(np.int64)
     v0 = vals0.astype(np.int64)
     assert np.all(np.diff(v0) >= 0)
