@@ -694,8 +694,14 @@ __global__ void __launch_bounds__(BwdShape<TILE, FH>::NT, MINB)
               evaluated * (unsigned long long)(8 * FH));
 }
 
+// Zero the per-record accumulators of the backward rasterizer, and (block 0)
+// its tile counter and evaluated-pair count.
 __global__ void k_zero_rec_grad(WsView v, int64_t cap) {
   if (dev_failed(v.hdr)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    v.hdr->tile_counter[1] = 0;
+    v.hdr->st.evaluated_pairs_bwd = 0;
+  }
   const int64_t nrec = min((int64_t)v.hdr->slots, cap);
   float4* g = reinterpret_cast<float4*>(v.rec_grad);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrec * 2;
@@ -825,9 +831,6 @@ cudaError_t launch_render(const ug_plan* plan, WsView v, float* image, float* al
 cudaError_t launch_render_backward_raster(const ug_plan* plan, WsView v, const float* image,
                                           const float* alpha, const float* grad_image,
                                           cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(&v.hdr->tile_counter[1], 0, sizeof(uint32_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&v.hdr->st.evaluated_pairs_bwd, 0, sizeof(int64_t), s);
-  if (e != cudaSuccess) return e;
   k_zero_rec_grad<<<device_sms() * 4, 256, 0, s>>>(v, plan->record_capacity);
   const uint32_t* vals = v.vals[plan->sort_passes & 1];
   if (plan->cfg.tile == 16)

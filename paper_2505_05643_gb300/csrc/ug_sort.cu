@@ -112,14 +112,48 @@ __global__ void __launch_bounds__(kSortThreads, 3)
   }
 }
 
-__global__ void k_tile_ranges(const uint32_t* __restrict__ keys, WsView v) {
+// A warp takes 32 x kRangeItems consecutive sorted instances (coalesced
+// loads, all issued before the comparisons); each key's neighbours come from
+// the next and previous lane, or from the warp's neighbouring items. A tile's
+// range starts where the key differs from the one before and ends where it
+// differs from the one after.
+constexpr int kRangeItems = 8;
+
+__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys, WsView v) {
   if (dev_failed(v.hdr)) return;
   const int64_t n = v.hdr->st.instances;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = keys[i] & kKeyTileMask;
-    if (i == 0 || (keys[i - 1] & kKeyTileMask) != k) v.ranges[k].x = (uint32_t)i;
-    if (i == n - 1 || (keys[i + 1] & kKeyTileMask) != k) v.ranges[k].y = (uint32_t)(i + 1);
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  constexpr int64_t span = 32 * kRangeItems;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * span < n;
+       w += nwarps) {
+    const int64_t base = w * span;
+    uint32_t k[kRangeItems];
+#pragma unroll
+    for (int u = 0; u < kRangeItems; ++u) {
+      const int64_t i = base + u * 32 + lane;
+      k[u] = i < n ? __ldg(keys + i) & kKeyTileMask : ~0u;  // ~0u: no tile
+    }
+    const uint32_t before = base > 0 ? __ldg(keys + base - 1) & kKeyTileMask : ~0u;
+    const uint32_t after = base + span < n ? __ldg(keys + base + span) & kKeyTileMask : ~0u;
+#pragma unroll
+    for (int u = 0; u < kRangeItems; ++u) {
+      // the keys just before lane 0 and just after lane 31 of this item
+      const uint32_t edge_prev =
+          u > 0 ? __shfl_sync(0xffffffffu, k[u > 0 ? u - 1 : 0], 31) : before;
+      const uint32_t edge_next =
+          u + 1 < kRangeItems ? __shfl_sync(0xffffffffu, k[u + 1 < kRangeItems ? u + 1 : u], 0)
+                              : after;
+      uint32_t kp = __shfl_up_sync(0xffffffffu, k[u], 1);
+      uint32_t kn = __shfl_down_sync(0xffffffffu, k[u], 1);
+      if (lane == 0) kp = edge_prev;
+      if (lane == 31) kn = edge_next;
+      const int64_t i = base + u * 32 + lane;
+      if (i < n) {
+        if (kp != k[u]) v.ranges[k[u]].x = (uint32_t)i;
+        if (kn != k[u]) v.ranges[k[u]].y = (uint32_t)(i + 1);
+      }
+    }
   }
 }
 
@@ -150,10 +184,7 @@ cudaError_t launch_bin_sort(const ug_plan* plan, WsView v, cudaStream_t s) {
   }
   cudaError_t e = cudaMemsetAsync(v.ranges, 0, sizeof(uint2) * (size_t)plan->total_tiles, s);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_tile_ranges<<<sms * 8, 256, 0, s>>>(v.keys[plan->sort_passes & 1], v);
+  k_tile_ranges<<<(unsigned)(device_sms() * 8), 256, 0, s>>>(v.keys[plan->sort_passes & 1], v);
   return cudaGetLastError();
 }
 
