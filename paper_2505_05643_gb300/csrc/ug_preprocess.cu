@@ -671,12 +671,11 @@ __global__ void __launch_bounds__(256) k_live(int ts, int cut, WsView v) {
        w0 += warps * 32u) {
     const uint32_t slot = w0 + lane;
     SlotTiles q = slot_tiles(make_uint2(1u, 1u), ts);
-    if (slot < slots) {
-      q = slot_tiles(v.rec_box[slot], ts);
-      if (q.nt) {
-        s_a[wl][lane] = v.rec_a[slot];
-        s_b[wl][lane] = v.rec_b[slot];
-      }
+    if (slot < slots) {  // the render data loaded with the box (read only for box tiles)
+      const uint2 bx = v.rec_box[slot];
+      s_a[wl][lane] = v.rec_a[slot];
+      s_b[wl][lane] = v.rec_b[slot];
+      q = slot_tiles(bx, ts);
     }
     s_t[wl][lane] = make_uint4(q.bx.x, q.bx.y, q.nx | (q.tx0 << 16), q.ty0);
     uint32_t incl = q.nt;
@@ -762,17 +761,22 @@ __global__ void __launch_bounds__(256, 4) k_emit(int ts, int cut, uint32_t inst_
     SlotTiles q = slot_tiles(make_uint2(1u, 1u), ts);
     unsigned long long mask = 0;
     if (slot < slots) {
+      // every input of the slot loaded at once (used only when it has instances)
       pre = v.inst_off[slot];
       const uint32_t nxt = slot + 1 < slots ? v.inst_off[slot + 1] : n_inst;
+      const uint2 bx = v.rec_box[slot];
+      const uint32_t plane = v.rec_plane[slot];
+      const unsigned long long lm = live_mask[slot];
+      const float4 ra = v.rec_a[slot], rb = v.rec_b[slot];
       cnt = nxt - pre;
       if (cnt) {
-        q = slot_tiles(v.rec_box[slot], ts);
-        const PlaneDev& pl = v.planes[v.rec_plane[slot]];
+        q = slot_tiles(bx, ts);
+        const PlaneDev& pl = v.planes[plane];
         tiles_x = (uint32_t)pl.tiles_x;
         key0 = (uint32_t)pl.tile_off + q.ty0 * tiles_x + q.tx0;
-        mask = live_mask[slot];
-        s_a[wl][lane] = v.rec_a[slot];
-        s_b[wl][lane] = v.rec_b[slot];
+        mask = lm;
+        s_a[wl][lane] = ra;
+        s_b[wl][lane] = rb;
         s_bx[wl][lane] = q.bx;
       }
     }
@@ -1008,32 +1012,38 @@ __global__ void __launch_bounds__(256)
     k_chain(ug_gaussians g, int64_t n, float beta, WsView v) {
   if (dev_failed(v.hdr)) return;
   const uint32_t slots = v.hdr->slots;
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < slots;
-       k += gridDim.x * blockDim.x) {
-    const uint4 e = v.list[k];
+  // the next entry of the list is read one iteration ahead, and every input
+  // of a record is loaded before its box is tested (one round trip)
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  uint4 e_next = k < slots ? v.list[k] : make_uint4(0u, 0u, 0u, 0u);
+  for (; k < slots; k += stride) {
+    const uint4 e = e_next;
+    if (k + stride < slots) e_next = v.list[k + stride];
     const uint32_t slot = e.z;
+    const uint2 box = v.rec_box[slot];
+    const float4 a0 = *reinterpret_cast<const float4*>(v.rec_grad + (size_t)slot * 8);
+    const float4 a1 = *reinterpret_cast<const float4*>(v.rec_grad + (size_t)slot * 8 + 4);
+    GaussParams prm;
+    load_params(g, n, e.x, COV, prm);
+    float ch[kChainFloats];
+    const float4* c4 = reinterpret_cast<const float4*>(v.rec_chain + (size_t)slot * kChainFloats);
+#pragma unroll
+    for (int q = 0; q < kChainFloats / 4; ++q) {
+      const float4 t = c4[q];
+      ch[4 * q] = t.x;
+      ch[4 * q + 1] = t.y;
+      ch[4 * q + 2] = t.z;
+      ch[4 * q + 3] = t.w;
+    }
     float out[12];
 #pragma unroll
     for (int q = 0; q < 12; ++q) out[q] = 0.f;
-    if (!box_empty(v.rec_box[slot])) {
-      const float4 a0 = *reinterpret_cast<const float4*>(v.rec_grad + (size_t)slot * 8);
-      const float4 a1 = *reinterpret_cast<const float4*>(v.rec_grad + (size_t)slot * 8 + 4);
+    if (!box_empty(box)) {
       const float acc[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const PlaneDev& pl = v.planes[e.y];
-      GaussParams prm;
-      load_params(g, n, e.x, COV, prm);
       Factor<float> f;
       make_factor<float, COV>(prm, beta, f);
-      float ch[kChainFloats];
-      const float4* c4 = reinterpret_cast<const float4*>(v.rec_chain + (size_t)slot * kChainFloats);
-#pragma unroll
-      for (int q = 0; q < kChainFloats / 4; ++q) {
-        const float4 t = c4[q];
-        ch[4 * q] = t.x;
-        ch[4 * q + 1] = t.y;
-        ch[4 * q + 2] = t.z;
-        ch[4 * q + 3] = t.w;
-      }
       float F[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) F[q] = f.F[q / 3][q % 3];
