@@ -446,9 +446,14 @@ constexpr float kFarCol = 1099511627776.f;  // 2^40
 // kernel turns them into the gradients of the Gaussian's parameters. The
 // FP32x2 arithmetic pairs two ROWS of one column, so the per-row terms (the
 // row's crossing, t2, lw2 - t2^2 and the row sums) are computed once per row
-// and not duplicated. Pixels outside the box (rows: lw2 - t2^2 = -inf;
-// columns: kFarCol) or the ellipsoid (CUT) get w = 0, never a NaN: every
-// factor that multiplies w stays finite.
+// and not duplicated. Pixels outside the box (rows: lw2 - t2^2 = -inf, or a
+// large finite exponent in the fast form; columns: kFarCol) or the ellipsoid
+// (CUT) get w = 0, never a NaN: every factor that multiplies w stays finite.
+// The fast form takes sum g t1^2 from the exponent n = t1^2 + t2^2 - lw2 the
+// weight needs anyway (nine packed operations per column and row pair
+// instead of ten); the rounding of n then costs about 2^-23 |t2^2 - lw2| of
+// the row's sum of |g|, which the exponent range of a non-zero weight keeps
+// near 2^-16 of it.
 template <int FH, int CUT, bool TAIL = false>
 __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, const float4& cr,
                                          uint2 bx, uint32_t cl, uint32_t rid,
@@ -475,6 +480,48 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, cons
   float2 a5p = make_float2(0.f, 0.f), a6p = make_float2(0.f, 0.f);
   // pixel factors of row pair rp, column c: pix[8 rp + c] = (r, r', -rC, -rC')
   const float4* __restrict__ pxr = pix + 4 * y0;
+  // Fast form (r11 <= 2^20, so every t1 and t1^2 of the footprint is finite):
+  // sum g t1^2 per row as sum g n - (t2^2 - lw2) sum g with n = t1^2 + t2^2 -
+  // lw2 the exponent already formed; pixels whose weight is zero get a large
+  // finite n (never 0 * inf).
+  constexpr float kBigN = 1.2676506e30f;  // 2^100
+  auto row_pair_fast = [&](int j) {
+    const int y = y0 + 2 * j;
+    const float2 k2 = make_float2((float)y, (float)(y + 1));
+    const float2 nsh = __ffma2_rn(kq, k2, ns0q);
+    const float2 nrs = __ffma2_rn(a1, k2, a0);
+    const float2 dy = __fadd2_rn(__fadd2_rn(k2, nyh), nyl);
+    const float2 t2 = __fmul2_rn(r22, dy);
+    const float2 t2sq = __fmul2_rn(t2, t2);
+    float2 crow = __fadd2_rn(t2sq, nlw);
+    if (y < ry0 || y > ry1) crow.x = kBigN;
+    if (y + 1 < ry0 || y + 1 > ry1) crow.y = kBigN;
+    float2 s1r = make_float2(0.f, 0.f), u1r = make_float2(0.f, 0.f), a4r = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float2 t1 = __ffma2_rn(r11, __fadd2_rn(colv[c], nsh), nrs);
+      float2 n2 = __ffma2_rn(t1, t1, crow);
+      if (CUT) {
+        const float2 q = __ffma2_rn(t1, t1, t2sq);
+        if (!(q.x <= bb.w)) n2.x = kBigN;
+        if (!(q.y <= bb.w)) n2.y = kBigN;
+      }
+      const float2 w = make_float2(fast_exp2_neg(n2.x), fast_exp2_neg(n2.y));
+      const float4 px = pxr[8 * j + c];
+      const float2 rr = make_float2(px.x, px.y);
+      const float2 g = __fmul2_rn(__ffma2_rn(rr, cc, make_float2(px.z, px.w)), w);
+      s0 = __ffma2_rn(rr, w, s0);
+      s1r = __fadd2_rn(s1r, g);
+      u1r = __ffma2_rn(g, t1, u1r);
+      a4r = __ffma2_rn(g, n2, a4r);
+    }
+    s1p = __fadd2_rn(s1p, s1r);
+    u1p = __fadd2_rn(u1p, u1r);
+    a4 = __ffma2_rn(make_float2(-crow.x, -crow.y), s1r, __fadd2_rn(a4, a4r));
+    a5p = __ffma2_rn(t2, u1r, a5p);
+    u2p = __ffma2_rn(t2, s1r, u2p);
+    a6p = __ffma2_rn(t2sq, s1r, a6p);
+  };
   auto row_pair = [&](int j) {
     const int y = y0 + 2 * j;
     const float2 k2 = make_float2((float)y, (float)(y + 1));
@@ -515,6 +562,9 @@ __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, cons
   if (TAIL) {
 #pragma unroll 1
     for (int j = 0; j < nrows / 2; ++j) row_pair(j);
+  } else if (ig.r11 <= 1048576.f) {
+#pragma unroll
+    for (int j = 0; j < FH / 2; ++j) row_pair_fast(j);
   } else {
 #pragma unroll
     for (int j = 0; j < FH / 2; ++j) row_pair(j);

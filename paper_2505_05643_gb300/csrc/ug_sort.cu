@@ -5,8 +5,8 @@
 // shared memory and writes them digit-major, (2) one exclusive scan over
 // (digit, block) gives every block the output base of each digit, (3) every
 // block ranks its keys stably (warps in order, each warp's items in element
-// order, equal digits found with __match_any_sync) and scatters keys and
-// values. Instances arrive in (Gaussian chunk, plane, Gaussian) order, so the
+// order, the lanes with equal digits found by one ballot per digit bit) and
+// scatters keys and values. Instances arrive in (Gaussian chunk, plane, Gaussian) order, so the
 // stable sort leaves each tile's records in ascending Gaussian order.
 #include "ug_scan.cuh"
 
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kSortThreads)
 // Warp w of block b holds elements b*kSortTile + w*32*kSortItems + k*32 + lane
 // (item k of lane `lane`): each warp ranks its 32*kSortItems keys in element
 // order with per-warp digit counters in shared memory (items in order, lanes in
-// order, equal digits found with __match_any_sync). The block then places its
+// order, equal digits found by ballots). The block then places its
 // keys in shared memory in digit order and writes them out so that consecutive
 // threads write consecutive addresses of each digit's output run.
 __global__ void __launch_bounds__(kSortThreads, 3)
@@ -75,7 +75,15 @@ __global__ void __launch_bounds__(kSortThreads, 3)
   for (int k = 0; k < kSortItems; ++k) {
     const bool valid = wbase + k * 32 < count;
     const uint32_t d = valid ? (kreg[k] >> shift) & 0xffu : 256u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    // the lanes with the same digit: one ballot per digit bit (faster here
+    // than __match_any_sync)
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+      const uint32_t bit = (d >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bal : ~bal;
+    }
     const uint32_t before = valid ? cnt[warp][d] : 0u;
     __syncwarp();
     if (valid && (peers & lt) == 0) cnt[warp][d] = before + __popc(peers);
