@@ -229,17 +229,18 @@ __device__ __forceinline__ float rect_q_lower_bound(const float4& a, float r22, 
   const float ylo = __fadd_rn((float)(ya - i0), 0.5f), yhi = __fadd_rn((float)(yb - i0), 0.5f);
   const float dylo = __fsub_rn(ylo, a.y), dyhi = __fsub_rn(yhi, a.y);
   const float slo = __fmaf_rn(-a.w, dylo, a.x), shi = __fmaf_rn(-a.w, dyhi, a.x);
-  const float u00 = __fsub_rn(xlo, slo), u10 = __fsub_rn(xhi, slo);
-  const float u01 = __fsub_rn(xlo, shi), u11 = __fsub_rn(xhi, shi);
-  const float umin = fminf(fminf(u00, u10), fminf(u01, u11));
-  const float umax = fmaxf(fmaxf(u00, u10), fmaxf(u01, u11));
+  // the least and greatest of the four corner differences x - s: rounding is
+  // monotone, so they are xlo - max(s) and xhi - min(s), rounded once
+  const float umin = __fsub_rn(xlo, fmaxf(slo, shi)), umax = __fsub_rn(xhi, fminf(slo, shi));
   const float ady = fmaxf(fabsf(dylo), fabsf(dyhi)), ay = fabsf(a.y);
   const float e1 = __fmul_rn(
       4.f * eps, __fadd_rn(__fadd_rn(fmaxf(fabsf(umin), fabsf(umax)), fmaxf(fabsf(slo), fabsf(shi))),
                            __fadd_rn(fabsf(a.x), __fmul_rn(fabsf(a.w), __fadd_rn(2.f * ady, ay)))));
   const float e2 = __fmul_rn(4.f * eps, __fadd_rn(ady, ay));
-  const float m1 = umin > e1 ? __fsub_rn(umin, e1) : (umax < -e1 ? __fsub_rn(-umax, e1) : 0.f);
-  const float m2 = dylo > e2 ? __fsub_rn(dylo, e2) : (dyhi < -e2 ? __fsub_rn(-dyhi, e2) : 0.f);
+  // distance of [umin, umax] from [-e1, e1]: umin - e1 above it, -umax - e1
+  // below it (umin <= umax, so at most one is positive), else 0
+  const float m1 = fmaxf(__fsub_rn(fmaxf(umin, -umax), e1), 0.f);
+  const float m2 = fmaxf(__fsub_rn(fmaxf(dylo, -dyhi), e2), 0.f);  // likewise (dylo <= dyhi)
   const float t1 = __fmul_rn(a.z, m1), t2 = __fmul_rn(r22, m2);
   return __fmaf_rn(t1, t1, __fmul_rn(t2, t2));
 }
@@ -311,23 +312,20 @@ __device__ __forceinline__ uint32_t tile_footprints16(const float4& a, const flo
     const float ylo = __fadd_rn((float)(ya - i0), 0.5f), yhi = __fadd_rn((float)(yb - i0), 0.5f);
     const float dylo = __fsub_rn(ylo, a.y), dyhi = __fsub_rn(yhi, a.y);
     const float slo = __fmaf_rn(-a.w, dylo, a.x), shi = __fmaf_rn(-a.w, dyhi, a.x);
+    const float s_hi = fmaxf(slo, shi), s_lo = fminf(slo, shi);
     const float ady = fmaxf(fabsf(dylo), fabsf(dyhi));
     const float smax = fmaxf(fabsf(slo), fabsf(shi));
     const float es = __fadd_rn(ax, __fmul_rn(aw, __fadd_rn(2.f * ady, ay)));
     const float e2 = __fmul_rn(4.f * eps, __fadd_rn(ady, ay));
-    const float m2 = dylo > e2 ? __fsub_rn(dylo, e2) : (dyhi < -e2 ? __fsub_rn(-dyhi, e2) : 0.f);
+    const float m2 = fmaxf(__fsub_rn(fmaxf(dylo, -dyhi), e2), 0.f);
     const float t2 = __fmul_rn(b.x, m2);
     const float t2sq = __fmul_rn(t2, t2);
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const float u00 = __fsub_rn(xlo[k], slo), u10 = __fsub_rn(xhi[k], slo);
-      const float u01 = __fsub_rn(xlo[k], shi), u11 = __fsub_rn(xhi[k], shi);
-      const float umin = fminf(fminf(u00, u10), fminf(u01, u11));
-      const float umax = fmaxf(fmaxf(u00, u10), fmaxf(u01, u11));
+      const float umin = __fsub_rn(xlo[k], s_hi), umax = __fsub_rn(xhi[k], s_lo);
       const float e1 =
           __fmul_rn(4.f * eps, __fadd_rn(__fadd_rn(fmaxf(fabsf(umin), fabsf(umax)), smax), es));
-      const float m1 =
-          umin > e1 ? __fsub_rn(umin, e1) : (umax < -e1 ? __fsub_rn(-umax, e1) : 0.f);
+      const float m1 = fmaxf(__fsub_rn(fmaxf(umin, -umax), e1), 0.f);
       const float t1 = __fmul_rn(a.z, m1);
       const float q = __fmaf_rn(t1, t1, t2sq);
       const bool live = xok[k] & yok & !(__fsub_rn(b.y, q) < -127.f) &
