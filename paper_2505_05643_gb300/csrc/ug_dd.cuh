@@ -149,18 +149,28 @@ __device__ __forceinline__ dd r_fma(dd a, float b, dd c) { return dd_add_sloppy(
 __device__ __forceinline__ dd m_div(dd a, dd b) { return dd(__fdiv_rn((float)a, (float)b)); }
 __device__ __forceinline__ dd m_sqrt(dd a) { return dd(__fsqrt_rn((float)a)); }
 
-// 1/x and 1/sqrt(x) to double-word accuracy: an FP32 estimate and one Newton
-// step evaluated in double words (the error of the estimate squares).
+// 1/x and 1/sqrt(x) to double-word accuracy: an FP32 estimate r and one
+// Newton step (the error of the estimate squares). The residual e, about
+// 2^-23 in size, is formed from exact steps and needs only FP32 accuracy
+// (its error is then about 2^-47), so r + r e comes out as a Fast2Sum.
+//  1/x: 1 - x.hi r is exact in one FMA when r is the correctly rounded
+//  reciprocal of x.hi (Markstein), then e = (1 - x.hi r) - x.lo r.
 __device__ __forceinline__ dd dd_rcp(dd x) {
   const float r = __frcp_rn(x.hi);
-  const dd e = dd_add(dd(1.f), -dd_mul(x, r));  // 1 - x r
-  return dd_add(dd(r), dd_mul(e, r));            // r + r (1 - x r)
+  const float e = __fmaf_rn(-x.lo, r, __fmaf_rn(-x.hi, r, 1.f));
+  return fast_two_sum(r, __fmul_rn(r, e));
 }
+//  1/sqrt(x): x r^2 = x.hi (t + t') + x.lo t with t + t' = r^2 exactly (2Prod)
+//  and x.hi t = p + p' exactly; 1 - p is exact (Sterbenz: p is within a few
+//  ulps of 1), so e = ((1 - p) - p') - (x.hi t' + x.lo t) and the result is
+//  r + r e / 2.
 __device__ __forceinline__ dd dd_rsqrt(dd x) {
   const float r = rsqrtf(x.hi);
-  const dd xr2 = dd_mul(dd_mul(x, r), r);                    // x r^2
-  const dd e = dd_mul(dd_add(dd(1.f), -xr2), 0.5f);          // (1 - x r^2) / 2
-  return dd_add(dd(r), dd_mul(e, r));                        // r + r (1 - x r^2) / 2
+  const dd t = two_prod(r, r);
+  const dd p = two_prod(x.hi, t.hi);
+  const float small = __fmaf_rn(x.hi, t.lo, __fmul_rn(x.lo, t.hi));
+  const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p.hi), p.lo), small);
+  return fast_two_sum(r, __fmul_rn(__fmul_rn(0.5f, r), e));
 }
 
 __device__ __forceinline__ dd ceil(dd x) {
