@@ -40,6 +40,47 @@ int device_sms() {
   return sms;
 }
 
+// ------------------------------------------------------------------ warp helpers
+// Transpose of a 32 x 32 bit matrix held one row per lane (bit c of lane r's
+// word is element (r, c)): afterwards lane c holds column c. Five butterfly
+// steps swap the off-diagonal blocks of ever smaller block pairs.
+__device__ __forceinline__ uint32_t warp_bit_transpose(uint32_t x, int lane) {
+  const uint32_t m[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int j = 16 >> k;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? (x & ~m[k]) | ((y >> j) & m[k]) : (x & m[k]) | ((y & m[k]) << j);
+  }
+  return x;
+}
+
+// Largest lane l whose non-decreasing per-lane value pre[l] is <= o.
+__device__ __forceinline__ int warp_search(uint32_t pre, uint32_t o) {
+  int l = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const uint32_t p = __shfl_sync(0xffffffffu, pre, l + step);
+    if (p <= o) l += step;
+  }
+  return l;
+}
+
+// Position of the n-th (0-based) set bit of m (which has more than n set bits).
+__device__ __forceinline__ uint32_t nth_set_bit(unsigned long long m, uint32_t n) {
+  uint32_t pos = 0;
+#pragma unroll
+  for (int w = 32; w >= 1; w >>= 1) {
+    const uint32_t c = (uint32_t)__popcll(m & ((1ull << w) - 1ull));
+    if (n >= c) {
+      n -= c;
+      m >>= w;
+      pos += (uint32_t)w;
+    }
+  }
+  return pos;
+}
+
 // ------------------------------------------------------------------ planes
 __global__ void __launch_bounds__(256)
     k_setup_planes(const ug_plane* planes, int P, int tile, int total_tiles,
@@ -233,7 +274,6 @@ struct CullWarp {
   float mu[3][32];
   float Fi[9][32];
   float R2[32], hb[32];
-  uint16_t queue[64];              // (plane << 5) | lane, a ring
   uint32_t bits[kCullPlanesSmem];  // candidate bits of the current plane group
 };
 
@@ -247,8 +287,8 @@ struct CullWarp {
 // 8.008 eps |mu - o|_1 of n.(mu - o), so |m3'| <= sqrt(thr1) + 2 Bm + 4.01 eps
 // (|mu|_1 + |o|_1) <= sqrt(thr1) + 20.03 eps (|mu|_1 + |o|_1): the test |m3'| <=
 // sqrt(thr1) + 24 eps (|mu|_1 + sqrt(3) max|o|) (one threshold per Gaussian,
-// rounded up) passes every pair that cull_pair passes. Pairs that pass it go
-// into the warp's queue and take the full test 32 at a time, every lane busy.
+// rounded up) passes every pair that cull_pair passes. Pairs that pass it
+// take the full test 32 at a time, every lane busy.
 template <int COV>
 __global__ void __launch_bounds__(256)
     k_cull(ug_gaussians g, int64_t n, int P, float chi2, float beta, float ratio, float reach,
@@ -319,7 +359,6 @@ __global__ void __launch_bounds__(256)
     if (lane == 0) v.gflag[chunk] = fl;
   }
   const float mx = W.mu[0][lane], my = W.mu[1][lane], mz = W.mu[2][lane];
-  const uint32_t lt = lanemask_lt();
   for (int p0 = 0; p0 < P; p0 += kCullPlanesSmem) {
     const int np = min(kCullPlanesSmem, P - p0);
     __syncthreads();
@@ -347,22 +386,33 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     if (!live_warp) continue;
     for (int q = lane; q < kCullPlanesSmem; q += 32) W.bits[q] = 0u;
-    uint32_t head = 0, count = 0;
-    for (int q = 0; q < np; ++q) {
-      const float4 nq = s_no[q];
-      const float m3 = __fsub_rn(__fmaf_rn(nq.z, mz, __fmaf_rn(nq.y, my, __fmul_rn(nq.x, mx))),
-                                 nq.w);
-      const uint32_t bal = __ballot_sync(0xffffffffu, fabsf(m3) <= T);
-      if ((bal >> lane) & 1u)
-        W.queue[(head + count + __popc(bal & lt)) % 64u] = (uint16_t)((q << 5) | lane);
-      count += __popc(bal);
-      __syncwarp();
-      const bool flush = q == np - 1;
-      while (count >= 32u || (flush && count > 0u)) {
-        const uint32_t m = min(count, 32u);
-        if ((uint32_t)lane < m) {
-          const uint32_t e = W.queue[(head + lane) % 64u];
-          const int eq = (int)(e >> 5), el = (int)(e & 31u);
+    // 32 planes at a time: every lane tests its Gaussian against each plane
+    // (bit j of `pass`), the bits are transposed so that lane j holds plane
+    // j's passing Gaussians, and the pairs, numbered plane by plane, take the
+    // full test 32 at a time (every lane busy)
+    for (int g0 = 0; g0 < np; g0 += 32) {
+      const int ng = min(32, np - g0);
+      uint32_t pass = 0;
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) {
+        const float4 nq = s_no[g0 + j];
+        const float m3 = __fsub_rn(
+            __fmaf_rn(nq.z, mz, __fmaf_rn(nq.y, my, __fmul_rn(nq.x, mx))), nq.w);
+        pass |= (uint32_t)((fabsf(m3) <= T) & (j < ng)) << j;
+      }
+      const uint32_t pm = warp_bit_transpose(pass, lane);  // plane g0 + lane's Gaussians
+      const uint32_t cnt = (uint32_t)__popc(pm);
+      const uint32_t incl = warp_incl_scan(cnt);
+      const uint32_t excl = incl - cnt;
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      for (uint32_t rb = 0; rb < total; rb += 32u) {
+        const uint32_t e = rb + (uint32_t)lane;
+        const int j = warp_search(excl, e);  // the plane of pair e
+        const uint32_t mj = __shfl_sync(0xffffffffu, pm, j);
+        const uint32_t ej = __shfl_sync(0xffffffffu, excl, j);
+        if (e < total) {
+          const int el = (int)nth_set_bit(mj, e - ej);
+          const int eq = g0 + j;
           CullGauss c;
 #pragma unroll
           for (int k = 0; k < 3; ++k) c.mu[k] = W.mu[k][el];
@@ -372,11 +422,9 @@ __global__ void __launch_bounds__(256)
           c.hb = W.hb[el];
           if (cull_pair(c, s_pl[eq], chi2)) atomicOr(&W.bits[eq], 1u << el);
         }
-        head = (head + m) % 64u;
-        count -= m;
-        __syncwarp();
       }
     }
+    __syncwarp();
     for (int q = lane; q < np; q += 32) v.mask[chunk * P + p0 + q] = W.bits[q];
     // the candidate scan's block partials (records, FP64 records): this
     // group's entries are consecutive, so they fall into at most two scan
@@ -422,20 +470,6 @@ struct CandStore {
 };
 
 // ------------------------------------------------------------------ 3. list
-// Transpose of a 32 x 32 bit matrix held one row per lane (bit c of lane r's
-// word is element (r, c)): afterwards lane c holds column c. Five butterfly
-// steps swap the off-diagonal blocks of ever smaller block pairs.
-__device__ __forceinline__ uint32_t warp_bit_transpose(uint32_t x, int lane) {
-  const uint32_t m[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const int j = 16 >> k;
-    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
-    x = (lane & j) ? (x & ~m[k]) | ((y >> j) & m[k]) : (x & m[k]) | ((y & m[k]) << j);
-  }
-  return x;
-}
-
 // One warp per chunk of 32 Gaussians, 32 planes at a time: the lanes load the
 // planes' candidate masks and bases (one plane per lane, coalesced), the
 // masks are transposed so that every lane holds its own Gaussian's planes, and
@@ -622,32 +656,6 @@ __device__ __forceinline__ bool box_tile_live(const float4& a, const float4& b, 
   const int j0 = bx.x & 0xffff, j1 = bx.x >> 16, i0 = bx.y & 0xffff, i1 = bx.y >> 16;
   return rect_live(a, b, j0, i0, max(j0, tx * tile), min(j1, tx * tile + tile - 1),
                    max(i0, ty * tile), min(i1, ty * tile + tile - 1), cut);
-}
-
-// Largest lane l whose non-decreasing per-lane value pre[l] is <= o.
-__device__ __forceinline__ int warp_search(uint32_t pre, uint32_t o) {
-  int l = 0;
-#pragma unroll
-  for (int step = 16; step > 0; step >>= 1) {
-    const uint32_t p = __shfl_sync(0xffffffffu, pre, l + step);
-    if (p <= o) l += step;
-  }
-  return l;
-}
-
-// Position of the n-th (0-based) set bit of m (which has more than n set bits).
-__device__ __forceinline__ uint32_t nth_set_bit(unsigned long long m, uint32_t n) {
-  uint32_t pos = 0;
-#pragma unroll
-  for (int w = 32; w >= 1; w >>= 1) {
-    const uint32_t c = (uint32_t)__popcll(m & ((1ull << w) - 1ull));
-    if (n >= c) {
-      n -= c;
-      m >>= w;
-      pos += (uint32_t)w;
-    }
-  }
-  return pos;
 }
 
 constexpr uint32_t kMaskTiles = 64;  // boxes up to this many tiles keep their live-tile mask
