@@ -55,8 +55,8 @@ BWD_OPS = 9
 # DRAM bytes (read + write) of one launch of each rasterizer on this workload,
 # from a one-pass ncu capture of the kernel as it stands; None when the kernel has
 # changed since the counters were taken.
-BWD_TRAFFIC = 681061632  # 594,883,328 read + 86,178,304 written (k_render_bwd, variant 0)
-FWD_TRAFFIC = 330480896  # 286,015,744 read + 44,465,152 written (k_render_fwd, variant 0)
+BWD_TRAFFIC = 620252672  # 537,629,952 read + 82,622,720 written (k_render_bwd, variant 0)
+FWD_TRAFFIC = 323985664  # 279,489,792 read + 44,495,872 written (k_render_fwd, variant 5)
 
 METRIC = "Gaussian·pixel evals/s and fwd+bwd train steps/s, 1M Gaussians, 1×GB300"
 WORKLOAD = "aniso_1m: 1,000,000 Gaussians, axis ratios log-uniform to 1e4, 64 planes/launch " \
