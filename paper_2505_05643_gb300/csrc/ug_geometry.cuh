@@ -412,6 +412,22 @@ __device__ __forceinline__ float to_f(T x) {
   return (float)x;
 }
 
+// x u + y v - d rounded to FP32. In double words the terms cancel to about
+// the Gaussian's extent: the high parts' products by 2Prod and their sums by
+// 2Sum, every error term and low part summed in FP32, one final rounding.
+__device__ __forceinline__ float lin2_minus(float x, float y, float u, float v, float d) {
+  return r_fma(x, u, r_fma(y, v, -d));
+}
+__device__ __forceinline__ float lin2_minus(dd x, dd y, float u, float v, dd d) {
+  const dd p = two_prod(x.hi, u), q = two_prod(y.hi, v);
+  const dd s = two_sum(p.hi, q.hi);
+  const dd t = two_sum(s.hi, -d.hi);
+  float e = __fmaf_rn(x.lo, u, p.lo);
+  e = __fmaf_rn(y.lo, v, __fadd_rn(e, q.lo));
+  e = __fadd_rn(e, __fsub_rn(__fadd_rn(s.lo, t.lo), d.lo));
+  return __fadd_rn(t.hi, e);
+}
+
 template <typename T, int COV>
 __device__ __forceinline__ void pair_lsq(const Factor<T>& f, const PlaneDev& pl,
                                          const PairGeo<T>& g, PairLsq<T>& o) {
@@ -457,7 +473,7 @@ __device__ __forceinline__ void pair_lsq(const Factor<T>& f, const PlaneDev& pl,
     o.nh[a] = to_f(nh[a]);
     // X_w(x*) - mu = x1* u + x2* v - (mu - o): the terms cancel to about the
     // Gaussian's extent, so this stays in T
-    o.ew[a] = to_f(r_fma(x, fr.r[0][a], r_fma(y, fr.r[1][a], -g.d[a])));
+    o.ew[a] = lin2_minus(x, y, fr.r[0][a], fr.r[1][a], g.d[a]);
   }
 }
 

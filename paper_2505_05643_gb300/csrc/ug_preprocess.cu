@@ -518,7 +518,9 @@ __device__ __forceinline__ void split_rel(float x, int n, float& h, float& l) {
   l = __fadd_rn(__fsub_rn(x, xp), __fsub_rn(b, bp));
 }
 __device__ __forceinline__ void split_rel(dd x, int n, float& h, float& l) {
-  const dd r = dd_add(x, dd((float)(-n)));
+  // a double word plus an FP32 number (DWPlusFP of Joldes, Muller and Popescu)
+  const dd s = two_sum(x.hi, (float)(-n));
+  const dd r = fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
   h = r.hi;
   l = r.lo;
 }
@@ -753,6 +755,11 @@ __global__ void __launch_bounds__(256, 4) k_emit(int ts, int cut, uint32_t inst_
   // footprint tests of all their instances
   __shared__ float4 s_a[8][32], s_b[8][32];
   __shared__ uint2 s_bx[8][32];
+  // the record kernels' counts into the status (they have all finished)
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    v.hdr->st.fp64_records = (int64_t)v.hdr->kept64;
+    v.hdr->st.box_pixels = (int64_t)v.hdr->box_pixels;
+  }
   if (dev_failed(v.hdr)) return;
   const uint32_t slots = v.hdr->slots;
   const uint32_t n_inst = (uint32_t)v.hdr->st.instances;
@@ -850,12 +857,6 @@ __global__ void __launch_bounds__(256, 4) k_emit(int ts, int cut, uint32_t inst_
   }
 }
 
-__global__ void k_finish_pre(WsView v) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    v.hdr->st.fp64_records = (int64_t)v.hdr->kept64;
-    v.hdr->st.box_pixels = (int64_t)v.hdr->box_pixels;
-  }
-}
 
 static int tile_shift(int tile) { return tile == 8 ? 3 : 4; }
 
@@ -905,7 +906,6 @@ static void launch_pre_cov(const ug_plan* plan, const ug_gaussians* g, WsView v,
   k_scan_down<1, SlotLoad, SlotStore, true><<<(unsigned)rblk, kScanThreads, 0, s>>>(
       sl, ss, plan->record_capacity, v.slot_part, v.hdr, rblk, 2, plan->instance_capacity);
   k_emit<<<lg, 256, 0, s>>>(ts, c.cutoff, (uint32_t)plan->instance_capacity, v);
-  k_finish_pre<<<1, 32, 0, s>>>(v);
 }
 
 cudaError_t launch_preprocess(const ug_plan* plan, const ug_gaussians* g, WsView v,

@@ -79,8 +79,13 @@ __global__ void __launch_bounds__(kSortThreads, 3)
     // than __match_any_sync)
     uint32_t peers = 0xffffffffu;
 #pragma unroll
-    for (int b = 0; b < 9; ++b) {
+    for (int b = 0; b < 8; ++b) {
       const uint32_t bit = (d >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bal : ~bal;
+    }
+    if (count < kSortTile) {  // the last block: its missing items carry digit 256
+      const uint32_t bit = d >> 8;
       const uint32_t bal = __ballot_sync(0xffffffffu, bit);
       peers &= bit ? bal : ~bal;
     }
