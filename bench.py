@@ -55,7 +55,7 @@ BWD_OPS = 9
 # DRAM bytes (read + write) of one launch of each rasterizer on this workload,
 # from a one-pass ncu capture of the kernel as it stands; None when the kernel has
 # changed since the counters were taken.
-BWD_TRAFFIC = 620252672  # 537,629,952 read + 82,622,720 written (k_render_bwd, variant 0)
+BWD_TRAFFIC = 551366656  # 473,574,912 read + 77,791,744 written (k_render_bwd, variant 5)
 FWD_TRAFFIC = 323985664  # 279,489,792 read + 44,495,872 written (k_render_fwd, variant 5)
 
 METRIC = "Gaussian·pixel evals/s and fwd+bwd train steps/s, 1M Gaussians, 1×GB300"

@@ -836,8 +836,9 @@ static cudaError_t dispatch_fwd(const ug_plan* plan, WsView v, const uint32_t* v
 // MINB resident blocks asked of the compiler, which bounds its registers):
 //   0: FH 8, NS 4, BATCH 128, MINB 4     1: FH 4, NS 4, BATCH 128, MINB 2 (tile 16)
 //   2: FH 8, NS 3, BATCH 128, MINB 5     3: FH 8, NS 4, BATCH 64, MINB 5
-//   4: FH 8, NS 3, BATCH 256, MINB 3
-// (2-4 for the 16 x 16 tile only).
+//   4: FH 8, NS 3, BATCH 256, MINB 3     5: FH 8, NS 4, BATCH 128, MINB 3 (128 registers a
+//   thread, no spills)
+// (2-5 for the 16 x 16 tile only).
 template <int TILE, int CUT>
 static cudaError_t dispatch_bwd(const ug_plan* plan, WsView v, const uint32_t* vals,
                                 const float* image, const float* alpha, const float* grad,
@@ -854,6 +855,7 @@ static cudaError_t dispatch_bwd(const ug_plan* plan, WsView v, const uint32_t* v
       case 2: return bwd_launch<TILE, 8, CUT, 3, 128, 5>(plan, v, vals, image, alpha, grad, s);
       case 3: return bwd_launch<TILE, 8, CUT, 4, 64, 5>(plan, v, vals, image, alpha, grad, s);
       case 4: return bwd_launch<TILE, 8, CUT, 3, 256, 3>(plan, v, vals, image, alpha, grad, s);
+      case 5: return bwd_launch<TILE, 8, CUT, 4, 128, 3>(plan, v, vals, image, alpha, grad, s);
       default: break;
     }
   }
@@ -861,7 +863,7 @@ static cudaError_t dispatch_bwd(const ug_plan* plan, WsView v, const uint32_t* v
 }
 
 int num_render_variants(int tile) { return tile == 16 ? 6 : tile == 8 ? 3 : 0; }
-int num_render_variants_bwd(int tile) { return tile == 16 ? 5 : tile == 8 ? 2 : 0; }
+int num_render_variants_bwd(int tile) { return tile == 16 ? 6 : tile == 8 ? 2 : 0; }
 
 cudaError_t launch_render(const ug_plan* plan, WsView v, float* image, float* alpha,
                           cudaStream_t s) {

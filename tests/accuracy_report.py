@@ -105,12 +105,12 @@ def main():
     g = synth.scale_rot_to_tri(g, 1e-4)
     sub = np.random.default_rng(0).choice(len(g["logit"]), 2000, replace=False)
     rows += case("aniso_1m tri, all 64 planes (gradients: 2000 Gaussians)", g, pl,
-                 R.make_config(cov_param=B.UG_COV_TRI, variant=5, variant_bwd=0), subset=sub)
+                 R.make_config(cov_param=B.UG_COV_TRI, variant=5, variant_bwd=5), subset=sub)
     g, poses, _ = synth.workload_train_200k()
     sub = np.random.default_rng(0).choice(len(g["logit"]), 2000, replace=False)
     rows += case("train_200k tri, the 32 poses of a step (gradients: 2000 Gaussians)", g,
                  synth.select_planes(poses, list(range(32))),
-                 R.make_config(cov_param=B.UG_COV_TRI, variant=5, variant_bwd=0), subset=sub)
+                 R.make_config(cov_param=B.UG_COV_TRI, variant=5, variant_bwd=5), subset=sub)
     g, _, train, _ = synth.workload_recon()
     novel = synth.planes_random(np.random.default_rng(7), [(512, 512)] * 512)
     pl5 = synth.concat_planes(synth.select_planes(train, [0, 1, 2, 3]),
@@ -118,7 +118,7 @@ def main():
     sub = np.random.default_rng(0).choice(len(g["logit"]), 1000, replace=False)
     rows += case("recon 3M tri, 4 training poses + a 512^2 novel slice (gradients: 1000 "
                  "Gaussians)", g, pl5,
-                 R.make_config(cov_param=B.UG_COV_TRI, variant=5, variant_bwd=0), subset=sub)
+                 R.make_config(cov_param=B.UG_COV_TRI, variant=5, variant_bwd=5), subset=sub)
     lines = ["| workload | output | n compared | n ambiguous (either decision valid) | max abs err | "
              "max err / tolerance, clear decisions | max err / tolerance, ambiguous pixels | "
              "fraction within tolerance |", "|---|---|---|---|---|---|---|---|"]

@@ -126,7 +126,7 @@ def test_grad_extreme_anisotropy():
     _check_grads(gpu, gref, gabs, oracle.param_names(0), "aniso cut")
 
 
-@pytest.mark.parametrize("tile,variant", [(16, v) for v in range(1, 5)] + [(8, 0), (8, 1)])
+@pytest.mark.parametrize("tile,variant", [(16, v) for v in range(1, 6)] + [(8, 0), (8, 1)])
 def test_grad_variants(tile, variant):
     """Every compiled backward variant (footprint height, stages, records per
     stage) against the oracle's gradient, on dense tiles that span several

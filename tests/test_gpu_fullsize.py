@@ -1,7 +1,7 @@
 """Parity at the bench workload's full size, in the launch configuration the
 bench times: the 1,000,000-Gaussian extreme-anisotropy scene (axis ratios
 log-uniform to 1e4, triangular front-end) on all 64 ragged planes (6,688,768
-pixels), tile 16, forward rasterizer variant 5, backward variant 0. Every
+pixels), tile 16, forward rasterizer variant 5, backward variant 5. Every
 pixel of the image and alpha is compared with the FP64 oracle at the stated
 tolerance, and every gradient entry of 2,000 sampled Gaussians (the oracle
 computes the gradient of any subset of Gaussians on its own)."""
@@ -38,7 +38,7 @@ def test_full_bench_workload_parity():
     g, pl = synth.workload_aniso_1m()
     g = synth.scale_rot_to_tri(g, 1e-4)
     n = len(g["logit"])
-    cfg = R.make_config(cov_param=B.UG_COV_TRI, tile=16, variant=5, variant_bwd=0)
+    cfg = R.make_config(cov_param=B.UG_COV_TRI, tile=16, variant=5, variant_bwd=5)
     ocfg = oracle_config(cfg)
     r = R.Renderer(n, pl, cfg)
     assert n == 1_000_000 and r.P == 64 and r.total_pixels == 6_688_768
@@ -102,7 +102,7 @@ def test_train_200k_full_step_parity():
     paper's initialisation, the 32 sweep poses of one step at 256^2."""
     g, poses, _ = synth.workload_train_200k()
     pl = synth.select_planes(poses, list(range(32)))
-    cfg = R.make_config(cov_param=B.UG_COV_TRI, tile=16, variant=5, variant_bwd=0)
+    cfg = R.make_config(cov_param=B.UG_COV_TRI, tile=16, variant=5, variant_bwd=5)
     ref = _parity(g, pl, cfg, 2000, 43, "train_200k step")
     assert ref["pairs"] > 5e8  # about 340 pairs per pixel
 
@@ -115,6 +115,6 @@ def test_recon_3m_sampled_planes_parity():
     novel = synth.planes_random(np.random.default_rng(7), [(512, 512)] * 512)
     pl = synth.concat_planes(synth.select_planes(train, [0, 1, 2, 3]),
                              synth.select_planes(novel, [0]))
-    cfg = R.make_config(cov_param=B.UG_COV_TRI, tile=16, variant=5, variant_bwd=0)
+    cfg = R.make_config(cov_param=B.UG_COV_TRI, tile=16, variant=5, variant_bwd=5)
     ref = _parity(g, pl, cfg, 1000, 47, "recon 3M")
     assert ref["pairs"] > 1e9
