@@ -6,8 +6,9 @@
 // (digit, block) gives every block the output base of each digit, (3) every
 // block ranks its keys stably (warps in order, each warp's items in element
 // order, the lanes with equal digits found by one ballot per digit bit) and
-// scatters keys and values. Instances arrive in (Gaussian chunk, plane, Gaussian) order, so the
-// stable sort leaves each tile's records in ascending Gaussian order.
+// scatters keys and values. Instances arrive in (Gaussian chunk, plane,
+// Gaussian) order, so the stable sort leaves each tile's records in ascending
+// Gaussian order.
 #include "ug_scan.cuh"
 
 namespace ug {
@@ -189,9 +190,10 @@ cudaError_t launch_bin_sort(const ug_plan* plan, WsView v, cudaStream_t s) {
     const int shift = 8 * pass;
     const int src = pass & 1, dst = src ^ 1;
     k_sort_hist<<<(unsigned)nblk, kSortThreads, 0, s>>>(v.keys[src], shift, nblk, v);
+    // block partials, then each down-sweep block sums those before its own
     k_scan_partial<1, HistLoad><<<(unsigned)sblk, kScanThreads, 0, s>>>(ld, entries, v.sort_part, v.hdr);
-    k_scan_top<1><<<1, 1024, 0, s>>>(v.sort_part, sblk, v.hdr, 0, 0, 0);
-    k_scan_down<1, HistLoad, HistStore><<<(unsigned)sblk, kScanThreads, 0, s>>>(ld, st, entries, v.sort_part, v.hdr);
+    k_scan_down<1, HistLoad, HistStore, true><<<(unsigned)sblk, kScanThreads, 0, s>>>(
+        ld, st, entries, v.sort_part, v.hdr, sblk, 0, 0);
     k_sort_scatter<<<(unsigned)nblk, kSortThreads, 0, s>>>(v.keys[src], v.vals[src], v.keys[dst],
                                                            v.vals[dst], shift, nblk, v);
   }

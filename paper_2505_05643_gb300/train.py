@@ -93,7 +93,7 @@ class TrainStep:
         """Kernels of this library launched by one step (memsets excluded)."""
         # preprocess: planes, cull, scan, list, 2 records, live tiles, scan, emit
         pre = 9
-        sort = 5 * int(self.r.plan.sort_passes) + 1  # per pass: hist, 3 scan, scatter; ranges
+        sort = 4 * int(self.r.plan.sort_passes) + 1  # per pass: hist, 2 scan, scatter; ranges
         # render 1, mse 2, backward: zero, raster, chain, gather = 4, adam 2
         return pre + sort + 1 + 2 + 4 + 2
 
