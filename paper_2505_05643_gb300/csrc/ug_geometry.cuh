@@ -1,10 +1,10 @@
 // Per-Gaussian and per-(plane, Gaussian) geometry of the plane rasterizer.
 //
 // Everything that decides which pairs exist (the covariance factor, the
-// FP64 switch, the phase-1 test and the pixel box) is written with explicit
-// round-to-nearest intrinsics, so the compiler cannot contract or reorder it:
-// the counting pass and the emitting pass, compiled into different kernels,
-// take bit-identical decisions.
+// extended-precision switch, the phase-1 test and the pixel box) is written
+// with explicit round-to-nearest intrinsics, so the compiler cannot contract
+// or reorder it: the counting pass and the emitting pass, compiled into
+// different kernels, take bit-identical decisions.
 #pragma once
 
 #include "ug_dd.cuh"
@@ -19,51 +19,19 @@ __device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ float r_div(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float r_sqrt(float a) { return __fsqrt_rn(a); }
-__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ double r_div(double a, double b) { return __ddiv_rn(a, b); }
-__device__ __forceinline__ double r_sqrt(double a) { return __dsqrt_rn(a); }
 
-// Division and square root of values that are already accurate: in the FP64
-// branch the cancellation-prone sums (the covariance inverse and determinant
-// terms) run in FP64, and these well-conditioned operations on their results
-// run on the FP32 units (relative error 2^-24, far below the decision
-// margins), because FP64 division and square root are slow on GB300.
+// Division and square root of values that are already accurate run in FP32
+// in both branches (relative error 2^-24, far below the decision margins).
 __device__ __forceinline__ float m_div(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float m_sqrt(float a) { return __fsqrt_rn(a); }
-__device__ __forceinline__ double m_div(double a, double b) {
-  return (double)__fdiv_rn((float)a, (float)b);
-}
-__device__ __forceinline__ double m_sqrt(double a) { return (double)__fsqrt_rn((float)a); }
-
-// FP64-accurate reciprocal and reciprocal square root from an FP32 seed and
-// two Newton steps in FP64 (relative error ~1e-16; FP64 division and square
-// root take far longer on GB300). Only for arguments in the FP32 normal range.
-__device__ __forceinline__ double rcp64(double x) {
-  double r = (double)__frcp_rn((float)x);
-  r = fma(r, fma(-x, r, 1.0), r);
-  r = fma(r, fma(-x, r, 1.0), r);
-  return r;
-}
-__device__ __forceinline__ double rsqrt64(double x) {
-  double r = (double)rsqrtf((float)x);
-  r = r * fma(-0.5 * x, r * r, 1.5);
-  r = r * fma(-0.5 * x, r * r, 1.5);
-  return r;
-}
 
 // Extended-precision reciprocal and reciprocal square root, by type.
-__device__ __forceinline__ double ext_rcp(double x) { return rcp64(x); }
-__device__ __forceinline__ double ext_rsqrt(double x) { return rsqrt64(x); }
 __device__ __forceinline__ dd ext_rcp(dd x) { return dd_rcp(x); }
 __device__ __forceinline__ dd ext_rsqrt(dd x) { return dd_rsqrt(x); }
 __device__ __forceinline__ float ext_rcp(float x) { return r_div(1.f, x); }
 __device__ __forceinline__ float ext_rsqrt(float x) { return r_div(1.f, r_sqrt(x)); }
 
 __device__ __forceinline__ int to_int(float x) { return (int)x; }
-__device__ __forceinline__ int to_int(double x) { return (int)x; }
 __device__ __forceinline__ int to_int(dd x) { return dd_to_int(x); }
 
 // Whether T is the extended-precision type of the thin-Gaussian branch.

@@ -863,7 +863,8 @@ static int tile_shift(int tile) { return tile == 8 ? 3 : 4; }
 cudaError_t launch_setup_planes(const ug_plan* plan, const ug_plane* d_planes, WsView v,
                                 cudaStream_t s) {
   k_setup_planes<<<1, 256, 0, s>>>(d_planes, plan->num_planes, plan->cfg.tile, plan->total_tiles,
-                                    plan->total_pixels, scan_blocks(plan->chunks * plan->num_planes),
+                                    plan->total_pixels,
+                                    scan_blocks(plan->chunks * plan->num_planes),
                                     scan_blocks(plan->record_capacity), v);
   return cudaGetLastError();
 }

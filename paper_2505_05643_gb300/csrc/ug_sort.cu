@@ -191,7 +191,8 @@ cudaError_t launch_bin_sort(const ug_plan* plan, WsView v, cudaStream_t s) {
     const int src = pass & 1, dst = src ^ 1;
     k_sort_hist<<<(unsigned)nblk, kSortThreads, 0, s>>>(v.keys[src], shift, nblk, v);
     // block partials, then each down-sweep block sums those before its own
-    k_scan_partial<1, HistLoad><<<(unsigned)sblk, kScanThreads, 0, s>>>(ld, entries, v.sort_part, v.hdr);
+    k_scan_partial<1, HistLoad><<<(unsigned)sblk, kScanThreads, 0, s>>>(ld, entries, v.sort_part,
+                                                                        v.hdr);
     k_scan_down<1, HistLoad, HistStore, true><<<(unsigned)sblk, kScanThreads, 0, s>>>(
         ld, st, entries, v.sort_part, v.hdr, sblk, 0, 0);
     k_sort_scatter<<<(unsigned)nblk, kSortThreads, 0, s>>>(v.keys[src], v.vals[src], v.keys[dst],
