@@ -13,9 +13,10 @@ moments), restored by a device copy inside the step, so the workload does not
 drift with the number of steps. `--impl reference` times the FP64 CPU oracle (the only other
 implementation of this method) on a bounded sample of the same workload.
 
-Beside `value`: `e2e` (the same step through the public API with the targets
-and poses copied from pinned host memory and the loss and status read back every
-step), `roofline` (the backward rasterizer's FP32-pipe fraction, the forward's
+Beside `value`: `e2e` (the same graph-captured step replayed through the public
+API with the targets and poses copied from pinned host memory and the loss and
+status read back every step; the targets double-buffered so that their copy
+overlaps the previous step), `roofline` (the backward rasterizer's FP32-pipe fraction, the forward's
 beside it, and every phase's time), `cpu_baseline` (the FP64 oracle on the host
 cores), `clocks` (SM clock and throttle reasons sampled during the timed
 region) and `gpu_launches`. Other modes: `--workload train_200k` (the batched
@@ -465,25 +466,38 @@ def run_ours(args):
     else:
         raise RuntimeError("capacity overflow in the phase-timing steps")
 
-    # ---- e2e: the public API with host buffers; the step's inputs (targets and
-    # plane poses) copied from pinned host memory, and its loss and status read
-    # back into pinned host memory, every step. The host runs up to two steps
-    # ahead of the device (double-buffered read-back): it reads step k's results
-    # after issuing step k + 1, as a training loop that logs its loss would.
+    # ---- e2e: the training step as a user runs it, from host buffers: the
+    # step's inputs (targets and plane poses) copied from pinned host memory, and
+    # its loss and status read back into pinned host memory, every step. The step
+    # is captured once per targets buffer (two device buffers: the next step's
+    # targets are copied on their own stream while the current step runs) and
+    # replayed; the plane poses are copied on the step's stream before each
+    # replay. The host runs up to two steps ahead of the device (double-buffered
+    # read-back): it reads step k's results after issuing step k + 1, as a
+    # training loop that logs its loss would.
     h_targets = torch.from_numpy(target).pin_memory()
     h_planes = torch.from_numpy(r.host_planes.view(np.uint8).copy()).pin_memory()
     h_loss = torch.zeros((2, 1), dtype=torch.float32).pin_memory()
     h_st = torch.zeros((2, 64), dtype=torch.uint8).pin_memory()
     copy_s = torch.cuda.Stream()
-    targets_in = torch.cuda.Event()
+    targets_in = [torch.cuda.Event(), torch.cuda.Event()]
     done = [torch.cuda.Event(), torch.cuda.Event()]
+    tbuf = [step.targets, torch.empty_like(step.targets)]
     for attempt in range(3):
         restore()
-        with torch.cuda.stream(s):
-            for k in range(args.warmup):
+        s.wait_stream(torch.cuda.current_stream())
+        graphs = []
+        for b in range(2):
+            step.targets = tbuf[b]
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
                 reset_on(s)
-                step.enqueue(s)
-        s.synchronize()
+                if world > 1:
+                    step.enqueue_local(s)  # the all-reduce runs eagerly after the replay
+                else:
+                    step.enqueue(s)
+            graphs.append(g)
+        step.targets = tbuf[0]
         e2e_st, e2e_loss = [], []
 
         def collect(b):
@@ -491,26 +505,34 @@ def run_ours(args):
             e2e_st.append(B.ug_ws_status.from_buffer_copy(h_st[b].numpy().tobytes()))
             e2e_loss.append(float(h_loss[b, 0]))
 
+        def one(k):
+            b = k % 2
+            # this buffer was last read by step k - 2
+            with torch.cuda.stream(copy_s):
+                if k >= 2:
+                    copy_s.wait_event(done[b])
+                tbuf[b].copy_(h_targets, non_blocking=True)
+                targets_in[b].record(copy_s)
+            r.d_planes.copy_(h_planes, non_blocking=True)
+            s.wait_event(targets_in[b])
+            graphs[b].replay()
+            if world > 1:
+                step.enqueue_update(s)
+            h_loss[b].copy_(step.loss[:1], non_blocking=True)
+            B.ug_read_status(r.plan, r.ws, h_st[b], s)
+            done[b].record(s)
+
+        with torch.cuda.stream(s):
+            for k in range(args.warmup):
+                one(k)
+        s.synchronize()
+        e2e_st, e2e_loss = [], []
         t0 = time.perf_counter()
         with torch.cuda.stream(s):
             for k in range(args.steps):
-                b = k % 2
                 if k >= 2:
-                    collect(b)  # step k - 2's results; its buffers are then free
-                # the targets travel on their own stream while the step renders
-                # (after the previous step, which reads them, has ended); the
-                # loss waits for them
-                with torch.cuda.stream(copy_s):
-                    if k >= 1:
-                        copy_s.wait_event(done[1 - b])
-                    step.targets.copy_(h_targets, non_blocking=True)
-                    targets_in.record(copy_s)
-                r.d_planes.copy_(h_planes, non_blocking=True)
-                reset_on(s)
-                step.enqueue(s, targets_ready=targets_in)
-                h_loss[b].copy_(step.loss[:1], non_blocking=True)
-                B.ug_read_status(r.plan, r.ws, h_st[b], s)
-                done[b].record(s)
+                    collect(k % 2)  # step k - 2's results; its buffers are then free
+                one(k)
             for k in range(max(args.steps - 2, 0), args.steps):
                 collect(k % 2)
         e2e_s = (time.perf_counter() - t0) / args.steps
