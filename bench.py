@@ -608,10 +608,13 @@ def run_ours(args):
         # 200k training workload (its own Gaussians, poses and targets)
         del step, renderer, r, graph
         torch.cuda.empty_cache()
-        tc = train_compare(args.compare_steps, 3)
+        tc = train_compare(args.compare_steps, 3, int(cfg.tile), int(cfg.variant),
+                           int(cfg.variant_bwd))
         acc = tc["accuracy"]
         lm = acc["loss_mean_last"]
         batching = {"workload": tc["config"]["workload"], "steps": tc["steps"],
+                    "tile": tc["config"]["tile"], "variant": tc["config"]["variant"],
+                    "variant_bwd": tc["config"]["variant_bwd"],
                     "batched_ms_per_step": tc["ms_per_step"],
                     "per_plane_ms_per_step": tc["per_plane"]["ms_per_step"],
                     "factor": tc["speedup"],
@@ -653,18 +656,21 @@ def run_ours(args):
 
 # ---------------------------------------------------------------- batching
 def run_train_compare(args):
-    print(json.dumps(train_compare(args.steps, args.warmup)), flush=True)
+    print(json.dumps(train_compare(args.steps, args.warmup, args.tile, args.variant,
+                                   args.variant_bwd)), flush=True)
     return 0
 
 
-def train_compare(K, W):
+def train_compare(K, W, tile=16, variant=0, variant_bwd=0):
     """Training workload (200,000 Gaussians in the paper's initialisation,
     fitted to a hidden 100,000-Gaussian volume on 32 sweep poses of 256x256 per
     step): the batched step (all 32 planes per launch, the whole step captured
     in one CUDA graph) against the plain form (preprocess, sort, render and
     backward launched plane by plane, gradients summed, then Adam), from the
     same initial state over the same pose schedule. Reports both step times,
-    the speed-up and the difference of the two loss trajectories."""
+    the speed-up and the difference of the two loss trajectories. Both forms
+    use the same tile edge and rasterizer variants (in the default bench line,
+    the autotuner's choice on the bench workload)."""
     import torch
     from paper_2505_05643_gb300 import binding as B
     from paper_2505_05643_gb300 import render as R
@@ -676,7 +682,8 @@ def train_compare(K, W):
     n, P, pool = len(g["logit"]), 32, len(poses["size"])
     npx = int(poses["size"][0, 0] * poses["size"][0, 1])
     windows = [[(P * k + j) % pool for j in range(P)] for k in range(pool // P)]
-    cfg = R.make_config(cov_param=B.UG_COV_TRI)
+    cfg = R.make_config(cov_param=B.UG_COV_TRI, tile=tile, variant=variant,
+                        variant_bwd=variant_bwd)
     # targets on every pose of the pool (untimed)
     hid = R.Renderer(len(hidden["logit"]), poses, R.make_config(cov_param=B.UG_COV_SCALE_ROT))
     tpool, _ = hid.forward(torch.from_numpy(R.pack_params(hidden, B.UG_COV_SCALE_ROT)).to(dev))
