@@ -126,6 +126,35 @@ def test_grad_extreme_anisotropy():
     _check_grads(gpu, gref, gabs, oracle.param_names(0), "aniso cut")
 
 
+def test_grad_needles_thinner_than_2e_minus_20_pixels():
+    """Records whose pixel-unit factor r11 exceeds 2^20 (needles a million
+    times thinner than a pixel) take the backward's ten-operation pixel loop
+    (the nine-operation form needs every t1^2 of the footprint finite). Their
+    box decisions sit within rounding of a pixel edge, so the oracle counts them
+    as ambiguous; the test checks that the records exist, that every gradient
+    entry is finite, and that the other Gaussians match the oracle."""
+    rng = np.random.default_rng(41)
+    g = synth.gaussians_scale_rot(rng, 600, 0.05, 0.2)
+    g["mean"] *= 0.5
+    k = 40  # needles: thin along x, on the plane z = 0, centred on pixel columns
+    cols = rng.integers(4, 28, k)
+    g["mean"][0, :k] = ((cols + 0.5 - 16) / 16).astype(np.float32)
+    g["mean"][1, :k] = rng.uniform(-0.5, 0.5, k).astype(np.float32)
+    g["mean"][2, :k] = 0.0
+    g["log_scale"][:, :k] = np.log(np.array([[1e-9], [0.1], [0.1]], np.float32))
+    g["quat"][:, :k] = np.array([[1.0], [0.0], [0.0], [0.0]], np.float32)
+    pl = synth._pack_planes(np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]]),
+                            np.array([[0.0, 1.0, 0.0]]), [(32, 32)])
+    target = rng.uniform(0, 1, pl["total_pixels"])
+    cfg = R.make_config(cov_param=B.UG_COV_SCALE_ROT, tile=16, variant=5, variant_bwd=5)
+    gpu, gref, gabs, grads = _backward_case(g, pl, cfg, target)
+    r, _, _, _ = gpu_render(g, pl, cfg)
+    dv = r.debug_views()
+    assert (dv["rec_a"][:, 2] > 2.0 ** 20).sum() >= k // 2
+    assert torch.isfinite(grads).all()
+    _check_grads(gpu, gref, gabs, oracle.param_names(1), "needles")
+
+
 @pytest.mark.parametrize("tile,variant", [(16, v) for v in range(1, 6)] + [(8, 0), (8, 1)])
 def test_grad_variants(tile, variant):
     """Every compiled backward variant (footprint height, stages, records per
