@@ -119,7 +119,8 @@ typedef struct {
   int32_t variant_bwd; /* backward rasterizer variant, 0 .. ug_num_variants_bwd(tile) - 1:
                           0 = 8-row footprints, 4 stages of 128 records (default), 1 = 4-row
                           footprints; tile 16 also 2 = 3 stages of 128 (more resident
-                          blocks), 3 = 4 stages of 64, 4 = 3 stages of 256 */
+                          blocks), 3 = 4 stages of 64, 4 = 3 stages of 256, 5 = 4 stages
+                          of 128 with three resident blocks (more registers a thread) */
   float fp32_reach;  /* the geometry also runs in extended precision when ||F||_F (|mu| +
                         max |o|) exceeds this (F the Gaussian's precision factor, o the plane
                         origins): FP32 differences mu - o then lose the bits that thin or
