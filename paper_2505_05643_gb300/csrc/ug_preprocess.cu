@@ -7,18 +7,23 @@
 //              structure-of-arrays loads) walks all planes (staged in shared
 //              memory) and sets one candidate bit per (plane, Gaussian) with a
 //              conservative FP32 test that carries a rigorous rounding bound:
-//              it only drops pairs that the exact test would drop too.
+//              it only drops pairs that the exact test would drop too. It adds
+//              the candidate counts to the next scan's block partials.
 //  2. scan     of the candidate counts in (chunk, plane) order: every
 //              candidate gets its record slot, so for any plane the records,
 //              and after the stable sort the tile lists, are in ascending
 //              Gaussian order.
 //  3. list     writes the candidates into a work list, FP32 part first, then
-//              the FP64 part.
-//  4. records  one thread per list entry: the exact FP32 or FP64 geometry
-//              (phase 1, box, in-plane conic, peak weight) and the record;
-//              candidates that the exact test rejects become empty slots.
-//  5. scan     of the records' tile counts, then emit the (tile, record)
-//              instances, one thread per record.
+//              the extended-precision part.
+//  4. records  one thread per list entry: the exact FP32 or double-word
+//              geometry (phase 1, box, in-plane conic, peak weight) and the
+//              record; candidates that the exact test rejects become empty
+//              slots.
+//  5. live     one warp per 32 record slots counts each record's box tiles
+//              that can hold a non-zero weight (adding them to the next scan's
+//              block partials); the scan gives every record its first instance,
+//              and the emit writes the (tile, record) instances, a warp's 32
+//              records' instances spread over its lanes.
 // The backward chain is one thread per record (per-record parameter
 // gradients), then a per-Gaussian gather in the same slot order: no atomics,
 // deterministic.
