@@ -451,9 +451,9 @@ constexpr float kFarCol = 1099511627776.f;  // 2^40
 // (CUT) get w = 0, never a NaN: every factor that multiplies w stays finite.
 // The fast form takes sum g t1^2 from the exponent n = t1^2 + t2^2 - lw2 the
 // weight needs anyway (nine packed operations per column and row pair
-// instead of ten); the rounding of n then costs about 2^-23 |t2^2 - lw2| of
-// the row's sum of |g|, which the exponent range of a non-zero weight keeps
-// near 2^-16 of it.
+// instead of ten); the roundings of n and of the row's sums then cost below
+// 2^-19 (t2^2 - lw2) times the row's sum of |g|, and t2^2 - lw2 <= 150 in a
+// row with a non-zero weight.
 template <int FH, int CUT, bool TAIL = false>
 __device__ __forceinline__ void bwd_item(const float4& a, const float4& bb, const float4& cr,
                                          uint2 bx, uint32_t cl, uint32_t rid,
